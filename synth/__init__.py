@@ -1,0 +1,141 @@
+"""Seeded synthetic inputs shared by the tests, the oracle checks and the benchmark.
+
+This module holds no contraction arithmetic: it only turns (seed, tensor id, element index)
+into numbers.  The generator is counter based, so any element can be produced on its own and
+the bits do not depend on numpy, torch or libm versions.
+
+Generator: SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+generators", OOPSLA 2014).  The value for counter ``n`` of a stream with key ``k`` is the
+SplitMix64 output function applied to ``k + (n + 1) * GAMMA``; the stream key itself is the
+output function applied to ``seed * GAMMA + tensor_id``.
+
+Layout convention: tensors are column-major (first label fastest).  As numpy arrays they are
+Fortran-ordered with ``shape[d]`` = extent of the d-th label; element ``n`` of the stream is
+the element with column-major linear index ``n``.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+GAMMA = 0x9E3779B97F4A7C15
+_M1 = 0xBF58476D1CE4E5B9
+_M2 = 0x94D049BB133111EB
+_MASK = (1 << 64) - 1
+_CHUNK = 1 << 22
+
+
+def mix64_int(z: int) -> int:
+    """SplitMix64 output function on one Python int (mod 2**64)."""
+    z &= _MASK
+    z = ((z ^ (z >> 30)) * _M1) & _MASK
+    z = ((z ^ (z >> 27)) * _M2) & _MASK
+    return z ^ (z >> 31)
+
+
+def stream_key(seed: int, tensor_id: int) -> int:
+    return mix64_int((seed * GAMMA + tensor_id) & _MASK)
+
+
+def _mix64_np(z: np.ndarray) -> np.ndarray:
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(_M1)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(_M2)
+        return z ^ (z >> np.uint64(31))
+
+
+def raw_bits(seed: int, tensor_id: int, start: int, count: int) -> np.ndarray:
+    """uint64 stream values for counters start .. start+count-1."""
+    key = np.uint64(stream_key(seed, tensor_id))
+    n = np.arange(start + 1, start + count + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        return _mix64_np(key + n * np.uint64(GAMMA))
+
+
+def _fill(count: int, fn) -> np.ndarray:
+    out = np.empty(count, dtype=np.float64)
+    for s in range(0, count, _CHUNK):
+        e = min(count, s + _CHUNK)
+        out[s:e] = fn(s, e - s)
+    return out
+
+
+def uniform(seed: int, tensor_id: int, count: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
+    """float64 values in [lo, hi): top 53 bits of each stream value as a fraction."""
+    def f(s, c):
+        u = (raw_bits(seed, tensor_id, s, c) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+        return lo + (hi - lo) * u
+    return _fill(count, f)
+
+
+def normal(seed: int, tensor_id: int, count: int, std: float = 1.0) -> np.ndarray:
+    """float64 normal(0, std) by the Box-Muller transform on counter pairs (2n, 2n+1)."""
+    def f(s, c):
+        bits = raw_bits(seed, tensor_id, 2 * s, 2 * c)
+        u = ((bits >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53  # (0, 1)
+        u1, u2 = u[0::2], u[1::2]
+        return std * np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    return _fill(count, f)
+
+
+def integers(seed: int, tensor_id: int, count: int, lo: int, hi: int) -> np.ndarray:
+    """float64 integers uniform in [lo, hi] (inclusive); exact in every float format used."""
+    span = hi - lo + 1
+    def f(s, c):
+        return (raw_bits(seed, tensor_id, s, c) % np.uint64(span)).astype(np.float64) + lo
+    return _fill(count, f)
+
+
+def tensor(extents, seed: int, tensor_id: int, kind: str = "uniform", dtype=np.float64,
+           scale: float = 1.0, **kw) -> np.ndarray:
+    """Column-major (Fortran-ordered) tensor of the given extents.
+
+    kind: "uniform" ([-1,1) times scale), "normal" (std = scale), "int" (integers in
+    [kw lo, kw hi]), "ones".
+    """
+    extents = tuple(int(e) for e in extents)
+    count = int(np.prod(extents, dtype=np.int64)) if extents else 1
+    if kind == "uniform":
+        v = uniform(seed, tensor_id, count) * scale
+    elif kind == "normal":
+        v = normal(seed, tensor_id, count, std=scale)
+    elif kind == "int":
+        v = integers(seed, tensor_id, count, kw.get("lo", -4), kw.get("hi", 4))
+    elif kind == "ones":
+        v = np.ones(count)
+    else:
+        raise ValueError(kind)
+    return np.asfortranarray(v.astype(dtype).reshape(extents, order="F"))
+
+
+def uniform_extents(seed: int, tensor_id: int, count: int, lo: int, hi: int) -> np.ndarray:
+    """int64 extents uniform in [lo, hi] (inclusive)."""
+    return integers(seed, tensor_id, count, lo, hi).astype(np.int64)
+
+
+# --- the same generator on a torch device (for inputs too large to build on the host) ----------
+
+def torch_uniform(seed: int, tensor_id: int, count: int, device, dtype=None, scale: float = 1.0):
+    """Bit-identical to ``uniform(...) * scale`` but built on ``device`` with int64 arithmetic
+    (two's-complement wraparound; logical shifts emulated with masks)."""
+    import torch
+    key = stream_key(seed, tensor_id)
+    key_s = key - (1 << 64) if key >= (1 << 63) else key
+    out = torch.empty(count, dtype=torch.float64, device=device)
+    g = GAMMA - (1 << 64)
+    m1 = _M1 - (1 << 64)
+    m2 = _M2 - (1 << 64)
+
+    def lsr(z, s):
+        return (z >> s) & ((1 << (64 - s)) - 1)
+
+    step = 1 << 24
+    for s in range(0, count, step):
+        c = min(count, s + step) - s
+        n = torch.arange(s + 1, s + c + 1, dtype=torch.int64, device=device)
+        z = n * g + key_s
+        z = (z ^ lsr(z, 30)) * m1
+        z = (z ^ lsr(z, 27)) * m2
+        z = z ^ lsr(z, 31)
+        u = lsr(z, 11).to(torch.float64) * 2.0 ** -53
+        out[s:s + c] = (-1.0 + 2.0 * u) * scale
+    return out if dtype is None else out.to(dtype)
