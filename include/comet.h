@@ -1,0 +1,226 @@
+/*
+ * comet.h — C ABI of the GB300 tensor-contraction library.
+ *
+ * The library evaluates dense tensor contractions written in index (Einstein) notation, the
+ * operation of the COMET paper (Section 2, "Tensor Contractions"; the operation grammar of
+ * Fig. 2b), by the transpose-transpose-GEMM-transpose (TTGT) reformulation of Section 2 and
+ * Section 6 ("TTGT", "Optimal permutation for TTGT"), with the multi-operand ordering of
+ * Section 6 ("Multi-Operand Expression") and the transpose of Section 6 ("Transpose
+ * optimization").  All device work runs in the library's own sm_103a kernels.
+ *
+ * Conventions shared by every entry point
+ *   Layout     Every tensor is dense and column-major in the label order written in the
+ *              expression: the first label has stride 1.  (A tensor declared with labels
+ *              [k,a,c,i] and extents (64,192,192,64) has element (k,a,c,i) at linear
+ *              position k + 64*(a + 192*(c + 192*i)).)
+ *   Ownership  The caller owns every device buffer and the stream.  A plan owns host memory
+ *              only.  Scratch space ("workspace") is allocated by the caller, sized by
+ *              comet_plan_workspace().  No entry point allocates device memory.
+ *   Pointers   Device pointers must be 16-byte aligned (COMET_ERR_ALIGN otherwise).
+ *   Streams    `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *              Work is enqueued asynchronously; nothing synchronises the host except
+ *              comet_sync_status() and comet_contract_host().
+ *   Errors     Every call returns a status code; nothing aborts the process, throws across
+ *              the ABI or traps on the device.  A kernel whose internal wait runs out of time
+ *              records COMET_ERR_TIMEOUT in a device status word and returns; the code
+ *              surfaces at the next comet_sync_status().
+ *   Threads    Plans are immutable after comet_plan() and may be used from several host
+ *              threads at once.
+ */
+#ifndef COMET_H
+#define COMET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct comet_plan_s *comet_plan_t;
+
+typedef enum {
+    COMET_OK = 0,
+    COMET_ERR_PARSE = 1,        /* expression does not follow the grammar */
+    COMET_ERR_LABEL = 2,        /* label without extent, or output label not on the right */
+    COMET_ERR_SHAPE = 3,        /* non-positive or inconsistent extent, size overflow */
+    COMET_ERR_DTYPE = 4,        /* unknown dtype or operands of different dtypes */
+    COMET_ERR_UNSUPPORTED = 5,  /* valid expression outside what the kernels implement */
+    COMET_ERR_ALIGN = 6,        /* device pointer not 16-byte aligned */
+    COMET_ERR_NULL = 7,         /* required pointer is NULL */
+    COMET_ERR_WORKSPACE = 8,    /* workspace missing or smaller than the plan needs */
+    COMET_ERR_CUDA = 9,         /* a CUDA runtime call failed (no device, launch error...) */
+    COMET_ERR_TIMEOUT = 10,     /* a device-side wait ran out of time (see comet_sync_status) */
+    COMET_ERR_INTERNAL = 11,
+    COMET_ERR_ARG = 12          /* an argument is out of range */
+} comet_status_t;
+
+typedef enum { COMET_F32 = 0, COMET_F64 = 1 } comet_dtype_t;
+
+typedef enum {
+    /* FP64 arithmetic: FP64 tensor-core MMA (mma.sync f64) with FP64 accumulation.  For
+       FP32-stored operands the values are widened exactly and the result rounded once. */
+    COMET_PREC_NATIVE = 0,
+    /* Split precision: each operand element x is split into three bfloat16 parts
+       hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid); six of the nine part products
+       (hh, hm, mh, hl, lh, mm) run on the tcgen05 tensor cores with FP32 accumulation in
+       tensor memory.  Target: normwise relative error <= 1e-6 against FP64. */
+    COMET_PREC_SPLIT_BF16 = 1
+} comet_precision_t;
+
+typedef enum {
+    COMET_ORDER_PLANNED = 0,    /* Section 6: fewest operations, ties broken deterministically */
+    COMET_ORDER_NATURAL = 1     /* left to right, the baseline of Table 1 */
+} comet_order_t;
+
+typedef struct {
+    const char *label;          /* label name as written in the expression */
+    int64_t extent;             /* > 0 */
+} comet_extent_t;
+
+typedef struct {
+    comet_precision_t precision;
+    comet_order_t order;
+    double alpha;               /* extra scale, multiplied into the expression's own alpha */
+    size_t workspace_cap;       /* 0 = unlimited; intermediates above it are refused */
+    int form;                   /* -1 = planner's choice; k >= 0 = k-th enumerated TTGT form
+                                   of every binary step (for the permutation ablation) */
+    int64_t kc;                 /* split path: K elements per FP32 accumulation chunk before
+                                   the chunk is added into the compensated sum (0 = whole K) */
+    int64_t timeout_ms;         /* device-side wait limit; 0 = default (2000 ms) */
+    int debug_flags;            /* bit 0: withhold one operand load in the split GEMM so that
+                                   its wait runs out (fault-injection test); others reserved */
+} comet_plan_opts_t;
+
+/* Fills *opts with the defaults: NATIVE precision, planned order, alpha 1, no cap, planner's
+ * form, kc 0, default timeout, no debug flags. */
+void comet_plan_opts_default(comet_plan_opts_t *opts);
+
+/*
+ * comet_plan — parse, classify and plan a contraction (Section 2; Section 5 ops ta.tc,
+ * ta.mult, ta.set; Section 6 TTGT, permutation choice and multi-operand order).
+ *
+ *   expr       "C[i,a,j,b] = A[k,a,c,i] * B[c,b,k,j]".  Accepted forms (Fig. 2b):
+ *              lhs "=", "+=" or "-=" rhs; rhs is an optional numeric alpha followed by one
+ *              or more labelled tensors joined by "*"; an optional "sum_{k,c}" after the
+ *              assignment names the summed labels and is checked.  Labels may be written in
+ *              [] or ().  The summed labels are those on the right that are not on the left.
+ *   extents    n_extents (label, extent) pairs covering every label of the expression.
+ *   dtypes     n_dtypes entries: one per right-hand operand, then the output.  All equal.
+ *   opts       NULL = defaults.
+ *   out_plan   receives the plan; release it with comet_plan_destroy().
+ *
+ * Supported: one operand (scaled copy / transpose, ta.copy) and two or more operands with
+ * every label in exactly two of {operands, output} (a binary tree of ta.tc steps).
+ * Labels in all three tensors (batch labels), repeated labels inside one tensor and labels
+ * summed inside a single operand give COMET_ERR_UNSUPPORTED.  No device work, no GPU needed.
+ */
+comet_status_t comet_plan(const char *expr, const comet_extent_t *extents, int n_extents,
+                          const comet_dtype_t *dtypes, int n_dtypes,
+                          const comet_plan_opts_t *opts, comet_plan_t *out_plan);
+
+/* Bytes of device workspace comet_contract() needs for this plan (may be 0). */
+comet_status_t comet_plan_workspace(comet_plan_t plan, size_t *bytes);
+
+/* Algorithmic flop count of the planned evaluation: sum over binary steps of
+ * 2 * product of the extents of all labels of the step. */
+comet_status_t comet_plan_flops(comet_plan_t plan, double *flops);
+
+/* Flop count the natural left-to-right order would need (the Table 1 baseline). */
+comet_status_t comet_plan_flops_natural(comet_plan_t plan, double *flops);
+
+/* Human-readable JSON description of the plan: steps, operand order, the M/N/K label groups
+ * and their order, the chosen form among those enumerated, costs.  Writes at most len bytes
+ * including the terminating NUL; COMET_ERR_ARG if it does not fit. */
+comet_status_t comet_plan_describe(comet_plan_t plan, char *buf, size_t len);
+
+/*
+ * comet_contract — evaluate the plan on device buffers (asynchronous on `stream`).
+ *   inputs     one device pointer per right-hand operand, in expression order.
+ *   output     device pointer to the left-hand tensor; read as well when the operator is
+ *              "+=" or "-=".
+ *   workspace  device scratch of at least comet_plan_workspace() bytes (may be NULL if 0).
+ * Output and inputs must not overlap.  Launch errors return COMET_ERR_CUDA.
+ */
+comet_status_t comet_contract(comet_plan_t plan, const void *const *inputs, void *output,
+                              void *workspace, void *stream);
+
+/*
+ * comet_contract_host — the same evaluation from host buffers: copies every input from host
+ * to the caller's device buffers, runs comet_contract() and copies the output back, all on
+ * `stream`, then synchronises the stream.  host_* may be pageable or pinned host memory;
+ * dev_* are caller-owned device buffers of the operands' sizes.  For "+=" / "-=" the host
+ * output is copied to the device first.  Returns the first error, including a device status
+ * word set by a kernel (as comet_sync_status()).
+ */
+comet_status_t comet_contract_host(comet_plan_t plan, const void *const *host_inputs,
+                                   void *host_output, void *const *dev_inputs, void *dev_output,
+                                   void *workspace, void *stream);
+
+/*
+ * comet_transpose — pure permutation of a dense tensor (Section 6, "Transpose optimization";
+ * the ta.copy of Section 5 with alpha = 1).  Elements are moved as raw 4- or 8-byte words,
+ * so the result is bit-exact (NaN payloads, -0.0, subnormals survive).
+ *   rank       1 .. 8
+ *   extents    input extents, column-major (extents[0] has stride 1)
+ *   perm       output dimension d is input dimension perm[d]: out.extent[d] =
+ *              extents[perm[d]] and out[j_0..j_{r-1}] = in[i] with i[perm[d]] = j_d
+ *   in, out    device buffers of prod(extents) elements; must not overlap
+ */
+comet_status_t comet_transpose(int rank, const int64_t *extents, const int *perm,
+                               comet_dtype_t dtype, const void *in, void *out, void *stream);
+
+/*
+ * Batched triples-like blocks (one persistent launch for many small, uneven contractions of
+ * the same expression; the 6-D triples output of Section 2's CCSD(T) remark).
+ *
+ * comet_plan_batched — expr must be a two-operand contraction.  label_names lists the
+ *   n_labels labels; extents is an n_blocks x n_labels row-major table (block b, label l at
+ *   extents[b*n_labels + l]).  dtypes as in comet_plan.  tile_hint: -1 = autotuned choice
+ *   (from the in-process cache, else the default), k >= 0 = k-th tile configuration.
+ */
+comet_status_t comet_plan_batched(const char *expr, int n_blocks, const char *const *label_names,
+                                  int n_labels, const int64_t *extents,
+                                  const comet_dtype_t *dtypes, int n_dtypes,
+                                  const comet_plan_opts_t *opts, int tile_hint,
+                                  comet_plan_t *out_plan);
+
+/* Number of tile configurations comet_plan_batched() accepts as tile_hint. */
+int comet_batched_num_tiles(void);
+
+/*
+ * comet_contract_batched — run every block in one persistent launch.
+ *   block_inputs   device array of n_blocks * n_in device pointers (block-major).
+ *   mode 0 (reduce): `result` is a device array of 2*n_blocks doubles; block b gets
+ *                  s_b = sum T*W and q_b = sum T^2 over its output T, with the weight W of the
+ *                  element with column-major linear index n given by
+ *                  h = fmix32(weight_key ^ fmix32(b * 0x9E3779B9 + n)) (MurmurHash3
+ *                  finalizer), W = (h >> 8) * 2^-23 - 1.  T is never stored.
+ *   mode 1 (store):  `result` is a device array of n_blocks device pointers; block b's output
+ *                  is written there in full (blocks whose pointer is NULL are skipped).
+ *   workspace      comet_plan_workspace() bytes.
+ */
+comet_status_t comet_contract_batched(comet_plan_t plan, const void *const *block_inputs,
+                                      int mode, void *result, uint32_t weight_key,
+                                      void *workspace, void *stream);
+
+/* Synchronises `stream`, then reads and clears the device status word: COMET_OK, or
+ * COMET_ERR_TIMEOUT if a kernel's wait ran out, or COMET_ERR_CUDA if the stream reported an
+ * error. */
+comet_status_t comet_sync_status(void *stream);
+
+void comet_plan_destroy(comet_plan_t plan);
+
+const char *comet_status_string(comet_status_t status);
+
+/* Detail of the last error returned to the calling host thread (empty if none). */
+const char *comet_last_error_message(void);
+
+/* Library version string. */
+const char *comet_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COMET_H */

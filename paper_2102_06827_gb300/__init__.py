@@ -1,0 +1,190 @@
+"""GB300 dense tensor contractions in index notation (COMET method, arXiv 2102.06827).
+
+Thin Python binding of the C ABI declared in include/comet.h.  Every step of a contraction
+runs in the library's sm_103a kernels; this module only marshals arguments.  PyTorch provides
+device memory and streams.  There is no CPU fallback: without the built library every entry
+point raises.
+
+Layout convention of the C ABI: column-major in the label order of the expression.  A
+column-major tensor with extents (e0, e1, ..., e_{r-1}) is a contiguous torch tensor of shape
+(e_{r-1}, ..., e1, e0); ``colmajor_empty`` makes one.  ``einsum`` (in ``autograd``) also
+accepts torch's own row-major convention.
+"""
+from __future__ import annotations
+
+import ctypes
+import re
+import json
+
+from . import _lib
+from ._lib import CometError, F32, F64, PREC_NATIVE, PREC_SPLIT_BF16, ORDER_NATURAL, ORDER_PLANNED
+
+__all__ = ["Plan", "BatchedPlan", "transpose", "sync_status", "colmajor_empty", "CometError",
+           "lib", "version", "PREC_NATIVE", "PREC_SPLIT_BF16", "F32", "F64"]
+
+
+def lib():
+    return _lib.load()
+
+
+def version() -> str:
+    return lib().comet_version().decode()
+
+
+def _dtype_code(dtype) -> int:
+    import torch
+    if dtype in (torch.float32, "f32", "float32", F32):
+        return F32
+    if dtype in (torch.float64, "f64", "float64", F64):
+        return F64
+    raise ValueError(f"unsupported dtype {dtype}")
+
+
+def _torch_dtype(code: int):
+    import torch
+    return torch.float32 if code == F32 else torch.float64
+
+
+def _prec_code(p) -> int:
+    if p in ("native", "fp64", PREC_NATIVE, None):
+        return PREC_NATIVE
+    if p in ("split_bf16", "split", PREC_SPLIT_BF16):
+        return PREC_SPLIT_BF16
+    raise ValueError(f"unknown precision {p}")
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def colmajor_empty(extents, dtype, device="cuda"):
+    """Contiguous torch tensor holding a column-major tensor of the given extents."""
+    import torch
+    return torch.empty(tuple(reversed([int(e) for e in extents])), dtype=dtype, device=device)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if t is None:
+        return ctypes.c_void_p(0)
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """comet_plan(): a planned contraction.
+
+    expr     "C[i,a,j,b] = A[k,a,c,i] * B[c,b,k,j]" (also "+=", "-=", "alpha * ...",
+             "sum_{k,c}" and 1..12 operands)
+    extents  {label: extent}
+    dtype    torch.float32 / torch.float64 (all operands)
+    """
+
+    def __init__(self, expr: str, extents: dict, dtype, precision="native", order="planned",
+                 alpha: float = 1.0, workspace_cap: int = 0, form: int = -1, kc: int = 0,
+                 timeout_ms: int = 0, debug_flags: int = 0):
+        L = lib()
+        self.expr = expr
+        self.extents = {str(k): int(v) for k, v in extents.items()}
+        self.dtype_code = _dtype_code(dtype)
+        self.dtype = _torch_dtype(self.dtype_code)
+        rhs = expr.split("=", 1)[1] if "=" in expr else ""
+        n_ops = len(re.findall(r"[A-Za-z_]\w*\s*[\[(]", rhs))
+        self.n_in = n_ops
+        ext = (_lib.Extent * max(1, len(self.extents)))(
+            *[_lib.Extent(k.encode(), v) for k, v in self.extents.items()])
+        dts = (ctypes.c_int * (n_ops + 1))(*([self.dtype_code] * (n_ops + 1)))
+        opts = _lib.PlanOpts()
+        L.comet_plan_opts_default(ctypes.byref(opts))
+        opts.precision = _prec_code(precision)
+        opts.order = ORDER_NATURAL if order == "natural" else ORDER_PLANNED
+        opts.alpha = alpha
+        opts.workspace_cap = workspace_cap
+        opts.form = form
+        opts.kc = kc
+        opts.timeout_ms = timeout_ms
+        opts.debug_flags = debug_flags
+        self.precision = opts.precision
+        h = ctypes.c_void_p()
+        _lib.check(L.comet_plan(expr.encode(), ext, len(self.extents), dts, n_ops + 1,
+                                ctypes.byref(opts), ctypes.byref(h)), "comet_plan")
+        self._h = h
+        ws = ctypes.c_size_t()
+        _lib.check(L.comet_plan_workspace(h, ctypes.byref(ws)), "comet_plan_workspace")
+        self.workspace_bytes = ws.value
+        f = ctypes.c_double()
+        _lib.check(L.comet_plan_flops(h, ctypes.byref(f)), "comet_plan_flops")
+        self.flops = f.value
+        _lib.check(L.comet_plan_flops_natural(h, ctypes.byref(f)), "comet_plan_flops_natural")
+        self.flops_natural = f.value
+        self.info = self.describe()
+
+    def describe(self) -> dict:
+        buf = ctypes.create_string_buffer(1 << 16)
+        _lib.check(lib().comet_plan_describe(self._h, buf, len(buf)), "comet_plan_describe")
+        return json.loads(buf.value.decode())
+
+    def workspace(self, device="cuda"):
+        """A caller-owned workspace buffer of the plan's size (torch allocation)."""
+        import torch
+        if self.workspace_bytes == 0:
+            return None
+        return torch.empty(self.workspace_bytes, dtype=torch.uint8, device=device)
+
+    def contract(self, inputs, output, workspace=None, stream=None):
+        """comet_contract(): device tensors in, device output tensor written (async)."""
+        if len(inputs) != self.n_in:
+            raise ValueError(f"{self.n_in} inputs expected")
+        arr = (ctypes.c_void_p * self.n_in)(*[t.data_ptr() for t in inputs])
+        _lib.check(lib().comet_contract(self._h, arr, _ptr(output), _ptr(workspace),
+                                        _stream_handle(stream)), "comet_contract")
+        return output
+
+    def contract_host(self, host_inputs, host_output, dev_inputs, dev_output, workspace=None, stream=None):
+        """comet_contract_host(): host buffers (numpy arrays or CPU tensors, column-major
+        memory) copied in, contracted, copied back; synchronises the stream."""
+        def hp(x):
+            return ctypes.c_void_p(x.ctypes.data if hasattr(x, "ctypes") else x.data_ptr())
+        hin = (ctypes.c_void_p * self.n_in)(*[hp(x).value for x in host_inputs])
+        din = (ctypes.c_void_p * self.n_in)(*[t.data_ptr() for t in dev_inputs])
+        _lib.check(lib().comet_contract_host(self._h, hin, hp(host_output), din, _ptr(dev_output),
+                                             _ptr(workspace), _stream_handle(stream)),
+                   "comet_contract_host")
+        return host_output
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().comet_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def transpose(x, extents, perm, out=None, stream=None):
+    """comet_transpose(): bit-exact permutation of a column-major tensor.
+
+    out.extent[d] = extents[perm[d]]; returns ``out`` (allocated column-major if None)."""
+    import torch
+    rank = len(extents)
+    if out is None:
+        out = colmajor_empty([extents[p] for p in perm], x.dtype, x.device)
+    ext = (ctypes.c_int64 * rank)(*[int(e) for e in extents])
+    pm = (ctypes.c_int * rank)(*[int(p) for p in perm])
+    code = F32 if x.dtype == torch.float32 else F64
+    _lib.check(lib().comet_transpose(rank, ext, pm, code, _ptr(x), _ptr(out), _stream_handle(stream)),
+               "comet_transpose")
+    return out
+
+
+def sync_status(stream=None):
+    """comet_sync_status(): synchronise and surface a device-side timeout."""
+    _lib.check(lib().comet_sync_status(_stream_handle(stream)), "comet_sync_status")

@@ -1,0 +1,290 @@
+// C ABI (include/comet.h): plan objects, dispatch of plan steps to the kernels, status word.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/comet.h"
+#include "batched.h"
+#include "launch.h"
+#include "plan.hpp"
+
+struct comet_plan_s {
+    comet::Plan p;
+};
+
+namespace comet {
+
+__device__ int g_status_word;
+
+static thread_local std::string t_last_error;
+
+static void set_error(const std::string &s) { t_last_error = s; }
+
+int *device_status_word() {
+    static std::mutex mu;
+    static int *ptrs[128] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptrs[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_status_word) != cudaSuccess) return nullptr;
+        ptrs[dev] = static_cast<int *>(p);
+    }
+    return ptrs[dev];
+}
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+static comet_status_t cuda_status(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return COMET_OK;
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return COMET_ERR_CUDA;
+}
+
+static int64_t timeout_ns(const Plan &P) {
+    int64_t ms = P.opts.timeout_ms > 0 ? P.opts.timeout_ms : 2000;
+    return ms * 1000000ll;
+}
+
+// pointer of a slot at launch time
+static void *slot_ptr(const Plan &P, int slot, const void *const *inputs, void *output, void *ws) {
+    const Slot &s = P.slots[slot];
+    if (s.kind == SLOT_INPUT) return const_cast<void *>(inputs[s.index]);
+    if (s.kind == SLOT_OUTPUT) return output;
+    return static_cast<char *>(ws) + s.ws_off;
+}
+
+static comet_status_t run_plan(const Plan &P, const void *const *inputs, void *output, void *ws,
+                               cudaStream_t stream) {
+    int *status = device_status_word();
+    if (!status) return cuda_status(cudaErrorNoDevice, "status word");
+    const int es = (int)dtype_size(P.dtype);
+    for (const Step &st : P.steps) {
+        double alpha = 1.0, beta = 0.0;
+        if (st.final_step) {
+            alpha = P.alpha;
+            if (P.op == 1) beta = 1.0;
+            if (P.op == 2) { alpha = -alpha; beta = 1.0; }
+        }
+        void *pa = slot_ptr(P, st.a, inputs, output, ws);
+        void *pc = slot_ptr(P, st.c, inputs, output, ws);
+        cudaError_t e = cudaSuccess;
+        if (st.kernel == KK_COPY) {
+            XposeParams x = st.copy;
+            x.in = pa; x.out = pc; x.alpha = alpha; x.beta = beta;
+            if (alpha == 1.0 && beta == 0.0) e = launch_move(x, es, st.copy_vec_in, st.copy_vec_out, stream);
+            else e = launch_scale(x, es, st.copy_vec_in, st.copy_vec_out, stream);
+            if (e != cudaSuccess) return cuda_status(e, "copy kernel");
+            continue;
+        }
+        void *pb = slot_ptr(P, st.b, inputs, output, ws);
+        GemmParams g = st.gemm;
+        g.A = st.form.swap ? pb : pa;
+        g.B = st.form.swap ? pa : pb;
+        g.C = pc;
+        g.alpha = alpha;
+        g.beta = beta;
+        g.status = status;
+        g.timeout_ns = timeout_ns(P);
+        if (st.kernel == KK_GEMM_F64) {
+            bool ak = g.k.n > 0 && (g.k.s0[0] == 1 || g.ma.n == 0 || (g.ma.s0[0] != 1 && g.k.s0[0] < g.ma.s0[0]));
+            bool bk = g.k.n > 0 && (g.k.s1[0] == 1 || g.nb.n == 0 || (g.nb.s0[0] != 1 && g.k.s1[0] < g.nb.s0[0]));
+            e = launch_gemm_f64(g, es, ak, bk, stream);
+            if (e != cudaSuccess) return cuda_status(e, "gemm_f64 kernel");
+        } else {
+            char *w = static_cast<char *>(ws);
+            XposeParams xa = st.pre_a, xb = st.pre_b;
+            xa.in = g.A; xa.out = w + st.ws_parts_a;
+            xb.in = g.B; xb.out = w + st.ws_parts_b;
+            e = launch_split(xa, es, st.pre_a_vec, st.pre_a_vout, stream);
+            if (e != cudaSuccess) return cuda_status(e, "split pre-pass (A)");
+            e = launch_split(xb, es, st.pre_b_vec, st.pre_b_vout, stream);
+            if (e != cudaSuccess) return cuda_status(e, "split pre-pass (B)");
+            e = launch_gemm_split(g, w + st.ws_parts_a, w + st.ws_parts_b, st.kpad, es, P.opts.debug_flags,
+                                  stream, 0);
+            if (e != cudaSuccess) return cuda_status(e, "split gemm kernel");
+        }
+    }
+    return COMET_OK;
+}
+
+}  // namespace comet
+
+using namespace comet;
+
+extern "C" {
+
+comet_status_t comet_plan(const char *expr, const comet_extent_t *extents, int n_extents,
+                          const comet_dtype_t *dtypes, int n_dtypes, const comet_plan_opts_t *opts,
+                          comet_plan_t *out_plan) {
+    if (!out_plan) return COMET_ERR_NULL;
+    *out_plan = nullptr;
+    comet_plan_s *h = new (std::nothrow) comet_plan_s;
+    if (!h) return COMET_ERR_INTERNAL;
+    std::string err;
+    comet_status_t st;
+    try {
+        st = build_plan(expr, extents, n_extents, dtypes, n_dtypes, opts, &h->p, &err);
+    } catch (...) {
+        st = COMET_ERR_INTERNAL;
+        err = "exception while planning";
+    }
+    if (st != COMET_OK) {
+        set_error(err);
+        delete h;
+        return st;
+    }
+    *out_plan = h;
+    return COMET_OK;
+}
+
+comet_status_t comet_plan_workspace(comet_plan_t plan, size_t *bytes) {
+    if (!plan || !bytes) return COMET_ERR_NULL;
+    *bytes = plan->p.batched ? plan->p.batched_ws : plan->p.workspace;
+    return COMET_OK;
+}
+
+comet_status_t comet_plan_flops(comet_plan_t plan, double *flops) {
+    if (!plan || !flops) return COMET_ERR_NULL;
+    *flops = plan->p.flops;
+    return COMET_OK;
+}
+
+comet_status_t comet_plan_flops_natural(comet_plan_t plan, double *flops) {
+    if (!plan || !flops) return COMET_ERR_NULL;
+    *flops = plan->p.flops_natural;
+    return COMET_OK;
+}
+
+comet_status_t comet_plan_describe(comet_plan_t plan, char *buf, size_t len) {
+    if (!plan || !buf) return COMET_ERR_NULL;
+    std::string s = plan->p.batched ? describe_batched(plan->p) : describe_plan(plan->p);
+    if (s.size() + 1 > len) return COMET_ERR_ARG;
+    std::memcpy(buf, s.c_str(), s.size() + 1);
+    return COMET_OK;
+}
+
+comet_status_t comet_contract(comet_plan_t plan, const void *const *inputs, void *output, void *workspace,
+                              void *stream) {
+    if (!plan || !inputs || !output) return COMET_ERR_NULL;
+    const Plan &P = plan->p;
+    if (P.batched) { set_error("batched plan: use comet_contract_batched"); return COMET_ERR_ARG; }
+    for (int i = 0; i < P.n_in; ++i) {
+        if (!inputs[i]) return COMET_ERR_NULL;
+        if (!aligned16(inputs[i])) return COMET_ERR_ALIGN;
+    }
+    if (!aligned16(output)) return COMET_ERR_ALIGN;
+    if (P.workspace > 0) {
+        if (!workspace) return COMET_ERR_WORKSPACE;
+        if (!aligned16(workspace)) return COMET_ERR_ALIGN;
+    }
+    return run_plan(P, inputs, output, workspace, static_cast<cudaStream_t>(stream));
+}
+
+comet_status_t comet_contract_host(comet_plan_t plan, const void *const *host_inputs, void *host_output,
+                                   void *const *dev_inputs, void *dev_output, void *workspace, void *stream) {
+    if (!plan || !host_inputs || !host_output || !dev_inputs || !dev_output) return COMET_ERR_NULL;
+    const Plan &P = plan->p;
+    if (P.batched) return COMET_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    size_t es = dtype_size(P.dtype);
+    for (int i = 0; i < P.n_in; ++i) {
+        if (!host_inputs[i] || !dev_inputs[i]) return COMET_ERR_NULL;
+        size_t bytes = (size_t)P.slots[i].elems * es;
+        comet_status_t st = cuda_status(cudaMemcpyAsync(dev_inputs[i], host_inputs[i], bytes,
+                                                        cudaMemcpyHostToDevice, s), "input copy");
+        if (st != COMET_OK) return st;
+    }
+    size_t out_bytes = 0;
+    for (auto &sl : P.slots) if (sl.kind == SLOT_OUTPUT) out_bytes = (size_t)sl.elems * es;
+    if (P.op != 0) {
+        comet_status_t st = cuda_status(cudaMemcpyAsync(dev_output, host_output, out_bytes,
+                                                        cudaMemcpyHostToDevice, s), "output copy in");
+        if (st != COMET_OK) return st;
+    }
+    comet_status_t st = comet_contract(plan, const_cast<const void *const *>(dev_inputs), dev_output, workspace, stream);
+    if (st != COMET_OK) return st;
+    st = cuda_status(cudaMemcpyAsync(host_output, dev_output, out_bytes, cudaMemcpyDeviceToHost, s), "output copy");
+    if (st != COMET_OK) return st;
+    return comet_sync_status(stream);
+}
+
+comet_status_t comet_transpose(int rank, const int64_t *extents, const int *perm, comet_dtype_t dtype,
+                               const void *in, void *out, void *stream) {
+    if (!extents || !perm || !in || !out) return COMET_ERR_NULL;
+    if (rank < 1 || rank > kMaxRank) return COMET_ERR_ARG;
+    if (dtype != COMET_F32 && dtype != COMET_F64) return COMET_ERR_DTYPE;
+    int seen[kMaxRank] = {0};
+    for (int d = 0; d < rank; ++d) {
+        if (perm[d] < 0 || perm[d] >= rank || seen[perm[d]]) return COMET_ERR_ARG;
+        seen[perm[d]] = 1;
+        if (extents[d] <= 0) return COMET_ERR_SHAPE;
+    }
+    if (!aligned16(in) || !aligned16(out)) return COMET_ERR_ALIGN;
+    int64_t si[kMaxRank], so_out[kMaxRank], so[kMaxRank];
+    int64_t s = 1;
+    long double tot = 1;
+    for (int d = 0; d < rank; ++d) { si[d] = s; s *= extents[d]; tot *= (long double)extents[d]; }
+    if (tot > 4.0e12L) return COMET_ERR_SHAPE;
+    s = 1;
+    for (int d = 0; d < rank; ++d) { so_out[d] = s; s *= extents[perm[d]]; }
+    for (int d = 0; d < rank; ++d) so[perm[d]] = so_out[d];
+    XposeParams x;
+    int vi, vo;
+    double eff;
+    setup_xpose(rank, extents, si, so, (int)dtype_size(dtype), &x, &vi, &vo, &eff);
+    if (x.u.total >= (1u << 31) || x.v.total >= (1u << 31) || x.r.total >= (1u << 31)) return COMET_ERR_SHAPE;
+    x.in = in; x.out = out; x.alpha = 1.0; x.beta = 0.0;
+    return cuda_status(launch_move(x, (int)dtype_size(dtype), vi, vo, static_cast<cudaStream_t>(stream)),
+                       "transpose kernel");
+}
+
+comet_status_t comet_sync_status(void *stream) {
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_status(e, "stream");
+    int *w = device_status_word();
+    if (!w) return cuda_status(cudaErrorNoDevice, "status word");
+    int v = 0, zero = 0;
+    e = cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e, "status read");
+    if (v != 0) {
+        e = cudaMemcpy(w, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_status(e, "status clear");
+        set_error("a device-side wait ran out of time");
+        return static_cast<comet_status_t>(v);
+    }
+    return COMET_OK;
+}
+
+void comet_plan_destroy(comet_plan_t plan) { delete plan; }
+
+const char *comet_status_string(comet_status_t s) {
+    switch (s) {
+        case COMET_OK: return "ok";
+        case COMET_ERR_PARSE: return "parse error";
+        case COMET_ERR_LABEL: return "label error";
+        case COMET_ERR_SHAPE: return "shape error";
+        case COMET_ERR_DTYPE: return "dtype error";
+        case COMET_ERR_UNSUPPORTED: return "unsupported";
+        case COMET_ERR_ALIGN: return "misaligned pointer";
+        case COMET_ERR_NULL: return "null pointer";
+        case COMET_ERR_WORKSPACE: return "workspace error";
+        case COMET_ERR_CUDA: return "cuda error";
+        case COMET_ERR_TIMEOUT: return "device wait timed out";
+        case COMET_ERR_INTERNAL: return "internal error";
+        case COMET_ERR_ARG: return "bad argument";
+    }
+    return "unknown status";
+}
+
+const char *comet_last_error_message(void) { return t_last_error.c_str(); }
+
+const char *comet_version(void) { return "comet-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,25 @@
+// Kernel launchers (host functions defined next to their kernels).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/comet.h"
+#include "params.h"
+
+namespace comet {
+
+cudaError_t launch_move(const XposeParams &p, int elem_bytes, int vi, int vo, cudaStream_t s);
+cudaError_t launch_scale(const XposeParams &p, int elem_bytes, int vi, int vo, cudaStream_t s);
+cudaError_t launch_split(const XposeParams &p, int elem_bytes, int vi, int vo, cudaStream_t s);
+
+cudaError_t launch_gemm_f64(const GemmParams &p, int elem_bytes, bool a_kcontig, bool b_kcontig,
+                            cudaStream_t s);
+
+cudaError_t launch_gemm_split(const GemmParams &p, const void *parts_a, const void *parts_b,
+                              int64_t kpad, int out_bytes, int debug_flags, cudaStream_t s,
+                              int max_ctas);
+
+// device status word of the current device (set by kernels whose waits run out)
+int *device_status_word();
+
+}  // namespace comet

@@ -1,0 +1,105 @@
+// Parameter blocks shared by the host planner and the device kernels.
+//
+// A "group" is an ordered list of labels fused into one GEMM dimension (the merging of
+// consecutive indices into one matrix index in the TTGT reformulation, Section 2: (a,b) -> i).
+// A group index g decomposes into digits, first label fastest (column-major merging), and each
+// digit has a stride in the tensors that hold that label.  Kernels never materialise index
+// tables: they decompose g with division by invariant integers.
+#pragma once
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define CM_HD __host__ __device__ __forceinline__
+#else
+#define CM_HD inline
+#endif
+
+namespace comet {
+
+constexpr int kMaxDigits = 8;   // labels per group / per tensor
+constexpr int kMaxRank = 8;
+
+// Unsigned 32-bit division by an invariant divisor (Granlund and Montgomery, "Division by
+// invariant integers using multiplication", PLDI 1994, Fig. 4.1): with l = ceil(log2 d),
+// m' = floor(2^32 (2^l - d) / d) + 1, sh1 = min(l,1), sh2 = max(l-1,0):
+//   t1 = mulhi(m', n);  q = (t1 + ((n - t1) >> sh1)) >> sh2,  exact for every n < 2^32.
+struct FastDiv {
+    uint32_t d, m, sh1, sh2;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+    FastDiv f;
+    f.d = d;
+    uint32_t l = 0;
+    while ((uint64_t(1) << l) < d) ++l;
+    f.m = (uint32_t)(((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1);
+    f.sh1 = l < 1 ? l : 1;
+    f.sh2 = l > 1 ? l - 1 : 0;
+    return f;
+}
+
+CM_HD uint32_t fd_div(uint32_t n, const FastDiv &f) {
+#if defined(__CUDA_ARCH__)
+    uint32_t t1 = __umulhi(f.m, n);
+#else
+    uint32_t t1 = (uint32_t)(((uint64_t)f.m * n) >> 32);
+#endif
+    return (t1 + ((n - t1) >> f.sh1)) >> f.sh2;
+}
+
+// Mixed-radix group with two stride sets (s0, s1): offset0(g) and offset1(g).
+struct Radix {
+    int n;                         // number of digits (0 = the group has the single index 0)
+    uint32_t total;                // product of extents
+    uint32_t ext[kMaxDigits];
+    FastDiv fd[kMaxDigits];
+    int64_t s0[kMaxDigits];
+    int64_t s1[kMaxDigits];
+};
+
+CM_HD void radix_offsets(const Radix &r, uint32_t g, int64_t &o0, int64_t &o1) {
+    int64_t a = 0, b = 0;
+#pragma unroll
+    for (int d = 0; d < kMaxDigits; ++d) {
+        if (d < r.n) {
+            uint32_t q = (d + 1 < r.n) ? fd_div(g, r.fd[d]) : 0;
+            uint32_t digit = (d + 1 < r.n) ? g - q * r.ext[d] : g;
+            a += (int64_t)digit * r.s0[d];
+            b += (int64_t)digit * r.s1[d];
+            g = q;
+        }
+    }
+    o0 = a;
+    o1 = b;
+}
+
+// Pure permutation / element-wise tiled copy (transpose engine).  The tensor's dims are split
+// into three groups: U (leading input dims: contiguous reads), V (leading output dims:
+// contiguous writes) and R (the rest).  A CTA moves a TU x TV tile of (u, v) for one or more
+// r.  s0 = input strides, s1 = output strides (elements).
+struct XposeParams {
+    Radix u, v, r;
+    const void *in;
+    void *out;
+    int64_t out_plane;             // split pre-pass: element distance between the 3 planes
+    double alpha;                  // scaled copy: out = alpha * in (+ beta * out)
+    double beta;
+    uint32_t tiles_u, tiles_v;     // tiles along U and V
+    uint32_t r_per_cta;            // R indices handled by one CTA
+};
+
+// Binary contraction as a GEMM over fused groups: C[m,n] = alpha * sum_k A[m,k] B[k,n]
+// (+ beta C).  ma: M digits with (A strides, C strides); nb: N digits with (B strides,
+// C strides); k: K digits with (A strides, B strides).
+struct GemmParams {
+    Radix ma, nb, k;
+    uint32_t M, N, K;
+    const void *A;
+    const void *B;
+    void *C;
+    double alpha, beta;
+    int *status;
+    int64_t timeout_ns;
+};
+
+}  // namespace comet

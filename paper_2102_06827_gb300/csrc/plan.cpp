@@ -1,0 +1,744 @@
+// Host planner.  See plan.hpp for the map to the paper.
+#include "plan.hpp"
+
+#include <algorithm>
+#include <cctype>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <functional>
+#include <limits>
+#include <map>
+#include <numeric>
+#include <set>
+#include <sstream>
+
+namespace comet {
+
+// Machine constants of the cost model (GB300): HBM copy bandwidth and dense tensor-core and
+// FP64 rates.  Only ratios matter for the choice; they are not reported anywhere.
+static const double kHbmBytesPerS = 6.8e12;
+static const double kBf16FlopsPerS = 1.67e15;
+static const double kF64FlopsPerS = 1.2e12;
+static const double kLaunchS = 3e-6;
+
+size_t dtype_size(comet_dtype_t t) { return t == COMET_F32 ? 4 : 8; }
+
+// ------------------------------------------------------------------------------------------
+// Parser: lhs (=|+=|-=) [sum_{labels}] factor (* factor)*, factor = number | Name[labels]
+// ------------------------------------------------------------------------------------------
+namespace {
+struct Cursor {
+    const char *s;
+    size_t i = 0;
+    void ws() { while (s[i] && std::isspace((unsigned char)s[i])) ++i; }
+    bool eat(char c) { ws(); if (s[i] == c) { ++i; return true; } return false; }
+    bool ident(std::string *out) {
+        ws();
+        size_t j = i;
+        if (!(std::isalpha((unsigned char)s[j]) || s[j] == '_')) return false;
+        while (std::isalnum((unsigned char)s[j]) || s[j] == '_') ++j;
+        out->assign(s + i, j - i);
+        i = j;
+        return true;
+    }
+};
+
+bool parse_labels(Cursor &c, std::vector<std::string> *labels, char close) {
+    labels->clear();
+    if (c.eat(close)) return true;
+    for (;;) {
+        std::string l;
+        if (!c.ident(&l)) return false;
+        labels->push_back(l);
+        if (c.eat(close)) return true;
+        if (!c.eat(',')) return false;
+    }
+}
+
+bool parse_tensor(Cursor &c, ParsedTensor *t) {
+    size_t save = c.i;
+    if (!c.ident(&t->name)) { c.i = save; return false; }
+    c.ws();
+    char open = c.s[c.i];
+    if (open != '[' && open != '(') { c.i = save; return false; }
+    ++c.i;
+    return parse_labels(c, &t->labels, open == '[' ? ']' : ')');
+}
+}  // namespace
+
+comet_status_t parse_expr(const char *s, ParsedExpr *e, std::string *err) {
+    if (!s) return COMET_ERR_NULL;
+    Cursor c{s};
+    if (!parse_tensor(c, &e->out)) { *err = "left-hand side is not a labelled tensor"; return COMET_ERR_PARSE; }
+    c.ws();
+    if (c.s[c.i] == '+' && c.s[c.i + 1] == '=') { e->op = 1; c.i += 2; }
+    else if (c.s[c.i] == '-' && c.s[c.i + 1] == '=') { e->op = 2; c.i += 2; }
+    else if (c.s[c.i] == '=') { e->op = 0; c.i += 1; }
+    else { *err = "expected =, += or -="; return COMET_ERR_PARSE; }
+    c.ws();
+    if (std::strncmp(c.s + c.i, "sum_{", 5) == 0) {
+        c.i += 5;
+        e->has_sum = true;
+        for (;;) {
+            c.ws();
+            if (c.eat('}')) break;
+            std::string l;
+            if (!c.ident(&l)) { *err = "bad label in sum_{...}"; return COMET_ERR_PARSE; }
+            e->sum_labels.push_back(l);
+            c.eat(',');
+        }
+    }
+    e->alpha = 1.0;
+    bool any = false;
+    for (;;) {
+        c.ws();
+        ParsedTensor t;
+        if (parse_tensor(c, &t)) {
+            e->ins.push_back(t);
+        } else {
+            char *end = nullptr;
+            double v = std::strtod(c.s + c.i, &end);
+            if (end == c.s + c.i) { *err = "expected a number or a labelled tensor"; return COMET_ERR_PARSE; }
+            e->alpha *= v;
+            c.i = end - c.s;
+        }
+        any = true;
+        c.ws();
+        if (c.s[c.i] == '\0') break;
+        if (!c.eat('*')) { *err = "expected *"; return COMET_ERR_PARSE; }
+    }
+    if (!any || e->ins.empty()) { *err = "no operand on the right-hand side"; return COMET_ERR_PARSE; }
+    return COMET_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Transpose engine set-up
+// ------------------------------------------------------------------------------------------
+namespace {
+void fill_radix(Radix *r, const std::vector<int> &dims, const int64_t *ext, const int64_t *s0,
+                const int64_t *s1) {
+    std::memset(r, 0, sizeof(*r));
+    r->n = (int)dims.size();
+    uint64_t tot = 1;
+    for (int d = 0; d < r->n; ++d) {
+        r->ext[d] = (uint32_t)ext[dims[d]];
+        r->fd[d] = make_fastdiv(r->ext[d]);
+        r->s0[d] = s0[dims[d]];
+        r->s1[d] = s1[dims[d]];
+        tot *= (uint64_t)ext[dims[d]];
+    }
+    r->total = (uint32_t)tot;
+}
+
+double run_eff(double run_bytes) { return std::min(1.0, run_bytes / 64.0); }
+}  // namespace
+
+void setup_xpose(int rank, const int64_t *ext_in, const int64_t *sin_in,
+                 const int64_t *sout_in, int elem_bytes, XposeParams *p, int *vec_in,
+                 int *vec_out, double *eff) {
+    std::memset(p, 0, sizeof(*p));
+    // drop extent-1 dims, then fuse neighbours that are contiguous on both sides
+    std::vector<int64_t> ext, si, so;
+    for (int d = 0; d < rank; ++d)
+        if (ext_in[d] != 1) { ext.push_back(ext_in[d]); si.push_back(sin_in[d]); so.push_back(sout_in[d]); }
+    if (ext.empty()) { ext.push_back(1); si.push_back(1); so.push_back(1); }
+    // order dims by input stride
+    std::vector<int> ord(ext.size());
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return si[a] < si[b]; });
+    std::vector<int64_t> e2, i2, o2;
+    for (int d : ord) {
+        if (!e2.empty() && si[d] == i2.back() * e2.back() && so[d] == o2.back() * e2.back() &&
+            (uint64_t)e2.back() * (uint64_t)ext[d] < (1ull << 31)) {
+            e2.back() *= ext[d];
+        } else {
+            e2.push_back(ext[d]); i2.push_back(si[d]); o2.push_back(so[d]);
+        }
+    }
+    int n = (int)e2.size();
+    std::vector<int> in_order(n), out_order(n);
+    std::iota(in_order.begin(), in_order.end(), 0);
+    std::iota(out_order.begin(), out_order.end(), 0);
+    std::stable_sort(out_order.begin(), out_order.end(), [&](int a, int b) { return o2[a] < o2[b]; });
+    const int64_t target = 64;  // tile edge in elements
+    std::vector<int> U, V;
+    std::vector<char> used(n, 0);
+    int dfi = in_order[0], dfo = out_order[0];
+    bool same = (dfi == dfo);
+    U.push_back(dfi); used[dfi] = 1;
+    int64_t pu = e2[dfi];
+    if (!same) { V.push_back(dfo); used[dfo] = 1; }
+    int64_t pv = same ? 1 : e2[dfo];
+    // extend U along the input order while contiguous in the input
+    for (int k = 1; k < n && pu < target; ++k) {
+        int d = in_order[k];
+        int prev = U.back();
+        if (used[d] || i2[d] != i2[prev] * e2[prev] || (uint64_t)pu * e2[d] >= (1ull << 31)) break;
+        U.push_back(d); used[d] = 1; pu *= e2[d];
+    }
+    if (!same) {
+        for (int k = 1; k < n && pv < target; ++k) {
+            int d = out_order[k];
+            int prev = V.back();
+            if (used[d] || o2[d] != o2[prev] * e2[prev] || (uint64_t)pv * e2[d] >= (1ull << 31)) break;
+            V.push_back(d); used[d] = 1; pv *= e2[d];
+        }
+    } else {
+        // copy mode: V is simply the next input dim (more rows per CTA)
+        for (int k = 0; k < n; ++k) {
+            int d = in_order[k];
+            if (!used[d]) { V.push_back(d); used[d] = 1; pv = e2[d]; break; }
+        }
+    }
+    std::vector<int> R;
+    for (int k = 0; k < n; ++k) if (!used[in_order[k]]) R.push_back(in_order[k]);
+    fill_radix(&p->u, U, e2.data(), i2.data(), o2.data());
+    fill_radix(&p->v, V, e2.data(), i2.data(), o2.data());
+    fill_radix(&p->r, R, e2.data(), i2.data(), o2.data());
+    p->tiles_u = (uint32_t)((p->u.total + target - 1) / target);
+    p->tiles_v = (uint32_t)((std::max<uint32_t>(p->v.total, 1) + target - 1) / target);
+    if (V.empty()) { p->v.total = 1; }
+    if (R.empty()) { p->r.total = 1; }
+    // vector widths: 16-byte accesses when every stride other than the fast digit's is a
+    // multiple of the width and the fast digit's extent is too
+    int w = 16 / elem_bytes;
+    auto ok_in = [&](int vw) {
+        if (p->u.s0[0] != 1 || p->u.ext[0] % vw) return false;
+        for (int d = 1; d < p->u.n; ++d) if (p->u.s0[d] % vw) return false;
+        for (int d = 0; d < p->v.n; ++d) if (p->v.s0[d] % vw) return false;
+        for (int d = 0; d < p->r.n; ++d) if (p->r.s0[d] % vw) return false;
+        return true;
+    };
+    auto ok_out = [&](int vw, bool copy) {
+        const Radix &f = copy ? p->u : p->v;
+        if (f.n == 0 || f.s1[0] != 1 || f.ext[0] % vw) return false;
+        for (int d = 1; d < f.n; ++d) if (f.s1[d] % vw) return false;
+        const Radix &g = copy ? p->v : p->u;
+        for (int d = 0; d < g.n; ++d) if (g.s1[d] % vw) return false;
+        for (int d = 0; d < p->r.n; ++d) if (p->r.s1[d] % vw) return false;
+        return true;
+    };
+    int vi = 1, vo = 1;
+    for (int vw = w; vw > 1; vw /= 2) if (ok_in(vw)) { vi = vw; break; }
+    for (int vw = w; vw > 1; vw /= 2) if (ok_out(vw, same)) { vo = vw; break; }
+    if (same) { int m = std::min(vi, vo); vi = vo = m; }
+    *vec_in = vi;
+    *vec_out = same ? -vo : vo;   // negative = copy mode (no smem transposition)
+    double run_in = (double)std::min<int64_t>(pu, target) * elem_bytes;
+    double run_out = (double)std::min<int64_t>(same ? pu : pv, target) * elem_bytes;
+    *eff = run_eff(run_in) * 0.5 + run_eff(run_out) * 0.5;
+    // CTAs: enough r per CTA to keep a few tiles in flight per SM without starving the grid
+    uint64_t tiles = (uint64_t)p->tiles_u * p->tiles_v;
+    uint64_t want_ctas = 152ull * 16;
+    uint64_t per = 1;
+    if (tiles * p->r.total > want_ctas) per = std::max<uint64_t>(1, (tiles * p->r.total) / want_ctas);
+    per = std::min<uint64_t>(per, 64);
+    p->r_per_cta = (uint32_t)per;
+}
+
+// ------------------------------------------------------------------------------------------
+// Planning
+// ------------------------------------------------------------------------------------------
+namespace {
+
+struct Ctx {
+    Plan *p;
+    std::vector<int64_t> &ext;
+    int64_t es;
+};
+
+int64_t prod_ext(const std::vector<int64_t> &ext, const std::vector<int> &labs) {
+    int64_t r = 1;
+    for (int l : labs) r *= ext[l];
+    return r;
+}
+
+int pos_of(const std::vector<int> &v, int x) {
+    for (size_t i = 0; i < v.size(); ++i) if (v[i] == x) return (int)i;
+    return -1;
+}
+
+// strides (elements) of a dense column-major tensor, by label id
+std::map<int, int64_t> label_strides(const std::vector<int> &labels, const std::vector<int64_t> &ext) {
+    std::map<int, int64_t> s;
+    int64_t st = 1;
+    for (int l : labels) { s[l] = st; st *= ext[l]; }
+    return s;
+}
+
+// length (elements) of the contiguous run that a group order gives in a tensor: the product of
+// the leading group labels that sit at strides 1, e0, e0*e1, ... in the tensor
+int64_t contiguous_run(const std::vector<int> &group, const std::map<int, int64_t> &st,
+                       const std::vector<int64_t> &ext) {
+    int64_t run = 1;
+    for (int l : group) {
+        auto it = st.find(l);
+        if (it == st.end() || it->second != run) break;
+        run *= ext[l];
+    }
+    return run;
+}
+
+void permutations(const std::vector<int> &base, std::vector<std::vector<int>> *out, size_t cap) {
+    std::vector<int> v = base;
+    std::sort(v.begin(), v.end());
+    do {
+        out->push_back(v);
+        if (out->size() >= cap) break;
+    } while (std::next_permutation(v.begin(), v.end()));
+}
+
+// candidate orders of one group: every permutation when few, else the orders in which the
+// labels appear in the given tensors
+std::vector<std::vector<int>> group_orders(const std::vector<int> &g,
+                                           const std::vector<const std::vector<int> *> &tensors) {
+    std::vector<std::vector<int>> res;
+    if (g.size() <= 4) {
+        permutations(g, &res, 24);
+        return res;
+    }
+    for (auto *t : tensors) {
+        std::vector<int> o;
+        for (int l : *t) if (pos_of(g, l) >= 0) o.push_back(l);
+        if (o.size() == g.size() && std::find(res.begin(), res.end(), o) == res.end()) res.push_back(o);
+    }
+    if (res.empty()) res.push_back(g);
+    return res;
+}
+
+// modelled time of one form of a binary step
+void cost_form(const Plan &P, const std::vector<int> &lx, const std::vector<int> &ly,
+               const std::vector<int> &lz, bool z_free_layout, int kernel, Form *f) {
+    const std::vector<int64_t> &ext = P.extent;
+    double es = (double)dtype_size(P.dtype);
+    const std::vector<int> &lm = f->swap ? ly : lx;   // M operand labels
+    const std::vector<int> &ln = f->swap ? lx : ly;
+    double M = (double)prod_ext(ext, f->M), N = (double)prod_ext(ext, f->N), K = (double)prod_ext(ext, f->K);
+    auto sm = label_strides(lm, ext), sn = label_strides(ln, ext);
+    std::vector<int> zl = lz;
+    if (z_free_layout) { zl = f->M; zl.insert(zl.end(), f->N.begin(), f->N.end()); }
+    auto sz = label_strides(zl, ext);
+    double run_c = (double)contiguous_run(f->M, sz, ext);
+    f->eff_store = run_eff(std::min(run_c, 32.0) * es * 2);
+    double t_store = M * N * es / (kHbmBytesPerS * f->eff_store);
+    if (kernel == KK_GEMM_SPLIT) {
+        // pre-passes: read the operand, write 3 bf16 planes in [rows][K] order; the transpose
+        // engine's efficiency follows from the runs on both sides
+        auto pre = [&](const std::vector<int> &lop, const std::vector<int> &rows, double *eff_out) {
+            std::vector<int64_t> e, si, so;
+            auto st = label_strides(lop, ext);
+            int64_t kpad = ((int64_t)K + 7) / 8 * 8;
+            int64_t s = 1;
+            std::map<int, int64_t> sout;
+            for (int l : f->K) { sout[l] = s; s *= ext[l]; }
+            s = kpad;
+            for (int l : rows) { sout[l] = s; s *= ext[l]; }
+            for (int l : lop) { e.push_back(ext[l]); si.push_back(st[l]); so.push_back(sout[l]); }
+            XposeParams xp;
+            int vi, vo;
+            double eff;
+            setup_xpose((int)e.size(), e.data(), si.data(), so.data(), (int)es, &xp, &vi, &vo, &eff);
+            *eff_out = eff;
+            double elems = (double)prod_ext(ext, lop);
+            return elems * (es + 6.0);
+        };
+        double bx = pre(lm, f->M, &f->eff_a), by = pre(ln, f->N, &f->eff_b);
+        f->pre_bytes = bx + by;
+        double t_pre = bx / (kHbmBytesPerS * f->eff_a) + by / (kHbmBytesPerS * f->eff_b) + 2 * kLaunchS;
+        double waste = (std::ceil(M / 128) * 128 * std::ceil(N / 256) * 256) / (M * N);
+        double t_mma = 6.0 * 2.0 * M * N * K * waste / kBf16FlopsPerS;
+        // the epilogue's stores overlap the next tile's main loop, but scattered stores still
+        // cost DRAM bandwidth: charge a share of them beyond the overlap
+        f->cost = t_pre + std::max(t_mma, t_store) + 0.25 * t_store + kLaunchS;
+    } else {
+        double ra = (double)std::max(contiguous_run(f->M, sm, ext), contiguous_run(f->K, sm, ext));
+        double rb = (double)std::max(contiguous_run(f->N, sn, ext), contiguous_run(f->K, sn, ext));
+        f->eff_a = run_eff(std::min(ra, 16.0) * es * 4);
+        f->eff_b = run_eff(std::min(rb, 16.0) * es * 4);
+        double waste = (std::ceil(M / 64) * 64 * std::ceil(N / 64) * 64) / (M * N);
+        double t_mma = 2.0 * M * N * K * waste / kF64FlopsPerS;
+        double t_load = (M * K / f->eff_a * std::ceil(N / 64) + N * K / f->eff_b * std::ceil(M / 64)) * es /
+                        (kHbmBytesPerS * 8);   // re-reads mostly hit L2
+        f->pre_bytes = 0;
+        f->cost = std::max(t_mma, t_load) + t_store + kLaunchS;
+    }
+}
+
+// flops of contracting the label sets of two subtrees
+double step_flops(const std::vector<int64_t> &ext, const std::vector<int> &a, const std::vector<int> &b) {
+    std::set<int> u(a.begin(), a.end());
+    u.insert(b.begin(), b.end());
+    double f = 2.0;
+    for (int l : u) f *= (double)ext[l];
+    return f;
+}
+
+}  // namespace
+
+comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n_extents,
+                          const comet_dtype_t *dtypes, int n_dtypes,
+                          const comet_plan_opts_t *opts_in, Plan *P, std::string *err) {
+    if (!expr) return COMET_ERR_NULL;
+    comet_plan_opts_t opts;
+    comet_plan_opts_default(&opts);
+    if (opts_in) opts = *opts_in;
+    if (opts.precision != COMET_PREC_NATIVE && opts.precision != COMET_PREC_SPLIT_BF16) {
+        *err = "unknown precision"; return COMET_ERR_ARG;
+    }
+    if (opts.kc < 0 || opts.timeout_ms < 0) { *err = "negative kc or timeout"; return COMET_ERR_ARG; }
+    P->opts = opts;
+    P->expr = expr;
+    comet_status_t st = parse_expr(expr, &P->parsed, err);
+    if (st != COMET_OK) return st;
+    const ParsedExpr &E = P->parsed;
+    P->n_in = (int)E.ins.size();
+    P->op = E.op;
+    P->alpha = E.alpha * opts.alpha;
+    // labels: ids in order of first appearance on the right-hand side
+    std::map<std::string, int> id;
+    for (auto &t : E.ins)
+        for (auto &l : t.labels)
+            if (!id.count(l)) { id[l] = (int)P->label_names.size(); P->label_names.push_back(l); }
+    for (auto &l : E.out.labels)
+        if (!id.count(l)) { *err = "output label " + l + " is on no right-hand operand"; return COMET_ERR_LABEL; }
+    int L = (int)P->label_names.size();
+    if (L > 64) { *err = "too many labels"; return COMET_ERR_UNSUPPORTED; }
+    P->extent.assign(L, -1);
+    if (n_extents < 0 || (n_extents > 0 && !extents)) return COMET_ERR_NULL;
+    for (int i = 0; i < n_extents; ++i) {
+        if (!extents[i].label) return COMET_ERR_NULL;
+        auto it = id.find(extents[i].label);
+        if (it == id.end()) continue;   // extents for unused labels are ignored
+        if (extents[i].extent <= 0) { *err = std::string("non-positive extent for ") + extents[i].label; return COMET_ERR_SHAPE; }
+        if (P->extent[it->second] != -1 && P->extent[it->second] != extents[i].extent) {
+            *err = std::string("two extents for ") + extents[i].label; return COMET_ERR_SHAPE;
+        }
+        P->extent[it->second] = extents[i].extent;
+    }
+    for (int l = 0; l < L; ++l)
+        if (P->extent[l] < 0) { *err = "no extent for label " + P->label_names[l]; return COMET_ERR_LABEL; }
+    // dtypes
+    if (!dtypes) return COMET_ERR_NULL;
+    if (n_dtypes != P->n_in + 1) { *err = "one dtype per operand and one for the output"; return COMET_ERR_DTYPE; }
+    for (int i = 0; i < n_dtypes; ++i) {
+        if (dtypes[i] != COMET_F32 && dtypes[i] != COMET_F64) { *err = "unknown dtype"; return COMET_ERR_DTYPE; }
+        if (dtypes[i] != dtypes[0]) { *err = "operands of different dtypes"; return COMET_ERR_DTYPE; }
+    }
+    P->dtype = dtypes[0];
+    // labelled tensors as id lists; structural checks (Section 2: contraction vs free labels)
+    std::vector<std::vector<int>> in_labs;
+    for (auto &t : E.ins) {
+        std::vector<int> v;
+        for (auto &l : t.labels) {
+            if (pos_of(v, id[l]) >= 0) { *err = "repeated label inside " + t.name; return COMET_ERR_UNSUPPORTED; }
+            v.push_back(id[l]);
+        }
+        if (v.size() > (size_t)kMaxRank) { *err = "rank above 8"; return COMET_ERR_UNSUPPORTED; }
+        in_labs.push_back(v);
+    }
+    std::vector<int> out_labs;
+    for (auto &l : E.out.labels) {
+        if (pos_of(out_labs, id[l]) >= 0) { *err = "repeated output label"; return COMET_ERR_UNSUPPORTED; }
+        out_labs.push_back(id[l]);
+    }
+    if (out_labs.size() > (size_t)kMaxRank) { *err = "rank above 8"; return COMET_ERR_UNSUPPORTED; }
+    std::vector<int> count(L, 0);
+    for (auto &v : in_labs) for (int l : v) ++count[l];
+    for (int l : out_labs) ++count[l];
+    if (P->n_in == 1) {
+        if (in_labs[0].size() != out_labs.size()) { *err = "summation inside a single operand"; return COMET_ERR_UNSUPPORTED; }
+    } else {
+        for (int l = 0; l < L; ++l) {
+            if (count[l] == 1) { *err = "label " + P->label_names[l] + " is summed inside a single operand"; return COMET_ERR_UNSUPPORTED; }
+            if (count[l] > 2) { *err = "label " + P->label_names[l] + " appears in more than two tensors (batch label)"; return COMET_ERR_UNSUPPORTED; }
+        }
+    }
+    if (E.has_sum) {
+        std::set<std::string> want, got(E.sum_labels.begin(), E.sum_labels.end());
+        for (int l = 0; l < L; ++l) if (pos_of(out_labs, l) < 0) want.insert(P->label_names[l]);
+        if (want != got) { *err = "sum_{...} does not name the summed labels"; return COMET_ERR_LABEL; }
+    }
+    // sizes
+    auto elems_of = [&](const std::vector<int> &v) {
+        long double e = 1;
+        for (int l : v) e *= (long double)P->extent[l];
+        return e;
+    };
+    for (auto &v : in_labs) if (elems_of(v) > 9.0e15L) { *err = "tensor too large"; return COMET_ERR_SHAPE; }
+    if (elems_of(out_labs) > 9.0e15L) { *err = "tensor too large"; return COMET_ERR_SHAPE; }
+    size_t es = dtype_size(P->dtype);
+
+    // slots: inputs, then the output
+    for (int i = 0; i < P->n_in; ++i) {
+        Slot s; s.kind = SLOT_INPUT; s.index = i; s.labels = in_labs[i];
+        s.elems = (int64_t)elems_of(in_labs[i]);
+        P->slots.push_back(s);
+    }
+    Slot so; so.kind = SLOT_OUTPUT; so.labels = out_labs; so.elems = (int64_t)elems_of(out_labs);
+    int out_slot = (int)P->slots.size();
+    P->slots.push_back(so);
+
+    // ---- single operand: scaled copy / transpose (ta.copy) ----
+    if (P->n_in == 1) {
+        Step s; s.a = 0; s.c = out_slot; s.kernel = KK_COPY; s.final_step = true; s.flops = 0;
+        P->steps.push_back(s);
+        P->tree = E.ins[0].name;
+    } else {
+        // ---- operand order (Section 6): DP over subsets, min flops; ties: min intermediate
+        // elements, then the left-most split ----
+        int n = P->n_in;
+        if (n > 12) { *err = "more than 12 operands"; return COMET_ERR_UNSUPPORTED; }
+        int full = (1 << n) - 1;
+        // labels of the intermediate of subset S: labels of S that also occur outside S
+        std::vector<std::vector<int>> sub_labels(1 << n);
+        for (int S = 1; S <= full; ++S) {
+            std::vector<int> inside(L, 0), outside(L, 0);
+            for (int t = 0; t < n; ++t)
+                for (int l : in_labs[t]) { if (S >> t & 1) inside[l] = 1; else outside[l] = 1; }
+            for (int l : out_labs) outside[l] = 1;
+            for (int l = 0; l < L; ++l) if (inside[l] && outside[l]) sub_labels[S].push_back(l);
+        }
+        const double INF = std::numeric_limits<double>::infinity();
+        std::vector<double> best_f(1 << n, INF), best_b(1 << n, INF);
+        std::vector<int> split(1 << n, 0);
+        for (int t = 0; t < n; ++t) { best_f[1 << t] = 0; best_b[1 << t] = 0; }
+        auto inter_bytes = [&](int S) { return (double)elems_of(sub_labels[S]) * es; };
+        auto natural_split = [&](int S) {   // left-to-right: split off the highest operand
+            int hi = 31 - __builtin_clz((unsigned)S);
+            return S & ~(1 << hi);
+        };
+        for (int S = 1; S <= full; ++S) {
+            if (__builtin_popcount((unsigned)S) < 2) continue;
+            if (opts.order == COMET_ORDER_NATURAL) {
+                int Lp = natural_split(S), R = S ^ Lp;
+                split[S] = Lp;
+                best_f[S] = best_f[Lp] + best_f[R] + step_flops(P->extent, sub_labels[Lp], sub_labels[R]);
+                best_b[S] = best_b[Lp] + best_b[R] + (S == full ? 0 : inter_bytes(S));
+                continue;
+            }
+            // enumerate L as a proper subset containing the lowest operand of S (each split once)
+            int low = S & -S;
+            for (int Lp = (S - 1) & S; Lp > 0; Lp = (Lp - 1) & S) {
+                if (!(Lp & low)) continue;
+                int R = S ^ Lp;
+                if (best_f[Lp] == INF || best_f[R] == INF) continue;
+                double ib = (S == full) ? 0 : inter_bytes(S);
+                if (S != full && opts.workspace_cap && ib > (double)opts.workspace_cap) continue;
+                double f = best_f[Lp] + best_f[R] + step_flops(P->extent, sub_labels[Lp], sub_labels[R]);
+                double b = best_b[Lp] + best_b[R] + ib;
+                // ties: fewer flops, fewer intermediate bytes, then the smaller (left-most) split
+                bool better = f < best_f[S] * (1 - 1e-12) ||
+                              (std::fabs(f - best_f[S]) <= 1e-12 * f &&
+                               (b < best_b[S] || (b == best_b[S] && Lp < split[S])));
+                if (better || best_f[S] == INF) { best_f[S] = f; best_b[S] = b; split[S] = Lp; }
+            }
+        }
+        if (best_f[full] == INF) { *err = "no order fits the workspace cap"; return COMET_ERR_WORKSPACE; }
+        P->flops = best_f[full];
+        // natural order flops for reference
+        {
+            double f = 0;
+            int S = 1;
+            for (int t = 1; t < n; ++t) {
+                int R = 1 << t;
+                f += step_flops(P->extent, sub_labels[S], sub_labels[R]);
+                S |= R;
+            }
+            P->flops_natural = f;
+        }
+        // emit steps post-order
+        std::function<int(int)> emit = [&](int S) -> int {
+            if (__builtin_popcount((unsigned)S) == 1) return __builtin_ctz((unsigned)S);
+            int Lp = split[S], R = S ^ Lp;
+            int a = emit(Lp), b = emit(R);
+            int c;
+            if (S == full) {
+                c = out_slot;
+            } else {
+                Slot s; s.kind = SLOT_INTER; s.labels = sub_labels[S];
+                s.elems = (int64_t)elems_of(sub_labels[S]);
+                c = (int)P->slots.size();
+                P->slots.push_back(s);
+            }
+            Step st; st.a = a; st.b = b; st.c = c; st.final_step = (S == full);
+            st.flops = step_flops(P->extent, sub_labels[Lp], sub_labels[R]);
+            P->steps.push_back(st);
+            return c;
+        };
+        std::function<std::string(int)> tree = [&](int S) -> std::string {
+            if (__builtin_popcount((unsigned)S) == 1) return E.ins[__builtin_ctz((unsigned)S)].name;
+            return "(" + tree(split[S]) + "*" + tree(S ^ split[S]) + ")";
+        };
+        emit(full);
+        P->tree = tree(full);
+    }
+
+    // ---- TTGT form of every binary step (Section 6) ----
+    int kernel = opts.precision == COMET_PREC_SPLIT_BF16 ? KK_GEMM_SPLIT : KK_GEMM_F64;
+    for (auto &st : P->steps) {
+        if (st.kernel == KK_COPY) continue;
+        st.kernel = kernel;
+        Slot &sa = P->slots[st.a], &sb = P->slots[st.b], &sc = P->slots[st.c];
+        bool free_layout = sc.kind == SLOT_INTER;
+        std::vector<int> I, J, K;   // free in a, free in b, contracted
+        for (int l : sa.labels) (pos_of(sb.labels, l) >= 0 ? K : I).push_back(l);
+        for (int l : sb.labels) if (pos_of(sa.labels, l) < 0) J.push_back(l);
+        for (int l : sc.labels)
+            if (pos_of(I, l) < 0 && pos_of(J, l) < 0) { *err = "internal: output label not free"; return COMET_ERR_INTERNAL; }
+        if (prod_ext(P->extent, I) >= (1ll << 31) || prod_ext(P->extent, J) >= (1ll << 31) ||
+            prod_ext(P->extent, K) >= (1ll << 31)) {
+            *err = "a merged GEMM dimension reaches 2^31"; return COMET_ERR_UNSUPPORTED;
+        }
+        std::vector<Form> forms;
+        for (int swap = 0; swap < 2; ++swap) {
+            const std::vector<int> &gm = swap ? J : I, &gn = swap ? I : J;
+            const std::vector<int> &lm = swap ? sb.labels : sa.labels, &ln = swap ? sa.labels : sb.labels;
+            auto om = group_orders(gm, {&sc.labels, &lm});
+            auto on = group_orders(gn, {&sc.labels, &ln});
+            auto ok = group_orders(K, {&lm, &ln});
+            for (auto &m : om) for (auto &nn : on) for (auto &k : ok) {
+                Form f; f.swap = swap; f.M = m; f.N = nn; f.K = k;
+                cost_form(*P, sa.labels, sb.labels, sc.labels, free_layout, kernel, &f);
+                forms.push_back(f);
+                if (forms.size() > 20000) break;
+            }
+        }
+        st.n_forms = (int)forms.size();
+        int pick = 0;
+        if (opts.form >= 0) {
+            pick = opts.form % st.n_forms;
+        } else {
+            for (int i = 1; i < st.n_forms; ++i)
+                if (forms[i].cost < forms[pick].cost * (1 - 1e-9)) pick = i;
+        }
+        st.form = forms[pick];
+        st.form_index = pick;
+        if (free_layout) {   // the intermediate is stored as [M][N]: the epilogue writes rows
+            sc.labels = st.form.M;
+            sc.labels.insert(sc.labels.end(), st.form.N.begin(), st.form.N.end());
+        }
+    }
+
+    // ---- workspace: intermediates, then one region for the split parts of any step ----
+    size_t off = 0;
+    auto align = [](size_t x) { return (x + 255) / 256 * 256; };
+    for (auto &s : P->slots)
+        if (s.kind == SLOT_INTER) { s.ws_off = off; off = align(off + (size_t)s.elems * es); }
+    size_t parts_base = off, parts_max = 0;
+    for (auto &st : P->steps) {
+        if (st.kernel != KK_GEMM_SPLIT) continue;
+        int64_t Kx = prod_ext(P->extent, st.form.K);
+        st.kpad = (Kx + 7) / 8 * 8;
+        int64_t rows_a = prod_ext(P->extent, st.form.M), rows_b = prod_ext(P->extent, st.form.N);
+        size_t ba = align((size_t)3 * rows_a * st.kpad * 2), bb = align((size_t)3 * rows_b * st.kpad * 2);
+        st.ws_parts_a = parts_base;
+        st.ws_parts_b = parts_base + ba;
+        parts_max = std::max(parts_max, ba + bb);
+    }
+    P->workspace = parts_base + parts_max;
+
+    // ---- precomputed parameter blocks ----
+    for (auto &st : P->steps) {
+        if (st.kernel == KK_COPY) {
+            const Slot &sa = P->slots[st.a], &sc = P->slots[st.c];
+            auto si = label_strides(sa.labels, P->extent), so2 = label_strides(sc.labels, P->extent);
+            std::vector<int64_t> e, a, b;
+            for (int l : sa.labels) { e.push_back(P->extent[l]); a.push_back(si[l]); b.push_back(so2[l]); }
+            double eff;
+            setup_xpose((int)e.size(), e.data(), a.data(), b.data(), (int)es, &st.copy,
+                        &st.copy_vec_in, &st.copy_vec_out, &eff);
+            continue;
+        }
+        const Slot &sa = P->slots[st.a], &sb = P->slots[st.b], &sc = P->slots[st.c];
+        const Slot &sm = st.form.swap ? sb : sa, &sn = st.form.swap ? sa : sb;
+        auto tm = label_strides(sm.labels, P->extent), tn = label_strides(sn.labels, P->extent),
+             tc = label_strides(sc.labels, P->extent);
+        GemmParams &g = st.gemm;
+        std::memset(&g, 0, sizeof(g));
+        std::vector<int64_t> ex(P->extent.begin(), P->extent.end());
+        std::vector<int64_t> s0(L), s1(L);
+        // M: (A strides, C strides)
+        for (int l : st.form.M) { s0[l] = tm[l]; s1[l] = tc[l]; }
+        fill_radix(&g.ma, st.form.M, ex.data(), s0.data(), s1.data());
+        for (int l : st.form.N) { s0[l] = tn[l]; s1[l] = tc[l]; }
+        fill_radix(&g.nb, st.form.N, ex.data(), s0.data(), s1.data());
+        for (int l : st.form.K) { s0[l] = tm[l]; s1[l] = tn[l]; }
+        fill_radix(&g.k, st.form.K, ex.data(), s0.data(), s1.data());
+        g.M = (uint32_t)prod_ext(P->extent, st.form.M);
+        g.N = (uint32_t)prod_ext(P->extent, st.form.N);
+        g.K = (uint32_t)prod_ext(P->extent, st.form.K);
+        g.ma.total = g.M; g.nb.total = g.N; g.k.total = g.K;
+        if (st.kernel == KK_GEMM_SPLIT) {
+            // pre-pass of each operand into [3][rows][kpad] bf16 planes (K order, then rows)
+            auto pre = [&](const Slot &so_, const std::vector<int> &rows, XposeParams *xp, int *vec_in, int *vec_out) {
+                auto st_ = label_strides(so_.labels, P->extent);
+                std::map<int, int64_t> sout;
+                int64_t s = 1;
+                for (int l : st.form.K) { sout[l] = s; s *= P->extent[l]; }
+                s = st.kpad;
+                for (int l : rows) { sout[l] = s; s *= P->extent[l]; }
+                std::vector<int64_t> e, a, b;
+                for (int l : so_.labels) { e.push_back(P->extent[l]); a.push_back(st_[l]); b.push_back(sout[l]); }
+                double eff;
+                setup_xpose((int)e.size(), e.data(), a.data(), b.data(), (int)es, xp, vec_in, vec_out, &eff);
+                int64_t rows_n = prod_ext(P->extent, rows);
+                xp->out_plane = rows_n * st.kpad;
+            };
+            pre(sm, st.form.M, &st.pre_a, &st.pre_a_vec, &st.pre_a_vout);
+            pre(sn, st.form.N, &st.pre_b, &st.pre_b_vec, &st.pre_b_vout);
+        }
+    }
+    P->flops = 0;
+    for (auto &st : P->steps) P->flops += st.flops;
+    if (P->n_in == 2) P->flops_natural = P->flops;
+    if (P->n_in == 1) P->flops_natural = 0;
+    return COMET_OK;
+}
+
+std::string describe_plan(const Plan &P) {
+    std::ostringstream o;
+    auto names = [&](const std::vector<int> &v) {
+        std::string s = "[";
+        for (size_t i = 0; i < v.size(); ++i) { if (i) s += ","; s += "\"" + P.label_names[v[i]] + "\""; }
+        return s + "]";
+    };
+    o << "{\"expr\":\"" << P.expr << "\",\"dtype\":\"" << (P.dtype == COMET_F32 ? "f32" : "f64")
+      << "\",\"precision\":\"" << (P.opts.precision == COMET_PREC_SPLIT_BF16 ? "split_bf16" : "native")
+      << "\",\"order\":\"" << P.tree << "\",\"flops\":" << P.flops << ",\"flops_natural\":" << P.flops_natural
+      << ",\"workspace\":" << P.workspace << ",\"steps\":[";
+    for (size_t i = 0; i < P.steps.size(); ++i) {
+        const Step &s = P.steps[i];
+        if (i) o << ",";
+        o << "{\"kernel\":\"" << (s.kernel == KK_COPY ? "copy" : s.kernel == KK_GEMM_SPLIT ? "gemm_split_bf16" : "gemm_f64")
+          << "\",\"a\":" << s.a << ",\"b\":" << s.b << ",\"c\":" << s.c
+          << ",\"a_labels\":" << names(P.slots[s.a].labels);
+        if (s.b >= 0) o << ",\"b_labels\":" << names(P.slots[s.b].labels);
+        o << ",\"c_labels\":" << names(P.slots[s.c].labels);
+        if (s.kernel != KK_COPY) {
+            o << ",\"swap\":" << s.form.swap << ",\"M\":" << names(s.form.M) << ",\"N\":" << names(s.form.N)
+              << ",\"K\":" << names(s.form.K) << ",\"n_forms\":" << s.n_forms << ",\"form_index\":" << s.form_index
+              << ",\"cost_s\":" << s.form.cost << ",\"pre_bytes\":" << s.form.pre_bytes
+              << ",\"eff_store\":" << s.form.eff_store << ",\"flops\":" << s.flops;
+        }
+        o << "}";
+    }
+    o << "]}";
+    return o.str();
+}
+
+}  // namespace comet
+
+extern "C" void comet_plan_opts_default(comet_plan_opts_t *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = COMET_PREC_NATIVE;
+    o->order = COMET_ORDER_PLANNED;
+    o->alpha = 1.0;
+    o->workspace_cap = 0;
+    o->form = -1;
+    o->kc = 0;
+    o->timeout_ms = 0;
+    o->debug_flags = 0;
+}

@@ -1,0 +1,110 @@
+// Host-side planner: parsing (Fig. 2b grammar), label classification (Section 2), operand
+// ordering (Section 6 "Multi-Operand Expression") and TTGT form choice (Section 6 "TTGT",
+// "Optimal permutation for TTGT").  No device work happens here.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/comet.h"
+#include "params.h"
+
+namespace comet {
+
+struct ParsedTensor {
+    std::string name;
+    std::vector<std::string> labels;
+};
+
+struct ParsedExpr {
+    ParsedTensor out;
+    std::vector<ParsedTensor> ins;
+    int op = 0;                  // 0 "=", 1 "+=", 2 "-="
+    double alpha = 1.0;
+    bool has_sum = false;
+    std::vector<std::string> sum_labels;
+};
+
+comet_status_t parse_expr(const char *s, ParsedExpr *e, std::string *err);
+
+enum KernelKind { KK_GEMM_F64 = 0, KK_GEMM_SPLIT = 1, KK_COPY = 2 };
+
+// One TTGT form of a binary step: which input provides the M (row) group, and the order of
+// the labels inside M, N and K (first = fastest in the merged index).
+struct Form {
+    int swap = 0;                // 0: the step's first input is the M operand
+    std::vector<int> M, N, K;
+    double cost = 0;             // modelled seconds
+    double pre_bytes = 0;        // bytes moved by explicit pre-passes
+    double eff_store = 1, eff_a = 1, eff_b = 1;
+};
+
+enum SlotKind { SLOT_INPUT = 0, SLOT_INTER = 1, SLOT_OUTPUT = 2 };
+
+struct Slot {
+    int kind = SLOT_INPUT;
+    int index = 0;               // input position for SLOT_INPUT
+    std::vector<int> labels;     // column-major label order of this tensor
+    int64_t elems = 1;
+    size_t ws_off = 0;           // SLOT_INTER: byte offset in the workspace
+};
+
+struct Step {
+    int a = -1, b = -1, c = -1;  // slots (b = -1 for a copy)
+    int kernel = KK_GEMM_F64;
+    Form form;
+    int n_forms = 1;
+    int form_index = 0;
+    double flops = 0;
+    bool final_step = false;
+    // split path workspace for the bf16 parts: [3][rows][kpad]
+    size_t ws_parts_a = 0, ws_parts_b = 0;
+    int64_t kpad = 0;
+    // precomputed parameter blocks (pointers filled at launch)
+    GemmParams gemm;             // for both GEMM kernels (offsets in elements)
+    XposeParams pre_a, pre_b;    // split pre-passes (A then B operand)
+    XposeParams copy;            // KK_COPY
+    int pre_a_vec = 1, pre_b_vec = 1, pre_a_vout = 1, pre_b_vout = 1;
+    int copy_vec_in = 1, copy_vec_out = 1;
+};
+
+struct Plan {
+    std::string expr;
+    ParsedExpr parsed;
+    std::vector<std::string> label_names;
+    std::vector<int64_t> extent;
+    int n_in = 0;
+    comet_dtype_t dtype = COMET_F64;
+    comet_plan_opts_t opts;
+    double alpha = 1.0;          // expression alpha times opts.alpha
+    int op = 0;
+    std::vector<Slot> slots;
+    std::vector<Step> steps;
+    size_t workspace = 0;
+    double flops = 0, flops_natural = 0;
+    std::string tree;            // parenthesised order, e.g. "((A*B)*C)"
+    // batched plans
+    bool batched = false;
+    int n_blocks = 0;
+    std::vector<int64_t> block_extents;   // n_blocks x n_labels
+    int tile_cfg = 0;
+    size_t batched_ws = 0;
+    std::vector<uint8_t> batched_table;   // host image of the per-block descriptors
+};
+
+size_t dtype_size(comet_dtype_t t);
+
+comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n_extents,
+                          const comet_dtype_t *dtypes, int n_dtypes,
+                          const comet_plan_opts_t *opts, Plan *plan, std::string *err);
+
+std::string describe_plan(const Plan &p);
+
+// Transpose engine set-up for a permutation of a dense column-major tensor with arbitrary
+// output strides.  in_strides/out_strides in elements; returns the vector widths usable for
+// loads and stores (1, 2 or 4 elements of elem_bytes).
+void setup_xpose(int rank, const int64_t *ext, const int64_t *in_strides,
+                 const int64_t *out_strides, int elem_bytes, XposeParams *p,
+                 int *vec_in, int *vec_out, double *eff);
+
+}  // namespace comet

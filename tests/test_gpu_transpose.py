@@ -1,0 +1,95 @@
+"""GPU parity of comet_transpose against the oracle's bit-move transpose (bit-exact)."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import from_dev, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def comet():
+    import paper_2102_06827_gb300 as c
+    return c
+
+
+def run(comet, a, perm):
+    x = to_dev(a)
+    out = comet.transpose(x, a.shape, perm)
+    comet.sync_status()
+    return from_dev(out)
+
+
+def test_extent24_fp64_perm_201(comet):
+    # the extent-24 FP64 workload: A[a,e,b] of 24^3 by (2,0,1), bit-exact
+    A = synth.tensor((24, 24, 24), 0, 0)
+    T = run(comet, A, (2, 0, 1))
+    assert T.tobytes(order="F") == oracle.transpose(A, (2, 0, 1)).tobytes(order="F")
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("perm", list(itertools.permutations(range(4))))
+def test_rank4_all_perms_ragged(comet, dtype, perm):
+    A = synth.tensor((7, 8, 5, 12), 1, 0, dtype=dtype)
+    T = run(comet, A, perm)
+    assert T.tobytes(order="F") == oracle.transpose(A, perm).tobytes(order="F")
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("case", range(8))
+def test_rank6_random_perms(comet, dtype, case):
+    rng = np.random.default_rng(100 + case)
+    perm = tuple(int(p) for p in rng.permutation(6))
+    ext = tuple(int(e) for e in synth.uniform_extents(7, case, 6, 2, 9))
+    A = synth.tensor(ext, 2, case, dtype=dtype)
+    T = run(comet, A, perm)
+    assert T.tobytes(order="F") == oracle.transpose(A, perm).tobytes(order="F")
+
+
+def test_special_bit_patterns_survive(comet):
+    bits = synth.raw_bits(3, 0, 0, 6 * 10 * 9)
+    A = np.asfortranarray(bits.view(np.float64).reshape((6, 10, 9), order="F")).copy(order="F")
+    flat = A.reshape(-1, order="F")
+    flat[:5] = [np.nan, -0.0, 5e-324, -np.inf, 1e-310]
+    A = np.asfortranarray(flat.reshape((6, 10, 9), order="F"))
+    T = run(comet, A, (1, 2, 0))
+    assert T.tobytes(order="F") == oracle.transpose(A, (1, 2, 0)).tobytes(order="F")
+    A32 = np.asfortranarray(bits.astype(np.uint32).view(np.float32).reshape((12, 10, 9), order="F"))
+    T32 = run(comet, A32, (2, 0, 1))
+    assert T32.tobytes(order="F") == oracle.transpose(A32, (2, 0, 1)).tobytes(order="F")
+
+
+@pytest.mark.parametrize("shape,perm", [((1,), (0,)), ((5, 1, 3), (1, 2, 0)), ((1, 1, 1), (2, 1, 0)),
+                                         ((300, 7), (1, 0)), ((8, 8, 8, 8, 8, 8), (5, 4, 3, 2, 1, 0)),
+                                         ((64, 3, 64), (2, 1, 0)), ((9, 130, 70), (0, 2, 1))])
+def test_edge_shapes(comet, shape, perm):
+    for dtype in (np.float32, np.float64):
+        A = synth.tensor(shape, 4, 0, dtype=dtype)
+        T = run(comet, A, perm)
+        assert T.tobytes(order="F") == oracle.transpose(A, perm).tobytes(order="F")
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_64mib_rank4(comet, dtype):
+    # a size of the transpose sweep: 64 MiB, many tiles, full comparison
+    n = (64 << 20) // np.dtype(dtype).itemsize
+    ext = (32, 64, 64, n // (32 * 64 * 64))
+    A = synth.tensor(ext, 5, 0, dtype=dtype)
+    for perm in [(1, 3, 0, 2), (3, 2, 1, 0), (0, 2, 1, 3)]:
+        T = run(comet, A, perm)
+        assert np.array_equal(T.view(np.uint8), oracle.transpose(A, perm).view(np.uint8))
+
+
+def test_rejects_bad_arguments(comet):
+    import torch
+    x = torch.zeros(16, device="cuda")
+    with pytest.raises(comet.CometError) as e:
+        comet.transpose(x, [4, 4], [1, 1])
+    assert e.value.name == "COMET_ERR_ARG"
+    with pytest.raises(comet.CometError) as e:
+        comet.transpose(x[1:], [3, 5], [1, 0], out=torch.zeros(15, device="cuda"))
+    assert e.value.name == "COMET_ERR_ALIGN"

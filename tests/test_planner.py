@@ -1,0 +1,198 @@
+"""Host-side tests of the C ABI: symbol exports, parsing, classification, the TTGT form
+enumeration (Section 2 / Section 6) and the multi-operand order (Section 6, Table 1).
+No GPU needed: comet_plan does no device work."""
+import itertools
+import os
+import re
+
+import pytest
+
+import paper_2102_06827_gb300 as comet
+from paper_2102_06827_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2102_06827_gb300 import build
+    build.build()
+
+
+def test_library_exports_every_declared_symbol():
+    header = open(os.path.join(ROOT, "include", "comet.h")).read()
+    declared = set(re.findall(r"\b(comet_[a-z_]+)\s*\(", header))
+    L = comet.lib()
+    for name in declared:
+        assert hasattr(L, name), name
+    assert declared <= set(_lib.EXPORTS) | {"comet_plan_opts_default"}
+    assert "sm_103a" in comet.version()
+
+
+def plan(expr, ext, dtype="f64", **kw):
+    return comet.Plan(expr, ext, dtype, **kw)
+
+
+def test_parse_errors_and_codes():
+    ext = dict(i=3, j=4, k=5)
+    for bad in ["C[i,j] A[i,k]*B[k,j]", "C[i,j = A[i,k]*B[k,j]", "C[i,j] = A[i,k]**B[k,j]",
+                "= A[i]", "C[i] = 2.0"]:
+        with pytest.raises(comet.CometError) as e:
+            plan(bad, ext)
+        assert e.value.name == "COMET_ERR_PARSE", bad
+    with pytest.raises(comet.CometError) as e:
+        plan("C[i,x] = A[i,k]*B[k,j]", ext)
+    assert e.value.name == "COMET_ERR_LABEL"
+    with pytest.raises(comet.CometError) as e:
+        plan("C[i,j] = A[i,k]*B[k,j]", dict(i=3, j=4))
+    assert e.value.name == "COMET_ERR_LABEL"
+    with pytest.raises(comet.CometError) as e:
+        plan("C[i,j] = A[i,k]*B[k,j]", dict(i=3, j=0, k=2))
+    assert e.value.name == "COMET_ERR_SHAPE"
+    # batch label, repeated label, summation inside one operand
+    for unsup in ["C[i,j,b] = A[i,k,b]*B[k,j,b]", "C[i,j] = A[i,i,k]*B[k,j]",
+                  "C[i,j] = A[i,k,l]*B[k,j]", "C[i] = A[i,k]"]:
+        with pytest.raises(comet.CometError) as e:
+            plan(unsup, dict(i=3, j=4, k=5, b=2, l=2))
+        assert e.value.name == "COMET_ERR_UNSUPPORTED", unsup
+    with pytest.raises(comet.CometError) as e:
+        plan("C[i,j] = sum_{j} A[i,k]*B[k,j]", ext)
+    assert e.value.name == "COMET_ERR_LABEL"
+
+
+def test_accepted_forms():
+    ext = dict(i=3, j=4, k=5, l=2)
+    plan("A[i,j] = 2.5 * D[j,i]", ext)                     # ta.copy with alpha
+    plan("C[i,k,l] = 0.5 * A[i,j] * B[j,k,l]", ext)         # alpha * contraction
+    p = plan("D[i,l] = A[i,j] * B[j,k] * C[k,l]", ext)      # multi-operand
+    assert len(p.info["steps"]) == 2
+    plan("C(i,j) += A(i,k) * B(k,j)", ext)
+    plan("C[i,j] -= sum_{k} A[i,k]*B[k,j]", ext)
+
+
+def _form_tuples(expr, ext):
+    p = plan(expr, ext)
+    n = p.info["steps"][0]["n_forms"]
+    forms = []
+    for k in range(n):
+        s = plan(expr, ext, form=k).info["steps"][0]
+        forms.append((s["swap"], tuple(s["M"]), tuple(s["N"]), tuple(s["K"])))
+    return p.info["steps"][0], forms
+
+
+def test_ttgt_enumeration_contains_the_papers_form():
+    # Section 2: C[a,b,c,d] = A[a,e,b,f]*B[d,f,c,e] -> TA[a,b,e,f], TB[e,f,d,c], C_p = TC[a,b,d,c]
+    ext = dict(a=3, b=4, c=5, d=6, e=2, f=7)
+    chosen, forms = _form_tuples("C[a,b,c,d] = A[a,e,b,f] * B[d,f,c,e]", ext)
+    assert (0, ("a", "b"), ("d", "c"), ("e", "f")) in forms
+    # every form uses the same label classes: free(A) = {a,b}, free(B) = {c,d}, K = {e,f}
+    for swap, M, N, K in forms:
+        assert set(K) == {"e", "f"}
+        assert {frozenset(M), frozenset(N)} == {frozenset("ab"), frozenset("cd")}
+    assert len(forms) == 2 * 2 * 2 * 2
+    # the planner's choice puts the output's stride-1 label first in M
+    assert chosen["M"][0] == "a" and chosen["swap"] == 0
+
+
+def test_ccsd_like_form_choice():
+    ext = dict(i=64, j=64, k=64, a=192, b=192, c=192)
+    s = plan("C[i,a,j,b] = A[k,a,c,i] * B[c,b,k,j]", ext, precision="split_bf16").info["steps"][0]
+    # the output's stride-1 label leads M, so the epilogue's warp stores are contiguous
+    assert s["M"] == ["i", "a"] and set(s["N"]) == {"j", "b"} and s["swap"] == 0
+    assert set(s["K"]) == {"k", "c"}
+    assert s["eff_store"] == 1.0
+
+
+def test_flops_and_workspace():
+    ext = dict(a=24, b=24, c=24, d=24, e=24)
+    p = plan("C[a,b,c,d] = A[a,e,b] * B[e,d,c]", ext)
+    assert p.flops == 2 * 24 ** 5
+    assert p.workspace_bytes == 0
+    ps = plan("C[a,b,c,d] = A[a,e,b] * B[e,d,c]", ext, precision="split_bf16")
+    kpad = 24 + (-24) % 8
+    assert ps.workspace_bytes >= 3 * 2 * kpad * (576 + 576)
+
+
+# ---- multi-operand order vs an explicit enumeration of every contraction sequence ----------
+
+def _labels_outside(sub, ops, out):
+    inside = set().union(*[set(ops[i]) for i in sub])
+    outside = set(out).union(*[set(ops[i]) for i in range(len(ops)) if i not in sub])
+    return inside & outside
+
+
+def brute_force_min_flops(ops, out, ext):
+    """Minimum total flops over every sequence of pairwise contractions (all binary trees)."""
+    best = [float("inf")]
+
+    def rec(items, cost):
+        # items: list of (frozenset of operand indices)
+        if len(items) == 1:
+            best[0] = min(best[0], cost)
+            return
+        for x, y in itertools.combinations(range(len(items)), 2):
+            a, b = items[x], items[y]
+            la = _labels_outside(a, ops, out)
+            lb = _labels_outside(b, ops, out)
+            f = 2.0
+            for l in la | lb:
+                f *= ext[l]
+            rest = [items[z] for z in range(len(items)) if z not in (x, y)]
+            rec(rest + [a | b], cost + f)
+
+    rec([frozenset([i]) for i in range(len(ops))], 0.0)
+    return best[0]
+
+
+def _table1_rows():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "table1_expressions.txt")):
+        if not line.strip() or line.startswith("#"):
+            continue
+        rhs, speedup = line.split("|")
+        ops = [t.split(",") for t in re.findall(r"\[([^\]]*)\]", rhs)]
+        ops = [[l.strip() for l in o] for o in ops]
+        counts = {}
+        for o in ops:
+            for l in o:
+                counts[l] = counts.get(l, 0) + 1
+        out = [l for o in ops for l in o if counts[l] == 1]
+        rows.append((rhs.strip(), ops, out, float(speedup)))
+    return rows
+
+
+@pytest.mark.parametrize("row", range(13))
+def test_table1_order_matches_brute_force(row):
+    rhs, ops, out, _ = _table1_rows()[row]
+    # occupied labels i,j,m,n small, virtual labels a,b,c,d,e,f large (synthetic extents)
+    ext = {l: (16 if l in "ijmn" else 48) for o in ops for l in o}
+    expr = f"X[{','.join(out)}] = {rhs}"
+    p = plan(expr, ext)
+    assert p.flops == pytest.approx(brute_force_min_flops(ops, out, ext), rel=1e-12)
+    pn = plan(expr, ext, order="natural")
+    assert pn.flops == pytest.approx(p.flops_natural, rel=1e-12)
+    assert pn.flops >= p.flops
+
+
+def test_chain_order_tie_and_workspace_cap():
+    # D[a,b] = A[a,i,j] * B[i,j,k,l] * C[k,l,b]: (A.B).C and A.(B.C) both cost 3.02e9 flops
+    ext = dict(a=256, b=256, i=48, j=48, k=48, l=48)
+    e = "D[a,b] = A[a,i,j] * B[i,j,k,l] * C[k,l,b]"
+    p = plan(e, ext, dtype="f32", precision="split_bf16")
+    assert p.flops == pytest.approx(2 * 256 * 48 ** 4 + 2 * 256 * 48 ** 2 * 256)
+    assert p.info["order"] in ("((A*B)*C)", "(A*(B*C))")
+    # an outer product A.C would need 256*48^4*256 elements: excluded by a cap
+    pc = plan(e, ext, dtype="f32", workspace_cap=1 << 30)
+    assert pc.flops == p.flops
+    with pytest.raises(comet.CometError) as err:
+        plan(e, ext, dtype="f32", workspace_cap=1024)
+    assert err.value.name == "COMET_ERR_WORKSPACE"
+
+
+def test_transpose_argument_checks():
+    import torch
+    x = torch.empty(8)
+    with pytest.raises(comet.CometError) as e:
+        comet.transpose(x, [2, 4], [0, 0], out=torch.empty(8), stream=0)
+    assert e.value.name == "COMET_ERR_ARG"
