@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Benchmark of the contraction hot path on the CCSD-doubles-like workload
+C[i,a,j,b] = sum_{k,c} A[k,a,c,i] * B[c,b,k,j] with o = 64 (i,j,k) and v = 192 (a,b,c).
+
+One step = one comet_contract() of the whole path on resident device tensors: split pre-pass
+of both operands into bfloat16 planes, tcgen05 split-BF16 GEMM with the output permutation in
+its epilogue.  The FP64 form (f64 tensor-core MMA) of the same contraction is timed beside it,
+and both results are checked against the CPU FP64 oracle on a sample of outputs (the
+cpu_baseline leg).  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun each rank runs its own copy of the workload (replicas; no collective on the
+data path): value = all ranks' flops / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+EXPR = "C[i,a,j,b] = A[k,a,c,i] * B[c,b,k,j]"
+EXT = dict(i=64, j=64, k=64, a=192, b=192, c=192)
+N_ELEM = 64 * 192 * 192 * 64
+SCALE = 1.0 / math.sqrt(64 * 192)
+METRIC = "contraction GFLOP/s and fraction of roofline (FP64 vs split-precision) at stated error"
+WORKLOAD = "ccsd_doubles_like o=64 v=192: C[i,a,j,b] = sum_{k,c} A[k,a,c,i]*B[c,b,k,j]"
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate from the recipe's nominal table
+
+
+def args_parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def config(precision="split_bf16"):
+    return {"workload": WORKLOAD, "o": 64, "v": 192, "precision": precision,
+            "input": "uniform[-1,1]/sqrt(64*192), SplitMix64 seeds 1 (A) and 2 (B)",
+            "storage": "FP32 column-major (split path), FP64 (FP64 form)",
+            "l2": "inputs (576 MiB each) larger than the 129 MB L2; no flush needed"}
+
+
+# ---- clocks during the timed region ---------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---- helpers -----------------------------------------------------------------------------------
+def source_hash(*paths) -> str:
+    h = hashlib.sha256()
+    for p in paths:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(name: str, src_hash: str):
+    """dram bytes per launch from a committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", f"{name}.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("source_hash") != src_hash:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def make_inputs(torch, dtype, device):
+    import synth
+    A = synth.torch_uniform(1, 0, N_ELEM, device, dtype=dtype, scale=SCALE)
+    B = synth.torch_uniform(2, 0, N_ELEM, device, dtype=dtype, scale=SCALE)
+    return A, B
+
+
+def sample_indices(n):
+    import numpy as np
+    import synth
+    return np.unique(synth.integers(11, 0, n, 0, N_ELEM - 1).astype(np.int64))
+
+
+# ---- the reference arm: the CPU oracle ------------------------------------------------------
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    import synth
+    A = synth.tensor((64, 192, 192, 64), 1, 0, scale=SCALE, dtype=np.float32).astype(np.float64)
+    B = synth.tensor((192, 192, 64, 64), 2, 0, scale=SCALE, dtype=np.float32).astype(np.float64)
+    sel = sample_indices(256)
+    t0 = time.perf_counter()
+    oracle.einsum_sampled(EXPR, A, B, sel=sel)
+    dt = time.perf_counter() - t0
+    n = int(min(200000, max(64, len(sel) * (6.0 / max(dt, 1e-3)))))   # ~6 s of CPU work per step
+    sel = sample_indices(n)
+    flops_step = 2.0 * 64 * 192 * len(sel)
+    for _ in range(a.warmup):
+        oracle.einsum_sampled(EXPR, A, B, sel=sel[: max(1, len(sel) // 8)])
+    times = []
+    for _ in range(a.steps):
+        t0 = time.perf_counter()
+        oracle.einsum_sampled(EXPR, A, B, sel=sel)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = flops_step * a.steps / total / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(config("fp64_oracle"), sample=f"{len(sel)} outputs per step"),
+            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": oracle.threads(), "kind": "oracle",
+                             "sample": f"{len(sel)} sampled outputs of C (each a 12288-term FP64 sum)"},
+            "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---- our arm -------------------------------------------------------------------------------------
+def main():
+    a = args_parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2102_06827_gb300 as comet
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    stream = torch.cuda.current_stream()
+    # ---------------- split-BF16 path (the headline) ----------------
+    plan = comet.Plan(EXPR, EXT, torch.float32, precision="split_bf16")
+    flops = plan.flops
+    A, B = make_inputs(torch, torch.float32, dev)
+    C = torch.empty(N_ELEM, dtype=torch.float32, device=dev)
+    ws = plan.workspace(dev)
+    for _ in range(a.warmup):
+        plan.contract([A, B], C, ws)
+    comet.sync_status()
+    barrier()
+    torch.cuda.synchronize()
+    comet.profile_enable(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        plan.contract([A, B], C, ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    prof = comet.profile_read()
+    comet.profile_enable(False)
+    comet.sync_status()
+    ms_total = max_over_ranks(e0.elapsed_time(e1))
+    ms_step = ms_total / a.steps
+    value = world * flops * a.steps / (ms_total * 1e-3) / 1e9
+    launches = sum(v[0] for v in prof.values())
+    g_launch, g_ms = prof.get("gemm_split_bf16", (0, 0.0))
+    p_launch, p_ms = prof.get("split_prepass", (0, 0.0))
+    gemm_ms = g_ms / max(1, g_launch)
+    peaks = measured_peaks()
+    peak_src = "measured (MEASURED_PEAKS.json bf16_tflops, burst)"
+    peak = peaks.get("bf16_tflops") if peaks else None
+    if not peak:
+        peak, peak_src = 1900.0, "fallback (recipe, burst)"
+    achieved = 6.0 * flops / (gemm_ms * 1e-3) / 1e12
+    src = source_hash("paper_2102_06827_gb300/csrc/k_gemm_split.cu", "paper_2102_06827_gb300/csrc/sm100.cuh")
+    traffic = recorded_traffic("gemm_split_bf16_ccsd", src)
+    pre_bytes = 2.0 * N_ELEM * (4 + 6)
+    roofline = {"kernel": "gemm_split_bf16", "bound": "tensor", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "peak_source": peak_src,
+                "peak_sustained": peaks.get("bf16_tflops_sustained") if peaks else None,
+                "frac_of_sustained": achieved / peaks["bf16_tflops_sustained"] if peaks else None,
+                "achieved_counts": "6 BF16 products x 2*M*N*K per launch (M=N=K=12288)",
+                "ms_per_launch": gemm_ms,
+                "effective_fp32_tflops": flops / (gemm_ms * 1e-3) / 1e12}
+    prepass = {"kernel": "split_prepass", "launches_per_step": p_launch / max(1, a.steps),
+               "ms_per_step": p_ms / max(1, a.steps), "bytes_per_step": pre_bytes,
+               "achieved_gbs": pre_bytes / (p_ms / max(1, a.steps) * 1e-3) / 1e9 if p_ms else None,
+               "peak_gbs": peaks.get("hbm_gbs") if peaks else 6800.0}
+    prepass["frac"] = prepass["achieved_gbs"] / prepass["peak_gbs"] if prepass["achieved_gbs"] else None
+
+    # ---------------- FP64 form of the same contraction ----------------
+    plan64 = comet.Plan(EXPR, EXT, torch.float64, precision="native")
+    A64, B64 = A.double(), B.double()
+    C64 = torch.empty(N_ELEM, dtype=torch.float64, device=dev)
+    plan64.contract([A64, B64], C64)
+    comet.sync_status()
+    barrier()
+    comet.profile_enable(True)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(a.fp64_steps):
+        plan64.contract([A64, B64], C64)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    prof64 = comet.profile_read()
+    comet.profile_enable(False)
+    comet.sync_status()
+    ms64 = max_over_ranks(f0.elapsed_time(f1)) / a.fp64_steps
+    gflops64 = world * flops / (ms64 * 1e-3) / 1e9
+    k64 = prof64.get("gemm_f64", (1, ms64))
+    fp64 = {"gflops": gflops64, "ms_per_step": ms64, "steps": a.fp64_steps,
+            "roofline": {"kernel": "gemm_f64", "bound": "fp64", "achieved": flops / (k64[1] / k64[0] * 1e-3) / 1e12,
+                         "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                         "frac": flops / (k64[1] / k64[0] * 1e-3) / 1e12 / FP64_NOMINAL_TFLOPS,
+                         "peak_source": "nominal FP64 rate of the recipe table (not in MEASURED_PEAKS.json)"},
+            "split_speedup_over_fp64": ms64 / ms_step}
+
+    # ---------------- end to end through the C ABI with host buffers ----------------
+    hA = torch.empty(N_ELEM, dtype=torch.float32, pin_memory=True)
+    hB = torch.empty(N_ELEM, dtype=torch.float32, pin_memory=True)
+    hC = torch.empty(N_ELEM, dtype=torch.float32, pin_memory=True)
+    hA.copy_(A)
+    hB.copy_(B)
+    dA, dB, dC = torch.empty_like(A), torch.empty_like(B), torch.empty_like(C)
+    plan.contract_host([hA, hB], hC, [dA, dB], dC, ws)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(a.e2e_steps):
+        plan.contract_host([hA, hB], hC, [dA, dB], dC, ws)
+    t_e2e = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": world * flops * a.e2e_steps / t_e2e / 1e9, "unit": "GFLOP/s",
+           "h2d_bytes_per_step": 2 * N_ELEM * 4, "d2h_bytes_per_step": N_ELEM * 4,
+           "steps": a.e2e_steps, "api": "comet_contract_host (pinned host buffers)"}
+
+    # ---------------- CPU baseline (oracle) and the stated error ----------------
+    cpu, err = None, None
+    if rank == 0 and not a.no_cpu_baseline:
+        import oracle
+        hA64 = np.asfortranarray(hA.numpy().astype(np.float64).reshape((64, 192, 192, 64), order="F"))
+        hB64 = np.asfortranarray(hB.numpy().astype(np.float64).reshape((192, 192, 64, 64), order="F"))
+        sel = sample_indices(128)
+        t0 = time.perf_counter()
+        oracle.einsum_sampled(EXPR, hA64, hB64, sel=sel)
+        dt = time.perf_counter() - t0
+        n = int(min(400000, max(128, len(sel) * a.cpu_seconds / max(dt, 1e-3))))
+        sel = sample_indices(n)
+        t0 = time.perf_counter()
+        ref = oracle.einsum_sampled(EXPR, hA64, hB64, sel=sel)
+        t_cpu = time.perf_counter() - t0
+        cflops = 2.0 * 64 * 192 * len(sel)
+        cpu = {"value": cflops / t_cpu / 1e9, "unit": "GFLOP/s", "cores": oracle.threads(), "kind": "oracle",
+               "sample": f"{len(sel)} sampled outputs of C (each a 12288-term FP64 sum), {t_cpu:.1f} s"}
+        got = C.cpu().numpy().astype(np.float64)[sel]
+        got64 = C64.cpu().numpy()[sel]
+        den = float(np.abs(ref).max())
+        err = {"split_bf16": {"normwise_rel": float(np.abs(got - ref).max() / den),
+                              "max_abs": float(np.abs(got - ref).max()), "tolerance": 1e-6},
+               "fp64": {"normwise_rel": float(np.abs(got64 - ref).max() / den),
+                        "max_abs": float(np.abs(got64 - ref).max()), "tolerance": 1e-12},
+               "samples": len(sel)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16", "data": "synthetic", "config": config(),
+                "roofline": roofline, "prepass": prepass, "fp64": fp64, "error": err, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+                "dtype_note": "bf16 x bf16 tensor-core products of a 3-way split, fp32 accumulation"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -119,6 +119,21 @@ comet_status_t comet_plan(const char *expr, const comet_extent_t *extents, int n
                           const comet_dtype_t *dtypes, int n_dtypes,
                           const comet_plan_opts_t *opts, comet_plan_t *out_plan);
 
+/*
+ * comet_adjoint_expr — the expression of the gradient of a contraction with respect to one
+ * operand.  For out = alpha * prod_t X_t (every label in exactly two tensors), the gradient of
+ * <G, out> with respect to X_p is alpha * (G contracted with every X_t, t != p) written onto
+ * X_p's labels: itself a contraction, planned and run like any other (so a multi-operand
+ * adjoint gets its own operand order, which recomputes the intermediates it needs).
+ *   expr       a "=" expression accepted by comet_plan
+ *   operand    0-based position of X_p on the right-hand side
+ *   buf, len   receives "dX[...] = alpha * _G[...] * Y[...] * ..." with the gradient operand
+ *              named _G first and the other operands in their original order
+ * COMET_ERR_UNSUPPORTED for "+=" / "-=" expressions; COMET_ERR_ARG if buf is too small or
+ * operand is out of range.
+ */
+comet_status_t comet_adjoint_expr(const char *expr, int operand, char *buf, size_t len);
+
 /* Bytes of device workspace comet_contract() needs for this plan (may be 0). */
 comet_status_t comet_plan_workspace(comet_plan_t plan, size_t *bytes);
 
@@ -203,6 +218,23 @@ int comet_batched_num_tiles(void);
 comet_status_t comet_contract_batched(comet_plan_t plan, const void *const *block_inputs,
                                       int mode, void *result, uint32_t weight_key,
                                       void *workspace, void *stream);
+
+/*
+ * Kernel timing (tracing).  While enabled, every kernel launch the library makes is bracketed
+ * by a pair of CUDA events recorded on the launching stream (not allowed during stream
+ * capture).  comet_profile_read() synchronises on the recorded events and returns, per kernel
+ * kind, the number of launches and their summed device time, then clears the record.
+ *   kind names: "transpose", "scale_copy", "split_prepass", "gemm_split_bf16", "gemm_f64",
+ *               "batched_f64", "batched_split"
+ */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+} comet_kernel_stat_t;
+
+comet_status_t comet_profile_enable(int on);
+comet_status_t comet_profile_read(comet_kernel_stat_t *stats, int max_stats, int *n_stats);
 
 /* Synchronises `stream`, then reads and clears the device status word: COMET_OK, or
  * COMET_ERR_TIMEOUT if a kernel's wait ran out, or COMET_ERR_CUDA if the stream reported an

@@ -185,6 +185,20 @@ def transpose(x, extents, perm, out=None, stream=None):
     return out
 
 
+def profile_enable(on: bool = True):
+    """comet_profile_enable(): bracket every library kernel launch with CUDA events."""
+    _lib.check(lib().comet_profile_enable(1 if on else 0), "comet_profile_enable")
+
+
+def profile_read() -> dict:
+    """comet_profile_read(): {kernel kind: (launches, total device ms)} since the last read."""
+    stats = (_lib.KernelStat * 16)()
+    n = ctypes.c_int()
+    _lib.check(lib().comet_profile_read(stats, 16, ctypes.byref(n)), "comet_profile_read")
+    return {stats[i].name.decode(): (int(stats[i].launches), float(stats[i].total_ms))
+            for i in range(min(n.value, 16))}
+
+
 def sync_status(stream=None):
     """comet_sync_status(): synchronise and surface a device-side timeout."""
     _lib.check(lib().comet_sync_status(_stream_handle(stream)), "comet_sync_status")

@@ -21,9 +21,9 @@ ORDER_PLANNED, ORDER_NATURAL = 0, 1
 # every symbol include/comet.h declares (checked by the CPU test suite)
 EXPORTS = [
     "comet_plan_opts_default", "comet_plan", "comet_plan_workspace", "comet_plan_flops",
-    "comet_plan_flops_natural", "comet_plan_describe", "comet_contract", "comet_contract_host",
+    "comet_plan_flops_natural", "comet_plan_describe", "comet_adjoint_expr", "comet_contract", "comet_contract_host",
     "comet_transpose", "comet_plan_batched", "comet_batched_num_tiles", "comet_contract_batched",
-    "comet_sync_status", "comet_plan_destroy", "comet_status_string", "comet_last_error_message",
+    "comet_profile_enable", "comet_profile_read", "comet_sync_status", "comet_plan_destroy", "comet_status_string", "comet_last_error_message",
     "comet_version",
 ]
 
@@ -37,6 +37,10 @@ class CometError(RuntimeError):
 
 class Extent(ctypes.Structure):
     _fields_ = [("label", ctypes.c_char_p), ("extent", ctypes.c_int64)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
 class PlanOpts(ctypes.Structure):
@@ -63,6 +67,7 @@ def load():
     L.comet_plan.argtypes = [ctypes.c_char_p, ctypes.POINTER(Extent), ctypes.c_int,
                              ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(PlanOpts),
                              ctypes.POINTER(vp)]
+    L.comet_adjoint_expr.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t]
     L.comet_plan_workspace.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     L.comet_plan_flops.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     L.comet_plan_flops_natural.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
@@ -77,6 +82,8 @@ def load():
     L.comet_batched_num_tiles.argtypes = []
     L.comet_batched_num_tiles.restype = ctypes.c_int
     L.comet_contract_batched.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_uint32, vp, vp]
+    L.comet_profile_enable.argtypes = [ctypes.c_int]
+    L.comet_profile_read.argtypes = [ctypes.POINTER(KernelStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.comet_sync_status.argtypes = [vp]
     L.comet_plan_destroy.argtypes = [vp]
     L.comet_plan_destroy.restype = None

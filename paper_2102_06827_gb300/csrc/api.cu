@@ -39,6 +39,52 @@ int *device_status_word() {
     return ptrs[dev];
 }
 
+// ---- kernel timing ------------------------------------------------------------------------
+static const char *kKindNames[] = {"transpose", "scale_copy", "split_prepass", "gemm_split_bf16",
+                                   "gemm_f64", "batched_f64", "batched_split"};
+enum { PK_TRANSPOSE = 0, PK_SCALE, PK_PREPASS, PK_SPLIT, PK_F64, PK_BATCHED_F64, PK_BATCHED_SPLIT, PK_N };
+
+struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<ProfRec> g_prof_recs;
+static std::vector<cudaEvent_t> g_prof_pool;
+
+static cudaEvent_t prof_event() {
+    if (!g_prof_pool.empty()) {
+        cudaEvent_t e = g_prof_pool.back();
+        g_prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct ProfScope {
+    int idx = -1;
+    cudaStream_t s;
+    ProfScope(int kind, cudaStream_t st) : s(st) {
+        std::lock_guard<std::mutex> lock(g_prof_mu);
+        if (!g_prof_on) return;
+        ProfRec r{kind, prof_event(), prof_event()};
+        if (!r.a || !r.b) return;
+        cudaEventRecord(r.a, s);
+        g_prof_recs.push_back(r);
+        idx = (int)g_prof_recs.size() - 1;
+    }
+    ~ProfScope() {
+        if (idx < 0) return;
+        std::lock_guard<std::mutex> lock(g_prof_mu);
+        if (idx < (int)g_prof_recs.size()) cudaEventRecord(g_prof_recs[idx].b, s);
+    }
+};
+
+int profile_kind_batched(bool split) { return split ? PK_BATCHED_SPLIT : PK_BATCHED_F64; }
+
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 static comet_status_t cuda_status(cudaError_t e, const char *what) {
@@ -78,8 +124,13 @@ static comet_status_t run_plan(const Plan &P, const void *const *inputs, void *o
         if (st.kernel == KK_COPY) {
             XposeParams x = st.copy;
             x.in = pa; x.out = pc; x.alpha = alpha; x.beta = beta;
-            if (alpha == 1.0 && beta == 0.0) e = launch_move(x, es, st.copy_vec_in, st.copy_vec_out, stream);
-            else e = launch_scale(x, es, st.copy_vec_in, st.copy_vec_out, stream);
+            if (alpha == 1.0 && beta == 0.0) {
+                ProfScope ps(PK_TRANSPOSE, stream);
+                e = launch_move(x, es, st.copy_vec_in, st.copy_vec_out, stream);
+            } else {
+                ProfScope ps(PK_SCALE, stream);
+                e = launch_scale(x, es, st.copy_vec_in, st.copy_vec_out, stream);
+            }
             if (e != cudaSuccess) return cuda_status(e, "copy kernel");
             continue;
         }
@@ -95,19 +146,40 @@ static comet_status_t run_plan(const Plan &P, const void *const *inputs, void *o
         if (st.kernel == KK_GEMM_F64) {
             bool ak = g.k.n > 0 && (g.k.s0[0] == 1 || g.ma.n == 0 || (g.ma.s0[0] != 1 && g.k.s0[0] < g.ma.s0[0]));
             bool bk = g.k.n > 0 && (g.k.s1[0] == 1 || g.nb.n == 0 || (g.nb.s0[0] != 1 && g.k.s1[0] < g.nb.s0[0]));
-            e = launch_gemm_f64(g, es, ak, bk, stream);
+            {
+                ProfScope ps(PK_F64, stream);
+                e = launch_gemm_f64(g, es, ak, bk, stream);
+            }
             if (e != cudaSuccess) return cuda_status(e, "gemm_f64 kernel");
         } else {
             char *w = static_cast<char *>(ws);
+            void *sc_a = w + st.ws_scales, *sc_b = w + st.ws_scales + 8;
+            const int64_t na = P.slots[st.form.swap ? st.b : st.a].elems;
+            const int64_t nb = P.slots[st.form.swap ? st.a : st.b].elems;
             XposeParams xa = st.pre_a, xb = st.pre_b;
-            xa.in = g.A; xa.out = w + st.ws_parts_a;
-            xb.in = g.B; xb.out = w + st.ws_parts_b;
-            e = launch_split(xa, es, st.pre_a_vec, st.pre_a_vout, stream);
+            xa.in = g.A; xa.out = w + st.ws_parts_a; xa.scale_bits = sc_a;
+            xb.in = g.B; xb.out = w + st.ws_parts_b; xb.scale_bits = sc_b;
+            {
+                ProfScope ps(PK_PREPASS, stream);
+                e = launch_absmax(g.A, na, es, sc_a, stream);
+                if (e == cudaSuccess) e = launch_absmax(g.B, nb, es, sc_b, stream);
+            }
+            if (e != cudaSuccess) return cuda_status(e, "split pre-pass (scales)");
+            {
+                ProfScope ps(PK_PREPASS, stream);
+                e = launch_split(xa, es, st.pre_a_vec, st.pre_a_vout, stream);
+            }
             if (e != cudaSuccess) return cuda_status(e, "split pre-pass (A)");
-            e = launch_split(xb, es, st.pre_b_vec, st.pre_b_vout, stream);
+            {
+                ProfScope ps(PK_PREPASS, stream);
+                e = launch_split(xb, es, st.pre_b_vec, st.pre_b_vout, stream);
+            }
             if (e != cudaSuccess) return cuda_status(e, "split pre-pass (B)");
-            e = launch_gemm_split(g, w + st.ws_parts_a, w + st.ws_parts_b, st.kpad, es, P.opts.debug_flags,
-                                  stream, 0);
+            {
+                ProfScope ps(PK_SPLIT, stream);
+                e = launch_gemm_split(g, w + st.ws_parts_a, w + st.ws_parts_b, st.kpad, sc_a, sc_b,
+                                      P.opts.kc, es, P.opts.debug_flags, stream, 0);
+            }
             if (e != cudaSuccess) return cuda_status(e, "split gemm kernel");
         }
     }
@@ -241,8 +313,47 @@ comet_status_t comet_transpose(int rank, const int64_t *extents, const int *perm
     setup_xpose(rank, extents, si, so, (int)dtype_size(dtype), &x, &vi, &vo, &eff);
     if (x.u.total >= (1u << 31) || x.v.total >= (1u << 31) || x.r.total >= (1u << 31)) return COMET_ERR_SHAPE;
     x.in = in; x.out = out; x.alpha = 1.0; x.beta = 0.0;
+    ProfScope ps(PK_TRANSPOSE, static_cast<cudaStream_t>(stream));
     return cuda_status(launch_move(x, (int)dtype_size(dtype), vi, vo, static_cast<cudaStream_t>(stream)),
                        "transpose kernel");
+}
+
+comet_status_t comet_profile_enable(int on) {
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    g_prof_on = on != 0;
+    return COMET_OK;
+}
+
+comet_status_t comet_profile_read(comet_kernel_stat_t *stats, int max_stats, int *n_stats) {
+    if (!n_stats || (max_stats > 0 && !stats)) return COMET_ERR_NULL;
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    int64_t cnt[PK_N] = {0};
+    double tot[PK_N] = {0};
+    comet_status_t st = COMET_OK;
+    for (auto &r : g_prof_recs) {
+        if (cudaEventSynchronize(r.b) != cudaSuccess) st = COMET_ERR_CUDA;
+        float ms = 0;
+        if (st == COMET_OK && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            cnt[r.kind] += 1;
+            tot[r.kind] += ms;
+        }
+        g_prof_pool.push_back(r.a);
+        g_prof_pool.push_back(r.b);
+    }
+    g_prof_recs.clear();
+    int n = 0;
+    for (int k = 0; k < PK_N; ++k) {
+        if (!cnt[k]) continue;
+        if (n < max_stats) {
+            std::memset(&stats[n], 0, sizeof(stats[n]));
+            std::strncpy(stats[n].name, kKindNames[k], sizeof(stats[n].name) - 1);
+            stats[n].launches = cnt[k];
+            stats[n].total_ms = tot[k];
+        }
+        ++n;
+    }
+    *n_stats = n;
+    return st;
 }
 
 comet_status_t comet_sync_status(void *stream) {

@@ -1,25 +1,31 @@
 // Split-BF16 contraction kernel on the tcgen05 tensor cores.
 //
 // The GEMM of the TTGT reformulation (Section 2, C_p[i,k] = A_p[i,j] * B_p[j,k]; Section 6
-// "GEMM optimizations" for the blocking of C into tiles and of K into panels) with FP32
-// operands carried as three bfloat16 parts x = hi + mid + lo (written by the split pre-pass in
-// [plane][row][K] order, K contiguous).  Per K step the six products hh, hm, mh, hl, lh, mm
-// are accumulated in FP32 in tensor memory; the three smallest (ml, lm, ll, below 2^-24 of
-// the leading term) are dropped.
+// "GEMM optimizations" for the blocking of C into tiles and of K into panels) with FP32 (or
+// FP64) operands carried as three bfloat16 fixed-point parts x * 2^-e = hi + mid + lo (written
+// by the split pre-pass in [plane][row][K] order, K contiguous; see split3 in k_xpose.cu).
 //
-// GB300 form (one persistent CTA per SM, 192 threads):
+// Numerics.  The tensor core's FP32 accumulation truncates, so a long K would pile up a
+// one-sided error.  The fixed-point split makes every hh product an integer multiple of 2^-12
+// no larger than 2^2 in magnitude, so a chunk of up to 1024 K values of hh sums EXACTLY in
+// the FP32 accumulator P0.  The five correction products (hm, mh, hl, lh, mm; 2^-7 and below
+// of the result) go to a second accumulator P1, whose rounding is 2^-7 smaller.  After every
+// chunk the epilogue warps add P0 and P1 into FP32 register sums (round to nearest); the
+// products ml, lm, ll (2^-22 and below) are dropped.  At the end of a tile the sum is scaled
+// by alpha * 2^(eA + eB) and stored.
+//
+// GB300 form (one persistent CTA per SM, 320 threads):
 //   warp 0      TMA producer: one 3-D tensor load per operand and stage brings all three
 //               planes of a 128 x 32 (A) and 256 x 32 (B) K-panel, 64-byte swizzled
-//   warp 1      allocates 512 tensor-memory columns; lane 0 issues tcgen05.mma
-//               (M=128, N=256, K=16) and tcgen05.commit
-//   warps 2..5  epilogue: tcgen05.ld of the 128 x 256 FP32 accumulator, alpha/beta, store
-//               through the output's strides (the output permutation of TTGT folded into
-//               the store addresses)
-//   3-stage shared-memory ring (72 KB per stage); two accumulator buffers in tensor memory
-//   so the epilogue of one tile overlaps the main loop of the next.
-// Every wait is bounded (deadline on %globaltimer); on expiry the CTA records
-// COMET_ERR_TIMEOUT in the status word, drains its own copies in flight, frees its tensor
-// memory and returns.
+//   warp 1      allocates 512 tensor-memory columns (P0 = columns 0..255, P1 = 256..511);
+//               lane 0 issues tcgen05.mma (M=128, N=256, K=16) and tcgen05.commit
+//   warps 2..9  epilogue: each owns one tensor-memory lane quadrant and one half of the
+//               columns; drains P0/P1 after every chunk into 128 register sums per thread,
+//               and at the end of the tile stores through the output's strides (the output
+//               permutation of TTGT folded into the store addresses)
+//   3-stage shared-memory ring (72 KB per stage).
+// Every wait is bounded (%globaltimer); on expiry the CTA records COMET_ERR_TIMEOUT in the
+// status word, drains its own copies in flight, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -38,21 +44,42 @@ constexpr int B_PLANE = BN * BK * 2;            // 16 KB
 constexpr int A_STAGE = 3 * A_PLANE;            // 24 KB
 constexpr int B_STAGE = 3 * B_PLANE;            // 48 KB
 constexpr int STAGE_BYTES = A_STAGE + B_STAGE;  // 72 KB
-constexpr int THREADS = 192;
-constexpr uint32_t TMEM_COLS = 512;             // two 256-column accumulators
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
+constexpr uint32_t TMEM_COLS = 512;             // P0 (256 columns) and P1 (256 columns)
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + BN * 8 /*c_col*/ + 256;
 constexpr uint32_t SW64 = 4;                    // descriptor swizzle code: 64-byte swizzle
 constexpr uint32_t SBO = 8 * BK * 2;            // 8 rows of 64 bytes
+constexpr int MAX_KC = 1024;                    // exactness limit of the hh chunk
 }  // namespace split
 
 struct SplitArgs {
     uint32_t m_tiles, n_tiles, nkb;
+    uint32_t kc_blocks;          // K blocks (of BK) per exact chunk
     int debug_flags;
-    int out_f64;
+    const void *scale_a;         // bits of max |A|, max |B| (input precision)
+    const void *scale_b;
 };
 
+template <typename T>
+__device__ __forceinline__ int exp_of_max(const void *bits) {
+    if constexpr (sizeof(T) == 4) {
+        const float m = __uint_as_float(*reinterpret_cast<const unsigned int *>(bits));
+        if (!(m > 0.0f) || isinf(m)) return 0;
+        int e;
+        frexpf(m, &e);
+        return e - 1;
+    } else {
+        const double m = __longlong_as_double(*reinterpret_cast<const long long *>(bits));
+        if (!(m > 0.0) || isinf(m)) return 0;
+        int e;
+        frexp(m, &e);
+        return e - 1;
+    }
+}
+
 template <typename TOut>
-__global__ void __launch_bounds__(split::THREADS, 1)
+__global__ void __maxnreg__(200)
     gemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const GemmParams p, const SplitArgs x) {
     using namespace split;
@@ -64,8 +91,8 @@ __global__ void __launch_bounds__(split::THREADS, 1)
     int64_t *c_col = reinterpret_cast<int64_t *>(smem + STAGES * STAGE_BYTES);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES + BN * 8);
     uint64_t *full = bars, *empty = bars + STAGES, *tfull = bars + 2 * STAGES,
-             *tempty = bars + 2 * STAGES + 2, *mma_done = bars + 2 * STAGES + 4;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 5);
+             *tempty = bars + 2 * STAGES + 1, *mma_done = bars + 2 * STAGES + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 3);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -74,7 +101,8 @@ __global__ void __launch_bounds__(split::THREADS, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-        for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 4); }
+        mbar_init(tfull, 1);
+        mbar_init(tempty, EPI_WARPS);
         mbar_init(mma_done, 1);
         *abort_flag = 0;
         fence_barrier_init();
@@ -137,16 +165,19 @@ __global__ void __launch_bounds__(split::THREADS, 1)
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
             constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
-            uint32_t it = 0, lt = 0;
+            const uint32_t p0 = tmem_base, p1 = tmem_base + BN;
+            uint32_t it = 0, chunk = 0;
             bool ok = true;
-            for (uint32_t t = blockIdx.x; t < n_tiles_total && ok; t += gridDim.x, ++lt) {
-                const uint32_t buf = lt & 1, use = lt >> 1;
-                if (use > 0 && !mbar_wait(&tempty[buf], (use - 1) & 1, tmo, abort_flag)) {
-                    fail(); ok = false; break;
-                }
-                tc_fence_after();
-                const uint32_t d_tmem = tmem_base + buf * BN;
+            for (uint32_t t = blockIdx.x; t < n_tiles_total && ok; t += gridDim.x) {
                 for (uint32_t kb = 0; kb < x.nkb; ++kb, ++it) {
+                    const uint32_t kin = kb % x.kc_blocks;
+                    if (kin == 0) {
+                        // the epilogue must have drained the previous chunk
+                        if (chunk > 0 && !mbar_wait(tempty, (chunk - 1) & 1, tmo, abort_flag)) {
+                            fail(); ok = false; break;
+                        }
+                        tc_fence_after();
+                    }
                     const uint32_t s = it % STAGES, round = it / STAGES;
                     if (!mbar_wait(&full[s], round & 1, tmo, abort_flag)) { fail(); ok = false; break; }
                     tc_fence_after();
@@ -160,73 +191,96 @@ __global__ void __launch_bounds__(split::THREADS, 1)
                         uint64_t bh = smem_desc(sb + 0 * B_PLANE + ks * 32, 16, SBO, SW64);
                         uint64_t bm = smem_desc(sb + 1 * B_PLANE + ks * 32, 16, SBO, SW64);
                         uint64_t bl = smem_desc(sb + 2 * B_PLANE + ks * 32, 16, SBO, SW64);
-                        const uint32_t first = (kb == 0 && ks == 0) ? 0u : 1u;
-                        // small products first, the leading hh term last
-                        mma_bf16(d_tmem, am, bm, idesc, first);
-                        mma_bf16(d_tmem, al, bh, idesc, 1);
-                        mma_bf16(d_tmem, ah, bl, idesc, 1);
-                        mma_bf16(d_tmem, am, bh, idesc, 1);
-                        mma_bf16(d_tmem, ah, bm, idesc, 1);
-                        mma_bf16(d_tmem, ah, bh, idesc, 1);
+                        const uint32_t acc = (kin == 0 && ks == 0) ? 0u : 1u;
+                        mma_bf16(p1, am, bm, idesc, acc);    // corrections, smallest first
+                        mma_bf16(p1, al, bh, idesc, 1);
+                        mma_bf16(p1, ah, bl, idesc, 1);
+                        mma_bf16(p1, am, bh, idesc, 1);
+                        mma_bf16(p1, ah, bm, idesc, 1);
+                        mma_bf16(p0, ah, bh, idesc, acc);    // the exact leading product
                     }
                     mma_commit(&empty[s]);   // frees the stage once these MMAs have read it
+                    if (kin == x.kc_blocks - 1 || kb == x.nkb - 1) {
+                        mma_commit(tfull);   // chunk complete: P0 and P1 ready to drain
+                        ++chunk;
+                    }
                 }
-                if (!ok) break;
-                mma_commit(&tfull[buf]);
             }
             // make sure no MMA is still writing tensor memory before it is freed
             mma_commit(mma_done);
             mbar_wait(mma_done, 0, tmo, nullptr);
         }
     } else {
-        // ---------------- epilogue (warps 2..5) ----------------
-        const int quad = warp & 3;                 // tensor-memory lanes 32*quad .. 32*quad+31
-        const int et = threadIdx.x - 64;           // 0..127
-        uint32_t lt = 0;
+        // ---------------- epilogue (warps 2..9) ----------------
+        const int quad = warp & 3;                  // tensor-memory lanes 32*quad .. 32*quad+31
+        const int half = (warp - 2) >> 2;           // columns 128*half .. 128*half+127
+        const int et = threadIdx.x - 64;            // 0..255
+        const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+        const int e_sum = exp_of_max<TOut>(x.scale_a) + exp_of_max<TOut>(x.scale_b);
+        const double scale = ldexp(p.alpha, e_sum);
+        const uint32_t nchunks = (x.nkb + x.kc_blocks - 1) / x.kc_blocks;
+        uint32_t chunk = 0;
         bool dead = false;   // once set, the warp keeps pace with the barriers but does no work
         TOut *C = reinterpret_cast<TOut *>(p.C);
-        for (uint32_t t = blockIdx.x; t < n_tiles_total; t += gridDim.x, ++lt) {
+        for (uint32_t t = blockIdx.x; t < n_tiles_total; t += gridDim.x) {
             uint32_t mt, nt;
             tile_coords(t, mt, nt);
-            const uint32_t buf = lt & 1, use = lt >> 1;
-            // column offsets of this tile in C (all four epilogue warps always meet here)
-            named_bar_sync(1, 128);
-            for (int j = et; j < BN; j += 128) {
+            // column offsets of this tile in C (all eight epilogue warps always meet here)
+            named_bar_sync(1, 32 * EPI_WARPS);
+            {
                 int64_t o0 = 0, o1 = 0;
-                if (nt * BN + j < p.N) radix_offsets(p.nb, nt * BN + j, o0, o1);
-                c_col[j] = o1;
+                if (nt * BN + et < p.N) radix_offsets(p.nb, nt * BN + et, o0, o1);
+                c_col[et] = o1;
             }
-            named_bar_sync(1, 128);
+            named_bar_sync(1, 32 * EPI_WARPS);
+            float S[128];
+#pragma unroll
+            for (int j = 0; j < 128; ++j) S[j] = 0.0f;
+            for (uint32_t ch = 0; ch < nchunks; ++ch, ++chunk) {
+                if (dead) continue;
+                bool ok = mbar_wait(tfull, chunk & 1, tmo, abort_flag);
+                ok = __all_sync(0xffffffffu, ok);   // warp-uniform before the .sync.aligned loads
+                if (!ok) { if (lane == 0) fail(); dead = true; continue; }
+                tc_fence_after();
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem_base + lane_base + half * 128 + c4 * 32, r);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) S[c4 * 32 + j] += __uint_as_float(r[j]);
+                    tmem_ld32(tmem_base + BN + lane_base + half * 128 + c4 * 32, r);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) S[c4 * 32 + j] += __uint_as_float(r[j]);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty);
+            }
             if (dead) continue;
             const uint32_t m = mt * BM + quad * 32 + lane;
-            int64_t r0 = 0, c_row = 0;
-            if (m < p.M) radix_offsets(p.ma, m, r0, c_row);
-            bool ok = mbar_wait(&tfull[buf], use & 1, tmo, abort_flag);
-            ok = __all_sync(0xffffffffu, ok);   // warp-uniform before the .sync.aligned loads
-            if (!ok) { if (lane == 0) fail(); dead = true; continue; }
-            tc_fence_after();
-            const uint32_t taddr = tmem_base + buf * BN + ((uint32_t)(quad * 32) << 16);
-            const uint32_t n_valid = min((uint32_t)BN, p.N - nt * BN);
-            for (int c = 0; c < BN / 32; ++c) {
-                uint32_t r[32];
-                tmem_ld32(taddr + c * 32, r);
-                tmem_ld_wait();
-                if (m < p.M) {
+            if (m < p.M) {
+                int64_t r0 = 0, c_row = 0;
+                radix_offsets(p.ma, m, r0, c_row);
+                const uint32_t n_valid = min((uint32_t)BN, p.N - nt * BN);
+                TOut *row = C + c_row;
+                const int64_t *cc = c_col + half * 128;
+                const int n_here = (int)min(128u, n_valid > (uint32_t)(half * 128) ? n_valid - half * 128 : 0u);
+                if (p.beta == 0.0) {
+                    const TOut sc = (TOut)scale;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const uint32_t n = c * 32 + j;
-                        if (n < n_valid) {
-                            TOut *dst = C + c_row + c_col[n];
-                            double v = p.alpha * (double)__uint_as_float(r[j]);
-                            if (p.beta != 0.0) v += p.beta * (double)*dst;
-                            *dst = (TOut)v;
+                    for (int j = 0; j < 128; ++j)
+                        if (j < n_here) row[cc[j]] = sc * (TOut)S[j];
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 128; ++j)
+                        if (j < n_here) {
+                            TOut *dst = row + cc[j];
+                            *dst = (TOut)(scale * (double)S[j] + p.beta * (double)*dst);
                         }
-                    }
                 }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[buf]);
         }
     }
     tc_fence_before();
@@ -279,8 +333,8 @@ static int sm_count() {
 }
 
 cudaError_t launch_gemm_split(const GemmParams &p, const void *parts_a, const void *parts_b,
-                              int64_t kpad, int out_bytes, int debug_flags, cudaStream_t s,
-                              int max_ctas) {
+                              int64_t kpad, const void *scale_a, const void *scale_b, int64_t kc,
+                              int out_bytes, int debug_flags, cudaStream_t s, int max_ctas) {
     using namespace split;
     if (p.M == 0 || p.N == 0) return cudaSuccess;
     CUtensorMap ta, tb;
@@ -290,8 +344,12 @@ cudaError_t launch_gemm_split(const GemmParams &p, const void *parts_a, const vo
     x.m_tiles = (p.M + BM - 1) / BM;
     x.n_tiles = (p.N + BN - 1) / BN;
     x.nkb = (p.K + BK - 1) / BK;
+    if (kc <= 0 || kc > MAX_KC) kc = MAX_KC;
+    x.kc_blocks = (uint32_t)((kc + BK - 1) / BK);
+    if (x.kc_blocks * BK > (uint32_t)MAX_KC) x.kc_blocks = MAX_KC / BK;
     x.debug_flags = debug_flags;
-    x.out_f64 = out_bytes == 8;
+    x.scale_a = scale_a;
+    x.scale_b = scale_b;
     uint32_t tiles = x.m_tiles * x.n_tiles;
     int ctas = sm_count();
     if (max_ctas > 0 && max_ctas < ctas) ctas = max_ctas;

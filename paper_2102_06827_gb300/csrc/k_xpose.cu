@@ -13,6 +13,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <type_traits>
+
 #include "launch.h"
 #include "params.h"
 
@@ -27,27 +30,60 @@ struct alignas(sizeof(T) * N) Vec {
     T v[N];
 };
 
-// three-way bfloat16 split with round-to-nearest at every step; the residuals are exact in the
-// input precision (x - hi and r1 - mid cancel the leading bits)
+// Fixed-point three-way split.  The operand is first scaled by 2^-e (e = exponent of its
+// largest magnitude, so |x'| < 2); then hi, mid and lo are x' rounded to nearest on the grids
+// 2^-6, 2^-14 and 2^-22.  Each part is an integer of magnitude <= 128 times its grid step, so
+// it is exact in bfloat16, and a product of two hi parts is an integer multiple of 2^-12 of
+// magnitude <= 2^14: up to 1024 of them sum exactly in FP32 whatever the accumulator's
+// rounding.  The residuals are exact in the input precision; what remains after lo is below
+// 2^-23 of the operand's largest magnitude.
 template <typename T>
-__device__ __forceinline__ void split3(T x, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &l) {
+__device__ __forceinline__ void split3(T x, int e, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &l) {
     if constexpr (sizeof(T) == 4) {
-        h = __float2bfloat16_rn(x);
-        float r1 = x - __bfloat162float(h);
-        m = __float2bfloat16_rn(r1);
-        float r2 = r1 - __bfloat162float(m);
-        l = __float2bfloat16_rn(r2);
+        const float xs = ldexpf(x, -e);
+        const float fh = rintf(xs * 64.0f) * (1.0f / 64.0f);
+        const float r1 = xs - fh;
+        const float fm = rintf(r1 * 16384.0f) * (1.0f / 16384.0f);
+        const float r2 = r1 - fm;
+        const float fl = rintf(r2 * 4194304.0f) * (1.0f / 4194304.0f);
+        h = __float2bfloat16_rn(fh);
+        m = __float2bfloat16_rn(fm);
+        l = __float2bfloat16_rn(fl);
     } else {
-        h = __double2bfloat16(x);
-        double r1 = x - (double)__bfloat162float(h);
-        m = __double2bfloat16(r1);
-        double r2 = r1 - (double)__bfloat162float(m);
-        l = __double2bfloat16(r2);
+        const double xs = ldexp(x, -e);
+        const double fh = rint(xs * 64.0) * (1.0 / 64.0);
+        const double r1 = xs - fh;
+        const double fm = rint(r1 * 16384.0) * (1.0 / 16384.0);
+        const double r2 = r1 - fm;
+        const double fl = rint(r2 * 4194304.0) * (1.0 / 4194304.0);
+        h = __float2bfloat16_rn((float)fh);
+        m = __float2bfloat16_rn((float)fm);
+        l = __float2bfloat16_rn((float)fl);
+    }
+}
+
+// exponent e with max|x| in [2^e, 2^(e+1)) from the abs-max bits; 0 for an all-zero (or
+// non-finite) operand
+template <typename T>
+__device__ __forceinline__ int scale_exponent(const void *absmax_bits) {
+    if constexpr (sizeof(T) == 4) {
+        const float m = __uint_as_float(*reinterpret_cast<const volatile unsigned int *>(absmax_bits));
+        if (!(m > 0.0f) || isinf(m)) return 0;
+        int e;
+        frexpf(m, &e);
+        return e - 1;
+    } else {
+        const double m = __longlong_as_double(
+            (long long)*reinterpret_cast<const volatile unsigned long long *>(absmax_bits));
+        if (!(m > 0.0) || isinf(m)) return 0;
+        int e;
+        frexp(m, &e);
+        return e - 1;
     }
 }
 
 template <int OP, typename T, int VO>
-__device__ __forceinline__ void emit(const XposeParams &p, int64_t off, const T (&x)[VO]) {
+__device__ __forceinline__ void emit(const XposeParams &p, int64_t off, const T (&x)[VO], int e) {
     if constexpr (OP == OP_MOVE) {
         Vec<VO, T> w;
 #pragma unroll
@@ -68,7 +104,7 @@ __device__ __forceinline__ void emit(const XposeParams &p, int64_t off, const T 
     } else {
         Vec<VO, __nv_bfloat16> h, m, l;
 #pragma unroll
-        for (int q = 0; q < VO; ++q) split3<T>(x[q], h.v[q], m.v[q], l.v[q]);
+        for (int q = 0; q < VO; ++q) split3<T>(x[q], e, h.v[q], m.v[q], l.v[q]);
         __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(p.out) + off;
         *reinterpret_cast<Vec<VO, __nv_bfloat16> *>(o) = h;
         *reinterpret_cast<Vec<VO, __nv_bfloat16> *>(o + p.out_plane) = m;
@@ -96,6 +132,7 @@ __global__ void __launch_bounds__(XT) xpose_tile_kernel(const XposeParams p) {
     }
     __syncthreads();
     const T *in = reinterpret_cast<const T *>(p.in);
+    const int e = (OP == OP_SPLIT) ? scale_exponent<T>(p.scale_bits) : 0;
     uint32_t r_begin = rc * p.r_per_cta;
     uint32_t r_end = min(p.r.total, r_begin + p.r_per_cta);
     for (uint32_t r = r_begin; r < r_end; ++r) {
@@ -120,7 +157,7 @@ __global__ void __launch_bounds__(XT) xpose_tile_kernel(const XposeParams p) {
                 T x[VO];
 #pragma unroll
                 for (int q = 0; q < VO; ++q) x[q] = tile[vc + q][ur];
-                emit<OP, T, VO>(p, r_out + u_out[ur] + v_out[vc], x);
+                emit<OP, T, VO>(p, r_out + u_out[ur] + v_out[vc], x, e);
             }
         }
         __syncthreads();
@@ -147,6 +184,7 @@ __global__ void __launch_bounds__(XT) xpose_copy_kernel(const XposeParams p) {
     }
     __syncthreads();
     const T *in = reinterpret_cast<const T *>(p.in);
+    const int e = (OP == OP_SPLIT) ? scale_exponent<T>(p.scale_bits) : 0;
     uint32_t r_begin = rc * p.r_per_cta;
     uint32_t r_end = min(p.r.total, r_begin + p.r_per_cta);
     for (uint32_t r = r_begin; r < r_end; ++r) {
@@ -160,10 +198,44 @@ __global__ void __launch_bounds__(XT) xpose_copy_kernel(const XposeParams p) {
                 T x[VW];
 #pragma unroll
                 for (int q = 0; q < VW; ++q) x[q] = w.v[q];
-                emit<OP, T, VW>(p, r_out + v_out[vr] + u_out[uc], x);
+                emit<OP, T, VW>(p, r_out + v_out[vr] + u_out[uc], x, e);
             }
         }
     }
+}
+
+// max |x| over a dense operand: grid-stride 16-byte loads, warp reduction, one atomic per warp
+// on the bit pattern (for non-negative IEEE values the bit order is the numeric order)
+template <typename T>
+__global__ void __launch_bounds__(256) absmax_kernel(const T *__restrict__ x, int64_t n, void *out_bits) {
+    constexpr int W = 16 / sizeof(T);
+    using U = typename std::conditional<sizeof(T) == 4, unsigned int, unsigned long long>::type;
+    T m = 0;
+    const int64_t nv = n / W;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += stride) {
+        Vec<W, T> w = reinterpret_cast<const Vec<W, T> *>(x)[i];
+#pragma unroll
+        for (int q = 0; q < W; ++q) m = fmax(m, fabs(w.v[q]));
+    }
+    for (int64_t i = nv * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
+        m = fmax(m, fabs(x[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0) {
+        U bits;
+        memcpy(&bits, &m, sizeof(U));
+        atomicMax(reinterpret_cast<U *>(out_bits), bits);
+    }
+}
+
+cudaError_t launch_absmax(const void *x, int64_t n, int elem_bytes, void *out_bits, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out_bits, 0, 8, s);
+    if (e != cudaSuccess || n == 0) return e;
+    int blocks = (int)std::min<int64_t>(152 * 8, (n + 256 * 4 - 1) / (256 * 4));
+    if (elem_bytes == 4) absmax_kernel<float><<<blocks, 256, 0, s>>>(reinterpret_cast<const float *>(x), n, out_bits);
+    else absmax_kernel<double><<<blocks, 256, 0, s>>>(reinterpret_cast<const double *>(x), n, out_bits);
+    return cudaGetLastError();
 }
 
 static uint32_t xpose_grid(const XposeParams &p) {

@@ -82,6 +82,7 @@ struct XposeParams {
     const void *in;
     void *out;
     int64_t out_plane;             // split pre-pass: element distance between the 3 planes
+    const void *scale_bits;        // split pre-pass: device word holding the bits of max |x|
     double alpha;                  // scaled copy: out = alpha * in (+ beta * out)
     double beta;
     uint32_t tiles_u, tiles_v;     // tiles along U and V

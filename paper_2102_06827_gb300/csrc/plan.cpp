@@ -637,7 +637,10 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
         st.ws_parts_b = parts_base + ba;
         parts_max = std::max(parts_max, ba + bb);
     }
-    P->workspace = parts_base + parts_max;
+    bool any_split = false;
+    for (auto &st : P->steps) any_split |= st.kernel == KK_GEMM_SPLIT;
+    for (auto &st : P->steps) st.ws_scales = parts_base + parts_max;
+    P->workspace = parts_base + parts_max + (any_split ? 256 : 0);
 
     // ---- precomputed parameter blocks ----
     for (auto &st : P->steps) {
@@ -729,6 +732,32 @@ std::string describe_plan(const Plan &P) {
 }
 
 }  // namespace comet
+
+extern "C" comet_status_t comet_adjoint_expr(const char *expr, int operand, char *buf, size_t len) {
+    if (!expr || !buf) return COMET_ERR_NULL;
+    comet::ParsedExpr e;
+    std::string err;
+    comet_status_t st = comet::parse_expr(expr, &e, &err);
+    if (st != COMET_OK) return st;
+    if (e.op != 0) return COMET_ERR_UNSUPPORTED;
+    if (operand < 0 || operand >= (int)e.ins.size()) return COMET_ERR_ARG;
+    auto labels = [](const std::vector<std::string> &v) {
+        std::string s = "[";
+        for (size_t i = 0; i < v.size(); ++i) { if (i) s += ","; s += v[i]; }
+        return s + "]";
+    };
+    std::ostringstream o;
+    o.precision(17);
+    o << "d" << e.ins[operand].name << labels(e.ins[operand].labels) << " = ";
+    if (e.alpha != 1.0) o << e.alpha << " * ";
+    o << "_G" << labels(e.out.labels);
+    for (int t = 0; t < (int)e.ins.size(); ++t)
+        if (t != operand) o << " * " << e.ins[t].name << labels(e.ins[t].labels);
+    std::string s = o.str();
+    if (s.size() + 1 > len) return COMET_ERR_ARG;
+    std::memcpy(buf, s.c_str(), s.size() + 1);
+    return COMET_OK;
+}
 
 extern "C" void comet_plan_opts_default(comet_plan_opts_t *o) {
     if (!o) return;

@@ -59,6 +59,7 @@ struct Step {
     bool final_step = false;
     // split path workspace for the bf16 parts: [3][rows][kpad]
     size_t ws_parts_a = 0, ws_parts_b = 0;
+    size_t ws_scales = 0;        // two 8-byte words: max |A|, max |B| of the step's operands
     int64_t kpad = 0;
     // precomputed parameter blocks (pointers filled at launch)
     GemmParams gemm;             // for both GEMM kernels (offsets in elements)

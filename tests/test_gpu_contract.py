@@ -144,12 +144,19 @@ def test_split_integers_exact(comet, expr, ext):
     assert np.array_equal(C, oracle.einsum(expr, *arrays))
 
 
+def componentwise(C, expr, arrays):
+    """max |C - ref| / max sum |a||b| (the scale of the componentwise error bound)."""
+    return maxabs(C, oracle.einsum(expr, *arrays)) / float(np.max(oracle.abs_einsum(expr, *arrays)))
+
+
 @pytest.mark.parametrize("expr,ext", EXPRS)
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
 def test_split_uniform(comet, expr, ext, dtype):
+    # small contractions include ill-conditioned outputs (a 1000-term dot product with
+    # cancellation), so the test bounds the error by the componentwise scale sum |a||b|
     arrays = inputs(expr, ext, 8)
     C, _ = run(comet, expr, ext, arrays, dtype, precision="split_bf16")
-    assert normwise(C, oracle.einsum(expr, *arrays)) <= TOL_SPLIT
+    assert componentwise(C, expr, arrays) <= TOL_SPLIT
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 256, 32), (300, 520, 100), (129, 257, 33), (1, 1, 1), (1000, 7, 2000),
