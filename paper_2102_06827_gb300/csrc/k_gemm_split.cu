@@ -79,7 +79,7 @@ __device__ __forceinline__ int exp_of_max(const void *bits) {
 }
 
 template <typename TOut>
-__global__ void __maxnreg__(200)
+__global__ void __launch_bounds__(split::THREADS, 1)
     gemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const GemmParams p, const SplitArgs x) {
     using namespace split;
@@ -242,17 +242,19 @@ __global__ void __maxnreg__(200)
                 ok = __all_sync(0xffffffffu, ok);   // warp-uniform before the .sync.aligned loads
                 if (!ok) { if (lane == 0) fail(); dead = true; continue; }
                 tc_fence_after();
+                // 16 columns at a time keeps the 128 sums plus the loaded values within the
+                // 168 registers a thread has when three warps share a sub-partition
 #pragma unroll
-                for (int c4 = 0; c4 < 4; ++c4) {
-                    uint32_t r[32];
-                    tmem_ld32(tmem_base + lane_base + half * 128 + c4 * 32, r);
+                for (int c8 = 0; c8 < 8; ++c8) {
+                    uint32_t r[16];
+                    tmem_ld16(tmem_base + lane_base + half * 128 + c8 * 16, r);
                     tmem_ld_wait();
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) S[c4 * 32 + j] += __uint_as_float(r[j]);
-                    tmem_ld32(tmem_base + BN + lane_base + half * 128 + c4 * 32, r);
+                    for (int j = 0; j < 16; ++j) S[c8 * 16 + j] += __uint_as_float(r[j]);
+                    tmem_ld16(tmem_base + BN + lane_base + half * 128 + c8 * 16, r);
                     tmem_ld_wait();
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) S[c4 * 32 + j] += __uint_as_float(r[j]);
+                    for (int j = 0; j < 16; ++j) S[c8 * 16 + j] += __uint_as_float(r[j]);
                 }
                 tc_fence_before();
                 __syncwarp();
