@@ -48,7 +48,41 @@ def args_parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", default=None, choices=["split", "f64", "transpose"],
+                    help="run one warm-up and one timed launch of a smaller case (for ncu) and exit")
     return ap.parse_args()
+
+
+def run_profile_case(case: str) -> int:
+    """Small cases for ncu captures: inputs above the 129 MB L2, a few GB on the device."""
+    import torch
+    import paper_2102_06827_gb300 as comet
+    import synth
+    dev = torch.device("cuda", 0)
+    if case == "transpose":
+        ext, perm = (64, 128, 128, 256), (3, 1, 0, 2)      # 1 GiB FP32, stride-1 dim moves
+        n = 64 * 128 * 128 * 256
+        x = synth.torch_uniform(5, 0, n, dev, dtype=torch.float32)
+        y = torch.empty_like(x)
+        for _ in range(2):
+            comet.transpose(x, ext, perm, out=y)
+        comet.sync_status()
+        print(json.dumps({"case": case, "extents": ext, "perm": perm, "bytes": 2 * 4 * n}))
+        return 0
+    o, v = (48, 160) if case == "split" else (16, 48)
+    ext = dict(i=o, j=o, k=o, a=v, b=v, c=v)
+    n = o * v * v * o
+    dt = torch.float32 if case == "split" else torch.float64
+    plan = comet.Plan(EXPR, ext, dt, precision="split_bf16" if case == "split" else "native")
+    A = synth.torch_uniform(1, 0, n, dev, dtype=dt, scale=1.0 / math.sqrt(o * v))
+    B = synth.torch_uniform(2, 0, n, dev, dtype=dt, scale=1.0 / math.sqrt(o * v))
+    C = torch.empty(n, dtype=dt, device=dev)
+    ws = plan.workspace(dev)
+    for _ in range(2):
+        plan.contract([A, B], C, ws)
+    comet.sync_status()
+    print(json.dumps({"case": case, "extents": ext, "flops": plan.flops, "workspace": plan.workspace_bytes}))
+    return 0
 
 
 def config(precision="split_bf16"):
@@ -189,6 +223,8 @@ def main():
     a = args_parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.profile_case:
+        return run_profile_case(a.profile_case)
     import numpy as np
     import torch
     import torch.distributed as dist
