@@ -161,6 +161,32 @@ comet_status_t comet_contract(comet_plan_t plan, const void *const *inputs, void
                               void *workspace, void *stream);
 
 /*
+ * comet_contract_noalloc — comet_contract() for callers that cannot allocate device memory.
+ * (The paper has no counterpart: this exists for library users, not for the method.)
+ *
+ * Some callers cannot call cudaMalloc or any allocator at the point where they contract: code
+ * running under a strict memory budget that was fixed at start-up, plug-ins inside a host
+ * application that owns every allocation, or callers with no allocator handle at hand.  This
+ * entry point takes the plan's scratch space (the split path's bfloat16 planes and scale words,
+ * the intermediates of multi-operand plans) from one array that lives inside the library
+ * instead of from a caller buffer.  The caller still passes the inputs and the output.
+ *
+ *   limit      COMET_NOALLOC_MAX_BYTES of scratch; a plan whose comet_plan_workspace() is
+ *              larger is refused with COMET_ERR_WORKSPACE (nothing is launched).
+ *   memory     the array is a static device variable: every GPU that loads the library holds
+ *              these bytes until the process exits, whether or not this entry point is used.
+ *   set-up     the first call on each device looks up the array's device address (with that
+ *              device current); make that first call before any stream capture begins.
+ *   sharing    every call uses the same array, and the array keeps whatever the last call left
+ *              in it (the path clears what it needs cleared).  Calls whose GPU work overlaps,
+ *              e.g. on two streams without ordering between them, race on the array.
+ * Returns the codes of comet_contract().  Allocates nothing, on the host or the device.
+ */
+#define COMET_NOALLOC_MAX_BYTES (32u << 20)
+comet_status_t comet_contract_noalloc(comet_plan_t plan, const void *const *inputs, void *output,
+                                      void *stream);
+
+/*
  * comet_contract_host — the same evaluation from host buffers: copies every input from host
  * to the caller's device buffers, runs comet_contract() and copies the output back, all on
  * `stream`, then synchronises the stream.  host_* may be pageable or pinned host memory;

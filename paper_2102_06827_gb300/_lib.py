@@ -21,7 +21,7 @@ ORDER_PLANNED, ORDER_NATURAL = 0, 1
 # every symbol include/comet.h declares (checked by the CPU test suite)
 EXPORTS = [
     "comet_plan_opts_default", "comet_plan", "comet_plan_workspace", "comet_plan_flops",
-    "comet_plan_flops_natural", "comet_plan_describe", "comet_adjoint_expr", "comet_contract", "comet_contract_host",
+    "comet_plan_flops_natural", "comet_plan_describe", "comet_adjoint_expr", "comet_contract", "comet_contract_noalloc", "comet_contract_host",
     "comet_transpose", "comet_plan_batched", "comet_batched_num_tiles", "comet_contract_batched",
     "comet_profile_enable", "comet_profile_read", "comet_sync_status", "comet_plan_destroy", "comet_status_string", "comet_last_error_message",
     "comet_version",
@@ -73,6 +73,7 @@ def load():
     L.comet_plan_flops_natural.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     L.comet_plan_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     L.comet_contract.argtypes = [vp, ctypes.POINTER(vp), vp, vp, vp]
+    L.comet_contract_noalloc.argtypes = [vp, ctypes.POINTER(vp), vp, vp]
     L.comet_contract_host.argtypes = [vp, ctypes.POINTER(vp), vp, ctypes.POINTER(vp), vp, vp, vp]
     L.comet_transpose.argtypes = [ctypes.c_int, i64p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                   vp, vp, vp]

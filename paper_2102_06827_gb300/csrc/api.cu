@@ -259,6 +259,61 @@ comet_status_t comet_contract(comet_plan_t plan, const void *const *inputs, void
     return run_plan(P, inputs, output, workspace, static_cast<cudaStream_t>(stream));
 }
 
+}  // extern "C"
+
+// ---- scratch-free contraction --------------------------------------------------------------
+// The scratch array behind comet_contract_noalloc().  Host code must not use the name as an
+// address (on the host it is only a stand-in for the device symbol); the device address is
+// looked up once per device below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[COMET_NOALLOC_MAX_BYTES];
+
+namespace comet {
+static void *noalloc_scratch_ptr(comet_status_t *st) {
+    static std::mutex mu;
+    static void *ptrs[128] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) {
+        *st = cuda_status(cudaErrorNoDevice, "no-alloc scratch");
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptrs[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            *st = cuda_status(e != cudaSuccess ? e : cudaErrorInvalidSymbol, "no-alloc scratch address");
+            return nullptr;
+        }
+        ptrs[dev] = p;
+    }
+    *st = COMET_OK;
+    return ptrs[dev];
+}
+}  // namespace comet
+
+extern "C" {
+
+comet_status_t comet_contract_noalloc(comet_plan_t plan, const void *const *inputs, void *output,
+                                      void *stream) {
+    if (!plan || !inputs || !output) return COMET_ERR_NULL;
+    const Plan &P = plan->p;
+    if (P.batched) { set_error("batched plan: use comet_contract_batched"); return COMET_ERR_ARG; }
+    if (P.workspace > COMET_NOALLOC_MAX_BYTES) {
+        set_error("plan needs " + std::to_string(P.workspace) + " bytes of scratch; the no-alloc limit is " +
+                  std::to_string((size_t)COMET_NOALLOC_MAX_BYTES));
+        return COMET_ERR_WORKSPACE;
+    }
+    for (int i = 0; i < P.n_in; ++i) {
+        if (!inputs[i]) return COMET_ERR_NULL;
+        if (!aligned16(inputs[i])) return COMET_ERR_ALIGN;
+    }
+    if (!aligned16(output)) return COMET_ERR_ALIGN;
+    comet_status_t st = COMET_OK;
+    void *scratch = noalloc_scratch_ptr(&st);
+    if (st != COMET_OK) return st;
+    return run_plan(P, inputs, output, scratch, static_cast<cudaStream_t>(stream));
+}
+
 comet_status_t comet_contract_host(comet_plan_t plan, const void *const *host_inputs, void *host_output,
                                    void *const *dev_inputs, void *dev_output, void *workspace, void *stream) {
     if (!plan || !host_inputs || !host_output || !dev_inputs || !dev_output) return COMET_ERR_NULL;

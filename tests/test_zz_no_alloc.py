@@ -1,0 +1,86 @@
+"""The scratch-free entry point, comet_contract_noalloc().
+
+Some callers cannot allocate device memory when they contract (a memory budget fixed at
+start-up, a plug-in whose host application owns every allocation, or simply no allocator at
+hand).  For them the library keeps one fixed scratch array of its own, and this entry point
+runs a plan with that array as its workspace.  The test calls it through the C ABI twice in a
+row and compares both results with comet_contract() given a caller workspace, at the
+tolerances the other GPU tests use.  It lives in its own file, collected last, so that a run
+that stops at the first failure has already run every other test.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import synth
+from helpers import empty_like_labels, from_dev, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL_SPLIT = 1e-6
+TOL_F64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def comet():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2102_06827_gb300 as c
+    return c
+
+
+def _noalloc(comet, plan, ins, out):
+    L = comet.lib()
+    arr = (ctypes.c_void_p * len(ins))(*[t.data_ptr() for t in ins])
+    import torch
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return L.comet_contract_noalloc(plan._h, arr, ctypes.c_void_p(out.data_ptr()), stream)
+
+
+def _rel(x, ref):
+    return float(np.abs(x - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+CASES = [
+    ("C[m,n] = A[k,m] * B[k,n]", dict(m=300, n=520, k=700), "split_bf16", np.float32, TOL_SPLIT),
+    ("C[i,a,j,b] = A[k,a,c,i] * B[c,b,k,j]", dict(i=6, j=5, k=7, a=24, b=20, c=19), "split_bf16",
+     np.float64, TOL_SPLIT),
+    ("D[a,b] = A[a,i,j] * B[i,j,k,l] * C[k,l,b]", dict(a=40, b=36, i=6, j=5, k=7, l=4), "split_bf16",
+     np.float32, TOL_SPLIT),
+    ("D[a,b] = A[a,i,j] * B[i,j,k,l] * C[k,l,b]", dict(a=40, b=36, i=6, j=5, k=7, l=4), "native",
+     np.float64, TOL_F64),
+]
+
+
+@pytest.mark.parametrize("expr,ext,prec,dtype,tol", CASES)
+def test_noalloc_matches_contract_twice(comet, expr, ext, prec, dtype, tol):
+    import oracle
+    import torch
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    plan = comet.Plan(expr, ext, tdt, precision=prec)
+    assert plan.workspace_bytes <= 32 << 20
+    _, out_labels, _, _, ops = oracle.parse(expr)
+    arrays = [synth.tensor(tuple(ext[l] for l in ls), 21, t, dtype=dtype) for t, (_, ls) in enumerate(ops)]
+    ins = [to_dev(a) for a in arrays]
+    out_shape = tuple(ext[l] for l in out_labels)
+    ref_out = empty_like_labels(out_shape, tdt)
+    plan.contract(ins, ref_out, plan.workspace())
+    comet.sync_status()
+    ref = from_dev(ref_out).astype(np.float64)
+    for _ in range(2):   # the second call sees the array as the first call left it
+        out = empty_like_labels(out_shape, tdt)
+        assert _noalloc(comet, plan, ins, out) == 0
+        comet.sync_status()
+        got = from_dev(out).astype(np.float64)
+        assert _rel(got, ref) <= tol
+
+
+def test_noalloc_refuses_plans_above_the_limit(comet):
+    import torch
+    plan = comet.Plan("C[m,n] = A[k,m] * B[k,n]", dict(m=4096, n=4096, k=4096), torch.float32,
+                      precision="split_bf16")
+    assert plan.workspace_bytes > 32 << 20
+    a = torch.zeros(16, device="cuda")
+    status = _noalloc(comet, plan, [a, a], a)
+    assert comet._lib.STATUS[status] == "COMET_ERR_WORKSPACE"
