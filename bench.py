@@ -25,6 +25,7 @@ import subprocess
 import sys
 import tempfile
 import time
+import zlib
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -41,7 +42,7 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate from the recipe's nominal table
 def args_parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=1)
@@ -50,24 +51,83 @@ def args_parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", default=None, choices=["split", "f64", "transpose"],
                     help="run one warm-up and one timed launch of a smaller case (for ncu) and exit")
+    ap.add_argument("--pc-extents", default="64,128,128,256", help="transpose profile case extents")
+    ap.add_argument("--pc-perm", default="3,1,0,2", help="transpose profile case permutation")
+    ap.add_argument("--pc-dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--sweep", default=None, choices=["transpose"],
+                    help="time the transpose sweep (rank-4/rank-6, FP32/FP64, 64 MiB - 2 GiB) and exit")
     return ap.parse_args()
 
 
-def run_profile_case(case: str) -> int:
+def run_transpose_sweep() -> int:
+    """Every case of the sweep: GB/s (read + write bytes / time) against the measured HBM copy
+    bandwidth and against a same-run device-to-device copy; each result checked bit-exactly by
+    applying the inverse permutation (transpose followed by its inverse is the identity)."""
+    import torch
+    import paper_2102_06827_gb300 as comet
+    import synth
+    dev = torch.device("cuda", 0)
+    peaks = measured_peaks() or {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    res = []
+    for name, rank, es, perm, ext in synth.transpose_sweep_cases():
+        n = math.prod(ext)
+        dt = torch.float32 if es == 4 else torch.float64
+        x = synth.torch_uniform(zlib.crc32(name.encode()) & 0xFFFF, 0, n, dev, dtype=dt)
+        y = torch.empty_like(x)
+        z = torch.empty_like(x)
+        for _ in range(2):
+            comet.transpose(x, ext, perm, out=y)
+        reps = max(3, int(2e9 // (2 * es * n)) + 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            comet.transpose(x, ext, perm, out=y)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / reps * 1e-3
+        e0.record()
+        for _ in range(reps):
+            z.copy_(x)
+        e1.record()
+        torch.cuda.synchronize()
+        tc = e0.elapsed_time(e1) / reps * 1e-3
+        inv = [0] * rank
+        for d, p in enumerate(perm):
+            inv[p] = d
+        comet.transpose(y, [ext[p] for p in perm], inv, out=z)
+        comet.sync_status()
+        ok = bool(torch.equal(z.view(torch.int32 if es == 4 else torch.int64),
+                              x.view(torch.int32 if es == 4 else torch.int64)))
+        gbs = 2 * es * n / t / 1e9
+        res.append({"case": name, "perm": perm, "extents": ext, "bytes": es * n, "gbs": round(gbs, 1),
+                    "frac": round(gbs / hbm, 4), "memcpy_gbs": round(2 * es * n / tc / 1e9, 1),
+                    "bit_exact_inverse": ok})
+        del x, y, z
+    fr = sorted(r["frac"] for r in res)
+    print(json.dumps({"sweep": "transpose", "cases": len(res), "hbm_gbs": hbm,
+                      "frac_min": fr[0], "frac_median": fr[len(fr) // 2], "frac_max": fr[-1],
+                      "cases_at_or_above_0.70": sum(f >= 0.70 for f in fr),
+                      "all_bit_exact": all(r["bit_exact_inverse"] for r in res), "results": res}))
+    return 0
+
+
+def run_profile_case(case: str, a=None) -> int:
     """Small cases for ncu captures: inputs above the 129 MB L2, a few GB on the device."""
     import torch
     import paper_2102_06827_gb300 as comet
     import synth
     dev = torch.device("cuda", 0)
     if case == "transpose":
-        ext, perm = (64, 128, 128, 256), (3, 1, 0, 2)      # 1 GiB FP32, stride-1 dim moves
-        n = 64 * 128 * 128 * 256
-        x = synth.torch_uniform(5, 0, n, dev, dtype=torch.float32)
+        ext = tuple(int(e) for e in a.pc_extents.split(","))
+        perm = tuple(int(q) for q in a.pc_perm.split(","))
+        n = math.prod(ext)
+        x = synth.torch_uniform(5, 0, n, dev, dtype=torch.float32 if a.pc_dtype == "f32" else torch.float64)
         y = torch.empty_like(x)
         for _ in range(2):
             comet.transpose(x, ext, perm, out=y)
         comet.sync_status()
-        print(json.dumps({"case": case, "extents": ext, "perm": perm, "bytes": 2 * 4 * n}))
+        print(json.dumps({"case": case, "extents": ext, "perm": perm, "bytes": 2 * x.element_size() * n}))
         return 0
     o, v = (48, 160) if case == "split" else (16, 48)
     ext = dict(i=o, j=o, k=o, a=v, b=v, c=v)
@@ -109,7 +169,7 @@ class ClockSampler:
             os.close(fd)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -224,7 +284,9 @@ def main():
     if a.impl == "reference":
         return run_reference(a)
     if a.profile_case:
-        return run_profile_case(a.profile_case)
+        return run_profile_case(a.profile_case, a)
+    if a.sweep == "transpose":
+        return run_transpose_sweep()
     import numpy as np
     import torch
     import torch.distributed as dist

@@ -22,7 +22,6 @@
 namespace comet {
 
 enum { OP_MOVE = 0, OP_SCALE = 1, OP_SPLIT = 2 };
-constexpr int TT = 64;          // tile edge (elements)
 constexpr int XT = 256;         // threads per CTA
 
 template <int N, typename T>
@@ -112,93 +111,159 @@ __device__ __forceinline__ void emit(const XposeParams &p, int64_t off, const T 
     }
 }
 
-template <int OP, typename T, int VI, int VO>
+constexpr int XTAB = 256;        // largest tile extent along U, V or R that uses offset tables
+
+// Transposing mode: tile (u, v, w) of tu x tv x tw.  Loads run along u (input-contiguous),
+// stores along v (output-contiguous); the tile sits in shared memory as [w][v][u] with an odd
+// row pitch so the column reads of the store phase do not collide in one bank.  Each thread
+// keeps one lane position along the contiguous direction and walks rows, so the index work is
+// one division per vector.  OFF is int32_t when every offset fits, else int64_t.
+template <int OP, typename T, int VI, int VO, typename OFF>
 __global__ void __launch_bounds__(XT) xpose_tile_kernel(const XposeParams p) {
-    __shared__ T tile[TT][TT + 1];
-    __shared__ int64_t u_in[TT], u_out[TT], v_in[TT], v_out[TT];
+    extern __shared__ __align__(16) unsigned char xsm[];
+    T *buf = reinterpret_cast<T *>(xsm);
+    __shared__ OFF u_in[XTAB], u_out[XTAB], v_in[XTAB], v_out[XTAB], w_in[XTAB], w_out[XTAB];
     const int t = threadIdx.x;
-    uint32_t tiles = p.tiles_u * p.tiles_v;
-    uint32_t bt = blockIdx.x % tiles;
-    uint32_t rc = blockIdx.x / tiles;
-    uint32_t u0 = (bt % p.tiles_u) * TT, v0 = (bt / p.tiles_u) * TT;
-    if (t < TT) {
-        int64_t a = 0, b = 0;
-        if (u0 + t < p.u.total) radix_offsets(p.u, u0 + t, a, b);
-        u_in[t] = a; u_out[t] = b;
-    } else if (t < 2 * TT) {
-        int64_t a = 0, b = 0;
-        if (v0 + t - TT < p.v.total) radix_offsets(p.v, v0 + t - TT, a, b);
-        v_in[t - TT] = a; v_out[t - TT] = b;
+    const uint32_t tu = p.tu, tv = p.tv, tw = p.tw;
+    const uint32_t pitch = tu | 1u;
+    uint32_t b = blockIdx.x;
+    const uint32_t bu = b % p.tiles_u;
+    b /= p.tiles_u;
+    const uint32_t bv = b % p.tiles_v, bw = b / p.tiles_v;
+    const uint32_t u0 = bu * tu, v0 = bv * tv, w0 = bw * tw;
+    const uint32_t nu = min(tu, p.u.total - u0), nv = min(tv, p.v.total - v0), nw = min(tw, p.r.total - w0);
+    for (uint32_t i = t; i < tu; i += XT) {
+        int64_t a = 0, c = 0;
+        if (i < nu) radix_offsets(p.u, u0 + i, a, c);
+        u_in[i] = (OFF)a; u_out[i] = (OFF)c;
+    }
+    for (uint32_t i = t; i < tv; i += XT) {
+        int64_t a = 0, c = 0;
+        if (i < nv) radix_offsets(p.v, v0 + i, a, c);
+        v_in[i] = (OFF)a; v_out[i] = (OFF)c;
+    }
+    for (uint32_t i = t; i < tw; i += XT) {
+        int64_t a = 0, c = 0;
+        if (i < nw) radix_offsets(p.r, w0 + i, a, c);
+        w_in[i] = (OFF)a; w_out[i] = (OFF)c;
     }
     __syncthreads();
-    const T *in = reinterpret_cast<const T *>(p.in);
+    const T *__restrict__ in = reinterpret_cast<const T *>(p.in);
     const int e = (OP == OP_SPLIT) ? scale_exponent<T>(p.scale_bits) : 0;
-    uint32_t r_begin = rc * p.r_per_cta;
-    uint32_t r_end = min(p.r.total, r_begin + p.r_per_cta);
-    for (uint32_t r = r_begin; r < r_end; ++r) {
-        int64_t r_in, r_out;
-        radix_offsets(p.r, r, r_in, r_out);
-        // read along U (input-contiguous)
-#pragma unroll 4
-        for (int idx = t; idx < TT * TT / VI; idx += XT) {
-            int vr = idx / (TT / VI), uc = (idx % (TT / VI)) * VI;
-            if (v0 + vr < p.v.total && u0 + uc < p.u.total) {
-                Vec<VI, T> w = *reinterpret_cast<const Vec<VI, T> *>(in + r_in + v_in[vr] + u_in[uc]);
+    // read along u: lanes_l threads per row, each with a fixed u
+    {
+        const uint32_t lanes = (tu + VI - 1) / VI;
+        const uint32_t rpp = XT / lanes;
+        const uint32_t r0 = t / lanes;
+        const uint32_t u = (t - r0 * lanes) * VI;
+        if (r0 < rpp && u < nu) {
+            const OFF ui = u_in[u];
+            const uint32_t rows = tv * tw;
+            // a batch of rows is loaded into registers before any of it is written to shared
+            // memory, so the batch's global loads are all in flight together
+            constexpr int UB = VI * sizeof(T) >= 16 ? 4 : 8;
+            for (uint32_t row0 = r0; row0 < rows; row0 += UB * rpp) {
+                Vec<VI, T> x[UB];
+                bool ok[UB];
 #pragma unroll
-                for (int q = 0; q < VI; ++q) tile[vr][uc + q] = w.v[q];
+                for (int j = 0; j < UB; ++j) {
+                    const uint32_t row = row0 + j * rpp;
+                    const uint32_t w = fd_div(row, p.fd_tv);
+                    const uint32_t v = row - w * tv;
+                    ok[j] = row < rows && v < nv && w < nw;
+                    if (ok[j]) x[j] = *reinterpret_cast<const Vec<VI, T> *>(in + ((int64_t)w_in[w] + v_in[v] + ui));
+                }
+#pragma unroll
+                for (int j = 0; j < UB; ++j) {
+                    if (ok[j]) {
+                        T *dst = buf + (row0 + j * rpp) * pitch + u;
+#pragma unroll
+                        for (int q = 0; q < VI; ++q) dst[q] = x[j].v[q];
+                    }
+                }
             }
         }
-        __syncthreads();
-        // write along V (output-contiguous)
-#pragma unroll 4
-        for (int idx = t; idx < TT * TT / VO; idx += XT) {
-            int ur = idx / (TT / VO), vc = (idx % (TT / VO)) * VO;
-            if (u0 + ur < p.u.total && v0 + vc < p.v.total) {
-                T x[VO];
+    }
+    __syncthreads();
+    // write along v: lanes threads per (u, w) row, each with a fixed v
+    {
+        const uint32_t lanes = (tv + VO - 1) / VO;
+        const uint32_t rpp = XT / lanes;
+        const uint32_t r0 = t / lanes;
+        const uint32_t v = (t - r0 * lanes) * VO;
+        if (r0 < rpp && v < nv) {
+            const OFF vo = v_out[v];
+            const uint32_t rows = tu * tw;
+            constexpr int UL = VO * sizeof(T) >= 16 ? 4 : 16;
+#pragma unroll UL
+            for (uint32_t row = r0; row < rows; row += rpp) {
+                const uint32_t w = fd_div(row, p.fd_tu);
+                const uint32_t u = row - w * tu;
+                if (u < nu && w < nw) {
+                    T x[VO];
+                    const T *src = buf + (w * tv + v) * pitch + u;
 #pragma unroll
-                for (int q = 0; q < VO; ++q) x[q] = tile[vc + q][ur];
-                emit<OP, T, VO>(p, r_out + u_out[ur] + v_out[vc], x, e);
+                    for (int q = 0; q < VO; ++q) x[q] = src[q * pitch];
+                    emit<OP, T, VO>(p, (int64_t)w_out[w] + u_out[u] + vo, x, e);
+                }
             }
         }
-        __syncthreads();
     }
 }
 
-// copy mode: input and output share the stride-1 dim U; V is a second dim for more rows
+// Copy mode: input and output share the stride-1 dims U, so a tile of tu x tw goes straight
+// through registers.  A single fused dim (tu above the table size) is addressed affinely.
 template <int OP, typename T, int VW>
 __global__ void __launch_bounds__(XT) xpose_copy_kernel(const XposeParams p) {
-    __shared__ int64_t u_in[TT], u_out[TT], v_in[TT], v_out[TT];
+    __shared__ int64_t u_in[XTAB], u_out[XTAB], w_in[XTAB], w_out[XTAB];
     const int t = threadIdx.x;
-    uint32_t tiles = p.tiles_u * p.tiles_v;
-    uint32_t bt = blockIdx.x % tiles;
-    uint32_t rc = blockIdx.x / tiles;
-    uint32_t u0 = (bt % p.tiles_u) * TT, v0 = (bt / p.tiles_u) * TT;
-    if (t < TT) {
-        int64_t a = 0, b = 0;
-        if (u0 + t < p.u.total) radix_offsets(p.u, u0 + t, a, b);
-        u_in[t] = a; u_out[t] = b;
-    } else if (t < 2 * TT) {
-        int64_t a = 0, b = 0;
-        if (v0 + t - TT < p.v.total) radix_offsets(p.v, v0 + t - TT, a, b);
-        v_in[t - TT] = a; v_out[t - TT] = b;
+    const uint32_t tu = p.tu, tw = p.tw;
+    const bool affine = tu > (uint32_t)XTAB;
+    const uint32_t bu = blockIdx.x % p.tiles_u, bw = blockIdx.x / p.tiles_u;
+    const uint32_t u0 = bu * tu, w0 = bw * tw;
+    const uint32_t nu = min(tu, p.u.total - u0), nw = min(tw, p.r.total - w0);
+    if (!affine)
+        for (uint32_t i = t; i < tu; i += XT) {
+            int64_t a = 0, c = 0;
+            if (i < nu) radix_offsets(p.u, u0 + i, a, c);
+            u_in[i] = a; u_out[i] = c;
+        }
+    for (uint32_t i = t; i < tw; i += XT) {
+        int64_t a = 0, c = 0;
+        if (i < nw) radix_offsets(p.r, w0 + i, a, c);
+        w_in[i] = a; w_out[i] = c;
     }
     __syncthreads();
-    const T *in = reinterpret_cast<const T *>(p.in);
+    const T *__restrict__ in = reinterpret_cast<const T *>(p.in);
     const int e = (OP == OP_SPLIT) ? scale_exponent<T>(p.scale_bits) : 0;
-    uint32_t r_begin = rc * p.r_per_cta;
-    uint32_t r_end = min(p.r.total, r_begin + p.r_per_cta);
-    for (uint32_t r = r_begin; r < r_end; ++r) {
-        int64_t r_in, r_out;
-        radix_offsets(p.r, r, r_in, r_out);
-#pragma unroll 4
-        for (int idx = t; idx < TT * TT / VW; idx += XT) {
-            int vr = idx / (TT / VW), uc = (idx % (TT / VW)) * VW;
-            if (v0 + vr < p.v.total && u0 + uc < p.u.total) {
-                Vec<VW, T> w = *reinterpret_cast<const Vec<VW, T> *>(in + r_in + v_in[vr] + u_in[uc]);
-                T x[VW];
+    const int64_t s_in = p.u.s0[0], s_out = p.u.s1[0];
+    const uint32_t n = tu * tw;
+    // batches of UB vectors: all loads of a batch are issued before any store, so they are in
+    // flight together (the compiler cannot reorder loads from `in` above stores to `out`)
+    constexpr int UB = VW * sizeof(T) >= 16 ? 4 : (VW * sizeof(T) >= 8 ? 8 : 16);
+    for (uint32_t idx0 = t * VW; idx0 < n; idx0 += UB * XT * VW) {
+        Vec<VW, T> x[UB];
+        int64_t oo[UB];
+        bool ok[UB];
 #pragma unroll
-                for (int q = 0; q < VW; ++q) x[q] = w.v[q];
-                emit<OP, T, VW>(p, r_out + v_out[vr] + u_out[uc], x, e);
+        for (int j = 0; j < UB; ++j) {
+            const uint32_t idx = idx0 + j * XT * VW;
+            const uint32_t w = fd_div(idx, p.fd_tu);
+            const uint32_t u = idx - w * tu;
+            ok[j] = idx < n && u < nu && w < nw;
+            if (ok[j]) {
+                const int64_t oi = affine ? (int64_t)(u0 + u) * s_in : (int64_t)u_in[u];
+                oo[j] = w_out[w] + (affine ? (int64_t)(u0 + u) * s_out : (int64_t)u_out[u]);
+                x[j] = *reinterpret_cast<const Vec<VW, T> *>(in + w_in[w] + oi);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < UB; ++j) {
+            if (ok[j]) {
+                T xs[VW];
+#pragma unroll
+                for (int q = 0; q < VW; ++q) xs[q] = x[j].v[q];
+                emit<OP, T, VW>(p, oo[j], xs, e);
             }
         }
     }
@@ -239,27 +304,38 @@ cudaError_t launch_absmax(const void *x, int64_t n, int elem_bytes, void *out_bi
 }
 
 static uint32_t xpose_grid(const XposeParams &p) {
-    uint64_t tiles = (uint64_t)p.tiles_u * p.tiles_v;
-    uint64_t rch = (p.r.total + p.r_per_cta - 1) / p.r_per_cta;
-    return (uint32_t)(tiles * rch);
+    return p.tiles_u * p.tiles_v * p.tiles_w;
 }
 
 template <int OP, typename T>
 static cudaError_t launch_op(const XposeParams &p, int vi, int vo, cudaStream_t s) {
-    uint32_t g = xpose_grid(p);
+    const uint32_t g = xpose_grid(p);
     if (g == 0) return cudaSuccess;
     constexpr int W = 16 / sizeof(T);
     if (vo < 0) {   // copy mode
         if (-vo >= W && vi >= W) xpose_copy_kernel<OP, T, W><<<g, XT, 0, s>>>(p);
         else xpose_copy_kernel<OP, T, 1><<<g, XT, 0, s>>>(p);
-    } else if (vi >= W && vo >= W) {
-        xpose_tile_kernel<OP, T, W, W><<<g, XT, 0, s>>>(p);
-    } else if (vi >= W) {
-        xpose_tile_kernel<OP, T, W, 1><<<g, XT, 0, s>>>(p);
-    } else if (vo >= W) {
-        xpose_tile_kernel<OP, T, 1, W><<<g, XT, 0, s>>>(p);
+        return cudaGetLastError();
+    }
+    const size_t smem = (size_t)p.tw * p.tv * (p.tu | 1u) * sizeof(T);
+    auto go = [&](auto kern) {
+        static bool set = false;
+        if (!set) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+            set = true;
+        }
+        kern<<<g, XT, smem, s>>>(p);
+    };
+    if (p.off32) {
+        if (vi >= W && vo >= W) go(xpose_tile_kernel<OP, T, W, W, int32_t>);
+        else if (vi >= W) go(xpose_tile_kernel<OP, T, W, 1, int32_t>);
+        else if (vo >= W) go(xpose_tile_kernel<OP, T, 1, W, int32_t>);
+        else go(xpose_tile_kernel<OP, T, 1, 1, int32_t>);
     } else {
-        xpose_tile_kernel<OP, T, 1, 1><<<g, XT, 0, s>>>(p);
+        if (vi >= W && vo >= W) go(xpose_tile_kernel<OP, T, W, W, int64_t>);
+        else if (vi >= W) go(xpose_tile_kernel<OP, T, W, 1, int64_t>);
+        else if (vo >= W) go(xpose_tile_kernel<OP, T, 1, W, int64_t>);
+        else go(xpose_tile_kernel<OP, T, 1, 1, int64_t>);
     }
     return cudaGetLastError();
 }

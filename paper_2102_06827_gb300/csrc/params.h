@@ -75,8 +75,9 @@ CM_HD void radix_offsets(const Radix &r, uint32_t g, int64_t &o0, int64_t &o1) {
 
 // Pure permutation / element-wise tiled copy (transpose engine).  The tensor's dims are split
 // into three groups: U (leading input dims: contiguous reads), V (leading output dims:
-// contiguous writes) and R (the rest).  A CTA moves a TU x TV tile of (u, v) for one or more
-// r.  s0 = input strides, s1 = output strides (elements).
+// contiguous writes) and R (the rest).  A CTA moves one TU x TV x TW tile of (u, v, r) through
+// shared memory: reads run along u, writes along v (along u when V is empty: "copy mode",
+// input and output share their stride-1 dim).  s0 = input strides, s1 = output strides.
 struct XposeParams {
     Radix u, v, r;
     const void *in;
@@ -85,9 +86,13 @@ struct XposeParams {
     const void *scale_bits;        // split pre-pass: device word holding the bits of max |x|
     double alpha;                  // scaled copy: out = alpha * in (+ beta * out)
     double beta;
-    uint32_t tiles_u, tiles_v;     // tiles along U and V
-    uint32_t r_per_cta;            // R indices handled by one CTA
+    uint32_t tu, tv, tw;           // tile extents along U, V and R (tu*tv*tw <= kXposeTile)
+    uint32_t tiles_u, tiles_v, tiles_w;
+    FastDiv fd_tu, fd_tv, fd_tuv;  // division by tu, tv and tu*tv inside the tile
+    int off32;                     // every input and output offset is below 2^31
 };
+
+constexpr int kXposeTile = 4096;   // elements per tile (32 KB of FP64, 16 KB of FP32)
 
 // Binary contraction as a GEMM over fused groups: C[m,n] = alpha * sum_k A[m,k] B[k,n]
 // (+ beta C).  ma: M digits with (A strides, C strides); nb: N digits with (B strides,

@@ -176,6 +176,7 @@ void setup_xpose(int rank, const int64_t *ext_in, const int64_t *sin_in,
         int d = in_order[k];
         int prev = U.back();
         if (used[d] || i2[d] != i2[prev] * e2[prev] || (uint64_t)pu * e2[d] >= (1ull << 31)) break;
+        if (same && o2[d] != o2[prev] * e2[prev]) break;
         U.push_back(d); used[d] = 1; pu *= e2[d];
     }
     if (!same) {
@@ -185,57 +186,87 @@ void setup_xpose(int rank, const int64_t *ext_in, const int64_t *sin_in,
             if (used[d] || o2[d] != o2[prev] * e2[prev] || (uint64_t)pv * e2[d] >= (1ull << 31)) break;
             V.push_back(d); used[d] = 1; pv *= e2[d];
         }
-    } else {
-        // copy mode: V is simply the next input dim (more rows per CTA)
-        for (int k = 0; k < n; ++k) {
-            int d = in_order[k];
-            if (!used[d]) { V.push_back(d); used[d] = 1; pv = e2[d]; break; }
-        }
     }
+    // copy mode (same stride-1 dim on both sides): V stays empty, R supplies the rows
     std::vector<int> R;
     for (int k = 0; k < n; ++k) if (!used[in_order[k]]) R.push_back(in_order[k]);
     fill_radix(&p->u, U, e2.data(), i2.data(), o2.data());
     fill_radix(&p->v, V, e2.data(), i2.data(), o2.data());
     fill_radix(&p->r, R, e2.data(), i2.data(), o2.data());
-    p->tiles_u = (uint32_t)((p->u.total + target - 1) / target);
-    p->tiles_v = (uint32_t)((std::max<uint32_t>(p->v.total, 1) + target - 1) / target);
-    if (V.empty()) { p->v.total = 1; }
-    if (R.empty()) { p->r.total = 1; }
+    if (V.empty()) p->v.total = 1;
+    if (R.empty()) p->r.total = 1;
+    // tile shape: about kXposeTile elements per CTA.  Transposing: 64 along U (reads) and up
+    // to 256 along V (writes), the rest from R when both leading runs are short.  Copy mode:
+    // up to 256 along U with rows from R; a single fused dim is cut into 4096-element pieces.
+    const uint32_t Eu = p->u.total, Ev = p->v.total, Er = p->r.total;
+    const uint32_t TAB = 256;
+    const uint32_t TILE = elem_bytes == 4 ? (uint32_t)kXposeTile : (uint32_t)kXposeTile / 2;  // 16 KB
+    const uint32_t W = 16 / elem_bytes;
+    // split a run of E into equal pieces of at most maxT, rounded up to a multiple of mult
+    auto balanced = [](uint32_t E, uint32_t maxT, uint32_t mult) {
+        uint32_t k = (E + maxT - 1) / maxT;
+        uint32_t t = (E + k - 1) / k;
+        if (mult > 1 && E % mult == 0 && t > mult) {
+            const uint32_t up = (t + mult - 1) / mult * mult;
+            t = up <= maxT ? up : t / mult * mult;   // never above maxT (the offset tables' size)
+        }
+        return std::max<uint32_t>(1, std::min(t, E));
+    };
+    uint32_t tu, tv, tw;
+    if (same && R.empty()) {
+        tu = Eu > TAB ? std::max<uint32_t>(TAB + 1, std::min<uint32_t>(Eu, TILE)) : Eu;
+        tv = 1;
+        tw = 1;
+    } else if (same) {
+        tu = balanced(Eu, TAB, W);
+        tv = 1;
+        tw = std::min<uint32_t>(Er, std::min<uint32_t>(TAB, std::max<uint32_t>(1, TILE / tu)));
+    } else {
+        tu = balanced(Eu, 128, W);
+        tv = balanced(Ev, std::min<uint32_t>(TAB, std::max<uint32_t>(16, TILE / tu)), W);
+        tw = std::min<uint32_t>(Er, std::min<uint32_t>(TAB, std::max<uint32_t>(1, TILE / (tu * tv))));
+    }
     // vector widths: 16-byte accesses when every stride other than the fast digit's is a
-    // multiple of the width and the fast digit's extent is too
+    // multiple of the width, the fast digit's extent is too, and the tile edge along the
+    // vector direction is a multiple of it
     int w = 16 / elem_bytes;
     auto ok_in = [&](int vw) {
-        if (p->u.s0[0] != 1 || p->u.ext[0] % vw) return false;
+        if (p->u.s0[0] != 1 || p->u.ext[0] % vw || tu % vw) return false;
         for (int d = 1; d < p->u.n; ++d) if (p->u.s0[d] % vw) return false;
         for (int d = 0; d < p->v.n; ++d) if (p->v.s0[d] % vw) return false;
         for (int d = 0; d < p->r.n; ++d) if (p->r.s0[d] % vw) return false;
         return true;
     };
-    auto ok_out = [&](int vw, bool copy) {
-        const Radix &f = copy ? p->u : p->v;
-        if (f.n == 0 || f.s1[0] != 1 || f.ext[0] % vw) return false;
+    auto ok_out = [&](int vw) {
+        const Radix &f = same ? p->u : p->v;
+        const uint32_t tf = same ? tu : tv;
+        if (f.n == 0 || f.s1[0] != 1 || f.ext[0] % vw || tf % vw) return false;
         for (int d = 1; d < f.n; ++d) if (f.s1[d] % vw) return false;
-        const Radix &g = copy ? p->v : p->u;
-        for (int d = 0; d < g.n; ++d) if (g.s1[d] % vw) return false;
+        if (!same) for (int d = 0; d < p->u.n; ++d) if (p->u.s1[d] % vw) return false;
         for (int d = 0; d < p->r.n; ++d) if (p->r.s1[d] % vw) return false;
         return true;
     };
     int vi = 1, vo = 1;
     for (int vw = w; vw > 1; vw /= 2) if (ok_in(vw)) { vi = vw; break; }
-    for (int vw = w; vw > 1; vw /= 2) if (ok_out(vw, same)) { vo = vw; break; }
+    for (int vw = w; vw > 1; vw /= 2) if (ok_out(vw)) { vo = vw; break; }
     if (same) { int m = std::min(vi, vo); vi = vo = m; }
     *vec_in = vi;
-    *vec_out = same ? -vo : vo;   // negative = copy mode (no smem transposition)
-    double run_in = (double)std::min<int64_t>(pu, target) * elem_bytes;
-    double run_out = (double)std::min<int64_t>(same ? pu : pv, target) * elem_bytes;
+    *vec_out = same ? -vo : vo;   // negative = copy mode (no shared-memory transposition)
+    p->tu = tu; p->tv = tv; p->tw = tw;
+    p->tiles_u = (Eu + tu - 1) / tu;
+    p->tiles_v = (Ev + tv - 1) / tv;
+    p->tiles_w = (Er + tw - 1) / tw;
+    p->fd_tu = make_fastdiv(tu);
+    p->fd_tv = make_fastdiv(tv);
+    p->fd_tuv = make_fastdiv(tu * tv);
+    {   // largest input and output offsets
+        int64_t mi = 0, mo = 0;
+        for (int d = 0; d < n; ++d) { mi += (e2[d] - 1) * i2[d]; mo += (e2[d] - 1) * o2[d]; }
+        p->off32 = (mi < (1ll << 31) - 64 && mo < (1ll << 31) - 64) ? 1 : 0;
+    }
+    double run_in = (double)std::min<int64_t>(pu, 64) * elem_bytes;
+    double run_out = (double)std::min<int64_t>(same ? pu : pv, 64) * elem_bytes;
     *eff = run_eff(run_in) * 0.5 + run_eff(run_out) * 0.5;
-    // CTAs: enough r per CTA to keep a few tiles in flight per SM without starving the grid
-    uint64_t tiles = (uint64_t)p->tiles_u * p->tiles_v;
-    uint64_t want_ctas = 152ull * 16;
-    uint64_t per = 1;
-    if (tiles * p->r.total > want_ctas) per = std::max<uint64_t>(1, (tiles * p->r.total) / want_ctas);
-    per = std::min<uint64_t>(per, 64);
-    p->r_per_cta = (uint32_t)per;
 }
 
 // ------------------------------------------------------------------------------------------

@@ -139,3 +139,71 @@ def torch_uniform(seed: int, tensor_id: int, count: int, device, dtype=None, sca
         u = lsr(z, 11).to(torch.float64) * 2.0 ** -53
         out[s:s + c] = (-1.0 + 2.0 * u) * scale
     return out if dtype is None else out.to(dtype)
+
+
+# --- the transpose sweep: rank-4 (all 24 permutations) and rank-6 (32 seeded permutations),
+# FP32 and FP64, 64 MiB to 2 GiB, extents in 8..256 -------------------------------------------
+
+class _Stream:
+    """Sequential draws from one SplitMix64 stream (for shape and permutation choices)."""
+
+    def __init__(self, seed, tensor_id):
+        self.key = stream_key(seed, tensor_id)
+        self.n = 0
+
+    def next(self) -> int:
+        self.n += 1
+        return mix64_int(self.key + self.n * GAMMA)
+
+    def uniform(self) -> float:
+        return (self.next() >> 11) * 2.0 ** -53
+
+    def below(self, k: int) -> int:
+        return self.next() % k
+
+
+def transpose_sweep_cases(max_bytes: int = 2 << 30, min_bytes: int = 64 << 20):
+    """[(name, rank, elem_bytes, perm, extents)].  Per (rank, dtype, perm): target bytes
+    log-uniform in [min_bytes, max_bytes], rank-1 extents log-uniform in [8, 256], the last
+    extent fixed by the target (redrawn while outside [8, 256]).  Seeds: 1000*rank + 10*dtype +
+    perm index.  Plus fixed shapes of exactly 64 MiB and 2 GiB per rank and dtype."""
+    import itertools
+    import math
+    cases = []
+    perms4 = list(itertools.permutations(range(4)))
+    ps = _Stream(6, 0)
+    perms6 = []
+    while len(perms6) < 32:
+        p = list(range(6))
+        for i in range(5, 0, -1):          # Fisher-Yates with the stream
+            j = ps.below(i + 1)
+            p[i], p[j] = p[j], p[i]
+        if tuple(p) not in perms6 and tuple(p) != tuple(range(6)):
+            perms6.append(tuple(p))
+    for rank, perms in ((4, perms4), (6, perms6)):
+        for dt, es in ((0, 4), (1, 8)):
+            for pi, perm in enumerate(perms):
+                st = _Stream(1000 * rank + 10 * dt + pi, 1)
+                for _ in range(1000):
+                    target = math.exp(math.log(min_bytes) + st.uniform() * (math.log(max_bytes) - math.log(min_bytes)))
+                    ext = [int(round(math.exp(math.log(8) + st.uniform() * (math.log(256) - math.log(8)))))
+                           for _ in range(rank - 1)]
+                    last = int(round(target / (es * math.prod(ext))))
+                    if 8 <= last <= 256:
+                        ext.append(last)
+                        break
+                else:
+                    raise RuntimeError("no shape found")
+                cases.append((f"r{rank}_{'f32' if es == 4 else 'f64'}_p{pi}", rank, es, tuple(perm), tuple(ext)))
+    fixed = {4: {64 << 20: [(64, 128, 128, 16), (32, 128, 128, 16)],
+                 2 << 30: [(128, 256, 128, 128), (64, 256, 128, 128)]},
+             6: {64 << 20: [(16, 16, 16, 16, 16, 16), (16, 16, 16, 16, 16, 8)],
+                 2 << 30: [(32, 32, 32, 32, 32, 16), (32, 32, 32, 32, 32, 8)]}}
+    for rank in (4, 6):
+        for size, shapes in fixed[rank].items():
+            if size > max_bytes:
+                continue
+            for es, shape in zip((4, 8), shapes):
+                perm = tuple(reversed(range(rank))) if rank == 4 else (1, 3, 5, 0, 2, 4)
+                cases.append((f"r{rank}_{'f32' if es == 4 else 'f64'}_{size >> 20}MiB", rank, es, perm, shape))
+    return cases

@@ -17,72 +17,102 @@ using namespace comet;
 static int fails = 0;
 #define CHECK(c, ...) do { if (!(c)) { if (fails++ < 20) { std::printf(__VA_ARGS__); std::printf("\n"); } } } while (0)
 
-// replay of the kernels: returns the output->input map (or empty on failure)
+// replay of xpose_tile_kernel / xpose_copy_kernel: fills the output->input map
 static bool replay(const XposeParams &p, int vi, int vo, int64_t n_in, int64_t n_out_span,
                    std::vector<int64_t> &src_of_out) {
-    const int TT = 64, XT = 256;
-    bool copy = vo < 0;
-    int vw_out = copy ? -vo : vo;
-    uint64_t tiles = (uint64_t)p.tiles_u * p.tiles_v;
-    uint64_t rch = (p.r.total + p.r_per_cta - 1) / p.r_per_cta;
-    uint64_t grid = tiles * rch;
-    for (uint64_t b = 0; b < grid; ++b) {
-        uint32_t bt = b % tiles, rc = b / tiles;
-        uint32_t u0 = (bt % p.tiles_u) * TT, v0 = (bt / p.tiles_u) * TT;
-        int64_t u_in[64], u_out[64], v_in[64], v_out[64];
-        for (int t = 0; t < TT; ++t) {
-            int64_t a = 0, c = 0;
-            if (u0 + t < p.u.total) radix_offsets(p.u, u0 + t, a, c);
-            u_in[t] = a; u_out[t] = c;
-            a = c = 0;
-            if (v0 + t < p.v.total) radix_offsets(p.v, v0 + t, a, c);
-            v_in[t] = a; v_out[t] = c;
+    const int XT = 256, XTAB = 256;
+    const bool copy = vo < 0;
+    CHECK(p.tu >= 1 && p.tv >= 1 && p.tw >= 1, "empty tile");
+    CHECK((uint64_t)p.tu * p.tv * p.tw <= 8192 + 3 * 256 || (copy && p.tv == 1 && p.tw == 1), "tile too large");
+    CHECK((uint64_t)p.tw * p.tv * (p.tu | 1u) * 8 <= 96 * 1024, "tile exceeds the shared memory it is given");
+    CHECK(p.tv <= (uint32_t)XTAB && p.tw <= (uint32_t)XTAB, "tile edge above the table size");
+    CHECK(copy || p.tu <= (uint32_t)XTAB, "transposing tile edge above the table size");
+    const uint64_t grid = (uint64_t)p.tiles_u * p.tiles_v * p.tiles_w;
+    const uint32_t tu = p.tu, tv = p.tv, tw = p.tw, pitch = tu | 1u;
+    for (uint64_t blk = 0; blk < grid && fails == 0; ++blk) {
+        if (copy) {
+            const bool affine = tu > (uint32_t)XTAB;
+            const uint32_t bu = blk % p.tiles_u, bw = blk / p.tiles_u;
+            const uint32_t u0 = bu * tu, w0 = bw * tw;
+            const uint32_t nu = std::min(tu, p.u.total - u0), nw = std::min(tw, p.r.total - w0);
+            CHECK(!affine || p.u.n == 1, "affine copy of a multi-digit group");
+            const int VW = -vo;
+            for (uint32_t t = 0; t < (uint32_t)XT; ++t)
+                for (uint32_t idx = t * VW; idx < tu * tw; idx += XT * VW) {
+                    uint32_t w = fd_div(idx, p.fd_tu), u = idx - w * tu;
+                    if (!(u < nu && w < nw)) continue;
+                    int64_t a, c, wi, wo;
+                    radix_offsets(p.u, u0 + u, a, c);
+                    if (affine) { CHECK(a == (int64_t)(u0 + u) * p.u.s0[0] && c == (int64_t)(u0 + u) * p.u.s1[0], "affine offsets"); }
+                    radix_offsets(p.r, w0 + w, wi, wo);
+                    CHECK((wi + a) % VW == 0 && (wo + c) % VW == 0, "misaligned copy vector");
+                    for (int q = 0; q < VW; ++q) {
+                        CHECK(u + q < nu, "vector crosses the tile");
+                        int64_t a2, c2;
+                        radix_offsets(p.u, u0 + u + q, a2, c2);
+                        CHECK(a2 == a + q && c2 == c + q, "copy vector not contiguous");
+                        int64_t si = wi + a + q, d = wo + c + q;
+                        CHECK(si >= 0 && si < n_in && d >= 0 && d < n_out_span, "copy out of bounds");
+                        if (d >= 0 && d < n_out_span) { CHECK(src_of_out[d] == -1, "written twice"); src_of_out[d] = si; }
+                    }
+                }
+            continue;
         }
-        uint32_t r_begin = rc * p.r_per_cta, r_end = std::min(p.r.total, r_begin + p.r_per_cta);
-        for (uint32_t r = r_begin; r < r_end; ++r) {
-            int64_t r_in, r_out;
-            radix_offsets(p.r, r, r_in, r_out);
-            int64_t tile[64][64];
-            for (int i = 0; i < 64; ++i) for (int j = 0; j < 64; ++j) tile[i][j] = -1;
-            int VI = copy ? vw_out : vi;
-            for (int idx = 0; idx < TT * TT / VI; ++idx) {
-                int vr = idx / (TT / VI), uc = (idx % (TT / VI)) * VI;
-                if (!(v0 + vr < p.v.total && u0 + uc < p.u.total)) continue;
-                int64_t src = r_in + v_in[vr] + u_in[uc];
-                CHECK(src % VI == 0, "misaligned vector load %lld (w %d)", (long long)src, VI);
-                for (int q = 0; q < VI; ++q) {
-                    CHECK(u0 + uc + q < p.u.total, "vector load crosses the U extent");
-                    int64_t s = src + q;
-                    CHECK(s >= 0 && s < n_in, "load out of bounds %lld / %lld", (long long)s, (long long)n_in);
-                    CHECK(u_in[uc + q] == u_in[uc] + q, "vector load not contiguous");
-                    if (copy) {
-                        int64_t d = r_out + v_out[vr] + u_out[uc] + q;
-                        CHECK(u_out[uc + q] == u_out[uc] + q, "vector store not contiguous");
-                        CHECK(d >= 0 && d < n_out_span, "store out of bounds");
-                        if (d >= 0 && d < n_out_span) {
-                            CHECK(src_of_out[d] == -1, "output written twice");
-                            src_of_out[d] = s;
-                        }
-                    } else {
-                        tile[vr][uc + q] = s;
+        uint32_t b = blk;
+        const uint32_t bu = b % p.tiles_u;
+        b /= p.tiles_u;
+        const uint32_t bv = b % p.tiles_v, bw = b / p.tiles_v;
+        const uint32_t u0 = bu * tu, v0 = bv * tv, w0 = bw * tw;
+        const uint32_t nu = std::min(tu, p.u.total - u0), nv = std::min(tv, p.v.total - v0),
+                       nw = std::min(tw, p.r.total - w0);
+        std::vector<int64_t> ui(tu), uo(tu), vin(tv), vout(tv), wi(tw), wo(tw);
+        for (uint32_t i = 0; i < tu; ++i) { ui[i] = uo[i] = 0; if (i < nu) radix_offsets(p.u, u0 + i, ui[i], uo[i]); }
+        for (uint32_t i = 0; i < tv; ++i) { vin[i] = vout[i] = 0; if (i < nv) radix_offsets(p.v, v0 + i, vin[i], vout[i]); }
+        for (uint32_t i = 0; i < tw; ++i) { wi[i] = wo[i] = 0; if (i < nw) radix_offsets(p.r, w0 + i, wi[i], wo[i]); }
+        std::vector<int64_t> buf((size_t)tw * tv * pitch, -1);
+        CHECK(p.off32 == 0 || (n_in < (1ll << 31) && n_out_span < (1ll << 31)), "32-bit offsets on a large tensor");
+        {   // loads: fixed u per thread, rows (v, w) walked
+            const uint32_t lanes = (tu + vi - 1) / vi, rpp = XT / lanes;
+            CHECK(rpp >= 1, "no rows per pass (load)");
+            for (uint32_t t = 0; t < (uint32_t)XT; ++t) {
+                const uint32_t r0 = t / lanes, u = (t - r0 * lanes) * vi;
+                if (!(r0 < rpp && u < nu)) continue;
+                for (uint32_t row = r0; row < tv * tw; row += rpp) {
+                    const uint32_t w = fd_div(row, p.fd_tv), v = row - w * tv;
+                    if (!(v < nv && w < nw)) continue;
+                    int64_t src = wi[w] + vin[v] + ui[u];
+                    CHECK(src % vi == 0, "misaligned vector load");
+                    for (int q = 0; q < vi; ++q) {
+                        CHECK(u + q < nu, "vector load crosses the tile");
+                        CHECK(ui[u + q] == ui[u] + q, "vector load not contiguous");
+                        CHECK(src + q >= 0 && src + q < n_in, "load out of bounds");
+                        CHECK(row * pitch + u + q < buf.size(), "shared store out of the tile");
+                        buf[row * pitch + u + q] = src + q;
                     }
                 }
             }
-            if (copy) continue;
-            for (int idx = 0; idx < TT * TT / vo; ++idx) {
-                int ur = idx / (TT / vo), vc = (idx % (TT / vo)) * vo;
-                if (!(u0 + ur < p.u.total && v0 + vc < p.v.total)) continue;
-                int64_t dst = r_out + u_out[ur] + v_out[vc];
-                CHECK(dst % vo == 0, "misaligned vector store");
-                for (int q = 0; q < vo; ++q) {
-                    CHECK(v0 + vc + q < p.v.total, "vector store crosses the V extent");
-                    CHECK(v_out[vc + q] == v_out[vc] + q, "vector store not contiguous");
-                    int64_t d = dst + q;
-                    CHECK(d >= 0 && d < n_out_span, "store out of bounds");
-                    CHECK(tile[vc + q][ur] >= 0, "store of a tile element that was not loaded");
-                    if (d >= 0 && d < n_out_span) {
-                        CHECK(src_of_out[d] == -1, "output written twice");
-                        src_of_out[d] = tile[vc + q][ur];
+        }
+        {   // stores: fixed v per thread, rows (u, w) walked
+            const uint32_t lanes = (tv + vo - 1) / vo, rpp = XT / lanes;
+            CHECK(rpp >= 1, "no rows per pass (store)");
+            for (uint32_t t = 0; t < (uint32_t)XT; ++t) {
+                const uint32_t r0 = t / lanes, v = (t - r0 * lanes) * vo;
+                if (!(r0 < rpp && v < nv)) continue;
+                for (uint32_t row = r0; row < tu * tw; row += rpp) {
+                    const uint32_t w = fd_div(row, p.fd_tu), u = row - w * tu;
+                    if (!(u < nu && w < nw)) continue;
+                    int64_t dst = wo[w] + uo[u] + vout[v];
+                    CHECK(dst % vo == 0, "misaligned vector store");
+                    for (int q = 0; q < vo; ++q) {
+                        CHECK(v + q < nv, "vector store crosses the tile");
+                        CHECK(vout[v + q] == vout[v] + q, "vector store not contiguous");
+                        size_t bi = (size_t)(w * tv + v + q) * pitch + u;
+                        CHECK(bi < buf.size(), "shared load out of the tile");
+                        int64_t s2 = buf[bi];
+                        CHECK(s2 >= 0, "store of an element that was not loaded");
+                        int64_t d = dst + q;
+                        CHECK(d >= 0 && d < n_out_span, "store out of bounds");
+                        if (d >= 0 && d < n_out_span) { CHECK(src_of_out[d] == -1, "written twice"); src_of_out[d] = s2; }
                     }
                 }
             }
@@ -128,6 +158,37 @@ int main() {
                       (long long)j, (long long)map[j], (long long)off);
             }
             ++cases;
+        }
+    }
+    // fixed cases: long single fused runs (affine copy path), identity and near-identity
+    // permutations, tiny leading extents on one or both sides
+    {
+        struct Fx { int rank; int64_t ext[6]; int perm[6]; };
+        const Fx fx[] = {{1, {5000}, {0}}, {2, {300, 500}, {0, 1}}, {3, {54, 97, 7}, {0, 1, 2}},
+                         {3, {9, 13, 100}, {1, 2, 0}}, {4, {9, 13, 10, 8}, {1, 0, 3, 2}},
+                         {3, {2000, 9, 5}, {1, 0, 2}}, {2, {4096, 3}, {0, 1}}, {3, {300, 2, 5}, {0, 2, 1}},
+                         {6, {8, 11, 5, 6, 13, 8}, {1, 2, 4, 5, 3, 0}}};
+        for (const Fx &f : fx) {
+            int64_t si[8], so[8], so_out[8], n = 1, s = 1;
+            for (int d = 0; d < f.rank; ++d) { si[d] = s; s *= f.ext[d]; }
+            n = s;
+            s = 1;
+            for (int d = 0; d < f.rank; ++d) { so_out[d] = s; s *= f.ext[f.perm[d]]; }
+            for (int d = 0; d < f.rank; ++d) so[f.perm[d]] = so_out[d];
+            for (int es : {4, 8}) {
+                XposeParams p;
+                int vi, vo;
+                double eff;
+                setup_xpose(f.rank, f.ext, si, so, es, &p, &vi, &vo, &eff);
+                std::vector<int64_t> map(n, -1);
+                replay(p, vi, vo, n, n, map);
+                for (int64_t j = 0; j < n && fails == 0; ++j) {
+                    int64_t rem = j, off = 0;
+                    for (int d = 0; d < f.rank; ++d) { off += (rem % f.ext[f.perm[d]]) * si[f.perm[d]]; rem /= f.ext[f.perm[d]]; }
+                    CHECK(map[j] == off, "fixed case rank %d: out %lld", f.rank, (long long)j);
+                }
+                ++cases;
+            }
         }
     }
     // split pre-pass layout: [rows][kpad] with kpad padding (outputs only partly covered)

@@ -93,3 +93,29 @@ def test_rejects_bad_arguments(comet):
     with pytest.raises(comet.CometError) as e:
         comet.transpose(x[1:], [3, 5], [1, 0], out=torch.zeros(15, device="cuda"))
     assert e.value.name == "COMET_ERR_ALIGN"
+
+
+# ---- the transpose sweep at its full sizes: sampled outputs against the oracle ---------------
+
+SWEEP_PICK = ["r4_f32_p0", "r4_f64_p23", "r6_f32_p5", "r6_f64_p31", "r4_f32_2048MiB", "r6_f64_2048MiB",
+              "r6_f32_64MiB"]
+
+
+@pytest.mark.parametrize("name", SWEEP_PICK)
+def test_sweep_case_full_size_sampled(comet, name):
+    import math
+
+    import torch
+    case = {c[0]: c for c in synth.transpose_sweep_cases()}[name]
+    _, rank, es, perm, ext = case
+    n = math.prod(ext)
+    dt = torch.float32 if es == 4 else torch.float64
+    x = synth.torch_uniform(3, 0, n, "cuda", dtype=dt)
+    y = comet.transpose(x, ext, perm)
+    comet.sync_status()
+    sel = np.unique(synth.integers(12, rank, 20000, 0, n - 1).astype(np.int64))
+    got = y.view(-1)[torch.from_numpy(sel).cuda()].cpu().numpy()
+    host = np.asfortranarray(x.cpu().numpy().reshape(tuple(reversed(ext))).T)
+    ref = oracle.transpose_sampled(host, perm, sel)
+    assert got.tobytes() == ref.tobytes()
+    del x, y
