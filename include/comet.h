@@ -212,13 +212,15 @@ comet_status_t comet_transpose(int rank, const int64_t *extents, const int *perm
                                comet_dtype_t dtype, const void *in, void *out, void *stream);
 
 /*
- * Batched triples-like blocks (one persistent launch for many small, uneven contractions of
- * the same expression; the 6-D triples output of Section 2's CCSD(T) remark).
+ * Batched triples-like blocks: many small contractions of the same expression with uneven
+ * extents, all run by one persistent launch (the 6-D triples output of the CCSD(T) remark in
+ * Section 2 is the model: T[a,b,c,i,j,k] = sum_d A[d,a,b,i] * B[c,d,j,k] per block).
  *
- * comet_plan_batched — expr must be a two-operand contraction.  label_names lists the
+ * comet_plan_batched — expr must be a two-operand "=" contraction.  label_names lists the
  *   n_labels labels; extents is an n_blocks x n_labels row-major table (block b, label l at
- *   extents[b*n_labels + l]).  dtypes as in comet_plan.  tile_hint: -1 = autotuned choice
- *   (from the in-process cache, else the default), k >= 0 = k-th tile configuration.
+ *   extents[b*n_labels + l]).  dtypes as in comet_plan.  tile_hint: -1 = the tile
+ *   configuration the autotuner recorded for this problem class in this process (else the
+ *   default), k >= 0 = the k-th configuration.  No device work.
  */
 comet_status_t comet_plan_batched(const char *expr, int n_blocks, const char *const *label_names,
                                   int n_labels, const int64_t *extents,
@@ -226,12 +228,26 @@ comet_status_t comet_plan_batched(const char *expr, int n_blocks, const char *co
                                   const comet_plan_opts_t *opts, int tile_hint,
                                   comet_plan_t *out_plan);
 
-/* Number of tile configurations comet_plan_batched() accepts as tile_hint. */
-int comet_batched_num_tiles(void);
+/* Number of tile configurations comet_plan_batched() accepts as tile_hint (for the precision
+ * of `plan`; NULL = the FP64 path). */
+int comet_batched_num_tiles(comet_plan_t plan);
+
+/* Selects tile configuration cfg for a batched plan. */
+comet_status_t comet_batched_set_tile(comet_plan_t plan, int cfg);
 
 /*
- * comet_contract_batched — run every block in one persistent launch.
- *   block_inputs   device array of n_blocks * n_in device pointers (block-major).
+ * comet_batched_prepare — copies the plan's per-block descriptors (label groups, strides,
+ * divisors, the longest-first block order and the tile prefix sums) into `workspace`
+ * (comet_plan_workspace() bytes) and synchronises the stream.  Call once per workspace,
+ * before any stream capture; comet_contract_batched() then only reads it.
+ */
+comet_status_t comet_batched_prepare(comet_plan_t plan, void *workspace, void *stream);
+
+/*
+ * comet_contract_batched — run every block in one persistent launch (capturable in a CUDA
+ * graph once comet_batched_prepare() has run on `workspace`).
+ *   block_inputs   device array of n_blocks * 2 device pointers (block-major: A_b, B_b),
+ *                  each a dense column-major operand of that block's extents.
  *   mode 0 (reduce): `result` is a device array of 2*n_blocks doubles; block b gets
  *                  s_b = sum T*W and q_b = sum T^2 over its output T, with the weight W of the
  *                  element with column-major linear index n given by
@@ -239,11 +255,23 @@ int comet_batched_num_tiles(void);
  *                  finalizer), W = (h >> 8) * 2^-23 - 1.  T is never stored.
  *   mode 1 (store):  `result` is a device array of n_blocks device pointers; block b's output
  *                  is written there in full (blocks whose pointer is NULL are skipped).
- *   workspace      comet_plan_workspace() bytes.
+ *   The launch resets its own work counter and, in mode 0, zeroes `result` first.
  */
 comet_status_t comet_contract_batched(comet_plan_t plan, const void *const *block_inputs,
                                       int mode, void *result, uint32_t weight_key,
                                       void *workspace, void *stream);
+
+/*
+ * comet_batched_autotune — times every tile configuration on the first sample_blocks blocks
+ * of the longest-first order (0 = all) in reduce mode, writes each configuration's time to
+ * ms_per_cfg (n_cfg entries, may be NULL), selects the fastest for `plan`, and records it for
+ * later comet_plan_batched(tile_hint = -1) calls of the same problem class in this process
+ * (and in the file named by the environment variable COMET_AUTOTUNE_CACHE, if set).
+ * Needs a prepared workspace; synchronises the stream; not capturable.
+ */
+comet_status_t comet_batched_autotune(comet_plan_t plan, const void *const *block_inputs, void *result,
+                                      void *workspace, int sample_blocks, void *stream,
+                                      double *ms_per_cfg, int n_cfg, int *best);
 
 /*
  * Kernel timing (tracing).  While enabled, every kernel launch the library makes is bracketed

@@ -169,6 +169,87 @@ class Plan:
             pass
 
 
+class BatchedPlan:
+    """comet_plan_batched(): many blocks of one two-operand expression, uneven extents.
+
+    label_names  the labels, in the column order of ``extents``
+    extents      integer array n_blocks x n_labels
+    """
+
+    def __init__(self, expr: str, label_names, extents, dtype, precision="native", tile: int = -1):
+        import numpy as np
+        L = lib()
+        self.expr = expr
+        ext = np.ascontiguousarray(np.asarray(extents, dtype=np.int64))
+        self.n_blocks, n_labels = ext.shape
+        self.dtype_code = _dtype_code(dtype)
+        self.dtype = _torch_dtype(self.dtype_code)
+        names = (ctypes.c_char_p * n_labels)(*[str(l).encode() for l in label_names])
+        dts = (ctypes.c_int * 3)(*([self.dtype_code] * 3))
+        opts = _lib.PlanOpts()
+        L.comet_plan_opts_default(ctypes.byref(opts))
+        opts.precision = _prec_code(precision)
+        h = ctypes.c_void_p()
+        _lib.check(L.comet_plan_batched(expr.encode(), self.n_blocks, names, n_labels,
+                                        ext.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), dts, 3,
+                                        ctypes.byref(opts), tile, ctypes.byref(h)), "comet_plan_batched")
+        self._h = h
+        ws = ctypes.c_size_t()
+        _lib.check(L.comet_plan_workspace(h, ctypes.byref(ws)), "comet_plan_workspace")
+        self.workspace_bytes = ws.value
+        f = ctypes.c_double()
+        _lib.check(L.comet_plan_flops(h, ctypes.byref(f)), "comet_plan_flops")
+        self.flops = f.value
+
+    def describe(self) -> dict:
+        buf = ctypes.create_string_buffer(1 << 14)
+        _lib.check(lib().comet_plan_describe(self._h, buf, len(buf)), "comet_plan_describe")
+        return json.loads(buf.value.decode())
+
+    def num_tiles(self) -> int:
+        return lib().comet_batched_num_tiles(self._h)
+
+    def set_tile(self, cfg: int):
+        _lib.check(lib().comet_batched_set_tile(self._h, cfg), "comet_batched_set_tile")
+
+    def workspace(self, device="cuda"):
+        import torch
+        return torch.empty(self.workspace_bytes, dtype=torch.uint8, device=device)
+
+    def prepare(self, workspace, stream=None):
+        """comet_batched_prepare(): upload the block descriptors (once, before capture)."""
+        _lib.check(lib().comet_batched_prepare(self._h, _ptr(workspace), _stream_handle(stream)),
+                   "comet_batched_prepare")
+
+    def contract(self, block_inputs, result, workspace, mode: int = 0, key: int = 1, stream=None):
+        """comet_contract_batched(): block_inputs is a device int64 tensor of 2*n_blocks
+        pointers; result holds 2*n_blocks doubles (mode 0) or n_blocks output pointers (mode 1)."""
+        _lib.check(lib().comet_contract_batched(self._h, _ptr(block_inputs), mode, _ptr(result), key,
+                                                _ptr(workspace), _stream_handle(stream)),
+                   "comet_contract_batched")
+
+    def autotune(self, block_inputs, result, workspace, sample_blocks: int = 0, stream=None):
+        """comet_batched_autotune(): (ms per configuration, chosen configuration)."""
+        n = self.num_tiles()
+        ms = (ctypes.c_double * n)()
+        best = ctypes.c_int()
+        _lib.check(lib().comet_batched_autotune(self._h, _ptr(block_inputs), _ptr(result), _ptr(workspace),
+                                                sample_blocks, _stream_handle(stream), ms, n,
+                                                ctypes.byref(best)), "comet_batched_autotune")
+        return [ms[i] for i in range(n)], best.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().comet_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def transpose(x, extents, perm, out=None, stream=None):
     """comet_transpose(): bit-exact permutation of a column-major tensor.
 

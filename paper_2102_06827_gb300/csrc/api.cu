@@ -83,7 +83,24 @@ struct ProfScope {
     }
 };
 
-int profile_kind_batched(bool split) { return split ? PK_BATCHED_SPLIT : PK_BATCHED_F64; }
+// hooks for kernels launched from other files (the batched launch sequence)
+int prof_begin(int kind, cudaStream_t s) {
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    if (!g_prof_on || kind < 0 || kind >= PK_N) return -1;
+    ProfRec r{kind, prof_event(), prof_event()};
+    if (!r.a || !r.b) return -1;
+    cudaEventRecord(r.a, s);
+    g_prof_recs.push_back(r);
+    return (int)g_prof_recs.size() - 1;
+}
+
+void prof_end(int idx, cudaStream_t s) {
+    if (idx < 0) return;
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    if (idx < (int)g_prof_recs.size()) cudaEventRecord(g_prof_recs[idx].b, s);
+}
+
+void set_error_message(const std::string &s) { set_error(s); }
 
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 

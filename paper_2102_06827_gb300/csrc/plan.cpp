@@ -731,6 +731,25 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
     return COMET_OK;
 }
 
+void gemm_params_for(const std::vector<int64_t> &extent, const std::vector<int> &lm,
+                     const std::vector<int> &ln, const std::vector<int> &lc, const Form &f,
+                     GemmParams *g) {
+    auto tm = label_strides(lm, extent), tn = label_strides(ln, extent), tc = label_strides(lc, extent);
+    std::memset(g, 0, sizeof(*g));
+    const int L = (int)extent.size();
+    std::vector<int64_t> s0(L), s1(L);
+    for (int l : f.M) { s0[l] = tm[l]; s1[l] = tc[l]; }
+    fill_radix(&g->ma, f.M, extent.data(), s0.data(), s1.data());
+    for (int l : f.N) { s0[l] = tn[l]; s1[l] = tc[l]; }
+    fill_radix(&g->nb, f.N, extent.data(), s0.data(), s1.data());
+    for (int l : f.K) { s0[l] = tm[l]; s1[l] = tn[l]; }
+    fill_radix(&g->k, f.K, extent.data(), s0.data(), s1.data());
+    g->M = (uint32_t)prod_ext(extent, f.M);
+    g->N = (uint32_t)prod_ext(extent, f.N);
+    g->K = (uint32_t)prod_ext(extent, f.K);
+    g->ma.total = g->M; g->nb.total = g->N; g->k.total = g->K;
+}
+
 std::string describe_plan(const Plan &P) {
     std::ostringstream o;
     auto names = [&](const std::vector<int> &v) {

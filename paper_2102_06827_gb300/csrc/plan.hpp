@@ -90,7 +90,10 @@ struct Plan {
     std::vector<int64_t> block_extents;   // n_blocks x n_labels
     int tile_cfg = 0;
     size_t batched_ws = 0;
-    std::vector<uint8_t> batched_table;   // host image of the per-block descriptors
+    std::vector<uint8_t> batched_table;   // host image of the prefix sums and the descriptors
+    std::vector<std::vector<uint32_t>> batched_prefix;   // per tile configuration
+    std::vector<double> block_flops;
+    bool batched_ak = false, batched_bk = false, batched_swap = false;
 };
 
 size_t dtype_size(comet_dtype_t t);
@@ -100,6 +103,12 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
                           const comet_plan_opts_t *opts, Plan *plan, std::string *err);
 
 std::string describe_plan(const Plan &p);
+
+// GEMM parameters of one binary step for given extents: lm / ln = labels of the M and N
+// operands, lc = labels of the output (all column-major), f = the TTGT form.
+void gemm_params_for(const std::vector<int64_t> &extent, const std::vector<int> &lm,
+                     const std::vector<int> &ln, const std::vector<int> &lc, const Form &f,
+                     GemmParams *g);
 
 // Transpose engine set-up for a permutation of a dense column-major tensor with arbitrary
 // output strides.  in_strides/out_strides in elements; returns the vector widths usable for

@@ -15,6 +15,8 @@ the element with column-major linear index ``n``.
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 GAMMA = 0x9E3779B97F4A7C15
@@ -207,3 +209,47 @@ def transpose_sweep_cases(max_bytes: int = 2 << 30, min_bytes: int = 64 << 20):
                 perm = tuple(reversed(range(rank))) if rank == 4 else (1, 3, 5, 0, 2, 4)
                 cases.append((f"r{rank}_{'f32' if es == 4 else 'f64'}_{size >> 20}MiB", rank, es, perm, shape))
     return cases
+
+
+def torch_normal(seed: int, tensor_id: int, count: int, device, dtype=None, std: float = 1.0):
+    """normal(0, std) on ``device`` by the Box-Muller transform of ``normal`` (same counters and
+    formula; values agree with the host version to within a few units in the last place of the
+    device's log/sqrt/cos)."""
+    import torch
+    key = stream_key(seed, tensor_id)
+    key_s = key - (1 << 64) if key >= (1 << 63) else key
+    g = GAMMA - (1 << 64)
+    m1 = _M1 - (1 << 64)
+    m2 = _M2 - (1 << 64)
+
+    def lsr(z, s):
+        return (z >> s) & ((1 << (64 - s)) - 1)
+
+    def mix(n):
+        z = n * g + key_s
+        z = (z ^ lsr(z, 30)) * m1
+        z = (z ^ lsr(z, 27)) * m2
+        return z ^ lsr(z, 31)
+
+    out = torch.empty(count, dtype=torch.float64, device=device)
+    step = 1 << 23
+    for s in range(0, count, step):
+        c = min(count, s + step) - s
+        n = torch.arange(2 * s + 1, 2 * (s + c) + 1, dtype=torch.int64, device=device)
+        u = (lsr(mix(n), 11).to(torch.float64) + 0.5) * 2.0 ** -53
+        u1, u2 = u[0::2], u[1::2]
+        out[s:s + c] = std * torch.sqrt(-2.0 * torch.log(u1)) * torch.cos(2.0 * math.pi * u2)
+    return out if dtype is None else out.to(dtype)
+
+
+def triples_blocks(n_blocks: int = 4096, lo: int = 8, hi: int = 32, seed: int = 3):
+    """Extents of the batched triples workload: an n_blocks x 7 table over the labels
+    (a, b, c, i, j, k, d), each uniform in [lo, hi], drawn from the seed."""
+    return integers(seed, 0, n_blocks * 7, lo, hi).astype(np.int64).reshape(n_blocks, 7)
+
+
+def normal_range(seed: int, tensor_id: int, start: int, count: int, std: float = 1.0) -> np.ndarray:
+    """Elements start .. start+count-1 of the ``normal`` stream."""
+    bits = raw_bits(seed, tensor_id, 2 * start, 2 * count)
+    u = ((bits >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53
+    return std * np.sqrt(-2.0 * np.log(u[0::2])) * np.cos(2.0 * np.pi * u[1::2])

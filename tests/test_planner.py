@@ -196,3 +196,29 @@ def test_transpose_argument_checks():
     with pytest.raises(comet.CometError) as e:
         comet.transpose(x, [2, 4], [0, 0], out=torch.empty(8), stream=0)
     assert e.value.name == "COMET_ERR_ARG"
+
+
+def test_batched_plan_structure():
+    import numpy as np
+    import synth
+    ext = synth.triples_blocks(64)
+    names = ["a", "b", "c", "i", "j", "k", "d"]
+    e = "T[a,b,c,i,j,k] = A[d,a,b,i] * B[c,d,j,k]"
+    for prec in ("native", "split_bf16"):
+        p = comet.BatchedPlan(e, names, ext, "f64", precision=prec)
+        info = p.describe()
+        assert info["batched"] and info["n_blocks"] == 64
+        flops = sum(2.0 * np.prod(r) for r in ext)
+        assert p.flops == pytest.approx(flops)
+        assert p.num_tiles() == (3 if prec == "split_bf16" else 4)
+        for c in range(p.num_tiles()):
+            p.set_tile(c)
+            assert p.describe()["tile_cfg"] == c
+        with pytest.raises(comet.CometError):
+            p.set_tile(p.num_tiles())
+    with pytest.raises(comet.CometError) as err:
+        comet.BatchedPlan("D[a,b] = A[a,i] * B[i,j] * C[j,b]", ["a", "b", "i", "j"], [[2, 2, 2, 2]], "f64")
+    assert err.value.name in ("COMET_ERR_UNSUPPORTED", "COMET_ERR_DTYPE")
+    with pytest.raises(comet.CometError) as err:
+        comet.BatchedPlan(e, names, np.zeros((2, 7), dtype=np.int64), "f64")
+    assert err.value.name == "COMET_ERR_SHAPE"
