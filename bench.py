@@ -54,6 +54,8 @@ def args_parse():
     ap.add_argument("--pc-extents", default="64,128,128,256", help="transpose profile case extents")
     ap.add_argument("--pc-perm", default="3,1,0,2", help="transpose profile case permutation")
     ap.add_argument("--pc-dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--workload", default="ccsd", choices=["ccsd", "triples"],
+                    help="ccsd: the headline line; triples: the batched workload (separate JSON line)")
     ap.add_argument("--sweep", default=None, choices=["transpose"],
                     help="time the transpose sweep (rank-4/rank-6, FP32/FP64, 64 MiB - 2 GiB) and exit")
     return ap.parse_args()
@@ -109,6 +111,59 @@ def run_transpose_sweep() -> int:
                       "frac_min": fr[0], "frac_median": fr[len(fr) // 2], "frac_max": fr[-1],
                       "cases_at_or_above_0.70": sum(f >= 0.70 for f in fr),
                       "all_bit_exact": all(r["bit_exact_inverse"] for r in res), "results": res}))
+    return 0
+
+
+def run_triples(a) -> int:
+    """The batched triples workload: 4096 blocks T[a,b,c,i,j,k] = sum_d A[d,a,b,i] * B[c,d,j,k],
+    every extent uniform in 8..32 (seed 3), inputs normal(0, 0.1); one persistent launch per
+    step inside a captured CUDA graph, reduce epilogue (s_b, q_b), tiles chosen by the
+    autotuner.  Prints one JSON line (not the headline line)."""
+    import numpy as np
+    import torch
+    import paper_2102_06827_gb300 as comet
+    import synth
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from batched_data import EXPR as TEXPR, LABELS, Blocks
+    ext = synth.triples_blocks(4096)
+    peaks = measured_peaks() or {}
+    out = {"workload": "batched triples: 4096 blocks, extents uniform 8..32 (seed 3), normal(0,0.1)",
+           "flops": float(np.sum(2.0 * np.prod(ext, axis=1)))}
+    for prec, dtype, dt, steps in (("split_bf16", np.float32, "f32", a.steps), ("native", np.float64, "f64", 1)):
+        blocks = Blocks(ext, dtype)
+        plan = comet.BatchedPlan(TEXPR, LABELS, ext, dt, precision=prec)
+        ws = plan.workspace()
+        plan.prepare(ws)
+        res = torch.zeros(2 * blocks.n, dtype=torch.float64, device="cuda")
+        ms, best = plan.autotune(blocks.ptrs, res, ws, sample_blocks=0 if prec == "split_bf16" else 96)
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            plan.contract(blocks.ptrs, res, ws, mode=0, key=1, stream=s)
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        comet.sync_status()
+        t = e0.elapsed_time(e1) / steps
+        gf = plan.flops / (t * 1e-3) / 1e9
+        entry = {"ms_per_step": t, "gflops": gf, "steps": steps, "tile_times_ms": ms, "tile_cfg": best,
+                 "tile": plan.describe()["tile"], "graph": True}
+        if prec == "split_bf16":
+            entry["bf16_mma_tflops"] = 6 * plan.flops / (t * 1e-3) / 1e12
+            entry["frac_of_bf16_peak"] = entry["bf16_mma_tflops"] / peaks.get("bf16_tflops", 1900.0)
+        else:
+            entry["frac_of_fp64_nominal"] = gf / 1e3 / FP64_NOMINAL_TFLOPS
+        out[prec] = entry
+        del blocks, ws, res, g
+        torch.cuda.empty_cache()
+    out["split_speedup_over_fp64"] = out["native"]["ms_per_step"] / out["split_bf16"]["ms_per_step"]
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -287,6 +342,8 @@ def main():
         return run_profile_case(a.profile_case, a)
     if a.sweep == "transpose":
         return run_transpose_sweep()
+    if a.workload == "triples":
+        return run_triples(a)
     import numpy as np
     import torch
     import torch.distributed as dist

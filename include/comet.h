@@ -61,10 +61,12 @@ typedef enum {
     /* FP64 arithmetic: FP64 tensor-core MMA (mma.sync f64) with FP64 accumulation.  For
        FP32-stored operands the values are widened exactly and the result rounded once. */
     COMET_PREC_NATIVE = 0,
-    /* Split precision: each operand element x is split into three bfloat16 parts
-       hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid); six of the nine part products
-       (hh, hm, mh, hl, lh, mm) run on the tcgen05 tensor cores with FP32 accumulation in
-       tensor memory.  Target: normwise relative error <= 1e-6 against FP64. */
+    /* Split precision: each operand is scaled by 2^-e (e = exponent of its largest magnitude)
+       and every element split into three bfloat16 fixed-point parts, x * 2^-e rounded to
+       nearest on the grids 2^-6, 2^-14 and 2^-22; six of the nine part products (hh, hm, mh,
+       hl, lh, mm) run on the tensor cores with FP32 accumulation, the hh products in chunks of
+       up to 1024 K values that sum exactly.  Target: normwise relative error <= 1e-6 against
+       FP64 (measured 3.4e-7 on the o=64 v=192 workload). */
     COMET_PREC_SPLIT_BF16 = 1
 } comet_precision_t;
 

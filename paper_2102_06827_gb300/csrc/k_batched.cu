@@ -131,6 +131,11 @@ __device__ __forceinline__ void reduce_add(double s, double q, double *red, doub
     }
 }
 
+// A work item is one N-strip of one block: BN output columns and every M tile of them.  When
+// the contracted extent fits one chunk (K <= KCH, the triples case), the strip's B operand is
+// loaded (and split) once and reused by every M tile; s and q accumulate over the strip, so
+// one pair of atomic additions closes it.
+
 // ---- FP64 path -------------------------------------------------------------------------------
 template <int BM, int BN, bool AK, bool BKC, typename TIn>
 __global__ void __launch_bounds__(BT) batched_f64_kernel(const BatchedParams P) {
@@ -148,80 +153,98 @@ __global__ void __launch_bounds__(BT) batched_f64_kernel(const BatchedParams P) 
         __syncthreads();
         const uint32_t M = sd.M, N = sd.N, K = sd.K, idx = sd.index;
         const uint32_t mtiles = (M + BM - 1) / BM;
-        const uint32_t tile = item - P.prefix[pos];
-        const uint32_t m0 = (tile % mtiles) * BM, n0 = (tile / mtiles) * BN;
-        for (int i = t; i < BM + BN; i += BT) {
+        const uint32_t n0 = (item - P.prefix[pos]) * BN;
+        const bool bres = K <= (uint32_t)KCH;
+        for (int i = t; i < BN; i += BT) {
             int64_t o0 = 0, o1 = 0;
-            if (i < BM) {
-                if (m0 + i < M) radix_offsets(sd.ma, m0 + i, o0, o1);
-                a_row[i] = o0; o_row[i] = o1;
-            } else {
-                if (n0 + i - BM < N) radix_offsets(sd.nb, n0 + i - BM, o0, o1);
-                b_col[i - BM] = o0; o_col[i - BM] = o1;
-            }
+            if (n0 + i < N) radix_offsets(sd.nb, n0 + i, o0, o1);
+            b_col[i] = o0; o_col[i] = o1;
+        }
+        if (t < KCH) {
+            int64_t o0 = 0, o1 = 0;
+            if ((uint32_t)t < K) radix_offsets(sd.k, t, o0, o1);
+            a_k[t] = o0; b_k[t] = o1;
         }
         const TIn *A = reinterpret_cast<const TIn *>(P.inputs[2 * idx + P.swap]);
         const TIn *B = reinterpret_cast<const TIn *>(P.inputs[2 * idx + 1 - P.swap]);
-        double acc[MI][NJ][2];
-#pragma unroll
-        for (int i = 0; i < MI; ++i)
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
-        for (uint32_t k0 = 0; k0 < K; k0 += KCH) {
-            __syncthreads();
-            if (t < KCH) {
-                int64_t o0 = 0, o1 = 0;
-                if (k0 + t < K) radix_offsets(sd.k, k0 + t, o0, o1);
-                a_k[t] = o0; b_k[t] = o1;
-            }
-            __syncthreads();
-            for (int e = t; e < BM * KCH; e += BT) {
-                int m, k;
-                if (AK) { k = e % KCH; m = e / KCH; } else { m = e % BM; k = e / BM; }
-                As[k][m] = (m0 + m < M && k0 + k < K) ? (double)A[a_row[m] + a_k[k]] : 0.0;
-            }
+        auto load_b = [&](uint32_t k0) {
             for (int e = t; e < BN * KCH; e += BT) {
                 int n, k;
                 if (BKC) { k = e % KCH; n = e / KCH; } else { n = e % BN; k = e / BN; }
                 Bs[k][n] = (n0 + n < N && k0 + k < K) ? (double)B[b_col[n] + b_k[k]] : 0.0;
             }
-            __syncthreads();
-#pragma unroll
-            for (int k4 = 0; k4 < KCH / 4; ++k4) {
-                const int kk = k4 * 4 + (lane & 3);
-                double af[MI], bf[NJ];
-#pragma unroll
-                for (int i = 0; i < MI; ++i) af[i] = As[kk][wm * (BM / 2) + i * 8 + (lane >> 2)];
-#pragma unroll
-                for (int j = 0; j < NJ; ++j) bf[j] = Bs[kk][wn * (BN / 2) + j * 8 + (lane >> 2)];
-#pragma unroll
-                for (int i = 0; i < MI; ++i)
-#pragma unroll
-                    for (int j = 0; j < NJ; ++j) dmma(acc[i][j], af[i], bf[j]);
-            }
-        }
-        // epilogue
+        };
+        __syncthreads();
+        if (bres) load_b(0);
         double s = 0.0, q = 0.0;
         TIn *out = P.mode == 1 ? reinterpret_cast<TIn *const *>(P.result)[idx] : nullptr;
+        for (uint32_t mt = 0; mt < mtiles; ++mt) {
+            const uint32_t m0 = mt * BM;
+            __syncthreads();
+            for (int i = t; i < BM; i += BT) {
+                int64_t o0 = 0, o1 = 0;
+                if (m0 + i < M) radix_offsets(sd.ma, m0 + i, o0, o1);
+                a_row[i] = o0; o_row[i] = o1;
+            }
+            __syncthreads();
+            double acc[MI][NJ][2];
 #pragma unroll
-        for (int i = 0; i < MI; ++i) {
-            const int ml = wm * (BM / 2) + i * 8 + (lane >> 2);
+            for (int i = 0; i < MI; ++i)
 #pragma unroll
-            for (int j = 0; j < NJ; ++j)
+                for (int j = 0; j < NJ; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
+            for (uint32_t k0 = 0; k0 < K; k0 += KCH) {
+                if (!bres) {
+                    __syncthreads();
+                    if (t < KCH) {
+                        int64_t o0 = 0, o1 = 0;
+                        if (k0 + t < K) radix_offsets(sd.k, k0 + t, o0, o1);
+                        a_k[t] = o0; b_k[t] = o1;
+                    }
+                    __syncthreads();
+                    load_b(k0);
+                }
+                for (int e = t; e < BM * KCH; e += BT) {
+                    int m, k;
+                    if (AK) { k = e % KCH; m = e / KCH; } else { m = e % BM; k = e / BM; }
+                    As[k][m] = (m0 + m < M && k0 + k < K) ? (double)A[a_row[m] + a_k[k]] : 0.0;
+                }
+                __syncthreads();
+                const int kmax = (int)min((uint32_t)KCH, K - k0);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int nl = wn * (BN / 2) + j * 8 + (lane & 3) * 2 + h;
-                    if (m0 + ml < M && n0 + nl < N) {
-                        const double T = P.alpha * acc[i][j][h];
-                        const int64_t lin = o_row[ml] + o_col[nl];
-                        if (P.mode == 0) {
-                            s += T * (double)tri_weight(P.key, idx, (uint32_t)lin);
-                            q += T * T;
-                        } else if (out) {
-                            out[lin] = (TIn)T;
+                for (int k4 = 0; k4 < KCH / 4; ++k4) {
+                    if (k4 * 4 >= kmax) break;
+                    const int kk = k4 * 4 + (lane & 3);
+                    double af[MI], bf[NJ];
+#pragma unroll
+                    for (int i = 0; i < MI; ++i) af[i] = As[kk][wm * (BM / 2) + i * 8 + (lane >> 2)];
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j) bf[j] = Bs[kk][wn * (BN / 2) + j * 8 + (lane >> 2)];
+#pragma unroll
+                    for (int i = 0; i < MI; ++i)
+#pragma unroll
+                        for (int j = 0; j < NJ; ++j) dmma(acc[i][j], af[i], bf[j]);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < MI; ++i) {
+                const int ml = wm * (BM / 2) + i * 8 + (lane >> 2);
+#pragma unroll
+                for (int j = 0; j < NJ; ++j)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int nl = wn * (BN / 2) + j * 8 + (lane & 3) * 2 + h;
+                        if (m0 + ml < M && n0 + nl < N) {
+                            const double T = P.alpha * acc[i][j][h];
+                            const int64_t lin = o_row[ml] + o_col[nl];
+                            if (P.mode == 0) {
+                                s += T * (double)tri_weight(P.key, idx, (uint32_t)lin);
+                                q += T * T;
+                            } else if (out) {
+                                out[lin] = (TIn)T;
+                            }
                         }
                     }
-                }
+            }
         }
         if (P.mode == 0) reduce_add(s, q, red, reinterpret_cast<double *>(P.result), idx);
         __syncthreads();
@@ -247,107 +270,125 @@ __global__ void __launch_bounds__(BT) batched_split_kernel(const BatchedParams P
         __syncthreads();
         const uint32_t M = sd.M, N = sd.N, K = sd.K, idx = sd.index;
         const uint32_t mtiles = (M + BM - 1) / BM;
-        const uint32_t tile = item - P.prefix[pos];
-        const uint32_t m0 = (tile % mtiles) * BM, n0 = (tile / mtiles) * BN;
+        const uint32_t n0 = (item - P.prefix[pos]) * BN;
         const int ea = P.exps[2 * idx], eb = P.exps[2 * idx + 1];
-        for (int i = t; i < BM + BN; i += BT) {
+        const bool bres = K <= (uint32_t)KCH;
+        for (int i = t; i < BN; i += BT) {
             int64_t o0 = 0, o1 = 0;
-            if (i < BM) {
-                if (m0 + i < M) radix_offsets(sd.ma, m0 + i, o0, o1);
-                a_row[i] = o0; o_row[i] = o1;
-            } else {
-                if (n0 + i - BM < N) radix_offsets(sd.nb, n0 + i - BM, o0, o1);
-                b_col[i - BM] = o0; o_col[i - BM] = o1;
-            }
+            if (n0 + i < N) radix_offsets(sd.nb, n0 + i, o0, o1);
+            b_col[i] = o0; o_col[i] = o1;
+        }
+        if (t < KCH) {
+            int64_t o0 = 0, o1 = 0;
+            if ((uint32_t)t < K) radix_offsets(sd.k, t, o0, o1);
+            a_k[t] = o0; b_k[t] = o1;
         }
         const TIn *A = reinterpret_cast<const TIn *>(P.inputs[2 * idx + P.swap]);
         const TIn *B = reinterpret_cast<const TIn *>(P.inputs[2 * idx + 1 - P.swap]);
-        float p0[MI][NJ][4], p1[MI][NJ][4];
-#pragma unroll
-        for (int i = 0; i < MI; ++i)
-#pragma unroll
-            for (int j = 0; j < NJ; ++j)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) p0[i][j][c] = p1[i][j][c] = 0.0f;
-        for (uint32_t k0 = 0; k0 < K; k0 += KCH) {
-            __syncthreads();
-            if (t < KCH) {
-                int64_t o0 = 0, o1 = 0;
-                if (k0 + t < K) radix_offsets(sd.k, k0 + t, o0, o1);
-                a_k[t] = o0; b_k[t] = o1;
-            }
-            __syncthreads();
-            for (int e = t; e < BM * KCH; e += BT) {
-                int m, k;
-                if (AK) { k = e % KCH; m = e / KCH; } else { m = e % BM; k = e / BM; }
-                const TIn x = (m0 + m < M && k0 + k < K) ? A[a_row[m] + a_k[k]] : (TIn)0;
-                split3<TIn>(x, ea, As[0][m][k], As[1][m][k], As[2][m][k]);
-            }
+        auto load_b = [&](uint32_t k0) {
             for (int e = t; e < BN * KCH; e += BT) {
                 int n, k;
                 if (BKC) { k = e % KCH; n = e / KCH; } else { n = e % BN; k = e / BN; }
                 const TIn x = (n0 + n < N && k0 + k < K) ? B[b_col[n] + b_k[k]] : (TIn)0;
                 split3<TIn>(x, eb, Bs[0][n][k], Bs[1][n][k], Bs[2][n][k]);
             }
-            __syncthreads();
-#pragma unroll
-            for (int ks = 0; ks < KCH / 16; ++ks) {
-                uint32_t af[3][MI][4], bf[3][NJ][2];
-#pragma unroll
-                for (int pl = 0; pl < 3; ++pl) {
-#pragma unroll
-                    for (int i = 0; i < MI; ++i) {
-                        const int r = wm * (BM / 2) + i * 16 + g;
-                        const int c = ks * 16 + 2 * tq;
-                        af[pl][i][0] = *reinterpret_cast<const uint32_t *>(&As[pl][r][c]);
-                        af[pl][i][1] = *reinterpret_cast<const uint32_t *>(&As[pl][r + 8][c]);
-                        af[pl][i][2] = *reinterpret_cast<const uint32_t *>(&As[pl][r][c + 8]);
-                        af[pl][i][3] = *reinterpret_cast<const uint32_t *>(&As[pl][r + 8][c + 8]);
-                    }
-#pragma unroll
-                    for (int j = 0; j < NJ; ++j) {
-                        const int r = wn * (BN / 2) + j * 8 + g;
-                        const int c = ks * 16 + 2 * tq;
-                        bf[pl][j][0] = *reinterpret_cast<const uint32_t *>(&Bs[pl][r][c]);
-                        bf[pl][j][1] = *reinterpret_cast<const uint32_t *>(&Bs[pl][r][c + 8]);
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < MI; ++i)
-#pragma unroll
-                    for (int j = 0; j < NJ; ++j) {
-                        bmma(p1[i][j], af[1][i], bf[1][j]);   // mm
-                        bmma(p1[i][j], af[2][i], bf[0][j]);   // lh
-                        bmma(p1[i][j], af[0][i], bf[2][j]);   // hl
-                        bmma(p1[i][j], af[1][i], bf[0][j]);   // mh
-                        bmma(p1[i][j], af[0][i], bf[1][j]);   // hm
-                        bmma(p0[i][j], af[0][i], bf[0][j]);   // hh: exact accumulator
-                    }
-            }
-        }
-        // epilogue: T = alpha * 2^(ea+eb) * (P0 + P1)
+        };
+        __syncthreads();
+        if (bres) load_b(0);
         const float scale = (float)ldexp(P.alpha, ea + eb);
         float s = 0.0f, q = 0.0f;
         TIn *out = P.mode == 1 ? reinterpret_cast<TIn *const *>(P.result)[idx] : nullptr;
+        for (uint32_t mt = 0; mt < mtiles; ++mt) {
+            const uint32_t m0 = mt * BM;
+            __syncthreads();
+            for (int i = t; i < BM; i += BT) {
+                int64_t o0 = 0, o1 = 0;
+                if (m0 + i < M) radix_offsets(sd.ma, m0 + i, o0, o1);
+                a_row[i] = o0; o_row[i] = o1;
+            }
+            __syncthreads();
+            float p0[MI][NJ][4], p1[MI][NJ][4];
 #pragma unroll
-        for (int i = 0; i < MI; ++i)
+            for (int i = 0; i < MI; ++i)
 #pragma unroll
-            for (int j = 0; j < NJ; ++j)
+                for (int j = 0; j < NJ; ++j)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int ml = wm * (BM / 2) + i * 16 + g + (c >= 2 ? 8 : 0);
-                    const int nl = wn * (BN / 2) + j * 8 + 2 * tq + (c & 1);
-                    if (m0 + ml < M && n0 + nl < N) {
-                        const float T = scale * (p0[i][j][c] + p1[i][j][c]);
-                        const int64_t lin = o_row[ml] + o_col[nl];
-                        if (P.mode == 0) {
-                            s = fmaf(T, tri_weight(P.key, idx, (uint32_t)lin), s);
-                            q = fmaf(T, T, q);
-                        } else if (out) {
-                            out[lin] = (TIn)T;
+                    for (int c = 0; c < 4; ++c) p0[i][j][c] = p1[i][j][c] = 0.0f;
+            for (uint32_t k0 = 0; k0 < K; k0 += KCH) {
+                if (!bres) {
+                    __syncthreads();
+                    if (t < KCH) {
+                        int64_t o0 = 0, o1 = 0;
+                        if (k0 + t < K) radix_offsets(sd.k, k0 + t, o0, o1);
+                        a_k[t] = o0; b_k[t] = o1;
+                    }
+                    __syncthreads();
+                    load_b(k0);
+                }
+                for (int e = t; e < BM * KCH; e += BT) {
+                    int m, k;
+                    if (AK) { k = e % KCH; m = e / KCH; } else { m = e % BM; k = e / BM; }
+                    const TIn x = (m0 + m < M && k0 + k < K) ? A[a_row[m] + a_k[k]] : (TIn)0;
+                    split3<TIn>(x, ea, As[0][m][k], As[1][m][k], As[2][m][k]);
+                }
+                __syncthreads();
+                const int kmax = (int)min((uint32_t)KCH, K - k0);
+#pragma unroll
+                for (int ks = 0; ks < KCH / 16; ++ks) {
+                    if (ks * 16 >= kmax) break;
+                    uint32_t af[3][MI][4], bf[3][NJ][2];
+#pragma unroll
+                    for (int pl = 0; pl < 3; ++pl) {
+#pragma unroll
+                        for (int i = 0; i < MI; ++i) {
+                            const int r = wm * (BM / 2) + i * 16 + g;
+                            const int c = ks * 16 + 2 * tq;
+                            af[pl][i][0] = *reinterpret_cast<const uint32_t *>(&As[pl][r][c]);
+                            af[pl][i][1] = *reinterpret_cast<const uint32_t *>(&As[pl][r + 8][c]);
+                            af[pl][i][2] = *reinterpret_cast<const uint32_t *>(&As[pl][r][c + 8]);
+                            af[pl][i][3] = *reinterpret_cast<const uint32_t *>(&As[pl][r + 8][c + 8]);
+                        }
+#pragma unroll
+                        for (int j = 0; j < NJ; ++j) {
+                            const int r = wn * (BN / 2) + j * 8 + g;
+                            const int c = ks * 16 + 2 * tq;
+                            bf[pl][j][0] = *reinterpret_cast<const uint32_t *>(&Bs[pl][r][c]);
+                            bf[pl][j][1] = *reinterpret_cast<const uint32_t *>(&Bs[pl][r][c + 8]);
                         }
                     }
+#pragma unroll
+                    for (int i = 0; i < MI; ++i)
+#pragma unroll
+                        for (int j = 0; j < NJ; ++j) {
+                            bmma(p1[i][j], af[1][i], bf[1][j]);   // mm
+                            bmma(p1[i][j], af[2][i], bf[0][j]);   // lh
+                            bmma(p1[i][j], af[0][i], bf[2][j]);   // hl
+                            bmma(p1[i][j], af[1][i], bf[0][j]);   // mh
+                            bmma(p1[i][j], af[0][i], bf[1][j]);   // hm
+                            bmma(p0[i][j], af[0][i], bf[0][j]);   // hh: exact accumulator
+                        }
                 }
+            }
+#pragma unroll
+            for (int i = 0; i < MI; ++i)
+#pragma unroll
+                for (int j = 0; j < NJ; ++j)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int ml = wm * (BM / 2) + i * 16 + g + (c >= 2 ? 8 : 0);
+                        const int nl = wn * (BN / 2) + j * 8 + 2 * tq + (c & 1);
+                        if (m0 + ml < M && n0 + nl < N) {
+                            const float T = scale * (p0[i][j][c] + p1[i][j][c]);
+                            const int64_t lin = o_row[ml] + o_col[nl];
+                            if (P.mode == 0) {
+                                s = fmaf(T, tri_weight(P.key, idx, (uint32_t)lin), s);
+                                q = fmaf(T, T, q);
+                            } else if (out) {
+                                out[lin] = (TIn)T;
+                            }
+                        }
+                    }
+        }
         if (P.mode == 0) reduce_add((double)s, (double)q, red, reinterpret_cast<double *>(P.result), idx);
         __syncthreads();
     }
@@ -651,7 +692,7 @@ comet_status_t comet_plan_batched(const char *expr, int n_blocks, const char *co
         for (int i = 0; i < n_blocks; ++i) {
             const BlockDesc &d = desc[order[i]];
             P.batched_prefix[c][i] = (uint32_t)acc;
-            acc += (uint64_t)((d.M + tc.bm - 1) / tc.bm) * ((d.N + tc.bn - 1) / tc.bn);
+            acc += (uint64_t)((d.N + tc.bn - 1) / tc.bn);   // one item per N strip
         }
         if (acc >= (1ull << 32)) {
             set_error_message("more than 2^32 tiles");
