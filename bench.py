@@ -54,7 +54,7 @@ def args_parse():
     ap.add_argument("--pc-extents", default="64,128,128,256", help="transpose profile case extents")
     ap.add_argument("--pc-perm", default="3,1,0,2", help="transpose profile case permutation")
     ap.add_argument("--pc-dtype", default="f32", choices=["f32", "f64"])
-    ap.add_argument("--workload", default="ccsd", choices=["ccsd", "triples"],
+    ap.add_argument("--workload", default="ccsd", choices=["ccsd", "triples", "small"],
                     help="ccsd: the headline line; triples: the batched workload (separate JSON line)")
     ap.add_argument("--sweep", default=None, choices=["transpose"],
                     help="time the transpose sweep (rank-4/rank-6, FP32/FP64, 64 MiB - 2 GiB) and exit")
@@ -163,6 +163,82 @@ def run_triples(a) -> int:
         del blocks, ws, res, g
         torch.cuda.empty_cache()
     out["split_speedup_over_fp64"] = out["native"]["ms_per_step"] / out["split_bf16"]["ms_per_step"]
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_small_and_chain(a) -> int:
+    """The extent-24 FP64 contraction (plus its bit-exact transpose) and the differentiated
+    three-operand chain (forward + backward through the autograd function, split-BF16 on FP32
+    storage).  Prints one JSON line (not the headline line)."""
+    import torch
+    import paper_2102_06827_gb300 as comet
+    from paper_2102_06827_gb300 import autograd
+    import synth
+    dev = torch.device("cuda", 0)
+    out = {}
+    # extent-24 FP64 contraction, timed as a captured graph of 100 launches
+    e24 = "C[a,b,c,d] = A[a,e,b] * B[e,d,c]"
+    ext = dict(a=24, b=24, c=24, d=24, e=24)
+    p = comet.Plan(e24, ext, torch.float64)
+    A = synth.torch_uniform(0, 0, 24 ** 3, dev)
+    B = synth.torch_uniform(0, 1, 24 ** 3, dev)
+    C = torch.empty(24 ** 4, dtype=torch.float64, device=dev)
+    T = torch.empty_like(A)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        p.contract([A, B], C, stream=s)
+        comet.transpose(A, (24, 24, 24), (2, 0, 1), out=T, stream=s)
+    torch.cuda.synchronize()
+    for name, fn in (("contract", lambda: p.contract([A, B], C, stream=s)),
+                     ("transpose", lambda: comet.transpose(A, (24, 24, 24), (2, 0, 1), out=T, stream=s))):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            for _ in range(100):
+                fn()
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) / 1000 * 1e3
+        out["extent24_" + name + "_us"] = us
+    out["extent24_contract_gflops"] = p.flops / (out["extent24_contract_us"] * 1e-6) / 1e9
+    out["extent24_transpose_gbs"] = 2 * 8 * 24 ** 3 / (out["extent24_transpose_us"] * 1e-6) / 1e9
+    # differentiated chain D[a,b] = A[a,i,j] B[i,j,k,l] C[k,l,b], split-BF16 on FP32 storage
+    ec = "D[a,b] = A[a,i,j] * B[i,j,k,l] * C[k,l,b]"
+    shapes = [(256, 48, 48), (48, 48, 48, 48), (48, 48, 256)]
+    xs = [synth.torch_uniform(4, t, math.prod(sh), dev, dtype=torch.float32).view(tuple(reversed(sh)))
+          .requires_grad_(True) for t, sh in enumerate(shapes)]
+    G = synth.torch_uniform(4, 9, 256 * 256, dev, dtype=torch.float32).view(256, 256)
+
+    def step():
+        for x in xs:
+            x.grad = None
+        D = autograd.einsum(ec, *xs, precision="split_bf16", layout="col")
+        D.backward(G)
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 10
+    pf = comet.Plan(ec, dict(a=256, b=256, i=48, j=48, k=48, l=48), torch.float32, precision="split_bf16")
+    bwd = sum(comet.Plan(autograd.adjoint_expr(ec, q), dict(a=256, b=256, i=48, j=48, k=48, l=48),
+                         torch.float32, precision="split_bf16").flops for q in range(3))
+    out["chain_fwd_bwd_ms"] = ms
+    out["chain_flops_fwd"] = pf.flops
+    out["chain_flops_bwd"] = bwd
+    out["chain_gflops"] = (pf.flops + bwd) / (ms * 1e-3) / 1e9
+    out["chain_order"] = pf.info["order"]
+    comet.sync_status()
     print(json.dumps(out), flush=True)
     return 0
 
@@ -344,6 +420,8 @@ def main():
         return run_transpose_sweep()
     if a.workload == "triples":
         return run_triples(a)
+    if a.workload == "small":
+        return run_small_and_chain(a)
     import numpy as np
     import torch
     import torch.distributed as dist

@@ -179,7 +179,10 @@ static comet_status_t run_plan(const Plan &P, const void *const *inputs, void *o
             {
                 ProfScope ps(PK_PREPASS, stream);
                 e = launch_absmax(g.A, na, es, sc_a, stream);
-                if (e == cudaSuccess) e = launch_absmax(g.B, nb, es, sc_b, stream);
+            }
+            if (e == cudaSuccess) {
+                ProfScope ps(PK_PREPASS, stream);
+                e = launch_absmax(g.B, nb, es, sc_b, stream);
             }
             if (e != cudaSuccess) return cuda_status(e, "split pre-pass (scales)");
             {
