@@ -54,6 +54,8 @@ def args_parse():
     ap.add_argument("--pc-extents", default="64,128,128,256", help="transpose profile case extents")
     ap.add_argument("--pc-perm", default="3,1,0,2", help="transpose profile case permutation")
     ap.add_argument("--pc-dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--ablation", action="store_true",
+                    help="Table 1 natural vs planned order, and every TTGT form vs the chosen one")
     ap.add_argument("--workload", default="ccsd", choices=["ccsd", "triples", "small"],
                     help="ccsd: the headline line; triples: the batched workload (separate JSON line)")
     ap.add_argument("--sweep", default=None, choices=["transpose"],
@@ -243,6 +245,117 @@ def run_small_and_chain(a) -> int:
     return 0
 
 
+def _time_plan(plan, ins, out, ws, reps=5, graph=False):
+    """ms per contraction: eager launches, or one captured CUDA graph of `reps` contractions
+    (which removes the host launch cost that dominates small multi-step plans)."""
+    import torch
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    for _ in range(2):
+        plan.contract(ins, out, ws, stream=s)
+    g = None
+    if graph:
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            for _ in range(reps):
+                plan.contract(ins, out, ws, stream=s)
+        with torch.cuda.stream(s):
+            g.replay()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):  # CUDAGraph.replay() launches on the current stream
+        e0.record(s)
+        if g is not None:
+            g.replay()
+        else:
+            for _ in range(reps):
+                plan.contract(ins, out, ws, stream=s)
+        e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_ablation(a) -> int:
+    """The paper's two ablations on this GPU (split-BF16 path, FP32 storage):
+    (1) the multi-operand expressions of Table 1, natural left-to-right order vs the planned
+        order, occupied labels i,j,m,n = o and virtual labels a..f = v for (o, v) = (24, 72)
+        and (64, 192), synthetic extents, timed eagerly and as one captured CUDA graph;
+    (2) every enumerated TTGT form of two contractions vs the planner's choice (best vs
+        arbitrary permutation).  Prints one JSON line."""
+    import re
+    import torch
+    import paper_2102_06827_gb300 as comet
+    import synth
+    dev = torch.device("cuda", 0)
+    out = {"table1": [], "forms": []}
+    rows = [l.split("|") for l in open(os.path.join(ROOT, "tests", "golden", "table1_expressions.txt"))
+            if l.strip() and not l.startswith("#")]
+    for (o_ext, v_ext) in ((24, 72), (64, 192)):
+        for rhs, paper in rows:
+            ops = [[x.strip() for x in t.split(",")] for t in re.findall(r"\[([^\]]*)\]", rhs)]
+            cnt = {}
+            for o in ops:
+                for l in o:
+                    cnt[l] = cnt.get(l, 0) + 1
+            outl = [l for o in ops for l in o if cnt[l] == 1]
+            ext = {l: (o_ext if l in "ijmn" else v_ext) for o in ops for l in o}
+            expr = f"X[{','.join(outl)}] = {rhs.strip()}"
+            ins = [synth.torch_uniform(7, t, math.prod(ext[l] for l in o), dev, dtype=torch.float32,
+                                       scale=1.0 / math.sqrt(math.prod(ext[l] for l in o)))
+                   for t, o in enumerate(ops)]
+            res = {"expr": expr, "o": o_ext, "v": v_ext, "paper_speedup": float(paper)}
+            for order in ("planned", "natural"):
+                p = comet.Plan(expr, ext, torch.float32, precision="split_bf16", order=order)
+                C = torch.empty(math.prod(ext[l] for l in outl), dtype=torch.float32, device=dev)
+                ws = p.workspace(dev)
+                res[order + "_ms"] = _time_plan(p, ins, C, ws)
+                res[order + "_graph_ms"] = _time_plan(p, ins, C, ws, graph=True)
+                comet.profile_enable(True)
+                comet.profile_read()
+                for _ in range(3):
+                    p.contract(ins, C, ws)
+                torch.cuda.synchronize()
+                res[order + "_kernels_ms"] = {k: (n / 3, t / 3) for k, (n, t) in comet.profile_read().items()}
+                comet.profile_enable(False)
+                res[order + "_flops"] = p.flops
+                res[order + "_tree"] = p.info["order"]
+                del ws, C
+            res["speedup"] = res["natural_ms"] / res["planned_ms"]
+            res["speedup_graph"] = res["natural_graph_ms"] / res["planned_graph_ms"]
+            res["flop_ratio"] = res["natural_flops"] / res["planned_flops"]
+            out["table1"].append(res)
+            del ins
+            torch.cuda.empty_cache()
+    cases = [("C[i,a,j,b] = A[k,a,c,i] * B[c,b,k,j]", dict(i=48, j=48, k=48, a=144, b=144, c=144)),
+             ("C[a,b,c,d] = A[a,e,b,f] * B[d,f,c,e]", dict(a=96, b=96, c=96, d=96, e=48, f=48))]
+    for expr, ext in cases:
+        p0 = comet.Plan(expr, ext, torch.float32, precision="split_bf16")
+        n = p0.info["steps"][0]["n_forms"]
+        tens = re.findall(r"\w+\[([^\]]*)\]", expr)
+        outl, ins_l = tens[0], tens[1:]
+        ins = [synth.torch_uniform(8, t, math.prod(ext[l.strip()] for l in o.split(",")), dev, dtype=torch.float32)
+               for t, o in enumerate(ins_l)]
+        C = torch.empty(math.prod(ext[l.strip()] for l in outl.split(",")), dtype=torch.float32, device=dev)
+        times = []
+        for k in range(n):
+            p = comet.Plan(expr, ext, torch.float32, precision="split_bf16", form=k)
+            ws = p.workspace(dev)
+            times.append(_time_plan(p, ins, C, ws, reps=3, graph=True))
+            del ws
+        chosen = p0.info["steps"][0]["form_index"]
+        srt = sorted(times)
+        out["forms"].append({"expr": expr, "n_forms": n, "chosen": chosen, "chosen_ms": times[chosen],
+                             "best_ms": srt[0], "median_ms": srt[len(srt) // 2], "worst_ms": srt[-1],
+                             "best_over_worst": srt[-1] / srt[0],
+                             "chosen_vs_best": times[chosen] / srt[0],
+                             "chosen_over_median_speedup": srt[len(srt) // 2] / times[chosen]})
+        torch.cuda.empty_cache()
+    comet.sync_status()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_profile_case(case: str, a=None) -> int:
     """Small cases for ncu captures: inputs above the 129 MB L2, a few GB on the device."""
     import torch
@@ -422,6 +535,8 @@ def main():
         return run_triples(a)
     if a.workload == "small":
         return run_small_and_chain(a)
+    if a.ablation:
+        return run_ablation(a)
     import numpy as np
     import torch
     import torch.distributed as dist
