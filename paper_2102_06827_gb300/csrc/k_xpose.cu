@@ -60,161 +60,206 @@ __device__ __forceinline__ void emit(const XposeParams &p, int64_t off, const T 
     }
 }
 
-constexpr int XTAB = 256;        // largest tile extent along U, V or R that uses offset tables
+constexpr int XTAB = 256;        // largest tile extent along U, V or R
 
-// Transposing mode: tile (u, v, w) of tu x tv x tw.  Loads run along u (input-contiguous),
-// stores along v (output-contiguous); the tile sits in shared memory as [w][v][u] with an odd
-// row pitch so the column reads of the store phase do not collide in one bank.  Each thread
-// keeps one lane position along the contiguous direction and walks rows, so the index work is
-// one division per vector.  OFF is int32_t when every offset fits, else int64_t.
+template <typename OFF>
+struct RowOut {
+    OFF o;          // output offset of the row's first element
+    int32_t s;      // tile position (shared memory) of the row's first element
+};
+
+// Transposing mode: tile (u, v, w) of tu x tv x tw.  U is the input's leading run (affine in
+// the input with stride su), V the output's (affine in the output with stride sv), R the rest.
+// The block first tabulates the input offset of every (v, w) row and the output offset of every
+// (u, w) row of its tile, so the two phases below cost one table read per row and no index
+// arithmetic per element.  Loads run along u, each thread keeping one u and walking rows; the
+// tile sits in shared memory as rows (v + nv*w) of pitch tu|1 (odd, so that the store phase's
+// column reads spread over the banks); stores run along v.  OFF is int32_t when every offset
+// fits, else int64_t.
 template <int OP, typename T, int VI, int VO, typename OFF>
 __global__ void __launch_bounds__(XT) xpose_tile_kernel(const XposeParams p) {
     extern __shared__ __align__(16) unsigned char xsm[];
-    T *buf = reinterpret_cast<T *>(xsm);
-    __shared__ OFF u_in[XTAB], u_out[XTAB], v_in[XTAB], v_out[XTAB], w_in[XTAB], w_out[XTAB];
+    __shared__ OFF uo[XTAB], vin[XTAB], win[XTAB], wout[XTAB];
     const int t = threadIdx.x;
     const uint32_t tu = p.tu, tv = p.tv, tw = p.tw;
     const uint32_t pitch = tu | 1u;
-    uint32_t b = blockIdx.x;
-    const uint32_t bu = b % p.tiles_u;
-    b /= p.tiles_u;
-    const uint32_t bv = b % p.tiles_v, bw = b / p.tiles_v;
+    T *buf = reinterpret_cast<T *>(xsm);
+    OFF *in_row = reinterpret_cast<OFF *>(xsm + align16(tv * tw * pitch * (uint32_t)sizeof(T)));
+    RowOut<OFF> *out_row =
+        reinterpret_cast<RowOut<OFF> *>(reinterpret_cast<unsigned char *>(in_row) + align16(tv * tw * (uint32_t)sizeof(OFF)));
+    const uint32_t b = fd_div(blockIdx.x, p.fd_tiles_u), bu = blockIdx.x - b * p.tiles_u;
+    const uint32_t bw = fd_div(b, p.fd_tiles_v), bv = b - bw * p.tiles_v;
     const uint32_t u0 = bu * tu, v0 = bv * tv, w0 = bw * tw;
     const uint32_t nu = min(tu, p.u.total - u0), nv = min(tv, p.v.total - v0), nw = min(tw, p.r.total - w0);
-    for (uint32_t i = t; i < tu; i += XT) {
-        int64_t a = 0, c = 0;
-        if (i < nu) radix_offsets(p.u, u0 + i, a, c);
-        u_in[i] = (OFF)a; u_out[i] = (OFF)c;
+    const int64_t su = p.u.s0[0], sv = p.v.s1[0];
+    for (uint32_t i = t; i < nu; i += XT) {
+        int64_t a, c;
+        radix_offsets(p.u, u0 + i, a, c);
+        uo[i] = (OFF)c;
     }
-    for (uint32_t i = t; i < tv; i += XT) {
-        int64_t a = 0, c = 0;
-        if (i < nv) radix_offsets(p.v, v0 + i, a, c);
-        v_in[i] = (OFF)a; v_out[i] = (OFF)c;
+    for (uint32_t i = t; i < nv; i += XT) {
+        int64_t a, c;
+        radix_offsets(p.v, v0 + i, a, c);
+        vin[i] = (OFF)a;
     }
-    for (uint32_t i = t; i < tw; i += XT) {
-        int64_t a = 0, c = 0;
-        if (i < nw) radix_offsets(p.r, w0 + i, a, c);
-        w_in[i] = (OFF)a; w_out[i] = (OFF)c;
+    for (uint32_t i = t; i < nw; i += XT) {
+        int64_t a, c;
+        radix_offsets(p.r, w0 + i, a, c);
+        win[i] = (OFF)a;
+        wout[i] = (OFF)c;
     }
     __syncthreads();
-    const T *__restrict__ in = reinterpret_cast<const T *>(p.in);
+    const uint32_t rows_v = nv * nw, rows_u = nu * nw;
+    for (uint32_t r = t; r < rows_v; r += XT) {
+        const uint32_t w = nv == tv ? fd_div(r, p.fd_tv) : r / nv, v = r - w * nv;
+        in_row[r] = (OFF)((int64_t)u0 * su + vin[v] + win[w]);
+    }
+    for (uint32_t r = t; r < rows_u; r += XT) {
+        const uint32_t w = nu == tu ? fd_div(r, p.fd_tu) : r / nu, u = r - w * nu;
+        RowOut<OFF> ro;
+        ro.o = (OFF)((int64_t)v0 * sv + uo[u] + wout[w]);
+        ro.s = (int32_t)(w * nv * pitch + u);
+        out_row[r] = ro;
+    }
+    __syncthreads();
     const int e = (OP == OP_SPLIT) ? scale_exponent<T>(p.scale_bits) : 0;
-    // read along u: lanes_l threads per row, each with a fixed u
-    {
-        const uint32_t lanes = (tu + VI - 1) / VI;
-        const uint32_t rpp = XT / lanes;
-        const uint32_t r0 = t / lanes;
+    {   // loads: p.ll threads per row, each with a fixed u; batches of rows in flight together
+        const uint32_t lanes = p.ll, rpp = p.rpp_l;
+        const uint32_t r0 = fd_div(t, p.fd_ll);
         const uint32_t u = (t - r0 * lanes) * VI;
         if (r0 < rpp && u < nu) {
-            const OFF ui = u_in[u];
-            const uint32_t rows = tv * tw;
-            // a batch of rows is loaded into registers before any of it is written to shared
-            // memory, so the batch's global loads are all in flight together
+            const T *__restrict__ src = reinterpret_cast<const T *>(p.in) + (int64_t)u * su;
+            T *dst = buf + u;
             constexpr int UB = VI * sizeof(T) >= 16 ? 4 : 8;
-            for (uint32_t row0 = r0; row0 < rows; row0 += UB * rpp) {
+            for (uint32_t row0 = r0; row0 < rows_v; row0 += UB * rpp) {
                 Vec<VI, T> x[UB];
-                bool ok[UB];
 #pragma unroll
                 for (int j = 0; j < UB; ++j) {
                     const uint32_t row = row0 + j * rpp;
-                    const uint32_t w = fd_div(row, p.fd_tv);
-                    const uint32_t v = row - w * tv;
-                    ok[j] = row < rows && v < nv && w < nw;
-                    if (ok[j]) x[j] = *reinterpret_cast<const Vec<VI, T> *>(in + ((int64_t)w_in[w] + v_in[v] + ui));
+                    if (row < rows_v) x[j] = *reinterpret_cast<const Vec<VI, T> *>(src + in_row[row]);
                 }
 #pragma unroll
                 for (int j = 0; j < UB; ++j) {
-                    if (ok[j]) {
-                        T *dst = buf + (row0 + j * rpp) * pitch + u;
+                    const uint32_t row = row0 + j * rpp;
+                    if (row < rows_v) {
+                        T *d = dst + row * pitch;
 #pragma unroll
-                        for (int q = 0; q < VI; ++q) dst[q] = x[j].v[q];
+                        for (int q = 0; q < VI; ++q) d[q] = x[j].v[q];
                     }
                 }
             }
         }
     }
     __syncthreads();
-    // write along v: lanes threads per (u, w) row, each with a fixed v
-    {
-        const uint32_t lanes = (tv + VO - 1) / VO;
-        const uint32_t rpp = XT / lanes;
-        const uint32_t r0 = t / lanes;
+    {   // stores: p.sl threads per row, each with a fixed v
+        const uint32_t lanes = p.sl, rpp = p.rpp_s;
+        const uint32_t r0 = fd_div(t, p.fd_sl);
         const uint32_t v = (t - r0 * lanes) * VO;
         if (r0 < rpp && v < nv) {
-            const OFF vo = v_out[v];
-            const uint32_t rows = tu * tw;
-            constexpr int UL = VO * sizeof(T) >= 16 ? 4 : 16;
+            const T *sb = buf + v * pitch;
+            const int64_t vo = (int64_t)v * sv;
+            constexpr int UL = VO * sizeof(T) >= 16 ? 4 : 8;
 #pragma unroll UL
-            for (uint32_t row = r0; row < rows; row += rpp) {
-                const uint32_t w = fd_div(row, p.fd_tu);
-                const uint32_t u = row - w * tu;
-                if (u < nu && w < nw) {
-                    T x[VO];
-                    const T *src = buf + (w * tv + v) * pitch + u;
+            for (uint32_t row = r0; row < rows_u; row += rpp) {
+                const RowOut<OFF> ro = out_row[row];
+                T x[VO];
 #pragma unroll
-                    for (int q = 0; q < VO; ++q) x[q] = src[q * pitch];
-                    emit<OP, T, VO>(p, (int64_t)w_out[w] + u_out[u] + vo, x, e);
-                }
+                for (int q = 0; q < VO; ++q) x[q] = sb[ro.s + q * pitch];
+                emit<OP, T, VO>(p, (int64_t)ro.o + vo, x, e);
             }
         }
     }
 }
 
-// Copy mode: input and output share the stride-1 dims U, so a tile of tu x tw goes straight
-// through registers.  A single fused dim (tu above the table size) is addressed affinely.
-template <int OP, typename T, int VW>
-__global__ void __launch_bounds__(XT) xpose_copy_kernel(const XposeParams p) {
-    __shared__ int64_t u_in[XTAB], u_out[XTAB], w_in[XTAB], w_out[XTAB];
+// Copy mode: input and output share the stride-1 dim U (a single digit, affine on both sides
+// with strides su, so), so a tile of tu x tw goes straight through registers.  Rows (the R
+// digits) are tabulated per block; each thread keeps one u and walks rows.
+template <int OP, typename T, int VW, typename OFF>
+__global__ void __launch_bounds__(XT, 6) xpose_copy_kernel(const XposeParams p) {
+    __shared__ OFF row_in[XTAB], row_out[XTAB];
     const int t = threadIdx.x;
     const uint32_t tu = p.tu, tw = p.tw;
-    const bool affine = tu > (uint32_t)XTAB;
-    const uint32_t bu = blockIdx.x % p.tiles_u, bw = blockIdx.x / p.tiles_u;
+    const uint32_t bw = fd_div(blockIdx.x, p.fd_tiles_u), bu = blockIdx.x - bw * p.tiles_u;
     const uint32_t u0 = bu * tu, w0 = bw * tw;
     const uint32_t nu = min(tu, p.u.total - u0), nw = min(tw, p.r.total - w0);
-    if (!affine)
-        for (uint32_t i = t; i < tu; i += XT) {
-            int64_t a = 0, c = 0;
-            if (i < nu) radix_offsets(p.u, u0 + i, a, c);
-            u_in[i] = a; u_out[i] = c;
-        }
-    for (uint32_t i = t; i < tw; i += XT) {
-        int64_t a = 0, c = 0;
-        if (i < nw) radix_offsets(p.r, w0 + i, a, c);
-        w_in[i] = a; w_out[i] = c;
+    const int64_t su = p.u.s0[0], so = p.u.s1[0];
+    for (uint32_t i = t; i < nw; i += XT) {
+        int64_t a, c;
+        radix_offsets(p.r, w0 + i, a, c);
+        row_in[i] = (OFF)(a + (int64_t)u0 * su);
+        row_out[i] = (OFF)(c + (int64_t)u0 * so);
     }
     __syncthreads();
     const T *__restrict__ in = reinterpret_cast<const T *>(p.in);
     const int e = (OP == OP_SPLIT) ? scale_exponent<T>(p.scale_bits) : 0;
-    const int64_t s_in = p.u.s0[0], s_out = p.u.s1[0];
-    const uint32_t n = tu * tw;
-    // batches of UB vectors: all loads of a batch are issued before any store, so they are in
-    // flight together (the compiler cannot reorder loads from `in` above stores to `out`)
-    constexpr int UB = VW * sizeof(T) >= 16 ? 4 : (VW * sizeof(T) >= 8 ? 8 : 16);
-    for (uint32_t idx0 = t * VW; idx0 < n; idx0 += UB * XT * VW) {
-        Vec<VW, T> x[UB];
-        int64_t oo[UB];
-        bool ok[UB];
+    constexpr int UB = VW * sizeof(T) >= 16 ? 4 : 8;
+    const uint32_t lanes = p.ll;
+    const uint32_t rpp = p.rpp_l;
+    const uint32_t r0 = fd_div(t, p.fd_ll);
+    const uint32_t u = (t - r0 * lanes) * VW;
+    if (!(r0 < rpp && u < nu)) return;
+    const T *__restrict__ src = in + (int64_t)u * su;
+    const int64_t uo = (int64_t)u * so;
+    // rows r0, r0 + rpp, ...: a ring of UB loads stays in flight; each store is followed by the
+    // load of the row UB passes ahead into the register it freed
+    Vec<VW, T> x[UB];
+#pragma unroll
+    for (int j = 0; j < UB; ++j) {
+        const uint32_t row = r0 + j * rpp;
+        if (row < nw) x[j] = *reinterpret_cast<const Vec<VW, T> *>(src + row_in[row]);
+    }
+    for (uint32_t row0 = r0; row0 < nw; row0 += UB * rpp) {
 #pragma unroll
         for (int j = 0; j < UB; ++j) {
-            const uint32_t idx = idx0 + j * XT * VW;
-            const uint32_t w = fd_div(idx, p.fd_tu);
-            const uint32_t u = idx - w * tu;
-            ok[j] = idx < n && u < nu && w < nw;
-            if (ok[j]) {
-                const int64_t oi = affine ? (int64_t)(u0 + u) * s_in : (int64_t)u_in[u];
-                oo[j] = w_out[w] + (affine ? (int64_t)(u0 + u) * s_out : (int64_t)u_out[u]);
-                x[j] = *reinterpret_cast<const Vec<VW, T> *>(in + w_in[w] + oi);
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < UB; ++j) {
-            if (ok[j]) {
+            const uint32_t row = row0 + j * rpp;
+            if (row < nw) {
                 T xs[VW];
 #pragma unroll
                 for (int q = 0; q < VW; ++q) xs[q] = x[j].v[q];
-                emit<OP, T, VW>(p, oo[j], xs, e);
+                emit<OP, T, VW>(p, (int64_t)row_out[row] + uo, xs, e);
+                const uint32_t nr = row + UB * rpp;
+                if (nr < nw) x[j] = *reinterpret_cast<const Vec<VW, T> *>(src + row_in[nr]);
             }
         }
+    }
+}
+
+// A single long run (copy mode, R empty), cut into pieces of up to kXposeTile elements: every
+// thread strides along u with 16-byte vectors; the ragged tail moves element-wise.
+template <int OP, typename T, int VW>
+__global__ void __launch_bounds__(XT) xpose_run_kernel(const XposeParams p) {
+    const int t = threadIdx.x;
+    const uint32_t tu = p.tu;
+    const uint32_t u0 = blockIdx.x * tu;
+    const uint32_t nu = min(tu, p.u.total - u0);
+    const int64_t su = p.u.s0[0], so = p.u.s1[0];
+    const T *__restrict__ in = reinterpret_cast<const T *>(p.in);
+    const int e = (OP == OP_SPLIT) ? scale_exponent<T>(p.scale_bits) : 0;
+    constexpr int UB = VW * sizeof(T) >= 16 ? 4 : 8;
+    const int64_t ri = (int64_t)u0 * su, ro = (int64_t)u0 * so;
+    const uint32_t nvec = nu / VW * VW;
+    for (uint32_t u00 = t * VW; u00 < nvec; u00 += UB * XT * VW) {
+        Vec<VW, T> x[UB];
+#pragma unroll
+        for (int j = 0; j < UB; ++j) {
+            const uint32_t u = u00 + j * XT * VW;
+            if (u < nvec) x[j] = *reinterpret_cast<const Vec<VW, T> *>(in + ri + (int64_t)u * su);
+        }
+#pragma unroll
+        for (int j = 0; j < UB; ++j) {
+            const uint32_t u = u00 + j * XT * VW;
+            if (u < nvec) {
+                T xs[VW];
+#pragma unroll
+                for (int q = 0; q < VW; ++q) xs[q] = x[j].v[q];
+                emit<OP, T, VW>(p, ro + (int64_t)u * so, xs, e);
+            }
+        }
+    }
+    if (t < (int)(nu - nvec)) {
+        const uint32_t u = nvec + t;
+        T xs[1] = {in[ri + (int64_t)u * su]};
+        emit<OP, T, 1>(p, ro + (int64_t)u * so, xs, e);
     }
 }
 
@@ -262,11 +307,23 @@ static cudaError_t launch_op(const XposeParams &p, int vi, int vo, cudaStream_t 
     if (g == 0) return cudaSuccess;
     constexpr int W = 16 / sizeof(T);
     if (vo < 0) {   // copy mode
-        if (-vo >= W && vi >= W) xpose_copy_kernel<OP, T, W><<<g, XT, 0, s>>>(p);
-        else xpose_copy_kernel<OP, T, 1><<<g, XT, 0, s>>>(p);
+        const bool wide = -vo >= W && vi >= W;
+        if (p.single_run) {
+            if (wide) xpose_run_kernel<OP, T, W><<<g, XT, 0, s>>>(p);
+            else xpose_run_kernel<OP, T, 1><<<g, XT, 0, s>>>(p);
+            return cudaGetLastError();
+        }
+        if (p.off32) {
+            if (wide) xpose_copy_kernel<OP, T, W, int32_t><<<g, XT, 0, s>>>(p);
+            else xpose_copy_kernel<OP, T, 1, int32_t><<<g, XT, 0, s>>>(p);
+        } else {
+            if (wide) xpose_copy_kernel<OP, T, W, int64_t><<<g, XT, 0, s>>>(p);
+            else xpose_copy_kernel<OP, T, 1, int64_t><<<g, XT, 0, s>>>(p);
+        }
         return cudaGetLastError();
     }
-    const size_t smem = (size_t)p.tw * p.tv * (p.tu | 1u) * sizeof(T);
+    const size_t smem = xpose_smem_bytes(p, (int)sizeof(T));
+    if (smem > 96 * 1024) return cudaErrorInvalidConfiguration;
     auto go = [&](auto kern) {
         static bool set = false;
         if (!set) {

@@ -89,10 +89,25 @@ struct XposeParams {
     uint32_t tu, tv, tw;           // tile extents along U, V and R (tu*tv*tw <= kXposeTile)
     uint32_t tiles_u, tiles_v, tiles_w;
     FastDiv fd_tu, fd_tv, fd_tuv;  // division by tu, tv and tu*tv inside the tile
+    uint32_t ll, sl;               // threads per tile row: load phase ceil(tu/vi), store phase ceil(tv/vo)
+    uint32_t rpp_l, rpp_s;         // rows per pass of the 256-thread block: 256/ll, 256/sl
+    FastDiv fd_ll, fd_sl, fd_tiles_u, fd_tiles_v;
     int off32;                     // every input and output offset is below 2^31
+    int single_run;                // copy mode with R empty: one long run, ragged tail allowed
 };
 
 constexpr int kXposeTile = 4096;   // elements per tile (32 KB of FP64, 16 KB of FP32)
+
+CM_HD uint32_t align16(uint32_t b) { return (b + 15u) & ~15u; }
+
+// Dynamic shared memory of the transposing kernel: the (u, v, w) tile with an odd row pitch,
+// then the input offsets of its (v, w) rows, then the output offsets and tile positions of its
+// (u, w) rows.
+CM_HD uint32_t xpose_smem_bytes(const XposeParams &p, int elem_bytes) {
+    const uint32_t off = p.off32 ? 4u : 8u;
+    const uint32_t rows_v = p.tv * p.tw, rows_u = p.tu * p.tw;
+    return align16(rows_v * (p.tu | 1u) * (uint32_t)elem_bytes) + align16(rows_v * off) + align16(rows_u * 2u * off);
+}
 
 // Binary contraction as a GEMM over fused groups: C[m,n] = alpha * sum_k A[m,k] B[k,n]
 // (+ beta C).  ma: M digits with (A strides, C strides); nb: N digits with (B strides,

@@ -200,7 +200,13 @@ void setup_xpose(int rank, const int64_t *ext_in, const int64_t *sin_in,
     // up to 256 along U with rows from R; a single fused dim is cut into 4096-element pieces.
     const uint32_t Eu = p->u.total, Ev = p->v.total, Er = p->r.total;
     const uint32_t TAB = 256;
-    const uint32_t TILE = elem_bytes == 4 ? (uint32_t)kXposeTile : (uint32_t)kXposeTile / 2;  // 16 KB
+    // 16 KB of elements per tile; COMET_XPOSE_TILE (elements, 1024..16384) overrides it for tuning
+    static const uint32_t tile_env = [] {
+        const char *s = std::getenv("COMET_XPOSE_TILE");
+        const long v = s ? std::strtol(s, nullptr, 10) : 0;
+        return (uint32_t)(v >= 1024 && v <= 16384 ? v : 0);
+    }();
+    const uint32_t TILE = tile_env ? tile_env : elem_bytes == 4 ? (uint32_t)kXposeTile : (uint32_t)kXposeTile / 2;
     const uint32_t W = 16 / elem_bytes;
     // split a run of E into equal pieces of at most maxT, rounded up to a multiple of mult
     auto balanced = [](uint32_t E, uint32_t maxT, uint32_t mult) {
@@ -218,9 +224,13 @@ void setup_xpose(int rank, const int64_t *ext_in, const int64_t *sin_in,
         tv = 1;
         tw = 1;
     } else if (same) {
+        // copy mode keeps no tile in shared memory: rows up to the table size, as long as the
+        // grid keeps about 16 blocks per SM
         tu = balanced(Eu, TAB, W);
         tv = 1;
-        tw = std::min<uint32_t>(Er, std::min<uint32_t>(TAB, std::max<uint32_t>(1, TILE / tu)));
+        const uint64_t rows = (uint64_t)Er * ((Eu + tu - 1) / tu);
+        const uint64_t want = (rows + 152 * 16 - 1) / (152 * 16);
+        tw = (uint32_t)std::min<uint64_t>(Er, std::min<uint64_t>(TAB, std::max<uint64_t>(std::max<uint32_t>(1, TILE / tu), want)));
     } else {
         tu = balanced(Eu, 128, W);
         tv = balanced(Ev, std::min<uint32_t>(TAB, std::max<uint32_t>(16, TILE / tu)), W);
@@ -246,16 +256,27 @@ void setup_xpose(int rank, const int64_t *ext_in, const int64_t *sin_in,
         for (int d = 0; d < p->r.n; ++d) if (p->r.s1[d] % vw) return false;
         return true;
     };
-    int vi = 1, vo = 1;
-    for (int vw = w; vw > 1; vw /= 2) if (ok_in(vw)) { vi = vw; break; }
-    for (int vw = w; vw > 1; vw /= 2) if (ok_out(vw)) { vo = vw; break; }
-    if (same) { int m = std::min(vi, vo); vi = vo = m; }
-    *vec_in = vi;
-    *vec_out = same ? -vo : vo;   // negative = copy mode (no shared-memory transposition)
+    // the kernels come in 16-byte and element-wide variants only.  A single long run (copy
+    // mode, R empty) moves its ragged tail element-wise, so only the strides matter there.
+    p->single_run = (same && R.empty() && Eu > TAB) ? 1 : 0;
+    const bool unit = p->u.s0[0] == 1 && p->u.s1[0] == 1;
+    const int vi = (p->single_run ? unit : ok_in(w)) ? w : 1;
+    const int vo = (p->single_run ? unit : ok_out(w)) ? w : 1;
+    const int vc = std::min(vi, vo);
+    *vec_in = same ? vc : vi;
+    *vec_out = same ? -vc : vo;   // negative = copy mode (no shared-memory transposition)
     p->tu = tu; p->tv = tv; p->tw = tw;
+    p->ll = (tu + *vec_in - 1) / *vec_in;
+    p->sl = same ? 1 : (tv + vo - 1) / vo;
+    p->rpp_l = 256 / p->ll;
+    p->rpp_s = 256 / p->sl;
+    p->fd_ll = make_fastdiv(p->ll);
+    p->fd_sl = make_fastdiv(p->sl);
     p->tiles_u = (Eu + tu - 1) / tu;
     p->tiles_v = (Ev + tv - 1) / tv;
     p->tiles_w = (Er + tw - 1) / tw;
+    p->fd_tiles_u = make_fastdiv(p->tiles_u);
+    p->fd_tiles_v = make_fastdiv(p->tiles_v);
     p->fd_tu = make_fastdiv(tu);
     p->fd_tv = make_fastdiv(tv);
     p->fd_tuv = make_fastdiv(tu * tv);

@@ -24,93 +24,144 @@ static bool replay(const XposeParams &p, int vi, int vo, int64_t n_in, int64_t n
     const bool copy = vo < 0;
     CHECK(p.tu >= 1 && p.tv >= 1 && p.tw >= 1, "empty tile");
     CHECK((uint64_t)p.tu * p.tv * p.tw <= 8192 + 3 * 256 || (copy && p.tv == 1 && p.tw == 1), "tile too large");
-    CHECK((uint64_t)p.tw * p.tv * (p.tu | 1u) * 8 <= 96 * 1024, "tile exceeds the shared memory it is given");
+    CHECK(copy || xpose_smem_bytes(p, 8) <= 96 * 1024, "tile exceeds the shared memory it is given");
     CHECK(p.tv <= (uint32_t)XTAB && p.tw <= (uint32_t)XTAB, "tile edge above the table size");
     CHECK(copy || p.tu <= (uint32_t)XTAB, "transposing tile edge above the table size");
+    CHECK(p.ll >= 1 && p.sl >= 1 && p.sl <= (uint32_t)XT, "lane counts");
+    CHECK(p.rpp_s == (uint32_t)XT / p.sl && (p.ll > (uint32_t)XT || p.rpp_l == (uint32_t)XT / p.ll), "rows per pass");
+    CHECK(copy || p.ll <= (uint32_t)XT, "load lanes above the block");
+    CHECK(p.ll == (p.tu + (uint32_t)(copy ? -vo : vi) - 1) / (uint32_t)(copy ? -vo : vi), "load lanes vs vector width");
+    CHECK(copy || p.sl == (p.tv + (uint32_t)vo - 1) / (uint32_t)vo, "store lanes vs vector width");
+    CHECK(vi == 1 || vi * 4 == 16 || vi * 8 == 16, "vector width");
     const uint64_t grid = (uint64_t)p.tiles_u * p.tiles_v * p.tiles_w;
     const uint32_t tu = p.tu, tv = p.tv, tw = p.tw, pitch = tu | 1u;
+    const int64_t su = p.u.s0[0];
+    {   // U is affine in the input with stride su (and, in copy mode, in the output with p.u.s1[0])
+        int64_t s = su;
+        for (int d = 0; d < p.u.n; ++d) { CHECK(p.u.s0[d] == s, "U not affine in the input"); s *= p.u.ext[d]; }
+        CHECK(!copy || p.u.n <= 1, "copy-mode U with several digits");
+    }
+    if (!copy) {   // V is affine in the output with stride sv
+        int64_t s = p.v.s1[0];
+        for (int d = 0; d < p.v.n; ++d) { CHECK(p.v.s1[d] == s, "V not affine in the output"); s *= p.v.ext[d]; }
+    }
     for (uint64_t blk = 0; blk < grid && fails == 0; ++blk) {
         if (copy) {
-            const bool affine = tu > (uint32_t)XTAB;
-            const uint32_t bu = blk % p.tiles_u, bw = blk / p.tiles_u;
+            const uint32_t bw = fd_div((uint32_t)blk, p.fd_tiles_u), bu = (uint32_t)blk - bw * p.tiles_u;
+            CHECK(bu == blk % p.tiles_u && bw == blk / p.tiles_u, "block decomposition");
             const uint32_t u0 = bu * tu, w0 = bw * tw;
             const uint32_t nu = std::min(tu, p.u.total - u0), nw = std::min(tw, p.r.total - w0);
-            CHECK(!affine || p.u.n == 1, "affine copy of a multi-digit group");
+            const int64_t so = p.u.s1[0];
             const int VW = -vo;
-            for (uint32_t t = 0; t < (uint32_t)XT; ++t)
-                for (uint32_t idx = t * VW; idx < tu * tw; idx += XT * VW) {
-                    uint32_t w = fd_div(idx, p.fd_tu), u = idx - w * tu;
-                    if (!(u < nu && w < nw)) continue;
-                    int64_t a, c, wi, wo;
-                    radix_offsets(p.u, u0 + u, a, c);
-                    if (affine) { CHECK(a == (int64_t)(u0 + u) * p.u.s0[0] && c == (int64_t)(u0 + u) * p.u.s1[0], "affine offsets"); }
-                    radix_offsets(p.r, w0 + w, wi, wo);
-                    CHECK((wi + a) % VW == 0 && (wo + c) % VW == 0, "misaligned copy vector");
-                    for (int q = 0; q < VW; ++q) {
-                        CHECK(u + q < nu, "vector crosses the tile");
-                        int64_t a2, c2;
-                        radix_offsets(p.u, u0 + u + q, a2, c2);
-                        CHECK(a2 == a + q && c2 == c + q, "copy vector not contiguous");
-                        int64_t si = wi + a + q, d = wo + c + q;
-                        CHECK(si >= 0 && si < n_in && d >= 0 && d < n_out_span, "copy out of bounds");
-                        if (d >= 0 && d < n_out_span) { CHECK(src_of_out[d] == -1, "written twice"); src_of_out[d] = si; }
-                    }
+            std::vector<int64_t> row_in(nw), row_out(nw);
+            CHECK(nw <= (uint32_t)XTAB, "rows above the table size");
+            for (uint32_t i = 0; i < nw; ++i) {
+                int64_t a, c;
+                radix_offsets(p.r, w0 + i, a, c);
+                row_in[i] = a + (int64_t)u0 * su;
+                row_out[i] = c + (int64_t)u0 * so;
+                CHECK(!p.off32 || (row_in[i] < (1ll << 31) && row_out[i] < (1ll << 31)), "32-bit row offset overflows");
+            }
+            auto move = [&](uint32_t u, uint32_t row) {
+                const int64_t si = row_in[row] + (int64_t)u * su, d = row_out[row] + (int64_t)u * so;
+                CHECK(si % VW == 0 && d % VW == 0, "misaligned copy vector");
+                for (int q = 0; q < VW; ++q) {
+                    CHECK(u + q < nu, "vector crosses the tile");
+                    CHECK(VW == 1 || (su == 1 && so == 1), "vector along a strided run");
+                    const int64_t a = si + q * su, c = d + q * so;
+                    CHECK(a >= 0 && a < n_in && c >= 0 && c < n_out_span, "copy out of bounds");
+                    if (c >= 0 && c < n_out_span) { CHECK(src_of_out[c] == -1, "written twice"); src_of_out[c] = a; }
                 }
+            };
+            const uint32_t lanes = p.ll;
+            if (p.single_run) {
+                CHECK(nw == 1 && p.r.total == 1, "long-row copy with several rows");
+                CHECK(p.tiles_u == 1 || tu % VW == 0, "long-row tiles do not start on a vector boundary");
+                const uint32_t nvec = nu / VW * VW;
+                for (uint32_t t = 0; t < (uint32_t)XT; ++t)
+                    for (uint32_t u = t * VW; u < nvec; u += XT * VW) move(u, 0);
+                CHECK(nu - nvec <= (uint32_t)XT, "tail longer than the block");
+                for (uint32_t t = 0; t < nu - nvec; ++t) {   // element-wise tail
+                    const uint32_t u = nvec + t;
+                    const int64_t a = row_in[0] + (int64_t)u * su, c = row_out[0] + (int64_t)u * so;
+                    CHECK(a >= 0 && a < n_in && c >= 0 && c < n_out_span, "tail out of bounds");
+                    if (c >= 0 && c < n_out_span) { CHECK(src_of_out[c] == -1, "written twice"); src_of_out[c] = a; }
+                }
+                continue;
+            }
+            CHECK(lanes <= (uint32_t)XT, "row copy with more lanes than threads");
+            const uint32_t rpp = p.rpp_l;
+            for (uint32_t t = 0; t < (uint32_t)XT; ++t) {
+                const uint32_t r0 = fd_div(t, p.fd_ll), u = (t - r0 * lanes) * VW;
+                if (!(r0 < rpp && u < nu)) continue;
+                for (uint32_t row = r0; row < nw; row += rpp) move(u, row);
+            }
             continue;
         }
-        uint32_t b = blk;
-        const uint32_t bu = b % p.tiles_u;
-        b /= p.tiles_u;
-        const uint32_t bv = b % p.tiles_v, bw = b / p.tiles_v;
+        const uint32_t b = fd_div((uint32_t)blk, p.fd_tiles_u), bu = (uint32_t)blk - b * p.tiles_u;
+        const uint32_t bw = fd_div(b, p.fd_tiles_v), bv = b - bw * p.tiles_v;
+        CHECK(bu == blk % p.tiles_u && bv == (blk / p.tiles_u) % p.tiles_v && bw == blk / p.tiles_u / p.tiles_v, "block decomposition");
         const uint32_t u0 = bu * tu, v0 = bv * tv, w0 = bw * tw;
         const uint32_t nu = std::min(tu, p.u.total - u0), nv = std::min(tv, p.v.total - v0),
                        nw = std::min(tw, p.r.total - w0);
-        std::vector<int64_t> ui(tu), uo(tu), vin(tv), vout(tv), wi(tw), wo(tw);
-        for (uint32_t i = 0; i < tu; ++i) { ui[i] = uo[i] = 0; if (i < nu) radix_offsets(p.u, u0 + i, ui[i], uo[i]); }
-        for (uint32_t i = 0; i < tv; ++i) { vin[i] = vout[i] = 0; if (i < nv) radix_offsets(p.v, v0 + i, vin[i], vout[i]); }
-        for (uint32_t i = 0; i < tw; ++i) { wi[i] = wo[i] = 0; if (i < nw) radix_offsets(p.r, w0 + i, wi[i], wo[i]); }
+        const int64_t sv = p.v.s1[0];
+        std::vector<int64_t> uo(nu), vin(nv), win(nw), wout(nw);
+        for (uint32_t i = 0; i < nu; ++i) { int64_t a; radix_offsets(p.u, u0 + i, a, uo[i]); CHECK(a == (int64_t)(u0 + i) * su, "U input offset"); }
+        for (uint32_t i = 0; i < nv; ++i) { int64_t c; radix_offsets(p.v, v0 + i, vin[i], c); CHECK(c == (int64_t)(v0 + i) * sv, "V output offset"); }
+        for (uint32_t i = 0; i < nw; ++i) radix_offsets(p.r, w0 + i, win[i], wout[i]);
+        const uint32_t rows_v = nv * nw, rows_u = nu * nw;
+        std::vector<int64_t> in_row(rows_v), out_o(rows_u), out_s(rows_u);
+        for (uint32_t r = 0; r < rows_v; ++r) {
+            uint32_t w = nv == tv ? fd_div(r, p.fd_tv) : r / nv, v = r - w * nv;
+            CHECK(w == r / nv, "row division (v)");
+            in_row[r] = (int64_t)u0 * su + vin[v] + win[w];
+        }
+        for (uint32_t r = 0; r < rows_u; ++r) {
+            uint32_t w = nu == tu ? fd_div(r, p.fd_tu) : r / nu, u = r - w * nu;
+            CHECK(w == r / nu, "row division (u)");
+            out_o[r] = (int64_t)v0 * sv + uo[u] + wout[w];
+            out_s[r] = (int64_t)w * nv * pitch + u;
+        }
+        for (uint32_t r = 0; r < rows_v; ++r) CHECK(!p.off32 || in_row[r] < (1ll << 31), "32-bit input row offset overflows");
+        for (uint32_t r = 0; r < rows_u; ++r) CHECK(!p.off32 || out_o[r] < (1ll << 31), "32-bit output row offset overflows");
         std::vector<int64_t> buf((size_t)tw * tv * pitch, -1);
-        CHECK(p.off32 == 0 || (n_in < (1ll << 31) && n_out_span < (1ll << 31)), "32-bit offsets on a large tensor");
-        {   // loads: fixed u per thread, rows (v, w) walked
-            const uint32_t lanes = (tu + vi - 1) / vi, rpp = XT / lanes;
+        {   // loads: p.ll threads per row, fixed u, rows (v, w) walked
+            const uint32_t lanes = p.ll, rpp = p.rpp_l;
             CHECK(rpp >= 1, "no rows per pass (load)");
             for (uint32_t t = 0; t < (uint32_t)XT; ++t) {
-                const uint32_t r0 = t / lanes, u = (t - r0 * lanes) * vi;
+                const uint32_t r0 = fd_div(t, p.fd_ll), u = (t - r0 * lanes) * vi;
                 if (!(r0 < rpp && u < nu)) continue;
-                for (uint32_t row = r0; row < tv * tw; row += rpp) {
-                    const uint32_t w = fd_div(row, p.fd_tv), v = row - w * tv;
-                    if (!(v < nv && w < nw)) continue;
-                    int64_t src = wi[w] + vin[v] + ui[u];
+                for (uint32_t row = r0; row < rows_v; row += rpp) {
+                    const int64_t src = (int64_t)u * su + in_row[row];
                     CHECK(src % vi == 0, "misaligned vector load");
                     for (int q = 0; q < vi; ++q) {
                         CHECK(u + q < nu, "vector load crosses the tile");
-                        CHECK(ui[u + q] == ui[u] + q, "vector load not contiguous");
+                        CHECK(vi == 1 || su == 1, "vector load along a strided run");
                         CHECK(src + q >= 0 && src + q < n_in, "load out of bounds");
-                        CHECK(row * pitch + u + q < buf.size(), "shared store out of the tile");
-                        buf[row * pitch + u + q] = src + q;
+                        const size_t bi = (size_t)row * pitch + u + q;
+                        CHECK(bi < buf.size(), "shared store out of the tile");
+                        if (bi < buf.size()) buf[bi] = src + q;
                     }
                 }
             }
         }
-        {   // stores: fixed v per thread, rows (u, w) walked
-            const uint32_t lanes = (tv + vo - 1) / vo, rpp = XT / lanes;
+        {   // stores: p.sl threads per row, fixed v, rows (u, w) walked
+            const uint32_t lanes = p.sl, rpp = p.rpp_s;
             CHECK(rpp >= 1, "no rows per pass (store)");
             for (uint32_t t = 0; t < (uint32_t)XT; ++t) {
-                const uint32_t r0 = t / lanes, v = (t - r0 * lanes) * vo;
+                const uint32_t r0 = fd_div(t, p.fd_sl), v = (t - r0 * lanes) * vo;
                 if (!(r0 < rpp && v < nv)) continue;
-                for (uint32_t row = r0; row < tu * tw; row += rpp) {
-                    const uint32_t w = fd_div(row, p.fd_tu), u = row - w * tu;
-                    if (!(u < nu && w < nw)) continue;
-                    int64_t dst = wo[w] + uo[u] + vout[v];
+                for (uint32_t row = r0; row < rows_u; row += rpp) {
+                    const int64_t dst = out_o[row] + (int64_t)v * sv;
                     CHECK(dst % vo == 0, "misaligned vector store");
                     for (int q = 0; q < vo; ++q) {
                         CHECK(v + q < nv, "vector store crosses the tile");
-                        CHECK(vout[v + q] == vout[v] + q, "vector store not contiguous");
-                        size_t bi = (size_t)(w * tv + v + q) * pitch + u;
+                        CHECK(vo == 1 || sv == 1, "vector store along a strided run");
+                        const size_t bi = (size_t)(v + q) * pitch + out_s[row];
                         CHECK(bi < buf.size(), "shared load out of the tile");
-                        int64_t s2 = buf[bi];
+                        const int64_t s2 = bi < buf.size() ? buf[bi] : -1;
                         CHECK(s2 >= 0, "store of an element that was not loaded");
-                        int64_t d = dst + q;
+                        const int64_t d = dst + q;
                         CHECK(d >= 0 && d < n_out_span, "store out of bounds");
                         if (d >= 0 && d < n_out_span) { CHECK(src_of_out[d] == -1, "written twice"); src_of_out[d] = s2; }
                     }
@@ -164,7 +215,7 @@ int main() {
     // permutations, tiny leading extents on one or both sides
     {
         struct Fx { int rank; int64_t ext[6]; int perm[6]; };
-        const Fx fx[] = {{1, {5000}, {0}}, {2, {300, 500}, {0, 1}}, {3, {54, 97, 7}, {0, 1, 2}},
+        const Fx fx[] = {{1, {5000}, {0}}, {1, {4999}, {0}}, {1, {8193}, {0}}, {2, {257, 3}, {0, 1}}, {2, {300, 500}, {0, 1}}, {3, {54, 97, 7}, {0, 1, 2}},
                          {3, {9, 13, 100}, {1, 2, 0}}, {4, {9, 13, 10, 8}, {1, 0, 3, 2}},
                          {3, {2000, 9, 5}, {1, 0, 2}}, {2, {4096, 3}, {0, 1}}, {3, {300, 2, 5}, {0, 2, 1}},
                          {6, {8, 11, 5, 6, 13, 8}, {1, 2, 4, 5, 3, 0}}};
