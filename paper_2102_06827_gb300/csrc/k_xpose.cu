@@ -77,7 +77,7 @@ struct RowOut {
 // column reads spread over the banks); stores run along v.  OFF is int32_t when every offset
 // fits, else int64_t.
 template <int OP, typename T, int VI, int VO, typename OFF>
-__global__ void __launch_bounds__(XT) xpose_tile_kernel(const XposeParams p) {
+__global__ void __launch_bounds__(XT, 8) xpose_tile_kernel(const XposeParams p) {
     extern __shared__ __align__(16) unsigned char xsm[];
     __shared__ OFF uo[XTAB], vin[XTAB], win[XTAB], wout[XTAB];
     const int t = threadIdx.x;
@@ -130,7 +130,9 @@ __global__ void __launch_bounds__(XT) xpose_tile_kernel(const XposeParams p) {
         if (r0 < rpp && u < nu) {
             const T *__restrict__ src = reinterpret_cast<const T *>(p.in) + (int64_t)u * su;
             T *dst = buf + u;
-            constexpr int UB = VI * sizeof(T) >= 16 ? 4 : 8;
+            // four vectors per batch keep the kernel within 32 registers, so eight blocks fit on
+            // an SM: residency matters more here than loads in flight per thread (measured)
+            constexpr int UB = 4;
             for (uint32_t row0 = r0; row0 < rows_v; row0 += UB * rpp) {
                 Vec<VI, T> x[UB];
 #pragma unroll
@@ -301,6 +303,17 @@ static uint32_t xpose_grid(const XposeParams &p) {
     return p.tiles_u * p.tiles_v * p.tiles_w;
 }
 
+// the shared-memory attribute is set once per kernel instantiation
+template <int OP, typename T, int VI, int VO, typename OFF>
+static void launch_tile(const XposeParams &p, uint32_t g, size_t smem, cudaStream_t s) {
+    static const bool attr = [] {
+        cudaFuncSetAttribute(xpose_tile_kernel<OP, T, VI, VO, OFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        return true;
+    }();
+    (void)attr;
+    xpose_tile_kernel<OP, T, VI, VO, OFF><<<g, XT, smem, s>>>(p);
+}
+
 template <int OP, typename T>
 static cudaError_t launch_op(const XposeParams &p, int vi, int vo, cudaStream_t s) {
     const uint32_t g = xpose_grid(p);
@@ -324,24 +337,16 @@ static cudaError_t launch_op(const XposeParams &p, int vi, int vo, cudaStream_t 
     }
     const size_t smem = xpose_smem_bytes(p, (int)sizeof(T));
     if (smem > 96 * 1024) return cudaErrorInvalidConfiguration;
-    auto go = [&](auto kern) {
-        static bool set = false;
-        if (!set) {
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-            set = true;
-        }
-        kern<<<g, XT, smem, s>>>(p);
-    };
     if (p.off32) {
-        if (vi >= W && vo >= W) go(xpose_tile_kernel<OP, T, W, W, int32_t>);
-        else if (vi >= W) go(xpose_tile_kernel<OP, T, W, 1, int32_t>);
-        else if (vo >= W) go(xpose_tile_kernel<OP, T, 1, W, int32_t>);
-        else go(xpose_tile_kernel<OP, T, 1, 1, int32_t>);
+        if (vi >= W && vo >= W) launch_tile<OP, T, W, W, int32_t>(p, g, smem, s);
+        else if (vi >= W) launch_tile<OP, T, W, 1, int32_t>(p, g, smem, s);
+        else if (vo >= W) launch_tile<OP, T, 1, W, int32_t>(p, g, smem, s);
+        else launch_tile<OP, T, 1, 1, int32_t>(p, g, smem, s);
     } else {
-        if (vi >= W && vo >= W) go(xpose_tile_kernel<OP, T, W, W, int64_t>);
-        else if (vi >= W) go(xpose_tile_kernel<OP, T, W, 1, int64_t>);
-        else if (vo >= W) go(xpose_tile_kernel<OP, T, 1, W, int64_t>);
-        else go(xpose_tile_kernel<OP, T, 1, 1, int64_t>);
+        if (vi >= W && vo >= W) launch_tile<OP, T, W, W, int64_t>(p, g, smem, s);
+        else if (vi >= W) launch_tile<OP, T, W, 1, int64_t>(p, g, smem, s);
+        else if (vo >= W) launch_tile<OP, T, 1, W, int64_t>(p, g, smem, s);
+        else launch_tile<OP, T, 1, 1, int64_t>(p, g, smem, s);
     }
     return cudaGetLastError();
 }

@@ -232,7 +232,9 @@ void setup_xpose(int rank, const int64_t *ext_in, const int64_t *sin_in,
         const uint64_t want = (rows + 152 * 16 - 1) / (152 * 16);
         tw = (uint32_t)std::min<uint64_t>(Er, std::min<uint64_t>(TAB, std::max<uint64_t>(std::max<uint32_t>(1, TILE / tu), want)));
     } else {
-        tu = balanced(Eu, 128, W);
+        // both runs at least 64 elements where the extents allow: a leading input run up to 128
+        // is kept whole, a longer one is cut into pieces of about 64
+        tu = Eu <= 128 ? Eu : balanced(Eu, 64, W);
         tv = balanced(Ev, std::min<uint32_t>(TAB, std::max<uint32_t>(16, TILE / tu)), W);
         tw = std::min<uint32_t>(Er, std::min<uint32_t>(TAB, std::max<uint32_t>(1, TILE / (tu * tv))));
     }
