@@ -4,9 +4,10 @@ C[i,a,j,b] = sum_{k,c} A[k,a,c,i] * B[c,b,k,j] with o = 64 (i,j,k) and v = 192 (
 
 One step = one comet_contract() of the whole path on resident device tensors: split pre-pass
 of both operands into bfloat16 planes, tcgen05 split-BF16 GEMM with the output permutation in
-its epilogue.  The FP64 form (f64 tensor-core MMA) of the same contraction is timed beside it,
-and both results are checked against the CPU FP64 oracle on a sample of outputs (the
-cpu_baseline leg).  Prints one JSON line (rank 0).
+its epilogue.  The FP64 form of the same contraction is timed beside it twice -- native (f64
+tensor-core MMA) and emulated on the BF16 tensor cores (six slices) -- and every result is
+checked against the CPU FP64 oracle on a sample of outputs (the cpu_baseline leg).  Prints one
+JSON line (rank 0).
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -46,6 +47,7 @@ def args_parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--emu-steps", type=int, default=5)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -644,6 +646,39 @@ def main():
                          "peak_source": "nominal FP64 rate of the recipe table (not in MEASURED_PEAKS.json)"},
             "split_speedup_over_fp64": ms64 / ms_step}
 
+    # ---------------- the same FP64 contraction emulated on the BF16 tensor cores ----------------
+    plan_e = comet.Plan(EXPR, EXT, torch.float64, precision="emu_f64")
+    ws_e = plan_e.workspace(dev)
+    Ce = torch.empty(N_ELEM, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        plan_e.contract([A64, B64], Ce, ws_e)
+    comet.sync_status()
+    barrier()
+    comet.profile_enable(True)
+    comet.profile_read()
+    f0.record(stream)
+    for _ in range(a.emu_steps):
+        plan_e.contract([A64, B64], Ce, ws_e)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    prof_e = comet.profile_read()
+    comet.profile_enable(False)
+    comet.sync_status()
+    ms_e = max_over_ranks(f0.elapsed_time(f1)) / a.emu_steps
+    ke = prof_e.get("gemm_emu_bf16x6", (1, ms_e))
+    pe = prof_e.get("split_prepass", (0, 0.0))
+    emu_gemm_ms = ke[1] / max(1, ke[0])
+    emu_achieved = 21.0 * flops / (emu_gemm_ms * 1e-3) / 1e12
+    fp64["emulated"] = {
+        "precision": "emu_f64 (six bf16 slices, 21 products, exact chunk sums folded into int64)",
+        "gflops": world * flops / (ms_e * 1e-3) / 1e9, "ms_per_step": ms_e, "steps": a.emu_steps,
+        "prepass_ms_per_step": pe[1] / max(1, a.emu_steps),
+        "roofline": {"kernel": "gemm_emu_bf16x6", "bound": "tensor", "achieved": emu_achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": emu_achieved / peak, "peak_source": peak_src,
+                     "achieved_counts": "21 BF16 products x 2*M*N*K per launch", "ms_per_launch": emu_gemm_ms},
+        "speedup_over_native_fp64": ms64 / ms_e}
+    del ws_e
+
     # ---------------- end to end through the C ABI with host buffers ----------------
     hA = torch.empty(N_ELEM, dtype=torch.float32, pin_memory=True)
     hB = torch.empty(N_ELEM, dtype=torch.float32, pin_memory=True)
@@ -681,11 +716,14 @@ def main():
                "sample": f"{len(sel)} sampled outputs of C (each a 12288-term FP64 sum), {t_cpu:.1f} s"}
         got = C.cpu().numpy().astype(np.float64)[sel]
         got64 = C64.cpu().numpy()[sel]
+        got_e = Ce.cpu().numpy()[sel]
         den = float(np.abs(ref).max())
         err = {"split_bf16": {"normwise_rel": float(np.abs(got - ref).max() / den),
                               "max_abs": float(np.abs(got - ref).max()), "tolerance": 1e-6},
                "fp64": {"normwise_rel": float(np.abs(got64 - ref).max() / den),
                         "max_abs": float(np.abs(got64 - ref).max()), "tolerance": 1e-12},
+               "emu_f64": {"normwise_rel": float(np.abs(got_e - ref).max() / den),
+                           "max_abs": float(np.abs(got_e - ref).max()), "tolerance": 1e-12},
                "samples": len(sel)}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": a.steps,

@@ -67,7 +67,16 @@ typedef enum {
        hl, lh, mm) run on the tensor cores with FP32 accumulation, the hh products in chunks of
        up to 1024 K values that sum exactly.  Target: normwise relative error <= 1e-6 against
        FP64 (measured 3.4e-7 on the o=64 v=192 workload). */
-    COMET_PREC_SPLIT_BF16 = 1
+    COMET_PREC_SPLIT_BF16 = 1,
+    /* FP64 emulated on the BF16 tensor cores (FP64 storage only, else COMET_ERR_DTYPE): each
+       operand is scaled by 2^-e and written as six integer-valued bfloat16 slices on the grids
+       2^-6, 2^-14, ..., 2^-46 (residual below 2^-47 of its largest magnitude); the 21 slice
+       products of weight <= 5 run on the tensor cores in chunks of 192 K values whose sums of
+       weight <= 4 are exact, and are folded into one 64-bit integer per output element, scaled
+       and rounded once to FP64.  Merged contraction length K <= 98304.  Target: normwise relative
+       error <= 1e-12 against FP64 (an extension of the split form; the paper has no reduced
+       precision). */
+    COMET_PREC_EMU_F64 = 2
 } comet_precision_t;
 
 typedef enum {

@@ -17,10 +17,10 @@ import re
 import json
 
 from . import _lib
-from ._lib import CometError, F32, F64, PREC_NATIVE, PREC_SPLIT_BF16, ORDER_NATURAL, ORDER_PLANNED
+from ._lib import CometError, F32, F64, PREC_NATIVE, PREC_SPLIT_BF16, PREC_EMU_F64, ORDER_NATURAL, ORDER_PLANNED
 
 __all__ = ["Plan", "BatchedPlan", "transpose", "sync_status", "colmajor_empty", "CometError",
-           "lib", "version", "PREC_NATIVE", "PREC_SPLIT_BF16", "F32", "F64"]
+           "lib", "version", "PREC_NATIVE", "PREC_SPLIT_BF16", "PREC_EMU_F64", "F32", "F64"]
 
 
 def lib():
@@ -50,6 +50,8 @@ def _prec_code(p) -> int:
         return PREC_NATIVE
     if p in ("split_bf16", "split", PREC_SPLIT_BF16):
         return PREC_SPLIT_BF16
+    if p in ("emu_f64", "emulated_fp64", PREC_EMU_F64):
+        return PREC_EMU_F64
     raise ValueError(f"unknown precision {p}")
 
 

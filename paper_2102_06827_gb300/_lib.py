@@ -15,7 +15,7 @@ STATUS = {
     11: "COMET_ERR_INTERNAL", 12: "COMET_ERR_ARG",
 }
 F32, F64 = 0, 1
-PREC_NATIVE, PREC_SPLIT_BF16 = 0, 1
+PREC_NATIVE, PREC_SPLIT_BF16, PREC_EMU_F64 = 0, 1, 2
 ORDER_PLANNED, ORDER_NATURAL = 0, 1
 
 # every symbol include/comet.h declares (checked by the CPU test suite)

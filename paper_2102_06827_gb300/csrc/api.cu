@@ -41,8 +41,8 @@ int *device_status_word() {
 
 // ---- kernel timing ------------------------------------------------------------------------
 static const char *kKindNames[] = {"transpose", "scale_copy", "split_prepass", "gemm_split_bf16",
-                                   "gemm_f64", "batched_f64", "batched_split"};
-enum { PK_TRANSPOSE = 0, PK_SCALE, PK_PREPASS, PK_SPLIT, PK_F64, PK_BATCHED_F64, PK_BATCHED_SPLIT, PK_N };
+                                   "gemm_f64", "batched_f64", "batched_split", "gemm_emu_bf16x6"};
+enum { PK_TRANSPOSE = 0, PK_SCALE, PK_PREPASS, PK_SPLIT, PK_F64, PK_BATCHED_F64, PK_BATCHED_SPLIT, PK_EMU, PK_N };
 
 struct ProfRec {
     int kind;
@@ -185,22 +185,28 @@ static comet_status_t run_plan(const Plan &P, const void *const *inputs, void *o
                 e = launch_absmax(g.B, nb, es, sc_b, stream);
             }
             if (e != cudaSuccess) return cuda_status(e, "split pre-pass (scales)");
+            auto split = st.kernel == KK_GEMM_EMU ? launch_split6 : launch_split;
             {
                 ProfScope ps(PK_PREPASS, stream);
-                e = launch_split(xa, es, st.pre_a_vec, st.pre_a_vout, stream);
+                e = split(xa, es, st.pre_a_vec, st.pre_a_vout, stream);
             }
             if (e != cudaSuccess) return cuda_status(e, "split pre-pass (A)");
             {
                 ProfScope ps(PK_PREPASS, stream);
-                e = launch_split(xb, es, st.pre_b_vec, st.pre_b_vout, stream);
+                e = split(xb, es, st.pre_b_vec, st.pre_b_vout, stream);
             }
             if (e != cudaSuccess) return cuda_status(e, "split pre-pass (B)");
-            {
+            if (st.kernel == KK_GEMM_EMU) {
+                ProfScope ps(PK_EMU, stream);
+                e = launch_gemm_emu(g, w + st.ws_parts_a, w + st.ws_parts_b, st.kpad, sc_a, sc_b,
+                                    P.opts.debug_flags, stream, 0);
+                if (e != cudaSuccess) return cuda_status(e, "emulated FP64 gemm kernel");
+            } else {
                 ProfScope ps(PK_SPLIT, stream);
                 e = launch_gemm_split(g, w + st.ws_parts_a, w + st.ws_parts_b, st.kpad, sc_a, sc_b,
                                       P.opts.kc, es, P.opts.debug_flags, stream, 0);
+                if (e != cudaSuccess) return cuda_status(e, "split gemm kernel");
             }
-            if (e != cudaSuccess) return cuda_status(e, "split gemm kernel");
         }
     }
     return COMET_OK;

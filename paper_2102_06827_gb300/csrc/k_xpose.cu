@@ -9,6 +9,7 @@
 //   OP_MOVE   raw 4/8-byte words (bit-exact permutation, comet_transpose)
 //   OP_SCALE  out = alpha * in (+ beta * out)  (ta.copy with alpha)
 //   OP_SPLIT  x -> three bfloat16 planes hi, mid, lo (split pre-pass of the split-BF16 GEMM)
+//   OP_SPLIT6 FP64 x -> six integer-valued bfloat16 planes (pre-pass of the FP64 emulation)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -22,7 +23,7 @@
 
 namespace comet {
 
-enum { OP_MOVE = 0, OP_SCALE = 1, OP_SPLIT = 2 };
+enum { OP_MOVE = 0, OP_SCALE = 1, OP_SPLIT = 2, OP_SPLIT6 = 3 };
 constexpr int XT = 256;         // threads per CTA
 
 template <int N, typename T>
@@ -49,7 +50,7 @@ __device__ __forceinline__ void emit(const XposeParams &p, int64_t off, const T 
             for (int q = 0; q < VO; ++q) w.v[q] = (T)(p.alpha * (double)x[q]);
         }
         *reinterpret_cast<Vec<VO, T> *>(o) = w;
-    } else {
+    } else if constexpr (OP == OP_SPLIT) {
         Vec<VO, __nv_bfloat16> h, m, l;
 #pragma unroll
         for (int q = 0; q < VO; ++q) split3<T>(x[q], e, h.v[q], m.v[q], l.v[q]);
@@ -57,6 +58,19 @@ __device__ __forceinline__ void emit(const XposeParams &p, int64_t off, const T 
         *reinterpret_cast<Vec<VO, __nv_bfloat16> *>(o) = h;
         *reinterpret_cast<Vec<VO, __nv_bfloat16> *>(o + p.out_plane) = m;
         *reinterpret_cast<Vec<VO, __nv_bfloat16> *>(o + 2 * p.out_plane) = l;
+    } else {
+        static_assert(sizeof(T) == 8, "the six-way split is for FP64 operands");
+        Vec<VO, __nv_bfloat16> sl[6];
+#pragma unroll
+        for (int q = 0; q < VO; ++q) {
+            __nv_bfloat16 v[6];
+            split6((double)x[q], e, v);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) sl[k].v[q] = v[k];
+        }
+        __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(p.out) + off;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) *reinterpret_cast<Vec<VO, __nv_bfloat16> *>(o + k * p.out_plane) = sl[k];
     }
 }
 
@@ -122,7 +136,7 @@ __global__ void __launch_bounds__(XT, 8) xpose_tile_kernel(const XposeParams p) 
         out_row[r] = ro;
     }
     __syncthreads();
-    const int e = (OP == OP_SPLIT) ? scale_exponent<T>(p.scale_bits) : 0;
+    const int e = (OP == OP_SPLIT || OP == OP_SPLIT6) ? scale_exponent<T>(p.scale_bits) : 0;
     {   // loads: p.ll threads per row, each with a fixed u; batches of rows in flight together
         const uint32_t lanes = p.ll, rpp = p.rpp_l;
         const uint32_t r0 = fd_div(t, p.fd_ll);
@@ -193,7 +207,7 @@ __global__ void __launch_bounds__(XT, 6) xpose_copy_kernel(const XposeParams p) 
     }
     __syncthreads();
     const T *__restrict__ in = reinterpret_cast<const T *>(p.in);
-    const int e = (OP == OP_SPLIT) ? scale_exponent<T>(p.scale_bits) : 0;
+    const int e = (OP == OP_SPLIT || OP == OP_SPLIT6) ? scale_exponent<T>(p.scale_bits) : 0;
     constexpr int UB = VW * sizeof(T) >= 16 ? 4 : 8;
     const uint32_t lanes = p.ll;
     const uint32_t rpp = p.rpp_l;
@@ -236,7 +250,7 @@ __global__ void __launch_bounds__(XT) xpose_run_kernel(const XposeParams p) {
     const uint32_t nu = min(tu, p.u.total - u0);
     const int64_t su = p.u.s0[0], so = p.u.s1[0];
     const T *__restrict__ in = reinterpret_cast<const T *>(p.in);
-    const int e = (OP == OP_SPLIT) ? scale_exponent<T>(p.scale_bits) : 0;
+    const int e = (OP == OP_SPLIT || OP == OP_SPLIT6) ? scale_exponent<T>(p.scale_bits) : 0;
     constexpr int UB = VW * sizeof(T) >= 16 ? 4 : 8;
     const int64_t ri = (int64_t)u0 * su, ro = (int64_t)u0 * so;
     const uint32_t nvec = nu / VW * VW;
@@ -367,6 +381,12 @@ cudaError_t launch_scale(const XposeParams &p, int elem_bytes, int vi, int vo, c
 cudaError_t launch_split(const XposeParams &p, int elem_bytes, int vi, int vo, cudaStream_t s) {
     if (elem_bytes == 4) return launch_op<OP_SPLIT, float>(p, vi, vo, s);
     return launch_op<OP_SPLIT, double>(p, vi, vo, s);
+}
+
+// FP64-emulation pre-pass: six integer-valued bfloat16 planes of an FP64 operand
+cudaError_t launch_split6(const XposeParams &p, int elem_bytes, int vi, int vo, cudaStream_t s) {
+    if (elem_bytes != 8) return cudaErrorInvalidValue;
+    return launch_op<OP_SPLIT6, double>(p, vi, vo, s);
 }
 
 }  // namespace comet

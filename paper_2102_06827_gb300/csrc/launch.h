@@ -11,6 +11,7 @@ namespace comet {
 cudaError_t launch_move(const XposeParams &p, int elem_bytes, int vi, int vo, cudaStream_t s);
 cudaError_t launch_scale(const XposeParams &p, int elem_bytes, int vi, int vo, cudaStream_t s);
 cudaError_t launch_split(const XposeParams &p, int elem_bytes, int vi, int vo, cudaStream_t s);
+cudaError_t launch_split6(const XposeParams &p, int elem_bytes, int vi, int vo, cudaStream_t s);
 
 cudaError_t launch_gemm_f64(const GemmParams &p, int elem_bytes, bool a_kcontig, bool b_kcontig,
                             cudaStream_t s);
@@ -21,6 +22,10 @@ cudaError_t launch_absmax(const void *x, int64_t n, int elem_bytes, void *out_bi
 cudaError_t launch_gemm_split(const GemmParams &p, const void *parts_a, const void *parts_b,
                               int64_t kpad, const void *scale_a, const void *scale_b, int64_t kc,
                               int out_bytes, int debug_flags, cudaStream_t s, int max_ctas);
+
+cudaError_t launch_gemm_emu(const GemmParams &p, const void *parts_a, const void *parts_b, int64_t kpad,
+                            const void *scale_a, const void *scale_b, int debug_flags, cudaStream_t s,
+                            int max_ctas);
 
 // device status word of the current device (set by kernels whose waits run out)
 int *device_status_word();

@@ -377,9 +377,11 @@ void cost_form(const Plan &P, const std::vector<int> &lx, const std::vector<int>
     double run_c = (double)contiguous_run(f->M, sz, ext);
     f->eff_store = run_eff(std::min(run_c, 32.0) * es * 2);
     double t_store = M * N * es / (kHbmBytesPerS * f->eff_store);
-    if (kernel == KK_GEMM_SPLIT) {
-        // pre-passes: read the operand, write 3 bf16 planes in [rows][K] order; the transpose
-        // engine's efficiency follows from the runs on both sides
+    if (kernel == KK_GEMM_SPLIT || kernel == KK_GEMM_EMU) {
+        // pre-passes: read the operand, write 3 (split) or 6 (emulated FP64) bf16 planes in
+        // [rows][K] order; the transpose engine's efficiency follows from the runs on both sides
+        const bool emu = kernel == KK_GEMM_EMU;
+        const double plane_bytes = emu ? 12.0 : 6.0;
         auto pre = [&](const std::vector<int> &lop, const std::vector<int> &rows, double *eff_out) {
             std::vector<int64_t> e, si, so;
             auto st = label_strides(lop, ext);
@@ -396,13 +398,14 @@ void cost_form(const Plan &P, const std::vector<int> &lx, const std::vector<int>
             setup_xpose((int)e.size(), e.data(), si.data(), so.data(), (int)es, &xp, &vi, &vo, &eff);
             *eff_out = eff;
             double elems = (double)prod_ext(ext, lop);
-            return elems * (es + 6.0);
+            return elems * (es + plane_bytes);
         };
         double bx = pre(lm, f->M, &f->eff_a), by = pre(ln, f->N, &f->eff_b);
         f->pre_bytes = bx + by;
         double t_pre = bx / (kHbmBytesPerS * f->eff_a) + by / (kHbmBytesPerS * f->eff_b) + 2 * kLaunchS;
-        double waste = (std::ceil(M / 128) * 128 * std::ceil(N / 256) * 256) / (M * N);
-        double t_mma = 6.0 * 2.0 * M * N * K * waste / kBf16FlopsPerS;
+        const double bn = emu ? 80.0 : 256.0, products = emu ? 21.0 : 6.0;
+        double waste = (std::ceil(M / 128) * 128 * std::ceil(N / bn) * bn) / (M * N);
+        double t_mma = products * 2.0 * M * N * K * waste / kBf16FlopsPerS;
         // the epilogue's stores overlap the next tile's main loop, but scattered stores still
         // cost DRAM bandwidth: charge a share of them beyond the overlap
         f->cost = t_pre + std::max(t_mma, t_store) + 0.25 * t_store + kLaunchS;
@@ -438,7 +441,8 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
     comet_plan_opts_t opts;
     comet_plan_opts_default(&opts);
     if (opts_in) opts = *opts_in;
-    if (opts.precision != COMET_PREC_NATIVE && opts.precision != COMET_PREC_SPLIT_BF16) {
+    if (opts.precision != COMET_PREC_NATIVE && opts.precision != COMET_PREC_SPLIT_BF16 &&
+        opts.precision != COMET_PREC_EMU_F64) {
         *err = "unknown precision"; return COMET_ERR_ARG;
     }
     if (opts.kc < 0 || opts.timeout_ms < 0) { *err = "negative kc or timeout"; return COMET_ERR_ARG; }
@@ -481,6 +485,9 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
         if (dtypes[i] != dtypes[0]) { *err = "operands of different dtypes"; return COMET_ERR_DTYPE; }
     }
     P->dtype = dtypes[0];
+    if (opts.precision == COMET_PREC_EMU_F64 && P->dtype != COMET_F64) {
+        *err = "the emulated FP64 precision takes FP64 operands"; return COMET_ERR_DTYPE;
+    }
     // labelled tensors as id lists; structural checks (Section 2: contraction vs free labels)
     std::vector<std::vector<int>> in_labs;
     for (auto &t : E.ins) {
@@ -630,7 +637,8 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
     }
 
     // ---- TTGT form of every binary step (Section 6) ----
-    int kernel = opts.precision == COMET_PREC_SPLIT_BF16 ? KK_GEMM_SPLIT : KK_GEMM_F64;
+    int kernel = opts.precision == COMET_PREC_SPLIT_BF16 ? KK_GEMM_SPLIT
+                 : opts.precision == COMET_PREC_EMU_F64 ? KK_GEMM_EMU : KK_GEMM_F64;
     for (auto &st : P->steps) {
         if (st.kernel == KK_COPY) continue;
         st.kernel = kernel;
@@ -644,6 +652,10 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
         if (prod_ext(P->extent, I) >= (1ll << 31) || prod_ext(P->extent, J) >= (1ll << 31) ||
             prod_ext(P->extent, K) >= (1ll << 31)) {
             *err = "a merged GEMM dimension reaches 2^31"; return COMET_ERR_UNSUPPORTED;
+        }
+        if (kernel == KK_GEMM_EMU && prod_ext(P->extent, K) > 98304) {
+            *err = "the emulated FP64 precision takes a merged contraction length of at most 98304";
+            return COMET_ERR_UNSUPPORTED;
         }
         std::vector<Form> forms;
         for (int swap = 0; swap < 2; ++swap) {
@@ -682,17 +694,18 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
         if (s.kind == SLOT_INTER) { s.ws_off = off; off = align(off + (size_t)s.elems * es); }
     size_t parts_base = off, parts_max = 0;
     for (auto &st : P->steps) {
-        if (st.kernel != KK_GEMM_SPLIT) continue;
+        if (st.kernel != KK_GEMM_SPLIT && st.kernel != KK_GEMM_EMU) continue;
         int64_t Kx = prod_ext(P->extent, st.form.K);
         st.kpad = (Kx + 7) / 8 * 8;
         int64_t rows_a = prod_ext(P->extent, st.form.M), rows_b = prod_ext(P->extent, st.form.N);
-        size_t ba = align((size_t)3 * rows_a * st.kpad * 2), bb = align((size_t)3 * rows_b * st.kpad * 2);
+        const size_t planes = st.kernel == KK_GEMM_EMU ? 6 : 3;
+        size_t ba = align(planes * rows_a * st.kpad * 2), bb = align(planes * rows_b * st.kpad * 2);
         st.ws_parts_a = parts_base;
         st.ws_parts_b = parts_base + ba;
         parts_max = std::max(parts_max, ba + bb);
     }
     bool any_split = false;
-    for (auto &st : P->steps) any_split |= st.kernel == KK_GEMM_SPLIT;
+    for (auto &st : P->steps) any_split |= st.kernel == KK_GEMM_SPLIT || st.kernel == KK_GEMM_EMU;
     for (auto &st : P->steps) st.ws_scales = parts_base + parts_max;
     P->workspace = parts_base + parts_max + (any_split ? 256 : 0);
 
@@ -727,8 +740,8 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
         g.N = (uint32_t)prod_ext(P->extent, st.form.N);
         g.K = (uint32_t)prod_ext(P->extent, st.form.K);
         g.ma.total = g.M; g.nb.total = g.N; g.k.total = g.K;
-        if (st.kernel == KK_GEMM_SPLIT) {
-            // pre-pass of each operand into [3][rows][kpad] bf16 planes (K order, then rows)
+        if (st.kernel == KK_GEMM_SPLIT || st.kernel == KK_GEMM_EMU) {
+            // pre-pass of each operand into [planes][rows][kpad] bf16 planes (K order, then rows)
             auto pre = [&](const Slot &so_, const std::vector<int> &rows, XposeParams *xp, int *vec_in, int *vec_out) {
                 auto st_ = label_strides(so_.labels, P->extent);
                 std::map<int, int64_t> sout;
@@ -781,13 +794,15 @@ std::string describe_plan(const Plan &P) {
         return s + "]";
     };
     o << "{\"expr\":\"" << P.expr << "\",\"dtype\":\"" << (P.dtype == COMET_F32 ? "f32" : "f64")
-      << "\",\"precision\":\"" << (P.opts.precision == COMET_PREC_SPLIT_BF16 ? "split_bf16" : "native")
+      << "\",\"precision\":\"" << (P.opts.precision == COMET_PREC_SPLIT_BF16 ? "split_bf16"
+                                       : P.opts.precision == COMET_PREC_EMU_F64 ? "emu_f64" : "native")
       << "\",\"order\":\"" << P.tree << "\",\"flops\":" << P.flops << ",\"flops_natural\":" << P.flops_natural
       << ",\"workspace\":" << P.workspace << ",\"steps\":[";
     for (size_t i = 0; i < P.steps.size(); ++i) {
         const Step &s = P.steps[i];
         if (i) o << ",";
-        o << "{\"kernel\":\"" << (s.kernel == KK_COPY ? "copy" : s.kernel == KK_GEMM_SPLIT ? "gemm_split_bf16" : "gemm_f64")
+        o << "{\"kernel\":\"" << (s.kernel == KK_COPY ? "copy" : s.kernel == KK_GEMM_SPLIT ? "gemm_split_bf16"
+                                    : s.kernel == KK_GEMM_EMU ? "gemm_emu_bf16x6" : "gemm_f64")
           << "\",\"a\":" << s.a << ",\"b\":" << s.b << ",\"c\":" << s.c
           << ",\"a_labels\":" << names(P.slots[s.a].labels);
         if (s.b >= 0) o << ",\"b_labels\":" << names(P.slots[s.b].labels);

@@ -1,4 +1,4 @@
-// Fixed-point three-way bfloat16 split shared by the split pre-pass and the batched kernels.
+// Fixed-point bfloat16 splits shared by the split pre-passes and the batched kernels.
 #pragma once
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -35,6 +35,33 @@ __device__ __forceinline__ void split3(T x, int e, __nv_bfloat16 &h, __nv_bfloat
         m = __float2bfloat16_rn((float)fm);
         l = __float2bfloat16_rn((float)fl);
     }
+}
+
+// Fixed-point six-way split of an FP64 value (the FP64-emulation pre-pass): x' = x 2^-e
+// (|x'| < 2) is rounded to the nearest multiple of 2^-46, X = round(x' 2^46) with |X| <= 2^47,
+// and X is written in balanced base 256: X = sum_k s_k 256^(5-k), s_1..s_5 in [-128, 127] and
+// |s_0| <= 128, so x' = sum_k s_k 2^-(6+8k) up to 2^-47 and every slice is an integer that
+// bfloat16 holds exactly (stored as the integer itself).  Integer arithmetic on the bits only:
+// the FP64 pipe of the GPU is not used.
+__device__ __forceinline__ void split6(double x, int e, __nv_bfloat16 (&s)[6]) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((bits >> 52) & 0x7FF);
+    unsigned long long m = bits & ((1ull << 52) - 1);
+    if (E != 0) m |= 1ull << 52;
+    // x' 2^46 = m 2^(max(E,1) - 1075 - e + 46): shift right by sh with rounding to nearest
+    const int sh = 1029 + e - (E != 0 ? E : 1);
+    long long X;
+    if (sh <= 0) X = (long long)(m << (-sh < 63 ? -sh : 63));
+    else if (sh < 63) X = (long long)((m + (1ull << (sh - 1))) >> sh);
+    else X = 0;
+    if (bits >> 63) X = -X;
+#pragma unroll
+    for (int k = 5; k >= 1; --k) {
+        const int d = (int)(signed char)(X & 0xFF);
+        s[k] = __int2bfloat16_rn(d);
+        X = (X - d) >> 8;
+    }
+    s[0] = __int2bfloat16_rn((int)X);
 }
 
 // exponent e with max|x| in [2^e, 2^(e+1)) from the abs-max bits; 0 for an all-zero (or

@@ -114,6 +114,26 @@ def test_flops_and_workspace():
     assert ps.workspace_bytes >= 3 * 2 * kpad * (576 + 576)
 
 
+def test_emulated_fp64_plans():
+    ext = dict(a=24, b=24, c=24, d=24, e=24)
+    p = plan("C[a,b,c,d] = A[a,e,b] * B[e,d,c]", ext, "f64", precision="emu_f64")
+    assert p.info["precision"] == "emu_f64"
+    assert p.info["steps"][0]["kernel"] == "gemm_emu_bf16x6"
+    kpad = 24 + (-24) % 8
+    assert p.workspace_bytes >= 6 * 2 * kpad * (576 + 576)
+    # FP64 storage only; merged contraction length up to 98304; not a batched precision
+    with pytest.raises(comet.CometError) as e:
+        plan("C[i,j] = A[i,k] * B[k,j]", dict(i=4, j=4, k=4), "f32", precision="emu_f64")
+    assert e.value.name == "COMET_ERR_DTYPE"
+    plan("C[i,j] = A[i,k] * B[k,j]", dict(i=4, j=4, k=98304), "f64", precision="emu_f64")
+    with pytest.raises(comet.CometError) as e:
+        plan("C[i,j] = A[i,k] * B[k,j]", dict(i=4, j=4, k=98305), "f64", precision="emu_f64")
+    assert e.value.name == "COMET_ERR_UNSUPPORTED"
+    with pytest.raises(comet.CometError) as e:
+        comet.BatchedPlan("C[a,b] = A[a,k] * B[k,b]", ["a", "b", "k"], [[2, 2, 2]], "f64", precision="emu_f64")
+    assert e.value.name == "COMET_ERR_UNSUPPORTED"
+
+
 # ---- multi-operand order vs an explicit enumeration of every contraction sequence ----------
 
 def _labels_outside(sub, ops, out):
