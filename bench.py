@@ -51,7 +51,7 @@ def args_parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-case", default=None, choices=["split", "f64", "transpose"],
+    ap.add_argument("--profile-case", default=None, choices=["split", "f64", "emu", "transpose"],
                     help="run one warm-up and one timed launch of a smaller case (for ncu) and exit")
     ap.add_argument("--pc-extents", default="64,128,128,256", help="transpose profile case extents")
     ap.add_argument("--pc-perm", default="3,1,0,2", help="transpose profile case permutation")
@@ -375,11 +375,11 @@ def run_profile_case(case: str, a=None) -> int:
         comet.sync_status()
         print(json.dumps({"case": case, "extents": ext, "perm": perm, "bytes": 2 * x.element_size() * n}))
         return 0
-    o, v = (48, 160) if case == "split" else (16, 48)
+    o, v = (48, 160) if case in ("split", "emu") else (16, 48)
     ext = dict(i=o, j=o, k=o, a=v, b=v, c=v)
     n = o * v * v * o
     dt = torch.float32 if case == "split" else torch.float64
-    plan = comet.Plan(EXPR, ext, dt, precision="split_bf16" if case == "split" else "native")
+    plan = comet.Plan(EXPR, ext, dt, precision={"split": "split_bf16", "emu": "emu_f64"}.get(case, "native"))
     A = synth.torch_uniform(1, 0, n, dev, dtype=dt, scale=1.0 / math.sqrt(o * v))
     B = synth.torch_uniform(2, 0, n, dev, dtype=dt, scale=1.0 / math.sqrt(o * v))
     C = torch.empty(n, dtype=dt, device=dev)

@@ -16,7 +16,8 @@
 // rounding; group 5 (2^-40 of the result) is inexact and rounded.  After every chunk the
 // epilogue converts the groups to integers and folds them into one int64 per output element in
 // units of 2^-44:  I += G0 2^32 + G1 2^24 + G2 2^16 + G3 2^8 + G4 + rint(G5 2^-8)  -- exact except
-// the last term.  The result is alpha 2^(eA+eB-44) I, rounded once to FP64.
+// the last term (G4 + rn(G5 2^-8) is formed exactly in FP32 first).  The result is
+// alpha 2^(eA+eB-44) I, rounded once to FP64.
 //
 // GB300 form (one persistent CTA per SM, 320 threads), as the split kernel:
 //   warp 0      TMA producer: one 3-D load per operand and stage brings all six planes of a
@@ -232,10 +233,10 @@ __global__ void __launch_bounds__(emu::THREADS, 1)
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) { if (lane == 0) fail(); dead = true; continue; }
                 tc_fence_after();
+                // groups 0..3: exact integers, one conversion each, shifted into 2^-44 units
 #pragma unroll 1
-                for (int w = 0; w < GROUPS; ++w) {
-                    const long long mult = w < GROUPS - 1 ? (1ll << (8 * (4 - w))) : 0ll;
-                    // the group's 40 columns in two batches of loads (24 + 16), one wait each
+                for (int w = 0; w < 4; ++w) {
+                    const int sh = 8 * (4 - w);
 #pragma unroll
                     for (int part = 0; part < 2; ++part) {
                         const int c0 = part == 0 ? 0 : 3, nc = part == 0 ? 3 : 2;
@@ -245,19 +246,36 @@ __global__ void __launch_bounds__(emu::THREADS, 1)
                             tmem_ld8(tmem_base + lane_base + w * BG + half * HALF + (c0 + c8) * 8,
                                      *reinterpret_cast<uint32_t(*)[8]>(&r[c8 * 8]));
                         tmem_ld_wait();
-                        if (w == GROUPS - 1 && part == 1) {
-                            // every group is in registers: the MMAs of the next chunk may start
-                            tc_fence_before();
-                            __syncwarp();
-                            if (lane == 0) mbar_arrive(tempty);
-                        }
 #pragma unroll
-                        for (int j = 0; j < nc * 8; ++j) {
-                            const float v = __uint_as_float(r[j]);
-                            // groups 0..4 hold exact integers; group 5 is rounded to 2^-44 units
-                            I[c0 * 8 + j] += mult ? (long long)__float2int_rn(v) * mult
-                                                  : (long long)__float2int_rn(v * (1.0f / 256.0f));
-                        }
+                        for (int j = 0; j < nc * 8; ++j)
+                            I[c0 * 8 + j] += (long long)__float2int_rn(__uint_as_float(r[j])) * (1ll << sh);
+                    }
+                }
+                // groups 4 and 5 merged exactly in FP32: G4 + rn(G5 2^-8) stays an integer below
+                // 2^24 (rn by the 1.5 * 2^23 addition, valid below 2^22), then one conversion
+#pragma unroll
+                for (int part = 0; part < 2; ++part) {
+                    const int c0 = part == 0 ? 0 : 3, nc = part == 0 ? 3 : 2;
+                    uint32_t r4[24], r5[24];
+#pragma unroll
+                    for (int c8 = 0; c8 < nc; ++c8) {
+                        tmem_ld8(tmem_base + lane_base + 4 * BG + half * HALF + (c0 + c8) * 8,
+                                 *reinterpret_cast<uint32_t(*)[8]>(&r4[c8 * 8]));
+                        tmem_ld8(tmem_base + lane_base + 5 * BG + half * HALF + (c0 + c8) * 8,
+                                 *reinterpret_cast<uint32_t(*)[8]>(&r5[c8 * 8]));
+                    }
+                    tmem_ld_wait();
+                    if (part == 1) {
+                        // every group is in registers: the MMAs of the next chunk may start
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(tempty);
+                    }
+                    const float magic = 12582912.0f;   // 1.5 * 2^23
+#pragma unroll
+                    for (int j = 0; j < nc * 8; ++j) {
+                        const float g5 = __fsub_rn(__fadd_rn(__uint_as_float(r5[j]) * (1.0f / 256.0f), magic), magic);
+                        I[c0 * 8 + j] += (long long)__float2int_rn(__fadd_rn(__uint_as_float(r4[j]), g5));
                     }
                 }
             }
