@@ -51,11 +51,12 @@ def args_parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-case", default=None, choices=["split", "f64", "emu", "transpose"],
+    ap.add_argument("--profile-case", default=None, choices=["split", "f64", "emu", "transpose", "triples"],
                     help="run one warm-up and one timed launch of a smaller case (for ncu) and exit")
     ap.add_argument("--pc-extents", default="64,128,128,256", help="transpose profile case extents")
     ap.add_argument("--pc-perm", default="3,1,0,2", help="transpose profile case permutation")
     ap.add_argument("--pc-dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--pc-tile", type=int, default=-1, help="batched tile configuration of --profile-case triples")
     ap.add_argument("--ablation", action="store_true",
                     help="Table 1 natural vs planned order, and every TTGT form vs the chosen one")
     ap.add_argument("--workload", default="ccsd", choices=["ccsd", "triples", "small"],
@@ -364,6 +365,21 @@ def run_profile_case(case: str, a=None) -> int:
     import paper_2102_06827_gb300 as comet
     import synth
     dev = torch.device("cuda", 0)
+    if case == "triples":   # 512 of the 4096 triples blocks (same extent generator), split, reduce mode
+        import numpy as np
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        from batched_data import EXPR as TEXPR, LABELS, Blocks
+        ext = synth.triples_blocks(512)
+        blocks = Blocks(ext, np.float32)
+        plan = comet.BatchedPlan(TEXPR, LABELS, ext, "f32", precision="split_bf16", tile=a.pc_tile)
+        ws = plan.workspace()
+        plan.prepare(ws)
+        res = torch.zeros(2 * blocks.n, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            plan.contract(blocks.ptrs, res, ws, mode=0, key=1)
+        comet.sync_status()
+        print(json.dumps({"case": case, "blocks": 512, "flops": plan.flops, "tile": plan.describe()["tile"]}))
+        return 0
     if case == "transpose":
         ext = tuple(int(e) for e in a.pc_extents.split(","))
         perm = tuple(int(q) for q in a.pc_perm.split(","))

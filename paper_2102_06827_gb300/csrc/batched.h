@@ -14,7 +14,10 @@ struct BlockDesc {
     uint32_t M, N, K;
     uint32_t index;              // the block's position in the caller's tables
     int64_t a_elems, b_elems;
-    uint32_t pad[2];
+    int64_t a_parts, b_parts;    // split path: workspace offsets of the operands' bfloat16 planes,
+                                 // [3][rows][kpad] each (rows = M for A, N for B)
+    uint32_t kpad;               // K rounded up to a multiple of 32
+    uint32_t pad;
 };
 
 constexpr int kBatchedCfgF64 = 4;     // tile configurations of the FP64 path
@@ -32,6 +35,7 @@ struct BatchedParams {
     unsigned int *counter;       // work counter (zeroed by the launch sequence)
     const int *exps;             // split path: scale exponents of the M and N operands, 2 per block
     double alpha;
+    char *ws;                    // workspace base (the split planes live at desc offsets)
 };
 
 std::string describe_batched(const Plan &p);

@@ -10,9 +10,10 @@
 //
 // Two arithmetic paths:
 //   FP64   f64 tensor-core MMA (mma.sync m8n8k4), FP64 accumulation
-//   split  the fixed-point three-way bfloat16 split of each operand (split.cuh) done in the
-//          kernel, six part products on the tensor cores (mma.sync m16n8k16 bf16, FP32
-//          accumulation); the hh products go to their own accumulator, exact for K <= 1024
+//   split  the fixed-point three-way bfloat16 split of each operand (split.cuh), written once
+//          per block by a pre-pass into GEMM-ready planes; six part products on the tensor
+//          cores (mma.sync m16n8k16 bf16, FP32 accumulation) over tiles copied with cp.async;
+//          the hh products go to their own accumulator, exact for K <= 1024
 // The output T of a block is either consumed in the epilogue (reduce mode: s_b = sum T*W and
 // q_b = sum T^2 with a hashed weight W per element, one pair of atomic adds per tile) or stored
 // (store mode).
@@ -252,13 +253,73 @@ __global__ void __launch_bounds__(BT) batched_f64_kernel(const BatchedParams P) 
 }
 
 // ---- split path --------------------------------------------------------------------------------
-template <int BM, int BN, bool AK, bool BKC, typename TIn>
-__global__ void __launch_bounds__(BT) batched_split_kernel(const BatchedParams P) {
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_b() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_b() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Split pre-pass of the batched split path: CTA c writes operand c%2 of block c/2 as three
+// bfloat16 planes [3][rows][kpad] (rows in the merged M or N order, K fastest, zero beyond K),
+// scaled by the block's exponent.  A warp takes 32 rows at a time: each lane resolves one row's
+// source offset, the warp then walks the rows with the lanes along K.
+template <typename TIn>
+__global__ void __launch_bounds__(256) batched_presplit_kernel(const BatchedParams P) {
+    __shared__ int64_t k_off[1024];
+    const BlockDesc &d = P.desc[blockIdx.x >> 1];
+    const int op = blockIdx.x & 1;
+    const Radix &rr = op ? d.nb : d.ma;
+    const uint32_t rows = op ? d.N : d.M, K = d.K, kpad = d.kpad;
+    const TIn *x = reinterpret_cast<const TIn *>(P.inputs[2 * d.index + (op ^ P.swap)]);
+    const int e = P.exps[2 * d.index + op];
+    __nv_bfloat16 *planes = reinterpret_cast<__nv_bfloat16 *>(P.ws + (op ? d.b_parts : d.a_parts));
+    const int64_t plane = (int64_t)rows * kpad;
+    for (uint32_t k = threadIdx.x; k < kpad; k += 256) {
+        int64_t o0 = 0, o1 = 0;
+        if (k < K) radix_offsets(d.k, k, o0, o1);
+        k_off[k] = op ? o1 : o0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t r0 = warp * 32; r0 < rows; r0 += 8 * 32) {
+        int64_t my = 0, o1 = 0;
+        if (r0 + lane < rows) radix_offsets(rr, r0 + lane, my, o1);
+        const uint32_t nr = min(32u, rows - r0);
+        for (uint32_t j = 0; j < nr; ++j) {
+            const int64_t ro = __shfl_sync(0xffffffffu, my, j);
+            const int64_t base = (int64_t)(r0 + j) * kpad;
+            for (uint32_t k = lane; k < kpad; k += 32) {
+                const TIn v = k < K ? x[ro + k_off[k]] : (TIn)0;
+                __nv_bfloat16 h, m, l;
+                split3<TIn>(v, e, h, m, l);
+                planes[base + k] = h;
+                planes[plane + base + k] = m;
+                planes[2 * plane + base + k] = l;
+            }
+        }
+    }
+}
+
+// Split path main kernel: the operands arrive pre-split (batched_presplit_kernel), so a tile is
+// three plane slabs of 32 K values copied with 16-byte cp.async; the M tiles of a strip are
+// double-buffered (the copies of tile m+1 run under the MMAs and the epilogue of tile m).
+template <int BM, int BN>
+struct SplitSmem {
+    static constexpr int KP = KCH + 8;                       // 80-byte rows: conflict-free fragments
+    static constexpr int A_TILE = 3 * BM * KP;               // bf16 elements
+    static constexpr int B_TILE = 3 * BN * KP;
+    static constexpr size_t BYTES = (size_t)(2 * A_TILE + B_TILE) * 2;
+};
+
+template <int BM, int BN, typename TIn>
+__global__ void __launch_bounds__(BT, BM * BN <= 4096 ? 4 : 2) batched_split_kernel(const BatchedParams P) {
     constexpr int MI = BM / 32, NJ = BN / 16;   // m16 / n8 MMA tiles per warp
-    constexpr int KP = KCH + 8;                 // padded row (80 bytes): conflict-free fragments
-    __shared__ __align__(16) __nv_bfloat16 As[3][BM][KP];
-    __shared__ __align__(16) __nv_bfloat16 Bs[3][BN][KP];
-    __shared__ int64_t a_row[BM], o_row[BM], b_col[BN], o_col[BN], a_k[KCH], b_k[KCH];
+    using SM = SplitSmem<BM, BN>;
+    constexpr int KP = SM::KP;
+    extern __shared__ __align__(16) __nv_bfloat16 dsm[];
+    __nv_bfloat16 *As0 = dsm, *As1 = dsm + SM::A_TILE, *Bs = dsm + 2 * SM::A_TILE;
+    __shared__ int64_t o_row[2][BM], o_col[BN];
     __shared__ __align__(16) BlockDesc sd;
     __shared__ double red[2 * BT / 32];
     __shared__ uint32_t s_item, s_pos;
@@ -268,45 +329,64 @@ __global__ void __launch_bounds__(BT) batched_split_kernel(const BatchedParams P
     while (next_item(P, item, pos, &s_item, &s_pos)) {
         copy_desc(P.desc + pos, &sd);
         __syncthreads();
-        const uint32_t M = sd.M, N = sd.N, K = sd.K, idx = sd.index;
+        const uint32_t M = sd.M, N = sd.N, K = sd.K, idx = sd.index, kpad = sd.kpad;
         const uint32_t mtiles = (M + BM - 1) / BM;
         const uint32_t n0 = (item - P.prefix[pos]) * BN;
         const int ea = P.exps[2 * idx], eb = P.exps[2 * idx + 1];
         const bool bres = K <= (uint32_t)KCH;
+        const __nv_bfloat16 *pa = reinterpret_cast<const __nv_bfloat16 *>(P.ws + sd.a_parts);
+        const __nv_bfloat16 *pb = reinterpret_cast<const __nv_bfloat16 *>(P.ws + sd.b_parts);
+        const int64_t plane_a = (int64_t)M * kpad, plane_b = (int64_t)N * kpad;
         for (int i = t; i < BN; i += BT) {
             int64_t o0 = 0, o1 = 0;
             if (n0 + i < N) radix_offsets(sd.nb, n0 + i, o0, o1);
-            b_col[i] = o0; o_col[i] = o1;
+            o_col[i] = o1;
         }
-        if (t < KCH) {
-            int64_t o0 = 0, o1 = 0;
-            if ((uint32_t)t < K) radix_offsets(sd.k, t, o0, o1);
-            a_k[t] = o0; b_k[t] = o1;
-        }
-        const TIn *A = reinterpret_cast<const TIn *>(P.inputs[2 * idx + P.swap]);
-        const TIn *B = reinterpret_cast<const TIn *>(P.inputs[2 * idx + 1 - P.swap]);
-        auto load_b = [&](uint32_t k0) {
-            for (int e = t; e < BN * KCH; e += BT) {
-                int n, k;
-                if (BKC) { k = e % KCH; n = e / KCH; } else { n = e % BN; k = e / BN; }
-                const TIn x = (n0 + n < N && k0 + k < K) ? B[b_col[n] + b_k[k]] : (TIn)0;
-                split3<TIn>(x, eb, Bs[0][n][k], Bs[1][n][k], Bs[2][n][k]);
+        // a [3][R][32] slab of plane rows r0.. at K offset k0 into shared memory (rows beyond
+        // `rows` are zero-filled); 4 copies of 16 bytes per row and plane
+        auto slab = [&](__nv_bfloat16 *dst, const __nv_bfloat16 *src, int64_t plane, uint32_t rows, uint32_t r0,
+                        uint32_t k0, int R) {
+            for (int c = t; c < 3 * R * 4; c += BT) {
+                const int pl = c / (R * 4), rem = c - pl * R * 4, r = rem >> 2, q = rem & 3;
+                const bool ok = r0 + r < rows;
+                const __nv_bfloat16 *s = src + pl * plane + (ok ? (int64_t)(r0 + r) * kpad + k0 + q * 8 : 0);
+                cp_async16((uint32_t)__cvta_generic_to_shared(dst + (pl * R + r) * KP + q * 8), s, ok ? 16u : 0u);
             }
         };
-        __syncthreads();
-        if (bres) load_b(0);
+        auto rows_of = [&](int buf, uint32_t m0) {
+            for (int i = t; i < BM; i += BT) {
+                int64_t o0 = 0, o1 = 0;
+                if (m0 + i < M) radix_offsets(sd.ma, m0 + i, o0, o1);
+                o_row[buf][i] = o1;
+            }
+        };
+        if (bres) {
+            slab(Bs, pb, plane_b, N, n0, 0, BN);
+            slab(As0, pa, plane_a, M, 0, 0, BM);
+            cp_async_commit_b();
+            rows_of(0, 0);
+        }
         const float scale = (float)ldexp(P.alpha, ea + eb);
         float s = 0.0f, q = 0.0f;
         TIn *out = P.mode == 1 ? reinterpret_cast<TIn *const *>(P.result)[idx] : nullptr;
         for (uint32_t mt = 0; mt < mtiles; ++mt) {
             const uint32_t m0 = mt * BM;
-            __syncthreads();
-            for (int i = t; i < BM; i += BT) {
-                int64_t o0 = 0, o1 = 0;
-                if (m0 + i < M) radix_offsets(sd.ma, m0 + i, o0, o1);
-                a_row[i] = o0; o_row[i] = o1;
+            const int buf = mt & 1;
+            const __nv_bfloat16 *As = buf ? As1 : As0;
+            if (bres) {
+                if (mt + 1 < mtiles) {   // prefetch the next M tile into the other buffer
+                    slab(buf ? As0 : As1, pa, plane_a, M, m0 + BM, 0, BM);
+                    cp_async_commit_b();
+                    rows_of(buf ^ 1, m0 + BM);
+                    cp_async_wait_b<1>();
+                } else {
+                    cp_async_wait_b<0>();
+                }
+                __syncthreads();
+            } else {
+                __syncthreads();
+                rows_of(buf, m0);
             }
-            __syncthreads();
             float p0[MI][NJ][4], p1[MI][NJ][4];
 #pragma unroll
             for (int i = 0; i < MI; ++i)
@@ -315,23 +395,14 @@ __global__ void __launch_bounds__(BT) batched_split_kernel(const BatchedParams P
 #pragma unroll
                     for (int c = 0; c < 4; ++c) p0[i][j][c] = p1[i][j][c] = 0.0f;
             for (uint32_t k0 = 0; k0 < K; k0 += KCH) {
-                if (!bres) {
+                if (!bres) {   // long K: one synchronous slab pair per chunk
                     __syncthreads();
-                    if (t < KCH) {
-                        int64_t o0 = 0, o1 = 0;
-                        if (k0 + t < K) radix_offsets(sd.k, k0 + t, o0, o1);
-                        a_k[t] = o0; b_k[t] = o1;
-                    }
+                    slab(Bs, pb, plane_b, N, n0, k0, BN);
+                    slab(const_cast<__nv_bfloat16 *>(As), pa, plane_a, M, m0, k0, BM);
+                    cp_async_commit_b();
+                    cp_async_wait_b<0>();
                     __syncthreads();
-                    load_b(k0);
                 }
-                for (int e = t; e < BM * KCH; e += BT) {
-                    int m, k;
-                    if (AK) { k = e % KCH; m = e / KCH; } else { m = e % BM; k = e / BM; }
-                    const TIn x = (m0 + m < M && k0 + k < K) ? A[a_row[m] + a_k[k]] : (TIn)0;
-                    split3<TIn>(x, ea, As[0][m][k], As[1][m][k], As[2][m][k]);
-                }
-                __syncthreads();
                 const int kmax = (int)min((uint32_t)KCH, K - k0);
 #pragma unroll
                 for (int ks = 0; ks < KCH / 16; ++ks) {
@@ -343,17 +414,19 @@ __global__ void __launch_bounds__(BT) batched_split_kernel(const BatchedParams P
                         for (int i = 0; i < MI; ++i) {
                             const int r = wm * (BM / 2) + i * 16 + g;
                             const int c = ks * 16 + 2 * tq;
-                            af[pl][i][0] = *reinterpret_cast<const uint32_t *>(&As[pl][r][c]);
-                            af[pl][i][1] = *reinterpret_cast<const uint32_t *>(&As[pl][r + 8][c]);
-                            af[pl][i][2] = *reinterpret_cast<const uint32_t *>(&As[pl][r][c + 8]);
-                            af[pl][i][3] = *reinterpret_cast<const uint32_t *>(&As[pl][r + 8][c + 8]);
+                            const __nv_bfloat16 *ap = As + (pl * BM + r) * KP + c;
+                            af[pl][i][0] = *reinterpret_cast<const uint32_t *>(ap);
+                            af[pl][i][1] = *reinterpret_cast<const uint32_t *>(ap + 8 * KP);
+                            af[pl][i][2] = *reinterpret_cast<const uint32_t *>(ap + 8);
+                            af[pl][i][3] = *reinterpret_cast<const uint32_t *>(ap + 8 * KP + 8);
                         }
 #pragma unroll
                         for (int j = 0; j < NJ; ++j) {
                             const int r = wn * (BN / 2) + j * 8 + g;
                             const int c = ks * 16 + 2 * tq;
-                            bf[pl][j][0] = *reinterpret_cast<const uint32_t *>(&Bs[pl][r][c]);
-                            bf[pl][j][1] = *reinterpret_cast<const uint32_t *>(&Bs[pl][r][c + 8]);
+                            const __nv_bfloat16 *bp = Bs + (pl * BN + r) * KP + c;
+                            bf[pl][j][0] = *reinterpret_cast<const uint32_t *>(bp);
+                            bf[pl][j][1] = *reinterpret_cast<const uint32_t *>(bp + 8);
                         }
                     }
 #pragma unroll
@@ -369,6 +442,7 @@ __global__ void __launch_bounds__(BT) batched_split_kernel(const BatchedParams P
                         }
                 }
             }
+            const int64_t *orow = o_row[buf];
 #pragma unroll
             for (int i = 0; i < MI; ++i)
 #pragma unroll
@@ -379,7 +453,7 @@ __global__ void __launch_bounds__(BT) batched_split_kernel(const BatchedParams P
                         const int nl = wn * (BN / 2) + j * 8 + 2 * tq + (c & 1);
                         if (m0 + ml < M && n0 + nl < N) {
                             const float T = scale * (p0[i][j][c] + p1[i][j][c]);
-                            const int64_t lin = o_row[ml] + o_col[nl];
+                            const int64_t lin = orow[ml] + o_col[nl];
                             if (P.mode == 0) {
                                 s = fmaf(T, tri_weight(P.key, idx, (uint32_t)lin), s);
                                 q = fmaf(T, T, q);
@@ -388,6 +462,7 @@ __global__ void __launch_bounds__(BT) batched_split_kernel(const BatchedParams P
                             }
                         }
                     }
+            if (bres) __syncthreads();   // the buffer of this tile is refilled two tiles later
         }
         if (P.mode == 0) reduce_add((double)s, (double)q, red, reinterpret_cast<double *>(P.result), idx);
         __syncthreads();
@@ -433,17 +508,19 @@ static TileCfg cfg_of(const Plan &P, int c) {
 }
 
 // workspace layout: [counter 256 B][exps 8*n][prefix n_cfg*(n+1)*4][descs n*sizeof(BlockDesc)]
+// [split path: the bfloat16 planes of every block's operands]
 struct BLayout {
-    size_t exps, prefix, desc, total;
+    size_t exps, prefix, desc, parts, total;
 };
 
-static BLayout layout_of(int n_blocks, int ncfg) {
+static BLayout layout_of(int n_blocks, int ncfg, size_t parts_bytes) {
     auto al = [](size_t x) { return (x + 255) / 256 * 256; };
     BLayout L;
     L.exps = 256;
     L.prefix = al(L.exps + 8 * (size_t)n_blocks);
     L.desc = al(L.prefix + 4 * (size_t)ncfg * (n_blocks + 1));
-    L.total = al(L.desc + sizeof(BlockDesc) * (size_t)n_blocks);
+    L.parts = al(L.desc + sizeof(BlockDesc) * (size_t)n_blocks);
+    L.total = al(L.parts + parts_bytes);
     return L;
 }
 
@@ -514,10 +591,14 @@ static cudaError_t launch_batched(const Plan &P, int cfg, const BatchedParams &b
     } while (0)
 #define CM_SPL(BMv, BNv, T)                                                                         \
     do {                                                                                            \
-        if (ak && bk) batched_split_kernel<BMv, BNv, true, true, T><<<ctas, BT, 0, s>>>(bp);       \
-        else if (ak) batched_split_kernel<BMv, BNv, true, false, T><<<ctas, BT, 0, s>>>(bp);       \
-        else if (bk) batched_split_kernel<BMv, BNv, false, true, T><<<ctas, BT, 0, s>>>(bp);       \
-        else batched_split_kernel<BMv, BNv, false, false, T><<<ctas, BT, 0, s>>>(bp);              \
+        static const bool attr = [] {                                                               \
+            cudaFuncSetAttribute(batched_split_kernel<BMv, BNv, T>,                                 \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,                       \
+                                 (int)SplitSmem<BMv, BNv>::BYTES);                                  \
+            return true;                                                                            \
+        }();                                                                                        \
+        (void)attr;                                                                                 \
+        batched_split_kernel<BMv, BNv, T><<<ctas, BT, SplitSmem<BMv, BNv>::BYTES, s>>>(bp);        \
     } while (0)
     if (!split) {
         if (f32) {
@@ -555,7 +636,7 @@ static int resident_ctas() {
 // the launch sequence of one batched contraction (on a prepared workspace)
 static comet_status_t run_batched(const Plan &P, const void *const *block_inputs, int mode, void *result,
                                   uint32_t key, void *ws, cudaStream_t s, int cfg, int sample_blocks) {
-    const BLayout L = layout_of(P.n_blocks, n_cfg(P));
+    const BLayout L = layout_of(P.n_blocks, n_cfg(P), P.batched_parts);
     char *w = static_cast<char *>(ws);
     BatchedParams bp;
     bp.desc = reinterpret_cast<const BlockDesc *>(w + L.desc);
@@ -572,6 +653,7 @@ static comet_status_t run_batched(const Plan &P, const void *const *block_inputs
     bp.counter = reinterpret_cast<unsigned int *>(w);
     bp.exps = reinterpret_cast<const int *>(w + L.exps);
     bp.alpha = P.alpha;
+    bp.ws = w;
     cudaError_t e = cudaMemsetAsync(w, 0, 16, s);
     if (e == cudaSuccess && mode == 0) e = cudaMemsetAsync(result, 0, 16 * (size_t)P.n_blocks, s);
     if (e != cudaSuccess) return COMET_ERR_CUDA;
@@ -579,8 +661,13 @@ static comet_status_t run_batched(const Plan &P, const void *const *block_inputs
     const int pk = split ? PK_BATCHED_SPLIT_ID : PK_BATCHED_F64_ID;
     int h = prof_begin(pk, s);
     if (split) {
-        if (P.dtype == COMET_F32) batched_absmax_kernel<float><<<2 * nb, 256, 0, s>>>(bp);
-        else batched_absmax_kernel<double><<<2 * nb, 256, 0, s>>>(bp);
+        if (P.dtype == COMET_F32) {
+            batched_absmax_kernel<float><<<2 * nb, 256, 0, s>>>(bp);
+            batched_presplit_kernel<float><<<2 * nb, 256, 0, s>>>(bp);
+        } else {
+            batched_absmax_kernel<double><<<2 * nb, 256, 0, s>>>(bp);
+            batched_presplit_kernel<double><<<2 * nb, 256, 0, s>>>(bp);
+        }
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
@@ -686,9 +773,26 @@ comet_status_t comet_plan_batched(const char *expr, int n_blocks, const char *co
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return P.block_flops[x] > P.block_flops[y]; });
     const int ncfg = n_cfg(P);
-    const BLayout L = layout_of(n_blocks, ncfg);
+    // split path: per-block plane offsets (relative to the workspace), in launch order
+    size_t parts = 0;
+    if (P.opts.precision == COMET_PREC_SPLIT_BF16) {
+        for (int i = 0; i < n_blocks; ++i) {
+            BlockDesc &d = desc[order[i]];
+            d.kpad = (d.K + 31) / 32 * 32;
+            d.a_parts = (int64_t)parts;
+            parts += ((size_t)3 * d.M * d.kpad * 2 + 255) / 256 * 256;
+            d.b_parts = (int64_t)parts;
+            parts += ((size_t)3 * d.N * d.kpad * 2 + 255) / 256 * 256;
+        }
+    }
+    P.batched_parts = parts;
+    const BLayout L = layout_of(n_blocks, ncfg, parts);
+    for (int i = 0; i < n_blocks && parts; ++i) {
+        desc[order[i]].a_parts += (int64_t)L.parts;
+        desc[order[i]].b_parts += (int64_t)L.parts;
+    }
     P.batched_ws = L.total;
-    P.batched_table.assign(L.total - L.prefix, 0);
+    P.batched_table.assign(L.parts - L.prefix, 0);
     P.batched_prefix.assign(ncfg, std::vector<uint32_t>(n_blocks + 1, 0));
     for (int c = 0; c < ncfg; ++c) {
         const TileCfg tc = cfg_of(P, c);
@@ -740,7 +844,7 @@ comet_status_t comet_batched_prepare(comet_plan_t plan, void *workspace, void *s
     const Plan &P = plan->p;
     if (!P.batched) return COMET_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(workspace) & 15u) != 0) return COMET_ERR_ALIGN;
-    const BLayout L = layout_of(P.n_blocks, n_cfg(P));
+    const BLayout L = layout_of(P.n_blocks, n_cfg(P), P.batched_parts);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemcpyAsync(static_cast<char *>(workspace) + L.prefix, P.batched_table.data(),
                                     P.batched_table.size(), cudaMemcpyHostToDevice, s);

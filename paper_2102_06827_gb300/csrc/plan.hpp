@@ -90,6 +90,7 @@ struct Plan {
     std::vector<int64_t> block_extents;   // n_blocks x n_labels
     int tile_cfg = 0;
     size_t batched_ws = 0;
+    size_t batched_parts = 0;             // split path: bytes of the pre-split operand planes
     std::vector<uint8_t> batched_table;   // host image of the prefix sums and the descriptors
     std::vector<std::vector<uint32_t>> batched_prefix;   // per tile configuration
     std::vector<double> block_flops;
