@@ -68,6 +68,20 @@ __device__ __forceinline__ float tri_weight(uint32_t key, uint32_t block, uint32
     return (float)(h >> 8) * (1.0f / 8388608.0f) - 1.0f;   // exact in FP32 (24-bit integer)
 }
 
+// the same weight from a precomputed block term hb = block * 0x9E3779B9 (32-bit wraparound)
+__device__ __forceinline__ float tri_weight_h(uint32_t key, uint32_t hb_plus_lin) {
+    const uint32_t h = fmix32(key ^ fmix32(hb_plus_lin));
+    return (float)(h >> 8) * (1.0f / 8388608.0f) - 1.0f;
+}
+
+// four 8x8 b16 matrices from shared memory; lane l supplies the address of row l%8 of matrix l/8
+__device__ __forceinline__ void ldsm_x4(const void *p, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+
 __device__ __forceinline__ void dmma(double (&d)[2], double a, double b) {
     asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
                  : "+d"(d[0]), "+d"(d[1])
@@ -410,23 +424,22 @@ __global__ void __launch_bounds__(BT, BM * BN <= 4096 ? 4 : 2) batched_split_ker
                     uint32_t af[3][MI][4], bf[3][NJ][2];
 #pragma unroll
                     for (int pl = 0; pl < 3; ++pl) {
+                        // A 16x16 fragments: lanes 0-15 rows 0-15 at k, lanes 16-31 the same rows at k+8
 #pragma unroll
                         for (int i = 0; i < MI; ++i) {
-                            const int r = wm * (BM / 2) + i * 16 + g;
-                            const int c = ks * 16 + 2 * tq;
-                            const __nv_bfloat16 *ap = As + (pl * BM + r) * KP + c;
-                            af[pl][i][0] = *reinterpret_cast<const uint32_t *>(ap);
-                            af[pl][i][1] = *reinterpret_cast<const uint32_t *>(ap + 8 * KP);
-                            af[pl][i][2] = *reinterpret_cast<const uint32_t *>(ap + 8);
-                            af[pl][i][3] = *reinterpret_cast<const uint32_t *>(ap + 8 * KP + 8);
+                            const int r = wm * (BM / 2) + i * 16 + (lane & 15);
+                            const int c = ks * 16 + (lane >> 4) * 8;
+                            ldsm_x4(As + (pl * BM + r) * KP + c, af[pl][i][0], af[pl][i][1], af[pl][i][2],
+                                    af[pl][i][3]);
                         }
+                        // B fragments of two n8 tiles: matrix l/8 = (tile j + (l/16), k half (l/8)%2)
 #pragma unroll
-                        for (int j = 0; j < NJ; ++j) {
-                            const int r = wn * (BN / 2) + j * 8 + g;
-                            const int c = ks * 16 + 2 * tq;
-                            const __nv_bfloat16 *bp = Bs + (pl * BN + r) * KP + c;
-                            bf[pl][j][0] = *reinterpret_cast<const uint32_t *>(bp);
-                            bf[pl][j][1] = *reinterpret_cast<const uint32_t *>(bp + 8);
+                        for (int j = 0; j < NJ; j += 2) {
+                            const int mi = lane >> 3;
+                            const int r = wn * (BN / 2) + (j + (mi >> 1)) * 8 + (lane & 7);
+                            const int c = ks * 16 + (mi & 1) * 8;
+                            ldsm_x4(Bs + (pl * BN + r) * KP + c, bf[pl][j][0], bf[pl][j][1], bf[pl][j + 1][0],
+                                    bf[pl][j + 1][1]);
                         }
                     }
 #pragma unroll
@@ -443,28 +456,63 @@ __global__ void __launch_bounds__(BT, BM * BN <= 4096 ? 4 : 2) batched_split_ker
                 }
             }
             const int64_t *orow = o_row[buf];
+            if (P.mode == 0) {
+                // reduce: s and q accumulate the unscaled sums (the scale is applied once per
+                // strip); output indices are below 2^32 (the plan refuses larger blocks)
+                uint32_t ro[MI][2], co[NJ][2];
 #pragma unroll
-            for (int i = 0; i < MI; ++i)
+                for (int i = 0; i < MI; ++i)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) ro[i][h] = (uint32_t)orow[wm * (BM / 2) + i * 16 + g + 8 * h];
 #pragma unroll
                 for (int j = 0; j < NJ; ++j)
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int ml = wm * (BM / 2) + i * 16 + g + (c >= 2 ? 8 : 0);
-                        const int nl = wn * (BN / 2) + j * 8 + 2 * tq + (c & 1);
-                        if (m0 + ml < M && n0 + nl < N) {
-                            const float T = scale * (p0[i][j][c] + p1[i][j][c]);
-                            const int64_t lin = orow[ml] + o_col[nl];
-                            if (P.mode == 0) {
-                                s = fmaf(T, tri_weight(P.key, idx, (uint32_t)lin), s);
-                                q = fmaf(T, T, q);
-                            } else if (out) {
-                                out[lin] = (TIn)T;
+                    for (int h = 0; h < 2; ++h) co[j][h] = (uint32_t)o_col[wn * (BN / 2) + j * 8 + 2 * tq + h];
+                const uint32_t hb = idx * 0x9E3779B9u, key = P.key;
+                if (m0 + BM <= M && n0 + BN <= N) {   // interior tile: no bounds per element
+#pragma unroll
+                    for (int i = 0; i < MI; ++i)
+#pragma unroll
+                        for (int j = 0; j < NJ; ++j)
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                const float u = p0[i][j][c] + p1[i][j][c];
+                                s = fmaf(u, tri_weight_h(key, hb + ro[i][c >> 1] + co[j][c & 1]), s);
+                                q = fmaf(u, u, q);
                             }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < MI; ++i)
+#pragma unroll
+                        for (int j = 0; j < NJ; ++j)
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                const int ml = wm * (BM / 2) + i * 16 + g + (c >= 2 ? 8 : 0);
+                                const int nl = wn * (BN / 2) + j * 8 + 2 * tq + (c & 1);
+                                if (m0 + ml < M && n0 + nl < N) {
+                                    const float u = p0[i][j][c] + p1[i][j][c];
+                                    s = fmaf(u, tri_weight_h(key, hb + ro[i][c >> 1] + co[j][c & 1]), s);
+                                    q = fmaf(u, u, q);
+                                }
+                            }
+                }
+            } else if (out) {
+#pragma unroll
+                for (int i = 0; i < MI; ++i)
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const int ml = wm * (BM / 2) + i * 16 + g + (c >= 2 ? 8 : 0);
+                            const int nl = wn * (BN / 2) + j * 8 + 2 * tq + (c & 1);
+                            if (m0 + ml < M && n0 + nl < N)
+                                out[orow[ml] + o_col[nl]] = (TIn)(scale * (p0[i][j][c] + p1[i][j][c]));
                         }
-                    }
+            }
             if (bres) __syncthreads();   // the buffer of this tile is refilled two tiles later
         }
-        if (P.mode == 0) reduce_add((double)s, (double)q, red, reinterpret_cast<double *>(P.result), idx);
+        if (P.mode == 0)
+            reduce_add((double)s * scale, (double)q * scale * scale, red, reinterpret_cast<double *>(P.result), idx);
         __syncthreads();
     }
 }
