@@ -41,8 +41,9 @@ int *device_status_word() {
 
 // ---- kernel timing ------------------------------------------------------------------------
 static const char *kKindNames[] = {"transpose", "scale_copy", "split_prepass", "gemm_split_bf16",
-                                   "gemm_f64", "batched_f64", "batched_split", "gemm_emu_bf16x6"};
-enum { PK_TRANSPOSE = 0, PK_SCALE, PK_PREPASS, PK_SPLIT, PK_F64, PK_BATCHED_F64, PK_BATCHED_SPLIT, PK_EMU, PK_N };
+                                   "gemm_f64", "batched_f64", "batched_split", "gemm_emu_bf16x6", "gemv"};
+enum { PK_TRANSPOSE = 0, PK_SCALE, PK_PREPASS, PK_SPLIT, PK_F64, PK_BATCHED_F64, PK_BATCHED_SPLIT, PK_EMU,
+       PK_GEMV, PK_N };
 
 struct ProfRec {
     int kind;
@@ -160,6 +161,21 @@ static comet_status_t run_plan(const Plan &P, const void *const *inputs, void *o
         g.beta = beta;
         g.status = status;
         g.timeout_ns = timeout_ns(P);
+        if (st.kernel == KK_GEMV) {
+            GemvParams v = st.gemv;
+            v.v = st.gemv_vec_is_a ? g.A : g.B;
+            v.X = st.gemv_vec_is_a ? g.B : g.A;
+            v.Y = pc;
+            v.alpha = alpha;
+            v.beta = beta;
+            v.partial = reinterpret_cast<double *>(static_cast<char *>(ws) + st.ws_partial);
+            {
+                ProfScope ps(PK_GEMV, stream);
+                e = launch_gemv(v, es, stream);
+            }
+            if (e != cudaSuccess) return cuda_status(e, "gemv kernel");
+            continue;
+        }
         if (st.kernel == KK_GEMM_F64) {
             bool ak = g.k.n > 0 && (g.k.s0[0] == 1 || g.ma.n == 0 || (g.ma.s0[0] != 1 && g.k.s0[0] < g.ma.s0[0]));
             bool bk = g.k.n > 0 && (g.k.s1[0] == 1 || g.nb.n == 0 || (g.nb.s0[0] != 1 && g.k.s1[0] < g.nb.s0[0]));

@@ -27,6 +27,8 @@ cudaError_t launch_gemm_emu(const GemmParams &p, const void *parts_a, const void
                             const void *scale_a, const void *scale_b, int debug_flags, cudaStream_t s,
                             int max_ctas);
 
+cudaError_t launch_gemv(const GemvParams &p, int elem_bytes, cudaStream_t s);
+
 // device status word of the current device (set by kernels whose waits run out)
 int *device_status_word();
 

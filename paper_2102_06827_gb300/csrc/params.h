@@ -123,4 +123,18 @@ struct GemmParams {
     int64_t timeout_ns;
 };
 
+// Tensor-times-vector step: y[n] = alpha * sum_k v[k] X[k, n] (+ beta y[n]).  n: free digits
+// with (X strides, y strides); k: contracted digits with (v strides, X strides).
+struct GemvParams {
+    Radix n, k;
+    uint32_t N, K;
+    const void *v;
+    const void *X;
+    void *Y;
+    double alpha, beta;
+    int n_fast;                    // 1: X's stride-1 dim is a free digit, 0: a contracted one
+    uint32_t nchunks;              // ceil(K / 1024)
+    double *partial;               // workspace: nchunks x N FP64 partial sums
+};
+
 }  // namespace comet

@@ -3,7 +3,9 @@
 
 #include <algorithm>
 #include <cctype>
+#include <climits>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -681,6 +683,8 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
         }
         st.form = forms[pick];
         st.form_index = pick;
+        // one operand without free labels: a tensor-times-vector step (HBM-bound, see k_gemv.cu)
+        if (st.form.M.empty() || st.form.N.empty()) st.kernel = KK_GEMV;
         if (free_layout) {   // the intermediate is stored as [M][N]: the epilogue writes rows
             sc.labels = st.form.M;
             sc.labels.insert(sc.labels.end(), st.form.N.begin(), st.form.N.end());
@@ -703,6 +707,13 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
         st.ws_parts_a = parts_base;
         st.ws_parts_b = parts_base + ba;
         parts_max = std::max(parts_max, ba + bb);
+    }
+    for (auto &st : P->steps) {
+        if (st.kernel != KK_GEMV) continue;
+        const int64_t Kx = prod_ext(P->extent, st.form.K);
+        const int64_t Nx = prod_ext(P->extent, st.form.M.empty() ? st.form.N : st.form.M);
+        st.ws_partial = parts_base;
+        parts_max = std::max(parts_max, align((size_t)((Kx + 1023) / 1024) * (size_t)Nx * 8));
     }
     bool any_split = false;
     for (auto &st : P->steps) any_split |= st.kernel == KK_GEMM_SPLIT || st.kernel == KK_GEMM_EMU;
@@ -740,6 +751,30 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
         g.N = (uint32_t)prod_ext(P->extent, st.form.N);
         g.K = (uint32_t)prod_ext(P->extent, st.form.K);
         g.ma.total = g.M; g.nb.total = g.N; g.k.total = g.K;
+        if (st.kernel == KK_GEMV) {
+            GemvParams &v = st.gemv;
+            std::memset(&v, 0, sizeof(v));
+            st.gemv_vec_is_a = st.form.M.empty();
+            if (st.gemv_vec_is_a) {          // y[n] = sum_k A[k] B[k, n]
+                v.n = g.nb;
+                v.k = g.k;
+                v.N = g.N;
+            } else {                         // y[m] = sum_k A[m, k] B[k]
+                v.n = g.ma;
+                v.k = g.k;
+                for (int d = 0; d < v.k.n; ++d) std::swap(v.k.s0[d], v.k.s1[d]);
+                v.N = g.M;
+            }
+            v.K = g.K;
+            v.n.total = v.N;
+            v.k.total = v.K;
+            int64_t min_n = INT64_MAX, min_k = INT64_MAX;
+            for (int d = 0; d < v.n.n; ++d) min_n = std::min(min_n, v.n.s0[d]);
+            for (int d = 0; d < v.k.n; ++d) min_k = std::min(min_k, v.k.s1[d]);
+            v.n_fast = min_n < min_k ? 1 : 0;
+            v.nchunks = (v.K + 1023) / 1024;
+            continue;
+        }
         if (st.kernel == KK_GEMM_SPLIT || st.kernel == KK_GEMM_EMU) {
             // pre-pass of each operand into [planes][rows][kpad] bf16 planes (K order, then rows)
             auto pre = [&](const Slot &so_, const std::vector<int> &rows, XposeParams *xp, int *vec_in, int *vec_out) {
@@ -802,7 +837,8 @@ std::string describe_plan(const Plan &P) {
         const Step &s = P.steps[i];
         if (i) o << ",";
         o << "{\"kernel\":\"" << (s.kernel == KK_COPY ? "copy" : s.kernel == KK_GEMM_SPLIT ? "gemm_split_bf16"
-                                    : s.kernel == KK_GEMM_EMU ? "gemm_emu_bf16x6" : "gemm_f64")
+                                    : s.kernel == KK_GEMM_EMU ? "gemm_emu_bf16x6"
+                                    : s.kernel == KK_GEMV ? "gemv" : "gemm_f64")
           << "\",\"a\":" << s.a << ",\"b\":" << s.b << ",\"c\":" << s.c
           << ",\"a_labels\":" << names(P.slots[s.a].labels);
         if (s.b >= 0) o << ",\"b_labels\":" << names(P.slots[s.b].labels);

@@ -27,7 +27,7 @@ struct ParsedExpr {
 
 comet_status_t parse_expr(const char *s, ParsedExpr *e, std::string *err);
 
-enum KernelKind { KK_GEMM_F64 = 0, KK_GEMM_SPLIT = 1, KK_COPY = 2, KK_GEMM_EMU = 3 };
+enum KernelKind { KK_GEMM_F64 = 0, KK_GEMM_SPLIT = 1, KK_COPY = 2, KK_GEMM_EMU = 3, KK_GEMV = 4 };
 
 // One TTGT form of a binary step: which input provides the M (row) group, and the order of
 // the labels inside M, N and K (first = fastest in the merged index).
@@ -65,6 +65,9 @@ struct Step {
     GemmParams gemm;             // for both GEMM kernels (offsets in elements)
     XposeParams pre_a, pre_b;    // split pre-passes (A then B operand)
     XposeParams copy;            // KK_COPY
+    GemvParams gemv;             // KK_GEMV (one operand has no free label)
+    bool gemv_vec_is_a = true;   // the vector is the GEMM's A (M) operand, else its B operand
+    size_t ws_partial = 0;       // KK_GEMV: workspace offset of the chunk partial sums
     int pre_a_vec = 1, pre_b_vec = 1, pre_a_vout = 1, pre_b_vout = 1;
     int copy_vec_in = 1, copy_vec_out = 1;
 };
