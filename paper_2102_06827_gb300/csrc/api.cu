@@ -153,54 +153,73 @@ static comet_status_t run_plan(const Plan &P, const void *const *inputs, void *o
             continue;
         }
         void *pb = slot_ptr(P, st.b, inputs, output, ws);
-        GemmParams g = st.gemm;
-        g.A = st.form.swap ? pb : pa;
-        g.B = st.form.swap ? pa : pb;
-        g.C = pc;
-        g.alpha = alpha;
-        g.beta = beta;
-        g.status = status;
-        g.timeout_ns = timeout_ns(P);
-        if (st.kernel == KK_GEMV) {
-            GemvParams v = st.gemv;
-            v.v = st.gemv_vec_is_a ? g.A : g.B;
-            v.X = st.gemv_vec_is_a ? g.B : g.A;
-            v.Y = pc;
-            v.alpha = alpha;
-            v.beta = beta;
-            v.partial = reinterpret_cast<double *>(static_cast<char *>(ws) + st.ws_partial);
-            {
-                ProfScope ps(PK_GEMV, stream);
-                e = launch_gemv(v, es, stream);
-            }
-            if (e != cudaSuccess) return cuda_status(e, "gemv kernel");
-            continue;
-        }
-        if (st.kernel == KK_GEMM_F64) {
-            bool ak = g.k.n > 0 && (g.k.s0[0] == 1 || g.ma.n == 0 || (g.ma.s0[0] != 1 && g.k.s0[0] < g.ma.s0[0]));
-            bool bk = g.k.n > 0 && (g.k.s1[0] == 1 || g.nb.n == 0 || (g.nb.s0[0] != 1 && g.k.s1[0] < g.nb.s0[0]));
-            {
-                ProfScope ps(PK_F64, stream);
-                e = launch_gemm_f64(g, es, ak, bk, stream);
-            }
-            if (e != cudaSuccess) return cuda_status(e, "gemm_f64 kernel");
-        } else {
-            char *w = static_cast<char *>(ws);
-            void *sc_a = w + st.ws_scales, *sc_b = w + st.ws_scales + 8;
+        char *w = static_cast<char *>(ws);
+        void *sc_a = w + st.ws_scales, *sc_b = w + st.ws_scales + 8;
+        const bool split_like = st.kernel == KK_GEMM_SPLIT || st.kernel == KK_GEMM_EMU;
+        if (split_like) {   // operand scales over the whole operands (every batch index shares them)
             const int64_t na = P.slots[st.form.swap ? st.b : st.a].elems;
             const int64_t nb = P.slots[st.form.swap ? st.a : st.b].elems;
-            XposeParams xa = st.pre_a, xb = st.pre_b;
-            xa.in = g.A; xa.out = w + st.ws_parts_a; xa.scale_bits = sc_a;
-            xb.in = g.B; xb.out = w + st.ws_parts_b; xb.scale_bits = sc_b;
             {
                 ProfScope ps(PK_PREPASS, stream);
-                e = launch_absmax(g.A, na, es, sc_a, stream);
+                e = launch_absmax(st.form.swap ? pb : pa, na, es, sc_a, stream);
             }
             if (e == cudaSuccess) {
                 ProfScope ps(PK_PREPASS, stream);
-                e = launch_absmax(g.B, nb, es, sc_b, stream);
+                e = launch_absmax(st.form.swap ? pa : pb, nb, es, sc_b, stream);
             }
             if (e != cudaSuccess) return cuda_status(e, "split pre-pass (scales)");
+        }
+        // one pass of the step's kernels per batch index (a single pass without batch labels;
+        // the gemv kernels take every batch index in one launch)
+        const int64_t passes = st.kernel == KK_GEMV ? 1 : st.n_batch;
+        for (int64_t bi = 0; bi < passes; ++bi) {
+            int64_t oa = 0, ob = 0, oc = 0, r = bi;
+            for (size_t d = 0; d < st.bt_ext.size(); ++d) {
+                const int64_t x = r % st.bt_ext[d];
+                r /= st.bt_ext[d];
+                oa += x * st.bt_sa[d];
+                ob += x * st.bt_sb[d];
+                oc += x * st.bt_sc[d];
+            }
+            void *qa = static_cast<char *>(pa) + oa * es;
+            void *qb = static_cast<char *>(pb) + ob * es;
+            void *qc = static_cast<char *>(pc) + oc * es;
+            GemmParams g = st.gemm;
+            g.A = st.form.swap ? qb : qa;
+            g.B = st.form.swap ? qa : qb;
+            g.C = qc;
+            g.alpha = alpha;
+            g.beta = beta;
+            g.status = status;
+            g.timeout_ns = timeout_ns(P);
+            if (st.kernel == KK_GEMV) {
+                GemvParams v = st.gemv;
+                v.v = st.gemv_vec_is_a ? g.A : g.B;
+                v.X = st.gemv_vec_is_a ? g.B : g.A;
+                v.Y = qc;
+                v.alpha = alpha;
+                v.beta = beta;
+                v.partial = reinterpret_cast<double *>(w + st.ws_partial);
+                {
+                    ProfScope ps(PK_GEMV, stream);
+                    e = launch_gemv(v, es, stream);
+                }
+                if (e != cudaSuccess) return cuda_status(e, "gemv kernel");
+                continue;
+            }
+            if (st.kernel == KK_GEMM_F64) {
+                bool ak = g.k.n > 0 && (g.k.s0[0] == 1 || g.ma.n == 0 || (g.ma.s0[0] != 1 && g.k.s0[0] < g.ma.s0[0]));
+                bool bk = g.k.n > 0 && (g.k.s1[0] == 1 || g.nb.n == 0 || (g.nb.s0[0] != 1 && g.k.s1[0] < g.nb.s0[0]));
+                {
+                    ProfScope ps(PK_F64, stream);
+                    e = launch_gemm_f64(g, es, ak, bk, stream);
+                }
+                if (e != cudaSuccess) return cuda_status(e, "gemm_f64 kernel");
+                continue;
+            }
+            XposeParams xa = st.pre_a, xb = st.pre_b;
+            xa.in = g.A; xa.out = w + st.ws_parts_a; xa.scale_bits = sc_a;
+            xb.in = g.B; xb.out = w + st.ws_parts_b; xb.scale_bits = sc_b;
             auto split = st.kernel == KK_GEMM_EMU ? launch_split6 : launch_split;
             {
                 ProfScope ps(PK_PREPASS, stream);

@@ -761,6 +761,10 @@ comet_status_t comet_plan_batched(const char *expr, int n_blocks, const char *co
         st = COMET_ERR_UNSUPPORTED;
         err = "batched plans take one two-operand \"=\" contraction";
     }
+    if (st == COMET_OK && !P.steps[0].form.Bt.empty()) {
+        st = COMET_ERR_UNSUPPORTED;
+        err = "batched plans take no batch labels (labels on both operands and the result)";
+    }
     if (st == COMET_OK && P.opts.precision == COMET_PREC_EMU_F64) {
         st = COMET_ERR_UNSUPPORTED;
         err = "batched plans take the native or the split precision";

@@ -4,7 +4,7 @@
 // bound by HBM, not by the tensor cores: a tiled tensor-core GEMM would waste all but one row
 // of each 128-row tile and would first write split planes of the large operand.
 //
-//   y[n] = alpha * sum_k v[k] * X[k, n]  (+ beta * y[n])
+//   y[b, n] = alpha * sum_k v[b, k] * X[b, k, n]  (+ beta * y[b, n]),  b over the batch labels
 //
 // Stage 1: blocks over (n tile, K chunk of 1024) read X in its own memory order -- threads along
 // n when X's stride-1 dim is a free label, along k (with a warp reduction per n) when it is a
@@ -59,10 +59,13 @@ __global__ void __launch_bounds__(gv::T) gemv_partial_kernel(const GemvParams p)
     __shared__ double red[NFAST ? NT_N : 1];
     const int t = threadIdx.x;
     constexpr int NT = NFAST ? NT_N : NT_K;
-    const uint32_t n0 = blockIdx.x * NT, k0 = blockIdx.y * KC;
+    const uint32_t tiles = (p.N + NT - 1) / NT;
+    const uint32_t bi = blockIdx.x / tiles, n0 = (blockIdx.x - bi * tiles) * NT, k0 = blockIdx.y * KC;
     const uint32_t nk = min((uint32_t)KC, p.K - k0), nn = min((uint32_t)NT, p.N - n0);
-    const T *v = reinterpret_cast<const T *>(p.v);
-    const T *X = reinterpret_cast<const T *>(p.X);
+    int64_t bo_v = 0, bo_x = 0;
+    radix_offsets(p.bv, bi, bo_v, bo_x);
+    const T *v = reinterpret_cast<const T *>(p.v) + bo_v;
+    const T *X = reinterpret_cast<const T *>(p.X) + bo_x;
     for (uint32_t i = t; i < (uint32_t)KC; i += gv::T) {
         int64_t ov = 0, ox = 0;
         if (i < nk) radix_offsets(p.k, k0 + i, ov, ox);
@@ -75,7 +78,7 @@ __global__ void __launch_bounds__(gv::T) gemv_partial_kernel(const GemvParams p)
         n_off[i] = ox;
     }
     __syncthreads();
-    double *out = p.partial + (size_t)blockIdx.y * p.N;
+    double *out = p.partial + ((size_t)bi * p.nchunks + blockIdx.y) * p.N;
     if (NFAST) {
         // threads along n (contiguous in X), two k phases
         const int tn = t % NT_N, tk = t / NT_N;
@@ -108,13 +111,16 @@ __global__ void __launch_bounds__(gv::T) gemv_partial_kernel(const GemvParams p)
 
 template <typename T>
 __global__ void __launch_bounds__(256) gemv_finish_kernel(const GemvParams p) {
-    const uint32_t n = blockIdx.x * 256 + threadIdx.x;
-    if (n >= p.N) return;
+    const uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= (uint64_t)p.n_batch * p.N) return;
+    const uint32_t bi = (uint32_t)(i / p.N), n = (uint32_t)(i - (uint64_t)bi * p.N);
     double s = 0.0;
-    for (uint32_t c = 0; c < p.nchunks; ++c) s += p.partial[(size_t)c * p.N + n];
-    int64_t ox = 0, oy = 0;
+    const double *part = p.partial + (size_t)bi * p.nchunks * p.N;
+    for (uint32_t c = 0; c < p.nchunks; ++c) s += part[(size_t)c * p.N + n];
+    int64_t ox = 0, oy = 0, by = 0, unused = 0;
     radix_offsets(p.n, n, ox, oy);
-    T *y = reinterpret_cast<T *>(p.Y) + oy;
+    radix_offsets(p.by, bi, by, unused);
+    T *y = reinterpret_cast<T *>(p.Y) + by + oy;
     const double r = p.alpha * s;
     *y = (T)(p.beta != 0.0 ? r + p.beta * (double)*y : r);
 }
@@ -123,15 +129,18 @@ cudaError_t launch_gemv(const GemvParams &p, int elem_bytes, cudaStream_t s) {
     using namespace gv;
     if (p.N == 0) return cudaSuccess;
     if (p.K == 0) return cudaErrorInvalidValue;
-    const dim3 grid1((p.N + (p.n_fast ? NT_N : NT_K) - 1) / (p.n_fast ? NT_N : NT_K), p.nchunks);
+    const uint64_t tiles = (p.N + (p.n_fast ? NT_N : NT_K) - 1) / (p.n_fast ? NT_N : NT_K);
+    if (tiles * p.n_batch >= (1ull << 31) || p.nchunks > 65535) return cudaErrorInvalidValue;
+    const dim3 grid1((uint32_t)(tiles * p.n_batch), p.nchunks);
+    const uint32_t grid2 = (uint32_t)(((uint64_t)p.n_batch * p.N + 255) / 256);
     if (elem_bytes == 4) {
         if (p.n_fast) gemv_partial_kernel<float, true><<<grid1, gv::T, 0, s>>>(p);
         else gemv_partial_kernel<float, false><<<grid1, gv::T, 0, s>>>(p);
-        gemv_finish_kernel<float><<<(p.N + 255) / 256, 256, 0, s>>>(p);
+        gemv_finish_kernel<float><<<grid2, 256, 0, s>>>(p);
     } else {
         if (p.n_fast) gemv_partial_kernel<double, true><<<grid1, gv::T, 0, s>>>(p);
         else gemv_partial_kernel<double, false><<<grid1, gv::T, 0, s>>>(p);
-        gemv_finish_kernel<double><<<(p.N + 255) / 256, 256, 0, s>>>(p);
+        gemv_finish_kernel<double><<<grid2, 256, 0, s>>>(p);
     }
     return cudaGetLastError();
 }

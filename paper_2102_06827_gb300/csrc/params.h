@@ -127,6 +127,8 @@ struct GemmParams {
 // with (X strides, y strides); k: contracted digits with (v strides, X strides).
 struct GemvParams {
     Radix n, k;
+    Radix bv, by;                  // batch digits: (v strides, X strides) and (y strides, unused)
+    uint32_t n_batch;              // product of the batch extents (1 without batch labels)
     uint32_t N, K;
     const void *v;
     const void *X;
@@ -134,7 +136,7 @@ struct GemvParams {
     double alpha, beta;
     int n_fast;                    // 1: X's stride-1 dim is a free digit, 0: a contracted one
     uint32_t nchunks;              // ceil(K / 1024)
-    double *partial;               // workspace: nchunks x N FP64 partial sums
+    double *partial;               // workspace: n_batch x nchunks x N FP64 partial sums
 };
 
 }  // namespace comet

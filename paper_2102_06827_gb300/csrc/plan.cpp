@@ -393,7 +393,11 @@ void cost_form(const Plan &P, const std::vector<int> &lx, const std::vector<int>
             for (int l : f->K) { sout[l] = s; s *= ext[l]; }
             s = kpad;
             for (int l : rows) { sout[l] = s; s *= ext[l]; }
-            for (int l : lop) { e.push_back(ext[l]); si.push_back(st[l]); so.push_back(sout[l]); }
+            for (int l : lop) {
+                if (pos_of(f->Bt, l) >= 0) continue;   // batch labels: one pre-pass per index
+                e.push_back(ext[l]); si.push_back(st[l]); so.push_back(sout[l]);
+            }
+            if (e.empty()) { e.push_back(1); si.push_back(1); so.push_back(1); }
             XposeParams xp;
             int vi, vo;
             double eff;
@@ -515,7 +519,6 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
     } else {
         for (int l = 0; l < L; ++l) {
             if (count[l] == 1) { *err = "label " + P->label_names[l] + " is summed inside a single operand"; return COMET_ERR_UNSUPPORTED; }
-            if (count[l] > 2) { *err = "label " + P->label_names[l] + " appears in more than two tensors (batch label)"; return COMET_ERR_UNSUPPORTED; }
         }
     }
     if (E.has_sum) {
@@ -646,11 +649,17 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
         st.kernel = kernel;
         Slot &sa = P->slots[st.a], &sb = P->slots[st.b], &sc = P->slots[st.c];
         bool free_layout = sc.kind == SLOT_INTER;
-        std::vector<int> I, J, K;   // free in a, free in b, contracted
-        for (int l : sa.labels) (pos_of(sb.labels, l) >= 0 ? K : I).push_back(l);
+        // free in a, free in b, contracted, batch (on both inputs and kept in the result)
+        std::vector<int> I, J, K, Bt;
+        for (int l : sa.labels) {
+            if (pos_of(sb.labels, l) < 0) I.push_back(l);
+            else (pos_of(sc.labels, l) >= 0 ? Bt : K).push_back(l);
+        }
         for (int l : sb.labels) if (pos_of(sa.labels, l) < 0) J.push_back(l);
         for (int l : sc.labels)
-            if (pos_of(I, l) < 0 && pos_of(J, l) < 0) { *err = "internal: output label not free"; return COMET_ERR_INTERNAL; }
+            if (pos_of(I, l) < 0 && pos_of(J, l) < 0 && pos_of(Bt, l) < 0) {
+                *err = "internal: output label not free"; return COMET_ERR_INTERNAL;
+            }
         if (prod_ext(P->extent, I) >= (1ll << 31) || prod_ext(P->extent, J) >= (1ll << 31) ||
             prod_ext(P->extent, K) >= (1ll << 31)) {
             *err = "a merged GEMM dimension reaches 2^31"; return COMET_ERR_UNSUPPORTED;
@@ -667,7 +676,7 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
             auto on = group_orders(gn, {&sc.labels, &ln});
             auto ok = group_orders(K, {&lm, &ln});
             for (auto &m : om) for (auto &nn : on) for (auto &k : ok) {
-                Form f; f.swap = swap; f.M = m; f.N = nn; f.K = k;
+                Form f; f.swap = swap; f.M = m; f.N = nn; f.K = k; f.Bt = Bt;
                 cost_form(*P, sa.labels, sb.labels, sc.labels, free_layout, kernel, &f);
                 forms.push_back(f);
                 if (forms.size() > 20000) break;
@@ -685,9 +694,23 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
         st.form_index = pick;
         // one operand without free labels: a tensor-times-vector step (HBM-bound, see k_gemv.cu)
         if (st.form.M.empty() || st.form.N.empty()) st.kernel = KK_GEMV;
-        if (free_layout) {   // the intermediate is stored as [M][N]: the epilogue writes rows
+        if (free_layout) {   // the intermediate is stored as [M][N][batch]: the epilogue writes rows
             sc.labels = st.form.M;
             sc.labels.insert(sc.labels.end(), st.form.N.begin(), st.form.N.end());
+            sc.labels.insert(sc.labels.end(), st.form.Bt.begin(), st.form.Bt.end());
+        }
+        if (prod_ext(P->extent, Bt) >= (1ll << 31)) { *err = "batch labels reach 2^31 indices"; return COMET_ERR_UNSUPPORTED; }
+        {   // batch offsets of the three tensors (strides of their full layouts)
+            auto ta = label_strides(sa.labels, P->extent), tb = label_strides(sb.labels, P->extent),
+                 tc = label_strides(sc.labels, P->extent);
+            st.n_batch = 1;
+            for (int l : Bt) {
+                st.bt_ext.push_back(P->extent[l]);
+                st.bt_sa.push_back(ta[l]);
+                st.bt_sb.push_back(tb[l]);
+                st.bt_sc.push_back(tc[l]);
+                st.n_batch *= P->extent[l];
+            }
         }
     }
 
@@ -713,7 +736,7 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
         const int64_t Kx = prod_ext(P->extent, st.form.K);
         const int64_t Nx = prod_ext(P->extent, st.form.M.empty() ? st.form.N : st.form.M);
         st.ws_partial = parts_base;
-        parts_max = std::max(parts_max, align((size_t)((Kx + 1023) / 1024) * (size_t)Nx * 8));
+        parts_max = std::max(parts_max, align((size_t)st.n_batch * (size_t)((Kx + 1023) / 1024) * (size_t)Nx * 8));
     }
     bool any_split = false;
     for (auto &st : P->steps) any_split |= st.kernel == KK_GEMM_SPLIT || st.kernel == KK_GEMM_EMU;
@@ -773,6 +796,20 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
             for (int d = 0; d < v.k.n; ++d) min_k = std::min(min_k, v.k.s1[d]);
             v.n_fast = min_n < min_k ? 1 : 0;
             v.nchunks = (v.K + 1023) / 1024;
+            {   // batch digits in-kernel: (vector, large operand) offsets and result offsets
+                std::vector<int> none;
+                std::vector<int64_t> sv(L, 0), sx(L, 0), sy(L, 0), zero(L, 0);
+                auto ta = label_strides(sa.labels, P->extent), tb = label_strides(sb.labels, P->extent),
+                     tc = label_strides(sc.labels, P->extent);
+                for (int l : st.form.Bt) {
+                    sv[l] = st.gemv_vec_is_a ? (st.form.swap ? tb[l] : ta[l]) : (st.form.swap ? ta[l] : tb[l]);
+                    sx[l] = st.gemv_vec_is_a ? (st.form.swap ? ta[l] : tb[l]) : (st.form.swap ? tb[l] : ta[l]);
+                    sy[l] = tc[l];
+                }
+                fill_radix(&v.bv, st.form.Bt, ex.data(), sv.data(), sx.data());
+                fill_radix(&v.by, st.form.Bt, ex.data(), sy.data(), zero.data());
+                v.n_batch = (uint32_t)st.n_batch;
+            }
             continue;
         }
         if (st.kernel == KK_GEMM_SPLIT || st.kernel == KK_GEMM_EMU) {
@@ -785,7 +822,11 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
                 s = st.kpad;
                 for (int l : rows) { sout[l] = s; s *= P->extent[l]; }
                 std::vector<int64_t> e, a, b;
-                for (int l : so_.labels) { e.push_back(P->extent[l]); a.push_back(st_[l]); b.push_back(sout[l]); }
+                for (int l : so_.labels) {
+                    if (pos_of(st.form.Bt, l) >= 0) continue;   // one pre-pass per batch index
+                    e.push_back(P->extent[l]); a.push_back(st_[l]); b.push_back(sout[l]);
+                }
+                if (e.empty()) { e.push_back(1); a.push_back(1); b.push_back(1); }
                 double eff;
                 setup_xpose((int)e.size(), e.data(), a.data(), b.data(), (int)es, xp, vec_in, vec_out, &eff);
                 int64_t rows_n = prod_ext(P->extent, rows);
@@ -845,7 +886,8 @@ std::string describe_plan(const Plan &P) {
         o << ",\"c_labels\":" << names(P.slots[s.c].labels);
         if (s.kernel != KK_COPY) {
             o << ",\"swap\":" << s.form.swap << ",\"M\":" << names(s.form.M) << ",\"N\":" << names(s.form.N)
-              << ",\"K\":" << names(s.form.K) << ",\"n_forms\":" << s.n_forms << ",\"form_index\":" << s.form_index
+              << ",\"K\":" << names(s.form.K) << ",\"batch\":" << names(s.form.Bt)
+              << ",\"n_forms\":" << s.n_forms << ",\"form_index\":" << s.form_index
               << ",\"cost_s\":" << s.form.cost << ",\"pre_bytes\":" << s.form.pre_bytes
               << ",\"eff_store\":" << s.form.eff_store << ",\"flops\":" << s.flops;
         }

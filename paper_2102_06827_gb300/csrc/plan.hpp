@@ -34,6 +34,7 @@ enum KernelKind { KK_GEMM_F64 = 0, KK_GEMM_SPLIT = 1, KK_COPY = 2, KK_GEMM_EMU =
 struct Form {
     int swap = 0;                // 0: the step's first input is the M operand
     std::vector<int> M, N, K;
+    std::vector<int> Bt;         // batch labels: on both inputs and the result (not merged)
     double cost = 0;             // modelled seconds
     double pre_bytes = 0;        // bytes moved by explicit pre-passes
     double eff_store = 1, eff_a = 1, eff_b = 1;
@@ -68,6 +69,10 @@ struct Step {
     GemvParams gemv;             // KK_GEMV (one operand has no free label)
     bool gemv_vec_is_a = true;   // the vector is the GEMM's A (M) operand, else its B operand
     size_t ws_partial = 0;       // KK_GEMV: workspace offset of the chunk partial sums
+    // batch labels of the step: the kernels run once per batch index, with the operands' and
+    // the result's base offsets (elements) of that index; extents and the three stride sets
+    std::vector<int64_t> bt_ext, bt_sa, bt_sb, bt_sc;
+    int64_t n_batch = 1;
     int pre_a_vec = 1, pre_b_vec = 1, pre_a_vout = 1, pre_b_vout = 1;
     int copy_vec_in = 1, copy_vec_out = 1;
 };

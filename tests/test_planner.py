@@ -50,9 +50,8 @@ def test_parse_errors_and_codes():
     with pytest.raises(comet.CometError) as e:
         plan("C[i,j] = A[i,k]*B[k,j]", dict(i=3, j=0, k=2))
     assert e.value.name == "COMET_ERR_SHAPE"
-    # batch label, repeated label, summation inside one operand
-    for unsup in ["C[i,j,b] = A[i,k,b]*B[k,j,b]", "C[i,j] = A[i,i,k]*B[k,j]",
-                  "C[i,j] = A[i,k,l]*B[k,j]", "C[i] = A[i,k]"]:
+    # repeated label, summation inside one operand
+    for unsup in ["C[i,j] = A[i,i,k]*B[k,j]", "C[i,j] = A[i,k,l]*B[k,j]", "C[i] = A[i,k]"]:
         with pytest.raises(comet.CometError) as e:
             plan(unsup, dict(i=3, j=4, k=5, b=2, l=2))
         assert e.value.name == "COMET_ERR_UNSUPPORTED", unsup
@@ -112,6 +111,26 @@ def test_flops_and_workspace():
     ps = plan("C[a,b,c,d] = A[a,e,b] * B[e,d,c]", ext, precision="split_bf16")
     kpad = 24 + (-24) % 8
     assert ps.workspace_bytes >= 3 * 2 * kpad * (576 + 576)
+
+
+def test_batch_labels():
+    # a label on both inputs and the result is a batch label of its step: not merged into M, N
+    # or K; the step runs once per batch index
+    ext = dict(i=3, j=4, k=5, b=6)
+    p = plan("C[i,j,b] = A[i,k,b]*B[k,j,b]", ext)
+    st = p.info["steps"][0]
+    assert st["batch"] == ["b"] and "b" not in st["M"] + st["N"] + st["K"]
+    assert p.flops == 2 * 3 * 4 * 5 * 6
+    # a label on three inputs: batch in the first step, contracted in the second
+    p = plan("s[] = x[i]*y[i]*z[i]", dict(i=7))
+    assert [s["batch"] for s in p.info["steps"]] == [["i"], []]
+    assert p.flops == 2 * 7 + 2 * 7
+    # batch labels and a multi-operand chain
+    p = plan("D[b,i] = A[b,i,j]*B[b,j,k]*C[b,k]", dict(b=4, i=5, j=6, k=7))
+    assert all(s["batch"] == ["b"] for s in p.info["steps"])
+    with pytest.raises(comet.CometError) as e:
+        comet.BatchedPlan("C[i,j,b] = A[i,k,b]*B[k,j,b]", ["i", "j", "k", "b"], [[2, 2, 2, 2]], "f64")
+    assert e.value.name == "COMET_ERR_UNSUPPORTED"
 
 
 def test_emulated_fp64_plans():
