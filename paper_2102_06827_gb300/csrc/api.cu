@@ -152,6 +152,21 @@ static comet_status_t run_plan(const Plan &P, const void *const *inputs, void *o
             if (e != cudaSuccess) return cuda_status(e, "copy kernel");
             continue;
         }
+        if (st.kernel == KK_REDUCE) {   // sum over labels private to the operand (gemv with v = 1)
+            GemvParams v = st.gemv;
+            v.X = pa;
+            v.v = nullptr;
+            v.Y = pc;
+            v.alpha = alpha;
+            v.beta = beta;
+            v.partial = reinterpret_cast<double *>(static_cast<char *>(ws) + st.ws_partial);
+            {
+                ProfScope ps(PK_GEMV, stream);
+                e = launch_gemv(v, es, stream);
+            }
+            if (e != cudaSuccess) return cuda_status(e, "reduction kernel");
+            continue;
+        }
         void *pb = slot_ptr(P, st.b, inputs, output, ws);
         char *w = static_cast<char *>(ws);
         void *sc_a = w + st.ws_scales, *sc_b = w + st.ws_scales + 8;

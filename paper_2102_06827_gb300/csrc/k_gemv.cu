@@ -11,7 +11,8 @@
 // contracted one -- and write one partial sum per (chunk, n) in FP64.  FP32 operands use the
 // compensated dot product of Ogita, Rump and Oishi (Dot2: TwoProduct by FMA, TwoSum), so the
 // chunk sum is as accurate as if computed in twice the working precision; FP64 operands use
-// FMA.  Stage 2 adds the chunk partials in FP64 and writes y through the output strides.
+// FMA.  Stage 2 adds the chunk partials in FP64 and writes y through the output strides.  With
+// v all ones the same kernels sum labels that occur in a single operand (a reduction).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(gv::T) gemv_partial_kernel(const GemvParams p)
         int64_t ov = 0, ox = 0;
         if (i < nk) radix_offsets(p.k, k0 + i, ov, ox);
         k_off[i] = ox;
-        vk[i] = i < nk ? v[ov] : (T)0;
+        vk[i] = i < nk ? (p.v_ones ? (T)1 : v[ov]) : (T)0;
     }
     for (uint32_t i = t; i < (uint32_t)NT; i += gv::T) {
         int64_t ox = 0, oy = 0;

@@ -135,6 +135,7 @@ struct GemvParams {
     void *Y;
     double alpha, beta;
     int n_fast;                    // 1: X's stride-1 dim is a free digit, 0: a contracted one
+    int v_ones;                    // 1: v is all ones (a sum over the k digits of X; v unused)
     uint32_t nchunks;              // ceil(K / 1024)
     double *partial;               // workspace: n_batch x nchunks x N FP64 partial sums
 };

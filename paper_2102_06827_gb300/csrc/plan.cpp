@@ -514,13 +514,8 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
     std::vector<int> count(L, 0);
     for (auto &v : in_labs) for (int l : v) ++count[l];
     for (int l : out_labs) ++count[l];
-    if (P->n_in == 1) {
-        if (in_labs[0].size() != out_labs.size()) { *err = "summation inside a single operand"; return COMET_ERR_UNSUPPORTED; }
-    } else {
-        for (int l = 0; l < L; ++l) {
-            if (count[l] == 1) { *err = "label " + P->label_names[l] + " is summed inside a single operand"; return COMET_ERR_UNSUPPORTED; }
-        }
-    }
+    // labels on a single operand and not on the output are summed inside that operand first
+    // (a reduction step); the rest of the plan sees the reduced operand
     if (E.has_sum) {
         std::set<std::string> want, got(E.sum_labels.begin(), E.sum_labels.end());
         for (int l = 0; l < L; ++l) if (pos_of(out_labs, l) < 0) want.insert(P->label_names[l]);
@@ -546,10 +541,35 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
     int out_slot = (int)P->slots.size();
     P->slots.push_back(so);
 
-    // ---- single operand: scaled copy / transpose (ta.copy) ----
+    // ---- reductions of labels private to one operand ----
+    std::vector<int> leaf_slot(P->n_in);
+    for (int t = 0; t < P->n_in; ++t) {
+        leaf_slot[t] = t;
+        std::vector<int> keep;
+        for (int l : in_labs[t]) if (count[l] > 1) keep.push_back(l);
+        if (keep.size() == in_labs[t].size()) continue;
+        Step r;
+        r.kernel = KK_REDUCE;
+        r.a = t;
+        r.flops = (double)elems_of(in_labs[t]);
+        if (P->n_in == 1) {
+            r.c = out_slot;
+            r.final_step = true;
+        } else {
+            Slot s; s.kind = SLOT_INTER; s.labels = keep; s.elems = (int64_t)elems_of(keep);
+            r.c = (int)P->slots.size();
+            P->slots.push_back(s);
+            leaf_slot[t] = r.c;
+        }
+        P->steps.push_back(r);
+        in_labs[t] = keep;
+    }
+    // ---- single operand: scaled copy / transpose (ta.copy), or the reduction above ----
     if (P->n_in == 1) {
-        Step s; s.a = 0; s.c = out_slot; s.kernel = KK_COPY; s.final_step = true; s.flops = 0;
-        P->steps.push_back(s);
+        if (P->steps.empty()) {
+            Step s; s.a = 0; s.c = out_slot; s.kernel = KK_COPY; s.final_step = true; s.flops = 0;
+            P->steps.push_back(s);
+        }
         P->tree = E.ins[0].name;
     } else {
         // ---- operand order (Section 6): DP over subsets, min flops; ties: min intermediate
@@ -616,7 +636,7 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
         }
         // emit steps post-order
         std::function<int(int)> emit = [&](int S) -> int {
-            if (__builtin_popcount((unsigned)S) == 1) return __builtin_ctz((unsigned)S);
+            if (__builtin_popcount((unsigned)S) == 1) return leaf_slot[__builtin_ctz((unsigned)S)];
             int Lp = split[S], R = S ^ Lp;
             int a = emit(Lp), b = emit(R);
             int c;
@@ -645,7 +665,7 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
     int kernel = opts.precision == COMET_PREC_SPLIT_BF16 ? KK_GEMM_SPLIT
                  : opts.precision == COMET_PREC_EMU_F64 ? KK_GEMM_EMU : KK_GEMM_F64;
     for (auto &st : P->steps) {
-        if (st.kernel == KK_COPY) continue;
+        if (st.kernel == KK_COPY || st.kernel == KK_REDUCE) continue;
         st.kernel = kernel;
         Slot &sa = P->slots[st.a], &sb = P->slots[st.b], &sc = P->slots[st.c];
         bool free_layout = sc.kind == SLOT_INTER;
@@ -732,6 +752,38 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
         parts_max = std::max(parts_max, ba + bb);
     }
     for (auto &st : P->steps) {
+        if (st.kernel == KK_REDUCE) {   // y[kept] = sum over the private labels of the operand
+            const Slot &sa = P->slots[st.a], &sc = P->slots[st.c];
+            auto ta = label_strides(sa.labels, P->extent), tc = label_strides(sc.labels, P->extent);
+            std::vector<int> kept = sc.labels, summed;
+            for (int l : sa.labels) if (pos_of(kept, l) < 0) summed.push_back(l);
+            std::vector<int64_t> ex(P->extent.begin(), P->extent.end()), s0(L, 0), s1(L, 0), zero(L, 0);
+            GemvParams &v = st.gemv;
+            std::memset(&v, 0, sizeof(v));
+            for (int l : kept) { s0[l] = ta[l]; s1[l] = tc[l]; }
+            fill_radix(&v.n, kept, ex.data(), s0.data(), s1.data());
+            for (int l : summed) { s0[l] = 0; s1[l] = ta[l]; }
+            fill_radix(&v.k, summed, ex.data(), s0.data(), s1.data());
+            v.N = (uint32_t)prod_ext(P->extent, kept);
+            v.K = (uint32_t)prod_ext(P->extent, summed);
+            v.n.total = v.N;
+            v.k.total = v.K;
+            if (prod_ext(P->extent, kept) >= (1ll << 31) || prod_ext(P->extent, summed) >= (1ll << 31)) {
+                *err = "a reduction dimension reaches 2^31"; return COMET_ERR_UNSUPPORTED;
+            }
+            int64_t min_n = INT64_MAX, min_k = INT64_MAX;
+            for (int d = 0; d < v.n.n; ++d) min_n = std::min(min_n, v.n.s0[d]);
+            for (int d = 0; d < v.k.n; ++d) min_k = std::min(min_k, v.k.s1[d]);
+            v.n_fast = min_n < min_k ? 1 : 0;
+            v.nchunks = (v.K + 1023) / 1024;
+            v.v_ones = 1;
+            v.n_batch = 1;
+            v.bv.total = 1;
+            v.by.total = 1;
+            st.ws_partial = parts_base;
+            parts_max = std::max(parts_max, align((size_t)v.nchunks * (size_t)v.N * 8));
+            continue;
+        }
         if (st.kernel != KK_GEMV) continue;
         const int64_t Kx = prod_ext(P->extent, st.form.K);
         const int64_t Nx = prod_ext(P->extent, st.form.M.empty() ? st.form.N : st.form.M);
@@ -745,6 +797,7 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
 
     // ---- precomputed parameter blocks ----
     for (auto &st : P->steps) {
+        if (st.kernel == KK_REDUCE) continue;
         if (st.kernel == KK_COPY) {
             const Slot &sa = P->slots[st.a], &sc = P->slots[st.c];
             auto si = label_strides(sa.labels, P->extent), so2 = label_strides(sc.labels, P->extent);
@@ -879,7 +932,7 @@ std::string describe_plan(const Plan &P) {
         if (i) o << ",";
         o << "{\"kernel\":\"" << (s.kernel == KK_COPY ? "copy" : s.kernel == KK_GEMM_SPLIT ? "gemm_split_bf16"
                                     : s.kernel == KK_GEMM_EMU ? "gemm_emu_bf16x6"
-                                    : s.kernel == KK_GEMV ? "gemv" : "gemm_f64")
+                                    : s.kernel == KK_GEMV ? "gemv" : s.kernel == KK_REDUCE ? "reduce" : "gemm_f64")
           << "\",\"a\":" << s.a << ",\"b\":" << s.b << ",\"c\":" << s.c
           << ",\"a_labels\":" << names(P.slots[s.a].labels);
         if (s.b >= 0) o << ",\"b_labels\":" << names(P.slots[s.b].labels);

@@ -27,7 +27,7 @@ struct ParsedExpr {
 
 comet_status_t parse_expr(const char *s, ParsedExpr *e, std::string *err);
 
-enum KernelKind { KK_GEMM_F64 = 0, KK_GEMM_SPLIT = 1, KK_COPY = 2, KK_GEMM_EMU = 3, KK_GEMV = 4 };
+enum KernelKind { KK_GEMM_F64 = 0, KK_GEMM_SPLIT = 1, KK_COPY = 2, KK_GEMM_EMU = 3, KK_GEMV = 4, KK_REDUCE = 5 };
 
 // One TTGT form of a binary step: which input provides the M (row) group, and the order of
 // the labels inside M, N and K (first = fastest in the merged index).

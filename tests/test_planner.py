@@ -50,8 +50,8 @@ def test_parse_errors_and_codes():
     with pytest.raises(comet.CometError) as e:
         plan("C[i,j] = A[i,k]*B[k,j]", dict(i=3, j=0, k=2))
     assert e.value.name == "COMET_ERR_SHAPE"
-    # repeated label, summation inside one operand
-    for unsup in ["C[i,j] = A[i,i,k]*B[k,j]", "C[i,j] = A[i,k,l]*B[k,j]", "C[i] = A[i,k]"]:
+    # repeated labels
+    for unsup in ["C[i,j] = A[i,i,k]*B[k,j]", "C[i] = A[i,i]"]:
         with pytest.raises(comet.CometError) as e:
             plan(unsup, dict(i=3, j=4, k=5, b=2, l=2))
         assert e.value.name == "COMET_ERR_UNSUPPORTED", unsup
@@ -131,6 +131,18 @@ def test_batch_labels():
     with pytest.raises(comet.CometError) as e:
         comet.BatchedPlan("C[i,j,b] = A[i,k,b]*B[k,j,b]", ["i", "j", "k", "b"], [[2, 2, 2, 2]], "f64")
     assert e.value.name == "COMET_ERR_UNSUPPORTED"
+
+
+def test_private_labels_are_reduced_first():
+    # a label on one operand only (and not on the output) is summed inside that operand first
+    p = plan("C[i] = A[i,k]", dict(i=3, k=5))
+    assert [s["kernel"] for s in p.info["steps"]] == ["reduce"]
+    p = plan("C[i,j] = A[i,k,l]*B[k,j]", dict(i=3, j=4, k=5, l=2))
+    kinds = [s["kernel"] for s in p.info["steps"]]
+    assert kinds[0] == "reduce" and len(kinds) == 2
+    assert p.info["steps"][0]["c_labels"] == ["i", "k"]
+    p = plan("C[i] = A[i]*B[k]", dict(i=3, k=5))
+    assert [s["kernel"] for s in p.info["steps"]] == ["reduce", "gemv"]
 
 
 def test_emulated_fp64_plans():
