@@ -223,6 +223,15 @@ comet_status_t comet_transpose(int rank, const int64_t *extents, const int *perm
                                comet_dtype_t dtype, const void *in, void *out, void *stream);
 
 /*
+ * comet_fill — every element of a dense device buffer set to one value (the ta.fill operation
+ * of the paper's tensor-algebra dialect, Section 5).
+ *   out    device buffer of n elements of dtype (16-byte aligned, else COMET_ERR_ALIGN)
+ *   value  rounded once to dtype
+ * Asynchronous on stream; n = 0 does nothing.
+ */
+comet_status_t comet_fill(void *out, int64_t n, double value, comet_dtype_t dtype, void *stream);
+
+/*
  * Batched triples-like blocks: many small contractions of the same expression with uneven
  * extents, all run by one persistent launch (the 6-D triples output of the CCSD(T) remark in
  * Section 2 is the model: T[a,b,c,i,j,k] = sum_d A[d,a,b,i] * B[c,d,j,k] per block).

@@ -19,7 +19,7 @@ import json
 from . import _lib
 from ._lib import CometError, F32, F64, PREC_NATIVE, PREC_SPLIT_BF16, PREC_EMU_F64, ORDER_NATURAL, ORDER_PLANNED
 
-__all__ = ["Plan", "BatchedPlan", "transpose", "sync_status", "colmajor_empty", "CometError",
+__all__ = ["Plan", "BatchedPlan", "transpose", "fill", "sync_status", "colmajor_empty", "CometError",
            "lib", "version", "PREC_NATIVE", "PREC_SPLIT_BF16", "PREC_EMU_F64", "F32", "F64"]
 
 
@@ -266,6 +266,14 @@ def transpose(x, extents, perm, out=None, stream=None):
     _lib.check(lib().comet_transpose(rank, ext, pm, code, _ptr(x), _ptr(out), _stream_handle(stream)),
                "comet_transpose")
     return out
+
+
+def fill(x, value, stream=None):
+    """comet_fill(): every element of the dense device tensor ``x`` set to ``value``."""
+    import torch
+    code = F32 if x.dtype == torch.float32 else F64
+    _lib.check(lib().comet_fill(_ptr(x), int(x.numel()), float(value), code, _stream_handle(stream)), "comet_fill")
+    return x
 
 
 def profile_enable(on: bool = True):

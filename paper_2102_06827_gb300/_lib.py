@@ -22,7 +22,7 @@ ORDER_PLANNED, ORDER_NATURAL = 0, 1
 EXPORTS = [
     "comet_plan_opts_default", "comet_plan", "comet_plan_workspace", "comet_plan_flops",
     "comet_plan_flops_natural", "comet_plan_describe", "comet_adjoint_expr", "comet_contract", "comet_contract_noalloc", "comet_contract_host",
-    "comet_transpose", "comet_plan_batched", "comet_batched_num_tiles", "comet_batched_set_tile",
+    "comet_transpose", "comet_fill", "comet_plan_batched", "comet_batched_num_tiles", "comet_batched_set_tile",
     "comet_batched_prepare", "comet_contract_batched", "comet_batched_autotune",
     "comet_profile_enable", "comet_profile_read", "comet_sync_status", "comet_plan_destroy", "comet_status_string", "comet_last_error_message",
     "comet_version",
@@ -78,6 +78,7 @@ def load():
     L.comet_contract_host.argtypes = [vp, ctypes.POINTER(vp), vp, ctypes.POINTER(vp), vp, vp, vp]
     L.comet_transpose.argtypes = [ctypes.c_int, i64p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                   vp, vp, vp]
+    L.comet_fill.argtypes = [vp, ctypes.c_int64, ctypes.c_double, ctypes.c_int, vp]
     L.comet_plan_batched.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
                                      ctypes.c_int, i64p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                      ctypes.POINTER(PlanOpts), ctypes.c_int, ctypes.POINTER(vp)]

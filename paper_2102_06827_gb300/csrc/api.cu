@@ -418,6 +418,16 @@ comet_status_t comet_contract_host(comet_plan_t plan, const void *const *host_in
     return comet_sync_status(stream);
 }
 
+comet_status_t comet_fill(void *out, int64_t n, double value, comet_dtype_t dtype, void *stream) {
+    if (n < 0) return COMET_ERR_SHAPE;
+    if (n == 0) return COMET_OK;
+    if (!out) return COMET_ERR_NULL;
+    if (dtype != COMET_F32 && dtype != COMET_F64) return COMET_ERR_DTYPE;
+    if (!aligned16(out)) return COMET_ERR_ALIGN;
+    return cuda_status(launch_fill(out, n, value, (int)dtype_size(dtype), static_cast<cudaStream_t>(stream)),
+                       "fill kernel");
+}
+
 comet_status_t comet_transpose(int rank, const int64_t *extents, const int *perm, comet_dtype_t dtype,
                                const void *in, void *out, void *stream) {
     if (!extents || !perm || !in || !out) return COMET_ERR_NULL;

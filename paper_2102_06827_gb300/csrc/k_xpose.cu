@@ -279,6 +279,27 @@ __global__ void __launch_bounds__(XT) xpose_run_kernel(const XposeParams p) {
     }
 }
 
+// every element of a dense buffer set to one value: grid-stride 16-byte stores, element tail
+template <typename T>
+__global__ void __launch_bounds__(256) fill_kernel(T *out, int64_t n, T value) {
+    constexpr int W = 16 / sizeof(T);
+    Vec<W, T> v;
+#pragma unroll
+    for (int q = 0; q < W; ++q) v.v[q] = value;
+    const int64_t nv = n / W, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += stride)
+        reinterpret_cast<Vec<W, T> *>(out)[i] = v;
+    for (int64_t i = nv * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) out[i] = value;
+}
+
+cudaError_t launch_fill(void *out, int64_t n, double value, int elem_bytes, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int blocks = (int)std::min<int64_t>(152 * 8, (n + 256 * 4 - 1) / (256 * 4));
+    if (elem_bytes == 4) fill_kernel<float><<<blocks, 256, 0, s>>>(reinterpret_cast<float *>(out), n, (float)value);
+    else fill_kernel<double><<<blocks, 256, 0, s>>>(reinterpret_cast<double *>(out), n, value);
+    return cudaGetLastError();
+}
+
 // max |x| over a dense operand: grid-stride 16-byte loads, warp reduction, one atomic per warp
 // on the bit pattern (for non-negative IEEE values the bit order is the numeric order)
 template <typename T>

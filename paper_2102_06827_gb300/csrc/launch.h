@@ -16,6 +16,8 @@ cudaError_t launch_split6(const XposeParams &p, int elem_bytes, int vi, int vo, 
 cudaError_t launch_gemm_f64(const GemmParams &p, int elem_bytes, bool a_kcontig, bool b_kcontig,
                             cudaStream_t s);
 
+cudaError_t launch_fill(void *out, int64_t n, double value, int elem_bytes, cudaStream_t s);
+
 // max |x| of a dense operand into *out_bits (zeroed first), as the bits of an input-precision value
 cudaError_t launch_absmax(const void *x, int64_t n, int elem_bytes, void *out_bits, cudaStream_t s);
 

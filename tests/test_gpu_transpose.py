@@ -119,3 +119,17 @@ def test_sweep_case_full_size_sampled(comet, name):
     ref = oracle.transpose_sampled(host, perm, sel)
     assert got.tobytes() == ref.tobytes()
     del x, y
+
+
+def test_fill(comet):
+    import torch
+    for dt, val in ((torch.float32, 1.25), (torch.float64, -3.5)):
+        for n in (0, 1, 5, 1027, 3_000_001):
+            x = torch.full((max(n, 1),), 7.0, dtype=dt, device="cuda")[:n] if n else torch.empty(0, dtype=dt, device="cuda")
+            comet.fill(x, val)
+            comet.sync_status()
+            assert bool((x == val).all())
+    y = torch.zeros(10, dtype=torch.float32, device="cuda")
+    with pytest.raises(comet.CometError) as e:
+        comet.fill(y[1:], 1.0)   # 4-byte offset: not 16-byte aligned
+    assert e.value.name == "COMET_ERR_ALIGN"
