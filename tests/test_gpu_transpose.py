@@ -133,3 +133,37 @@ def test_fill(comet):
     with pytest.raises(comet.CometError) as e:
         comet.fill(y[1:], 1.0)   # 4-byte offset: not 16-byte aligned
     assert e.value.name == "COMET_ERR_ALIGN"
+
+
+@pytest.mark.parametrize("extents,perm", [((65539, 32771), (1, 0)), ((5, 32771, 16385), (0, 2, 1))])
+def test_above_2_31_elements(comet, extents, perm):
+    # more than 2^31 elements: the 64-bit offset variants of the tile and copy kernels.  Each
+    # input word holds the low 32 bits of its own linear index, so a sampled check sees any
+    # misplaced element.
+    import torch
+    n = int(np.prod(extents))
+    assert n > 2 ** 31
+    x = torch.empty(n, dtype=torch.int32, device="cuda")
+    step = 1 << 28
+    for s in range(0, n, step):
+        c = min(n, s + step) - s
+        x[s:s + c] = torch.arange(s, s + c, dtype=torch.int64, device="cuda").to(torch.int32)
+    xf = x.view(torch.float32)
+    out = torch.empty_like(xf)
+    comet.transpose(xf, extents, perm, out=out)
+    comet.sync_status()
+    g = torch.Generator(device="cuda").manual_seed(61)
+    j = torch.randint(0, n, (1 << 20,), device="cuda", generator=g, dtype=torch.int64)
+    # output index j -> output coordinates (column-major over out extents) -> input linear index
+    oext = [extents[p] for p in perm]
+    rem, i = j.clone(), torch.zeros_like(j)
+    istr = np.cumprod([1] + list(extents[:-1])).tolist()
+    for d in range(len(oext)):
+        coord = rem % oext[d]
+        rem = rem // oext[d]
+        i += coord * int(istr[perm[d]])
+    got = out.view(torch.int32)[j]
+    want = i.to(torch.int32)
+    assert bool((got == want).all())
+    del x, out
+    torch.cuda.empty_cache()
