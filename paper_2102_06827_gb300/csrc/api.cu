@@ -453,6 +453,10 @@ comet_status_t comet_transpose(int rank, const int64_t *extents, const int *perm
     double eff;
     setup_xpose(rank, extents, si, so, (int)dtype_size(dtype), &x, &vi, &vo, &eff);
     if (x.u.total >= (1u << 31) || x.v.total >= (1u << 31) || x.r.total >= (1u << 31)) return COMET_ERR_SHAPE;
+    if ((uint64_t)x.tiles_u * x.tiles_v * x.tiles_w >= (1ull << 31)) {
+        set_error("transpose: more than 2^31 tiles");
+        return COMET_ERR_SHAPE;
+    }
     x.in = in; x.out = out; x.alpha = 1.0; x.beta = 0.0;
     ProfScope ps(PK_TRANSPOSE, static_cast<cudaStream_t>(stream));
     return cuda_status(launch_move(x, (int)dtype_size(dtype), vi, vo, static_cast<cudaStream_t>(stream)),

@@ -141,7 +141,22 @@ __global__ void __launch_bounds__(XT, 8) xpose_tile_kernel(const XposeParams p) 
         const uint32_t lanes = p.ll, rpp = p.rpp_l;
         const uint32_t r0 = fd_div(t, p.fd_ll);
         const uint32_t u = (t - r0 * lanes) * VI;
-        if (r0 < rpp && u < nu) {
+        if constexpr (VI == 1) {
+            // element loads as asynchronous copies straight into the tile: every row of the
+            // thread is in flight at once and no register holds the data
+            if (r0 < rpp && u < nu) {
+                const T *__restrict__ src = reinterpret_cast<const T *>(p.in) + (int64_t)u * su;
+                const uint32_t dst = (uint32_t)__cvta_generic_to_shared(buf + u);
+                for (uint32_t row = r0; row < rows_v; row += rpp) {
+                    const uint32_t d = dst + row * pitch * (uint32_t)sizeof(T);
+                    if (sizeof(T) == 4)
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src + in_row[row]) : "memory");
+                    else
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src + in_row[row]) : "memory");
+                }
+            }
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+        } else if (r0 < rpp && u < nu) {
             const T *__restrict__ src = reinterpret_cast<const T *>(p.in) + (int64_t)u * su;
             T *dst = buf + u;
             // four vectors per batch keep the kernel within 32 registers, so eight blocks fit on
@@ -216,6 +231,28 @@ __global__ void __launch_bounds__(XT, 6) xpose_copy_kernel(const XposeParams p) 
     if (!(r0 < rpp && u < nu)) return;
     const T *__restrict__ src = in + (int64_t)u * su;
     const int64_t uo = (int64_t)u * so;
+    if constexpr (VW == 1) {
+        // element-wise rows: every load of the thread goes out at once as an asynchronous copy
+        // into its own slots of the tile (no register holds the data), then the thread stores
+        // what it copied; no other thread reads these slots, so no block barrier is needed
+        extern __shared__ __align__(16) unsigned char csm[];
+        T *stage = reinterpret_cast<T *>(csm);
+        const uint32_t base = (uint32_t)__cvta_generic_to_shared(stage + u);
+        for (uint32_t row = r0; row < nw; row += rpp) {
+            const uint32_t d = base + row * tu * (uint32_t)sizeof(T);
+            if (sizeof(T) == 4)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src + row_in[row]) : "memory");
+            else
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src + row_in[row]) : "memory");
+        }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+#pragma unroll 4
+        for (uint32_t row = r0; row < nw; row += rpp) {
+            T xs[1] = {stage[row * tu + u]};
+            emit<OP, T, 1>(p, (int64_t)row_out[row] + uo, xs, e);
+        }
+        return;
+    }
     // rows r0, r0 + rpp, ...: a ring of UB loads stays in flight; each store is followed by the
     // load of the row UB passes ahead into the register it freed
     Vec<VW, T> x[UB];
@@ -361,12 +398,13 @@ static cudaError_t launch_op(const XposeParams &p, int vi, int vo, cudaStream_t 
             else xpose_run_kernel<OP, T, 1><<<g, XT, 0, s>>>(p);
             return cudaGetLastError();
         }
+        const size_t stage = (size_t)p.tu * p.tw * sizeof(T);   // element-wise rows stage in shared memory
         if (p.off32) {
             if (wide) xpose_copy_kernel<OP, T, W, int32_t><<<g, XT, 0, s>>>(p);
-            else xpose_copy_kernel<OP, T, 1, int32_t><<<g, XT, 0, s>>>(p);
+            else xpose_copy_kernel<OP, T, 1, int32_t><<<g, XT, stage, s>>>(p);
         } else {
             if (wide) xpose_copy_kernel<OP, T, W, int64_t><<<g, XT, 0, s>>>(p);
-            else xpose_copy_kernel<OP, T, 1, int64_t><<<g, XT, 0, s>>>(p);
+            else xpose_copy_kernel<OP, T, 1, int64_t><<<g, XT, stage, s>>>(p);
         }
         return cudaGetLastError();
     }

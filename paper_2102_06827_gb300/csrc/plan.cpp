@@ -269,6 +269,8 @@ void setup_xpose(int rank, const int64_t *ext_in, const int64_t *sin_in,
     const int vc = std::min(vi, vo);
     *vec_in = same ? vc : vi;
     *vec_out = same ? -vc : vo;   // negative = copy mode (no shared-memory transposition)
+    if (same && !p->single_run && vc == 1)   // element-wise copy rows stage in shared memory:
+        tw = std::min<uint32_t>(tw, std::max<uint32_t>(1, TILE / tu));   // keep the tile at TILE
     p->tu = tu; p->tv = tv; p->tw = tw;
     p->ll = (tu + *vec_in - 1) / *vec_in;
     p->sl = same ? 1 : (tv + vo - 1) / vo;

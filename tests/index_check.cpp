@@ -73,6 +73,7 @@ static bool replay(const XposeParams &p, int vi, int vo, int64_t n_in, int64_t n
                     if (c >= 0 && c < n_out_span) { CHECK(src_of_out[c] == -1, "written twice"); src_of_out[c] = a; }
                 }
             };
+            CHECK(VW != 1 || (uint64_t)tu * tw * 8 <= 48 * 1024, "copy-mode stage above 48 KB of shared memory");
             const uint32_t lanes = p.ll;
             if (p.single_run) {
                 CHECK(nw == 1 && p.r.total == 1, "long-row copy with several rows");
@@ -240,6 +241,35 @@ int main() {
                 }
                 ++cases;
             }
+        }
+    }
+    // launch limits on large shapes (extents 8..256, the transpose workload's range): grid below
+    // 2^31 blocks, the transposing tile within its 96 KB of shared memory, the element-wise copy
+    // stage within the default 48 KB
+    for (int it = 0; it < 20000 && fails == 0; ++it) {
+        const int rank = it % 2 ? 6 : 4;
+        int64_t ext[8], si[8], so[8], so_out[8];
+        int perm[8];
+        long double tot = 1;
+        for (int d = 0; d < rank; ++d) { ext[d] = 8 + rng() % 249; tot *= ext[d]; }
+        if (tot > 2147483648.0L) continue;   // the workload's shapes stay at or below 2 GiB
+        for (int d = 0; d < rank; ++d) perm[d] = d;
+        std::shuffle(perm, perm + rank, rng);
+        int64_t s = 1;
+        for (int d = 0; d < rank; ++d) { si[d] = s; s *= ext[d]; }
+        s = 1;
+        for (int d = 0; d < rank; ++d) { so_out[d] = s; s *= ext[perm[d]]; }
+        for (int d = 0; d < rank; ++d) so[perm[d]] = so_out[d];
+        for (int es : {4, 8}) {
+            XposeParams p;
+            int vi, vo;
+            double eff;
+            setup_xpose(rank, ext, si, so, es, &p, &vi, &vo, &eff);
+            const uint64_t grid = (uint64_t)p.tiles_u * p.tiles_v * p.tiles_w;
+            CHECK(grid < (1ull << 31), "grid of %llu blocks", (unsigned long long)grid);
+            if (vo > 0) CHECK(xpose_smem_bytes(p, es) <= 96 * 1024, "tile shared memory %u", xpose_smem_bytes(p, es));
+            if (vo == -1 && !p.single_run)
+                CHECK((uint64_t)p.tu * p.tw * es <= 48 * 1024, "copy stage of %llu bytes", (unsigned long long)p.tu * p.tw * es);
         }
     }
     // split pre-pass layout: [rows][kpad] with kpad padding (outputs only partly covered)
