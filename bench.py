@@ -540,6 +540,43 @@ def run_reference(a):
     return 0
 
 
+# ---- replicas: one process per GPU, no collective on the data path ---------------------------
+class Replicas:
+    """The rank layout of a torchrun launch (RANK / LOCAL_RANK / WORLD_SIZE): every rank runs its
+    own copy of the workload; the job's time is the slowest rank's (max over ranks) and its value
+    all ranks' work over that time.  backend: "nccl" on GPUs, "gloo" in the CPU tests."""
+
+    def __init__(self, backend: str, device=None):
+        import torch.distributed as dist
+        self.dist = dist
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.device = device
+        if self.world > 1 and not dist.is_initialized():
+            dist.init_process_group(backend)
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def max(self, x: float) -> float:
+        if self.world == 1:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def throughput(self, units_per_rank: float, seconds: float) -> float:
+        """whole-job units per second: every rank's units over the slowest rank's time"""
+        return self.world * units_per_rank / self.max(seconds)
+
+    def close(self):
+        if self.world > 1 and self.dist.is_initialized():
+            self.dist.destroy_process_group()
+
+
 # ---- our arm -------------------------------------------------------------------------------------
 def main():
     a = args_parse()
@@ -557,27 +594,15 @@ def main():
         return run_ablation(a)
     import numpy as np
     import torch
-    import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    reps = Replicas("nccl", dev)
+    world, rank = reps.world, reps.rank
     import paper_2102_06827_gb300 as comet
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier = reps.barrier
+    max_over_ranks = reps.max
 
     stream = torch.cuda.current_stream()
     # ---------------- split-BF16 path (the headline) ----------------
@@ -749,8 +774,7 @@ def main():
                 "e2e": e2e, "gpu_launches": launches, "clocks": clk,
                 "dtype_note": "bf16 x bf16 tensor-core products of a 3-way split, fp32 accumulation"}
         print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    reps.close()
     return 0
 
 
