@@ -51,7 +51,7 @@ def args_parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-case", default=None, choices=["split", "f64", "emu", "transpose", "triples"],
+    ap.add_argument("--profile-case", default=None, choices=["split", "f64", "emu", "transpose", "triples", "gemv"],
                     help="run one warm-up and one timed launch of a smaller case (for ncu) and exit")
     ap.add_argument("--pc-extents", default="64,128,128,256", help="transpose profile case extents")
     ap.add_argument("--pc-perm", default="3,1,0,2", help="transpose profile case permutation")
@@ -365,6 +365,21 @@ def run_profile_case(case: str, a=None) -> int:
     import paper_2102_06827_gb300 as comet
     import synth
     dev = torch.device("cuda", 0)
+    if case == "gemv":   # the two tensor-times-vector steps of Table 1 row 1 at o=64 v=192 (FP32, split)
+        e = "X[i,a] = A[c,d,m,n] * B[i,n,a,d] * C[m,c]"
+        ext = dict(c=192, d=192, m=64, n=64, i=64, a=192)
+        ops = [("c", "d", "m", "n"), ("i", "n", "a", "d"), ("m", "c")]
+        ins = [synth.torch_uniform(7, t, math.prod(ext[l] for l in o), dev, dtype=torch.float32)
+               for t, o in enumerate(ops)]
+        plan = comet.Plan(e, ext, torch.float32, precision="split_bf16")
+        X = torch.empty(64 * 192, dtype=torch.float32, device=dev)
+        ws = plan.workspace(dev)
+        for _ in range(2):
+            plan.contract(ins, X, ws)
+        comet.sync_status()
+        print(json.dumps({"case": case, "steps": [s["kernel"] for s in plan.info["steps"]],
+                          "large_operand_bytes": 4 * 192 * 192 * 64 * 64}))
+        return 0
     if case == "triples":   # 512 of the 4096 triples blocks (same extent generator), split, reduce mode
         import numpy as np
         sys.path.insert(0, os.path.join(ROOT, "tests"))

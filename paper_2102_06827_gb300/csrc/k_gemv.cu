@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(gv::T) gemv_partial_kernel(const GemvParams p)
         Acc<T> a;
         if ((uint32_t)tn < nn) {
             const T *x = X + n_off[tn];
-#pragma unroll 4
+#pragma unroll 8
             for (uint32_t k = tk; k < nk; k += 2) a.add(vk[k], x[k_off[k]]);
         }
         if (tk == 1) red[tn] = a.value();
