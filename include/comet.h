@@ -101,10 +101,14 @@ typedef struct {
     int64_t timeout_ms;         /* device-side wait limit; 0 = default (2000 ms) */
     int debug_flags;            /* bit 0: withhold one operand load in the split GEMM so that
                                    its wait runs out (fault-injection test); others reserved */
+    int ksplit;                 /* split path: K slices per output tile; 0 = planner's choice
+                                   (more slices when a GEMM has fewer tiles than the GPU has
+                                   SMs; their FP32 partials are summed by a second kernel),
+                                   1 = off, k > 1 = k slices */
 } comet_plan_opts_t;
 
 /* Fills *opts with the defaults: NATIVE precision, planned order, alpha 1, no cap, planner's
- * form, kc 0, default timeout, no debug flags. */
+ * form, kc 0, default timeout, no debug flags, planner's K slicing. */
 void comet_plan_opts_default(comet_plan_opts_t *opts);
 
 /*

@@ -254,7 +254,8 @@ static comet_status_t run_plan(const Plan &P, const void *const *inputs, void *o
             } else {
                 ProfScope ps(PK_SPLIT, stream);
                 e = launch_gemm_split(g, w + st.ws_parts_a, w + st.ws_parts_b, st.kpad, sc_a, sc_b,
-                                      P.opts.kc, es, P.opts.debug_flags, stream, 0);
+                                      P.opts.kc, es, P.opts.debug_flags, stream, 0, st.ksplit,
+                                      reinterpret_cast<float *>(w + st.ws_ksplit));
                 if (e != cudaSuccess) return cuda_status(e, "split gemm kernel");
             }
         }

@@ -56,6 +56,9 @@ constexpr int MAX_KC = 1024;                    // exactness limit of the hh chu
 struct SplitArgs {
     uint32_t m_tiles, n_tiles, nkb;
     uint32_t kc_blocks;          // K blocks (of BK) per exact chunk
+    uint32_t ksplit;             // K slices (1 = whole K per tile; > 1: FP32 partials to `partial`)
+    uint32_t kslice_blocks;      // K blocks per slice
+    float *partial;              // ksplit x N x M partial sums (scaled by 2^(eA+eB)), m fastest
     int debug_flags;
     const void *scale_a;         // bits of max |A|, max |B| (input precision)
     const void *scale_b;
@@ -78,7 +81,7 @@ __device__ __forceinline__ int exp_of_max(const void *bits) {
     }
 }
 
-template <typename TOut>
+template <typename TOut, bool KSPLIT>
 __global__ void __launch_bounds__(split::THREADS, 1)
     gemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const GemmParams p, const SplitArgs x) {
@@ -97,7 +100,20 @@ __global__ void __launch_bounds__(split::THREADS, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t tmo = (uint64_t)p.timeout_ns;
-    const uint32_t n_tiles_total = x.m_tiles * x.n_tiles;
+    const uint32_t n_tiles_total = x.m_tiles * x.n_tiles * (KSPLIT ? x.ksplit : 1u);
+    // work item t: K slice t / (m_tiles n_tiles), output tile t % (m_tiles n_tiles)
+    auto kslice = [&](uint32_t t, uint32_t &kb0, uint32_t &kb1) -> uint32_t {
+        if constexpr (!KSPLIT) {
+            kb0 = 0;
+            kb1 = x.nkb;
+            return 0;
+        } else {
+            const uint32_t ks = t / (x.m_tiles * x.n_tiles);
+            kb0 = ks * x.kslice_blocks;
+            kb1 = min(x.nkb, kb0 + x.kslice_blocks);
+            return ks;
+        }
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -121,6 +137,7 @@ __global__ void __launch_bounds__(split::THREADS, 1)
     };
     // tile t -> (m tile, n tile): bands of 16 m-tiles, n-major inside a band, for L2 reuse
     auto tile_coords = [&](uint32_t t, uint32_t &mt, uint32_t &nt) {
+        if constexpr (KSPLIT) t %= x.m_tiles * x.n_tiles;
         const uint32_t G = 16;
         uint32_t band = t / (G * x.n_tiles);
         uint32_t base = band * G;
@@ -137,9 +154,10 @@ __global__ void __launch_bounds__(split::THREADS, 1)
             bool ok = true;
             bool injected = false;
             for (uint32_t t = blockIdx.x; t < n_tiles_total && ok; t += gridDim.x) {
-                uint32_t mt, nt;
+                uint32_t mt, nt, kb0, kb1;
                 tile_coords(t, mt, nt);
-                for (uint32_t kb = 0; kb < x.nkb; ++kb, ++it) {
+                kslice(t, kb0, kb1);
+                for (uint32_t kb = kb0; kb < kb1; ++kb, ++it) {
                     const uint32_t s = it % STAGES, round = it / STAGES;
                     if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1, tmo, abort_flag)) {
                         fail(); ok = false; break;
@@ -169,8 +187,10 @@ __global__ void __launch_bounds__(split::THREADS, 1)
             uint32_t it = 0, chunk = 0;
             bool ok = true;
             for (uint32_t t = blockIdx.x; t < n_tiles_total && ok; t += gridDim.x) {
-                for (uint32_t kb = 0; kb < x.nkb; ++kb, ++it) {
-                    const uint32_t kin = kb % x.kc_blocks;
+                uint32_t kb0, kb1;
+                kslice(t, kb0, kb1);
+                for (uint32_t kb = kb0; kb < kb1; ++kb, ++it) {
+                    const uint32_t kin = (KSPLIT ? kb - kb0 : kb) % x.kc_blocks;
                     if (kin == 0) {
                         // the epilogue must have drained the previous chunk
                         if (chunk > 0 && !mbar_wait(tempty, (chunk - 1) & 1, tmo, abort_flag)) {
@@ -200,7 +220,7 @@ __global__ void __launch_bounds__(split::THREADS, 1)
                         mma_bf16(p0, ah, bh, idesc, acc);    // the exact leading product
                     }
                     mma_commit(&empty[s]);   // frees the stage once these MMAs have read it
-                    if (kin == x.kc_blocks - 1 || kb == x.nkb - 1) {
+                    if (kin == x.kc_blocks - 1 || kb == kb1 - 1) {
                         mma_commit(tfull);   // chunk complete: P0 and P1 ready to drain
                         ++chunk;
                     }
@@ -218,13 +238,14 @@ __global__ void __launch_bounds__(split::THREADS, 1)
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
         const int e_sum = exp_of_max<TOut>(x.scale_a) + exp_of_max<TOut>(x.scale_b);
         const double scale = ldexp(p.alpha, e_sum);
-        const uint32_t nchunks = (x.nkb + x.kc_blocks - 1) / x.kc_blocks;
         uint32_t chunk = 0;
         bool dead = false;   // once set, the warp keeps pace with the barriers but does no work
         TOut *C = reinterpret_cast<TOut *>(p.C);
         for (uint32_t t = blockIdx.x; t < n_tiles_total; t += gridDim.x) {
-            uint32_t mt, nt;
+            uint32_t mt, nt, kb0, kb1;
             tile_coords(t, mt, nt);
+            const uint32_t ks = kslice(t, kb0, kb1);
+            const uint32_t nchunks = (kb1 - kb0 + x.kc_blocks - 1) / x.kc_blocks;
             // column offsets of this tile in C (all eight epilogue warps always meet here)
             named_bar_sync(1, 32 * EPI_WARPS);
             {
@@ -262,6 +283,18 @@ __global__ void __launch_bounds__(split::THREADS, 1)
             }
             if (dead) continue;
             const uint32_t m = mt * BM + quad * 32 + lane;
+            if constexpr (KSPLIT) {   // K slice partial: scaled sums to P[ks][n][m] (m fastest, coalesced)
+                if (m < p.M) {
+                    const uint32_t n_valid = min((uint32_t)BN, p.N - nt * BN);
+                    const int n_here = (int)min(128u, n_valid > (uint32_t)(half * 128) ? n_valid - half * 128 : 0u);
+                    const float sc = (float)ldexp(1.0, e_sum);
+                    float *P = x.partial + ((size_t)ks * p.N + nt * BN + half * 128) * p.M + m;
+#pragma unroll
+                    for (int j = 0; j < 128; ++j)
+                        if (j < n_here) P[(size_t)j * p.M] = sc * S[j];
+                }
+                continue;
+            }
             if (m < p.M) {
                 int64_t r0 = 0, c_row = 0;
                 radix_offsets(p.ma, m, r0, c_row);
@@ -289,6 +322,22 @@ __global__ void __launch_bounds__(split::THREADS, 1)
     __syncthreads();
     tc_fence_after();
     if (warp == 1) tmem_dealloc(tmem_base, TMEM_COLS);
+}
+
+// K-slice partials -> C: C[m, n] = alpha * sum_ks P[ks][n][m] (+ beta C), through C's strides
+template <typename TOut>
+__global__ void __launch_bounds__(256) split_reduce_kernel(const GemmParams p, const float *P, uint32_t ksplit) {
+    const uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= (uint64_t)p.M * p.N) return;
+    const uint32_t n = (uint32_t)(i / p.M), m = (uint32_t)(i - (uint64_t)n * p.M);
+    double s = 0.0;
+    for (uint32_t k = 0; k < ksplit; ++k) s += (double)P[((size_t)k * p.N + n) * p.M + m];
+    int64_t a, cm, b, cn;
+    radix_offsets(p.ma, m, a, cm);
+    radix_offsets(p.nb, n, b, cn);
+    TOut *c = reinterpret_cast<TOut *>(p.C) + cm + cn;
+    const double r = p.alpha * s;
+    *c = (TOut)(p.beta != 0.0 ? r + p.beta * (double)*c : r);
 }
 
 // ---- host side --------------------------------------------------------------------------------
@@ -334,9 +383,23 @@ static int sm_count() {
     return n;
 }
 
+// the shared-memory attribute is set once per kernel instantiation
+template <typename TOut, bool KSPLIT>
+static void launch_split_kernel(const CUtensorMap &ta, const CUtensorMap &tb, const GemmParams &p,
+                                const SplitArgs &x, int ctas, cudaStream_t s) {
+    static const bool attr = [] {
+        cudaFuncSetAttribute(gemm_split_kernel<TOut, KSPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             split::SMEM_BYTES);
+        return true;
+    }();
+    (void)attr;
+    gemm_split_kernel<TOut, KSPLIT><<<ctas, split::THREADS, split::SMEM_BYTES, s>>>(ta, tb, p, x);
+}
+
 cudaError_t launch_gemm_split(const GemmParams &p, const void *parts_a, const void *parts_b,
                               int64_t kpad, const void *scale_a, const void *scale_b, int64_t kc,
-                              int out_bytes, int debug_flags, cudaStream_t s, int max_ctas) {
+                              int out_bytes, int debug_flags, cudaStream_t s, int max_ctas,
+                              uint32_t ksplit, float *partial) {
     using namespace split;
     if (p.M == 0 || p.N == 0) return cudaSuccess;
     CUtensorMap ta, tb;
@@ -352,24 +415,27 @@ cudaError_t launch_gemm_split(const GemmParams &p, const void *parts_a, const vo
     x.debug_flags = debug_flags;
     x.scale_a = scale_a;
     x.scale_b = scale_b;
-    uint32_t tiles = x.m_tiles * x.n_tiles;
+    if (ksplit < 1 || !partial) ksplit = 1;
+    x.kslice_blocks = (x.nkb + ksplit - 1) / ksplit;    // at least one K block per slice
+    x.ksplit = (x.nkb + x.kslice_blocks - 1) / x.kslice_blocks;
+    x.partial = partial;
+    uint32_t tiles = x.m_tiles * x.n_tiles * x.ksplit;
     int ctas = sm_count();
     if (max_ctas > 0 && max_ctas < ctas) ctas = max_ctas;
     if ((uint32_t)ctas > tiles) ctas = (int)tiles;
-    static bool attr_set[2] = {false, false};
     if (out_bytes == 8) {
-        if (!attr_set[1]) {
-            cudaFuncSetAttribute(gemm_split_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-            attr_set[1] = true;
-        }
-        gemm_split_kernel<double><<<ctas, THREADS, SMEM_BYTES, s>>>(ta, tb, p, x);
+        if (x.ksplit > 1) launch_split_kernel<double, true>(ta, tb, p, x, ctas, s);
+        else launch_split_kernel<double, false>(ta, tb, p, x, ctas, s);
     } else {
-        if (!attr_set[0]) {
-            cudaFuncSetAttribute(gemm_split_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-            attr_set[0] = true;
-        }
-        gemm_split_kernel<float><<<ctas, THREADS, SMEM_BYTES, s>>>(ta, tb, p, x);
+        if (x.ksplit > 1) launch_split_kernel<float, true>(ta, tb, p, x, ctas, s);
+        else launch_split_kernel<float, false>(ta, tb, p, x, ctas, s);
     }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || x.ksplit == 1) return e;
+    const uint64_t n = (uint64_t)p.M * p.N;
+    const uint32_t blocks = (uint32_t)((n + 255) / 256);
+    if (out_bytes == 8) split_reduce_kernel<double><<<blocks, 256, 0, s>>>(p, partial, x.ksplit);
+    else split_reduce_kernel<float><<<blocks, 256, 0, s>>>(p, partial, x.ksplit);
     return cudaGetLastError();
 }
 

@@ -21,9 +21,12 @@ cudaError_t launch_fill(void *out, int64_t n, double value, int elem_bytes, cuda
 // max |x| of a dense operand into *out_bits (zeroed first), as the bits of an input-precision value
 cudaError_t launch_absmax(const void *x, int64_t n, int elem_bytes, void *out_bits, cudaStream_t s);
 
+// ksplit > 1: K sliced over more work items, FP32 partials in `partial` (ksplit x M x N floats)
+// summed by a reduce kernel into C
 cudaError_t launch_gemm_split(const GemmParams &p, const void *parts_a, const void *parts_b,
                               int64_t kpad, const void *scale_a, const void *scale_b, int64_t kc,
-                              int out_bytes, int debug_flags, cudaStream_t s, int max_ctas);
+                              int out_bytes, int debug_flags, cudaStream_t s, int max_ctas,
+                              uint32_t ksplit = 1, float *partial = nullptr);
 
 cudaError_t launch_gemm_emu(const GemmParams &p, const void *parts_a, const void *parts_b, int64_t kpad,
                             const void *scale_a, const void *scale_b, int debug_flags, cudaStream_t s,

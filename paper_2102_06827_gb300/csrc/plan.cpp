@@ -751,7 +751,20 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
         size_t ba = align(planes * rows_a * st.kpad * 2), bb = align(planes * rows_b * st.kpad * 2);
         st.ws_parts_a = parts_base;
         st.ws_parts_b = parts_base + ba;
-        parts_max = std::max(parts_max, ba + bb);
+        // K slices: a split GEMM with fewer output tiles than SMs spreads K over more work items
+        // (slices of at least 256 K values, partials at most 256 MB)
+        st.ksplit = 1;
+        if (st.kernel == KK_GEMM_SPLIT && opts.ksplit != 1) {
+            const int64_t tiles = ((rows_a + 127) / 128) * ((rows_b + 255) / 256);
+            const int64_t nkb = (Kx + 31) / 32;
+            int64_t k = opts.ksplit > 1 ? opts.ksplit
+                                        : std::min<int64_t>({(152 + tiles - 1) / tiles, nkb / 8, 16});
+            while (k > 1 && (double)k * rows_a * rows_b * 4 > 256.0 * (1 << 20)) --k;
+            st.ksplit = (uint32_t)std::max<int64_t>(1, std::min<int64_t>(k, nkb));
+        }
+        st.ws_ksplit = parts_base + ba + bb;
+        const size_t bk = st.ksplit > 1 ? align((size_t)st.ksplit * rows_a * rows_b * 4) : 0;
+        parts_max = std::max(parts_max, ba + bb + bk);
     }
     for (auto &st : P->steps) {
         if (st.kernel == KK_REDUCE) {   // y[kept] = sum over the private labels of the operand
@@ -944,7 +957,8 @@ std::string describe_plan(const Plan &P) {
               << ",\"K\":" << names(s.form.K) << ",\"batch\":" << names(s.form.Bt)
               << ",\"n_forms\":" << s.n_forms << ",\"form_index\":" << s.form_index
               << ",\"cost_s\":" << s.form.cost << ",\"pre_bytes\":" << s.form.pre_bytes
-              << ",\"eff_store\":" << s.form.eff_store << ",\"flops\":" << s.flops;
+              << ",\"eff_store\":" << s.form.eff_store << ",\"flops\":" << s.flops
+              << ",\"ksplit\":" << s.ksplit;
         }
         o << "}";
     }
@@ -991,4 +1005,5 @@ extern "C" void comet_plan_opts_default(comet_plan_opts_t *o) {
     o->kc = 0;
     o->timeout_ms = 0;
     o->debug_flags = 0;
+    o->ksplit = 0;
 }

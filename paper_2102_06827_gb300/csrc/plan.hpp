@@ -62,6 +62,8 @@ struct Step {
     size_t ws_parts_a = 0, ws_parts_b = 0;
     size_t ws_scales = 0;        // two 8-byte words: max |A|, max |B| of the step's operands
     int64_t kpad = 0;
+    uint32_t ksplit = 1;         // split GEMM: K slices per output tile
+    size_t ws_ksplit = 0;        // workspace offset of the slices' FP32 partials
     // precomputed parameter blocks (pointers filled at launch)
     GemmParams gemm;             // for both GEMM kernels (offsets in elements)
     XposeParams pre_a, pre_b;    // split pre-passes (A then B operand)

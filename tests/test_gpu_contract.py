@@ -202,3 +202,21 @@ def test_timeout_surfaces_and_context_survives(comet):
     assert err.value.name == "COMET_ERR_TIMEOUT"
     C, _ = run(comet, e, ext, arrays, np.float32, precision="split_bf16")
     assert np.array_equal(C, oracle.einsum(e, *arrays))
+
+
+@pytest.mark.parametrize("ksplit", [0, 3, 16])
+def test_split_k_slices(comet, ksplit):
+    # a GEMM with few output tiles: K sliced over more work items, FP32 partials summed by a
+    # second kernel (0 = the planner's choice); alpha and += go through the reduce kernel
+    e = "C[m,n] = A[k,m] * B[k,n]"
+    ext = dict(m=300, n=200, k=3001)
+    arrays = inputs(e, ext, 13)
+    ref = oracle.einsum(e, *arrays)
+    C, p = run(comet, e, ext, arrays, np.float32, precision="split_bf16", ksplit=ksplit)
+    assert p.info["steps"][0]["ksplit"] > 1
+    assert normwise(C, ref) <= TOL_SPLIT
+    ints = inputs(e, ext, 14, kind="int", lo=-2, hi=2)
+    C0 = synth.tensor((300, 200), 14, 7, kind="int")
+    C, _ = run(comet, "C[m,n] += 2.0 * A[k,m] * B[k,n]", ext, ints, np.float32, precision="split_bf16",
+               ksplit=ksplit, out_init=C0)
+    assert np.array_equal(C, C0 + 2.0 * oracle.einsum(e, *ints))
