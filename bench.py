@@ -748,9 +748,25 @@ def main():
     for _ in range(a.e2e_steps):
         plan.contract_host([hA, hB], hC, [dA, dB], dC, ws)
     t_e2e = max_over_ranks(time.perf_counter() - t0)
+    # the host result against the device result of the timed steps (the slices take their own
+    # operand scales, so the two agree to the split path's error, not bitwise)
+    e2e_diff = float((hC.to(dev) - C).abs().max() / C.abs().max())
+    # the same call with the slice pipeline switched off (copies, contraction, copy back in order)
+    plan_serial = comet.Plan(EXPR, EXT, torch.float32, precision="split_bf16", host_slices=1)
+    plan_serial.contract_host([hA, hB], hC, [dA, dB], dC, ws)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(a.e2e_steps):
+        plan_serial.contract_host([hA, hB], hC, [dA, dB], dC, ws)
+    t_serial = max_over_ranks(time.perf_counter() - t0)
+    plan_serial.close()
     e2e = {"value": world * flops * a.e2e_steps / t_e2e / 1e9, "unit": "GFLOP/s",
            "h2d_bytes_per_step": 2 * N_ELEM * 4, "d2h_bytes_per_step": N_ELEM * 4,
-           "steps": a.e2e_steps, "api": "comet_contract_host (pinned host buffers)"}
+           "steps": a.e2e_steps, "api": "comet_contract_host (pinned host buffers)",
+           "ms_per_step": 1e3 * t_e2e / a.e2e_steps, "host_pipe": plan.info.get("host_pipe"),
+           "max_rel_diff_vs_device": e2e_diff,
+           "serial_value": world * flops * a.e2e_steps / t_serial / 1e9,
+           "serial_ms_per_step": 1e3 * t_serial / a.e2e_steps}
 
     # ---------------- CPU baseline (oracle) and the stated error ----------------
     cpu, err = None, None

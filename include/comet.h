@@ -105,10 +105,14 @@ typedef struct {
                                    (more slices when a GEMM has fewer tiles than the GPU has
                                    SMs; their FP32 partials are summed by a second kernel),
                                    1 = off, k > 1 = k slices */
+    int host_slices;            /* comet_contract_host on a one-step split or emulated plan:
+                                   slices of the larger operand that are copied in, multiplied
+                                   and copied back in a pipeline; 0 = planner's choice, 1 = off
+                                   (copy all inputs, contract, copy back), s > 1 = s slices */
 } comet_plan_opts_t;
 
 /* Fills *opts with the defaults: NATIVE precision, planned order, alpha 1, no cap, planner's
- * form, kc 0, default timeout, no debug flags, planner's K slicing. */
+ * form, kc 0, default timeout, no debug flags, planner's K slicing and host slices. */
 void comet_plan_opts_default(comet_plan_opts_t *opts);
 
 /*
@@ -125,10 +129,12 @@ void comet_plan_opts_default(comet_plan_opts_t *opts);
  *   opts       NULL = defaults.
  *   out_plan   receives the plan; release it with comet_plan_destroy().
  *
- * Supported: one operand (scaled copy / transpose, ta.copy) and two or more operands with
- * every label in exactly two of {operands, output} (a binary tree of ta.tc steps).
- * Labels in all three tensors (batch labels), repeated labels inside one tensor and labels
- * summed inside a single operand give COMET_ERR_UNSUPPORTED.  No device work, no GPU needed.
+ * Supported: one operand (scaled copy / transpose, ta.copy) and two or more operands joined
+ * in a binary tree of ta.tc steps.  A label on both operands of a step and on its result is a
+ * batch label (the step's GEMM runs once per batch index); a label on one operand only, and
+ * not on the result, is summed inside that operand by a reduction step before the tree.
+ * Repeated labels inside one tensor (diagonals) give COMET_ERR_UNSUPPORTED.  No device work,
+ * no GPU needed.
  */
 comet_status_t comet_plan(const char *expr, const comet_extent_t *extents, int n_extents,
                           const comet_dtype_t *dtypes, int n_dtypes,
@@ -203,11 +209,21 @@ comet_status_t comet_contract_noalloc(comet_plan_t plan, const void *const *inpu
 
 /*
  * comet_contract_host — the same evaluation from host buffers: copies every input from host
- * to the caller's device buffers, runs comet_contract() and copies the output back, all on
- * `stream`, then synchronises the stream.  host_* may be pageable or pinned host memory;
- * dev_* are caller-owned device buffers of the operands' sizes.  For "+=" / "-=" the host
- * output is copied to the device first.  Returns the first error, including a device status
- * word set by a kernel (as comet_sync_status()).
+ * to the caller's device buffers, runs the plan and copies the output back, then synchronises
+ * `stream`.  host_* may be pageable or pinned host memory; dev_* are caller-owned device
+ * buffers of the operands' sizes (16-byte aligned).  For "+=" / "-=" the host output is copied
+ * to the device as well.  Returns the first error, including a device status word set by a
+ * kernel (as comet_sync_status()).
+ *
+ * Pipeline: for a one-step split or emulated-FP64 plan whose description lists "host_pipe"
+ * (comet_plan_opts_t.host_slices), and with every host buffer pinned, the larger operand is
+ * copied in slices along the last label of its GEMM row group and each slice is multiplied
+ * while the next one is copied in and the previous result slice is copied out (two extra
+ * streams of the call, joined into `stream` before it returns).  The result equals that of
+ * comet_contract() up to the operand scales of the split, which are taken per slice.  After
+ * the call that operand's device buffer holds its slices one after another, each in its own
+ * compact column-major layout; the device output holds the result.  Otherwise every copy and
+ * kernel runs in order on `stream`.
  */
 comet_status_t comet_contract_host(comet_plan_t plan, const void *const *host_inputs,
                                    void *host_output, void *const *dev_inputs, void *dev_output,

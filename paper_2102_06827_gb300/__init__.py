@@ -89,7 +89,7 @@ class Plan:
 
     def __init__(self, expr: str, extents: dict, dtype, precision="native", order="planned",
                  alpha: float = 1.0, workspace_cap: int = 0, form: int = -1, kc: int = 0,
-                 timeout_ms: int = 0, debug_flags: int = 0, ksplit: int = 0):
+                 timeout_ms: int = 0, debug_flags: int = 0, ksplit: int = 0, host_slices: int = 0):
         L = lib()
         self.expr = expr
         self.extents = {str(k): int(v) for k, v in extents.items()}
@@ -112,6 +112,7 @@ class Plan:
         opts.timeout_ms = timeout_ms
         opts.debug_flags = debug_flags
         opts.ksplit = ksplit
+        opts.host_slices = host_slices
         self.precision = opts.precision
         h = ctypes.c_void_p()
         _lib.check(L.comet_plan(expr.encode(), ext, len(self.extents), dts, n_ops + 1,

@@ -1,6 +1,7 @@
 // C ABI (include/comet.h): plan objects, dispatch of plan steps to the kernels, status word.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -263,6 +264,172 @@ static comet_status_t run_plan(const Plan &P, const void *const *inputs, void *o
     return COMET_OK;
 }
 
+static bool pinned_host(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+// One slice of a column-major tensor along one label: `height` runs of `width` bytes, `pitch`
+// bytes apart, between a strided and a compact or strided layout.  One plain copy when there is
+// a single run; a 2-D copy while the pitch is below 2^31; otherwise one copy per run.
+static cudaError_t copy_slice(void *dst, size_t dpitch, const void *src, size_t spitch, size_t width,
+                              size_t height, cudaMemcpyKind kind, cudaStream_t s) {
+    if (height == 1) return cudaMemcpyAsync(dst, src, width, kind, s);
+    if (dpitch < (1ull << 31) && spitch < (1ull << 31))
+        return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, height, kind, s);
+    for (size_t r = 0; r < height; ++r) {
+        cudaError_t e = cudaMemcpyAsync(static_cast<char *>(dst) + r * dpitch,
+                                        static_cast<const char *>(src) + r * spitch, width, kind, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// comet_contract_host through the slice pipeline of a one-step split / emulated-FP64 plan: W is
+// copied whole, X in slices along its row group's last label into compact device slices; a
+// slice's scale, pre-pass and GEMM wait for its copy and run while the next slice is copied;
+// the result slice goes back on a third stream while the next GEMM runs.  The GEMM of a slice
+// is the step's GEMM with that group shortened to the slice's rows, writing the result through
+// the full result strides from the slice's first element on.
+static comet_status_t run_host_pipe(const Plan &P, const void *const *host_in, void *host_out,
+                                    void *const *dev_in, void *dev_out, void *ws, cudaStream_t s) {
+    const HostPipe &h = P.pipe;
+    const Step &st = P.steps[0];
+    const size_t es = dtype_size(P.dtype);
+    int *status = device_status_word();
+    if (!status) return cuda_status(cudaErrorNoDevice, "status word");
+    struct Res {
+        cudaStream_t cin = nullptr, cout = nullptr;
+        std::vector<cudaEvent_t> ev;
+        ~Res() {
+            for (cudaEvent_t e : ev) if (e) cudaEventDestroy(e);
+            if (cin) cudaStreamDestroy(cin);
+            if (cout) cudaStreamDestroy(cout);
+        }
+    } r;
+    const int n = h.n_chunks;
+    cudaError_t e = cudaStreamCreateWithFlags(&r.cin, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r.cout, cudaStreamNonBlocking);
+    r.ev.assign(3 + 2 * n, nullptr);
+    for (auto &x : r.ev)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_status(e, "host pipeline streams");
+    cudaEvent_t e0 = r.ev[0], e_w = r.ev[1], e_end = r.ev[2];
+    cudaEvent_t *e_in = &r.ev[3], *e_g = &r.ev[3 + n];
+
+    double alpha = P.alpha, beta = 0.0;
+    if (P.op == 1) beta = 1.0;
+    if (P.op == 2) { alpha = -alpha; beta = 1.0; }
+    const bool x_is_b = h.side == 1;
+    char *w = static_cast<char *>(ws);
+    void *sc_a = w + st.ws_scales, *sc_b = w + st.ws_scales + 8;
+    void *sc_x = x_is_b ? sc_b : sc_a, *sc_w = x_is_b ? sc_a : sc_b;
+    char *parts_x = w + (x_is_b ? st.ws_parts_b : st.ws_parts_a);
+    char *parts_w = w + (x_is_b ? st.ws_parts_a : st.ws_parts_b);
+    const bool emu = st.kernel == KK_GEMM_EMU;
+    auto split = emu ? launch_split6 : launch_split;
+    const char *hx = static_cast<const char *>(host_in[h.x_in]);
+    char *dx = static_cast<char *>(dev_in[h.x_in]);
+    char *dc = static_cast<char *>(dev_out);
+    char *hc = static_cast<char *>(host_out);
+    const size_t x_unit = (size_t)h.x_inner * h.x_outer * es;      // compact bytes per unit of L
+    const size_t x_pitch = (size_t)h.x_inner * h.ext * es, c_pitch = (size_t)h.c_inner * h.ext * es;
+
+    // copies in: W whole, then the slices of X (and of the result for "+=" / "-=") in order
+    e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(r.cin, e0, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(r.cout, e0, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dev_in[h.w_in], host_in[h.w_in], (size_t)P.slots[h.w_in].elems * es,
+                            cudaMemcpyHostToDevice, r.cin);
+    if (e == cudaSuccess) e = cudaEventRecord(e_w, r.cin);
+    for (int q = 0; q < n && e == cudaSuccess; ++q) {
+        const int64_t l0 = (int64_t)q * h.chunk, lc = std::min(h.chunk, h.ext - l0);
+        const size_t xw = (size_t)h.x_inner * lc * es;
+        e = copy_slice(dx + l0 * x_unit, xw, hx + (size_t)l0 * h.x_inner * es, x_pitch, xw,
+                       (size_t)h.x_outer, cudaMemcpyHostToDevice, r.cin);
+        if (e == cudaSuccess && P.op != 0) {
+            const size_t off = (size_t)l0 * h.c_inner * es;
+            e = copy_slice(dc + off, c_pitch, hc + off, c_pitch, (size_t)h.c_inner * lc * es,
+                           (size_t)h.c_outer, cudaMemcpyHostToDevice, r.cin);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e_in[q], r.cin);
+    }
+    if (e != cudaSuccess) return cuda_status(e, "host pipeline copy in");
+
+    // W: scale and pre-pass once
+    e = cudaStreamWaitEvent(s, e_w, 0);
+    if (e == cudaSuccess) {
+        ProfScope ps(PK_PREPASS, s);
+        e = launch_absmax(dev_in[h.w_in], P.slots[h.w_in].elems, (int)es, sc_w, s);
+    }
+    if (e == cudaSuccess) {
+        XposeParams xw = x_is_b ? st.pre_a : st.pre_b;
+        xw.in = dev_in[h.w_in]; xw.out = parts_w; xw.scale_bits = sc_w;
+        ProfScope ps(PK_PREPASS, s);
+        e = split(xw, (int)es, x_is_b ? st.pre_a_vec : st.pre_b_vec, x_is_b ? st.pre_a_vout : st.pre_b_vout, s);
+    }
+    if (e != cudaSuccess) return cuda_status(e, "host pipeline pre-pass (whole operand)");
+
+    for (int q = 0; q < n; ++q) {
+        const int64_t l0 = (int64_t)q * h.chunk, lc = std::min(h.chunk, h.ext - l0);
+        const int cls = lc == h.chunk ? 0 : 1;
+        char *xs = dx + l0 * x_unit;
+        e = cudaStreamWaitEvent(s, e_in[q], 0);
+        if (e == cudaSuccess) {
+            ProfScope ps(PK_PREPASS, s);
+            e = launch_absmax(xs, h.x_inner * lc * h.x_outer, (int)es, sc_x, s);
+        }
+        if (e == cudaSuccess) {
+            XposeParams xp = h.pre[cls];
+            xp.in = xs; xp.out = parts_x; xp.scale_bits = sc_x;
+            ProfScope ps(PK_PREPASS, s);
+            e = split(xp, (int)es, h.pre_vec[cls], h.pre_vout[cls], s);
+        }
+        if (e != cudaSuccess) return cuda_status(e, "host pipeline pre-pass (slice)");
+        GemmParams g = st.gemm;
+        Radix &rg = x_is_b ? g.nb : g.ma;
+        const uint32_t rows = (uint32_t)(h.rows_inner * lc);
+        rg.ext[rg.n - 1] = (uint32_t)lc;
+        rg.fd[rg.n - 1] = make_fastdiv((uint32_t)lc);
+        rg.total = rows;
+        if (x_is_b) g.N = rows; else g.M = rows;
+        g.A = x_is_b ? dev_in[h.w_in] : xs;
+        g.B = x_is_b ? xs : dev_in[h.w_in];
+        g.C = dc + (size_t)l0 * h.c_inner * es;
+        g.alpha = alpha;
+        g.beta = beta;
+        g.status = status;
+        g.timeout_ns = timeout_ns(P);
+        void *pa = x_is_b ? parts_w : parts_x, *pb = x_is_b ? parts_x : parts_w;
+        if (emu) {
+            ProfScope ps(PK_EMU, s);
+            e = launch_gemm_emu(g, pa, pb, st.kpad, sc_a, sc_b, P.opts.debug_flags, s, 0);
+        } else {
+            ProfScope ps(PK_SPLIT, s);
+            e = launch_gemm_split(g, pa, pb, st.kpad, sc_a, sc_b, P.opts.kc, (int)es, P.opts.debug_flags, s, 0,
+                                  st.ksplit, reinterpret_cast<float *>(w + st.ws_ksplit));
+        }
+        if (e != cudaSuccess) return cuda_status(e, "host pipeline gemm");
+        e = cudaEventRecord(e_g[q], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(r.cout, e_g[q], 0);
+        if (e == cudaSuccess) {
+            const size_t off = (size_t)l0 * h.c_inner * es;
+            e = copy_slice(hc + off, c_pitch, dc + off, c_pitch, (size_t)h.c_inner * lc * es,
+                           (size_t)h.c_outer, cudaMemcpyDeviceToHost, r.cout);
+        }
+        if (e != cudaSuccess) return cuda_status(e, "host pipeline copy out");
+    }
+    e = cudaEventRecord(e_end, r.cout);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, e_end, 0);
+    if (e != cudaSuccess) return cuda_status(e, "host pipeline join");
+    return COMET_OK;
+}
+
 }  // namespace comet
 
 using namespace comet;
@@ -398,6 +565,17 @@ comet_status_t comet_contract_host(comet_plan_t plan, const void *const *host_in
     if (P.batched) return COMET_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     size_t es = dtype_size(P.dtype);
+    if (P.pipe.ok) {   // slice pipeline: pinned host buffers, aligned device buffers
+        bool ok = pinned_host(host_output) && aligned16(dev_output) && (P.workspace == 0 || aligned16(workspace));
+        for (int i = 0; i < P.n_in && ok; ++i)
+            ok = host_inputs[i] && dev_inputs[i] && pinned_host(host_inputs[i]) && aligned16(dev_inputs[i]);
+        if (ok && P.workspace > 0 && !workspace) return COMET_ERR_WORKSPACE;
+        if (ok) {
+            comet_status_t st = run_host_pipe(P, host_inputs, host_output, dev_inputs, dev_output, workspace, s);
+            if (st != COMET_OK) return st;
+            return comet_sync_status(stream);
+        }
+    }
     for (int i = 0; i < P.n_in; ++i) {
         if (!host_inputs[i] || !dev_inputs[i]) return COMET_ERR_NULL;
         size_t bytes = (size_t)P.slots[i].elems * es;

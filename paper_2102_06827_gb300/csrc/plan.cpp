@@ -440,6 +440,109 @@ double step_flops(const std::vector<int64_t> &ext, const std::vector<int> &a, co
     return f;
 }
 
+// Pre-pass of one operand (labels in its column-major order, dense with extents ext) into
+// [planes][rows][kpad] bf16 planes: K labels first (fastest), then the row group's labels.
+void prepass_params(const Step &st, const std::vector<int> &labels, const std::vector<int> &rows,
+                    const std::vector<int64_t> &ext, int64_t es, XposeParams *xp, int *vec_in,
+                    int *vec_out) {
+    auto st_ = label_strides(labels, ext);
+    std::map<int, int64_t> sout;
+    int64_t s = 1;
+    for (int l : st.form.K) { sout[l] = s; s *= ext[l]; }
+    s = st.kpad;
+    for (int l : rows) { sout[l] = s; s *= ext[l]; }
+    std::vector<int64_t> e, a, b;
+    for (int l : labels) {
+        if (pos_of(st.form.Bt, l) >= 0) continue;   // one pre-pass per batch index
+        e.push_back(ext[l]); a.push_back(st_[l]); b.push_back(sout[l]);
+    }
+    if (e.empty()) { e.push_back(1); a.push_back(1); b.push_back(1); }
+    double eff;
+    setup_xpose((int)e.size(), e.data(), a.data(), b.data(), (int)es, xp, vec_in, vec_out, &eff);
+    xp->out_plane = prod_ext(ext, rows) * st.kpad;
+}
+
+// Slices of the host-buffer pipeline (see HostPipe).  The slice count minimises a small event
+// model: the inputs cross the host link one after another (W, then the slices of X), each
+// slice's pre-pass and GEMM start when both its copy and the previous GEMM are done, and the
+// result slices go back in order.  A GEMM takes whole waves of output tiles over the SMs, so
+// slicing costs the partial last wave of every slice.
+void setup_host_pipe(Plan *P, int64_t es, int want) {
+    const Step &st = P->steps[0];
+    const Slot &sa = P->slots[st.a], &sb = P->slots[st.b], &sc = P->slots[st.c];
+    const Slot &sm = st.form.swap ? sb : sa, &sn = st.form.swap ? sa : sb;
+    HostPipe h;
+    h.side = sn.elems >= sm.elems ? 1 : 0;
+    const Slot &sx = h.side ? sn : sm, &sw = h.side ? sm : sn;
+    const std::vector<int> &rows = h.side ? st.form.N : st.form.M;
+    h.x_in = sx.index;
+    h.w_in = sw.index;
+    h.label = rows.back();
+    h.ext = P->extent[h.label];
+    if (h.ext < 2) return;
+    auto tx = label_strides(sx.labels, P->extent), tc = label_strides(sc.labels, P->extent);
+    h.x_inner = tx[h.label];
+    h.x_outer = sx.elems / (h.x_inner * h.ext);
+    h.c_inner = tc[h.label];
+    h.c_outer = sc.elems / (h.c_inner * h.ext);
+    h.rows_inner = prod_ext(P->extent, rows) / h.ext;
+    const bool emu = st.kernel == KK_GEMM_EMU;
+    const int64_t tm = 128, tn = emu ? 80 : 256;          // output tile of the GEMM kernel
+    const int64_t rows_w = prod_ext(P->extent, h.side ? st.form.M : st.form.N);
+    const double prods = emu ? 21.0 / 0.6 : 6.0;             // bf16 products per tile (emu: drain-bound)
+    const double t_tile = 2.0 * tm * tn * (double)st.kpad * prods / (kBf16FlopsPerS / 152);
+    const double bw_in = 200e9, bw_out = 180e9, t_slice = 20e-6;
+    const double planes = emu ? 12.0 : 6.0;
+    auto tiles_of = [&](int64_t lc) {
+        const int64_t r = h.rows_inner * lc;
+        return h.side ? ((rows_w + tm - 1) / tm) * ((r + tn - 1) / tn)
+                      : ((r + tm - 1) / tm) * ((rows_w + tn - 1) / tn);
+    };
+    auto model = [&](int64_t n) {
+        const int64_t chunk = (h.ext + n - 1) / n, cnt = (h.ext + chunk - 1) / chunk;
+        double in = (double)sw.elems * es / bw_in, gemm = 0, out = 0;
+        in += (double)sw.elems * (es + planes) / kHbmBytesPerS;   // W's pre-pass runs before any GEMM
+        for (int64_t q = 0; q < cnt; ++q) {
+            const int64_t lc = std::min(chunk, h.ext - q * chunk);
+            const double xb = (double)h.x_inner * lc * h.x_outer * es, cb = (double)h.c_inner * lc * h.c_outer * es;
+            in += (xb + (P->op != 0 ? cb : 0)) / bw_in;
+            const double work = (double)((tiles_of(lc) + 151) / 152) * t_tile +
+                                xb / es * (es + planes) / kHbmBytesPerS + (cnt > 1 ? t_slice : 0);
+            gemm = std::max(gemm, in) + work;
+            out = std::max(out, gemm) + cb / bw_out;
+        }
+        return out;
+    };
+    auto aligned = [&](int64_t chunk) {   // every slice of X starts on a 16-byte boundary
+        return ((int64_t)chunk * h.x_inner * h.x_outer * es) % 16 == 0;
+    };
+    int64_t best = 1;
+    double best_t = model(1);
+    h.model_s[0] = best_t;
+    if (want > 1) {
+        const int64_t n = std::min<int64_t>(want, h.ext);
+        if (aligned((h.ext + n - 1) / n)) { best = n; best_t = model(n); }
+    } else {
+        for (int64_t n : {2, 3, 4, 6, 8, 12, 16}) {
+            if (n > h.ext || !aligned((h.ext + n - 1) / n)) continue;
+            const double t = model(n);
+            if (t < best_t * 0.97) { best = n; best_t = t; }
+        }
+    }
+    if (best == 1) return;
+    h.chunk = (h.ext + best - 1) / best;
+    h.n_chunks = (int)((h.ext + h.chunk - 1) / h.chunk);
+    h.model_s[1] = best_t;
+    const int64_t tail = h.ext - (h.n_chunks - 1) * h.chunk;
+    for (int c = 0; c < 2; ++c) {
+        std::vector<int64_t> e = P->extent;
+        e[h.label] = c == 0 ? h.chunk : tail;
+        prepass_params(st, sx.labels, rows, e, es, &h.pre[c], &h.pre_vec[c], &h.pre_vout[c]);
+    }
+    h.ok = true;
+    P->pipe = h;
+}
+
 }  // namespace
 
 comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n_extents,
@@ -882,27 +985,18 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
         }
         if (st.kernel == KK_GEMM_SPLIT || st.kernel == KK_GEMM_EMU) {
             // pre-pass of each operand into [planes][rows][kpad] bf16 planes (K order, then rows)
-            auto pre = [&](const Slot &so_, const std::vector<int> &rows, XposeParams *xp, int *vec_in, int *vec_out) {
-                auto st_ = label_strides(so_.labels, P->extent);
-                std::map<int, int64_t> sout;
-                int64_t s = 1;
-                for (int l : st.form.K) { sout[l] = s; s *= P->extent[l]; }
-                s = st.kpad;
-                for (int l : rows) { sout[l] = s; s *= P->extent[l]; }
-                std::vector<int64_t> e, a, b;
-                for (int l : so_.labels) {
-                    if (pos_of(st.form.Bt, l) >= 0) continue;   // one pre-pass per batch index
-                    e.push_back(P->extent[l]); a.push_back(st_[l]); b.push_back(sout[l]);
-                }
-                if (e.empty()) { e.push_back(1); a.push_back(1); b.push_back(1); }
-                double eff;
-                setup_xpose((int)e.size(), e.data(), a.data(), b.data(), (int)es, xp, vec_in, vec_out, &eff);
-                int64_t rows_n = prod_ext(P->extent, rows);
-                xp->out_plane = rows_n * st.kpad;
-            };
-            pre(sm, st.form.M, &st.pre_a, &st.pre_a_vec, &st.pre_a_vout);
-            pre(sn, st.form.N, &st.pre_b, &st.pre_b_vec, &st.pre_b_vout);
+            prepass_params(st, sm.labels, st.form.M, P->extent, es, &st.pre_a, &st.pre_a_vec, &st.pre_a_vout);
+            prepass_params(st, sn.labels, st.form.N, P->extent, es, &st.pre_b, &st.pre_b_vec, &st.pre_b_vout);
         }
+    }
+    // ---- host-buffer pipeline of one-step split / emulated plans (comet_contract_host) ----
+    P->pipe = HostPipe();
+    if (P->steps.size() == 1 && opts.host_slices != 1) {
+        const Step &st = P->steps[0];
+        if ((st.kernel == KK_GEMM_SPLIT || st.kernel == KK_GEMM_EMU) && st.n_batch == 1 && st.b >= 0 && P->slots[st.a].kind == SLOT_INPUT &&
+            P->slots[st.b].kind == SLOT_INPUT && P->slots[st.c].kind == SLOT_OUTPUT &&
+            !st.form.M.empty() && !st.form.N.empty())
+            setup_host_pipe(P, es, opts.host_slices);
     }
     P->flops = 0;
     for (auto &st : P->steps) P->flops += st.flops;
@@ -962,7 +1056,13 @@ std::string describe_plan(const Plan &P) {
         }
         o << "}";
     }
-    o << "]}";
+    o << "]";
+    if (P.pipe.ok)
+        o << ",\"host_pipe\":{\"slices\":" << P.pipe.n_chunks << ",\"label\":\""
+          << P.label_names[P.pipe.label] << "\",\"chunk\":" << P.pipe.chunk << ",\"side\":\""
+          << (P.pipe.side ? "N" : "M") << "\",\"model_s\":[" << P.pipe.model_s[0] << ","
+          << P.pipe.model_s[1] << "]}";
+    o << "}";
     return o.str();
 }
 
@@ -1006,4 +1106,5 @@ extern "C" void comet_plan_opts_default(comet_plan_opts_t *o) {
     o->timeout_ms = 0;
     o->debug_flags = 0;
     o->ksplit = 0;
+    o->host_slices = 0;
 }

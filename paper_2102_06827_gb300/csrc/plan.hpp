@@ -79,6 +79,27 @@ struct Step {
     int copy_vec_in = 1, copy_vec_out = 1;
 };
 
+// Host-buffer pipeline of a one-step split or emulated-FP64 plan (comet_contract_host): the
+// larger operand X is copied to the device in slices along the last (slowest) label L of its
+// GEMM row group; the other operand W is copied whole first.  Each slice lands compact (its
+// own column-major layout with L shortened), is pre-passed and multiplied while the next slice
+// is copied, and the matching slice of the result is copied back while the next one is
+// multiplied.  Slice j of the GEMM covers rows [l0*rows_inner, (l0+lc)*rows_inner) of its group.
+struct HostPipe {
+    bool ok = false;
+    int side = 1;                // 1: X is the N operand (GEMM B), 0: the M operand (GEMM A)
+    int x_in = 1, w_in = 0;      // input positions of X and W
+    int label = -1;              // L
+    int64_t ext = 0, chunk = 0;  // extent of L and of one slice (the last one may be shorter)
+    int n_chunks = 0;
+    int64_t x_inner = 1, x_outer = 1;  // X elements below L (its stride), and the count above it
+    int64_t c_inner = 1, c_outer = 1;  // the same for the result
+    int64_t rows_inner = 1;      // GEMM rows of X's group per unit of L
+    XposeParams pre[2];          // pre-pass of a compact slice: full slice, short last slice
+    int pre_vec[2] = {1, 1}, pre_vout[2] = {1, 1};
+    double model_s[2] = {0, 0};  // modelled seconds: unpipelined, pipelined
+};
+
 struct Plan {
     std::string expr;
     ParsedExpr parsed;
@@ -105,6 +126,7 @@ struct Plan {
     std::vector<std::vector<uint32_t>> batched_prefix;   // per tile configuration
     std::vector<double> block_flops;
     bool batched_ak = false, batched_bk = false, batched_swap = false;
+    HostPipe pipe;                        // comet_contract_host slicing (one-step plans)
 };
 
 size_t dtype_size(comet_dtype_t t);

@@ -273,3 +273,30 @@ def test_batched_plan_structure():
     with pytest.raises(comet.CometError) as err:
         comet.BatchedPlan(e, names, np.zeros((2, 7), dtype=np.int64), "f64")
     assert err.value.name == "COMET_ERR_SHAPE"
+
+
+def test_host_pipeline_plans():
+    """comet_contract_host slicing: one-step split / emulated plans only, along the last label
+    of the larger operand's row group, with every slice starting on a 16-byte boundary."""
+    ccsd = "C[i,a,j,b] = A[k,a,c,i] * B[c,b,k,j]"
+    full = dict(i=64, j=64, k=64, a=192, b=192, c=192)
+    hp = plan(ccsd, full, "f32", precision="split_bf16").info["host_pipe"]
+    assert hp["slices"] > 1 and hp["side"] == "N" and hp["label"] == "j"
+    assert hp["model_s"][1] < hp["model_s"][0]
+    assert 64 % hp["chunk"] == 0 or hp["slices"] == -(-64 // hp["chunk"])
+    assert "host_pipe" in plan(ccsd, full, "f64", precision="emu_f64").info
+    for kw in (dict(precision="native"), dict(precision="split_bf16", host_slices=1)):
+        assert "host_pipe" not in plan(ccsd, full, "f32", **kw).info
+    chain = "D[i,l] = A[i,j] * B[j,k] * C[k,l]"
+    assert "host_pipe" not in plan(chain, dict(i=2048, j=2048, k=2048, l=2048), "f32",
+                                   precision="split_bf16").info
+    # explicit slice counts: ceil(ext / s) per slice, the last one shorter
+    hp = plan(ccsd, dict(i=16, j=18, k=16, a=40, b=48, c=48), "f32", precision="split_bf16",
+              host_slices=4).info["host_pipe"]
+    assert (hp["chunk"], hp["slices"]) == (5, 4)
+    # B[k,n] slices of n hold k=5 FP32 values per unit: 3 units = 60 bytes is not 16-aligned
+    e = "C[m,n] = A[m,k] * B[k,n]"
+    assert "host_pipe" not in plan(e, dict(m=4, n=9, k=5), "f32", precision="split_bf16",
+                                   host_slices=3).info
+    hp = plan(e, dict(m=4, n=9, k=8), "f32", precision="split_bf16", host_slices=3).info["host_pipe"]
+    assert hp["label"] == "n" and hp["chunk"] == 3
