@@ -133,12 +133,42 @@ void comet_plan_opts_default(comet_plan_opts_t *opts);
  * in a binary tree of ta.tc steps.  A label on both operands of a step and on its result is a
  * batch label (the step's GEMM runs once per batch index); a label on one operand only, and
  * not on the result, is summed inside that operand by a reduction step before the tree.
- * Repeated labels inside one tensor (diagonals) give COMET_ERR_UNSUPPORTED.  No device work,
- * no GPU needed.
+ * A label written twice inside one tensor takes its diagonal.  No device work, no GPU needed.
  */
 comet_status_t comet_plan(const char *expr, const comet_extent_t *extents, int n_extents,
                           const comet_dtype_t *dtypes, int n_dtypes,
                           const comet_plan_opts_t *opts, comet_plan_t *out_plan);
+
+/*
+ * comet_view_t — one dimension of a stored tensor taken as a slice (Section 4: a label whose
+ * range differs from the one the tensor was declared with makes a view, and the operation
+ * works on that slice).  The operation reads or writes the indices lo, lo + step, ...,
+ * lo + (n - 1) step of a dimension that the stored tensor declares with `declared` indices,
+ * n being the extent of the dimension's label in the expression.
+ */
+typedef struct {
+    int operand;                /* 0 .. n_in-1: right-hand operands in expression order;
+                                   n_in: the left-hand tensor */
+    int dim;                    /* position of the dimension in that tensor's labels as written */
+    int64_t declared;           /* extent of the dimension in the stored tensor */
+    int64_t lo;                 /* first index taken, >= 0 */
+    int64_t step;               /* increment, >= 1; lo + (n - 1) step < declared */
+} comet_view_t;
+
+/*
+ * comet_plan_views — comet_plan() on views of stored tensors.  The pointers later passed to
+ * comet_contract() are the stored (declared) tensors, dense column-major; the plan touches only
+ * the view's elements (an output view leaves the rest of the stored tensor unchanged).  Each
+ * (operand, dim) pair may appear once; dimensions not listed are whole.  A label written twice
+ * inside one tensor (a diagonal, e.g. "t[] = A[i,i]") is accepted by comet_plan() as well: both
+ * dimensions take the label's indices.  Views need views' element counts below 2^31 per tensor;
+ * batched plans take no views or diagonals.  Errors: COMET_ERR_ARG (operand or dim out of
+ * range, a pair given twice), COMET_ERR_SHAPE (declared < 1, lo < 0, step < 1, or the range
+ * past the declared extent), then as comet_plan().
+ */
+comet_status_t comet_plan_views(const char *expr, const comet_extent_t *extents, int n_extents,
+                                const comet_view_t *views, int n_views, const comet_dtype_t *dtypes,
+                                int n_dtypes, const comet_plan_opts_t *opts, comet_plan_t *out_plan);
 
 /*
  * comet_adjoint_expr — the expression of the gradient of a contraction with respect to one

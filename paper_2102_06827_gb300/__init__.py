@@ -85,11 +85,15 @@ class Plan:
              "sum_{k,c}" and 1..12 operands)
     extents  {label: extent}
     dtype    torch.float32 / torch.float64 (all operands)
+    views    optional [(operand, dim, declared, lo, step), ...] (comet_plan_views): dimension
+             `dim` (as written) of right-hand operand `operand` (n_in = the left-hand tensor)
+             is stored with `declared` indices and the operation takes lo, lo+step, ...
     """
 
     def __init__(self, expr: str, extents: dict, dtype, precision="native", order="planned",
                  alpha: float = 1.0, workspace_cap: int = 0, form: int = -1, kc: int = 0,
-                 timeout_ms: int = 0, debug_flags: int = 0, ksplit: int = 0, host_slices: int = 0):
+                 timeout_ms: int = 0, debug_flags: int = 0, ksplit: int = 0, host_slices: int = 0,
+                 views=None):
         L = lib()
         self.expr = expr
         self.extents = {str(k): int(v) for k, v in extents.items()}
@@ -115,8 +119,14 @@ class Plan:
         opts.host_slices = host_slices
         self.precision = opts.precision
         h = ctypes.c_void_p()
-        _lib.check(L.comet_plan(expr.encode(), ext, len(self.extents), dts, n_ops + 1,
-                                ctypes.byref(opts), ctypes.byref(h)), "comet_plan")
+        if views:
+            vs = (_lib.View * len(views))(*[_lib.View(int(o), int(d), int(n), int(lo), int(st))
+                                            for o, d, n, lo, st in views])
+            _lib.check(L.comet_plan_views(expr.encode(), ext, len(self.extents), vs, len(views), dts,
+                                          n_ops + 1, ctypes.byref(opts), ctypes.byref(h)), "comet_plan_views")
+        else:
+            _lib.check(L.comet_plan(expr.encode(), ext, len(self.extents), dts, n_ops + 1,
+                                    ctypes.byref(opts), ctypes.byref(h)), "comet_plan")
         self._h = h
         ws = ctypes.c_size_t()
         _lib.check(L.comet_plan_workspace(h, ctypes.byref(ws)), "comet_plan_workspace")

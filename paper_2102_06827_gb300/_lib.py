@@ -20,7 +20,7 @@ ORDER_PLANNED, ORDER_NATURAL = 0, 1
 
 # every symbol include/comet.h declares (checked by the CPU test suite)
 EXPORTS = [
-    "comet_plan_opts_default", "comet_plan", "comet_plan_workspace", "comet_plan_flops",
+    "comet_plan_opts_default", "comet_plan", "comet_plan_views", "comet_plan_workspace", "comet_plan_flops",
     "comet_plan_flops_natural", "comet_plan_describe", "comet_adjoint_expr", "comet_contract", "comet_contract_noalloc", "comet_contract_host",
     "comet_transpose", "comet_fill", "comet_plan_batched", "comet_batched_num_tiles", "comet_batched_set_tile",
     "comet_batched_prepare", "comet_contract_batched", "comet_batched_autotune",
@@ -38,6 +38,11 @@ class CometError(RuntimeError):
 
 class Extent(ctypes.Structure):
     _fields_ = [("label", ctypes.c_char_p), ("extent", ctypes.c_int64)]
+
+
+class View(ctypes.Structure):
+    _fields_ = [("operand", ctypes.c_int), ("dim", ctypes.c_int), ("declared", ctypes.c_int64),
+                ("lo", ctypes.c_int64), ("step", ctypes.c_int64)]
 
 
 class KernelStat(ctypes.Structure):
@@ -69,6 +74,9 @@ def load():
     L.comet_plan.argtypes = [ctypes.c_char_p, ctypes.POINTER(Extent), ctypes.c_int,
                              ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(PlanOpts),
                              ctypes.POINTER(vp)]
+    L.comet_plan_views.argtypes = [ctypes.c_char_p, ctypes.POINTER(Extent), ctypes.c_int,
+                                   ctypes.POINTER(View), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                   ctypes.c_int, ctypes.POINTER(PlanOpts), ctypes.POINTER(vp)]
     L.comet_adjoint_expr.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t]
     L.comet_plan_workspace.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     L.comet_plan_flops.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]

@@ -118,11 +118,19 @@ static int64_t timeout_ns(const Plan &P) {
 }
 
 // pointer of a slot at launch time
+// pointer of a slot at launch time (inputs and the output: the first element the plan touches)
 static void *slot_ptr(const Plan &P, int slot, const void *const *inputs, void *output, void *ws) {
     const Slot &s = P.slots[slot];
-    if (s.kind == SLOT_INPUT) return const_cast<void *>(inputs[s.index]);
-    if (s.kind == SLOT_OUTPUT) return output;
+    const size_t off = (size_t)s.offset * dtype_size(P.dtype);
+    if (s.kind == SLOT_INPUT) return static_cast<char *>(const_cast<void *>(inputs[s.index])) + off;
+    if (s.kind == SLOT_OUTPUT) return static_cast<char *>(output) + off;
     return static_cast<char *>(ws) + s.ws_off;
+}
+
+// max |x| over the elements of a step operand (a strided walk for views)
+static cudaError_t operand_absmax(const Slot &s, const void *p, int es, void *out, cudaStream_t stream) {
+    if (s.view) return launch_absmax_view(p, s.vradix, es, out, stream);
+    return launch_absmax(p, s.elems, es, out, stream);
 }
 
 static comet_status_t run_plan(const Plan &P, const void *const *inputs, void *output, void *ws,
@@ -173,15 +181,14 @@ static comet_status_t run_plan(const Plan &P, const void *const *inputs, void *o
         void *sc_a = w + st.ws_scales, *sc_b = w + st.ws_scales + 8;
         const bool split_like = st.kernel == KK_GEMM_SPLIT || st.kernel == KK_GEMM_EMU;
         if (split_like) {   // operand scales over the whole operands (every batch index shares them)
-            const int64_t na = P.slots[st.form.swap ? st.b : st.a].elems;
-            const int64_t nb = P.slots[st.form.swap ? st.a : st.b].elems;
+            const Slot &sa_ = P.slots[st.form.swap ? st.b : st.a], &sb_ = P.slots[st.form.swap ? st.a : st.b];
             {
                 ProfScope ps(PK_PREPASS, stream);
-                e = launch_absmax(st.form.swap ? pb : pa, na, es, sc_a, stream);
+                e = operand_absmax(sa_, st.form.swap ? pb : pa, es, sc_a, stream);
             }
             if (e == cudaSuccess) {
                 ProfScope ps(PK_PREPASS, stream);
-                e = launch_absmax(st.form.swap ? pa : pb, nb, es, sc_b, stream);
+                e = operand_absmax(sb_, st.form.swap ? pa : pb, es, sc_b, stream);
             }
             if (e != cudaSuccess) return cuda_status(e, "split pre-pass (scales)");
         }
@@ -446,7 +453,31 @@ comet_status_t comet_plan(const char *expr, const comet_extent_t *extents, int n
     std::string err;
     comet_status_t st;
     try {
-        st = build_plan(expr, extents, n_extents, dtypes, n_dtypes, opts, &h->p, &err);
+        st = build_plan(expr, extents, n_extents, nullptr, 0, dtypes, n_dtypes, opts, &h->p, &err);
+    } catch (...) {
+        st = COMET_ERR_INTERNAL;
+        err = "exception while planning";
+    }
+    if (st != COMET_OK) {
+        set_error(err);
+        delete h;
+        return st;
+    }
+    *out_plan = h;
+    return COMET_OK;
+}
+
+comet_status_t comet_plan_views(const char *expr, const comet_extent_t *extents, int n_extents,
+                                const comet_view_t *views, int n_views, const comet_dtype_t *dtypes,
+                                int n_dtypes, const comet_plan_opts_t *opts, comet_plan_t *out_plan) {
+    if (!out_plan) return COMET_ERR_NULL;
+    *out_plan = nullptr;
+    comet_plan_s *h = new (std::nothrow) comet_plan_s;
+    if (!h) return COMET_ERR_INTERNAL;
+    std::string err;
+    comet_status_t st;
+    try {
+        st = build_plan(expr, extents, n_extents, views, n_views, dtypes, n_dtypes, opts, &h->p, &err);
     } catch (...) {
         st = COMET_ERR_INTERNAL;
         err = "exception while planning";
@@ -578,13 +609,13 @@ comet_status_t comet_contract_host(comet_plan_t plan, const void *const *host_in
     }
     for (int i = 0; i < P.n_in; ++i) {
         if (!host_inputs[i] || !dev_inputs[i]) return COMET_ERR_NULL;
-        size_t bytes = (size_t)P.slots[i].elems * es;
+        size_t bytes = (size_t)P.slots[i].storage * es;
         comet_status_t st = cuda_status(cudaMemcpyAsync(dev_inputs[i], host_inputs[i], bytes,
                                                         cudaMemcpyHostToDevice, s), "input copy");
         if (st != COMET_OK) return st;
     }
     size_t out_bytes = 0;
-    for (auto &sl : P.slots) if (sl.kind == SLOT_OUTPUT) out_bytes = (size_t)sl.elems * es;
+    for (auto &sl : P.slots) if (sl.kind == SLOT_OUTPUT) out_bytes = (size_t)sl.storage * es;
     if (P.op != 0) {
         comet_status_t st = cuda_status(cudaMemcpyAsync(dev_output, host_output, out_bytes,
                                                         cudaMemcpyHostToDevice, s), "output copy in");

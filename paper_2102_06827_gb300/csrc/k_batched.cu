@@ -753,7 +753,7 @@ comet_status_t comet_plan_batched(const char *expr, int n_blocks, const char *co
     for (int l = 0; l < n_labels; ++l) ex[l] = comet_extent_t{label_names[l], extents[l]};
     comet_status_t st;
     try {
-        st = build_plan(expr, ex.data(), n_labels, dtypes, n_dtypes, opts, &P, &err);
+        st = build_plan(expr, ex.data(), n_labels, nullptr, 0, dtypes, n_dtypes, opts, &P, &err);
     } catch (...) {
         st = COMET_ERR_INTERNAL;
     }
@@ -764,6 +764,10 @@ comet_status_t comet_plan_batched(const char *expr, int n_blocks, const char *co
     if (st == COMET_OK && !P.steps[0].form.Bt.empty()) {
         st = COMET_ERR_UNSUPPORTED;
         err = "batched plans take no batch labels (labels on both operands and the result)";
+    }
+    if (st == COMET_OK && (P.slots[0].view || P.slots[1].view || P.slots[2].view)) {
+        st = COMET_ERR_UNSUPPORTED;
+        err = "batched plans take no repeated labels";
     }
     if (st == COMET_OK && P.opts.precision == COMET_PREC_EMU_F64) {
         st = COMET_ERR_UNSUPPORTED;

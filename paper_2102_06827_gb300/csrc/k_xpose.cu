@@ -371,6 +371,35 @@ cudaError_t launch_absmax(const void *x, int64_t n, int elem_bytes, void *out_bi
     return cudaGetLastError();
 }
 
+// max |x| over a strided view: each thread walks elements through the radix (smallest stride
+// first, so neighbouring threads touch neighbouring addresses where the view allows)
+template <typename T>
+__global__ void __launch_bounds__(256) absmax_view_kernel(const T *__restrict__ x, const Radix r, void *out_bits) {
+    using U = typename std::conditional<sizeof(T) == 4, unsigned int, unsigned long long>::type;
+    T m = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < r.total; i += gridDim.x * blockDim.x) {
+        int64_t o0 = 0, o1 = 0;
+        radix_offsets(r, i, o0, o1);
+        m = fmax(m, fabs(x[o0]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0) {
+        U bits;
+        memcpy(&bits, &m, sizeof(U));
+        atomicMax(reinterpret_cast<U *>(out_bits), bits);
+    }
+}
+
+cudaError_t launch_absmax_view(const void *x, const Radix &r, int elem_bytes, void *out_bits, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out_bits, 0, 8, s);
+    if (e != cudaSuccess || r.total == 0) return e;
+    int blocks = (int)std::min<int64_t>(152 * 8, ((int64_t)r.total + 255) / 256);
+    if (elem_bytes == 4) absmax_view_kernel<float><<<blocks, 256, 0, s>>>(reinterpret_cast<const float *>(x), r, out_bits);
+    else absmax_view_kernel<double><<<blocks, 256, 0, s>>>(reinterpret_cast<const double *>(x), r, out_bits);
+    return cudaGetLastError();
+}
+
 static uint32_t xpose_grid(const XposeParams &p) {
     return p.tiles_u * p.tiles_v * p.tiles_w;
 }

@@ -20,6 +20,8 @@ cudaError_t launch_fill(void *out, int64_t n, double value, int elem_bytes, cuda
 
 // max |x| of a dense operand into *out_bits (zeroed first), as the bits of an input-precision value
 cudaError_t launch_absmax(const void *x, int64_t n, int elem_bytes, void *out_bits, cudaStream_t s);
+// the same over the r.total elements of a strided view at offsets r (digit strides s0)
+cudaError_t launch_absmax_view(const void *x, const Radix &r, int elem_bytes, void *out_bits, cudaStream_t s);
 
 // ksplit > 1: K sliced over more work items, FP32 partials in `partial` (ksplit x M x N floats)
 // summed by a reduce kernel into C

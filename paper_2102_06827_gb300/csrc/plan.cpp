@@ -139,7 +139,7 @@ double run_eff(double run_bytes) { return std::min(1.0, run_bytes / 64.0); }
 
 void setup_xpose(int rank, const int64_t *ext_in, const int64_t *sin_in,
                  const int64_t *sout_in, int elem_bytes, XposeParams *p, int *vec_in,
-                 int *vec_out, double *eff) {
+                 int *vec_out, double *eff, int64_t in_off, int64_t out_off) {
     std::memset(p, 0, sizeof(*p));
     // drop extent-1 dims, then fuse neighbours that are contiguous on both sides
     std::vector<int64_t> ext, si, so;
@@ -245,7 +245,7 @@ void setup_xpose(int rank, const int64_t *ext_in, const int64_t *sin_in,
     // vector direction is a multiple of it
     int w = 16 / elem_bytes;
     auto ok_in = [&](int vw) {
-        if (p->u.s0[0] != 1 || p->u.ext[0] % vw || tu % vw) return false;
+        if (in_off % vw || p->u.s0[0] != 1 || p->u.ext[0] % vw || tu % vw) return false;
         for (int d = 1; d < p->u.n; ++d) if (p->u.s0[d] % vw) return false;
         for (int d = 0; d < p->v.n; ++d) if (p->v.s0[d] % vw) return false;
         for (int d = 0; d < p->r.n; ++d) if (p->r.s0[d] % vw) return false;
@@ -254,7 +254,7 @@ void setup_xpose(int rank, const int64_t *ext_in, const int64_t *sin_in,
     auto ok_out = [&](int vw) {
         const Radix &f = same ? p->u : p->v;
         const uint32_t tf = same ? tu : tv;
-        if (f.n == 0 || f.s1[0] != 1 || f.ext[0] % vw || tf % vw) return false;
+        if (out_off % vw || f.n == 0 || f.s1[0] != 1 || f.ext[0] % vw || tf % vw) return false;
         for (int d = 1; d < f.n; ++d) if (f.s1[d] % vw) return false;
         if (!same) for (int d = 0; d < p->u.n; ++d) if (p->u.s1[d] % vw) return false;
         for (int d = 0; d < p->r.n; ++d) if (p->r.s1[d] % vw) return false;
@@ -263,7 +263,7 @@ void setup_xpose(int rank, const int64_t *ext_in, const int64_t *sin_in,
     // the kernels come in 16-byte and element-wide variants only.  A single long run (copy
     // mode, R empty) moves its ragged tail element-wise, so only the strides matter there.
     p->single_run = (same && R.empty() && Eu > TAB) ? 1 : 0;
-    const bool unit = p->u.s0[0] == 1 && p->u.s1[0] == 1;
+    const bool unit = p->u.s0[0] == 1 && p->u.s1[0] == 1 && in_off % w == 0 && out_off % w == 0;
     const int vi = (p->single_run ? unit : ok_in(w)) ? w : 1;
     const int vo = (p->single_run ? unit : ok_out(w)) ? w : 1;
     const int vc = std::min(vi, vo);
@@ -324,6 +324,13 @@ std::map<int, int64_t> label_strides(const std::vector<int> &labels, const std::
     int64_t st = 1;
     for (int l : labels) { s[l] = st; st *= ext[l]; }
     return s;
+}
+
+// strides of a slot as stored: the stored tensor's (views included) for inputs and the output,
+// dense column-major for intermediates
+std::map<int, int64_t> slot_strides(const Plan &P, const Slot &s) {
+    if (s.kind == SLOT_INTER) return label_strides(s.labels, P.extent);
+    return s.strides;
 }
 
 // length (elements) of the contiguous run that a group order gives in a tensor: the product of
@@ -442,10 +449,9 @@ double step_flops(const std::vector<int64_t> &ext, const std::vector<int> &a, co
 
 // Pre-pass of one operand (labels in its column-major order, dense with extents ext) into
 // [planes][rows][kpad] bf16 planes: K labels first (fastest), then the row group's labels.
-void prepass_params(const Step &st, const std::vector<int> &labels, const std::vector<int> &rows,
-                    const std::vector<int64_t> &ext, int64_t es, XposeParams *xp, int *vec_in,
-                    int *vec_out) {
-    auto st_ = label_strides(labels, ext);
+void prepass_params(const Step &st, const std::vector<int> &labels, std::map<int, int64_t> st_,
+                    int64_t in_off, const std::vector<int> &rows, const std::vector<int64_t> &ext,
+                    int64_t es, XposeParams *xp, int *vec_in, int *vec_out) {
     std::map<int, int64_t> sout;
     int64_t s = 1;
     for (int l : st.form.K) { sout[l] = s; s *= ext[l]; }
@@ -458,7 +464,7 @@ void prepass_params(const Step &st, const std::vector<int> &labels, const std::v
     }
     if (e.empty()) { e.push_back(1); a.push_back(1); b.push_back(1); }
     double eff;
-    setup_xpose((int)e.size(), e.data(), a.data(), b.data(), (int)es, xp, vec_in, vec_out, &eff);
+    setup_xpose((int)e.size(), e.data(), a.data(), b.data(), (int)es, xp, vec_in, vec_out, &eff, in_off, 0);
     xp->out_plane = prod_ext(ext, rows) * st.kpad;
 }
 
@@ -537,7 +543,8 @@ void setup_host_pipe(Plan *P, int64_t es, int want) {
     for (int c = 0; c < 2; ++c) {
         std::vector<int64_t> e = P->extent;
         e[h.label] = c == 0 ? h.chunk : tail;
-        prepass_params(st, sx.labels, rows, e, es, &h.pre[c], &h.pre_vec[c], &h.pre_vout[c]);
+        prepass_params(st, sx.labels, label_strides(sx.labels, e), 0, rows, e, es, &h.pre[c], &h.pre_vec[c],
+                       &h.pre_vout[c]);
     }
     h.ok = true;
     P->pipe = h;
@@ -546,8 +553,8 @@ void setup_host_pipe(Plan *P, int64_t es, int want) {
 }  // namespace
 
 comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n_extents,
-                          const comet_dtype_t *dtypes, int n_dtypes,
-                          const comet_plan_opts_t *opts_in, Plan *P, std::string *err) {
+                          const comet_view_t *views, int n_views, const comet_dtype_t *dtypes,
+                          int n_dtypes, const comet_plan_opts_t *opts_in, Plan *P, std::string *err) {
     if (!expr) return COMET_ERR_NULL;
     comet_plan_opts_t opts;
     comet_plan_opts_default(&opts);
@@ -599,23 +606,53 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
     if (opts.precision == COMET_PREC_EMU_F64 && P->dtype != COMET_F64) {
         *err = "the emulated FP64 precision takes FP64 operands"; return COMET_ERR_DTYPE;
     }
-    // labelled tensors as id lists; structural checks (Section 2: contraction vs free labels)
-    std::vector<std::vector<int>> in_labs;
+    // labelled tensors as id lists (each label once; a label written twice is a diagonal);
+    // structural checks (Section 2: contraction vs free labels)
+    std::vector<std::vector<int>> written;   // per tensor (inputs, then the output): labels as written
     for (auto &t : E.ins) {
         std::vector<int> v;
-        for (auto &l : t.labels) {
-            if (pos_of(v, id[l]) >= 0) { *err = "repeated label inside " + t.name; return COMET_ERR_UNSUPPORTED; }
-            v.push_back(id[l]);
-        }
+        for (auto &l : t.labels) v.push_back(id[l]);
         if (v.size() > (size_t)kMaxRank) { *err = "rank above 8"; return COMET_ERR_UNSUPPORTED; }
-        in_labs.push_back(v);
+        written.push_back(v);
     }
-    std::vector<int> out_labs;
-    for (auto &l : E.out.labels) {
-        if (pos_of(out_labs, id[l]) >= 0) { *err = "repeated output label"; return COMET_ERR_UNSUPPORTED; }
-        out_labs.push_back(id[l]);
+    {
+        std::vector<int> v;
+        for (auto &l : E.out.labels) v.push_back(id[l]);
+        if (v.size() > (size_t)kMaxRank) { *err = "rank above 8"; return COMET_ERR_UNSUPPORTED; }
+        written.push_back(v);
     }
-    if (out_labs.size() > (size_t)kMaxRank) { *err = "rank above 8"; return COMET_ERR_UNSUPPORTED; }
+    auto unique_of = [&](const std::vector<int> &v) {
+        std::vector<int> u;
+        for (int l : v) if (pos_of(u, l) < 0) u.push_back(l);
+        return u;
+    };
+    std::vector<std::vector<int>> in_labs;
+    for (int t = 0; t < P->n_in; ++t) in_labs.push_back(unique_of(written[t]));
+    std::vector<int> out_labs = unique_of(written[P->n_in]);
+    // views: per written dimension (declared extent, lo, step); default the whole dimension
+    const int n_t = P->n_in + 1;
+    std::vector<std::vector<int64_t>> decl(n_t), lo(n_t), step(n_t);
+    for (int t = 0; t < n_t; ++t)
+        for (int l : written[t]) { decl[t].push_back(P->extent[l]); lo[t].push_back(0); step[t].push_back(1); }
+    if (n_views < 0 || (n_views > 0 && !views)) return COMET_ERR_NULL;
+    {
+        std::set<std::pair<int, int>> seen;
+        for (int v = 0; v < n_views; ++v) {
+            const comet_view_t &w = views[v];
+            if (w.operand < 0 || w.operand >= n_t || w.dim < 0 || w.dim >= (int)written[w.operand].size()) {
+                *err = "view: operand or dimension out of range"; return COMET_ERR_ARG;
+            }
+            if (!seen.insert({w.operand, w.dim}).second) { *err = "view: dimension given twice"; return COMET_ERR_ARG; }
+            const int64_t n = P->extent[written[w.operand][w.dim]];
+            if (w.declared < 1 || w.lo < 0 || w.step < 1 ||
+                (long double)w.lo + (long double)(n - 1) * (long double)w.step >= (long double)w.declared) {
+                *err = "view: range outside the declared extent"; return COMET_ERR_SHAPE;
+            }
+            decl[w.operand][w.dim] = w.declared;
+            lo[w.operand][w.dim] = w.lo;
+            step[w.operand][w.dim] = w.step;
+        }
+    }
     std::vector<int> count(L, 0);
     for (auto &v : in_labs) for (int l : v) ++count[l];
     for (int l : out_labs) ++count[l];
@@ -636,13 +673,47 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
     if (elems_of(out_labs) > 9.0e15L) { *err = "tensor too large"; return COMET_ERR_SHAPE; }
     size_t es = dtype_size(P->dtype);
 
-    // slots: inputs, then the output
+    // slots: inputs, then the output, with the strides of their stored tensors
+    auto stored_layout = [&](int t, Slot *s) -> comet_status_t {
+        long double storage = 1;
+        int64_t S = 1;
+        s->offset = 0;
+        s->strides.clear();
+        for (size_t d = 0; d < written[t].size(); ++d) {
+            s->strides[written[t][d]] += step[t][d] * S;
+            s->offset += lo[t][d] * S;
+            storage *= (long double)decl[t][d];
+            if (storage > 9.0e15L) { *err = "tensor too large"; return COMET_ERR_SHAPE; }
+            S *= decl[t][d];
+        }
+        s->storage = (int64_t)storage;
+        // declared >= lo + (n-1) step + 1 >= n: with no repeated label, offset 0 and
+        // storage = elems, every dimension is whole (dense)
+        s->view = written[t].size() != s->labels.size() || s->offset != 0 || s->storage != s->elems;
+        if (s->view) {
+            if (s->elems >= (1ll << 31)) { *err = "views of 2^31 elements or more"; return COMET_ERR_UNSUPPORTED; }
+            std::vector<int> byst = s->labels;   // abs-max walk: smallest stride first
+            std::stable_sort(byst.begin(), byst.end(), [&](int a, int b) { return s->strides[a] < s->strides[b]; });
+            std::vector<int64_t> ex(P->extent.begin(), P->extent.end()), s0(P->extent.size(), 0),
+                s1(P->extent.size(), 0);
+            for (int l : byst) s0[l] = s->strides[l];
+            fill_radix(&s->vradix, byst, ex.data(), s0.data(), s1.data());
+            s->vradix.total = (uint32_t)s->elems;
+        }
+        return COMET_OK;
+    };
     for (int i = 0; i < P->n_in; ++i) {
         Slot s; s.kind = SLOT_INPUT; s.index = i; s.labels = in_labs[i];
         s.elems = (int64_t)elems_of(in_labs[i]);
+        comet_status_t vs = stored_layout(i, &s);
+        if (vs != COMET_OK) return vs;
         P->slots.push_back(s);
     }
     Slot so; so.kind = SLOT_OUTPUT; so.labels = out_labs; so.elems = (int64_t)elems_of(out_labs);
+    {
+        comet_status_t vs = stored_layout(P->n_in, &so);
+        if (vs != COMET_OK) return vs;
+    }
     int out_slot = (int)P->slots.size();
     P->slots.push_back(so);
 
@@ -826,8 +897,7 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
         }
         if (prod_ext(P->extent, Bt) >= (1ll << 31)) { *err = "batch labels reach 2^31 indices"; return COMET_ERR_UNSUPPORTED; }
         {   // batch offsets of the three tensors (strides of their full layouts)
-            auto ta = label_strides(sa.labels, P->extent), tb = label_strides(sb.labels, P->extent),
-                 tc = label_strides(sc.labels, P->extent);
+            auto ta = slot_strides(*P, sa), tb = slot_strides(*P, sb), tc = slot_strides(*P, sc);
             st.n_batch = 1;
             for (int l : Bt) {
                 st.bt_ext.push_back(P->extent[l]);
@@ -872,7 +942,7 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
     for (auto &st : P->steps) {
         if (st.kernel == KK_REDUCE) {   // y[kept] = sum over the private labels of the operand
             const Slot &sa = P->slots[st.a], &sc = P->slots[st.c];
-            auto ta = label_strides(sa.labels, P->extent), tc = label_strides(sc.labels, P->extent);
+            auto ta = slot_strides(*P, sa), tc = slot_strides(*P, sc);
             std::vector<int> kept = sc.labels, summed;
             for (int l : sa.labels) if (pos_of(kept, l) < 0) summed.push_back(l);
             std::vector<int64_t> ex(P->extent.begin(), P->extent.end()), s0(L, 0), s1(L, 0), zero(L, 0);
@@ -918,18 +988,18 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
         if (st.kernel == KK_REDUCE) continue;
         if (st.kernel == KK_COPY) {
             const Slot &sa = P->slots[st.a], &sc = P->slots[st.c];
-            auto si = label_strides(sa.labels, P->extent), so2 = label_strides(sc.labels, P->extent);
+            auto si = slot_strides(*P, sa), so2 = slot_strides(*P, sc);
             std::vector<int64_t> e, a, b;
             for (int l : sa.labels) { e.push_back(P->extent[l]); a.push_back(si[l]); b.push_back(so2[l]); }
             double eff;
             setup_xpose((int)e.size(), e.data(), a.data(), b.data(), (int)es, &st.copy,
-                        &st.copy_vec_in, &st.copy_vec_out, &eff);
+                        &st.copy_vec_in, &st.copy_vec_out, &eff, sa.kind == SLOT_INTER ? 0 : sa.offset,
+                        sc.kind == SLOT_INTER ? 0 : sc.offset);
             continue;
         }
         const Slot &sa = P->slots[st.a], &sb = P->slots[st.b], &sc = P->slots[st.c];
         const Slot &sm = st.form.swap ? sb : sa, &sn = st.form.swap ? sa : sb;
-        auto tm = label_strides(sm.labels, P->extent), tn = label_strides(sn.labels, P->extent),
-             tc = label_strides(sc.labels, P->extent);
+        auto tm = slot_strides(*P, sm), tn = slot_strides(*P, sn), tc = slot_strides(*P, sc);
         GemmParams &g = st.gemm;
         std::memset(&g, 0, sizeof(g));
         std::vector<int64_t> ex(P->extent.begin(), P->extent.end());
@@ -970,8 +1040,7 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
             {   // batch digits in-kernel: (vector, large operand) offsets and result offsets
                 std::vector<int> none;
                 std::vector<int64_t> sv(L, 0), sx(L, 0), sy(L, 0), zero(L, 0);
-                auto ta = label_strides(sa.labels, P->extent), tb = label_strides(sb.labels, P->extent),
-                     tc = label_strides(sc.labels, P->extent);
+                auto ta = slot_strides(*P, sa), tb = slot_strides(*P, sb), tc = slot_strides(*P, sc);
                 for (int l : st.form.Bt) {
                     sv[l] = st.gemv_vec_is_a ? (st.form.swap ? tb[l] : ta[l]) : (st.form.swap ? ta[l] : tb[l]);
                     sx[l] = st.gemv_vec_is_a ? (st.form.swap ? ta[l] : tb[l]) : (st.form.swap ? tb[l] : ta[l]);
@@ -985,8 +1054,10 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
         }
         if (st.kernel == KK_GEMM_SPLIT || st.kernel == KK_GEMM_EMU) {
             // pre-pass of each operand into [planes][rows][kpad] bf16 planes (K order, then rows)
-            prepass_params(st, sm.labels, st.form.M, P->extent, es, &st.pre_a, &st.pre_a_vec, &st.pre_a_vout);
-            prepass_params(st, sn.labels, st.form.N, P->extent, es, &st.pre_b, &st.pre_b_vec, &st.pre_b_vout);
+            prepass_params(st, sm.labels, slot_strides(*P, sm), sm.kind == SLOT_INTER ? 0 : sm.offset,
+                           st.form.M, P->extent, es, &st.pre_a, &st.pre_a_vec, &st.pre_a_vout);
+            prepass_params(st, sn.labels, slot_strides(*P, sn), sn.kind == SLOT_INTER ? 0 : sn.offset,
+                           st.form.N, P->extent, es, &st.pre_b, &st.pre_b_vec, &st.pre_b_vout);
         }
     }
     // ---- host-buffer pipeline of one-step split / emulated plans (comet_contract_host) ----
@@ -995,7 +1066,8 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
         const Step &st = P->steps[0];
         if ((st.kernel == KK_GEMM_SPLIT || st.kernel == KK_GEMM_EMU) && st.n_batch == 1 && st.b >= 0 && P->slots[st.a].kind == SLOT_INPUT &&
             P->slots[st.b].kind == SLOT_INPUT && P->slots[st.c].kind == SLOT_OUTPUT &&
-            !st.form.M.empty() && !st.form.N.empty())
+            !st.form.M.empty() && !st.form.N.empty() && !P->slots[st.a].view &&
+            !P->slots[st.b].view && !P->slots[st.c].view)
             setup_host_pipe(P, es, opts.host_slices);
     }
     P->flops = 0;
@@ -1057,6 +1129,25 @@ std::string describe_plan(const Plan &P) {
         o << "}";
     }
     o << "]";
+    bool any_view = false;
+    for (auto &sl : P.slots) any_view |= sl.view;
+    if (any_view) {   // inputs (tensor = position) and the output (tensor = n_in) taken as views
+        o << ",\"views\":[";
+        bool first = true;
+        for (auto &sl : P.slots) {
+            if (!sl.view) continue;
+            o << (first ? "" : ",") << "{\"tensor\":" << (sl.kind == SLOT_INPUT ? sl.index : P.n_in)
+              << ",\"offset\":" << sl.offset << ",\"storage\":" << sl.storage << ",\"strides\":{";
+            bool f2 = true;
+            for (int l : sl.labels) {
+                o << (f2 ? "" : ",") << "\"" << P.label_names[l] << "\":" << sl.strides.at(l);
+                f2 = false;
+            }
+            o << "}}";
+            first = false;
+        }
+        o << "]";
+    }
     if (P.pipe.ok)
         o << ",\"host_pipe\":{\"slices\":" << P.pipe.n_chunks << ",\"label\":\""
           << P.label_names[P.pipe.label] << "\",\"chunk\":" << P.pipe.chunk << ",\"side\":\""

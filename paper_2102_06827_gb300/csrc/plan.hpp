@@ -3,6 +3,7 @@
 // "Optimal permutation for TTGT").  No device work happens here.
 #pragma once
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -45,9 +46,18 @@ enum SlotKind { SLOT_INPUT = 0, SLOT_INTER = 1, SLOT_OUTPUT = 2 };
 struct Slot {
     int kind = SLOT_INPUT;
     int index = 0;               // input position for SLOT_INPUT
-    std::vector<int> labels;     // column-major label order of this tensor
-    int64_t elems = 1;
+    std::vector<int> labels;     // column-major label order of this tensor (each label once)
+    int64_t elems = 1;           // elements the operation touches (product of label extents)
     size_t ws_off = 0;           // SLOT_INTER: byte offset in the workspace
+    // inputs and the output: element strides by label id and the offset of the first element
+    // touched.  A plain tensor is dense column-major (offset 0, storage = elems); a view (a
+    // dimension sliced by lo:step, or a label written twice, i.e. a diagonal) has the strides
+    // of its stored tensor times the steps, summed over the dimensions that share a label.
+    bool view = false;
+    std::map<int, int64_t> strides;
+    int64_t offset = 0;
+    int64_t storage = 1;         // elements of the stored tensor (declared extents)
+    Radix vradix;                // view inputs: every label, smallest stride first (abs-max)
 };
 
 struct Step {
@@ -132,8 +142,8 @@ struct Plan {
 size_t dtype_size(comet_dtype_t t);
 
 comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n_extents,
-                          const comet_dtype_t *dtypes, int n_dtypes,
-                          const comet_plan_opts_t *opts, Plan *plan, std::string *err);
+                          const comet_view_t *views, int n_views, const comet_dtype_t *dtypes,
+                          int n_dtypes, const comet_plan_opts_t *opts, Plan *plan, std::string *err);
 
 std::string describe_plan(const Plan &p);
 
@@ -145,9 +155,10 @@ void gemm_params_for(const std::vector<int64_t> &extent, const std::vector<int> 
 
 // Transpose engine set-up for a permutation of a dense column-major tensor with arbitrary
 // output strides.  in_strides/out_strides in elements; returns the vector widths usable for
-// loads and stores (1, 2 or 4 elements of elem_bytes).
+// loads and stores (1, 2 or 4 elements of elem_bytes).  in_off / out_off: element offsets of
+// the first element from 16-byte aligned bases (16-byte accesses need them aligned too).
 void setup_xpose(int rank, const int64_t *ext, const int64_t *in_strides,
                  const int64_t *out_strides, int elem_bytes, XposeParams *p,
-                 int *vec_in, int *vec_out, double *eff);
+                 int *vec_in, int *vec_out, double *eff, int64_t in_off = 0, int64_t out_off = 0);
 
 }  // namespace comet

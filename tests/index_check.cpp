@@ -18,8 +18,10 @@ static int fails = 0;
 #define CHECK(c, ...) do { if (!(c)) { if (fails++ < 20) { std::printf(__VA_ARGS__); std::printf("\n"); } } } while (0)
 
 // replay of xpose_tile_kernel / xpose_copy_kernel: fills the output->input map
+// in_off / out_off: element offsets of the first element (views) from 16-byte aligned bases;
+// n_in / n_out_span and src_of_out count from the bases
 static bool replay(const XposeParams &p, int vi, int vo, int64_t n_in, int64_t n_out_span,
-                   std::vector<int64_t> &src_of_out) {
+                   std::vector<int64_t> &src_of_out, int64_t in_off = 0, int64_t out_off = 0) {
     const int XT = 256, XTAB = 256;
     const bool copy = vo < 0;
     CHECK(p.tu >= 1 && p.tv >= 1 && p.tw >= 1, "empty tile");
@@ -63,7 +65,7 @@ static bool replay(const XposeParams &p, int vi, int vo, int64_t n_in, int64_t n
                 CHECK(!p.off32 || (row_in[i] < (1ll << 31) && row_out[i] < (1ll << 31)), "32-bit row offset overflows");
             }
             auto move = [&](uint32_t u, uint32_t row) {
-                const int64_t si = row_in[row] + (int64_t)u * su, d = row_out[row] + (int64_t)u * so;
+                const int64_t si = in_off + row_in[row] + (int64_t)u * su, d = out_off + row_out[row] + (int64_t)u * so;
                 CHECK(si % VW == 0 && d % VW == 0, "misaligned copy vector");
                 for (int q = 0; q < VW; ++q) {
                     CHECK(u + q < nu, "vector crosses the tile");
@@ -84,7 +86,7 @@ static bool replay(const XposeParams &p, int vi, int vo, int64_t n_in, int64_t n
                 CHECK(nu - nvec <= (uint32_t)XT, "tail longer than the block");
                 for (uint32_t t = 0; t < nu - nvec; ++t) {   // element-wise tail
                     const uint32_t u = nvec + t;
-                    const int64_t a = row_in[0] + (int64_t)u * su, c = row_out[0] + (int64_t)u * so;
+                    const int64_t a = in_off + row_in[0] + (int64_t)u * su, c = out_off + row_out[0] + (int64_t)u * so;
                     CHECK(a >= 0 && a < n_in && c >= 0 && c < n_out_span, "tail out of bounds");
                     if (c >= 0 && c < n_out_span) { CHECK(src_of_out[c] == -1, "written twice"); src_of_out[c] = a; }
                 }
@@ -133,7 +135,7 @@ static bool replay(const XposeParams &p, int vi, int vo, int64_t n_in, int64_t n
                 const uint32_t r0 = fd_div(t, p.fd_ll), u = (t - r0 * lanes) * vi;
                 if (!(r0 < rpp && u < nu)) continue;
                 for (uint32_t row = r0; row < rows_v; row += rpp) {
-                    const int64_t src = (int64_t)u * su + in_row[row];
+                    const int64_t src = in_off + (int64_t)u * su + in_row[row];
                     CHECK(src % vi == 0, "misaligned vector load");
                     for (int q = 0; q < vi; ++q) {
                         CHECK(u + q < nu, "vector load crosses the tile");
@@ -153,7 +155,7 @@ static bool replay(const XposeParams &p, int vi, int vo, int64_t n_in, int64_t n
                 const uint32_t r0 = fd_div(t, p.fd_sl), v = (t - r0 * lanes) * vo;
                 if (!(r0 < rpp && v < nv)) continue;
                 for (uint32_t row = r0; row < rows_u; row += rpp) {
-                    const int64_t dst = out_o[row] + (int64_t)v * sv;
+                    const int64_t dst = out_off + out_o[row] + (int64_t)v * sv;
                     CHECK(dst % vo == 0, "misaligned vector store");
                     for (int q = 0; q < vo; ++q) {
                         CHECK(v + q < nv, "vector store crosses the tile");
@@ -243,6 +245,55 @@ int main() {
             }
         }
     }
+    // views: strided slices (lo, step) of stored tensors on both sides at element offsets that
+    // need not be 16-byte aligned; every view element lands once, from the right element
+    for (int it = 0; it < 3000 && fails == 0; ++it) {
+        const int rank = 1 + rng() % 4;
+        int64_t ext[8], decl_in[8], decl_out[8], lo_in[8], lo_out[8], st_in[8], st_out[8];
+        int perm[8];
+        int64_t n = 1;
+        for (int d = 0; d < rank; ++d) {
+            const int pick = rng() % 6;
+            ext[d] = pick < 1 ? 1 : pick < 3 ? 1 + rng() % 9 : 4 * (1 + rng() % 12) + (pick == 5 ? 1 : 0);
+            n *= ext[d];
+        }
+        if (n > 100000) continue;
+        for (int d = 0; d < rank; ++d) perm[d] = d;
+        std::shuffle(perm, perm + rank, rng);
+        for (int d = 0; d < rank; ++d) {   // input dimension d, output dimension d (label perm[d])
+            st_in[d] = rng() % 3 == 0 ? 1 + rng() % 3 : 1;
+            lo_in[d] = rng() % 3;
+            decl_in[d] = lo_in[d] + (ext[d] - 1) * st_in[d] + 1 + rng() % 3;
+            st_out[d] = rng() % 3 == 0 ? 1 + rng() % 3 : 1;
+            lo_out[d] = rng() % 3;
+            decl_out[d] = lo_out[d] + (ext[perm[d]] - 1) * st_out[d] + 1 + rng() % 3;
+        }
+        int64_t si[8], so[8], S = 1, in_off = 0, out_off = 0, n_in = 1, n_out = 1;
+        for (int d = 0; d < rank; ++d) { si[d] = st_in[d] * S; in_off += lo_in[d] * S; S *= decl_in[d]; }
+        n_in = S;
+        S = 1;
+        for (int d = 0; d < rank; ++d) { so[perm[d]] = st_out[d] * S; out_off += lo_out[d] * S; S *= decl_out[d]; }
+        n_out = S;
+        if (n_in > 2000000 || n_out > 2000000) continue;
+        for (int es : {4, 8}) {
+            XposeParams p;
+            int vi, vo;
+            double eff;
+            setup_xpose(rank, ext, si, so, es, &p, &vi, &vo, &eff, in_off, out_off);
+            std::vector<int64_t> map(n_out, -1);
+            replay(p, vi, vo, n_in, n_out, map, in_off, out_off);
+            int64_t hit = 0;
+            for (int64_t q = 0; q < n; ++q) {   // view element q (input index order)
+                int64_t rem = q, a = in_off, c = out_off;
+                for (int d = 0; d < rank; ++d) { const int64_t x = rem % ext[d]; rem /= ext[d]; a += x * si[d]; c += x * so[d]; }
+                CHECK(map[c] == a, "view case %d: out %lld from %lld, expected %lld", it, (long long)c,
+                      (long long)map[c], (long long)a);
+            }
+            for (int64_t c = 0; c < n_out; ++c) hit += map[c] >= 0;
+            CHECK(hit == n, "view case %d: %lld outputs written, %lld expected", it, (long long)hit, (long long)n);
+            ++cases;
+        }
+    }
     // launch limits on large shapes (extents 8..256, the transpose workload's range): grid below
     // 2^31 blocks, the transposing tile within its 96 KB of shared memory, the element-wise copy
     // stage within the default 48 KB
@@ -320,7 +371,7 @@ int main() {
             o.precision = prec ? COMET_PREC_SPLIT_BF16 : COMET_PREC_NATIVE;
             Plan P;
             std::string err;
-            if (build_plan(e, all.data(), (int)all.size(), dt, 3, &o, &P, &err) != COMET_OK) {
+            if (build_plan(e, all.data(), (int)all.size(), nullptr, 0, dt, 3, &o, &P, &err) != COMET_OK) {
                 CHECK(false, "plan failed: %s (%s)", e, err.c_str());
                 continue;
             }

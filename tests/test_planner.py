@@ -50,11 +50,6 @@ def test_parse_errors_and_codes():
     with pytest.raises(comet.CometError) as e:
         plan("C[i,j] = A[i,k]*B[k,j]", dict(i=3, j=0, k=2))
     assert e.value.name == "COMET_ERR_SHAPE"
-    # repeated labels
-    for unsup in ["C[i,j] = A[i,i,k]*B[k,j]", "C[i] = A[i,i]"]:
-        with pytest.raises(comet.CometError) as e:
-            plan(unsup, dict(i=3, j=4, k=5, b=2, l=2))
-        assert e.value.name == "COMET_ERR_UNSUPPORTED", unsup
     with pytest.raises(comet.CometError) as e:
         plan("C[i,j] = sum_{j} A[i,k]*B[k,j]", ext)
     assert e.value.name == "COMET_ERR_LABEL"
@@ -300,3 +295,39 @@ def test_host_pipeline_plans():
                                    host_slices=3).info
     hp = plan(e, dict(m=4, n=9, k=8), "f32", precision="split_bf16", host_slices=3).info["host_pipe"]
     assert hp["label"] == "n" and hp["chunk"] == 3
+
+
+def test_views_and_diagonals_layout():
+    """comet_plan_views: strides = stored strides x steps, summed over dimensions that share a
+    label (diagonals); offset = sum of lo x stored strides; checks of the view arguments."""
+    p = plan("C[i,j] = A[i,k] * B[k,j]", dict(i=4, j=5, k=6), "f32", precision="split_bf16",
+             views=[(0, 0, 10, 2, 2), (1, 1, 12, 1, 1), (2, 0, 9, 3, 1)])
+    v = {x["tensor"]: x for x in p.info["views"]}
+    assert v[0] == {"tensor": 0, "offset": 2, "storage": 60, "strides": {"i": 2, "k": 10}}
+    assert v[1] == {"tensor": 1, "offset": 6, "storage": 72, "strides": {"k": 1, "j": 6}}
+    assert v[2] == {"tensor": 2, "offset": 3, "storage": 45, "strides": {"i": 1, "j": 9}}
+    assert "host_pipe" not in p.info
+    # diagonals need no view arguments: A[i,i] has stride 1 + 5 for i
+    p = plan("t[] = A[i,i]", dict(i=5))
+    assert p.info["views"] == [{"tensor": 0, "offset": 0, "storage": 25, "strides": {"i": 6}}]
+    assert p.info["steps"][0]["kernel"] == "reduce"
+    p = plan("C[i,j] = A[i,k,k] * B[k,j]", dict(i=4, j=3, k=7))
+    assert p.info["views"][0]["strides"] == {"i": 1, "k": 4 + 28}
+    p = plan("D[i,i] = A[i,k] * B[k,i]", dict(i=4, k=3))
+    assert p.info["steps"][0]["batch"] == ["i"]
+    assert p.info["views"] == [{"tensor": 2, "offset": 0, "storage": 16, "strides": {"i": 5}}]
+    # a whole dimension given as a view is no view
+    p = plan("C[i,j] = A[i,k] * B[k,j]", dict(i=4, j=5, k=6), views=[(0, 0, 4, 0, 1)])
+    assert "views" not in p.info
+    bad = [([(3, 0, 10, 0, 1)], "COMET_ERR_ARG"), ([(0, 2, 10, 0, 1)], "COMET_ERR_ARG"),
+           ([(0, 0, 10, 0, 1), (0, 0, 10, 1, 1)], "COMET_ERR_ARG"),
+           ([(0, 0, 10, 0, 4)], "COMET_ERR_SHAPE"), ([(0, 0, 10, 7, 1)], "COMET_ERR_SHAPE"),
+           ([(0, 0, 10, -1, 1)], "COMET_ERR_SHAPE"), ([(0, 0, 10, 0, 0)], "COMET_ERR_SHAPE"),
+           ([(0, 0, 0, 0, 1)], "COMET_ERR_SHAPE")]
+    for views, code in bad:
+        with pytest.raises(comet.CometError) as e:
+            plan("C[i,j] = A[i,k] * B[k,j]", dict(i=4, j=5, k=6), views=views)
+        assert e.value.name == code, views
+    with pytest.raises(comet.CometError) as e:
+        comet.BatchedPlan("C[i,j] = A[i,k,k] * B[k,j]", ["i", "j", "k"], [[3, 4, 5]], "f64")
+    assert e.value.name == "COMET_ERR_UNSUPPORTED"
