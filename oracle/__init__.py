@@ -16,6 +16,10 @@ Functions (each follows the paper's definition it names):
   triples_reduce   the reduction s = sum T*W, q = sum T^2 of one triples block (a reading:
                    the 6-D triples outputs are consumed in place, not stored)
   grad_exprs       the adjoint expressions of a contraction (each is again a contraction)
+  triples_energy   one block of the fused accumulation: T = sum of permuted contributions
+                   (each a contraction, Section 2), E = sum T^2 / D with D the signed sum of
+                   per-label orbital-energy vectors (the CCSD(T) pattern the paper's Section 3
+                   cites: a 6-D output from two 4-D inputs, several terms per block)
 """
 from __future__ import annotations
 
@@ -271,3 +275,25 @@ def grad_exprs(expr: str):
         pre = "" if alpha == 1.0 else f"{alpha!r} * "
         res.append(f"d{x}[{','.join(lx)}] = {pre}{' * '.join([g] + others)}")
     return res
+
+
+def triples_energy(terms, operands, eps, signs):
+    """One block of the fused triples accumulation, by definition:
+
+        T = sum_p einsum(terms[p], X_p, Y_p)      (each term carries its own alpha)
+        D[l_1, ..., l_n] = sum_q signs[q] * eps[q][l_q]   (l_q: the q-th label of T)
+        E = sum over every element of T^2 / D
+
+    ``terms`` share the left-hand side (T's labels); ``operands`` = [(X_p, Y_p), ...];
+    ``eps`` = one vector per T label, in T's label order.  Returns (E, T)."""
+    T = None
+    for e, (X, Y) in zip(terms, operands):
+        t = einsum(e, X, Y)
+        T = t if T is None else T + t
+    n = T.ndim
+    D = np.zeros(T.shape)
+    for q in range(n):
+        shape = [1] * n
+        shape[q] = T.shape[q]
+        D = D + signs[q] * np.asarray(eps[q], dtype=np.float64).reshape(shape)
+    return float(np.sum(T * T / D)), T

@@ -304,3 +304,66 @@ def test_golden_fixture_table1_parses():
                 counts[l] = counts.get(l, 0) + 1
         assert all(c in (1, 2) for c in counts.values())
         assert float(speedup) >= 1.0
+
+
+# ---- fused triples accumulation and energy ----------------------------------------------------
+
+TRI_TERMS = ["T[a,b,c,i,j,k] = X[d,a,b,i] * Y[c,d,j,k]",
+             "T[a,b,c,i,j,k] = -0.5 * X[d,c,b,i] * Y[a,d,j,k]",
+             "T[a,b,c,i,j,k] = 2.0 * X[d,a,b,k] * Y[c,d,j,i]"]
+
+
+def _tri_block(ext, seed):
+    ops = []
+    for t, e in enumerate(TRI_TERMS):
+        _, _, _, _, operands = oracle.parse(e)
+        ops.append(tuple(synth.tensor(tuple(ext[l] for l in ls), seed, 2 * t + q)
+                         for q, (_, ls) in enumerate(operands)))
+    eps = [synth.tensor((ext[l],), seed, 10 + q) + (1.5 if l in "abc" else -1.5)
+           for q, l in enumerate("abcijk")]
+    return ops, eps
+
+
+def test_triples_energy_brute_force_loops():
+    ext = dict(a=2, b=3, c=2, i=2, j=3, k=2, d=2)
+    ops, eps = _tri_block(ext, 31)
+    signs = [-1, -1, -1, 1, 1, 1]
+    E, T = oracle.triples_energy(TRI_TERMS, ops, eps, signs)
+    (X1, Y1), (X2, Y2), (X3, Y3) = ops
+    e_ref = 0.0
+    for a in range(2):
+        for b in range(3):
+            for c in range(2):
+                for i in range(2):
+                    for j in range(3):
+                        for k in range(2):
+                            t = 0.0
+                            for d in range(2):
+                                t += X1[d, a, b, i] * Y1[c, d, j, k]
+                                t += -0.5 * X2[d, c, b, i] * Y2[a, d, j, k]
+                                t += 2.0 * X3[d, a, b, k] * Y3[c, d, j, i]
+                            assert abs(T[a, b, c, i, j, k] - t) <= 1e-15
+                            D = -eps[0][a] - eps[1][b] - eps[2][c] + eps[3][i] + eps[4][j] + eps[5][k]
+                            e_ref += t * t / D
+    assert abs(E - e_ref) <= 1e-13 * abs(e_ref)
+    assert E < 0   # every denominator is negative
+
+
+def test_triples_energy_cancelling_terms_and_closed_form():
+    ext = dict(a=3, b=2, c=4, i=2, j=3, k=2, d=5)
+    X = synth.tensor((5, 3, 2, 2), 32, 0)
+    Y = synth.tensor((4, 5, 3, 2), 32, 1)
+    eps = [np.full(ext[l], 0.25) for l in "abcijk"]
+    terms = ["T[a,b,c,i,j,k] = X[d,a,b,i] * Y[c,d,j,k]", "T[a,b,c,i,j,k] = -1.0 * X[d,a,b,i] * Y[c,d,j,k]"]
+    E, T = oracle.triples_energy(terms, [(X, Y), (X, Y)], eps, [1, 1, -1, 1, 1, 1])
+    assert E == 0.0 and not T.any()
+    # d = 1 and outer-product operands: T = x_a x_b x_i y_c y_j y_k; with D = 1 everywhere
+    # E = product of the six squared norms
+    v = {l: synth.tensor((ext[l],), 33, q) for q, l in enumerate("abcijk")}
+    X1 = np.einsum("a,b,i->abi", v["a"], v["b"], v["i"]).reshape((1, 3, 2, 2), order="C")
+    Y1 = np.einsum("c,j,k->cjk", v["c"], v["j"], v["k"]).reshape((4, 1, 3, 2), order="C")
+    eps1 = [np.full(ext[l], 1.0 / 6.0) for l in "abcijk"]
+    E1, _ = oracle.triples_energy(terms[:1], [(np.asfortranarray(X1), np.asfortranarray(Y1))], eps1,
+                                  [1] * 6)
+    closed = np.prod([float(np.dot(v[l], v[l])) for l in "abcijk"])
+    assert abs(E1 - closed) <= 1e-13 * closed
