@@ -59,8 +59,11 @@ def args_parse():
     ap.add_argument("--pc-tile", type=int, default=-1, help="batched tile configuration of --profile-case triples")
     ap.add_argument("--ablation", action="store_true",
                     help="Table 1 natural vs planned order, and every TTGT form vs the chosen one")
-    ap.add_argument("--workload", default="ccsd", choices=["ccsd", "triples", "small"],
-                    help="ccsd: the headline line; triples: the batched workload (separate JSON line)")
+    ap.add_argument("--workload", default="ccsd", choices=["ccsd", "triples", "small", "triples_energy"],
+                    help="ccsd: the headline line; triples: the batched workload; triples_energy: the "
+                         "fused nine-term accumulation with its energy epilogue (separate JSON lines)")
+    ap.add_argument("--te-blocks", type=int, default=4096, help="triples_energy: blocks")
+    ap.add_argument("--te-f64-blocks", type=int, default=64, help="triples_energy: blocks of the FP64 leg")
     ap.add_argument("--sweep", default=None, choices=["transpose"],
                     help="time the transpose sweep (rank-4/rank-6, FP32/FP64, 64 MiB - 2 GiB) and exit")
     return ap.parse_args()
@@ -168,6 +171,115 @@ def run_triples(a) -> int:
         del blocks, ws, res, g
         torch.cuda.empty_cache()
     out["split_speedup_over_fp64"] = out["native"]["ms_per_step"] / out["split_bf16"]["ms_per_step"]
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_triples_energy(a) -> int:
+    """The fused CCSD(T)-style accumulation: per block, T[a,b,c,i,j,k] = the nine permuted terms
+    sign * X_p[d,..] * Y_p[..,d,..] and E_b = sum T^2 / D_b, with D the signed sum of per-label
+    eps vectors; extents uniform 8..32 (the batched triples table, seed 3), operands uniform
+    [-1,1) (seed 11), eps uniform in [1,2) (virtual) and [-2,-1) (occupied).  One launch per step;
+    T never goes to memory.  Parity on the three smallest blocks against the CPU oracle.  Prints
+    one JSON line (not the headline line)."""
+    import numpy as np
+    import torch
+    import paper_2102_06827_gb300 as comet
+    import synth
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from triples_terms import LABELS, SIGNS, T_LABELS, operand_labels, terms
+    dev = torch.device("cuda", 0)
+    tl = terms()
+    col = {l: q for q, l in enumerate(LABELS)}
+    out = {"workload": "fused triples energy: nine permuted terms per block, E_b = sum T^2/D_b; "
+                       "extents uniform 8..32 (seed 3), operands uniform [-1,1) (seed 11)"}
+
+    def build(n_blocks, dtype):
+        ext = synth.triples_blocks(4096)[:n_blocks]
+        sizes, eps_sizes = [], []
+        for b in range(n_blocks):
+            for e in tl:
+                for ls in operand_labels(e):
+                    sizes.append(int(np.prod([ext[b, col[l]] for l in ls])))
+            for l in T_LABELS:
+                eps_sizes.append(int(ext[b, col[l]]))
+        sizes = np.array(sizes, dtype=np.int64)
+        total = int(sizes.sum())
+        buf = torch.empty(total, dtype=dtype, device=dev)
+        chunk = 1 << 27
+        for c0 in range(0, total, chunk):
+            n = min(chunk, total - c0)
+            buf[c0:c0 + n] = synth.torch_uniform(11, c0 // chunk, n, dev).to(dtype)
+        offs = np.concatenate([[0], np.cumsum(sizes)[:-1]]) * buf.element_size()
+        ops = torch.tensor(offs, dtype=torch.int64, device=dev) + buf.data_ptr()
+        eps_sizes = np.array(eps_sizes, dtype=np.int64)
+        shift = np.concatenate([np.full(n, 1.5 if q % 6 < 3 else -1.5) for q, n in enumerate(eps_sizes)])
+        ebuf = (synth.torch_uniform(12, 0, int(eps_sizes.sum()), dev) * 0.5 +
+                torch.from_numpy(shift).to(dev)).to(dtype)
+        eoffs = np.concatenate([[0], np.cumsum(eps_sizes)[:-1]]) * ebuf.element_size()
+        eps = torch.tensor(eoffs, dtype=torch.int64, device=dev) + ebuf.data_ptr()
+        return ext, buf, ops, ebuf, eps, sizes, eps_sizes
+
+    def parity(ext, buf, ebuf, sizes, eps_sizes, energies, dtype, n_check=3):
+        import oracle
+        hb = buf  # host copies of the checked blocks only
+        per_block = len(tl) * 2
+        starts = np.concatenate([[0], np.cumsum(sizes)])
+        estarts = np.concatenate([[0], np.cumsum(eps_sizes)])
+        sel = np.argsort(np.prod(ext[:, :6], axis=1))[:n_check]
+        worst = 0.0
+        for b in sel:
+            ops = []
+            for p, e in enumerate(tl):
+                pair = []
+                for q, ls in enumerate(operand_labels(e)):
+                    k = b * per_block + 2 * p + q
+                    v = hb[int(starts[k]):int(starts[k + 1])].double().cpu().numpy()
+                    pair.append(np.reshape(v, [int(ext[b, col[l]]) for l in ls], order="F"))
+                ops.append(tuple(pair))
+            eps = [ebuf[int(estarts[b * 6 + q]):int(estarts[b * 6 + q + 1])].double().cpu().numpy()
+                   for q in range(6)]
+            ref = oracle.triples_energy(tl, ops, eps, SIGNS)[0]
+            worst = max(worst, abs(float(energies[b]) - ref) / abs(ref))
+        return {"blocks": [int(x) for x in sel], "max_rel_err": worst}
+
+    for name, dtype, n_blocks, steps in (("f32", torch.float32, a.te_blocks, max(1, min(a.steps, 3))),
+                                         ("f64", torch.float64, a.te_f64_blocks, 1)):
+        ext, buf, ops, ebuf, eps, sizes, eps_sizes = build(n_blocks, dtype)
+        plan = comet.TriplesPlan(tl, LABELS, ext, SIGNS, dtype)
+        ws = plan.workspace(dev)
+        plan.prepare(ws)
+        en = torch.empty(n_blocks, dtype=torch.float64, device=dev)
+        plan.energy(ops, eps, en, ws)   # warm-up
+        comet.sync_status()
+        clocks = ClockSampler(0)
+        clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            plan.energy(ops, eps, en, ws)
+        e1.record()
+        torch.cuda.synchronize()
+        ck = clocks.stop() or {}
+        comet.sync_status()
+        t = e0.elapsed_time(e1) / steps
+        energies = en.cpu().numpy()
+        sm_mhz = ck.get("sm_mhz") or 1900.0
+        # FMA pipe peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flops per clock (FP64:
+        # the nominal 1.25 TFLOP/s); the kernel's useful flops are plan.flops
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12 if name == "f32" else FP64_NOMINAL_TFLOPS
+        achieved = plan.flops / (t * 1e-3) / 1e12
+        out[name] = {"blocks": n_blocks, "ms_per_step": t, "steps": steps, "tflops": achieved,
+                     "roofline": {"bound": "alu" if name == "f32" else "fp64", "achieved": achieved,
+                                  "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                                  "peak_source": ("FP32 FMA lanes x median SM clock under load" if name == "f32"
+                                                  else "nominal FP64 rate")},
+                     "tiles": plan.info["tiles"], "flops": plan.flops, "clocks": ck,
+                     "energy_sum": float(energies.sum()),
+                     "parity": parity(ext, buf, ebuf, sizes, eps_sizes, energies, dtype)}
+        del buf, ebuf, ops, eps, ws, en
+        torch.cuda.empty_cache()
     print(json.dumps(out), flush=True)
     return 0
 
@@ -605,6 +717,8 @@ def main():
         return run_triples(a)
     if a.workload == "small":
         return run_small_and_chain(a)
+    if a.workload == "triples_energy":
+        return run_triples_energy(a)
     if a.ablation:
         return run_ablation(a)
     import numpy as np

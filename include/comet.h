@@ -171,6 +171,48 @@ comet_status_t comet_plan_views(const char *expr, const comet_extent_t *extents,
                                 int n_dtypes, const comet_plan_opts_t *opts, comet_plan_t *out_plan);
 
 /*
+ * comet_plan_triples — fused accumulation of permuted contributions into six-index blocks and
+ * their energies (the CCSD(T) pattern of Section 3: a 6-D output from two 4-D inputs, with
+ * several permuted terms per block):
+ *     T_b = sum_p alpha_p * X_bp * Y_bp             (term p: the contraction terms[p])
+ *     E_b = sum over the elements of T_b of T_b^2 / D_b,
+ *     D_b[l_1..l_6] = sum_q signs[q] * eps_bq[l_q]  (l_q: the q-th label of T)
+ * T never goes to memory: each CTA holds a 4^6 tile of T_b in registers, adds every term's
+ * contribution into it and reduces its energy.
+ *   terms        n_terms (1..16) expressions with the same left-hand side T[l_1,...,l_6] (six
+ *                distinct labels) and two four-label operands that share exactly one label (the
+ *                summed one) and hold three labels of T each, e.g.
+ *                "T[a,b,c,i,j,k] = -1.0 * X[d,c,b,i] * Y[a,d,j,k]"
+ *   label_names  n_labels (<= 16) names covering every label of the terms
+ *   extents      n_blocks x n_labels extents >= 1 (row b: block b, columns as label_names)
+ *   signs        six entries, +1 or -1, in T's label order
+ *   dtype        COMET_F32 (FP32 products and sums of T) or COMET_F64; energies are FP64
+ * Errors: COMET_ERR_PARSE / COMET_ERR_LABEL / COMET_ERR_UNSUPPORTED for terms outside this form,
+ * COMET_ERR_SHAPE for extents below 1 or a block of 2^31 tiles or more, COMET_ERR_ARG otherwise.
+ * comet_plan_workspace() gives the device bytes of the block table.
+ */
+comet_status_t comet_plan_triples(const char *const *terms, int n_terms, const char *const *label_names,
+                                  int n_labels, int n_blocks, const int64_t *extents, const int *signs,
+                                  comet_dtype_t dtype, comet_plan_t *out_plan);
+
+/* comet_triples_prepare — uploads the block table into the workspace (once per workspace). */
+comet_status_t comet_triples_prepare(comet_plan_t plan, void *workspace, void *stream);
+
+/*
+ * comet_triples_energy — evaluates a triples plan (asynchronous on `stream`; graph-capturable
+ * after comet_triples_prepare).
+ *   operands   device array of n_blocks * n_terms * 2 device pointers, block-major: X then Y of
+ *              term 0, then of term 1, ...; each operand dense column-major in its term's label
+ *              order with the block's extents; 16-byte alignment not required
+ *   eps        device array of n_blocks * 6 device pointers to the eps vectors (dtype of the plan),
+ *              in T's label order
+ *   energies   device array of n_blocks doubles, overwritten
+ *   workspace  the prepared workspace
+ */
+comet_status_t comet_triples_energy(comet_plan_t plan, const void *operands, const void *eps,
+                                    double *energies, void *workspace, void *stream);
+
+/*
  * comet_adjoint_expr — the expression of the gradient of a contraction with respect to one
  * operand.  For out = alpha * prod_t X_t (every label in exactly two tensors), the gradient of
  * <G, out> with respect to X_p is alpha * (G contracted with every X_t, t != p) written onto

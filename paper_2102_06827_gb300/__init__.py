@@ -264,6 +264,72 @@ class BatchedPlan:
             pass
 
 
+class TriplesPlan:
+    """comet_plan_triples(): fused accumulation of permuted terms into six-index blocks and the
+    block energies E_b = sum T_b^2 / D_b (see include/comet.h).
+
+    terms        expressions "T[a,b,c,i,j,k] = [alpha *] X[d,a,b,i] * Y[c,d,j,k]" (same T)
+    label_names  every label, the columns of ``extents``
+    extents      n_blocks x n_labels integers
+    signs        six +1 / -1, the sign of each T label's eps in D
+    """
+
+    def __init__(self, terms, label_names, extents, signs, dtype):
+        import numpy as np
+        L = lib()
+        ext = np.ascontiguousarray(np.asarray(extents, dtype=np.int64))
+        self.n_blocks, n_labels = ext.shape
+        self.n_terms = len(terms)
+        self.dtype = _torch_dtype(_dtype_code(dtype))
+        tv = (ctypes.c_char_p * len(terms))(*[t.encode() for t in terms])
+        nv = (ctypes.c_char_p * n_labels)(*[n.encode() for n in label_names])
+        sv = (ctypes.c_int * 6)(*[int(x) for x in signs])
+        self._ext = ext
+        h = ctypes.c_void_p()
+        _lib.check(L.comet_plan_triples(tv, len(terms), nv, n_labels, self.n_blocks,
+                                        ext.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), sv,
+                                        _dtype_code(dtype), ctypes.byref(h)), "comet_plan_triples")
+        self._h = h
+        ws = ctypes.c_size_t()
+        _lib.check(L.comet_plan_workspace(h, ctypes.byref(ws)), "comet_plan_workspace")
+        self.workspace_bytes = ws.value
+        f = ctypes.c_double()
+        _lib.check(L.comet_plan_flops(h, ctypes.byref(f)), "comet_plan_flops")
+        self.flops = f.value
+        self.info = self.describe()
+
+    def describe(self) -> dict:
+        buf = ctypes.create_string_buffer(1 << 16)
+        _lib.check(lib().comet_plan_describe(self._h, buf, len(buf)), "comet_plan_describe")
+        return json.loads(buf.value.decode())
+
+    def workspace(self, device="cuda"):
+        import torch
+        return torch.empty(max(16, self.workspace_bytes), dtype=torch.uint8, device=device)
+
+    def prepare(self, workspace, stream=None):
+        _lib.check(lib().comet_triples_prepare(self._h, _ptr(workspace), _stream_handle(stream)),
+                   "comet_triples_prepare")
+
+    def energy(self, operand_ptrs, eps_ptrs, energies, workspace, stream=None):
+        """operand_ptrs: device int64 tensor of n_blocks*n_terms*2 pointers (X, Y per term);
+        eps_ptrs: device int64 tensor of n_blocks*6 pointers; energies: device float64[n_blocks]."""
+        _lib.check(lib().comet_triples_energy(self._h, _ptr(operand_ptrs), _ptr(eps_ptrs), _ptr(energies),
+                                              _ptr(workspace), _stream_handle(stream)), "comet_triples_energy")
+        return energies
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().comet_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def transpose(x, extents, perm, out=None, stream=None):
     """comet_transpose(): bit-exact permutation of a column-major tensor.
 

@@ -24,6 +24,7 @@ EXPORTS = [
     "comet_plan_flops_natural", "comet_plan_describe", "comet_adjoint_expr", "comet_contract", "comet_contract_noalloc", "comet_contract_host",
     "comet_transpose", "comet_fill", "comet_plan_batched", "comet_batched_num_tiles", "comet_batched_set_tile",
     "comet_batched_prepare", "comet_contract_batched", "comet_batched_autotune",
+    "comet_plan_triples", "comet_triples_prepare", "comet_triples_energy",
     "comet_profile_enable", "comet_profile_read", "comet_sync_status", "comet_plan_destroy", "comet_status_string", "comet_last_error_message",
     "comet_version",
 ]
@@ -99,6 +100,11 @@ def load():
     L.comet_batched_autotune.argtypes = [vp, vp, vp, vp, ctypes.c_int, vp,
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]
+    L.comet_plan_triples.argtypes = [ctypes.POINTER(ctypes.c_char_p), ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_char_p), ctypes.c_int, ctypes.c_int, i64p,
+                                     ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(vp)]
+    L.comet_triples_prepare.argtypes = [vp, vp, vp]
+    L.comet_triples_energy.argtypes = [vp, vp, vp, vp, vp, vp]
     L.comet_profile_enable.argtypes = [ctypes.c_int]
     L.comet_profile_read.argtypes = [ctypes.POINTER(KernelStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.comet_sync_status.argtypes = [vp]

@@ -42,9 +42,10 @@ int *device_status_word() {
 
 // ---- kernel timing ------------------------------------------------------------------------
 static const char *kKindNames[] = {"transpose", "scale_copy", "split_prepass", "gemm_split_bf16",
-                                   "gemm_f64", "batched_f64", "batched_split", "gemm_emu_bf16x6", "gemv"};
+                                   "gemm_f64", "batched_f64", "batched_split", "gemm_emu_bf16x6", "gemv",
+                                   "triples_energy"};
 enum { PK_TRANSPOSE = 0, PK_SCALE, PK_PREPASS, PK_SPLIT, PK_F64, PK_BATCHED_F64, PK_BATCHED_SPLIT, PK_EMU,
-       PK_GEMV, PK_N };
+       PK_GEMV, PK_TRIPLES, PK_N };
 
 struct ProfRec {
     int kind;
@@ -511,7 +512,8 @@ comet_status_t comet_plan_flops_natural(comet_plan_t plan, double *flops) {
 
 comet_status_t comet_plan_describe(comet_plan_t plan, char *buf, size_t len) {
     if (!plan || !buf) return COMET_ERR_NULL;
-    std::string s = plan->p.batched ? describe_batched(plan->p) : describe_plan(plan->p);
+    std::string s = plan->p.batched ? describe_batched(plan->p)
+                    : plan->p.triples ? describe_triples(plan->p) : describe_plan(plan->p);
     if (s.size() + 1 > len) return COMET_ERR_ARG;
     std::memcpy(buf, s.c_str(), s.size() + 1);
     return COMET_OK;
@@ -522,6 +524,7 @@ comet_status_t comet_contract(comet_plan_t plan, const void *const *inputs, void
     if (!plan || !inputs || !output) return COMET_ERR_NULL;
     const Plan &P = plan->p;
     if (P.batched) { set_error("batched plan: use comet_contract_batched"); return COMET_ERR_ARG; }
+    if (P.triples) { set_error("triples plan: use comet_triples_energy"); return COMET_ERR_ARG; }
     for (int i = 0; i < P.n_in; ++i) {
         if (!inputs[i]) return COMET_ERR_NULL;
         if (!aligned16(inputs[i])) return COMET_ERR_ALIGN;
@@ -573,6 +576,7 @@ comet_status_t comet_contract_noalloc(comet_plan_t plan, const void *const *inpu
     if (!plan || !inputs || !output) return COMET_ERR_NULL;
     const Plan &P = plan->p;
     if (P.batched) { set_error("batched plan: use comet_contract_batched"); return COMET_ERR_ARG; }
+    if (P.triples) { set_error("triples plan: use comet_triples_energy"); return COMET_ERR_ARG; }
     if (P.workspace > COMET_NOALLOC_MAX_BYTES) {
         set_error("plan needs " + std::to_string(P.workspace) + " bytes of scratch; the no-alloc limit is " +
                   std::to_string((size_t)COMET_NOALLOC_MAX_BYTES));
@@ -593,7 +597,7 @@ comet_status_t comet_contract_host(comet_plan_t plan, const void *const *host_in
                                    void *const *dev_inputs, void *dev_output, void *workspace, void *stream) {
     if (!plan || !host_inputs || !host_output || !dev_inputs || !dev_output) return COMET_ERR_NULL;
     const Plan &P = plan->p;
-    if (P.batched) return COMET_ERR_ARG;
+    if (P.batched || P.triples) return COMET_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     size_t es = dtype_size(P.dtype);
     if (P.pipe.ok) {   // slice pipeline: pinned host buffers, aligned device buffers

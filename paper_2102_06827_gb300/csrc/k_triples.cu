@@ -1,0 +1,667 @@
+// Fused triples accumulation and energy (comet_plan_triples / comet_triples_energy).
+//
+// The CCSD(T) pattern the paper's Section 3 cites: a six-index block T_b built from two
+// four-index operands per term, with several permuted terms summed into the same T_b, and an
+// energy E_b = sum T_b^2 / D_b whose denominator is a signed sum of per-label vectors.  Every term
+// contracts a single label (the paper's Section 2 contraction with K = that label's extent),
+// so each term is a tiny-K outer-product sum and T_b is far larger than the operands: writing
+// T_b to memory and reading it back per term would make the path bound by HBM traffic that the
+// algorithm does not need.  Here T_b never leaves the SM:
+//
+//   * a work item is one 4^6 tile of one block; persistent CTAs take items in chunks from one
+//     atomic counter, walking the blocks in order;
+//   * each of the 256 threads holds 16 elements of the tile in registers: 4 x 4 along two
+//     "owned" labels, the other four labels fixed per thread;
+//   * a step is one term and one chunk of its summed label (32 values for FP32, 16 for FP64):
+//     the X and Y tiles (chunk x 4^3) of step s+1 are copied into shared memory with cp.async
+//     while step s runs on the other buffer; each thread adds its 16 dot products into per-term
+//     sums and, when the term is complete, alpha times them into T.  Depending on whether its
+//     owned labels sit on X or Y, a thread reads 4 + 4, 16 + 1 or 1 + 16 values per summed
+//     index (four code paths);
+//   * after the last term, the thread's 16 elements give their T^2 / D, summed in FP64 per
+//     thread across the CTA's items of one block and added to E_b once per block change.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <new>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "../../include/comet.h"
+#include "launch.h"
+#include "params.h"
+#include "plan.hpp"
+
+struct comet_plan_s {
+    comet::Plan p;
+};
+
+namespace comet {
+
+int prof_begin(int kind, cudaStream_t s);
+void prof_end(int idx, cudaStream_t s);
+void set_error_message(const std::string &s);
+
+namespace tri {
+constexpr int TS = 4;          // tile edge per label
+constexpr int NT = 256;        // threads: 4^4 fixed-label combinations
+constexpr int KC = 32;         // summed-label values staged per pass (FP32; 16 for FP64)
+constexpr int R = TS * TS * TS;   // operand tile rows (three T labels)
+constexpr int RP = R + 4;         // row pitch: 16-byte aligned rows, shifted banks
+constexpr int CHUNK = 16;      // items taken per counter increment
+constexpr int PK_TRIPLES_ID = 9;
+
+struct TermDev {
+    double alpha;
+    int8_t x_q[4], y_q[4];     // T label position per operand dimension, -1 = summed label
+    int8_t x_col[4], y_col[4]; // extent-table column per operand dimension
+    int8_t x_dig[4], y_dig[4]; // tile-row digit per dimension (owned labels first), -1 = summed
+    int8_t d_col;
+    int8_t pad[7];
+};
+
+struct Args {
+    int n_terms, n_labels, n_blocks;
+    int8_t t_col[6], own[2], fixed[4];
+    float own_sign[2], fixed_sign[4];
+    TermDev term[16];
+    const int32_t *ext;        // n_blocks x n_labels
+    const int64_t *prefix;     // n_blocks + 1
+    const void *const *ops;    // n_blocks x n_terms x 2
+    const void *const *eps;    // n_blocks x 6
+    double *energies;
+    unsigned long long *counter;
+    int64_t total;
+};
+}  // namespace tri
+
+using namespace tri;
+
+// value of a 6-entry register array at a runtime position (a select chain: no local memory)
+__device__ __forceinline__ int pick6(const int (&v)[6], int q) {
+    int r = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) r = q == i ? v[i] : r;
+    return r;
+}
+
+// Operand tile addressing of one step (term p, summed-label chunk k0): element (kk, r) of the
+// tile sits at base + kk * sd + digit0(r) * s0 + digit1(r) * s1 + digit2(r) * s2 (the operand's
+// three T labels in its dimension order, 2-bit digits of r), present when kk < kn and each
+// digit is below rem (the tile's remaining extent along that label, at most 4).  32-bit offsets:
+// every operand has fewer than 2^31 elements (checked when planning).
+struct TileAddr {
+    int base, sd, s[3], rem[3];
+};
+
+template <typename T>
+constexpr int kc_of() { return sizeof(T) == 4 ? KC : KC / 2; }
+
+__device__ __forceinline__ void cp_async_elem(void *dst, const void *src, int bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if (bytes == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// issue the asynchronous copies of one operand tile into S (entries outside the tile are not
+// written: they only feed T elements outside the block, which the energy skips)
+// Step entries of one operand: index idx -> (kk, r) with 8 consecutive kk and 4 consecutive r
+// per 32 lanes: with the row pitch = 4 mod 32 floats the lanes of a warp hit 32 different banks.
+template <int KCt>
+__device__ __forceinline__ void entry(int idx, int &kk, int &r) {
+    constexpr int hb = KCt / 8 == 4 ? 2 : 1;   // bits of the high kk part
+    const int rest = idx >> 5;
+    kk = ((rest & (KCt / 8 - 1)) << 3) | (idx & 7);
+    r = ((rest >> hb) << 2) | ((idx >> 3) & 3);
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_async(T (*S)[RP], const T *__restrict__ src, const TileAddr &ta, int kn) {
+    constexpr int kc = kc_of<T>();
+#pragma unroll
+    for (int it = 0; it < kc * R / NT; ++it) {
+        const int idx = threadIdx.x + it * NT;
+        int kk, r;
+        entry<kc>(idx, kk, r);
+        const int d0 = r & 3, d1 = (r >> 2) & 3, d2 = r >> 4;
+        if (kk < kn && d0 < ta.rem[0] && d1 < ta.rem[1] && d2 < ta.rem[2])
+            cp_async_elem(&S[kk][r], src + (ta.base + kk * ta.sd + d0 * ta.s[0] + d1 * ta.s[1] + d2 * ta.s[2]),
+                          (int)sizeof(T));
+    }
+}
+
+// addressing of one operand for a step: q / col per dimension (q = -1: the summed label)
+__device__ __forceinline__ TileAddr tile_addr(const int8_t *q, const int8_t *col, const int8_t *dig,
+                                              const int32_t *ext_b, const int (&tbase)[6], const int (&text)[6],
+                                              int k0) {
+    TileAddr ta;
+    int st = 1;
+    ta.base = 0;
+    ta.sd = 0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        if (q[m] < 0) {
+            ta.sd = st;
+            ta.base += k0 * st;
+        } else {
+            const int b0 = pick6(tbase, q[m]);
+            const int rm = min(TS, pick6(text, q[m]) - b0);
+            ta.base += b0 * st;
+            if (dig[m] == 0) { ta.s[0] = st; ta.rem[0] = rm; }
+            if (dig[m] == 1) { ta.s[1] = st; ta.rem[1] = rm; }
+            if (dig[m] == 2) { ta.s[2] = st; ta.rem[2] = rm; }
+        }
+        st *= ext_b[col[m]];
+    }
+    return ta;
+}
+
+// alpha times the X entries this thread copied for a step (after their copies completed)
+template <typename T>
+__device__ __forceinline__ void scale_own(T (*S)[RP], const TileAddr &ta, int kn, T alpha) {
+    constexpr int kc = kc_of<T>();
+#pragma unroll
+    for (int it = 0; it < kc * R / NT; ++it) {
+        const int idx = threadIdx.x + it * NT;
+        int kk, r;
+        entry<kc>(idx, kk, r);
+        const int d0 = r & 3, d1 = (r >> 2) & 3, d2 = r >> 4;
+        if (kk < kn && d0 < ta.rem[0] && d1 < ta.rem[1] && d2 < ta.rem[2]) S[kk][r] *= alpha;
+    }
+}
+
+// four consecutive shared-memory values (16-byte aligned): one 128-bit load for FP32, two for FP64
+__device__ __forceinline__ void load4(const float *p, float (&o)[4]) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void load4(const double *p, double (&o)[4]) {
+    const double2 v0 = reinterpret_cast<const double2 *>(p)[0], v1 = reinterpret_cast<const double2 *>(p)[1];
+    o[0] = v0.x; o[1] = v0.y; o[2] = v1.x; o[3] = v1.y;
+}
+
+// The thread's 16 contributions of one step: acc[u][v] += sum_kk X[kk][rx(u,v)] * Y[kk][ry(u,v)].
+// Owned labels are the fastest tile digits: u (or v) runs along 4 consecutive entries.
+// case 0: u on X, v on Y; 1: u on Y, v on X; 2: both on X (u, then v = digit 1); 3: both on Y.
+template <typename T>
+__device__ __forceinline__ void step_compute(const T (*Xs)[RP], const T (*Ys)[RP], int kn, int rx, int ry,
+                                             int kase, T (&acc)[16]) {
+    if (kase == 0) {
+#pragma unroll 2
+        for (int kk = 0; kk < kn; ++kk) {
+            T xu[4], yv[4];
+            load4(&Xs[kk][rx], xu);
+            load4(&Ys[kk][ry], yv);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u * 4 + v] = fma(xu[u], yv[v], acc[u * 4 + v]);
+        }
+    } else if (kase == 1) {
+#pragma unroll 2
+        for (int kk = 0; kk < kn; ++kk) {
+            T yu[4], xv[4];
+            load4(&Ys[kk][ry], yu);
+            load4(&Xs[kk][rx], xv);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u * 4 + v] = fma(xv[v], yu[u], acc[u * 4 + v]);
+        }
+    } else if (kase == 2) {
+#pragma unroll 2
+        for (int kk = 0; kk < kn; ++kk) {
+            const T y = Ys[kk][ry];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                T xq[4];
+                load4(&Xs[kk][rx + 4 * v], xq);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u * 4 + v] = fma(xq[u], y, acc[u * 4 + v]);
+            }
+        }
+    } else {
+#pragma unroll 2
+        for (int kk = 0; kk < kn; ++kk) {
+            const T x = Xs[kk][rx];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                T yq[4];
+                load4(&Ys[kk][ry + 4 * v], yq);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u * 4 + v] = fma(x, yq[u], acc[u * 4 + v]);
+            }
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT, 3) triples_kernel(const Args a) {
+    constexpr int kc = kc_of<T>();
+    __shared__ __align__(16) T Xs[2][kc][RP];
+    __shared__ __align__(16) T Ys[2][kc][RP];
+    __shared__ int32_t s_ext[16];
+    __shared__ int64_t s_item;
+    __shared__ double s_red[NT / 32];
+    __shared__ TermDev s_term[16];
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        if (t == i) s_term[i] = a.term[i];
+    int f[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) f[j] = (t >> (2 * j)) & 3;
+
+    int b = 0;                 // current block
+    double e_acc = 0.0;
+    auto flush = [&](int blk) {   // CTA sum of e_acc into E[blk]
+        double v = e_acc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((t & 31) == 0) s_red[t >> 5] = v;
+        __syncthreads();
+        if (t == 0) {
+            double sum = 0;
+            for (int w = 0; w < NT / 32; ++w) sum += s_red[w];
+            if (sum != 0.0) atomicAdd(a.energies + blk, sum);
+        }
+        __syncthreads();
+        e_acc = 0.0;
+    };
+    bool have = false;
+    while (true) {
+        if (t == 0) s_item = (int64_t)atomicAdd(a.counter, (unsigned long long)CHUNK);
+        __syncthreads();
+        const int64_t first = s_item;
+        __syncthreads();
+        if (first >= a.total) break;
+        const int64_t last = min(first + (int64_t)CHUNK, a.total);
+        for (int64_t item = first; item < last; ++item) {
+            // block of this item (blocks are walked in order: search from the current one, or
+            // from the start when the chunk lies before it)
+            int nb = b;
+            if (item < a.prefix[nb]) nb = 0;
+            if (item >= a.prefix[nb + 1]) {
+                int lo = nb, hi = a.n_blocks;   // prefix[lo] <= item < prefix[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (a.prefix[mid] <= item) lo = mid; else hi = mid;
+                }
+                nb = lo;
+            }
+            if (!have || nb != b) {
+                if (have) flush(b);
+                b = nb;
+                have = true;
+                if (t < a.n_labels) s_ext[t] = a.ext[(int64_t)b * a.n_labels + t];
+                __syncthreads();
+            }
+            // tile coordinates (first T label fastest)
+            int tbase[6], text[6];
+            int64_t rem = item - a.prefix[b];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                text[q] = s_ext[a.t_col[q]];
+                const int nt = (text[q] + TS - 1) / TS;
+                tbase[q] = (int)(rem % nt) * TS;
+                rem /= nt;
+            }
+            T acc[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) acc[e] = T(0);
+            // steps: (term p, chunk k0) in order; step s+1's tiles are copied while step s runs
+            int p = 0, k0 = 0, buf = 0;
+            auto issue = [&](int pp, int kk0, int bb) {
+                const TermDev &tm = s_term[pp];
+                const int K = s_ext[tm.d_col];
+                const int kn = min(kc, K - kk0);
+                const T *X = reinterpret_cast<const T *>(a.ops[((int64_t)b * a.n_terms + pp) * 2]);
+                const T *Y = reinterpret_cast<const T *>(a.ops[((int64_t)b * a.n_terms + pp) * 2 + 1]);
+                const TileAddr tx = tile_addr(tm.x_q, tm.x_col, tm.x_dig, s_ext, tbase, text, kk0);
+                stage_async<T>(Xs[bb], X, tx, kn);
+                stage_async<T>(Ys[bb], Y, tile_addr(tm.y_q, tm.y_col, tm.y_dig, s_ext, tbase, text, kk0), kn);
+                cp_async_commit();
+                return tx;
+            };
+            __syncthreads();   // the previous item's last step is done with both buffers
+            TileAddr tx_cur = issue(0, 0, 0);
+            while (p < a.n_terms) {
+                const TermDev &tm = s_term[p];
+                const int K = s_ext[tm.d_col];
+                const int kn = min(kc, K - k0);
+                int pn = p, kn0 = k0 + kc;   // next step
+                if (kn0 >= K) { pn = p + 1; kn0 = 0; }
+                cp_async_wait_all();
+                if (tm.alpha != 1.0) scale_own<T>(Xs[buf], tx_cur, kn, (T)tm.alpha);
+                __syncthreads();   // step s is in buffer buf; step s-1's reads of buf^1 are done
+                TileAddr tx_next = tx_cur;
+                if (pn < a.n_terms) tx_next = issue(pn, kn0, buf ^ 1);
+                // tile-row offsets of this thread's fixed labels, and where its owned labels sit
+                int rx = 0, ry = 0;
+                bool u_on_x = false, v_on_x = false;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const int qx = tm.x_q[m], qy = tm.y_q[m];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (qx == a.fixed[j]) rx += f[j] << (2 * tm.x_dig[m]);
+                        if (qy == a.fixed[j]) ry += f[j] << (2 * tm.y_dig[m]);
+                    }
+                    u_on_x |= qx == a.own[0];
+                    v_on_x |= qx == a.own[1];
+                }
+                const int kase = u_on_x ? (v_on_x ? 2 : 0) : (v_on_x ? 1 : 3);
+                step_compute<T>(Xs[buf], Ys[buf], kn, rx, ry, kase, acc);
+                p = pn;
+                k0 = kn0;
+                buf ^= 1;
+                tx_cur = tx_next;
+            }
+            int own_b[2], own_e[2], fix_c[4], fix_e[4];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) { own_b[j] = pick6(tbase, a.own[j]); own_e[j] = pick6(text, a.own[j]); }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) { fix_c[j] = pick6(tbase, a.fixed[j]) + f[j]; fix_e[j] = pick6(text, a.fixed[j]); }
+            // energy of the thread's elements: D = sum_q sign_q eps_q[coordinate q]
+            bool fixed_ok = true;
+            double dfix = 0.0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const bool in = fix_c[j] < fix_e[j];
+                fixed_ok &= in;
+                if (in) dfix += a.fixed_sign[j] *
+                                (double)reinterpret_cast<const T *>(a.eps[(int64_t)b * 6 + a.fixed[j]])[fix_c[j]];
+            }
+            if (fixed_ok) {
+                const T *e0 = reinterpret_cast<const T *>(a.eps[(int64_t)b * 6 + a.own[0]]);
+                const T *e1 = reinterpret_cast<const T *>(a.eps[(int64_t)b * 6 + a.own[1]]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int c0 = own_b[0] + u;
+                    if (c0 >= own_e[0]) continue;
+                    const double d0 = dfix + a.own_sign[0] * (double)e0[c0];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const int c1 = own_b[1] + v;
+                        if (c1 >= own_e[1]) continue;
+                        const double tv = (double)acc[u * 4 + v];
+                        e_acc += tv * tv / (d0 + a.own_sign[1] * (double)e1[c1]);
+                    }
+                }
+            }
+        }
+    }
+    if (have) flush(b);
+}
+
+// ---- host side ------------------------------------------------------------------------------
+
+static comet_status_t plan_triples(const char *const *terms, int n_terms, const char *const *names,
+                                   int n_labels, int n_blocks, const int64_t *extents, const int *signs,
+                                   comet_dtype_t dtype, Plan *P, std::string *err) {
+    if (!terms || !names || !extents || !signs) return COMET_ERR_NULL;
+    if (n_terms < 1 || n_terms > 16) { *err = "1 to 16 terms"; return COMET_ERR_ARG; }
+    if (n_labels < 7 || n_labels > 16) { *err = "7 to 16 labels"; return COMET_ERR_ARG; }
+    if (n_blocks < 1) { *err = "no blocks"; return COMET_ERR_ARG; }
+    if (dtype != COMET_F32 && dtype != COMET_F64) { *err = "unknown dtype"; return COMET_ERR_DTYPE; }
+    std::map<std::string, int> col;
+    for (int l = 0; l < n_labels; ++l) {
+        if (!names[l]) return COMET_ERR_NULL;
+        if (col.count(names[l])) { *err = "label named twice"; return COMET_ERR_ARG; }
+        col[names[l]] = l;
+    }
+    TriplesPlan &tp = P->tri;
+    tp = TriplesPlan();
+    tp.n_terms = n_terms;
+    tp.n_labels = n_labels;
+    tp.n_blocks = n_blocks;
+    std::vector<std::string> tl;
+    std::ostringstream all;
+    for (int p = 0; p < n_terms; ++p) {
+        if (!terms[p]) return COMET_ERR_NULL;
+        ParsedExpr e;
+        comet_status_t st = parse_expr(terms[p], &e, err);
+        if (st != COMET_OK) return st;
+        if (e.op != 0 || e.ins.size() != 2) { *err = "a term is T[...] = [alpha *] X[...] * Y[...]"; return COMET_ERR_UNSUPPORTED; }
+        if (e.out.labels.size() != 6) { *err = "T has six labels"; return COMET_ERR_UNSUPPORTED; }
+        if (p == 0) tl = e.out.labels;
+        else if (e.out.labels != tl) { *err = "every term writes T with the same labels in the same order"; return COMET_ERR_LABEL; }
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j < i; ++j)
+                if (tl[i] == tl[j]) { *err = "repeated label in T"; return COMET_ERR_UNSUPPORTED; }
+        const auto &X = e.ins[0].labels, &Y = e.ins[1].labels;
+        if (X.size() != 4 || Y.size() != 4) { *err = "operands have four labels"; return COMET_ERR_UNSUPPORTED; }
+        TriTerm tt;
+        tt.alpha = e.alpha;
+        std::string dlab;
+        int seen[6] = {0, 0, 0, 0, 0, 0};
+        for (int side = 0; side < 2; ++side) {
+            const auto &L = side ? Y : X;
+            const auto &O = side ? X : Y;
+            for (int m = 0; m < 4; ++m) {
+                if (!col.count(L[m])) { *err = "label " + L[m] + " has no extent column"; return COMET_ERR_LABEL; }
+                int q = -1;
+                for (int i = 0; i < 6; ++i) if (tl[i] == L[m]) q = i;
+                const bool on_other = std::find(O.begin(), O.end(), L[m]) != O.end();
+                if (q < 0) {
+                    if (!on_other) { *err = "label " + L[m] + " is on one operand only and not on T"; return COMET_ERR_UNSUPPORTED; }
+                    if (!dlab.empty() && dlab != L[m]) { *err = "a term sums exactly one label"; return COMET_ERR_UNSUPPORTED; }
+                    dlab = L[m];
+                } else {
+                    if (on_other) { *err = "a label of T on both operands"; return COMET_ERR_UNSUPPORTED; }
+                    ++seen[q];
+                }
+                (side ? tt.y_q : tt.x_q)[m] = q;
+                (side ? tt.y_col : tt.x_col)[m] = col[L[m]];
+            }
+        }
+        if (dlab.empty()) { *err = "a term sums exactly one label"; return COMET_ERR_UNSUPPORTED; }
+        int cx = 0;
+        for (int m = 0; m < 4; ++m) cx += tt.x_q[m] < 0;
+        if (cx != 1) { *err = "the summed label appears once per operand"; return COMET_ERR_UNSUPPORTED; }
+        for (int q = 0; q < 6; ++q)
+            if (seen[q] != 1) { *err = "every label of T on exactly one operand"; return COMET_ERR_UNSUPPORTED; }
+        tt.d_col = col[dlab];
+        tp.terms.push_back(tt);
+        all << (p ? " ; " : "") << terms[p];
+    }
+    for (int q = 0; q < 6; ++q) {
+        if (!col.count(tl[q])) { *err = "label " + tl[q] + " has no extent column"; return COMET_ERR_LABEL; }
+        tp.t_col[q] = col[tl[q]];
+        if (signs[q] != 1 && signs[q] != -1) { *err = "signs are +1 or -1"; return COMET_ERR_ARG; }
+        tp.signs[q] = signs[q];
+    }
+    // owned pair: the two T labels that sit on different operands in the most terms
+    int best = -1;
+    for (int i = 0; i < 6; ++i)
+        for (int j = i + 1; j < 6; ++j) {
+            int split = 0;
+            for (auto &tt : tp.terms) {
+                bool ix = false, jx = false;
+                for (int m = 0; m < 4; ++m) { ix |= tt.x_q[m] == i; jx |= tt.x_q[m] == j; }
+                split += ix != jx;
+            }
+            if (split > best) { best = split; tp.own[0] = i; tp.own[1] = j; }
+        }
+    // block table
+    tp.ext.resize((size_t)n_blocks * n_labels);
+    tp.prefix.assign(n_blocks + 1, 0);
+    double flops = 0;
+    for (int b = 0; b < n_blocks; ++b) {
+        int64_t tiles = 1;
+        double tel = 1;
+        for (int l = 0; l < n_labels; ++l) {
+            const int64_t x = extents[(size_t)b * n_labels + l];
+            if (x < 1 || x > (1 << 30)) { *err = "extents between 1 and 2^30"; return COMET_ERR_SHAPE; }
+            tp.ext[(size_t)b * n_labels + l] = (int32_t)x;
+        }
+        for (int q = 0; q < 6; ++q) {
+            const int64_t x = extents[(size_t)b * n_labels + tp.t_col[q]];
+            tiles *= (x + TS - 1) / TS;
+            tel *= (double)x;
+            if (tiles >= (1ll << 31)) { *err = "a block of 2^31 tiles or more"; return COMET_ERR_SHAPE; }
+        }
+        for (auto &tt : tp.terms) {
+            flops += 2.0 * tel * (double)extents[(size_t)b * n_labels + tt.d_col];
+            for (int side = 0; side < 2; ++side) {   // 32-bit element offsets inside every operand
+                long double n = 1;
+                for (int m = 0; m < 4; ++m) n *= (long double)extents[(size_t)b * n_labels + (side ? tt.y_col : tt.x_col)[m]];
+                if (n >= 2147483648.0L) { *err = "an operand of 2^31 elements or more"; return COMET_ERR_SHAPE; }
+            }
+        }
+        tp.prefix[b + 1] = tp.prefix[b] + tiles;
+    }
+    size_t off = 0;
+    auto align = [](size_t x) { return (x + 255) / 256 * 256; };
+    tp.ws_ext = off;
+    off = align(off + tp.ext.size() * sizeof(int32_t));
+    tp.ws_prefix = off;
+    off = align(off + tp.prefix.size() * sizeof(int64_t));
+    tp.ws_counter = off;
+    off = align(off + 8);
+    P->triples = true;
+    P->batched = false;
+    P->workspace = off;
+    P->dtype = dtype;
+    P->flops = flops;
+    P->flops_natural = flops;
+    P->expr = all.str();
+    return COMET_OK;
+}
+
+std::string describe_triples(const Plan &P) {
+    const TriplesPlan &tp = P.tri;
+    std::ostringstream o;
+    o.precision(17);
+    o << "{\"triples\":true,\"terms\":" << tp.n_terms << ",\"blocks\":" << tp.n_blocks
+      << ",\"dtype\":\"" << (P.dtype == COMET_F32 ? "f32" : "f64") << "\",\"tiles\":" << tp.prefix.back()
+      << ",\"tile\":[4,4,4,4,4,4],\"own\":[" << tp.own[0] << "," << tp.own[1] << "],\"flops\":" << P.flops
+      << ",\"workspace\":" << P.workspace << "}";
+    return o.str();
+}
+
+}  // namespace comet
+
+using namespace comet;
+
+extern "C" {
+
+comet_status_t comet_plan_triples(const char *const *terms, int n_terms, const char *const *label_names,
+                                  int n_labels, int n_blocks, const int64_t *extents, const int *signs,
+                                  comet_dtype_t dtype, comet_plan_t *out_plan) {
+    if (!out_plan) return COMET_ERR_NULL;
+    *out_plan = nullptr;
+    comet_plan_s *h = new (std::nothrow) comet_plan_s;
+    if (!h) return COMET_ERR_INTERNAL;
+    std::string err;
+    comet_status_t st;
+    try {
+        st = plan_triples(terms, n_terms, label_names, n_labels, n_blocks, extents, signs, dtype, &h->p, &err);
+    } catch (...) {
+        st = COMET_ERR_INTERNAL;
+        err = "exception while planning";
+    }
+    if (st != COMET_OK) {
+        set_error_message(err);
+        delete h;
+        return st;
+    }
+    *out_plan = h;
+    return COMET_OK;
+}
+
+comet_status_t comet_triples_prepare(comet_plan_t plan, void *workspace, void *stream) {
+    if (!plan || !workspace) return COMET_ERR_NULL;
+    const Plan &P = plan->p;
+    if (!P.triples) { set_error_message("not a triples plan"); return COMET_ERR_ARG; }
+    if ((reinterpret_cast<uintptr_t>(workspace) & 15u) != 0) return COMET_ERR_ALIGN;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *w = static_cast<char *>(workspace);
+    cudaError_t e = cudaMemcpyAsync(w + P.tri.ws_ext, P.tri.ext.data(), P.tri.ext.size() * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w + P.tri.ws_prefix, P.tri.prefix.data(), P.tri.prefix.size() * sizeof(int64_t),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host tables may go away after the call
+    if (e != cudaSuccess) { set_error_message(cudaGetErrorString(e)); return COMET_ERR_CUDA; }
+    return COMET_OK;
+}
+
+comet_status_t comet_triples_energy(comet_plan_t plan, const void *operands, const void *eps, double *energies,
+                                    void *workspace, void *stream) {
+    if (!plan || !operands || !eps || !energies || !workspace) return COMET_ERR_NULL;
+    const Plan &P = plan->p;
+    if (!P.triples) { set_error_message("not a triples plan"); return COMET_ERR_ARG; }
+    if ((reinterpret_cast<uintptr_t>(workspace) & 15u) != 0) return COMET_ERR_ALIGN;
+    const TriplesPlan &tp = P.tri;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *w = static_cast<char *>(workspace);
+    Args a;
+    std::memset(&a, 0, sizeof(a));
+    a.n_terms = tp.n_terms;
+    a.n_labels = tp.n_labels;
+    a.n_blocks = tp.n_blocks;
+    int nf = 0;
+    for (int q = 0; q < 6; ++q) {
+        a.t_col[q] = (int8_t)tp.t_col[q];
+        if (q != tp.own[0] && q != tp.own[1]) {
+            a.fixed_sign[nf] = (float)tp.signs[q];
+            a.fixed[nf++] = (int8_t)q;
+        }
+    }
+    for (int j = 0; j < 2; ++j) {
+        a.own[j] = (int8_t)tp.own[j];
+        a.own_sign[j] = (float)tp.signs[tp.own[j]];
+    }
+    for (int p = 0; p < tp.n_terms; ++p) {
+        const TriTerm &tt = tp.terms[p];
+        a.term[p].alpha = tt.alpha;
+        for (int m = 0; m < 4; ++m) {
+            a.term[p].x_q[m] = (int8_t)tt.x_q[m];
+            a.term[p].y_q[m] = (int8_t)tt.y_q[m];
+            a.term[p].x_col[m] = (int8_t)tt.x_col[m];
+            a.term[p].y_col[m] = (int8_t)tt.y_col[m];
+        }
+        a.term[p].d_col = (int8_t)tt.d_col;
+        // tile digits: the owned labels an operand holds come first (own[0], then own[1]), so
+        // that they run along consecutive shared-memory entries; then its fixed labels
+        for (int side = 0; side < 2; ++side) {
+            const int *q = side ? tt.y_q : tt.x_q;
+            int8_t *dig = side ? a.term[p].y_dig : a.term[p].x_dig;
+            int nd = 0;
+            for (int m = 0; m < 4; ++m) dig[m] = -1;
+            for (int o = 0; o < 2; ++o)
+                for (int m = 0; m < 4; ++m) if (q[m] == tp.own[o]) dig[m] = (int8_t)nd++;
+            for (int m = 0; m < 4; ++m) if (q[m] >= 0 && dig[m] < 0) dig[m] = (int8_t)nd++;
+        }
+    }
+    a.ext = reinterpret_cast<const int32_t *>(w + tp.ws_ext);
+    a.prefix = reinterpret_cast<const int64_t *>(w + tp.ws_prefix);
+    a.ops = static_cast<const void *const *>(operands);
+    a.eps = static_cast<const void *const *>(eps);
+    a.energies = energies;
+    a.counter = reinterpret_cast<unsigned long long *>(w + tp.ws_counter);
+    a.total = tp.prefix.back();
+    cudaError_t e = cudaMemsetAsync(energies, 0, sizeof(double) * tp.n_blocks, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.counter, 0, 8, s);
+    if (e != cudaSuccess) { set_error_message(cudaGetErrorString(e)); return COMET_ERR_CUDA; }
+    if (a.total == 0) return COMET_OK;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t grid = std::min<int64_t>((int64_t)sms * 4, (a.total + CHUNK - 1) / CHUNK);
+    int h = prof_begin(PK_TRIPLES_ID, s);
+    if (P.dtype == COMET_F32) triples_kernel<float><<<(unsigned)grid, NT, 0, s>>>(a);
+    else triples_kernel<double><<<(unsigned)grid, NT, 0, s>>>(a);
+    e = cudaGetLastError();
+    prof_end(h, s);
+    if (e != cudaSuccess) { set_error_message(cudaGetErrorString(e)); return COMET_ERR_CUDA; }
+    return COMET_OK;
+}
+
+}  // extern "C"

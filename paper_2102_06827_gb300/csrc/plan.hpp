@@ -110,6 +110,26 @@ struct HostPipe {
     double model_s[2] = {0, 0};  // modelled seconds: unpipelined, pipelined
 };
 
+// Fused triples accumulation (comet_plan_triples): T_b = sum_p alpha_p X_bp * Y_bp over terms
+// that each contract one label between two 4-index operands into the same six-index T, and
+// E_b = sum T_b^2 / D_b.  Label maps per term; extents per block.
+struct TriTerm {
+    double alpha = 1.0;
+    int x_q[4] = {0, 0, 0, 0}, y_q[4] = {0, 0, 0, 0};   // per operand dimension: T label position, -1 = summed
+    int x_col[4] = {0, 0, 0, 0}, y_col[4] = {0, 0, 0, 0};   // extent-table column of each dimension's label
+    int d_col = 0;                                       // extent-table column of the summed label
+};
+struct TriplesPlan {
+    int n_terms = 0, n_labels = 0, n_blocks = 0;
+    std::vector<TriTerm> terms;
+    int t_col[6] = {0, 0, 0, 0, 0, 0};   // extent-table column of each T label
+    int signs[6] = {1, 1, 1, 1, 1, 1};   // sign of each T label's eps in D
+    int own[2] = {0, 1};                 // T labels a thread holds 4 x 4 of (the other four are fixed)
+    std::vector<int32_t> ext;            // n_blocks x n_labels
+    std::vector<int64_t> prefix;         // tiles (4 per label) before each block; n_blocks + 1
+    size_t ws_ext = 0, ws_prefix = 0, ws_counter = 0;
+};
+
 struct Plan {
     std::string expr;
     ParsedExpr parsed;
@@ -137,6 +157,8 @@ struct Plan {
     std::vector<double> block_flops;
     bool batched_ak = false, batched_bk = false, batched_swap = false;
     HostPipe pipe;                        // comet_contract_host slicing (one-step plans)
+    bool triples = false;                 // comet_plan_triples
+    TriplesPlan tri;
 };
 
 size_t dtype_size(comet_dtype_t t);
@@ -146,6 +168,7 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
                           int n_dtypes, const comet_plan_opts_t *opts, Plan *plan, std::string *err);
 
 std::string describe_plan(const Plan &p);
+std::string describe_triples(const Plan &p);
 
 // GEMM parameters of one binary step for given extents: lm / ln = labels of the M and N
 // operands, lc = labels of the output (all column-major), f = the TTGT form.

@@ -1,6 +1,7 @@
 """Host-side tests of the C ABI: symbol exports, parsing, classification, the TTGT form
 enumeration (Section 2 / Section 6) and the multi-operand order (Section 6, Table 1).
 No GPU needed: comet_plan does no device work."""
+import ctypes
 import itertools
 import os
 import re
@@ -331,3 +332,52 @@ def test_views_and_diagonals_layout():
     with pytest.raises(comet.CometError) as e:
         comet.BatchedPlan("C[i,j] = A[i,k,k] * B[k,j]", ["i", "j", "k"], [[3, 4, 5]], "f64")
     assert e.value.name == "COMET_ERR_UNSUPPORTED"
+
+
+def test_triples_plans():
+    import sys
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from triples_terms import LABELS, SIGNS, terms
+    ext = [[5, 6, 7, 3, 4, 5, 9], [8, 8, 8, 8, 8, 8, 40]]
+    p = comet.TriplesPlan(terms(), LABELS, ext, SIGNS, "f32")
+    info = p.info
+    assert info["triples"] and info["terms"] == 9 and info["blocks"] == 2
+    # tiles of 4 per label: 2*2*2*1*1*2 + 2^6
+    assert info["tiles"] == 16 + 64
+    assert info["flops"] == 9 * 2 * (5 * 6 * 7 * 3 * 4 * 5 * 9 + 8 ** 6 * 40)
+    # the owned pair sits on different operands in as many terms as any pair can (6 of 9)
+    import oracle
+
+    def split(x, y):
+        n = 0
+        for t in terms():
+            xl = oracle.parse(t)[4][0][1]
+            n += (x in xl) != (y in xl)
+        return n
+    a, b = info["own"]
+    best = max(split(x, y) for x, y in itertools.combinations("abcijk", 2))
+    assert split("abcijk"[a], "abcijk"[b]) == best == 6
+    bad = [
+        (["T[a,b,c,i,j,k] = X[d,a,b,i] * Y[c,d,j,k] * Z[d]"], "COMET_ERR_UNSUPPORTED"),   # three operands
+        (["T[a,b,c,i,j] = X[d,a,b,i] * Y[c,d,j]"], "COMET_ERR_UNSUPPORTED"),             # five labels
+        (["T[a,b,c,i,j,k] = X[d,a,b,i] * Y[c,e,j,k]"], "COMET_ERR_UNSUPPORTED"),         # no shared label
+        (["T[a,b,c,i,j,k] = X[a,a,b,i] * Y[c,d,j,k]"], "COMET_ERR_UNSUPPORTED"),         # T label twice
+        (["T[a,b,c,i,j,k] = X[d,a,b,i] * Y[c,d,j,k]", "T[b,a,c,i,j,k] = X[d,a,b,i] * Y[c,d,j,k]"],
+         "COMET_ERR_LABEL"),                                                            # different T order
+        (["T[a,b,c,i,j,k] += X[d,a,b,i] * Y[c,d,j,k]"], "COMET_ERR_UNSUPPORTED"),        # accumulate
+        (["T[a,b,c,i,j,k] = X[d,a,b,i] * Y[c,d,j,q]"], "COMET_ERR_LABEL"),               # no column for q
+    ]
+    for tl, code in bad:
+        with pytest.raises(comet.CometError) as e:
+            comet.TriplesPlan(tl, LABELS + ["e"], [[4] * 8], SIGNS, "f64")
+        assert e.value.name == code, tl
+    for ext_bad, code in (([[4, 4, 4, 4, 4, 0, 4]], "COMET_ERR_SHAPE"),):
+        with pytest.raises(comet.CometError) as e:
+            comet.TriplesPlan(terms(), LABELS, ext_bad, SIGNS, "f64")
+        assert e.value.name == code
+    with pytest.raises(comet.CometError) as e:
+        comet.TriplesPlan(terms(), LABELS, [[4] * 7], [1, 1, 1, 1, 1, 2], "f64")
+    assert e.value.name == "COMET_ERR_ARG"
+    # a triples plan refuses the contraction entry point (checked before any device work)
+    ptrs = (ctypes.c_void_p * 18)(*([16] * 18))
+    assert comet.lib().comet_contract(p._h, ptrs, ctypes.c_void_p(16), ctypes.c_void_p(16), None) == 12
