@@ -186,7 +186,8 @@ comet_status_t comet_plan_views(const char *expr, const comet_extent_t *extents,
  *   label_names  n_labels (<= 16) names covering every label of the terms
  *   extents      n_blocks x n_labels extents >= 1 (row b: block b, columns as label_names)
  *   signs        six entries, +1 or -1, in T's label order
- *   dtype        COMET_F32 (FP32 products and sums of T) or COMET_F64; energies are FP64
+ *   dtype        COMET_F32 (T, each T^2 / D and a tile's sum of them in FP32) or COMET_F64;
+ *                the block energies are summed in FP64
  * Errors: COMET_ERR_PARSE / COMET_ERR_LABEL / COMET_ERR_UNSUPPORTED for terms outside this form,
  * COMET_ERR_SHAPE for extents below 1 or a block of 2^31 tiles or more, COMET_ERR_ARG otherwise.
  * comet_plan_workspace() gives the device bytes of the block table.

@@ -250,6 +250,9 @@ __global__ void __launch_bounds__(NT, 3) triples_kernel(const Args a) {
     __shared__ int64_t s_item;
     __shared__ double s_red[NT / 32];
     __shared__ TermDev s_term[16];
+    __shared__ uint16_t s_dig[16][NT];    // per term and thread: rx | ry << 6 | case << 12
+    __shared__ TileAddr s_ta[16][2];      // per term of the current tile: X and Y at k0 = 0
+    __shared__ const void *s_ops[32];     // the current block's operand pointers
     const int t = threadIdx.x;
 #pragma unroll
     for (int i = 0; i < 16; ++i)
@@ -257,6 +260,27 @@ __global__ void __launch_bounds__(NT, 3) triples_kernel(const Args a) {
     int f[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) f[j] = (t >> (2 * j)) & 3;
+    __syncthreads();
+    // tile-row offsets of this thread's fixed labels in each term's X and Y, and where its owned
+    // labels sit (the same for every tile)
+    for (int p = 0; p < a.n_terms; ++p) {
+        const TermDev &tm = s_term[p];
+        int rx = 0, ry = 0;
+        bool u_on_x = false, v_on_x = false;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int qx = tm.x_q[m], qy = tm.y_q[m];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (qx == a.fixed[j]) rx += f[j] << (2 * tm.x_dig[m]);
+                if (qy == a.fixed[j]) ry += f[j] << (2 * tm.y_dig[m]);
+            }
+            u_on_x |= qx == a.own[0];
+            v_on_x |= qx == a.own[1];
+        }
+        const int kase = u_on_x ? (v_on_x ? 2 : 0) : (v_on_x ? 1 : 3);
+        s_dig[p][t] = (uint16_t)(rx | (ry << 6) | (kase << 12));
+    }
 
     int b = 0;                 // current block
     double e_acc = 0.0;
@@ -300,100 +324,98 @@ __global__ void __launch_bounds__(NT, 3) triples_kernel(const Args a) {
                 b = nb;
                 have = true;
                 if (t < a.n_labels) s_ext[t] = a.ext[(int64_t)b * a.n_labels + t];
+                if (t < 2 * a.n_terms) s_ops[t] = a.ops[(int64_t)b * a.n_terms * 2 + t];
                 __syncthreads();
             }
-            // tile coordinates (first T label fastest)
+            // tile coordinates (first T label fastest; fewer than 2^31 tiles per block)
             int tbase[6], text[6];
-            int64_t rem = item - a.prefix[b];
+            int rem = (int)(item - a.prefix[b]);
 #pragma unroll
             for (int q = 0; q < 6; ++q) {
                 text[q] = s_ext[a.t_col[q]];
                 const int nt = (text[q] + TS - 1) / TS;
-                tbase[q] = (int)(rem % nt) * TS;
-                rem /= nt;
+                const int qt = rem / nt;
+                tbase[q] = (rem - qt * nt) * TS;
+                rem = qt;
             }
+            __syncthreads();   // the previous item's steps are done with both buffers and s_ta
+            if (t < 2 * a.n_terms) {   // operand addressing of every term for this tile
+                const TermDev &tm = s_term[t >> 1];
+                s_ta[t >> 1][t & 1] = (t & 1) ? tile_addr(tm.y_q, tm.y_col, tm.y_dig, s_ext, tbase, text, 0)
+                                              : tile_addr(tm.x_q, tm.x_col, tm.x_dig, s_ext, tbase, text, 0);
+            }
+            __syncthreads();
             T acc[16];
 #pragma unroll
             for (int e = 0; e < 16; ++e) acc[e] = T(0);
             // steps: (term p, chunk k0) in order; step s+1's tiles are copied while step s runs
             int p = 0, k0 = 0, buf = 0;
-            auto issue = [&](int pp, int kk0, int bb) {
-                const TermDev &tm = s_term[pp];
-                const int K = s_ext[tm.d_col];
-                const int kn = min(kc, K - kk0);
-                const T *X = reinterpret_cast<const T *>(a.ops[((int64_t)b * a.n_terms + pp) * 2]);
-                const T *Y = reinterpret_cast<const T *>(a.ops[((int64_t)b * a.n_terms + pp) * 2 + 1]);
-                const TileAddr tx = tile_addr(tm.x_q, tm.x_col, tm.x_dig, s_ext, tbase, text, kk0);
-                stage_async<T>(Xs[bb], X, tx, kn);
-                stage_async<T>(Ys[bb], Y, tile_addr(tm.y_q, tm.y_col, tm.y_dig, s_ext, tbase, text, kk0), kn);
-                cp_async_commit();
-                return tx;
+            // addressing of term pp's operand (0: X, 1: Y) at summed-label chunk kk0
+            auto addr = [&](int pp, int side, int kk0) {
+                TileAddr ta = s_ta[pp][side];
+                ta.base += kk0 * ta.sd;
+                return ta;
             };
-            __syncthreads();   // the previous item's last step is done with both buffers
-            TileAddr tx_cur = issue(0, 0, 0);
+            auto issue = [&](int pp, int kk0, int bb) {
+                const int K = s_ext[s_term[pp].d_col];
+                const int kn = min(kc, K - kk0);
+                const T *X = reinterpret_cast<const T *>(s_ops[2 * pp]);
+                const T *Y = reinterpret_cast<const T *>(s_ops[2 * pp + 1]);
+                stage_async<T>(Xs[bb], X, addr(pp, 0, kk0), kn);
+                stage_async<T>(Ys[bb], Y, addr(pp, 1, kk0), kn);
+                cp_async_commit();
+            };
+            issue(0, 0, 0);
             while (p < a.n_terms) {
-                const TermDev &tm = s_term[p];
-                const int K = s_ext[tm.d_col];
+                const int K = s_ext[s_term[p].d_col];
+                const double alpha = s_term[p].alpha;
                 const int kn = min(kc, K - k0);
                 int pn = p, kn0 = k0 + kc;   // next step
                 if (kn0 >= K) { pn = p + 1; kn0 = 0; }
                 cp_async_wait_all();
-                if (tm.alpha != 1.0) scale_own<T>(Xs[buf], tx_cur, kn, (T)tm.alpha);
+                if (alpha != 1.0) scale_own<T>(Xs[buf], addr(p, 0, k0), kn, (T)alpha);
                 __syncthreads();   // step s is in buffer buf; step s-1's reads of buf^1 are done
-                TileAddr tx_next = tx_cur;
-                if (pn < a.n_terms) tx_next = issue(pn, kn0, buf ^ 1);
-                // tile-row offsets of this thread's fixed labels, and where its owned labels sit
-                int rx = 0, ry = 0;
-                bool u_on_x = false, v_on_x = false;
-#pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    const int qx = tm.x_q[m], qy = tm.y_q[m];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        if (qx == a.fixed[j]) rx += f[j] << (2 * tm.x_dig[m]);
-                        if (qy == a.fixed[j]) ry += f[j] << (2 * tm.y_dig[m]);
-                    }
-                    u_on_x |= qx == a.own[0];
-                    v_on_x |= qx == a.own[1];
-                }
-                const int kase = u_on_x ? (v_on_x ? 2 : 0) : (v_on_x ? 1 : 3);
-                step_compute<T>(Xs[buf], Ys[buf], kn, rx, ry, kase, acc);
+                if (pn < a.n_terms) issue(pn, kn0, buf ^ 1);
+                const int dg = s_dig[p][t];
+                step_compute<T>(Xs[buf], Ys[buf], kn, dg & 63, (dg >> 6) & 63, dg >> 12, acc);
                 p = pn;
                 k0 = kn0;
                 buf ^= 1;
-                tx_cur = tx_next;
             }
             int own_b[2], own_e[2], fix_c[4], fix_e[4];
 #pragma unroll
             for (int j = 0; j < 2; ++j) { own_b[j] = pick6(tbase, a.own[j]); own_e[j] = pick6(text, a.own[j]); }
 #pragma unroll
             for (int j = 0; j < 4; ++j) { fix_c[j] = pick6(tbase, a.fixed[j]) + f[j]; fix_e[j] = pick6(text, a.fixed[j]); }
-            // energy of the thread's elements: D = sum_q sign_q eps_q[coordinate q]
+            // energy of the thread's elements: D = sum_q sign_q eps_q[coordinate q], in the
+            // precision of T (FP32: one FP32 reciprocal per element, the tile's 16 terms summed in
+            // FP32 and added to the FP64 block sum once; FP64: all in FP64)
             bool fixed_ok = true;
-            double dfix = 0.0;
+            T dfix = T(0);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const bool in = fix_c[j] < fix_e[j];
                 fixed_ok &= in;
-                if (in) dfix += a.fixed_sign[j] *
-                                (double)reinterpret_cast<const T *>(a.eps[(int64_t)b * 6 + a.fixed[j]])[fix_c[j]];
+                if (in) dfix += (T)a.fixed_sign[j] * reinterpret_cast<const T *>(a.eps[(int64_t)b * 6 + a.fixed[j]])[fix_c[j]];
             }
             if (fixed_ok) {
                 const T *e0 = reinterpret_cast<const T *>(a.eps[(int64_t)b * 6 + a.own[0]]);
                 const T *e1 = reinterpret_cast<const T *>(a.eps[(int64_t)b * 6 + a.own[1]]);
+                T tile_e = T(0);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int c0 = own_b[0] + u;
                     if (c0 >= own_e[0]) continue;
-                    const double d0 = dfix + a.own_sign[0] * (double)e0[c0];
+                    const T d0 = dfix + (T)a.own_sign[0] * e0[c0];
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
                         const int c1 = own_b[1] + v;
                         if (c1 >= own_e[1]) continue;
-                        const double tv = (double)acc[u * 4 + v];
-                        e_acc += tv * tv / (d0 + a.own_sign[1] * (double)e1[c1]);
+                        const T tv = acc[u * 4 + v];
+                        tile_e += tv * tv / (d0 + (T)a.own_sign[1] * e1[c1]);
                     }
                 }
+                e_acc += (double)tile_e;
             }
         }
     }

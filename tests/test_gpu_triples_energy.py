@@ -2,10 +2,11 @@
 FP64 oracle (oracle.triples_energy: T as the sum of the nine permuted contraction terms,
 E = sum T^2 / D).
 
-Integer inputs make every product and partial sum of T exact in FP32 and FP64, so T is exact
-and E differs from the oracle's only by the order of its FP64 sum: relative 1e-12.  Uniform
-inputs: FP64 within 1e-12, FP32 within 2e-5 relative per block (FP32 sums of 9 K products per
-element; squared in E).
+Integer inputs make every product and partial sum of T exact in FP32 and FP64, so T is exact:
+E then differs from the oracle's by the order of the FP64 sum (FP64 plans, relative 1e-12) or
+by the FP32 rounding of each T^2 / D and of a tile's 16-term sum (FP32 plans, relative 1e-6).
+Uniform inputs: FP64 within 1e-12, FP32 within 2e-5 relative per block (FP32 sums of 9 K
+products per element; squared in E).
 """
 import numpy as np
 import pytest
@@ -74,7 +75,8 @@ SHAPES = [
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
 def test_integers_exact(comet, exts, dtype):
     got, ref, _ = run(comet, exts, dtype, 3, kind="int", lo=-3, hi=3)
-    assert np.all(np.abs(got - ref) <= 1e-12 * np.abs(ref) + 1e-300)
+    tol = 1e-12 if dtype == np.float64 else 1e-6
+    assert np.all(np.abs(got - ref) <= tol * np.abs(ref) + 1e-300)
 
 
 @pytest.mark.parametrize("exts", SHAPES + [rand_exts(8, 8, 2, 11, d_hi=36)])
