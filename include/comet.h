@@ -109,6 +109,8 @@ typedef struct {
                                    slices of the larger operand that are copied in, multiplied
                                    and copied back in a pipeline; 0 = planner's choice, 1 = off
                                    (copy all inputs, contract, copy back), s > 1 = s slices */
+    int host_slices_w;          /* the same pipeline (unless host_slices is 1): slices of the
+                                   smaller operand (0 = planner's choice, 1 = whole, s > 1 = s) */
 } comet_plan_opts_t;
 
 /* Fills *opts with the defaults: NATIVE precision, planned order, alpha 1, no cap, planner's

@@ -93,7 +93,7 @@ class Plan:
     def __init__(self, expr: str, extents: dict, dtype, precision="native", order="planned",
                  alpha: float = 1.0, workspace_cap: int = 0, form: int = -1, kc: int = 0,
                  timeout_ms: int = 0, debug_flags: int = 0, ksplit: int = 0, host_slices: int = 0,
-                 views=None):
+                 views=None, host_slices_w: int = 0):
         L = lib()
         self.expr = expr
         self.extents = {str(k): int(v) for k, v in extents.items()}
@@ -117,6 +117,7 @@ class Plan:
         opts.debug_flags = debug_flags
         opts.ksplit = ksplit
         opts.host_slices = host_slices
+        opts.host_slices_w = host_slices_w
         self.precision = opts.precision
         h = ctypes.c_void_p()
         if views:

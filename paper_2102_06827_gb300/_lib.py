@@ -54,7 +54,7 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("order", ctypes.c_int), ("alpha", ctypes.c_double),
                 ("workspace_cap", ctypes.c_size_t), ("form", ctypes.c_int), ("kc", ctypes.c_int64),
                 ("timeout_ms", ctypes.c_int64), ("debug_flags", ctypes.c_int),
-                ("ksplit", ctypes.c_int), ("host_slices", ctypes.c_int)]
+                ("ksplit", ctypes.c_int), ("host_slices", ctypes.c_int), ("host_slices_w", ctypes.c_int)]
 
 
 _lib = None

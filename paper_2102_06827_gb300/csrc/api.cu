@@ -297,12 +297,13 @@ static cudaError_t copy_slice(void *dst, size_t dpitch, const void *src, size_t 
     return cudaSuccess;
 }
 
-// comet_contract_host through the slice pipeline of a one-step split / emulated-FP64 plan: W is
-// copied whole, X in slices along its row group's last label into compact device slices; a
-// slice's scale, pre-pass and GEMM wait for its copy and run while the next slice is copied;
-// the result slice goes back on a third stream while the next GEMM runs.  The GEMM of a slice
-// is the step's GEMM with that group shortened to the slice's rows, writing the result through
-// the full result strides from the slice's first element on.
+// comet_contract_host through the slice pipeline of a one-step split / emulated-FP64 plan: X
+// (and possibly W) cross in slices along the last label of their GEMM row groups into compact
+// device slices, in the order W_0, X_0, W_1.., X_1..  Each slice gets its own scale word and
+// pre-pass as soon as its copy is in; GEMM block (i, j) multiplies W slice i by X slice j (the
+// step's GEMM with both row groups shortened, writing the result through the full result
+// strides from the block's first element), column by column; result slice j goes back on a
+// third stream after its last GEMM while the next ones run.
 static comet_status_t run_host_pipe(const Plan &P, const void *const *host_in, void *host_out,
                                     void *const *dev_in, void *dev_out, void *ws, cudaStream_t s) {
     const HostPipe &h = P.pipe;
@@ -319,110 +320,140 @@ static comet_status_t run_host_pipe(const Plan &P, const void *const *host_in, v
             if (cout) cudaStreamDestroy(cout);
         }
     } r;
-    const int n = h.n_chunks;
+    const int n = h.n_chunks, nw = h.w_n;
+    if (nw > 31) return COMET_ERR_INTERNAL;   // one scale word per W slice in the 256-byte region
     cudaError_t e = cudaStreamCreateWithFlags(&r.cin, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r.cout, cudaStreamNonBlocking);
-    r.ev.assign(3 + 2 * n, nullptr);
+    r.ev.assign(2 + 2 * n + nw, nullptr);
     for (auto &x : r.ev)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_status(e, "host pipeline streams");
-    cudaEvent_t e0 = r.ev[0], e_w = r.ev[1], e_end = r.ev[2];
-    cudaEvent_t *e_in = &r.ev[3], *e_g = &r.ev[3 + n];
+    cudaEvent_t e0 = r.ev[0], e_end = r.ev[1];
+    cudaEvent_t *e_in = &r.ev[2], *e_g = &r.ev[2 + n], *e_w = &r.ev[2 + 2 * n];
 
     double alpha = P.alpha, beta = 0.0;
     if (P.op == 1) beta = 1.0;
     if (P.op == 2) { alpha = -alpha; beta = 1.0; }
     const bool x_is_b = h.side == 1;
     char *w = static_cast<char *>(ws);
-    void *sc_a = w + st.ws_scales, *sc_b = w + st.ws_scales + 8;
-    void *sc_x = x_is_b ? sc_b : sc_a, *sc_w = x_is_b ? sc_a : sc_b;
+    char *sc_x = w + st.ws_scales;
+    auto sc_w = [&](int i) { return w + st.ws_scales + 8 * (1 + i); };
     char *parts_x = w + (x_is_b ? st.ws_parts_b : st.ws_parts_a);
-    char *parts_w = w + (x_is_b ? st.ws_parts_a : st.ws_parts_b);
+    char *parts_w0 = w + (x_is_b ? st.ws_parts_a : st.ws_parts_b);
     const bool emu = st.kernel == KK_GEMM_EMU;
+    const size_t n_planes = emu ? 6 : 3;
+    // W slice i's planes sit one after another (every slice but the last has w_chunk label values)
+    auto parts_w = [&](int i) {
+        return parts_w0 + (size_t)i * n_planes * (size_t)(h.w_rows_inner * h.w_chunk) * (size_t)st.kpad * 2;
+    };
     auto split = emu ? launch_split6 : launch_split;
     const char *hx = static_cast<const char *>(host_in[h.x_in]);
+    const char *hw = static_cast<const char *>(host_in[h.w_in]);
     char *dx = static_cast<char *>(dev_in[h.x_in]);
+    char *dw = static_cast<char *>(dev_in[h.w_in]);
     char *dc = static_cast<char *>(dev_out);
     char *hc = static_cast<char *>(host_out);
     const size_t x_unit = (size_t)h.x_inner * h.x_outer * es;      // compact bytes per unit of L
+    const size_t w_unit = (size_t)h.w_inner * h.w_outer * es;
     const size_t x_pitch = (size_t)h.x_inner * h.ext * es, c_pitch = (size_t)h.c_inner * h.ext * es;
+    const size_t w_pitch = (size_t)h.w_inner * h.w_ext * es;
+    auto lx_of = [&](int q) { return std::min(h.chunk, h.ext - (int64_t)q * h.chunk); };
+    auto lw_of = [&](int i) { return std::min(h.w_chunk, h.w_ext - (int64_t)i * h.w_chunk); };
 
-    // copies in: W whole, then the slices of X (and of the result for "+=" / "-=") in order
+    // copies in: W_0, X_0, W_1.., X_1.. (and the result slices for "+=" / "-=" with X's)
     e = cudaEventRecord(e0, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(r.cin, e0, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(r.cout, e0, 0);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(dev_in[h.w_in], host_in[h.w_in], (size_t)P.slots[h.w_in].elems * es,
-                            cudaMemcpyHostToDevice, r.cin);
-    if (e == cudaSuccess) e = cudaEventRecord(e_w, r.cin);
-    for (int q = 0; q < n && e == cudaSuccess; ++q) {
-        const int64_t l0 = (int64_t)q * h.chunk, lc = std::min(h.chunk, h.ext - l0);
+    auto copy_w = [&](int i) {
+        const int64_t l0 = (int64_t)i * h.w_chunk, lc = lw_of(i);
+        const size_t ww = (size_t)h.w_inner * lc * es;
+        cudaError_t ee = copy_slice(dw + l0 * w_unit, ww, hw + (size_t)l0 * h.w_inner * es, w_pitch, ww,
+                                    (size_t)h.w_outer, cudaMemcpyHostToDevice, r.cin);
+        if (ee == cudaSuccess) ee = cudaEventRecord(e_w[i], r.cin);
+        return ee;
+    };
+    auto copy_x = [&](int q) {
+        const int64_t l0 = (int64_t)q * h.chunk, lc = lx_of(q);
         const size_t xw = (size_t)h.x_inner * lc * es;
-        e = copy_slice(dx + l0 * x_unit, xw, hx + (size_t)l0 * h.x_inner * es, x_pitch, xw,
-                       (size_t)h.x_outer, cudaMemcpyHostToDevice, r.cin);
-        if (e == cudaSuccess && P.op != 0) {
+        cudaError_t ee = copy_slice(dx + l0 * x_unit, xw, hx + (size_t)l0 * h.x_inner * es, x_pitch, xw,
+                                    (size_t)h.x_outer, cudaMemcpyHostToDevice, r.cin);
+        if (ee == cudaSuccess && P.op != 0) {
             const size_t off = (size_t)l0 * h.c_inner * es;
-            e = copy_slice(dc + off, c_pitch, hc + off, c_pitch, (size_t)h.c_inner * lc * es,
-                           (size_t)h.c_outer, cudaMemcpyHostToDevice, r.cin);
+            ee = copy_slice(dc + off, c_pitch, hc + off, c_pitch, (size_t)h.c_inner * lc * es,
+                            (size_t)h.c_outer, cudaMemcpyHostToDevice, r.cin);
         }
-        if (e == cudaSuccess) e = cudaEventRecord(e_in[q], r.cin);
-    }
+        if (ee == cudaSuccess) ee = cudaEventRecord(e_in[q], r.cin);
+        return ee;
+    };
+    if (e == cudaSuccess) e = copy_w(0);
+    if (e == cudaSuccess) e = copy_x(0);
+    for (int i = 1; i < nw && e == cudaSuccess; ++i) e = copy_w(i);
+    for (int q = 1; q < n && e == cudaSuccess; ++q) e = copy_x(q);
     if (e != cudaSuccess) return cuda_status(e, "host pipeline copy in");
 
-    // W: scale and pre-pass once
-    e = cudaStreamWaitEvent(s, e_w, 0);
-    if (e == cudaSuccess) {
-        ProfScope ps(PK_PREPASS, s);
-        e = launch_absmax(dev_in[h.w_in], P.slots[h.w_in].elems, (int)es, sc_w, s);
-    }
-    if (e == cudaSuccess) {
-        XposeParams xw = x_is_b ? st.pre_a : st.pre_b;
-        xw.in = dev_in[h.w_in]; xw.out = parts_w; xw.scale_bits = sc_w;
-        ProfScope ps(PK_PREPASS, s);
-        e = split(xw, (int)es, x_is_b ? st.pre_a_vec : st.pre_b_vec, x_is_b ? st.pre_a_vout : st.pre_b_vout, s);
-    }
-    if (e != cudaSuccess) return cuda_status(e, "host pipeline pre-pass (whole operand)");
-
+    // scale and pre-pass of one slice, on the compute stream after its copy
+    auto prep = [&](cudaEvent_t ready, char *src, int64_t n_elems, void *scale, const XposeParams &tmpl,
+                    int vec, int vout, char *planes) {
+        cudaError_t ee = cudaStreamWaitEvent(s, ready, 0);
+        if (ee == cudaSuccess) {
+            ProfScope ps(PK_PREPASS, s);
+            ee = launch_absmax(src, n_elems, (int)es, scale, s);
+        }
+        if (ee == cudaSuccess) {
+            XposeParams xp = tmpl;
+            xp.in = src; xp.out = planes; xp.scale_bits = scale;
+            ProfScope ps(PK_PREPASS, s);
+            ee = split(xp, (int)es, vec, vout, s);
+        }
+        return ee;
+    };
     for (int q = 0; q < n; ++q) {
-        const int64_t l0 = (int64_t)q * h.chunk, lc = std::min(h.chunk, h.ext - l0);
+        const int64_t l0 = (int64_t)q * h.chunk, lc = lx_of(q);
         const int cls = lc == h.chunk ? 0 : 1;
         char *xs = dx + l0 * x_unit;
-        e = cudaStreamWaitEvent(s, e_in[q], 0);
-        if (e == cudaSuccess) {
-            ProfScope ps(PK_PREPASS, s);
-            e = launch_absmax(xs, h.x_inner * lc * h.x_outer, (int)es, sc_x, s);
+        e = prep(e_in[q], xs, h.x_inner * lc * h.x_outer, sc_x, h.pre[cls], h.pre_vec[cls], h.pre_vout[cls], parts_x);
+        if (e != cudaSuccess) return cuda_status(e, "host pipeline pre-pass (X slice)");
+        for (int i = 0; i < nw; ++i) {
+            const int64_t m0 = (int64_t)i * h.w_chunk, mc = lw_of(i);
+            char *wsl = dw + m0 * w_unit;
+            if (q == 0) {
+                const int wcls = mc == h.w_chunk ? 0 : 1;
+                e = prep(e_w[i], wsl, h.w_inner * mc * h.w_outer, sc_w(i), h.w_pre[wcls], h.w_pre_vec[wcls],
+                         h.w_pre_vout[wcls], parts_w(i));
+                if (e != cudaSuccess) return cuda_status(e, "host pipeline pre-pass (W slice)");
+            }
+            GemmParams g = st.gemm;
+            Radix &rx = x_is_b ? g.nb : g.ma;
+            Radix &rw = x_is_b ? g.ma : g.nb;
+            const uint32_t rows_x = (uint32_t)(h.rows_inner * lc), rows_w = (uint32_t)(h.w_rows_inner * mc);
+            rx.ext[rx.n - 1] = (uint32_t)lc;
+            rx.fd[rx.n - 1] = make_fastdiv((uint32_t)lc);
+            rx.total = rows_x;
+            rw.ext[rw.n - 1] = (uint32_t)mc;
+            rw.fd[rw.n - 1] = make_fastdiv((uint32_t)mc);
+            rw.total = rows_w;
+            if (x_is_b) { g.N = rows_x; g.M = rows_w; } else { g.M = rows_x; g.N = rows_w; }
+            g.A = x_is_b ? static_cast<void *>(wsl) : static_cast<void *>(xs);
+            g.B = x_is_b ? static_cast<void *>(xs) : static_cast<void *>(wsl);
+            g.C = dc + ((size_t)l0 * h.c_inner + (size_t)m0 * h.wc_inner) * es;
+            g.alpha = alpha;
+            g.beta = beta;
+            g.status = status;
+            g.timeout_ns = timeout_ns(P);
+            void *pa = x_is_b ? static_cast<void *>(parts_w(i)) : static_cast<void *>(parts_x);
+            void *pb = x_is_b ? static_cast<void *>(parts_x) : static_cast<void *>(parts_w(i));
+            void *sa = x_is_b ? static_cast<void *>(sc_w(i)) : static_cast<void *>(sc_x);
+            void *sb = x_is_b ? static_cast<void *>(sc_x) : static_cast<void *>(sc_w(i));
+            if (emu) {
+                ProfScope ps(PK_EMU, s);
+                e = launch_gemm_emu(g, pa, pb, st.kpad, sa, sb, P.opts.debug_flags, s, 0);
+            } else {
+                ProfScope ps(PK_SPLIT, s);
+                e = launch_gemm_split(g, pa, pb, st.kpad, sa, sb, P.opts.kc, (int)es, P.opts.debug_flags, s, 0,
+                                      st.ksplit, reinterpret_cast<float *>(w + st.ws_ksplit));
+            }
+            if (e != cudaSuccess) return cuda_status(e, "host pipeline gemm");
         }
-        if (e == cudaSuccess) {
-            XposeParams xp = h.pre[cls];
-            xp.in = xs; xp.out = parts_x; xp.scale_bits = sc_x;
-            ProfScope ps(PK_PREPASS, s);
-            e = split(xp, (int)es, h.pre_vec[cls], h.pre_vout[cls], s);
-        }
-        if (e != cudaSuccess) return cuda_status(e, "host pipeline pre-pass (slice)");
-        GemmParams g = st.gemm;
-        Radix &rg = x_is_b ? g.nb : g.ma;
-        const uint32_t rows = (uint32_t)(h.rows_inner * lc);
-        rg.ext[rg.n - 1] = (uint32_t)lc;
-        rg.fd[rg.n - 1] = make_fastdiv((uint32_t)lc);
-        rg.total = rows;
-        if (x_is_b) g.N = rows; else g.M = rows;
-        g.A = x_is_b ? dev_in[h.w_in] : xs;
-        g.B = x_is_b ? xs : dev_in[h.w_in];
-        g.C = dc + (size_t)l0 * h.c_inner * es;
-        g.alpha = alpha;
-        g.beta = beta;
-        g.status = status;
-        g.timeout_ns = timeout_ns(P);
-        void *pa = x_is_b ? parts_w : parts_x, *pb = x_is_b ? parts_x : parts_w;
-        if (emu) {
-            ProfScope ps(PK_EMU, s);
-            e = launch_gemm_emu(g, pa, pb, st.kpad, sc_a, sc_b, P.opts.debug_flags, s, 0);
-        } else {
-            ProfScope ps(PK_SPLIT, s);
-            e = launch_gemm_split(g, pa, pb, st.kpad, sc_a, sc_b, P.opts.kc, (int)es, P.opts.debug_flags, s, 0,
-                                  st.ksplit, reinterpret_cast<float *>(w + st.ws_ksplit));
-        }
-        if (e != cudaSuccess) return cuda_status(e, "host pipeline gemm");
         e = cudaEventRecord(e_g[q], s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(r.cout, e_g[q], 0);
         if (e == cudaSuccess) {

@@ -473,7 +473,7 @@ void prepass_params(const Step &st, const std::vector<int> &labels, std::map<int
 // slice's pre-pass and GEMM start when both its copy and the previous GEMM are done, and the
 // result slices go back in order.  A GEMM takes whole waves of output tiles over the SMs, so
 // slicing costs the partial last wave of every slice.
-void setup_host_pipe(Plan *P, int64_t es, int want) {
+void setup_host_pipe(Plan *P, int64_t es, int want, int want_w) {
     const Step &st = P->steps[0];
     const Slot &sa = P->slots[st.a], &sb = P->slots[st.b], &sc = P->slots[st.c];
     const Slot &sm = st.form.swap ? sb : sa, &sn = st.form.swap ? sa : sb;
@@ -481,70 +481,101 @@ void setup_host_pipe(Plan *P, int64_t es, int want) {
     h.side = sn.elems >= sm.elems ? 1 : 0;
     const Slot &sx = h.side ? sn : sm, &sw = h.side ? sm : sn;
     const std::vector<int> &rows = h.side ? st.form.N : st.form.M;
+    const std::vector<int> &wrows = h.side ? st.form.M : st.form.N;
     h.x_in = sx.index;
     h.w_in = sw.index;
     h.label = rows.back();
     h.ext = P->extent[h.label];
     if (h.ext < 2) return;
-    auto tx = label_strides(sx.labels, P->extent), tc = label_strides(sc.labels, P->extent);
+    auto tx = label_strides(sx.labels, P->extent), tc = label_strides(sc.labels, P->extent),
+         tw = label_strides(sw.labels, P->extent);
     h.x_inner = tx[h.label];
     h.x_outer = sx.elems / (h.x_inner * h.ext);
     h.c_inner = tc[h.label];
     h.c_outer = sc.elems / (h.c_inner * h.ext);
     h.rows_inner = prod_ext(P->extent, rows) / h.ext;
+    h.w_label = wrows.back();
+    h.w_ext = P->extent[h.w_label];
+    h.w_inner = tw[h.w_label];
+    h.w_outer = sw.elems / (h.w_inner * h.w_ext);
+    h.wc_inner = tc[h.w_label];
+    h.w_rows_inner = prod_ext(P->extent, wrows) / h.w_ext;
     const bool emu = st.kernel == KK_GEMM_EMU;
     const int64_t tm = 128, tn = emu ? 80 : 256;          // output tile of the GEMM kernel
-    const int64_t rows_w = prod_ext(P->extent, h.side ? st.form.M : st.form.N);
     const double prods = emu ? 21.0 / 0.6 : 6.0;             // bf16 products per tile (emu: drain-bound)
     const double t_tile = 2.0 * tm * tn * (double)st.kpad * prods / (kBf16FlopsPerS / 152);
     const double bw_in = 200e9, bw_out = 180e9, t_slice = 20e-6;
     const double planes = emu ? 12.0 : 6.0;
-    auto tiles_of = [&](int64_t lc) {
-        const int64_t r = h.rows_inner * lc;
-        return h.side ? ((rows_w + tm - 1) / tm) * ((r + tn - 1) / tn)
-                      : ((r + tm - 1) / tm) * ((rows_w + tn - 1) / tn);
+    auto tiles_of = [&](int64_t lx, int64_t lw) {
+        const int64_t r = h.rows_inner * lx, rw = h.w_rows_inner * lw;
+        return h.side ? ((rw + tm - 1) / tm) * ((r + tn - 1) / tn) : ((r + tm - 1) / tm) * ((rw + tn - 1) / tn);
     };
-    auto model = [&](int64_t n) {
-        const int64_t chunk = (h.ext + n - 1) / n, cnt = (h.ext + chunk - 1) / chunk;
-        double in = (double)sw.elems * es / bw_in, gemm = 0, out = 0;
-        in += (double)sw.elems * (es + planes) / kHbmBytesPerS;   // W's pre-pass runs before any GEMM
-        for (int64_t q = 0; q < cnt; ++q) {
-            const int64_t lc = std::min(chunk, h.ext - q * chunk);
-            const double xb = (double)h.x_inner * lc * h.x_outer * es, cb = (double)h.c_inner * lc * h.c_outer * es;
-            in += (xb + (P->op != 0 ? cb : 0)) / bw_in;
-            const double work = (double)((tiles_of(lc) + 151) / 152) * t_tile +
-                                xb / es * (es + planes) / kHbmBytesPerS + (cnt > 1 ? t_slice : 0);
-            gemm = std::max(gemm, in) + work;
-            out = std::max(out, gemm) + cb / bw_out;
+    // event model: copies in the order W_0, X_0, W_1.., X_1..; the compute stream runs, per X
+    // slice j, its pre-pass, then (for j = 0 after each W slice's pre-pass) the GEMMs of W
+    // slices 0.. against it; the result slice j goes back after its last GEMM
+    auto model = [&](int64_t nx, int64_t nw) {
+        const int64_t cx = (h.ext + nx - 1) / nx, cntx = (h.ext + cx - 1) / cx;
+        const int64_t cw = (h.w_ext + nw - 1) / nw, cntw = (h.w_ext + cw - 1) / cw;
+        auto lx_of = [&](int64_t j) { return std::min(cx, h.ext - j * cx); };
+        auto lw_of = [&](int64_t i) { return std::min(cw, h.w_ext - i * cw); };
+        std::vector<double> rx(cntx), rw(cntw);
+        double c = 0;
+        auto xbytes = [&](int64_t j) { return (double)h.x_inner * lx_of(j) * h.x_outer * es; };
+        auto cbytes = [&](int64_t j) { return (double)h.c_inner * lx_of(j) * h.c_outer * es; };
+        auto wbytes = [&](int64_t i) { return (double)h.w_inner * lw_of(i) * h.w_outer * es; };
+        c += wbytes(0) / bw_in; rw[0] = c;
+        c += (xbytes(0) + (P->op != 0 ? cbytes(0) : 0)) / bw_in; rx[0] = c;
+        for (int64_t i = 1; i < cntw; ++i) { c += wbytes(i) / bw_in; rw[i] = c; }
+        for (int64_t j = 1; j < cntx; ++j) { c += (xbytes(j) + (P->op != 0 ? cbytes(j) : 0)) / bw_in; rx[j] = c; }
+        const bool sliced = cntx > 1 || cntw > 1;
+        double t = 0, out = 0;
+        for (int64_t j = 0; j < cntx; ++j) {
+            t = std::max(t, rx[j]) + xbytes(j) / es * (es + planes) / kHbmBytesPerS;
+            for (int64_t i = 0; i < cntw; ++i) {
+                if (j == 0) t = std::max(t, rw[i]) + wbytes(i) / es * (es + planes) / kHbmBytesPerS;
+                t += (double)((tiles_of(lx_of(j), lw_of(i)) + 151) / 152) * t_tile + (sliced ? t_slice : 0);
+            }
+            out = std::max(out, t) + cbytes(j) / bw_out;
         }
         return out;
     };
-    auto aligned = [&](int64_t chunk) {   // every slice of X starts on a 16-byte boundary
-        return ((int64_t)chunk * h.x_inner * h.x_outer * es) % 16 == 0;
+    auto aligned = [&](int64_t chunk, int64_t unit) {   // every slice starts on a 16-byte boundary
+        return ((int64_t)chunk * unit * es) % 16 == 0;
     };
-    int64_t best = 1;
-    double best_t = model(1);
+    const int64_t xu = h.x_inner * h.x_outer, wu = h.w_inner * h.w_outer;
+    int64_t best = 1, best_w = 1;
+    double best_t = model(1, 1);
     h.model_s[0] = best_t;
-    if (want > 1) {
-        const int64_t n = std::min<int64_t>(want, h.ext);
-        if (aligned((h.ext + n - 1) / n)) { best = n; best_t = model(n); }
-    } else {
-        for (int64_t n : {2, 3, 4, 6, 8, 12, 16}) {
-            if (n > h.ext || !aligned((h.ext + n - 1) / n)) continue;
-            const double t = model(n);
-            if (t < best_t * 0.97) { best = n; best_t = t; }
+    std::vector<int64_t> cand_x, cand_w;
+    if (want > 1) cand_x.push_back(std::min<int64_t>(want, h.ext));
+    else cand_x = {1, 2, 3, 4, 6, 8, 12, 16};
+    if (want_w > 1) cand_w.push_back(std::min<int64_t>(want_w, h.w_ext));
+    else if (want_w == 0) cand_w = {1, 2, 3, 4, 6, 8};
+    else cand_w = {1};
+    const bool forced = want > 1 || want_w > 1;
+    for (int64_t nx : cand_x)
+        for (int64_t nw : cand_w) {
+            if (nx > h.ext || nw > h.w_ext || (nx == 1 && nw == 1)) continue;
+            if (!aligned((h.ext + nx - 1) / nx, xu) || !aligned((h.w_ext + nw - 1) / nw, wu)) continue;
+            const double t = model(nx, nw);
+            if (forced ? (best == 1 && best_w == 1) || t < best_t : t < best_t * 0.97) { best = nx; best_w = nw; best_t = t; }
         }
-    }
-    if (best == 1) return;
+    if (best == 1 && best_w == 1) return;
     h.chunk = (h.ext + best - 1) / best;
     h.n_chunks = (int)((h.ext + h.chunk - 1) / h.chunk);
+    h.w_chunk = (h.w_ext + best_w - 1) / best_w;
+    h.w_n = (int)((h.w_ext + h.w_chunk - 1) / h.w_chunk);
     h.model_s[1] = best_t;
-    const int64_t tail = h.ext - (h.n_chunks - 1) * h.chunk;
+    const int64_t tail = h.ext - (h.n_chunks - 1) * h.chunk, w_tail = h.w_ext - (h.w_n - 1) * h.w_chunk;
     for (int c = 0; c < 2; ++c) {
         std::vector<int64_t> e = P->extent;
         e[h.label] = c == 0 ? h.chunk : tail;
         prepass_params(st, sx.labels, label_strides(sx.labels, e), 0, rows, e, es, &h.pre[c], &h.pre_vec[c],
                        &h.pre_vout[c]);
+        std::vector<int64_t> ew = P->extent;
+        ew[h.w_label] = c == 0 ? h.w_chunk : w_tail;
+        prepass_params(st, sw.labels, label_strides(sw.labels, ew), 0, wrows, ew, es, &h.w_pre[c],
+                       &h.w_pre_vec[c], &h.w_pre_vout[c]);
     }
     h.ok = true;
     P->pipe = h;
@@ -1068,7 +1099,7 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
             P->slots[st.b].kind == SLOT_INPUT && P->slots[st.c].kind == SLOT_OUTPUT &&
             !st.form.M.empty() && !st.form.N.empty() && !P->slots[st.a].view &&
             !P->slots[st.b].view && !P->slots[st.c].view)
-            setup_host_pipe(P, es, opts.host_slices);
+            setup_host_pipe(P, es, opts.host_slices, opts.host_slices_w);
     }
     P->flops = 0;
     for (auto &st : P->steps) P->flops += st.flops;
@@ -1151,7 +1182,8 @@ std::string describe_plan(const Plan &P) {
     if (P.pipe.ok)
         o << ",\"host_pipe\":{\"slices\":" << P.pipe.n_chunks << ",\"label\":\""
           << P.label_names[P.pipe.label] << "\",\"chunk\":" << P.pipe.chunk << ",\"side\":\""
-          << (P.pipe.side ? "N" : "M") << "\",\"model_s\":[" << P.pipe.model_s[0] << ","
+          << (P.pipe.side ? "N" : "M") << "\",\"w_slices\":" << P.pipe.w_n << ",\"w_label\":\""
+          << P.label_names[P.pipe.w_label] << "\",\"w_chunk\":" << P.pipe.w_chunk << ",\"model_s\":[" << P.pipe.model_s[0] << ","
           << P.pipe.model_s[1] << "]}";
     o << "}";
     return o.str();
@@ -1198,4 +1230,5 @@ extern "C" void comet_plan_opts_default(comet_plan_opts_t *o) {
     o->debug_flags = 0;
     o->ksplit = 0;
     o->host_slices = 0;
+    o->host_slices_w = 0;
 }

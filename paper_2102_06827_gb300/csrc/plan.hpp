@@ -107,6 +107,15 @@ struct HostPipe {
     int64_t rows_inner = 1;      // GEMM rows of X's group per unit of L
     XposeParams pre[2];          // pre-pass of a compact slice: full slice, short last slice
     int pre_vec[2] = {1, 1}, pre_vout[2] = {1, 1};
+    // W may be sliced too, along the last label of its own row group, so that the first GEMMs
+    // start before all of W has crossed: GEMM block (i, j) = W slice i x X slice j, each W slice
+    // with its own scale and planes; order: W_0, X_0, W_1.., then X_1.. (GEMMs column by column)
+    int w_label = -1;
+    int64_t w_ext = 1, w_chunk = 1;
+    int w_n = 1;
+    int64_t w_inner = 1, w_outer = 1, wc_inner = 1, w_rows_inner = 1;
+    XposeParams w_pre[2];
+    int w_pre_vec[2] = {1, 1}, w_pre_vout[2] = {1, 1};
     double model_s[2] = {0, 0};  // modelled seconds: unpipelined, pipelined
 };
 

@@ -52,19 +52,24 @@ def inputs(expr, ext, seed, kind="uniform", **kw):
 CCSD = "C[i,a,j,b] = A[k,a,c,i] * B[c,b,k,j]"
 
 
-@pytest.mark.parametrize("slices,ext", [
-    (4, dict(i=16, j=16, k=16, a=48, b=48, c=48)),     # equal slices
-    (4, dict(i=16, j=18, k=16, a=48, b=40, c=48)),     # A larger: slices of a (M group)
-    (4, dict(i=16, j=18, k=16, a=40, b=48, c=48)),     # chunk 5, short last slice of 3
-    (16, dict(i=8, j=16, k=8, a=40, b=24, c=40)),      # one unit of the label per slice
+@pytest.mark.parametrize("slices,w_slices,ext", [
+    (4, 1, dict(i=16, j=16, k=16, a=48, b=48, c=48)),     # equal slices
+    (4, 1, dict(i=16, j=18, k=16, a=48, b=40, c=48)),     # A larger: slices of a (M group)
+    (4, 1, dict(i=16, j=18, k=16, a=40, b=48, c=48)),     # chunk 5, short last slice of 3
+    (16, 1, dict(i=8, j=16, k=8, a=40, b=24, c=40)),      # one unit of the label per slice
+    (4, 4, dict(i=16, j=16, k=16, a=48, b=48, c=48)),     # both operands in slices
+    (3, 5, dict(i=16, j=14, k=16, a=46, b=44, c=48)),     # both ragged
 ])
-def test_pipeline_split(comet, slices, ext):
+def test_pipeline_split(comet, slices, w_slices, ext):
     A, B = inputs(CCSD, ext, 3)
-    C, p, dout = run_host(comet, CCSD, ext, [A, B], np.float32, "split_bf16", host_slices=slices)
+    C, p, dout = run_host(comet, CCSD, ext, [A, B], np.float32, "split_bf16", host_slices=slices,
+                          host_slices_w=w_slices)
     hp = p.info.get("host_pipe")
     step = p.info["steps"][0]
-    assert hp is not None and hp["slices"] > 1
+    assert hp is not None and hp["slices"] * hp["w_slices"] > 1
+    assert hp["w_slices"] == min(w_slices, ext[hp["w_label"]]) or w_slices == 1
     assert hp["label"] == (step["N"] if hp["side"] == "N" else step["M"])[-1]
+    assert hp["w_label"] == (step["M"] if hp["side"] == "N" else step["N"])[-1]
     assert normwise(C, oracle.einsum(CCSD, A, B)) <= 1e-6
     # the device output holds the result as well
     import torch
@@ -85,9 +90,10 @@ def test_pipeline_sliced_m_operand(comet):
     e = "C[m,n] = A[m,k] * B[k,n]"
     ext = dict(m=600, n=136, k=72)
     A, B = inputs(e, ext, 5)
-    C, p, _ = run_host(comet, e, ext, [A, B], np.float32, "split_bf16", host_slices=3)
+    C, p, _ = run_host(comet, e, ext, [A, B], np.float32, "split_bf16", host_slices=3, host_slices_w=2)
     hp = p.info["host_pipe"]
     assert hp["side"] == "M" and hp["label"] == "m" and hp["slices"] == 3
+    assert hp["w_label"] == "n" and hp["w_slices"] == 2
     assert normwise(C, oracle.einsum(e, A, B)) <= 1e-6
 
 
@@ -96,8 +102,9 @@ def test_pipeline_accumulate_alpha(comet):
     ext = dict(i=300, j=520, k=96)
     A, B = inputs(e, ext, 6)
     C0 = synth.tensor((300, 520), 6, 9).astype(np.float32).astype(np.float64)
-    C, p, _ = run_host(comet, e, ext, [A, B], np.float32, "split_bf16", out_init=C0, host_slices=4)
-    assert p.info["host_pipe"]["slices"] == 4
+    C, p, _ = run_host(comet, e, ext, [A, B], np.float32, "split_bf16", out_init=C0, host_slices=4,
+                       host_slices_w=3)
+    assert p.info["host_pipe"]["slices"] == 4 and p.info["host_pipe"]["w_slices"] == 3
     ref = oracle.einsum(e, A, B, out=np.asfortranarray(C0.copy()))
     assert normwise(C, ref) <= 2e-6
 
@@ -105,8 +112,8 @@ def test_pipeline_accumulate_alpha(comet):
 def test_pipeline_emulated_f64(comet):
     ext = dict(i=8, j=20, k=8, a=40, b=24, c=40)
     A, B = inputs(CCSD, ext, 7)
-    C, p, _ = run_host(comet, CCSD, ext, [A, B], np.float64, "emu_f64", host_slices=3)
-    assert p.info["host_pipe"]["slices"] == 3
+    C, p, _ = run_host(comet, CCSD, ext, [A, B], np.float64, "emu_f64", host_slices=3, host_slices_w=2)
+    assert p.info["host_pipe"]["slices"] == 3 and p.info["host_pipe"]["w_slices"] == 2
     assert normwise(C, oracle.einsum(CCSD, A, B)) <= 1e-12
 
 
