@@ -286,8 +286,8 @@ comet_status_t comet_contract_noalloc(comet_plan_t plan, const void *const *inpu
  * comet_contract_host — the same evaluation from host buffers: copies every input from host
  * to the caller's device buffers, runs the plan and copies the output back, then synchronises
  * `stream`.  host_* may be pageable or pinned host memory; dev_* are caller-owned device
- * buffers of the operands' sizes (16-byte aligned).  For "+=" / "-=" the host output is copied
- * to the device as well.  Returns the first error, including a device status word set by a
+ * buffers of the operands' sizes (16-byte aligned; for views, the stored tensors' sizes).  For
+ * "+=" / "-=" and for an output view the host output is copied to the device as well.  Returns the first error, including a device status word set by a
  * kernel (as comet_sync_status()).
  *
  * Pipeline: for a one-step split or emulated-FP64 plan whose description lists "host_pipe"

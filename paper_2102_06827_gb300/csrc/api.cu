@@ -650,8 +650,10 @@ comet_status_t comet_contract_host(comet_plan_t plan, const void *const *host_in
         if (st != COMET_OK) return st;
     }
     size_t out_bytes = 0;
-    for (auto &sl : P.slots) if (sl.kind == SLOT_OUTPUT) out_bytes = (size_t)sl.storage * es;
-    if (P.op != 0) {
+    bool out_view = false;
+    for (auto &sl : P.slots)
+        if (sl.kind == SLOT_OUTPUT) { out_bytes = (size_t)sl.storage * es; out_view = sl.view; }
+    if (P.op != 0 || out_view) {   // read as well, or only partly written (a view)
         comet_status_t st = cuda_status(cudaMemcpyAsync(dev_output, host_output, out_bytes,
                                                         cudaMemcpyHostToDevice, s), "output copy in");
         if (st != COMET_OK) return st;

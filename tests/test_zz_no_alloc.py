@@ -84,3 +84,21 @@ def test_noalloc_refuses_plans_above_the_limit(comet):
     a = torch.zeros(16, device="cuda")
     status = _noalloc(comet, plan, [a, a], a)
     assert comet._lib.STATUS[status] == "COMET_ERR_WORKSPACE"
+
+
+def test_noalloc_on_views(comet):
+    # a plan on views (strided slices of stored tensors) through the scratch-free entry point
+    import torch
+    e = "C[i,j] = A[i,k] * B[k,j]"
+    ext = dict(i=70, j=90, k=50)
+    views = [(0, 0, 160, 3, 2), (2, 1, 200, 5, 2)]
+    A = synth.tensor((160, 50), 24, 0).astype(np.float32)
+    B = synth.tensor((50, 90), 24, 1).astype(np.float32)
+    C0 = synth.tensor((70, 200), 24, 2).astype(np.float32)
+    p = comet.Plan(e, ext, torch.float32, precision="split_bf16", views=views)
+    ins = [to_dev(A, np.float32), to_dev(B, np.float32)]
+    out_ref, out = to_dev(C0, np.float32), to_dev(C0, np.float32)
+    p.contract(ins, out_ref, p.workspace())
+    assert _noalloc(comet, p, ins, out) == 0
+    comet.sync_status()
+    assert torch.equal(out, out_ref)
