@@ -39,7 +39,7 @@ def block_inputs(ext, seed, block, kind="uniform", **kw):
     for p, e in enumerate(terms()):
         ops.append(tuple(synth.tensor(tuple(ext[l] for l in ls), seed, 1000 * block + 2 * p + q, kind=kind, **kw)
                          for q, ls in enumerate(operand_labels(e))))
-    # virtual energies in [1, 2), occupied in [-2, -1): every denominator is below -3
+    # virtual energies in [1, 2), occupied in [-2, -1): every denominator is below -6
     eps = [synth.tensor((ext[l],), seed, 1000 * block + 100 + q) * 0.5 + (1.5 if l in "abc" else -1.5)
            for q, l in enumerate(T_LABELS)]
     return ops, eps
