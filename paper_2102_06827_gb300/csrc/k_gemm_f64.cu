@@ -7,9 +7,9 @@
 // Arithmetic: FP64 tensor-core MMA (mma.sync.m8n8k4 f64) with FP64 accumulation; FP32-stored
 // operands are widened exactly on load and the result is rounded once on store.
 //
-// Blocking: 64 x 64 output tile per CTA, K in blocks of 16, four warps of 32 x 32; the next
-// K block is loaded into registers while the current one is multiplied (double-buffered
-// shared memory).
+// Blocking: TM x TM output tile per CTA (TM = 64; 32 when 64-wide tiles would leave SMs idle),
+// K in blocks of 16, four warps of TM/2 x TM/2; the next K block is loaded into registers while
+// the current one is multiplied (double-buffered shared memory).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -18,7 +18,7 @@
 
 namespace comet {
 
-constexpr int FBM = 64, FBN = 64, FBK = 16, FPAD = 4;
+constexpr int FBK = 16, FPAD = 4;
 constexpr int FTHREADS = 128;
 
 __device__ __forceinline__ void dmma(double (&d)[2], double a, double b) {
@@ -29,38 +29,39 @@ __device__ __forceinline__ void dmma(double (&d)[2], double a, double b) {
 
 // A tile: FBM rows (m) x FBK cols (k); element (m,k) at a_row[m] + a_k[k].  The thread map
 // follows the contiguous direction of the operand in memory.
-template <typename TIn, bool KCONTIG>
+template <typename TIn, bool KCONTIG, int TM>
 __device__ __forceinline__ void load_tile(const TIn *__restrict__ base, const int64_t *rowoff,
                                           const int64_t *koff, uint32_t row0, uint32_t rows,
-                                          uint32_t k0, uint32_t K, double (&r)[8]) {
+                                          uint32_t k0, uint32_t K, double (&r)[TM * FBK / FTHREADS]) {
     const int t = threadIdx.x;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < TM * FBK / FTHREADS; ++i) {
         int idx = t + i * FTHREADS;
         int m, k;
         if (KCONTIG) { k = idx % FBK; m = idx / FBK; }
-        else { m = idx % FBM; k = idx / FBM; }
+        else { m = idx % TM; k = idx / TM; }
         double v = 0.0;
         if (row0 + m < rows && k0 + k < K) v = (double)base[rowoff[m] + koff[k]];
         r[i] = v;
     }
 }
 
-template <bool KCONTIG>
-__device__ __forceinline__ void store_tile(double (*s)[FBM + FPAD], const double (&r)[8]) {
+template <bool KCONTIG, int TM>
+__device__ __forceinline__ void store_tile(double (*s)[TM + FPAD], const double (&r)[TM * FBK / FTHREADS]) {
     const int t = threadIdx.x;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < TM * FBK / FTHREADS; ++i) {
         int idx = t + i * FTHREADS;
         int m, k;
         if (KCONTIG) { k = idx % FBK; m = idx / FBK; }
-        else { m = idx % FBM; k = idx / FBM; }
+        else { m = idx % TM; k = idx / TM; }
         s[k][m] = r[i];
     }
 }
 
-template <typename TIn, bool AK, bool BK>
+template <typename TIn, bool AK, bool BK, int TM>
 __global__ void __launch_bounds__(FTHREADS) gemm_f64_kernel(const GemmParams p) {
+    constexpr int FBM = TM, FBN = TM, FI = TM / 16, NL = TM * FBK / FTHREADS;
     __shared__ double As[2][FBK][FBM + FPAD];
     __shared__ double Bs[2][FBK][FBN + FPAD];
     __shared__ int64_t a_row[FBM], b_col[FBN], c_row[FBM], c_col[FBN];
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(FTHREADS) gemm_f64_kernel(const GemmParams p) 
         int64_t o0 = 0, o1 = 0;
         if (m0 + t < p.M) radix_offsets(p.ma, m0 + t, o0, o1);
         a_row[t] = o0; c_row[t] = o1;
-    } else {
+    } else if (t < FBM + FBN) {
         int j = t - FBM;
         int64_t o0 = 0, o1 = 0;
         if (n0 + j < p.N) radix_offsets(p.nb, n0 + j, o0, o1);
@@ -91,17 +92,17 @@ __global__ void __launch_bounds__(FTHREADS) gemm_f64_kernel(const GemmParams p) 
     k_offsets(0, 0);
     __syncthreads();
 
-    double acc[4][4][2];
+    double acc[FI][FI][2];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < FI; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
+        for (int j = 0; j < FI; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
 
-    double ra[8], rb[8];
-    load_tile<TIn, AK>(A, a_row, a_k[0], m0, p.M, 0, p.K, ra);
-    load_tile<TIn, BK>(B, b_col, b_k[0], n0, p.N, 0, p.K, rb);
-    store_tile<AK>(As[0], ra);
-    store_tile<BK>(Bs[0], rb);
+    double ra[NL], rb[NL];
+    load_tile<TIn, AK, TM>(A, a_row, a_k[0], m0, p.M, 0, p.K, ra);
+    load_tile<TIn, BK, TM>(B, b_col, b_k[0], n0, p.N, 0, p.K, rb);
+    store_tile<AK, TM>(As[0], ra);
+    store_tile<BK, TM>(Bs[0], rb);
     const uint32_t nkb = (p.K + FBK - 1) / FBK;
     if (nkb > 1) k_offsets(1, FBK);
     __syncthreads();
@@ -110,25 +111,25 @@ __global__ void __launch_bounds__(FTHREADS) gemm_f64_kernel(const GemmParams p) 
         const int cur = kb & 1, nxt = cur ^ 1;
         const bool more = kb + 1 < nkb;
         if (more) {
-            load_tile<TIn, AK>(A, a_row, a_k[nxt], m0, p.M, (kb + 1) * FBK, p.K, ra);
-            load_tile<TIn, BK>(B, b_col, b_k[nxt], n0, p.N, (kb + 1) * FBK, p.K, rb);
+            load_tile<TIn, AK, TM>(A, a_row, a_k[nxt], m0, p.M, (kb + 1) * FBK, p.K, ra);
+            load_tile<TIn, BK, TM>(B, b_col, b_k[nxt], n0, p.N, (kb + 1) * FBK, p.K, rb);
         }
 #pragma unroll
         for (int k4 = 0; k4 < FBK / 4; ++k4) {
             const int kk = k4 * 4 + (lane & 3);
-            double af[4], bf[4];
+            double af[FI], bf[FI];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) af[i] = As[cur][kk][wm * 32 + i * 8 + (lane >> 2)];
+            for (int i = 0; i < FI; ++i) af[i] = As[cur][kk][wm * (TM / 2) + i * 8 + (lane >> 2)];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) bf[j] = Bs[cur][kk][wn * 32 + j * 8 + (lane >> 2)];
+            for (int j = 0; j < FI; ++j) bf[j] = Bs[cur][kk][wn * (TM / 2) + j * 8 + (lane >> 2)];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < FI; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) dmma(acc[i][j], af[i], bf[j]);
+                for (int j = 0; j < FI; ++j) dmma(acc[i][j], af[i], bf[j]);
         }
         if (more) {
-            store_tile<AK>(As[nxt], ra);
-            store_tile<BK>(Bs[nxt], rb);
+            store_tile<AK, TM>(As[nxt], ra);
+            store_tile<BK, TM>(Bs[nxt], rb);
         }
         __syncthreads();
         if (kb + 2 < nkb) k_offsets(cur, (kb + 2) * FBK);
@@ -139,14 +140,14 @@ __global__ void __launch_bounds__(FTHREADS) gemm_f64_kernel(const GemmParams p) 
     // epilogue: C[m,n] = alpha * acc (+ beta * C), stored through the C strides of M and N
     TIn *C = reinterpret_cast<TIn *>(p.C);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int ml = wm * 32 + i * 8 + (lane >> 2);
+    for (int i = 0; i < FI; ++i) {
+        const int ml = wm * (TM / 2) + i * 8 + (lane >> 2);
         if (m0 + ml >= p.M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < FI; ++j) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int nl = wn * 32 + j * 8 + (lane & 3) * 2 + h;
+                const int nl = wn * (TM / 2) + j * 8 + (lane & 3) * 2 + h;
                 if (n0 + nl >= p.N) continue;
                 TIn *dst = C + c_row[ml] + c_col[nl];
                 double v = p.alpha * acc[i][j][h];
@@ -160,9 +161,21 @@ __global__ void __launch_bounds__(FTHREADS) gemm_f64_kernel(const GemmParams p) 
 cudaError_t launch_gemm_f64(const GemmParams &p, int elem_bytes, bool a_kcontig, bool b_kcontig,
                             cudaStream_t s) {
     if (p.M == 0 || p.N == 0) return cudaSuccess;
-    dim3 grid((p.M + FBM - 1) / FBM, (p.N + FBN - 1) / FBN);
+    static int sms = [] {
+        int dev = 0, n = 152;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        return n;
+    }();
+    // 64-wide tiles unless they would leave SMs idle
+    const uint64_t tiles64 = (uint64_t)((p.M + 63) / 64) * ((p.N + 63) / 64);
+    const int tm = tiles64 < (uint64_t)sms ? 32 : 64;
+    dim3 grid((p.M + tm - 1) / tm, (p.N + tm - 1) / tm);
     if (grid.y > 65535) return cudaErrorInvalidConfiguration;
-#define CM_LAUNCH(T, a, b) gemm_f64_kernel<T, a, b><<<grid, FTHREADS, 0, s>>>(p)
+#define CM_LAUNCH(T, a, b)                                                               \
+    do {                                                                                 \
+        if (tm == 32) gemm_f64_kernel<T, a, b, 32><<<grid, FTHREADS, 0, s>>>(p);         \
+        else gemm_f64_kernel<T, a, b, 64><<<grid, FTHREADS, 0, s>>>(p);                  \
+    } while (0)
     if (elem_bytes == 8) {
         if (a_kcontig && b_kcontig) CM_LAUNCH(double, true, true);
         else if (a_kcontig) CM_LAUNCH(double, true, false);
