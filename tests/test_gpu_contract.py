@@ -191,6 +191,19 @@ def test_ccsd_like_full_size_sampled(comet):
         assert normwise(got, ref) <= tol, prec
 
 
+def test_ccsd_like_full_size_integers_exact(comet):
+    # the same workload on integers in [-2, 2]: every sum stays below 2^24, so the split path's
+    # exact hh chunks and fixed-point parts give the exact result at full size (sampled)
+    e = "C[i,a,j,b] = A[k,a,c,i] * B[c,b,k,j]"
+    ext = dict(i=64, j=64, k=64, a=192, b=192, c=192)
+    A = synth.tensor((64, 192, 192, 64), 13, 0, kind="int", lo=-2, hi=2, dtype=np.float32)
+    B = synth.tensor((192, 192, 64, 64), 13, 1, kind="int", lo=-2, hi=2, dtype=np.float32)
+    sel = np.unique(synth.integers(14, 0, 20000, 0, 64 * 192 * 64 * 192 - 1).astype(np.int64))
+    ref = oracle.einsum_sampled(e, A, B, sel=sel)
+    C, _ = run(comet, e, ext, [A, B], np.float32, precision="split_bf16")
+    assert np.array_equal(np.ravel(C, order="F")[sel], ref)
+
+
 def test_timeout_surfaces_and_context_survives(comet):
     # fault injection on the host side of the protocol: one operand load is withheld, the
     # kernel's bounded wait runs out, the status word reports it, and the GPU stays usable
