@@ -212,7 +212,8 @@ def run_triples_energy(a) -> int:
     sign * X_p[d,..] * Y_p[..,d,..] and E_b = sum T^2 / D_b, with D the signed sum of per-label
     eps vectors; extents uniform 8..32 (the batched triples table, seed 3), operands uniform
     [-1,1) (seed 11), eps uniform in [1,2) (virtual) and [-2,-1) (occupied).  One launch per step;
-    T never goes to memory.  Parity on the three smallest blocks against the CPU oracle.  Prints
+    T never goes to memory.  CPU baseline leg: the oracle on the three smallest blocks (timed, and
+    the error of the GPU energies against it).  Prints
     one JSON line (not the headline line)."""
     import numpy as np
     import torch
@@ -252,14 +253,16 @@ def run_triples_energy(a) -> int:
         eps = torch.tensor(eoffs, dtype=torch.int64, device=dev) + ebuf.data_ptr()
         return ext, buf, ops, ebuf, eps, sizes, eps_sizes
 
-    def parity(ext, buf, ebuf, sizes, eps_sizes, energies, dtype, n_check=3):
+    def cpu_baseline(ext, buf, ebuf, sizes, eps_sizes, energies, dtype, n_check=3):
+        """the CPU baseline leg: the oracle on the three smallest blocks, timed on the host cores,
+        and the relative error of the GPU energies of those blocks against it"""
         import oracle
         hb = buf  # host copies of the checked blocks only
         per_block = len(tl) * 2
         starts = np.concatenate([[0], np.cumsum(sizes)])
         estarts = np.concatenate([[0], np.cumsum(eps_sizes)])
         sel = np.argsort(np.prod(ext[:, :6], axis=1))[:n_check]
-        worst = 0.0
+        worst, t_cpu, flops = 0.0, 0.0, 0.0
         for b in sel:
             ops = []
             for p, e in enumerate(tl):
@@ -271,9 +274,14 @@ def run_triples_energy(a) -> int:
                 ops.append(tuple(pair))
             eps = [ebuf[int(estarts[b * 6 + q]):int(estarts[b * 6 + q + 1])].double().cpu().numpy()
                    for q in range(6)]
+            t0 = time.perf_counter()
             ref = oracle.triples_energy(tl, ops, eps, SIGNS)[0]
+            t_cpu += time.perf_counter() - t0
+            flops += len(tl) * 2.0 * float(np.prod(ext[b, :7]))
             worst = max(worst, abs(float(energies[b]) - ref) / abs(ref))
-        return {"blocks": [int(x) for x in sel], "max_rel_err": worst}
+        return {"value": flops / t_cpu / 1e9, "unit": "GFLOP/s", "cores": oracle.threads(), "kind": "oracle",
+                "sample": f"blocks {[int(x) for x in sel]} (the smallest), whole energies",
+                "max_rel_err": worst}
 
     for name, dtype, n_blocks, steps in (("f32", torch.float32, a.te_blocks, max(1, min(a.steps, 3))),
                                          ("f64", torch.float64, a.te_f64_blocks, 1)):
@@ -309,7 +317,7 @@ def run_triples_energy(a) -> int:
                                                   else "nominal FP64 rate")},
                      "tiles": plan.info["tiles"], "flops": plan.flops, "clocks": ck,
                      "energy_sum": float(energies.sum()),
-                     "parity": parity(ext, buf, ebuf, sizes, eps_sizes, energies, dtype)}
+                     "cpu_baseline": cpu_baseline(ext, buf, ebuf, sizes, eps_sizes, energies, dtype)}
         del buf, ebuf, ops, eps, ws, en
         torch.cuda.empty_cache()
     print(json.dumps(out), flush=True)
