@@ -314,7 +314,9 @@ static comet_status_t run_host_pipe(const Plan &P, const void *const *host_in, v
     struct Res {
         cudaStream_t cin = nullptr, cout = nullptr;
         std::vector<cudaEvent_t> ev;
-        ~Res() {
+        ~Res() {   // the copy streams finish before the call returns (its host buffers stay in use)
+            if (cin) cudaStreamSynchronize(cin);
+            if (cout) cudaStreamSynchronize(cout);
             for (cudaEvent_t e : ev) if (e) cudaEventDestroy(e);
             if (cin) cudaStreamDestroy(cin);
             if (cout) cudaStreamDestroy(cout);
