@@ -6,6 +6,7 @@ import itertools
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_2102_06827_gb300 as comet
@@ -342,8 +343,11 @@ def test_triples_plans():
     p = comet.TriplesPlan(terms(), LABELS, ext, SIGNS, "f32")
     info = p.info
     assert info["triples"] and info["terms"] == 9 and info["blocks"] == 2
-    # tiles of 4 per label: 2*2*2*1*1*2 + 2^6
-    assert info["tiles"] == 16 + 64
+    # tiles per label of the reported edges (4 for the fixed labels; the owned pair's edges
+    # depend on the precision)
+    edges = info["tile"]
+    assert sorted(edges).count(4) >= 4 and len(edges) == 6
+    assert info["tiles"] == sum(int(np.prod([-(-row[q] // edges[q]) for q in range(6)])) for row in ext)
     assert info["flops"] == 9 * 2 * (5 * 6 * 7 * 3 * 4 * 5 * 9 + 8 ** 6 * 40)
     # the owned pair sits on different operands in as many terms as any pair can (6 of 9)
     import oracle
