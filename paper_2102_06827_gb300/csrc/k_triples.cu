@@ -101,16 +101,13 @@ struct TileAddr {
 template <typename T>
 constexpr int kc_of() { return sizeof(T) == 4 ? KC : KC / 2; }
 
-__device__ __forceinline__ void cp_async_elem(void *dst, const void *src, int bytes) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    if (bytes == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
-    else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+__device__ __forceinline__ void cp_async_elem(unsigned dst, const void *src, int bytes) {
+    if (bytes == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// issue the asynchronous copies of one operand tile into S (entries outside the tile are not
-// written: they only feed T elements outside the block, which the energy skips)
 // Step entries of one operand: index idx -> (kk, r) with 8 consecutive kk and 4 consecutive r
 // per 32 lanes: with the row pitch = 4 mod 32 floats the lanes of a warp hit 32 different banks.
 template <int KCt>
@@ -121,25 +118,45 @@ __device__ __forceinline__ void entry(int idx, int &kk, int &r) {
     r = ((rest >> hb) << 2) | ((idx >> 3) & 3);
 }
 
+// A thread's entries are idx = threadIdx.x + it * NT, it < kc * R / NT.  Since NT is a multiple
+// of 32 * kc / 8, all of them have the kk of it = 0 and r = r0 + it * RS (RS = NT / kc, r0 < RS):
+// digit 0 of r is fixed, and for RS = 8 digit 1 is h + 2 (it & 1) and digit 2 is it / 2, for
+// RS = 16 digit 1 is h and digit 2 is it (h = r0 / 4).  So the row offset along digit 0 and the
+// summed label is formed once per step, and each entry adds two stride multiples with
+// compile-time factors.
+template <typename T>
+struct Lane {
+    static constexpr int kc = kc_of<T>(), RS = NT / kc, NIT = kc * R / NT;
+    static_assert(RS == 8 || RS == 16, "lane pattern");
+    int kk, r0, d0, h;
+    __device__ __forceinline__ Lane() {
+        entry<kc>((int)threadIdx.x, kk, r0);
+        d0 = r0 & 3;
+        h = r0 >> 2;
+    }
+    static __device__ __forceinline__ constexpr int dd1(int it) { return RS == 8 ? 2 * (it & 1) : 0; }
+    static __device__ __forceinline__ constexpr int d2(int it) { return RS == 8 ? it >> 1 : it; }
+};
+
+// issue the asynchronous copies of one operand tile into S (entries outside the tile are not
+// written: they only feed T elements outside the block, which the energy skips)
 template <typename T>
 __device__ __forceinline__ void stage_async(T (*S)[RP], const T *__restrict__ src, const TileAddr &ta, int kn) {
-    constexpr int kc = kc_of<T>();
+    using L = Lane<T>;
+    const L ln;
+    if (ln.kk >= kn || ln.d0 >= ta.rem[0]) return;
+    const T *row = src + (ta.base + ln.kk * ta.sd + ln.d0 * ta.s[0] + ln.h * ta.s[1]);
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(&S[ln.kk][ln.r0]);
 #pragma unroll
-    for (int it = 0; it < kc * R / NT; ++it) {
-        const int idx = threadIdx.x + it * NT;
-        int kk, r;
-        entry<kc>(idx, kk, r);
-        const int d0 = r & 3, d1 = (r >> 2) & 3, d2 = r >> 4;
-        if (kk < kn && d0 < ta.rem[0] && d1 < ta.rem[1] && d2 < ta.rem[2])
-            cp_async_elem(&S[kk][r], src + (ta.base + kk * ta.sd + d0 * ta.s[0] + d1 * ta.s[1] + d2 * ta.s[2]),
-                          (int)sizeof(T));
-    }
+    for (int it = 0; it < L::NIT; ++it)
+        if (ln.h + L::dd1(it) < ta.rem[1] && L::d2(it) < ta.rem[2])
+            cp_async_elem(dst + (unsigned)(it * L::RS * (int)sizeof(T)),
+                          row + (L::dd1(it) * ta.s[1] + L::d2(it) * ta.s[2]), (int)sizeof(T));
 }
 
 // addressing of one operand for a step: q / col per dimension (q = -1: the summed label)
 __device__ __forceinline__ TileAddr tile_addr(const int8_t *q, const int8_t *col, const int8_t *dig,
-                                              const int32_t *ext_b, const int (&tbase)[6], const int (&text)[6],
-                                              int k0) {
+                                              const int32_t *ext_b, const int *tbase, const int *text, int k0) {
     TileAddr ta;
     int st = 1;
     ta.base = 0;
@@ -150,8 +167,8 @@ __device__ __forceinline__ TileAddr tile_addr(const int8_t *q, const int8_t *col
             ta.sd = st;
             ta.base += k0 * st;
         } else {
-            const int b0 = pick6(tbase, q[m]);
-            const int rm = min(TS, pick6(text, q[m]) - b0);
+            const int b0 = tbase[q[m]];
+            const int rm = min(TS, text[q[m]] - b0);
             ta.base += b0 * st;
             if (dig[m] == 0) { ta.s[0] = st; ta.rem[0] = rm; }
             if (dig[m] == 1) { ta.s[1] = st; ta.rem[1] = rm; }
@@ -165,15 +182,13 @@ __device__ __forceinline__ TileAddr tile_addr(const int8_t *q, const int8_t *col
 // alpha times the X entries this thread copied for a step (after their copies completed)
 template <typename T>
 __device__ __forceinline__ void scale_own(T (*S)[RP], const TileAddr &ta, int kn, T alpha) {
-    constexpr int kc = kc_of<T>();
+    using L = Lane<T>;
+    const L ln;
+    if (ln.kk >= kn || ln.d0 >= ta.rem[0]) return;
+    T *row = &S[ln.kk][ln.r0];
 #pragma unroll
-    for (int it = 0; it < kc * R / NT; ++it) {
-        const int idx = threadIdx.x + it * NT;
-        int kk, r;
-        entry<kc>(idx, kk, r);
-        const int d0 = r & 3, d1 = (r >> 2) & 3, d2 = r >> 4;
-        if (kk < kn && d0 < ta.rem[0] && d1 < ta.rem[1] && d2 < ta.rem[2]) S[kk][r] *= alpha;
-    }
+    for (int it = 0; it < L::NIT; ++it)
+        if (ln.h + L::dd1(it) < ta.rem[1] && L::d2(it) < ta.rem[2]) row[it * L::RS] *= alpha;
 }
 
 // four consecutive shared-memory values (16-byte aligned): one 128-bit load for FP32, two for FP64
@@ -253,6 +268,7 @@ __global__ void __launch_bounds__(NT, 3) triples_kernel(const Args a) {
     __shared__ uint16_t s_dig[16][NT];    // per term and thread: rx | ry << 6 | case << 12
     __shared__ TileAddr s_ta[16][2];      // per term of the current tile: X and Y at k0 = 0
     __shared__ const void *s_ops[32];     // the current block's operand pointers
+    __shared__ int s_tile[2][12];         // tile bases and block extents per T label, two items
     const int t = threadIdx.x;
 #pragma unroll
     for (int i = 0; i < 16; ++i)
@@ -299,6 +315,7 @@ __global__ void __launch_bounds__(NT, 3) triples_kernel(const Args a) {
         e_acc = 0.0;
     };
     bool have = false;
+    int slot = 0;
     while (true) {
         if (t == 0) s_item = (int64_t)atomicAdd(a.counter, (unsigned long long)CHUNK);
         __syncthreads();
@@ -327,17 +344,21 @@ __global__ void __launch_bounds__(NT, 3) triples_kernel(const Args a) {
                 if (t < 2 * a.n_terms) s_ops[t] = a.ops[(int64_t)b * a.n_terms * 2 + t];
                 __syncthreads();
             }
-            // tile coordinates (first T label fastest; fewer than 2^31 tiles per block)
-            int tbase[6], text[6];
-            int rem = (int)(item - a.prefix[b]);
-#pragma unroll
-            for (int q = 0; q < 6; ++q) {
-                text[q] = s_ext[a.t_col[q]];
-                const int nt = (text[q] + TS - 1) / TS;
-                const int qt = rem / nt;
-                tbase[q] = (rem - qt * nt) * TS;
-                rem = qt;
+            // tile coordinates (first T label fastest; fewer than 2^31 tiles per block), by one
+            // thread into the slot the previous item does not read
+            const int *tbase = s_tile[slot], *text = s_tile[slot] + 6;
+            if (t == 0) {
+                int rem = (int)(item - a.prefix[b]);
+                for (int q = 0; q < 6; ++q) {
+                    const int e = s_ext[a.t_col[q]];
+                    const int nt = (e + TS - 1) / TS;
+                    const int qt = rem / nt;
+                    s_tile[slot][q] = (rem - qt * nt) * TS;
+                    s_tile[slot][6 + q] = e;
+                    rem = qt;
+                }
             }
+            slot ^= 1;
             __syncthreads();   // the previous item's steps are done with both buffers and s_ta
             if (t < 2 * a.n_terms) {   // operand addressing of every term for this tile
                 const TermDev &tm = s_term[t >> 1];
@@ -372,21 +393,32 @@ __global__ void __launch_bounds__(NT, 3) triples_kernel(const Args a) {
                 const int kn = min(kc, K - k0);
                 int pn = p, kn0 = k0 + kc;   // next step
                 if (kn0 >= K) { pn = p + 1; kn0 = 0; }
+                // alpha = -1: T - S = -(-T + S) in every rounding, so the accumulators are negated
+                // around the term instead of scaling its X entries
+                const bool neg = alpha == -1.0;
                 cp_async_wait_all();
-                if (alpha != 1.0) scale_own<T>(Xs[buf], addr(p, 0, k0), kn, (T)alpha);
+                if (alpha != 1.0 && !neg) scale_own<T>(Xs[buf], addr(p, 0, k0), kn, (T)alpha);
                 __syncthreads();   // step s is in buffer buf; step s-1's reads of buf^1 are done
                 if (pn < a.n_terms) issue(pn, kn0, buf ^ 1);
                 const int dg = s_dig[p][t];
+                if (neg && k0 == 0) {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) acc[e] = -acc[e];
+                }
                 step_compute<T>(Xs[buf], Ys[buf], kn, dg & 63, (dg >> 6) & 63, dg >> 12, acc);
+                if (neg && pn != p) {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) acc[e] = -acc[e];
+                }
                 p = pn;
                 k0 = kn0;
                 buf ^= 1;
             }
             int own_b[2], own_e[2], fix_c[4], fix_e[4];
 #pragma unroll
-            for (int j = 0; j < 2; ++j) { own_b[j] = pick6(tbase, a.own[j]); own_e[j] = pick6(text, a.own[j]); }
+            for (int j = 0; j < 2; ++j) { own_b[j] = tbase[a.own[j]]; own_e[j] = text[a.own[j]]; }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) { fix_c[j] = pick6(tbase, a.fixed[j]) + f[j]; fix_e[j] = pick6(text, a.fixed[j]); }
+            for (int j = 0; j < 4; ++j) { fix_c[j] = tbase[a.fixed[j]] + f[j]; fix_e[j] = text[a.fixed[j]]; }
             // energy of the thread's elements: D = sum_q sign_q eps_q[coordinate q], in the
             // precision of T (FP32: one FP32 reciprocal per element, the tile's 16 terms summed in
             // FP32 and added to the FP64 block sum once; FP64: all in FP64)
