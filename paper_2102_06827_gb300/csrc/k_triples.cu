@@ -366,6 +366,12 @@ __global__ void __launch_bounds__(NT, 3) triples_kernel(const Args a) {
                                               : tile_addr(tm.x_q, tm.x_col, tm.x_dig, s_ext, tbase, text, 0);
             }
             __syncthreads();
+            // a thread whose fixed-label coordinates lie outside the block (the ragged last tile
+            // along a label) still copies and meets every barrier, but skips the products: whole
+            // warps of such threads free their issue slots
+            bool fixed_ok = true;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) fixed_ok &= tbase[a.fixed[j]] + f[j] < text[a.fixed[j]];
             T acc[16];
 #pragma unroll
             for (int e = 0; e < 16; ++e) acc[e] = T(0);
@@ -405,7 +411,7 @@ __global__ void __launch_bounds__(NT, 3) triples_kernel(const Args a) {
 #pragma unroll
                     for (int e = 0; e < 16; ++e) acc[e] = -acc[e];
                 }
-                step_compute<T>(Xs[buf], Ys[buf], kn, dg & 63, (dg >> 6) & 63, dg >> 12, acc);
+                if (fixed_ok) step_compute<T>(Xs[buf], Ys[buf], kn, dg & 63, (dg >> 6) & 63, dg >> 12, acc);
                 if (neg && pn != p) {
 #pragma unroll
                     for (int e = 0; e < 16; ++e) acc[e] = -acc[e];
@@ -414,23 +420,18 @@ __global__ void __launch_bounds__(NT, 3) triples_kernel(const Args a) {
                 k0 = kn0;
                 buf ^= 1;
             }
-            int own_b[2], own_e[2], fix_c[4], fix_e[4];
+            int own_b[2], own_e[2];
 #pragma unroll
             for (int j = 0; j < 2; ++j) { own_b[j] = tbase[a.own[j]]; own_e[j] = text[a.own[j]]; }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) { fix_c[j] = tbase[a.fixed[j]] + f[j]; fix_e[j] = text[a.fixed[j]]; }
             // energy of the thread's elements: D = sum_q sign_q eps_q[coordinate q], in the
             // precision of T (FP32: one FP32 reciprocal per element, the tile's 16 terms summed in
             // FP32 and added to the FP64 block sum once; FP64: all in FP64)
-            bool fixed_ok = true;
-            T dfix = T(0);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const bool in = fix_c[j] < fix_e[j];
-                fixed_ok &= in;
-                if (in) dfix += (T)a.fixed_sign[j] * reinterpret_cast<const T *>(a.eps[(int64_t)b * 6 + a.fixed[j]])[fix_c[j]];
-            }
             if (fixed_ok) {
+                T dfix = T(0);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    dfix += (T)a.fixed_sign[j] *
+                            reinterpret_cast<const T *>(a.eps[(int64_t)b * 6 + a.fixed[j]])[tbase[a.fixed[j]] + f[j]];
                 const T *e0 = reinterpret_cast<const T *>(a.eps[(int64_t)b * 6 + a.own[0]]);
                 const T *e1 = reinterpret_cast<const T *>(a.eps[(int64_t)b * 6 + a.own[1]]);
                 T tile_e = T(0);
