@@ -14,10 +14,11 @@
 //     "owned" labels, the other four labels fixed per thread;
 //   * a step is one term and one chunk of its summed label (32 values for FP32, 16 for FP64):
 //     the X and Y tiles (chunk x 4^3) of step s+1 are copied into shared memory with cp.async
-//     while step s runs on the other buffer; each thread adds its 16 dot products into per-term
-//     sums and, when the term is complete, alpha times them into T.  Depending on whether its
-//     owned labels sit on X or Y, a thread reads 4 + 4, 16 + 1 or 1 + 16 values per summed
-//     index (four code paths);
+//     while step s runs on the other buffer; each thread adds its 16 dot products into its T
+//     elements (a term with alpha = -1 negates them before and after; any other alpha but 1
+//     scales the term's X entries in shared memory).  Depending on whether its owned labels sit
+//     on X or Y, a thread reads 4 + 4, 16 + 1 or 1 + 16 values per summed index (four code
+//     paths);
 //   * after the last term, the thread's 16 elements give their T^2 / D, summed in FP64 per
 //     thread across the CTA's items of one block and added to E_b once per block change.
 #include <cuda_runtime.h>
@@ -61,7 +62,9 @@ struct TermDev {
     int8_t x_col[4], y_col[4]; // extent-table column per operand dimension
     int8_t x_dig[4], y_dig[4]; // tile-row digit per dimension (owned labels first), -1 = summed
     int8_t d_col;
-    int8_t pad[7];
+    int8_t amode;              // alpha: 0 = 1, 1 = -1, 2 = any other value (integer tests per step:
+                               // the FP64 pipe is slow on this part)
+    int8_t pad[6];
 };
 
 struct Args {
@@ -395,15 +398,15 @@ __global__ void __launch_bounds__(NT, 3) triples_kernel(const Args a) {
             issue(0, 0, 0);
             while (p < a.n_terms) {
                 const int K = s_ext[s_term[p].d_col];
-                const double alpha = s_term[p].alpha;
+                const int amode = s_term[p].amode;
                 const int kn = min(kc, K - k0);
                 int pn = p, kn0 = k0 + kc;   // next step
                 if (kn0 >= K) { pn = p + 1; kn0 = 0; }
                 // alpha = -1: T - S = -(-T + S) in every rounding, so the accumulators are negated
                 // around the term instead of scaling its X entries
-                const bool neg = alpha == -1.0;
+                const bool neg = amode == 1;
                 cp_async_wait_all();
-                if (alpha != 1.0 && !neg) scale_own<T>(Xs[buf], addr(p, 0, k0), kn, (T)alpha);
+                if (amode == 2) scale_own<T>(Xs[buf], addr(p, 0, k0), kn, (T)s_term[p].alpha);
                 __syncthreads();   // step s is in buffer buf; step s-1's reads of buf^1 are done
                 if (pn < a.n_terms) issue(pn, kn0, buf ^ 1);
                 const int dg = s_dig[p][t];
@@ -677,6 +680,7 @@ comet_status_t comet_triples_energy(comet_plan_t plan, const void *operands, con
     for (int p = 0; p < tp.n_terms; ++p) {
         const TriTerm &tt = tp.terms[p];
         a.term[p].alpha = tt.alpha;
+        a.term[p].amode = (int8_t)(tt.alpha == 1.0 ? 0 : tt.alpha == -1.0 ? 1 : 2);
         for (int m = 0; m < 4; ++m) {
             a.term[p].x_q[m] = (int8_t)tt.x_q[m];
             a.term[p].y_q[m] = (int8_t)tt.y_q[m];
