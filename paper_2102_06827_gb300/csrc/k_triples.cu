@@ -210,8 +210,9 @@ __device__ __forceinline__ void load4(const double *p, double (&o)[4]) {
 template <typename T>
 __device__ __forceinline__ void step_compute(const T (*Xs)[RP], const T (*Ys)[RP], int kn, int rx, int ry,
                                              int kase, T (&acc)[16]) {
+    constexpr int UK = sizeof(T) == 4 ? 4 : 2;   // summed indices unrolled (FP64: registers)
     if (kase == 0) {
-#pragma unroll 2
+#pragma unroll UK
         for (int kk = 0; kk < kn; ++kk) {
             T xu[4], yv[4];
             load4(&Xs[kk][rx], xu);
@@ -222,7 +223,7 @@ __device__ __forceinline__ void step_compute(const T (*Xs)[RP], const T (*Ys)[RP
                 for (int v = 0; v < 4; ++v) acc[u * 4 + v] = fma(xu[u], yv[v], acc[u * 4 + v]);
         }
     } else if (kase == 1) {
-#pragma unroll 2
+#pragma unroll UK
         for (int kk = 0; kk < kn; ++kk) {
             T yu[4], xv[4];
             load4(&Ys[kk][ry], yu);
@@ -233,7 +234,7 @@ __device__ __forceinline__ void step_compute(const T (*Xs)[RP], const T (*Ys)[RP
                 for (int v = 0; v < 4; ++v) acc[u * 4 + v] = fma(xv[v], yu[u], acc[u * 4 + v]);
         }
     } else if (kase == 2) {
-#pragma unroll 2
+#pragma unroll UK
         for (int kk = 0; kk < kn; ++kk) {
             const T y = Ys[kk][ry];
 #pragma unroll
@@ -245,7 +246,7 @@ __device__ __forceinline__ void step_compute(const T (*Xs)[RP], const T (*Ys)[RP
             }
         }
     } else {
-#pragma unroll 2
+#pragma unroll UK
         for (int kk = 0; kk < kn; ++kk) {
             const T x = Xs[kk][rx];
 #pragma unroll
