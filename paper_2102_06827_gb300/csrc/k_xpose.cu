@@ -415,6 +415,23 @@ static void launch_tile(const XposeParams &p, uint32_t g, size_t smem, cudaStrea
     xpose_tile_kernel<OP, T, VI, VO, OFF><<<g, XT, smem, s>>>(p);
 }
 
+// vector widths W (16 bytes), 2 (8 bytes, FP32 only) and 1, chosen at run time
+template <int OP, typename T, int VI, typename OFF>
+static void launch_tile_vo(const XposeParams &p, int vo, uint32_t g, size_t smem, cudaStream_t s) {
+    constexpr int W = 16 / sizeof(T), H = W == 4 ? 2 : 1;
+    if (vo >= W) launch_tile<OP, T, VI, W, OFF>(p, g, smem, s);
+    else if (W == 4 && vo == 2) launch_tile<OP, T, VI, H, OFF>(p, g, smem, s);
+    else launch_tile<OP, T, VI, 1, OFF>(p, g, smem, s);
+}
+
+template <int OP, typename T, typename OFF>
+static void launch_tile_v(const XposeParams &p, int vi, int vo, uint32_t g, size_t smem, cudaStream_t s) {
+    constexpr int W = 16 / sizeof(T), H = W == 4 ? 2 : 1;
+    if (vi >= W) launch_tile_vo<OP, T, W, OFF>(p, vo, g, smem, s);
+    else if (W == 4 && vi == 2) launch_tile_vo<OP, T, H, OFF>(p, vo, g, smem, s);
+    else launch_tile_vo<OP, T, 1, OFF>(p, vo, g, smem, s);
+}
+
 template <int OP, typename T>
 static cudaError_t launch_op(const XposeParams &p, int vi, int vo, cudaStream_t s) {
     const uint32_t g = xpose_grid(p);
@@ -439,17 +456,8 @@ static cudaError_t launch_op(const XposeParams &p, int vi, int vo, cudaStream_t 
     }
     const size_t smem = xpose_smem_bytes(p, (int)sizeof(T));
     if (smem > 96 * 1024) return cudaErrorInvalidConfiguration;
-    if (p.off32) {
-        if (vi >= W && vo >= W) launch_tile<OP, T, W, W, int32_t>(p, g, smem, s);
-        else if (vi >= W) launch_tile<OP, T, W, 1, int32_t>(p, g, smem, s);
-        else if (vo >= W) launch_tile<OP, T, 1, W, int32_t>(p, g, smem, s);
-        else launch_tile<OP, T, 1, 1, int32_t>(p, g, smem, s);
-    } else {
-        if (vi >= W && vo >= W) launch_tile<OP, T, W, W, int64_t>(p, g, smem, s);
-        else if (vi >= W) launch_tile<OP, T, W, 1, int64_t>(p, g, smem, s);
-        else if (vo >= W) launch_tile<OP, T, 1, W, int64_t>(p, g, smem, s);
-        else launch_tile<OP, T, 1, 1, int64_t>(p, g, smem, s);
-    }
+    if (p.off32) launch_tile_v<OP, T, int32_t>(p, vi, vo, g, smem, s);
+    else launch_tile_v<OP, T, int64_t>(p, vi, vo, g, smem, s);
     return cudaGetLastError();
 }
 

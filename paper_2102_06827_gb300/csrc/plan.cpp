@@ -220,6 +220,13 @@ void setup_xpose(int rank, const int64_t *ext_in, const int64_t *sin_in,
         }
         return std::max<uint32_t>(1, std::min(t, E));
     };
+    // rounding unit of a tile edge along a leading run (transposing mode): W, or 2 for an FP32
+    // run whose first extent is even but not a multiple of 4 (it moves as 8-byte vectors)
+    auto edge_mult = [&](const Radix &r) -> uint32_t {
+        if (W != 4 || r.n == 0 || r.ext[0] % 2 != 0 || r.ext[0] % 4 == 0 || r.total % 4 == 0) return W;
+        return 2;
+    };
+    const uint32_t mu = edge_mult(p->u), mv = edge_mult(p->v);
     uint32_t tu, tv, tw;
     if (same && R.empty()) {
         tu = Eu > TAB ? std::max<uint32_t>(TAB + 1, std::min<uint32_t>(Eu, TILE)) : Eu;
@@ -236,13 +243,13 @@ void setup_xpose(int rank, const int64_t *ext_in, const int64_t *sin_in,
     } else {
         // both runs at least 64 elements where the extents allow: a leading input run up to 128
         // is kept whole, a longer one is cut into pieces of about 64
-        tu = Eu <= 128 ? Eu : balanced(Eu, 64, W);
-        tv = balanced(Ev, std::min<uint32_t>(TAB, std::max<uint32_t>(16, TILE / tu)), W);
+        tu = Eu <= 128 ? Eu : balanced(Eu, 64, mu);
+        tv = balanced(Ev, std::min<uint32_t>(TAB, std::max<uint32_t>(16, TILE / tu)), mv);
         tw = std::min<uint32_t>(Er, std::min<uint32_t>(TAB, std::max<uint32_t>(1, TILE / (tu * tv))));
     }
     // vector widths: 16-byte accesses when every stride other than the fast digit's is a
     // multiple of the width, the fast digit's extent is too, and the tile edge along the
-    // vector direction is a multiple of it
+    // vector direction is a multiple of it; else 8-byte accesses for FP32 on the same terms
     int w = 16 / elem_bytes;
     auto ok_in = [&](int vw) {
         if (in_off % vw || p->u.s0[0] != 1 || p->u.ext[0] % vw || tu % vw) return false;
@@ -260,12 +267,15 @@ void setup_xpose(int rank, const int64_t *ext_in, const int64_t *sin_in,
         for (int d = 0; d < p->r.n; ++d) if (p->r.s1[d] % vw) return false;
         return true;
     };
-    // the kernels come in 16-byte and element-wide variants only.  A single long run (copy
+    // the transposing kernel comes in 16-byte, 8-byte (FP32) and element-wide variants, copy
+    // mode in 16-byte and element-wide ones (measured: its element-wise rows, all in flight as
+    // asynchronous copies, beat 8-byte vectors through registers).  A single long run (copy
     // mode, R empty) moves its ragged tail element-wise, so only the strides matter there.
     p->single_run = (same && R.empty() && Eu > TAB) ? 1 : 0;
     const bool unit = p->u.s0[0] == 1 && p->u.s1[0] == 1 && in_off % w == 0 && out_off % w == 0;
-    const int vi = (p->single_run ? unit : ok_in(w)) ? w : 1;
-    const int vo = (p->single_run ? unit : ok_out(w)) ? w : 1;
+    auto pick = [&](const auto &ok) { return ok(w) ? w : (w == 4 && !same && ok(2)) ? 2 : 1; };
+    const int vi = p->single_run ? (unit ? w : 1) : pick(ok_in);
+    const int vo = p->single_run ? (unit ? w : 1) : pick(ok_out);
     const int vc = std::min(vi, vo);
     *vec_in = same ? vc : vi;
     *vec_out = same ? -vc : vo;   // negative = copy mode (no shared-memory transposition)
