@@ -3,7 +3,8 @@
 //
 // GB300 form: the input's leading (stride-1) dims are fused into U and the output's into V.  A
 // CTA stages a 64 x 64 (u, v) tile in shared memory: global reads run along U, global writes
-// along V, both as 16-byte vectors where the strides allow.  When input and output share the
+// along V, both as 16-byte vectors where the strides allow (8-byte for an FP32 run of even
+// extent).  When input and output share the
 // same stride-1 dim ("copy mode") the tile needs no transposition and goes straight through
 // registers.  The same engine performs three element operations:
 //   OP_MOVE   raw 4/8-byte words (bit-exact permutation, comet_transpose)
