@@ -192,6 +192,15 @@ void setup_xpose(int rank, const int64_t *ext_in, const int64_t *sin_in,
     // copy mode (same stride-1 dim on both sides): V stays empty, R supplies the rows
     std::vector<int> R;
     for (int k = 0; k < n; ++k) if (!used[in_order[k]]) R.push_back(in_order[k]);
+    // copy mode with a short shared run (under 128 bytes): a block's rows would otherwise follow
+    // the input order only, and each would land as a separate short piece of the output; the
+    // row digit nearest to the run in the output comes second, so that a block's rows also
+    // form contiguous spans of the output
+    if (same && R.size() >= 2 && pu * elem_bytes < 128) {
+        size_t best = 1;
+        for (size_t k = 2; k < R.size(); ++k) if (o2[R[k]] < o2[R[best]]) best = k;
+        if (o2[R[best]] < o2[R[0]]) std::rotate(R.begin() + 1, R.begin() + best, R.begin() + best + 1);
+    }
     fill_radix(&p->u, U, e2.data(), i2.data(), o2.data());
     fill_radix(&p->v, V, e2.data(), i2.data(), o2.data());
     fill_radix(&p->r, R, e2.data(), i2.data(), o2.data());
