@@ -84,14 +84,6 @@ struct Args {
 
 using namespace tri;
 
-// value of a 6-entry register array at a runtime position (a select chain: no local memory)
-__device__ __forceinline__ int pick6(const int (&v)[6], int q) {
-    int r = 0;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) r = q == i ? v[i] : r;
-    return r;
-}
-
 // Operand tile addressing of one step (term p, summed-label chunk k0): element (kk, r) of the
 // tile sits at base + kk * sd + digit0(r) * s0 + digit1(r) * s1 + digit2(r) * s2 (the operand's
 // three T labels in its dimension order, 2-bit digits of r), present when kk < kn and each
