@@ -241,8 +241,9 @@ comet_status_t comet_plan_flops(comet_plan_t plan, double *flops);
 comet_status_t comet_plan_flops_natural(comet_plan_t plan, double *flops);
 
 /* Human-readable JSON description of the plan: steps, operand order, the M/N/K label groups
- * and their order, the chosen form among those enumerated, costs.  Writes at most len bytes
- * including the terminating NUL; COMET_ERR_ARG if it does not fit. */
+ * and their order, the chosen form among those enumerated, costs; for a pure permutation step
+ * the transpose engine's vector widths in elements (a negative vec_out: copy mode) and tile.
+ * Writes at most len bytes including the terminating NUL; COMET_ERR_ARG if it does not fit. */
 comet_status_t comet_plan_describe(comet_plan_t plan, char *buf, size_t len);
 
 /*

@@ -1168,6 +1168,9 @@ std::string describe_plan(const Plan &P) {
           << ",\"a_labels\":" << names(P.slots[s.a].labels);
         if (s.b >= 0) o << ",\"b_labels\":" << names(P.slots[s.b].labels);
         o << ",\"c_labels\":" << names(P.slots[s.c].labels);
+        if (s.kernel == KK_COPY)   // transpose engine: vector widths (negative out = copy mode), tile
+            o << ",\"vec_in\":" << s.copy_vec_in << ",\"vec_out\":" << s.copy_vec_out << ",\"tile\":["
+              << s.copy.tu << "," << s.copy.tv << "," << s.copy.tw << "]";
         if (s.kernel != KK_COPY) {
             o << ",\"swap\":" << s.form.swap << ",\"M\":" << names(s.form.M) << ",\"N\":" << names(s.form.N)
               << ",\"K\":" << names(s.form.K) << ",\"batch\":" << names(s.form.Bt)

@@ -246,6 +246,28 @@ def test_transpose_argument_checks():
     assert e.value.name == "COMET_ERR_ARG"
 
 
+def test_transpose_vector_widths():
+    # 16-byte vectors where the leading runs allow, 8-byte ones for FP32 runs of even extent in
+    # the transposing kernel, element-wise rows in copy mode otherwise (widths in elements;
+    # a negative vec_out marks copy mode)
+    def step(expr, ext, dtype):
+        return comet.Plan(expr, ext, dtype).info["steps"][0]
+    t = "C[c,b,d,a] = A[a,b,c,d]"
+    s = step(t, dict(a=232, b=16, c=148, d=54), "f32")
+    assert (s["kernel"], s["vec_in"], s["vec_out"]) == ("copy", 4, 4)
+    s = step(t, dict(a=230, b=16, c=146, d=54), "f32")
+    assert (s["vec_in"], s["vec_out"]) == (2, 2) and s["tile"][0] % 2 == 0 and s["tile"][1] % 2 == 0
+    s = step(t, dict(a=231, b=16, c=146, d=54), "f32")
+    assert (s["vec_in"], s["vec_out"]) == (1, 2)
+    s = step(t, dict(a=230, b=16, c=146, d=54), "f64")
+    assert (s["vec_in"], s["vec_out"]) == (2, 2)
+    # copy mode (the first label stays first): 8-byte rows are not used there
+    s = step("C[a,e,d,b,c,f] = A[a,b,c,d,e,f]", dict(a=14, b=30, c=31, d=42, e=62, f=12), "f32")
+    assert (s["vec_in"], s["vec_out"]) == (1, -1)
+    s = step("C[a,e,d,b,c,f] = A[a,b,c,d,e,f]", dict(a=16, b=30, c=31, d=42, e=62, f=12), "f32")
+    assert (s["vec_in"], s["vec_out"]) == (4, -4)
+
+
 def test_batched_plan_structure():
     import numpy as np
     import synth
