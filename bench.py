@@ -37,7 +37,6 @@ N_ELEM = 64 * 192 * 192 * 64
 SCALE = 1.0 / math.sqrt(64 * 192)
 METRIC = "contraction GFLOP/s and fraction of roofline (FP64 vs split-precision) at stated error"
 WORKLOAD = "ccsd_doubles_like o=64 v=192: C[i,a,j,b] = sum_{k,c} A[k,a,c,i]*B[c,b,k,j]"
-FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate from the recipe's nominal table
 
 
 def args_parse():
@@ -64,22 +63,74 @@ def args_parse():
                          "fused nine-term accumulation with its energy epilogue (separate JSON lines)")
     ap.add_argument("--te-blocks", type=int, default=4096, help="triples_energy: blocks")
     ap.add_argument("--te-f64-blocks", type=int, default=64, help="triples_energy: blocks of the FP64 leg")
+    ap.add_argument("--peak", default=None, choices=["fp64"],
+                    help="measure the FP64 pipe (DFMA and f64 tensor-core MMA probes) and exit")
     ap.add_argument("--sweep", default=None, choices=["transpose"],
                     help="time the transpose sweep (rank-4/rank-6, FP32/FP64, 64 MiB - 2 GiB) and exit")
     return ap.parse_args()
 
 
+def measure_fp64_peak(repeats: int = 3) -> dict:
+    """FP64 throughput on this GPU: each probe kernel of the library (DFMA chains, and f64
+    tensor-core MMA chains of three shapes) launched after a warm-up, timed with CUDA events on
+    its stream, best of `repeats`.  The peak is the fastest probe: it is the denominator of every
+    FP64 roofline fraction in the bench lines."""
+    import torch
+    import paper_2102_06827_gb300 as comet
+    s = torch.cuda.current_stream()
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    res = {}
+    for kind, name in comet.FP64_PROBES.items():
+        iters = 256
+        comet.probe_fp64(kind, iters, sink)   # warm-up (and module load)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = 0.0
+        for _ in range(repeats + 1):
+            e0.record(s)
+            fl = comet.probe_fp64(kind, iters, sink)
+            e1.record(s)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            if ms < 20.0 and iters < (1 << 20):   # grow the launch to ~50 ms before trusting it
+                iters = int(iters * 50.0 / max(ms, 1e-3))
+                continue
+            best = max(best, fl / (ms * 1e-3) / 1e12)
+        res[name] = round(best, 4)
+    comet.sync_status()
+    peak_name = max(res, key=res.get)
+    return {"tflops": res[peak_name], "probe": peak_name, "probes_tflops": res,
+            "how": "bench.py FP64 probes (comet_probe_fp64): independent chains, one launch of ~50 ms, "
+                   "CUDA events, best of 3"}
+
+
+def run_peak_fp64(a) -> int:
+    import torch
+    torch.cuda.set_device(0)
+    clocks = ClockSampler(0)
+    clocks.start()
+    res = measure_fp64_peak()
+    res["clocks"] = clocks.stop()
+    print(json.dumps({"peak": "fp64", **res}), flush=True)
+    return 0
+
+
 def run_transpose_sweep() -> int:
     """Every case of the sweep: GB/s (read + write bytes / time) against the measured HBM copy
-    bandwidth and against a same-run device-to-device copy; each result checked bit-exactly by
-    applying the inverse permutation (transpose followed by its inverse is the identity)."""
+    bandwidth and against a same-run device-to-device copy.  Each result is checked bit for bit
+    against the oracle on a seeded sample of outputs (the first and last elements included):
+    that is the mode's CPU-baseline leg, timed on the host cores.  The inverse permutation
+    applied to the result must also give the input back bit for bit."""
+    import numpy as np
     import torch
+    import oracle
     import paper_2102_06827_gb300 as comet
     import synth
     dev = torch.device("cuda", 0)
     peaks = measured_peaks() or {}
     hbm = peaks.get("hbm_gbs", 6800.0)
     res = []
+    cpu_s, cpu_bytes, n_checked = 0.0, 0, 0
     for name, rank, es, perm, ext in synth.transpose_sweep_cases():
         n = math.prod(ext)
         dt = torch.float32 if es == 4 else torch.float64
@@ -109,16 +160,33 @@ def run_transpose_sweep() -> int:
         comet.sync_status()
         ok = bool(torch.equal(z.view(torch.int32 if es == 4 else torch.int64),
                               x.view(torch.int32 if es == 4 else torch.int64)))
+        # the oracle leg: seeded sample of outputs (plus the first and the last), bits compared
+        sel = np.unique(np.concatenate([[0, n - 1], synth.integers(
+            zlib.crc32(name.encode()) & 0xFFFF, 1, 65536, 0, n - 1).astype(np.int64)]))
+        got = y[torch.from_numpy(sel).to(dev)].cpu().numpy()
+        host = np.asfortranarray(x.cpu().numpy().reshape(tuple(reversed(ext))).T)
+        t0 = time.perf_counter()
+        ref = oracle.transpose_sampled(host, perm, sel)
+        cpu_s += time.perf_counter() - t0
+        cpu_bytes += 2 * es * len(sel)
+        n_checked += len(sel)
+        oracle_ok = got.tobytes() == ref.tobytes()
         gbs = 2 * es * n / t / 1e9
         res.append({"case": name, "perm": perm, "extents": ext, "bytes": es * n, "gbs": round(gbs, 1),
                     "frac": round(gbs / hbm, 4), "memcpy_gbs": round(2 * es * n / tc / 1e9, 1),
-                    "bit_exact_inverse": ok})
-        del x, y, z
+                    "bit_exact_oracle": oracle_ok, "oracle_samples": len(sel), "bit_exact_inverse": ok})
+        del x, y, z, host
     fr = sorted(r["frac"] for r in res)
     print(json.dumps({"sweep": "transpose", "cases": len(res), "hbm_gbs": hbm,
                       "frac_min": fr[0], "frac_median": fr[len(fr) // 2], "frac_max": fr[-1],
                       "cases_at_or_above_0.70": sum(f >= 0.70 for f in fr),
-                      "all_bit_exact": all(r["bit_exact_inverse"] for r in res), "results": res}))
+                      "all_bit_exact_oracle": all(r["bit_exact_oracle"] for r in res),
+                      "all_bit_exact_inverse": all(r["bit_exact_inverse"] for r in res),
+                      "cpu_baseline": {"value": cpu_bytes / max(cpu_s, 1e-9) / 1e9, "unit": "GB/s",
+                                       "cores": oracle.threads(), "kind": "oracle",
+                                       "sample": f"{n_checked} sampled outputs over {len(res)} cases "
+                                                 "(each case: its first and last outputs and 65536 seeded ones)"},
+                      "results": res}))
     return 0
 
 
@@ -135,6 +203,7 @@ def run_triples(a) -> int:
     from batched_data import EXPR as TEXPR, LABELS, Blocks
     ext = synth.triples_blocks(4096)
     peaks = measured_peaks() or {}
+    fp64_peak = measure_fp64_peak()
     out = {"workload": "batched triples: 4096 blocks, extents uniform 8..32 (seed 3), normal(0,0.1)",
            "flops": float(np.sum(2.0 * np.prod(ext, axis=1)))}
     for prec, dtype, dt, steps in (("split_bf16", np.float32, "f32", a.steps), ("native", np.float64, "f64", 1)):
@@ -166,7 +235,9 @@ def run_triples(a) -> int:
             entry["bf16_mma_tflops"] = 6 * plan.flops / (t * 1e-3) / 1e12
             entry["frac_of_bf16_peak"] = entry["bf16_mma_tflops"] / peaks.get("bf16_tflops", 1900.0)
         else:
-            entry["frac_of_fp64_nominal"] = gf / 1e3 / FP64_NOMINAL_TFLOPS
+            entry["roofline"] = {"bound": "fp64", "achieved": gf / 1e3, "peak": fp64_peak["tflops"],
+                                 "unit": "TFLOP/s", "frac": gf / 1e3 / fp64_peak["tflops"],
+                                 "peak_source": "measured: " + fp64_peak["how"] + ", " + fp64_peak["probe"]}
         out[prec] = entry
         del blocks, ws, res, g
         torch.cuda.empty_cache()
@@ -226,6 +297,7 @@ def run_triples_energy(a) -> int:
     col = {l: q for q, l in enumerate(LABELS)}
     out = {"workload": "fused triples energy: nine permuted terms per block, E_b = sum T^2/D_b; "
                        "extents uniform 8..32 (seed 3), operands uniform [-1,1) (seed 11)"}
+    fp64_peak = measure_fp64_peak()
 
     def build(n_blocks, dtype):
         ext = synth.triples_blocks(4096)[:n_blocks]
@@ -307,14 +379,15 @@ def run_triples_energy(a) -> int:
         energies = en.cpu().numpy()
         sm_mhz = ck.get("sm_mhz") or 1900.0
         # FMA pipe peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flops per clock (FP64:
-        # the nominal 1.25 TFLOP/s); the kernel's useful flops are plan.flops
-        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12 if name == "f32" else FP64_NOMINAL_TFLOPS
+        # the measured FP64 probe peak); the kernel's useful flops are plan.flops
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12 if name == "f32" else fp64_peak["tflops"]
         achieved = plan.flops / (t * 1e-3) / 1e12
         out[name] = {"blocks": n_blocks, "ms_per_step": t, "steps": steps, "tflops": achieved,
                      "roofline": {"bound": "alu" if name == "f32" else "fp64", "achieved": achieved,
                                   "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                                   "peak_source": ("FP32 FMA lanes x median SM clock under load" if name == "f32"
-                                                  else "nominal FP64 rate")},
+                                                  else "measured: " + fp64_peak["how"] + ", "
+                                                  + fp64_peak["probe"])},
                      "tiles": plan.info["tiles"], "flops": plan.flops, "clocks": ck,
                      "energy_sum": float(energies.sum()),
                      "cpu_baseline": cpu_baseline(ext, buf, ebuf, sizes, eps_sizes, energies, dtype)}
@@ -753,6 +826,8 @@ def main():
         return run_profile_case(a.profile_case, a)
     if a.sweep == "transpose":
         return run_transpose_sweep()
+    if a.peak == "fp64":
+        return run_peak_fp64(a)
     if a.workload == "triples":
         return run_triples(a)
     if a.workload == "small":
@@ -823,6 +898,15 @@ def main():
                 "achieved_counts": "6 BF16 products x 2*M*N*K per launch (M=N=K=12288)",
                 "ms_per_launch": gemm_ms,
                 "effective_fp32_tflops": flops / (gemm_ms * 1e-3) / 1e12}
+    # the cuBLAS peak was taken at its own clocks: time x SM clock makes the two comparable
+    peak_mhz = ((peaks or {}).get("clocks_under_load") or {}).get("sm_mhz_median")
+    run_mhz = (clk or {}).get("sm_mhz")
+    if peak_mhz and run_mhz:
+        roofline["clock_normalised"] = {
+            "sm_mhz_this_run": run_mhz, "sm_mhz_of_peak_measurement": peak_mhz,
+            "frac_at_equal_clock": achieved / peak * peak_mhz / run_mhz,
+            "note": "frac x (peak's median SM clock / this run's median SM clock): the work per clock "
+                    "against cuBLAS's"}
     prepass = {"kernel": "split_prepass", "launches_per_step": p_launch / max(1, a.steps),
                "ms_per_step": p_ms / max(1, a.steps), "bytes_per_step": pre_bytes,
                "achieved_gbs": pre_bytes / (p_ms / max(1, a.steps) * 1e-3) / 1e9 if p_ms else None,
@@ -831,7 +915,9 @@ def main():
 
     # ---------------- FP64 form of the same contraction ----------------
     plan64 = comet.Plan(EXPR, EXT, torch.float64, precision="native")
-    A64, B64 = A.double(), B.double()
+    # genuine FP64 operands (53-bit uniforms of the same seeds), not FP32 data widened: the
+    # products then round in FP64 and the stated FP64 error means something
+    A64, B64 = make_inputs(torch, torch.float64, dev)
     C64 = torch.empty(N_ELEM, dtype=torch.float64, device=dev)
     plan64.contract([A64, B64], C64)
     comet.sync_status()
@@ -849,11 +935,14 @@ def main():
     ms64 = max_over_ranks(f0.elapsed_time(f1)) / a.fp64_steps
     gflops64 = world * flops / (ms64 * 1e-3) / 1e9
     k64 = prof64.get("gemm_f64", (1, ms64))
+    fp64_peak = measure_fp64_peak()
     fp64 = {"gflops": gflops64, "ms_per_step": ms64, "steps": a.fp64_steps,
             "roofline": {"kernel": "gemm_f64", "bound": "fp64", "achieved": flops / (k64[1] / k64[0] * 1e-3) / 1e12,
-                         "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                         "frac": flops / (k64[1] / k64[0] * 1e-3) / 1e12 / FP64_NOMINAL_TFLOPS,
-                         "peak_source": "nominal FP64 rate of the recipe table (not in MEASURED_PEAKS.json)"},
+                         "peak": fp64_peak["tflops"], "unit": "TFLOP/s",
+                         "frac": flops / (k64[1] / k64[0] * 1e-3) / 1e12 / fp64_peak["tflops"],
+                         "peak_source": "measured in this run: " + fp64_peak["how"] + ", fastest probe "
+                                        + fp64_peak["probe"],
+                         "probes_tflops": fp64_peak["probes_tflops"]},
             "split_speedup_over_fp64": ms64 / ms_step}
 
     # ---------------- the same FP64 contraction emulated on the BF16 tensor cores ----------------
@@ -940,16 +1029,23 @@ def main():
         cflops = 2.0 * 64 * 192 * len(sel)
         cpu = {"value": cflops / t_cpu / 1e9, "unit": "GFLOP/s", "cores": oracle.threads(), "kind": "oracle",
                "sample": f"{len(sel)} sampled outputs of C (each a 12288-term FP64 sum), {t_cpu:.1f} s"}
+        # the FP64 forms ran on genuine FP64 operands: their reference is the oracle on those
+        del hA64, hB64
+        gA64 = np.asfortranarray(A64.cpu().numpy().reshape((64, 192, 192, 64), order="F"))
+        gB64 = np.asfortranarray(B64.cpu().numpy().reshape((192, 192, 64, 64), order="F"))
+        ref64 = oracle.einsum_sampled(EXPR, gA64, gB64, sel=sel)
+        del gA64, gB64
         got = C.cpu().numpy().astype(np.float64)[sel]
         got64 = C64.cpu().numpy()[sel]
         got_e = Ce.cpu().numpy()[sel]
-        den = float(np.abs(ref).max())
-        err = {"split_bf16": {"normwise_rel": float(np.abs(got - ref).max() / den),
-                              "max_abs": float(np.abs(got - ref).max()), "tolerance": 1e-6},
-               "fp64": {"normwise_rel": float(np.abs(got64 - ref).max() / den),
-                        "max_abs": float(np.abs(got64 - ref).max()), "tolerance": 1e-12},
-               "emu_f64": {"normwise_rel": float(np.abs(got_e - ref).max() / den),
-                           "max_abs": float(np.abs(got_e - ref).max()), "tolerance": 1e-12},
+        den, den64 = float(np.abs(ref).max()), float(np.abs(ref64).max())
+
+        def e_of(x, r, d, tol, inputs):
+            return {"normwise_rel": float(np.abs(x - r).max() / d), "max_abs": float(np.abs(x - r).max()),
+                    "tolerance": tol, "inputs": inputs}
+        err = {"split_bf16": e_of(got, ref, den, 1e-6, "FP32 uniforms"),
+               "fp64": e_of(got64, ref64, den64, 1e-12, "FP64 uniforms (53-bit)"),
+               "emu_f64": e_of(got_e, ref64, den64, 1e-12, "FP64 uniforms (53-bit)"),
                "samples": len(sel)}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": a.steps,

@@ -277,7 +277,13 @@ comet_status_t comet_contract(comet_plan_t plan, const void *const *inputs, void
  *   sharing    every call uses the same array, and the array keeps whatever the last call left
  *              in it (the path clears what it needs cleared).  Calls whose GPU work overlaps,
  *              e.g. on two streams without ordering between them, race on the array.
- * Returns the codes of comet_contract().  Allocates nothing, on the host or the device.
+ *   reset      the looked-up address belongs to the device's current context: after
+ *              cudaDeviceReset() (or any teardown of the primary context) the library's device
+ *              state, this address included, is stale; reload the library before further calls.
+ * Returns the codes of comet_contract().  Allocates no device memory: no cudaMalloc and no
+ * allocator call on any path.  Host-side bookkeeping is not covered by that promise: a refusal
+ * builds its error message, and with the kernel profiler on (comet_profile_enable) the call
+ * creates CUDA timing events like every other entry point.
  */
 #define COMET_NOALLOC_MAX_BYTES (32u << 20)
 comet_status_t comet_contract_noalloc(comet_plan_t plan, const void *const *inputs, void *output,
@@ -405,6 +411,20 @@ typedef struct {
 
 comet_status_t comet_profile_enable(int on);
 comet_status_t comet_profile_read(comet_kernel_stat_t *stats, int max_stats, int *n_stats);
+
+/*
+ * comet_probe_fp64 — FP64 throughput probe, the measured denominator of the FP64 rooflines
+ * (a measurement utility; the paper has no counterpart).  Launches one kernel on `stream` that
+ * keeps the FP64 pipe busy with independent dependency chains and no memory traffic; the caller
+ * times it (CUDA events on the same stream) and divides *flops by the elapsed time.
+ *   kind   0 DFMA (FP64 FMA pipe), 1 f64 tensor-core MMA m8n8k4, 2 m16n8k4, 3 m16n8k16
+ *   iters  loop trips per thread, 1 .. 2^24 (the launch's duration grows linearly with it)
+ *   flops  host out: the FP64 flops the launch performs (an FMA counts 2)
+ *   sink   device buffer of at least 8 bytes (caller-owned; written only under a condition
+ *          that never holds, so that the arithmetic cannot be dropped by the compiler)
+ * Errors: COMET_ERR_NULL, COMET_ERR_ARG (kind or iters out of range), COMET_ERR_CUDA (launch).
+ */
+comet_status_t comet_probe_fp64(int kind, int iters, double *flops, void *sink, void *stream);
 
 /* Synchronises `stream`, then reads and clears the device status word: COMET_OK, or
  * COMET_ERR_TIMEOUT if a kernel's wait ran out, or COMET_ERR_CUDA if the stream reported an

@@ -372,3 +372,15 @@ def profile_read() -> dict:
 def sync_status(stream=None):
     """comet_sync_status(): synchronise and surface a device-side timeout."""
     _lib.check(lib().comet_sync_status(_stream_handle(stream)), "comet_sync_status")
+
+
+FP64_PROBES = {0: "dfma", 1: "dmma_m8n8k4", 2: "dmma_m16n8k4", 3: "dmma_m16n8k16"}
+
+
+def probe_fp64(kind: int, iters: int, sink, stream=None) -> float:
+    """comet_probe_fp64(): launches one FP64 throughput probe kernel (``FP64_PROBES[kind]``) on
+    the stream and returns the flops it performs; the caller times the launch."""
+    f = ctypes.c_double()
+    _lib.check(lib().comet_probe_fp64(int(kind), int(iters), ctypes.byref(f), _ptr(sink),
+                                      _stream_handle(stream)), "comet_probe_fp64")
+    return f.value

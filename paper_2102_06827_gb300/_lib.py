@@ -25,7 +25,7 @@ EXPORTS = [
     "comet_transpose", "comet_fill", "comet_plan_batched", "comet_batched_num_tiles", "comet_batched_set_tile",
     "comet_batched_prepare", "comet_contract_batched", "comet_batched_autotune",
     "comet_plan_triples", "comet_triples_prepare", "comet_triples_energy",
-    "comet_profile_enable", "comet_profile_read", "comet_sync_status", "comet_plan_destroy", "comet_status_string", "comet_last_error_message",
+    "comet_profile_enable", "comet_profile_read", "comet_probe_fp64", "comet_sync_status", "comet_plan_destroy", "comet_status_string", "comet_last_error_message",
     "comet_version",
 ]
 
@@ -107,6 +107,7 @@ def load():
     L.comet_triples_energy.argtypes = [vp, vp, vp, vp, vp, vp]
     L.comet_profile_enable.argtypes = [ctypes.c_int]
     L.comet_profile_read.argtypes = [ctypes.POINTER(KernelStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.comet_probe_fp64.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp, vp]
     L.comet_sync_status.argtypes = [vp]
     L.comet_plan_destroy.argtypes = [vp]
     L.comet_plan_destroy.restype = None
