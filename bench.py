@@ -192,22 +192,27 @@ def run_transpose_sweep() -> int:
 
 def run_triples(a) -> int:
     """The batched triples workload: 4096 blocks T[a,b,c,i,j,k] = sum_d A[d,a,b,i] * B[c,d,j,k],
-    every extent uniform in 8..32 (seed 3), inputs normal(0, 0.1); one persistent launch per
-    step inside a captured CUDA graph, reduce epilogue (s_b, q_b), tiles chosen by the
-    autotuner.  Prints one JSON line (not the headline line)."""
+    every extent uniform in 8..32 (seed 3), inputs normal(0, 0.1); one launch sequence per step
+    (abs-max, split pre-pass, the persistent kernel) inside a captured CUDA graph, reduce epilogue
+    (s_b, q_b), tiles chosen by the autotuner.  The CPU baseline leg runs the oracle on the
+    smallest, the median and the largest block (timed) and states the error of the GPU's s_b and
+    q_b against it.  Prints one JSON line (not the headline line)."""
     import numpy as np
     import torch
     import paper_2102_06827_gb300 as comet
     import synth
     sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from batched_data import EXPR as TEXPR, LABELS, Blocks
+    from batched_data import EXPR as TEXPR, LABELS, Blocks, shapes
     ext = synth.triples_blocks(4096)
     peaks = measured_peaks() or {}
     fp64_peak = measure_fp64_peak()
+    fl = 2.0 * np.prod(ext, axis=1)
+    order = np.argsort(fl, kind="stable")
+    check = [int(order[0]), int(order[len(order) // 2]), int(order[-1])]
     out = {"workload": "batched triples: 4096 blocks, extents uniform 8..32 (seed 3), normal(0,0.1)",
-           "flops": float(np.sum(2.0 * np.prod(ext, axis=1)))}
+           "flops": float(np.sum(fl))}
     for prec, dtype, dt, steps in (("split_bf16", np.float32, "f32", a.steps), ("native", np.float64, "f64", 1)):
-        blocks = Blocks(ext, dtype)
+        blocks = Blocks(ext, dtype, exact_blocks=check)
         plan = comet.BatchedPlan(TEXPR, LABELS, ext, dt, precision=prec)
         ws = plan.workspace()
         plan.prepare(ws)
@@ -220,24 +225,72 @@ def run_triples(a) -> int:
             plan.contract(blocks.ptrs, res, ws, mode=0, key=1, stream=s)
         g.replay()
         torch.cuda.synchronize()
+        clocks = ClockSampler(0)
+        clocks.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(steps):
             g.replay()
         e1.record()
         torch.cuda.synchronize()
+        ck = clocks.stop()
         comet.sync_status()
         t = e0.elapsed_time(e1) / steps
         gf = plan.flops / (t * 1e-3) / 1e9
+        info = plan.describe()
         entry = {"ms_per_step": t, "gflops": gf, "steps": steps, "tile_times_ms": ms, "tile_cfg": best,
-                 "tile": plan.describe()["tile"], "graph": True}
+                 "tile": info["tile"], "kernel": info.get("kernel"), "graph": True, "clocks": ck}
+        # kernel-only times (eager launches, library profiler)
+        comet.profile_enable(True)
+        comet.profile_read()
+        n_prof = 2 if prec == "split_bf16" else 1
+        for _ in range(n_prof):
+            plan.contract(blocks.ptrs, res, ws, mode=0, key=1)
+        torch.cuda.synchronize()
+        prof = {k: (n, t_ms / n_prof) for k, (n, t_ms) in comet.profile_read().items()}
+        comet.profile_enable(False)
+        entry["kernels_ms"] = prof
         if prec == "split_bf16":
-            entry["bf16_mma_tflops"] = 6 * plan.flops / (t * 1e-3) / 1e12
-            entry["frac_of_bf16_peak"] = entry["bf16_mma_tflops"] / peaks.get("bf16_tflops", 1900.0)
+            k_ms = prof.get("batched_split", (1, t))[1]
+            tile = info["tile"]
+            # MMA work the kernel issues: K in chunks of 16, M in 128-row tiles, N in strips
+            issued = sum(6 * 2.0 * (-(-int(r[3] * r[0] * r[1]) // tile[0]) * tile[0]) *
+                         (-(-int(r[2] * r[4] * r[5]) // tile[1]) * tile[1]) * (-(-int(r[6]) // 16) * 16) for r in ext)
+            achieved = 6 * plan.flops / (k_ms * 1e-3) / 1e12
+            peak = peaks.get("bf16_tflops", 1900.0)
+            entry["roofline"] = {"kernel": "batched_split (tcgen05)", "bound": "tensor", "achieved": achieved,
+                                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                                 "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)",
+                                 "achieved_counts": "6 BF16 products x 2*M*N*K per block, unpadded",
+                                 "issued_mma_tflops": issued / (k_ms * 1e-3) / 1e12,
+                                 "issued_frac": issued / (k_ms * 1e-3) / 1e12 / peak,
+                                 "issued_counts": "6 x 2 x M rounded to 128 x N rounded to the strip x K rounded to 16",
+                                 "ms_per_launch": k_ms}
+            entry["prepass_ms"] = prof.get("batched_prepass", (0, 0.0))[1]
         else:
-            entry["roofline"] = {"bound": "fp64", "achieved": gf / 1e3, "peak": fp64_peak["tflops"],
-                                 "unit": "TFLOP/s", "frac": gf / 1e3 / fp64_peak["tflops"],
+            k_ms = prof.get("batched_f64", (1, t))[1]
+            entry["roofline"] = {"kernel": "batched_f64", "bound": "fp64", "achieved": plan.flops / (k_ms * 1e-3) / 1e12,
+                                 "peak": fp64_peak["tflops"], "unit": "TFLOP/s",
+                                 "frac": plan.flops / (k_ms * 1e-3) / 1e12 / fp64_peak["tflops"],
                                  "peak_source": "measured: " + fp64_peak["how"] + ", " + fp64_peak["probe"]}
+        # CPU baseline leg: the oracle on three blocks, and the error of the GPU's (s_b, q_b)
+        import oracle
+        got = res.cpu().numpy().reshape(-1, 2)
+        t_cpu, cfl, es, eq = 0.0, 0.0, 0.0, 0.0
+        for b in check:
+            A = blocks.host_operand(b, 0).astype(np.float64)
+            B = blocks.host_operand(b, 1).astype(np.float64)
+            t0 = time.perf_counter()
+            sr, qr = oracle.triples_reduce(A, B, 1, b)
+            t_cpu += time.perf_counter() - t0
+            cfl += fl[b]
+            n_el = float(np.prod(shapes(ext[b])[2]))
+            eq = max(eq, abs(got[b, 1] - qr) / qr)
+            es = max(es, abs(got[b, 0] - sr) / np.sqrt(qr * n_el))
+        entry["cpu_baseline"] = {"value": cfl / t_cpu / 1e9, "unit": "GFLOP/s", "cores": oracle.threads(),
+                                 "kind": "oracle", "sample": f"blocks {check} (smallest, median, largest), s_b and q_b"}
+        entry["error"] = {"q_rel": eq, "s_rel_to_sqrt_qn": es, "blocks": check,
+                          "tolerance": 1e-6 if prec == "split_bf16" else 1e-12}
         out[prec] = entry
         del blocks, ws, res, g
         torch.cuda.empty_cache()
@@ -256,21 +309,26 @@ def run_triples(a) -> int:
     table = torch.tensor(offs * 4, dtype=torch.int64, device="cuda") + obuf.data_ptr()
     plan.contract(blocks.ptrs, table, ws, mode=1)
     torch.cuda.synchronize()
+    comet.profile_enable(True)
+    comet.profile_read()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(2):
         plan.contract(blocks.ptrs, table, ws, mode=1)
     e1.record()
     torch.cuda.synchronize()
+    prof = comet.profile_read()
+    comet.profile_enable(False)
     comet.sync_status()
     t = e0.elapsed_time(e1) / 2
+    k_ms = prof.get("batched_split", (2, 2 * t))[1] / 2
     wbytes = float(elems[:n_s].sum()) * 4
     hbm = (peaks or {}).get("hbm_gbs", 6792.1)
-    out["store_split_bf16"] = {"blocks": n_s, "ms_per_launch": t, "output_bytes": wbytes,
+    out["store_split_bf16"] = {"blocks": n_s, "ms_per_launch": t, "kernel_ms": k_ms, "output_bytes": wbytes,
                                "gflops": plan.flops / (t * 1e-3) / 1e9,
-                               "roofline": {"bound": "hbm", "achieved": wbytes / (t * 1e-3) / 1e9,
+                               "roofline": {"bound": "hbm", "achieved": wbytes / (k_ms * 1e-3) / 1e9,
                                             "peak": hbm, "unit": "GB/s",
-                                            "frac": wbytes / (t * 1e-3) / 1e9 / hbm,
+                                            "frac": wbytes / (k_ms * 1e-3) / 1e9 / hbm,
                                             "algorithmic_bytes": "4 B per output element written"}}
     del blocks, ws, obuf, table
     torch.cuda.empty_cache()

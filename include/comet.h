@@ -371,13 +371,18 @@ comet_status_t comet_batched_prepare(comet_plan_t plan, void *workspace, void *s
  *   block_inputs   device array of n_blocks * 2 device pointers (block-major: A_b, B_b),
  *                  each a dense column-major operand of that block's extents.
  *   mode 0 (reduce): `result` is a device array of 2*n_blocks doubles; block b gets
- *                  s_b = sum T*W and q_b = sum T^2 over its output T, with the weight W of the
- *                  element with column-major linear index n given by
- *                  h = fmix32(weight_key ^ fmix32(b * 0x9E3779B9 + n)) (MurmurHash3
- *                  finalizer), W = (h >> 8) * 2^-23 - 1.  T is never stored.
+ *                  s_b = sum T*W and q_b = sum T^2 over its output T.  The weight of an
+ *                  element is W = h(weight_key, b, oA) * h(~weight_key, b, oB), where the
+ *                  element's column-major linear index in T is oA + oB, oA the part that the
+ *                  labels of the expression's first operand contribute and oB that of the
+ *                  second operand's labels, and h(k, b, x) = (fmix32(k ^ fmix32(b *
+ *                  0x9E3779B9 + x)) >> 8) * 2^-23 - 1 (MurmurHash3 finalizer, 32-bit
+ *                  wraparound).  T is never stored.
  *   mode 1 (store):  `result` is a device array of n_blocks device pointers; block b's output
  *                  is written there in full (blocks whose pointer is NULL are skipped).
  *   The launch resets its own work counter and, in mode 0, zeroes `result` first.
+ *   Split precision runs on the tcgen05 tensor cores (blocks of K <= 1024); its waits are
+ *   bounded by opts.timeout_ms (COMET_ERR_TIMEOUT at comet_sync_status() when one runs out).
  */
 comet_status_t comet_contract_batched(comet_plan_t plan, const void *const *block_inputs,
                                       int mode, void *result, uint32_t weight_key,
@@ -401,7 +406,8 @@ comet_status_t comet_batched_autotune(comet_plan_t plan, const void *const *bloc
  * capture).  comet_profile_read() synchronises on the recorded events and returns, per kernel
  * kind, the number of launches and their summed device time, then clears the record.
  *   kind names: "transpose", "scale_copy", "split_prepass", "gemm_split_bf16", "gemm_f64",
- *               "batched_f64", "batched_split"
+ *               "batched_f64", "batched_split" (the tcgen05 kernel), "batched_prepass" (its
+ *               abs-max and split passes), "gemm_emu_bf16x6", "gemv", "triples_energy"
  */
 typedef struct {
     char name[32];

@@ -62,8 +62,8 @@ def lib():
                                             ctypes.c_uint32, ctypes.c_uint32,
                                             ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_double)]
-        L.oracle_triples_weight.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
-        L.oracle_triples_weight.restype = ctypes.c_double
+        L.oracle_triples_factor.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
+        L.oracle_triples_factor.restype = ctypes.c_double
         L.oracle_threads.restype = ctypes.c_int
         L.oracle_fmix32.argtypes = [ctypes.c_uint32]
         L.oracle_fmix32.restype = ctypes.c_uint32
@@ -240,12 +240,15 @@ def fmix32(h: int) -> int:
     return lib().oracle_fmix32(h)
 
 
-def triples_weight(key: int, block: int, lin: int) -> float:
-    return lib().oracle_triples_weight(key, block, lin)
+def triples_factor(key: int, block: int, x: int) -> float:
+    """h(key, block, x) = (fmix32(key ^ fmix32(block * 0x9E3779B9 + x)) >> 8) * 2^-23 - 1."""
+    return lib().oracle_triples_factor(key & 0xFFFFFFFF, block, x & 0xFFFFFFFF)
 
 
 def triples_reduce(A: np.ndarray, B: np.ndarray, key: int, block: int):
-    """(s, q) for T[a,b,c,i,j,k] = sum_d A[d,a,b,i] * B[c,d,j,k]:  s = sum T*W, q = sum T^2."""
+    """(s, q) for T[a,b,c,i,j,k] = sum_d A[d,a,b,i] * B[c,d,j,k]:  s = sum T*W, q = sum T^2,
+    W = h(key, block, oA) * h(~key, block, oB) with oA (oB) the part of the element's
+    column-major linear index that A's labels a, b, i (B's labels c, j, k) contribute."""
     A = np.asfortranarray(A, dtype=np.float64)
     B = np.asfortranarray(B, dtype=np.float64)
     d, a, b, i = A.shape

@@ -188,18 +188,22 @@ static uint32_t or_fmix32(uint32_t h) {
 
 uint32_t oracle_fmix32(uint32_t h) { return or_fmix32(h); }
 
-/* Weight of element `lin` of triples block `block` under key `key`: a value in [-1, 1),
- * W = (fmix32(key ^ fmix32(block * 0x9E3779B9 + lin)) >> 8) * 2^-23 - 1. */
-double oracle_triples_weight(uint32_t key, uint32_t block, uint32_t lin) {
-    uint32_t h = or_fmix32(key ^ or_fmix32(block * 0x9E3779B9u + lin));
+/* One factor of the triples weight: a value in [-1, 1),
+ *   h(k, b, x) = (fmix32(k ^ fmix32(b * 0x9E3779B9 + x)) >> 8) * 2^-23 - 1
+ * (32-bit unsigned arithmetic with wraparound). */
+double oracle_triples_factor(uint32_t key, uint32_t block, uint32_t x) {
+    uint32_t h = or_fmix32(key ^ or_fmix32(block * 0x9E3779B9u + x));
     return (double)(h >> 8) * (1.0 / 8388608.0) - 1.0;
 }
 
 /* Reduction of one triples block  T[a,b,c,i,j,k] = sum_d A[d,a,b,i] * B[c,d,j,k]  without
- * storing T: s = sum T * W(lin), q = sum T^2, with lin the column-major linear index of
- * (a,b,c,i,j,k).  ext = {a, b, c, i, j, k, d} extents.  Each element of T is summed over d
- * in order; the partial sums of s and q run over fixed chunks of 4096 elements and the chunk
- * sums are added in order, so the result does not depend on the thread count. */
+ * storing T: s = sum T * W, q = sum T^2.  The weight of element (a,b,c,i,j,k) is the product
+ *   W = h(key, block, oA) * h(~key, block, oB)
+ * where lin = oA + oB is its column-major linear index in T, oA the part the labels of the
+ * first operand (a, b, i) contribute and oB the part of the second operand's labels (c, j, k).
+ * ext = {a, b, c, i, j, k, d} extents.  Each element of T is summed over d in order; the
+ * partial sums of s and q run over fixed chunks of 4096 elements and the chunk sums are added
+ * in order, so the result does not depend on the thread count. */
 int oracle_triples_reduce(const int64_t *ext, const double *A, const double *B,
                           uint32_t key, uint32_t block, double *s_out, double *q_out)
 {
@@ -211,6 +215,8 @@ int oracle_triples_reduce(const int64_t *ext, const double *A, const double *B,
     double *ps = (double *)malloc(sizeof(double) * (size_t)(n_ch ? n_ch : 1));
     double *pq = (double *)malloc(sizeof(double) * (size_t)(n_ch ? n_ch : 1));
     if (!ps || !pq) { free(ps); free(pq); return -3; }
+    /* column-major strides of T[a,b,c,i,j,k] */
+    const int64_t st_b = ea, st_c = ea * eb, st_i = ea * eb * ec, st_j = st_i * ei, st_k = st_j * ej;
     #pragma omp parallel for schedule(static)
     for (int64_t c = 0; c < n_ch; ++c) {
         double s = 0.0, q = 0.0;
@@ -229,7 +235,11 @@ int oracle_triples_reduce(const int64_t *ext, const double *A, const double *B,
                 double bv = B[cc + ec * (d + ed * (j + ej * k))];     /* B[c,d,j,k] */
                 t += av * bv;
             }
-            s += t * oracle_triples_weight(key, block, (uint32_t)lin);
+            const int64_t oA = a + st_b * b + st_i * i;
+            const int64_t oB = st_c * cc + st_j * j + st_k * k;
+            const double w = oracle_triples_factor(key, block, (uint32_t)oA) *
+                             oracle_triples_factor(~key, block, (uint32_t)oB);
+            s += t * w;
             q += t * t;
         }
         ps[c] = s;

@@ -191,7 +191,8 @@ class BatchedPlan:
     extents      integer array n_blocks x n_labels
     """
 
-    def __init__(self, expr: str, label_names, extents, dtype, precision="native", tile: int = -1):
+    def __init__(self, expr: str, label_names, extents, dtype, precision="native", tile: int = -1,
+                 timeout_ms: int = 0, debug_flags: int = 0):
         import numpy as np
         L = lib()
         self.expr = expr
@@ -204,6 +205,8 @@ class BatchedPlan:
         opts = _lib.PlanOpts()
         L.comet_plan_opts_default(ctypes.byref(opts))
         opts.precision = _prec_code(precision)
+        opts.timeout_ms = timeout_ms
+        opts.debug_flags = debug_flags
         h = ctypes.c_void_p()
         _lib.check(L.comet_plan_batched(expr.encode(), self.n_blocks, names, n_labels,
                                         ext.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), dts, 3,

@@ -43,9 +43,9 @@ int *device_status_word() {
 // ---- kernel timing ------------------------------------------------------------------------
 static const char *kKindNames[] = {"transpose", "scale_copy", "split_prepass", "gemm_split_bf16",
                                    "gemm_f64", "batched_f64", "batched_split", "gemm_emu_bf16x6", "gemv",
-                                   "triples_energy"};
+                                   "triples_energy", "batched_prepass"};
 enum { PK_TRANSPOSE = 0, PK_SCALE, PK_PREPASS, PK_SPLIT, PK_F64, PK_BATCHED_F64, PK_BATCHED_SPLIT, PK_EMU,
-       PK_GEMV, PK_TRIPLES, PK_N };
+       PK_GEMV, PK_TRIPLES, PK_BATCHED_PREPASS, PK_N };
 
 struct ProfRec {
     int kind;

@@ -1,0 +1,540 @@
+// Batched split-BF16 contractions on the tcgen05 tensor cores: one persistent launch over many
+// small, uneven blocks of one two-operand expression (the 6-D triples outputs of the CCSD(T)
+// remark in Section 2, T[a,b,c,i,j,k] = sum_d A[d,a,b,i] * B[c,d,j,k]; every block is the GEMM
+// of its TTGT view with the permutations folded into the index arithmetic).
+//
+// Operands.  A pre-pass splits each block operand once into the fixed-point bfloat16 parts
+// hi, mid, lo (split.cuh) and writes them in "plane rows" of 16 K values (32 bytes): operand X
+// occupies nk16 chunks x 3 planes x rows_pad rows, [chunk][plane][row], zero beyond its rows
+// and its K.  All blocks' planes form one array, so ONE two-dimensional tensor map serves every
+// block: a 128-row box at row (block base + (chunk*3 + plane)*rows_pad + r0) is a 32-byte
+// swizzled K-major operand tile of the MMA.  Zero padding rows make out-of-range outputs
+// exactly zero, so the reduction needs no masks.
+//
+// Work items are (block, strip of BN output columns), blocks longest first, dealt to the
+// persistent CTAs round robin.  A block with K <= 32 keeps its strip's B tile (all K chunks
+// and planes, BN rows) resident in shared memory while its M tiles stream through a ring;
+// larger K streams the B chunks beside the A chunks.
+//
+// Roles (320 threads, one CTA per SM):
+//   warp 0      TMA producer (one elected lane)
+//   warp 1      tensor memory allocation; one lane issues tcgen05.mma (M=128, N=BN or 128,
+//               K=16, bf16 in, FP32 accumulate) and tcgen05.commit
+//   warps 2..9  epilogue: warp w owns tensor-memory lanes 32*(w%4).. (rows) and half the
+//               columns; drains a tile with tcgen05.ld while the MMA fills the next buffer
+//
+// Numerics.  Six part products per K chunk (hh, hm, mh, hl, lh, mm; ml, lm, ll dropped, as
+// in the large split GEMM).  Blocks of this plan with K <= 32 (at most two hh MMAs per tile)
+// share one accumulator: the correction products are accumulated first and the hh products
+// last, so the accumulator's truncating FP32 additions cost at most one unit in the last
+// place of the running sum per hh MMA.  A plan with any K > 32 keeps the hh products in an
+// accumulator of their own (P0, exact for K <= 1024) and the corrections in P1.
+//
+// Epilogue.  Reduce mode: per thread (one output row m) sum_n T[m,n] v[n] and sum_n T^2 with
+// packed FP32x2 FMAs, v[n] the column factor of the weight (triples_weight.cuh) formed once per
+// strip; the row factor u[m] multiplies the row's sum; per-tile sums are added with a
+// compensated (two-sum) FP32 accumulation, per-item totals in FP64 with one atomic pair per
+// warp.  Store mode: alpha 2^(eA+eB) T through the output's strides.
+//
+// Every wait is bounded (%globaltimer); on expiry the CTA records COMET_ERR_TIMEOUT in the
+// status word, waits (bounded) for its own copies in flight, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+#include <stdint.h>
+
+#include "../../include/comet.h"
+#include "batched.h"
+#include "params.h"
+#include "sm100.cuh"
+#include "split.cuh"
+#include "triples_weight.cuh"
+
+namespace comet {
+
+
+namespace {
+
+__device__ __forceinline__ uint64_t pack2(uint32_t lo, uint32_t hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1,%2};" : "=l"(r) : "r"(lo), "r"(hi));
+    return r;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ float lo_f(uint64_t x) { return __uint_as_float((uint32_t)x); }
+__device__ __forceinline__ float hi_f(uint64_t x) { return __uint_as_float((uint32_t)(x >> 32)); }
+
+// sum += x with the rounding error of the addition collected in comp (Knuth's two-sum)
+__device__ __forceinline__ void two_sum_add(float &sum, float &comp, float x) {
+    const float t = sum + x;
+    const float z = t - sum;
+    comp += (sum - (t - z)) + (x - z);
+    sum = t;
+}
+
+// block of work item `it`: prefix[pos] <= it < prefix[pos + 1]
+__device__ __forceinline__ uint32_t find_block(const uint32_t *prefix, uint32_t n_blocks, uint32_t it) {
+    uint32_t lo = 0, hi = n_blocks;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (prefix[mid] <= it) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// K-major, 32-byte-swizzled operand tile at shared address `a` (rows 32 bytes apart)
+__device__ __forceinline__ uint64_t tile_desc(uint32_t a) {
+    return sm100::smem_desc(a, 16, btc::SBO, btc::SW32);
+}
+
+}  // namespace
+
+template <int BN, bool DUAL, typename TIn>
+__global__ void __launch_bounds__(btc::THREADS, 1)
+    batched_tc_kernel(const __grid_constant__ CUtensorMap map, const BatchedParams P) {
+    using namespace btc;
+    using namespace sm100;
+    using C = Cfg<BN>;
+    constexpr uint32_t BUF_COLS = DUAL ? 2 * BN : BN;   // P0 (and P1) of one tile
+    constexpr uint32_t NBUF = TMEM_COLS / BUF_COLS;     // accumulator buffers in flight
+    constexpr int HALVES = BN / BOX_ROWS;               // 128-row boxes per strip
+    static_assert(NBUF >= 1 && NBUF <= 4, "tensor-memory buffers");
+
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    uint8_t *smem = smem_raw + (((raw + 1023) & ~1023u) - raw);
+    uint8_t *strip = smem;                                          // 2 x STRIP_BYTES
+    uint8_t *ring = smem + 2 * C::STRIP_BYTES;                      // RING x SLOT_BYTES
+    float *vcol = reinterpret_cast<float *>(ring + RING * SLOT_BYTES);   // BN column factors
+    int64_t *ocol = reinterpret_cast<int64_t *>(vcol + BN);              // BN column offsets
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ocol + BN);
+    uint64_t *ring_full = bars, *ring_empty = bars + RING, *strip_full = bars + 2 * RING,
+             *strip_empty = strip_full + 2, *acc_full = strip_empty + 2, *acc_empty = acc_full + 4,
+             *mma_done = acc_empty + 4;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t tmo = (uint64_t)P.timeout_ns;
+    const uint32_t n_items = P.total_tiles;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < RING; ++s) { mbar_init(&ring_full[s], 1); mbar_init(&ring_empty[s], 1); }
+        for (int s = 0; s < 2; ++s) { mbar_init(&strip_full[s], 1); mbar_init(&strip_empty[s], 1); }
+        for (int s = 0; s < 4; ++s) { mbar_init(&acc_full[s], 1); mbar_init(&acc_empty[s], EPI_WARPS); }
+        mbar_init(mma_done, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+        tma_prefetch_desc(&map);
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    auto fail = [&]() {
+        *abort_flag = 1;
+        atomicExch(P.status, (int)COMET_ERR_TIMEOUT);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            uint32_t rit = 0, sit = 0;
+            bool ok = true, injected = false;
+            // one ring slot: three 128-row plane boxes of chunk kc, rows r0.. of an operand
+            auto load_slot = [&](int64_t row0, uint32_t pad, uint32_t kc, uint32_t r0) -> bool {
+                const uint32_t s = rit % RING, rnd = rit / RING;
+                if (rnd > 0 && !mbar_wait(&ring_empty[s], (rnd - 1) & 1, tmo, abort_flag)) return false;
+                mbar_arrive_expect_tx(&ring_full[s], SLOT_BYTES);
+                ++rit;
+                if ((P.debug_flags & 1) && !injected && blockIdx.x == 0) {
+                    injected = true;   // fault injection: this slot's loads are withheld
+                    return true;
+                }
+                uint8_t *dst = ring + s * SLOT_BYTES;
+                for (uint32_t p = 0; p < 3; ++p)
+                    tma_load_2d(&map, &ring_full[s], dst + p * BOX_BYTES, 0,
+                                (int)(row0 + (int64_t)(kc * 3 + p) * pad + r0));
+                return true;
+            };
+            for (uint32_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+                const uint32_t pos = find_block(P.prefix, P.n_blocks, it);
+                const BlockDesc *d = P.desc + pos;
+                const uint32_t n0 = (it - P.prefix[pos]) * BN;
+                const uint32_t nk = d->nk16, mtiles = (d->M + BM - 1) / BM;
+                const int64_t a0 = d->a_row0, b0 = d->b_row0;
+                const uint32_t mp = d->m_pad, np = d->n_pad;
+                const bool res = nk <= (uint32_t)MAX_RES_NK;
+                if (res) {
+                    const uint32_t sl = sit & 1, rnd = sit >> 1;
+                    if (rnd > 0 && !mbar_wait(&strip_empty[sl], (rnd - 1) & 1, tmo, abort_flag)) {
+                        fail(); ok = false; break;
+                    }
+                    mbar_arrive_expect_tx(&strip_full[sl], nk * 3 * BN * ROW);
+                    ++sit;
+                    uint8_t *dst = strip + sl * C::STRIP_BYTES;
+                    for (uint32_t kc = 0; kc < nk; ++kc)
+                        for (uint32_t p = 0; p < 3; ++p)
+                            for (int h = 0; h < HALVES; ++h)
+                                tma_load_2d(&map, &strip_full[sl], dst + ((kc * 3 + p) * BN + h * BOX_ROWS) * ROW, 0,
+                                            (int)(b0 + (int64_t)(kc * 3 + p) * np + n0 + h * BOX_ROWS));
+                }
+                for (uint32_t mt = 0; mt < mtiles && ok; ++mt)
+                    for (uint32_t kc = 0; kc < nk && ok; ++kc) {
+                        ok = load_slot(a0, mp, kc, mt * BM);
+                        for (int h = 0; h < HALVES && ok && !res; ++h) ok = load_slot(b0, np, kc, n0 + h * BOX_ROWS);
+                    }
+                if (!ok) fail();
+            }
+            // drain: wait (bounded) for every load still in flight before the CTA may exit
+            for (uint32_t j = rit > (uint32_t)RING ? rit - RING : 0; j < rit; ++j)
+                mbar_wait(&ring_full[j % RING], (j / RING) & 1, tmo, nullptr);
+            for (uint32_t j = sit > 2u ? sit - 2 : 0; j < sit; ++j) mbar_wait(&strip_full[j & 1], (j >> 1) & 1, tmo, nullptr);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            constexpr uint32_t idesc_full = idesc_bf16_f32(BM, BN);
+            constexpr uint32_t idesc_half = idesc_bf16_f32(BM, BOX_ROWS);
+            uint32_t rit = 0, sit = 0, tit = 0;
+            bool ok = true;
+            auto wait_slot = [&](uint32_t j) -> bool {
+                return mbar_wait(&ring_full[j % RING], (j / RING) & 1, tmo, abort_flag);
+            };
+            for (uint32_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+                const uint32_t pos = find_block(P.prefix, P.n_blocks, it);
+                const BlockDesc *d = P.desc + pos;
+                const uint32_t nk = d->nk16, mtiles = (d->M + BM - 1) / BM;
+                const bool res = nk <= (uint32_t)MAX_RES_NK;
+                uint32_t sl = 0;
+                if (res) {
+                    sl = sit & 1;
+                    if (!mbar_wait(&strip_full[sl], (sit >> 1) & 1, tmo, abort_flag)) { fail(); ok = false; break; }
+                    tc_fence_after();
+                }
+                const uint32_t sbase = smem_u32(strip + sl * C::STRIP_BYTES);
+                for (uint32_t mt = 0; mt < mtiles && ok; ++mt) {
+                    const uint32_t buf = tit % NBUF, rnd = tit / NBUF;
+                    if (rnd > 0 && !mbar_wait(&acc_empty[buf], (rnd - 1) & 1, tmo, abort_flag)) {
+                        fail(); ok = false; break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d0 = tmem_base + buf * BUF_COLS, d1 = DUAL ? d0 + BN : d0;
+                    if (res) {
+                        for (uint32_t kc = 0; kc < nk && ok; ++kc) ok = wait_slot(rit + kc);
+                        if (!ok) { fail(); break; }
+                        tc_fence_after();
+                        uint64_t ad[MAX_RES_NK][3], bd[MAX_RES_NK][3];
+#pragma unroll
+                        for (int kc = 0; kc < MAX_RES_NK; ++kc) {
+                            const uint32_t sa = smem_u32(ring + ((rit + kc) % RING) * SLOT_BYTES);
+#pragma unroll
+                            for (int p = 0; p < 3; ++p) {
+                                ad[kc][p] = tile_desc(sa + p * BOX_BYTES);
+                                bd[kc][p] = tile_desc(sbase + (kc * 3 + p) * BN * ROW);
+                            }
+                        }
+                        // corrections of every chunk first (smallest first), the hh products last
+#pragma unroll
+                        for (int kc = 0; kc < MAX_RES_NK; ++kc) {
+                            if (kc >= (int)nk) break;
+                            mma_bf16(d1, ad[kc][1], bd[kc][1], idesc_full, kc > 0 ? 1u : 0u);   // mm
+                            mma_bf16(d1, ad[kc][2], bd[kc][0], idesc_full, 1);                 // lh
+                            mma_bf16(d1, ad[kc][0], bd[kc][2], idesc_full, 1);                 // hl
+                            mma_bf16(d1, ad[kc][1], bd[kc][0], idesc_full, 1);                 // mh
+                            mma_bf16(d1, ad[kc][0], bd[kc][1], idesc_full, 1);                 // hm
+                        }
+#pragma unroll
+                        for (int kc = 0; kc < MAX_RES_NK; ++kc) {
+                            if (kc >= (int)nk) break;
+                            mma_bf16(d0, ad[kc][0], bd[kc][0], idesc_full, (DUAL && kc == 0) ? 0u : 1u);   // hh
+                        }
+                        for (uint32_t kc = 0; kc < nk; ++kc) mma_commit(&ring_empty[(rit + kc) % RING]);
+                        rit += nk;
+                    } else {
+                        // K > 32 (dual accumulators): A chunk slot, then the B chunk's HALVES slots
+                        for (uint32_t kc = 0; kc < nk && ok; ++kc) {
+                            for (int q = 0; q <= HALVES && ok; ++q) ok = wait_slot(rit + q);
+                            if (!ok) { fail(); break; }
+                            tc_fence_after();
+                            const uint32_t sa = smem_u32(ring + (rit % RING) * SLOT_BYTES);
+                            const uint64_t a_h = tile_desc(sa), a_m = tile_desc(sa + BOX_BYTES),
+                                           a_l = tile_desc(sa + 2 * BOX_BYTES);
+                            for (int h = 0; h < HALVES; ++h) {
+                                const uint32_t sb = smem_u32(ring + ((rit + 1 + h) % RING) * SLOT_BYTES);
+                                const uint64_t b_h = tile_desc(sb), b_m = tile_desc(sb + BOX_BYTES),
+                                               b_l = tile_desc(sb + 2 * BOX_BYTES);
+                                const uint32_t acc = kc > 0 ? 1u : 0u;
+                                const uint32_t e0 = d0 + h * BOX_ROWS, e1 = d1 + h * BOX_ROWS;
+                                mma_bf16(e1, a_m, b_m, idesc_half, acc);
+                                mma_bf16(e1, a_l, b_h, idesc_half, 1);
+                                mma_bf16(e1, a_h, b_l, idesc_half, 1);
+                                mma_bf16(e1, a_m, b_h, idesc_half, 1);
+                                mma_bf16(e1, a_h, b_m, idesc_half, 1);
+                                mma_bf16(e0, a_h, b_h, idesc_half, acc);
+                            }
+                            for (int q = 0; q <= HALVES; ++q) mma_commit(&ring_empty[(rit + q) % RING]);
+                            rit += 1 + HALVES;
+                        }
+                        if (!ok) break;
+                    }
+                    mma_commit(&acc_full[buf]);   // tile complete: the epilogue may drain it
+                    ++tit;
+                }
+                if (!ok) break;
+                if (res) {
+                    mma_commit(&strip_empty[sl]);   // frees the strip once its MMAs have read it
+                    ++sit;
+                }
+            }
+            // no MMA may still write tensor memory when it is freed
+            mma_commit(mma_done);
+            mbar_wait(mma_done, 0, tmo, nullptr);
+        }
+    } else {
+        // ---------------- epilogue (warps 2..9) ----------------
+        const int quad = warp & 3;                   // tensor-memory lanes 32*quad .. +31
+        const int half = (warp - 2) >> 2;            // columns half*BN/2 .. +BN/2-1
+        const int et = threadIdx.x - 64;             // 0..255
+        const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+        const uint32_t key_m = P.swap ? ~P.key : P.key, key_n = ~key_m;
+        uint32_t tit = 0;
+        bool dead = false;   // once set, the warp keeps pace with the named barriers only
+        for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+            const uint32_t pos = find_block(P.prefix, P.n_blocks, it);
+            const BlockDesc *d = P.desc + pos;
+            const uint32_t M = d->M, N = d->N, idx = d->index, mtiles = (M + BM - 1) / BM;
+            const uint32_t n0 = (it - P.prefix[pos]) * BN;
+            const uint32_t hb = idx * 0x9E3779B9u;
+            const int e_sum = P.exps[2 * idx] + P.exps[2 * idx + 1];
+            // the strip's column offsets and weight factors (all eight warps meet here)
+            named_bar_sync(1, 32 * EPI_WARPS);
+            for (int n = et; n < BN; n += 32 * EPI_WARPS) {
+                int64_t o0 = 0, o1 = 0;
+                const bool nv = n0 + n < N;
+                if (nv) radix_offsets(d->nb, n0 + n, o0, o1);
+                ocol[n] = o1;
+                vcol[n] = nv ? tri_factor(key_n, hb, (uint32_t)o1) : 0.0f;
+            }
+            named_bar_sync(1, 32 * EPI_WARPS);
+            float S = 0.0f, cS = 0.0f, Q = 0.0f, cQ = 0.0f;
+            TIn *out = P.mode == 1 ? reinterpret_cast<TIn *const *>(P.result)[idx] : nullptr;
+            const double scale = ldexp(P.alpha, e_sum);
+            for (uint32_t mt = 0; mt < mtiles; ++mt, ++tit) {
+                const uint32_t buf = tit % NBUF, rnd = tit / NBUF;
+                if (dead) continue;
+                bool ok = mbar_wait(&acc_full[buf], rnd & 1, tmo, abort_flag);
+                ok = __all_sync(0xffffffffu, ok);   // warp-uniform before the .sync.aligned loads
+                if (!ok) { if (lane == 0) fail(); dead = true; continue; }
+                tc_fence_after();
+                const uint32_t m = mt * BM + quad * 32 + lane;
+                const bool mv = m < M;
+                int64_t r0 = 0, orow = 0;
+                if (mv) radix_offsets(d->ma, m, r0, orow);
+                const uint32_t taddr = tmem_base + lane_base + buf * BUF_COLS + half * (BN / 2);
+                if (P.mode == 0) {
+                    uint64_t ps = 0, pq = 0;   // two FP32 lanes each
+#pragma unroll
+                    for (int c = 0; c < BN / 2; c += 32) {
+                        uint32_t r[32], r1[DUAL ? 32 : 1];
+                        tmem_ld32(taddr + c, r);
+                        if constexpr (DUAL) tmem_ld32(taddr + BN + c, r1);
+                        tmem_ld_wait();
+                        if (c + 32 >= BN / 2) {   // every value of the tile is in registers
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&acc_empty[buf]);
+                        }
+                        const uint64_t *v2 = reinterpret_cast<const uint64_t *>(vcol + half * (BN / 2) + c);
+#pragma unroll
+                        for (int j = 0; j < 32; j += 2) {
+                            uint64_t t = pack2(r[j], r[j + 1]);
+                            if constexpr (DUAL) t = add2(t, pack2(r1[j], r1[j + 1]));   // P0 + P1
+                            ps = fma2(t, v2[j >> 1], ps);
+                            pq = fma2(t, t, pq);
+                        }
+                    }
+                    if (mv) {
+                        two_sum_add(S, cS, (lo_f(ps) + hi_f(ps)) * tri_factor(key_m, hb, (uint32_t)orow));
+                        two_sum_add(Q, cQ, lo_f(pq) + hi_f(pq));
+                    }
+                } else {
+#pragma unroll 1
+                    for (int c = 0; c < BN / 2; c += 32) {
+                        uint32_t r[32];
+                        tmem_ld32(taddr + c, r);
+                        if constexpr (DUAL) {
+                            uint32_t r1[32];
+                            tmem_ld32(taddr + BN + c, r1);
+                            tmem_ld_wait();
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(r1[j]));
+                        } else {
+                            tmem_ld_wait();
+                        }
+                        if (c + 32 >= BN / 2) {
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&acc_empty[buf]);
+                        }
+                        if (mv && out) {
+                            TIn *row = out + orow;
+                            const TIn sc = (TIn)scale;
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                const int n = half * (BN / 2) + c + j;
+                                if (n0 + n < N) row[ocol[n]] = sc * (TIn)__uint_as_float(r[j]);
+                            }
+                        }
+                    }
+                }
+            }
+            if (P.mode == 0 && !dead) {
+                double s = (double)S + (double)cS, q = (double)Q + (double)cQ;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    s += __shfl_down_sync(0xffffffffu, s, o);
+                    q += __shfl_down_sync(0xffffffffu, q, o);
+                }
+                if (lane == 0) {
+                    double *res = reinterpret_cast<double *>(P.result);
+                    atomicAdd(res + 2 * idx, s * scale);
+                    atomicAdd(res + 2 * idx + 1, q * scale * scale);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem_base, TMEM_COLS);
+}
+
+// Split pre-pass: CTA c writes operand c%2 of block c/2 (launch order) as plane rows
+// [chunk][plane][row] of 16 K values, rows to the operand's padded row count, scaled by the
+// block's exponent; one thread per row, 32 bytes per store group (coalesced across the warp).
+template <typename TIn>
+__global__ void __launch_bounds__(256) batched_presplit_tc_kernel(const BatchedParams P) {
+    __shared__ int64_t k_off[1024];
+    const BlockDesc &d = P.desc[blockIdx.x >> 1];
+    const int op = blockIdx.x & 1;
+    const Radix &rr = op ? d.nb : d.ma;
+    const uint32_t rows = op ? d.N : d.M, pad = op ? d.n_pad : d.m_pad, K = d.K, nk = d.nk16;
+    const TIn *x = reinterpret_cast<const TIn *>(P.inputs[2 * d.index + (op ^ P.swap)]);
+    const int e = P.exps[2 * d.index + op];
+    uint4 *base = reinterpret_cast<uint4 *>(P.planes + (op ? d.b_row0 : d.a_row0) * kBatchedPlaneRow);
+    for (uint32_t k = threadIdx.x; k < nk * 16; k += 256) {
+        int64_t o0 = 0, o1 = 0;
+        if (k < K) radix_offsets(d.k, k, o0, o1);
+        k_off[k] = op ? o1 : o0;
+    }
+    __syncthreads();
+    for (uint32_t r = threadIdx.x; r < pad; r += 256) {
+        int64_t ro = 0, o1 = 0;
+        const bool valid = r < rows;
+        if (valid) radix_offsets(rr, r, ro, o1);
+        for (uint32_t kc = 0; kc < nk; ++kc) {
+            uint32_t w[3][8];
+#pragma unroll
+            for (int j = 0; j < 16; j += 2) {
+                __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+                const uint32_t k = kc * 16 + j;
+                const TIn v0 = (valid && k < K) ? x[ro + k_off[k]] : (TIn)0;
+                const TIn v1 = (valid && k + 1 < K) ? x[ro + k_off[k + 1]] : (TIn)0;
+                split3<TIn>(v0, e, h0, m0, l0);
+                split3<TIn>(v1, e, h1, m1, l1);
+                w[0][j >> 1] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                w[1][j >> 1] = (uint32_t)__bfloat16_as_ushort(m0) | ((uint32_t)__bfloat16_as_ushort(m1) << 16);
+                w[2][j >> 1] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            }
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                uint4 *dst = base + ((size_t)(kc * 3 + p) * pad + r) * 2;
+                dst[0] = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+                dst[1] = make_uint4(w[p][4], w[p][5], w[p][6], w[p][7]);
+            }
+        }
+    }
+}
+
+// ---- host side --------------------------------------------------------------------------------
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        cudaDriverEntryPointQueryResult q;
+        void *f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }
+    return fn;
+}
+
+cudaError_t launch_batched_presplit(const BatchedParams &bp, int n_blocks, bool f64_in, cudaStream_t s) {
+    if (n_blocks <= 0) return cudaSuccess;
+    if (f64_in) batched_presplit_tc_kernel<double><<<2 * n_blocks, 256, 0, s>>>(bp);
+    else batched_presplit_tc_kernel<float><<<2 * n_blocks, 256, 0, s>>>(bp);
+    return cudaGetLastError();
+}
+
+template <int BN, bool DUAL, typename TIn>
+static void launch_tc(const CUtensorMap &m, const BatchedParams &bp, int ctas, cudaStream_t s) {
+    static const bool attr = [] {
+        cudaFuncSetAttribute(batched_tc_kernel<BN, DUAL, TIn>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             btc::Cfg<BN>::SMEM);
+        return true;
+    }();
+    (void)attr;
+    batched_tc_kernel<BN, DUAL, TIn><<<ctas, btc::THREADS, btc::Cfg<BN>::SMEM, s>>>(m, bp);
+}
+
+cudaError_t launch_batched_tc(const BatchedParams &bp, int64_t plane_rows, int strip, bool dual, bool f64_in,
+                              cudaStream_t s) {
+    if (bp.total_tiles == 0) return cudaSuccess;
+    auto enc = encode_fn();
+    if (!enc || plane_rows <= 0 || plane_rows >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
+    // one map over every block's plane rows: 16 bf16 per row, 128-row boxes, 32-byte swizzle
+    CUtensorMap m;
+    cuuint64_t dims[2] = {16, (cuuint64_t)plane_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kBatchedPlaneRow};
+    cuuint32_t box[2] = {16, (cuuint32_t)btc::BOX_ROWS};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, bp.planes, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int ctas = (int)std::min<uint32_t>(bp.total_tiles, (uint32_t)std::max(1, sms));
+#define CM_TC(BNv, DUALv)                                                            \
+    do {                                                                             \
+        if (f64_in) launch_tc<BNv, DUALv, double>(m, bp, ctas, s);                   \
+        else launch_tc<BNv, DUALv, float>(m, bp, ctas, s);                           \
+    } while (0)
+    if (strip == 256) {
+        if (dual) CM_TC(256, true); else CM_TC(256, false);
+    } else {
+        if (dual) CM_TC(128, true); else CM_TC(128, false);
+    }
+#undef CM_TC
+    return cudaGetLastError();
+}
+
+}  // namespace comet

@@ -165,6 +165,8 @@ struct Plan {
     std::vector<std::vector<uint32_t>> batched_prefix;   // per tile configuration
     std::vector<double> block_flops;
     bool batched_ak = false, batched_bk = false, batched_swap = false;
+    bool batched_dual = false;            // split path: some block has K > 32 (hh kept apart)
+    int64_t batched_plane_rows = 0;       // split path: rows of 16 bf16 in the plane region
     HostPipe pipe;                        // comet_contract_host slicing (one-step plans)
     bool triples = false;                 // comet_plan_triples
     TriplesPlan tri;

@@ -1,6 +1,10 @@
 """GPU parity of the batched triples path (one persistent launch over many uneven blocks)
 against the oracle: stored blocks elementwise, reduced blocks through s_b = sum T*W and
-q_b = sum T^2; every tile configuration; CUDA-graph replay; the autotuner."""
+q_b = sum T^2; every tile configuration, both accumulator layouts of the tensor-core split
+kernel (one accumulator for K <= 32, the hh products apart when some K > 32); the full-size
+workload on its smallest, middle and largest blocks; a withheld load (bounded waits);
+CUDA-graph replay; the autotuner.  Split tolerance 1e-6 (normwise per block, and relative on
+q_b), FP64 1e-12."""
 import numpy as np
 import pytest
 
@@ -57,45 +61,91 @@ def _check_reduce(blocks, got, b, tol):
     assert abs(got[b, 0] - s) <= tol * np.sqrt(q * n), (b, got[b, 0], s)
 
 
+# uneven blocks: degenerate extents, K from 1 to 40 (K > 32 streams the B chunks and keeps the
+# hh products in an accumulator of their own), strips with ragged column tails, M below 128
 SMALL = np.array([[2, 3, 1, 4, 2, 3, 5], [7, 1, 2, 3, 5, 2, 1], [3, 3, 3, 3, 3, 3, 3], [1, 1, 1, 1, 1, 1, 1],
-                  [9, 8, 7, 6, 5, 4, 33], [5, 6, 2, 7, 3, 4, 40], [16, 5, 9, 2, 3, 11, 6], [4, 4, 4, 8, 8, 8, 2]])
+                  [9, 8, 7, 6, 5, 4, 33], [5, 6, 2, 7, 3, 4, 40], [16, 5, 9, 2, 3, 11, 6], [4, 4, 4, 8, 8, 8, 2],
+                  [20, 13, 11, 3, 17, 2, 16], [1, 2, 31, 1, 9, 1, 17]])
+# the same blocks with K <= 32: the tile's correction and hh products share one accumulator
+SMALL_K32 = np.concatenate([SMALL[:, :6], np.minimum(SMALL[:, 6:], 32)], axis=1)
 
 
+@pytest.mark.parametrize("table", ["k_to_40", "k_to_32"])
 @pytest.mark.parametrize("prec,dtype,tol", [("native", np.float64, 1e-12), ("native", np.float32, 1e-12),
                                             ("split_bf16", np.float32, 1e-6), ("split_bf16", np.float64, 1e-6)])
-def test_small_uneven_blocks_every_tile(comet, prec, dtype, tol):
-    blocks = Blocks(SMALL, dtype, exact_blocks=range(len(SMALL)))
-    plan = comet.BatchedPlan(EXPR, LABELS, SMALL, "f32" if dtype == np.float32 else "f64", precision=prec)
+def test_small_uneven_blocks_every_tile(comet, prec, dtype, tol, table):
+    ext = SMALL if table == "k_to_40" else SMALL_K32
+    if prec == "native" and table == "k_to_32":
+        pytest.skip("the FP64 kernel has one accumulator layout")
+    blocks = Blocks(ext, dtype, exact_blocks=range(len(ext)))
+    plan = comet.BatchedPlan(EXPR, LABELS, ext, "f32" if dtype == np.float32 else "f64", precision=prec)
+    if prec == "split_bf16":
+        assert plan.describe()["kernel"] == "tcgen05"
+        assert plan.describe()["dual_accumulators"] == (1 if table == "k_to_40" else 0)
     for cfg in range(plan.num_tiles()):
         plan.set_tile(cfg)
-        outs = _store(comet, plan, blocks, range(len(SMALL)))
+        outs = _store(comet, plan, blocks, range(len(ext)))
         for b, T in outs.items():
             A = blocks.host_operand(b, 0).astype(np.float64)
             B = blocks.host_operand(b, 1).astype(np.float64)
             ref = oracle.einsum(EXPR, A, B)
             err = np.abs(T - ref).max() / max(np.abs(ref).max(), 1e-300)
-            # an FP32 output adds its own rounding (2^-24) to whatever path computed it
-            limit = tol if dtype == np.float64 else (2.0 ** -23 if prec == "native" else 2e-6)
+            # an FP32 output of the FP64 path adds its own rounding (2^-24)
+            limit = 2.0 ** -23 if (prec == "native" and dtype == np.float32) else tol
             assert err <= limit, (cfg, b, err)
         got = _reduce(comet, plan, blocks)
-        for b in range(len(SMALL)):
-            _check_reduce(blocks, got, b, max(tol, 1e-13) * (1 if prec == "native" else 4))
+        for b in range(len(ext)):
+            _check_reduce(blocks, got, b, tol)
 
 
 def test_full_size_triples_sampled(comet):
-    # 4096 blocks, every extent uniform in 8..32, normal(0, 0.1); a seeded subset checked
+    # 4096 blocks, every extent uniform in 8..32, normal(0, 0.1); the two smallest, the
+    # quartiles and the two largest blocks checked against the oracle, the largest one also
+    # stored and compared element by element
+    import torch
     ext = synth.triples_blocks(4096)
     fl = 2.0 * np.prod(ext, axis=1)
-    order = np.argsort(fl)
-    pick = sorted({int(order[0]), int(order[1]), int(order[len(order) // 4]), int(order[len(order) // 2])})
-    for prec, dtype, dt, tol in (("split_bf16", np.float32, "f32", 4e-6), ("native", np.float64, "f64", 1e-12)):
+    order = np.argsort(fl, kind="stable")
+    n = len(order)
+    pick = sorted({int(order[0]), int(order[1]), int(order[n // 4]), int(order[n // 2]), int(order[3 * n // 4]),
+                   int(order[-2]), int(order[-1])})
+    largest = int(order[-1])
+    for prec, dtype, dt, tol in (("split_bf16", np.float32, "f32", 1e-6), ("native", np.float64, "f64", 1e-12)):
         blocks = Blocks(ext, dtype, exact_blocks=pick)
         plan = comet.BatchedPlan(EXPR, LABELS, ext, dt, precision=prec)
         got = _reduce(comet, plan, blocks)
         assert np.all(got[:, 1] > 0)
         for b in pick:
             _check_reduce(blocks, got, b, tol)
+        if prec == "split_bf16":
+            T = _store(comet, plan, blocks, [largest])[largest]
+            A = blocks.host_operand(largest, 0).astype(np.float64)
+            B = blocks.host_operand(largest, 1).astype(np.float64)
+            ref = oracle.einsum(EXPR, A, B)
+            assert np.abs(T - ref).max() / np.abs(ref).max() <= tol
+            del T, ref
         del blocks
+        torch.cuda.empty_cache()
+
+
+def test_withheld_load_times_out_and_context_survives(comet):
+    # fault injection on the host side of the protocol: one operand load of the tensor-core
+    # kernel is withheld, its bounded wait runs out, the status word reports it, and the next
+    # launch on the same context is correct
+    blocks = Blocks(SMALL_K32, np.float32, exact_blocks=range(len(SMALL_K32)))
+    bad = comet.BatchedPlan(EXPR, LABELS, SMALL_K32, "f32", precision="split_bf16", timeout_ms=100, debug_flags=1)
+    import torch
+    res = torch.zeros(2 * blocks.n, dtype=torch.float64, device="cuda")
+    ws = bad.workspace()
+    bad.prepare(ws)
+    bad.contract(blocks.ptrs, res, ws, mode=0, key=KEY)
+    with pytest.raises(comet.CometError) as err:
+        comet.sync_status()
+    assert err.value.name == "COMET_ERR_TIMEOUT"
+    good = comet.BatchedPlan(EXPR, LABELS, SMALL_K32, "f32", precision="split_bf16")
+    got = _reduce(comet, good, blocks)
+    for b in range(len(SMALL_K32)):
+        _check_reduce(blocks, got, b, 1e-6)
 
 
 def test_graph_replay_and_autotune(comet):

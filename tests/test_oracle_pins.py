@@ -277,17 +277,51 @@ def test_splitmix64_published_vector():
     assert synth.mix64_int(1234567 + 2 * synth.GAMMA) == 3203168211198807973
 
 
+_M32 = 0xFFFFFFFF
+
+
+def _fmix32(h):
+    # the MurmurHash3 finalizer as published, written out here so that the weight pin does not
+    # rest on the oracle's own hash
+    h ^= h >> 16
+    h = (h * 0x85EBCA6B) & _M32
+    h ^= h >> 13
+    h = (h * 0xC2B2AE35) & _M32
+    h ^= h >> 16
+    return h
+
+
+def _factor(key, block, x):
+    return (_fmix32((key ^ _fmix32((block * 0x9E3779B9 + x) & _M32)) & _M32) >> 8) * 2.0 ** -23 - 1.0
+
+
+def test_weight_factor_by_definition():
+    assert _fmix32(1) == 0x514E28B7 and _fmix32(0xFFFFFFFF) == 0x81F16F39   # published vectors
+    for key, block, x in ((77, 5, 0), (77, 5, 123456), (0xDEADBEEF, 4095, 0xFFFFFFFF), (0, 0, 1)):
+        assert oracle.triples_factor(key, block, x) == _factor(key, block, x)
+    vals = [oracle.triples_factor(3, 1, x) for x in range(4096)]
+    assert min(vals) >= -1.0 and max(vals) < 1.0 and abs(np.mean(vals)) < 0.05
+
+
 def test_triples_reduce_matches_materialised_block():
-    ea, eb, ec, ei, ej, ek, ed = 2, 3, 2, 3, 2, 2, 4
+    # distinct extents, so that a weight built on the wrong label split or the wrong key fails
+    ea, eb, ec, ei, ej, ek, ed = 2, 3, 4, 3, 2, 5, 4
     A = synth.tensor((ed, ea, eb, ei), 18, 0, kind="normal", scale=0.1)
     B = synth.tensor((ec, ed, ej, ek), 18, 1, kind="normal", scale=0.1)
     T = oracle.einsum("T[a,b,c,i,j,k] = A[d,a,b,i] * B[c,d,j,k]", A, B)
-    flat = np.ravel(T, order="F")
-    W = np.array([oracle.triples_weight(77, 5, n) for n in range(flat.size)])
-    s, q = oracle.triples_reduce(A, B, 77, 5)
-    np.testing.assert_allclose(s, float(np.dot(flat, W)), rtol=1e-13)
-    np.testing.assert_allclose(q, float(np.dot(flat, flat)), rtol=1e-13)
-    assert np.all((W >= -1.0) & (W < 1.0))
+    a, b, c, i, j, k = np.indices(T.shape)
+    oA = a + ea * b + ea * eb * ec * i                              # labels of A: a, b, i
+    oB = ea * eb * c + ea * eb * ec * ei * j + ea * eb * ec * ei * ej * k   # labels of B: c, j, k
+    assert np.array_equal(oA + oB, np.arange(T.size).reshape(T.shape, order="F"))
+    key, blk = 77, 5
+    fa = np.vectorize(lambda x: _factor(key, blk, int(x)))(oA)
+    fb = np.vectorize(lambda x: _factor(key ^ _M32, blk, int(x)))(oB)
+    s, q = oracle.triples_reduce(A, B, key, blk)
+    np.testing.assert_allclose(s, float(np.sum(T * fa * fb)), rtol=1e-13)
+    np.testing.assert_allclose(q, float(np.sum(T * T)), rtol=1e-13)
+    # the same block under another key or block number gives another s (the weight is keyed)
+    assert abs(oracle.triples_reduce(A, B, key + 1, blk)[0] - s) > 1e-6 * np.sqrt(q)
+    assert abs(oracle.triples_reduce(A, B, key, blk + 1)[0] - s) > 1e-6 * np.sqrt(q)
 
 
 def test_golden_fixture_table1_parses():

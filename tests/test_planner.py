@@ -280,7 +280,19 @@ def test_batched_plan_structure():
         assert info["batched"] and info["n_blocks"] == 64
         flops = sum(2.0 * np.prod(r) for r in ext)
         assert p.flops == pytest.approx(flops)
-        assert p.num_tiles() == (3 if prec == "split_bf16" else 4)
+        assert p.num_tiles() == (2 if prec == "split_bf16" else 4)
+        if prec == "split_bf16":
+            # tcgen05 kernel; K = d <= 32 everywhere, so one accumulator per tile; each operand's
+            # planes hold ceil(K/16) chunks x 3 planes x rows rounded up to 256
+            assert info["kernel"] == "tcgen05" and info["dual_accumulators"] == 0
+            rows = 0
+            for a, b, c, i, j, k, d in ext:
+                r = lambda x: -(-x // 256) * 256
+                rows += -(-d // 16) * 3 * (r(a * b * i) + r(c * j * k))
+            assert info["plane_rows"] == rows
+            ext2 = ext.copy()
+            ext2[5, 6] = 40   # one block with K = 40: the hh products get their own accumulator
+            assert comet.BatchedPlan(e, names, ext2, "f64", precision=prec).describe()["dual_accumulators"] == 1
         for c in range(p.num_tiles()):
             p.set_tile(c)
             assert p.describe()["tile_cfg"] == c

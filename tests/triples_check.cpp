@@ -1,0 +1,167 @@
+// CPU replay of the index arithmetic of the fused triples kernel (k_triples.cu, thread tiles of
+// 4 x 4) on the argument block the real host code builds (triples_plan.cpp), for FP32 (32
+// summed values per step) and FP64 (16).  Terms, labels, signs and one block's extents come
+// from the command line: argv = n_terms, the terms, the 7 label names, 6 signs, 7 extents.
+// For every thread, every term and a set of tiles that includes the first and the ragged last
+// tile along every label, it checks:
+//   - the staging entries (kk, r) of stage_async stay inside the [kc][RP] shared tile, and the
+//     global element offsets they read lie inside the operand (all digits guarded by rem);
+//   - the 16-byte shared loads of step_compute start on 16-byte boundaries and stay in the row;
+//   - the energy epilogue's eps reads stay inside the eps vectors;
+//   - the static shared arrays the 16-byte loads use have 16-byte-multiple row pitches.
+// Exit status 0 = pass.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../paper_2102_06827_gb300/csrc/triples.h"
+
+using namespace comet;
+using namespace comet::tri;
+
+static int fails = 0;
+#define CHECK(c, ...) do { if (!(c)) { if (fails++ < 20) { std::printf(__VA_ARGS__); std::printf("\n"); } } } while (0)
+
+// the kernel's entry(): staging entry idx -> (kk, r)
+static void entry(int KCt, int idx, int &kk, int &r) {
+    const int hb = KCt / 8 == 4 ? 2 : 1;
+    const int rest = idx >> 5;
+    kk = ((rest & (KCt / 8 - 1)) << 3) | (idx & 7);
+    r = ((rest >> hb) << 2) | ((idx >> 3) & 3);
+}
+
+struct TA { int base, sd, s[3], rem[3]; };
+
+// the kernel's tile_addr(), with the element count of the operand it addresses
+static TA tile_addr(const int8_t *q, const int8_t *col, const int8_t *dig, const int32_t *ext_b, const int *tbase,
+                    const int *text, int k0, int64_t *n_elems) {
+    TA ta{};
+    int st = 1;
+    for (int m = 0; m < 4; ++m) {
+        if (q[m] < 0) {
+            ta.sd = st;
+            ta.base += k0 * st;
+        } else {
+            const int b0 = tbase[q[m]];
+            const int rm = std::min(TS, text[q[m]] - b0);
+            ta.base += b0 * st;
+            if (dig[m] == 0) { ta.s[0] = st; ta.rem[0] = rm; }
+            if (dig[m] == 1) { ta.s[1] = st; ta.rem[1] = rm; }
+            if (dig[m] == 2) { ta.s[2] = st; ta.rem[2] = rm; }
+        }
+        st *= ext_b[col[m]];
+    }
+    *n_elems = st;
+    return ta;
+}
+
+static void replay(const Args &a, const int32_t *ext_b, int elem) {
+    const int kc = elem == 4 ? KC : KC / 2, RS = NT / kc, NIT = kc * R / NT;
+    CHECK(RS == 8 || RS == 16, "lane pattern");
+    CHECK((RP * elem) % 16 == 0, "row pitch of the staged tiles not a multiple of 16 bytes");
+    int text[6], ntile[6];
+    for (int q = 0; q < 6; ++q) {
+        text[q] = ext_b[a.t_col[q]];
+        ntile[q] = (text[q] + TS - 1) / TS;
+    }
+    // tiles: every combination of the first and the last tile along each label
+    for (int mask = 0; mask < 64; ++mask) {
+        int tbase[6];
+        for (int q = 0; q < 6; ++q) tbase[q] = ((mask >> q) & 1) ? (ntile[q] - 1) * TS : 0;
+        for (int t = 0; t < NT; ++t) {
+            int f[4];
+            for (int j = 0; j < 4; ++j) f[j] = (t >> (2 * j)) & 3;
+            bool fixed_ok = true;
+            for (int j = 0; j < 4; ++j) fixed_ok &= tbase[a.fixed[j]] + f[j] < text[a.fixed[j]];
+            for (int p = 0; p < a.n_terms; ++p) {
+                const TermDev &tm = a.term[p];
+                const int K = ext_b[tm.d_col];
+                // s_dig: rx, ry and the case, as the kernel forms them
+                int rx = 0, ry = 0;
+                bool u_on_x = false, v_on_x = false;
+                for (int m = 0; m < 4; ++m) {
+                    for (int j = 0; j < 4; ++j) {
+                        if (tm.x_q[m] == a.fixed[j]) rx += f[j] << (2 * tm.x_dig[m]);
+                        if (tm.y_q[m] == a.fixed[j]) ry += f[j] << (2 * tm.y_dig[m]);
+                    }
+                    u_on_x |= tm.x_q[m] == a.own[0];
+                    v_on_x |= tm.x_q[m] == a.own[1];
+                }
+                const int kase = u_on_x ? (v_on_x ? 2 : 0) : (v_on_x ? 1 : 3);
+                CHECK(rx < 64 && ry < 64, "row offsets above 6 bits");
+                // 16-byte shared loads of step_compute: (row start, elements read)
+                auto vec_load = [&](int r) {
+                    CHECK((r * elem) % 16 == 0, "misaligned 16-byte shared load (term %d, r %d)", p, r);
+                    CHECK(r + 4 <= R, "shared load beyond the row");
+                };
+                if (kase == 0) { vec_load(rx); vec_load(ry); }
+                else if (kase == 1) { vec_load(ry); vec_load(rx); }
+                else if (kase == 2) { for (int v = 0; v < 4; ++v) vec_load(rx + 4 * v); CHECK(ry < R, "scalar load"); }
+                else { for (int v = 0; v < 4; ++v) vec_load(ry + 4 * v); CHECK(rx < R, "scalar load"); }
+                (void)fixed_ok;
+                // staging of every step of this term
+                for (int k0 = 0; k0 < K; k0 += kc) {
+                    const int kn = std::min(kc, K - k0);
+                    for (int side = 0; side < 2; ++side) {
+                        int64_t n_el = 0;
+                        const TA ta = side ? tile_addr(tm.y_q, tm.y_col, tm.y_dig, ext_b, tbase, text, k0, &n_el)
+                                           : tile_addr(tm.x_q, tm.x_col, tm.x_dig, ext_b, tbase, text, k0, &n_el);
+                        int kk, r0;
+                        entry(kc, t, kk, r0);
+                        CHECK(kk < kc && r0 < RS, "entry decomposition");
+                        const int d0 = r0 & 3, h = r0 >> 2;
+                        if (kk >= kn || d0 >= ta.rem[0]) continue;
+                        for (int it = 0; it < NIT; ++it) {
+                            const int dd1 = RS == 8 ? 2 * (it & 1) : 0, d2 = RS == 8 ? it >> 1 : it;
+                            if (!(h + dd1 < ta.rem[1] && d2 < ta.rem[2])) continue;
+                            const int r = r0 + it * RS;
+                            CHECK(r < R, "staged row %d beyond R", r);
+                            // the entry holds digits (d0, h + dd1, d2) of row r
+                            CHECK((r & 3) == d0 && ((r >> 2) & 3) == h + dd1 && (r >> 4) == d2, "entry digits");
+                            const int64_t off = (int64_t)ta.base + (int64_t)kk * ta.sd + (int64_t)d0 * ta.s[0] +
+                                                (int64_t)(h + dd1) * ta.s[1] + (int64_t)d2 * ta.s[2];
+                            CHECK(off >= 0 && off < n_el, "global read outside the operand (term %d side %d)", p, side);
+                        }
+                    }
+                }
+            }
+            // energy: eps reads of the thread's fixed labels and its owned 4 x 4
+            if (fixed_ok) {
+                for (int j = 0; j < 4; ++j) CHECK(tbase[a.fixed[j]] + f[j] < text[a.fixed[j]], "eps (fixed)");
+                for (int o = 0; o < 2; ++o)
+                    for (int u = 0; u < 4; ++u)
+                        if (tbase[a.own[o]] + u < text[a.own[o]]) CHECK(tbase[a.own[o]] + u >= 0, "eps (owned)");
+            }
+        }
+    }
+}
+
+int main(int argc, char **argv) {
+    if (argc < 2) { std::printf("usage\n"); return 2; }
+    const int nt = std::atoi(argv[1]);
+    if (argc != 2 + nt + 7 + 6 + 7) { std::printf("bad arguments\n"); return 2; }
+    std::vector<const char *> terms(argv + 2, argv + 2 + nt);
+    const char *names[7];
+    for (int l = 0; l < 7; ++l) names[l] = argv[2 + nt + l];
+    int signs[6];
+    for (int q = 0; q < 6; ++q) signs[q] = std::atoi(argv[2 + nt + 7 + q]);
+    int64_t ext[7];
+    for (int l = 0; l < 7; ++l) ext[l] = std::atoll(argv[2 + nt + 13 + l]);
+    for (int e : {4, 8}) {
+        Plan P;
+        std::string err;
+        comet_status_t st = plan_triples(terms.data(), nt, names, 7, 1, ext, signs, e == 4 ? COMET_F32 : COMET_F64,
+                                         &P, &err);
+        CHECK(st == COMET_OK, "plan: %s", err.c_str());
+        if (st != COMET_OK) continue;
+        Args a;
+        std::memset(&a, 0, sizeof(a));
+        triples_args(P, &a);
+        replay(a, P.tri.ext.data(), e);
+    }
+    std::printf("%d failures\n", fails);
+    return fails ? 1 : 0;
+}
