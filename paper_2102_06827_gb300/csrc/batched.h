@@ -17,22 +17,37 @@ struct BlockDesc {
     uint32_t M, N, K;
     uint32_t index;              // the block's position in the caller's tables
     int64_t a_elems, b_elems;
-    // split path: the operands' bfloat16 planes, in rows of 16 K values (32 bytes) counted from
-    // the start of the plane region; operand X occupies nk16 chunks x 3 planes x x_pad rows,
-    // [chunk][plane][row], rows beyond M (N) and K values beyond K zero
+    // split path: the operands' bfloat16 planes, in rows of 32 K values (64 bytes) counted from
+    // the start of the plane region; operand X occupies ceil(K/32) chunks x 3 planes x x_pad
+    // rows, [chunk][plane][row], rows beyond M (N) and K values beyond K zero
     int64_t a_row0, b_row0;
-    uint32_t nk16;               // K in chunks of 16
+    uint32_t nk16;               // K in MMA steps of 16
     uint32_t m_pad, n_pad;       // M and N rounded up to a multiple of 256
     uint32_t pad[3];
 };
 
+// One work item of the tensor-core split kernel (block, strip of output columns), built on the
+// host per tile configuration so that the kernel's roles read it with one 48-byte load.
+struct ItemRec {
+    uint32_t pos;                // the block's position in launch order (descriptor index)
+    uint32_t index;              // the block's position in the caller's tables
+    uint32_t n0;                 // first output column of the strip
+    uint32_t mtiles;             // 128-row tiles of the block
+    uint32_t nk16, M, N;
+    uint32_t m_pad, n_pad;
+    int32_t a_row0, b_row0;      // first plane row of each operand
+    uint32_t pad;
+};
+static_assert(sizeof(ItemRec) == 48, "item records are read as three 16-byte words");
+
 constexpr int kBatchedCfgF64 = 4;     // tile configurations of the FP64 path
 constexpr int kBatchedCfgSplit = 2;   // tile configurations of the split path (strip widths)
-constexpr int kBatchedPlaneRow = 32;  // bytes of one plane row (16 bfloat16 K values)
+constexpr int kBatchedPlaneRow = 64;  // bytes of one plane row (32 bfloat16 K values)
 
 struct BatchedParams {
     const BlockDesc *desc;       // n_blocks descriptors, longest first
     const uint32_t *prefix;      // n_blocks + 1 work-item prefix sums for the launched configuration
+    const ItemRec *items;        // split path: the launched configuration's work items
     uint32_t n_blocks, total_tiles;
     const void *const *inputs;   // 2 per block (caller's order)
     int swap;                    // 1: the M operand is the block's second input
@@ -61,18 +76,20 @@ inline int n_cfg(const Plan &P) { return P.opts.precision == COMET_PREC_SPLIT_BF
 inline TileCfg cfg_of(const Plan &P, int c) { return batched_cfg(P.opts.precision == COMET_PREC_SPLIT_BF16, c); }
 
 // workspace layout: [counter 256 B][exps 8*n][prefix n_cfg*(n+1)*4][descs n*sizeof(BlockDesc)]
-// [split path: the plane rows of every block's operands]
+// [split path: item records of every configuration][split path: the plane rows of every
+// block's operands]
 struct BLayout {
-    size_t exps, prefix, desc, parts, total;
+    size_t exps, prefix, desc, items, parts, total;
 };
 
-inline BLayout layout_of(int n_blocks, int ncfg, size_t parts_bytes) {
+inline BLayout layout_of(int n_blocks, int ncfg, size_t item_bytes, size_t parts_bytes) {
     auto al = [](size_t x) { return (x + 255) / 256 * 256; };
     BLayout L;
     L.exps = 256;
     L.prefix = al(L.exps + 8 * (size_t)n_blocks);
     L.desc = al(L.prefix + 4 * (size_t)ncfg * (n_blocks + 1));
-    L.parts = al(L.desc + sizeof(BlockDesc) * (size_t)n_blocks);
+    L.items = al(L.desc + sizeof(BlockDesc) * (size_t)n_blocks);
+    L.parts = al(L.items + item_bytes);
     L.total = al(L.parts + parts_bytes);
     return L;
 }
@@ -80,23 +97,25 @@ inline BLayout layout_of(int n_blocks, int ncfg, size_t parts_bytes) {
 // geometry of the tensor-core batched kernel (k_batched_tc.cu), shared with its CPU replay
 namespace btc {
 constexpr int BM = 128;                               // tile rows (tcgen05 M, tensor-memory lanes)
-constexpr int ROW = kBatchedPlaneRow;                 // 32 bytes: 16 bf16 K values
+constexpr int ROW = kBatchedPlaneRow;                 // 64 bytes: 32 bf16 K values (one chunk)
 constexpr int BOX_ROWS = 128;
-constexpr int BOX_BYTES = BOX_ROWS * ROW;             // 4 KB: one plane of one 128-row chunk tile
-constexpr int SLOT_BYTES = 3 * BOX_BYTES;             // 12 KB: three planes
-constexpr int RING = 8;                               // ring slots
-constexpr int MAX_RES_NK = 2;                         // K <= 32: the strip's B tile stays resident
+constexpr int BOX_BYTES = BOX_ROWS * ROW;             // 8 KB: one plane of one 128-row chunk tile
+constexpr int SLOT_BYTES = 3 * BOX_BYTES;             // 24 KB: three planes
+constexpr int RING = 5;                               // ring slots
+constexpr int MAX_RES_NK = 2;                         // K <= 32 (one chunk, at most two MMA steps):
+                                                      // the strip's B tile stays resident
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t SW32 = 6;                          // descriptor swizzle code: 32-byte swizzle
-constexpr uint32_t SBO = 8 * ROW;                     // 8-row core-matrix groups, 256 bytes apart
+constexpr uint32_t SW64 = 4;                          // descriptor swizzle code: 64-byte swizzle
+constexpr uint32_t SBO = 8 * ROW;                     // 8-row core-matrix groups, 512 bytes apart
 
 template <int BN>
 struct Cfg {
-    static constexpr int STRIP_BYTES = MAX_RES_NK * 3 * BN * ROW;     // 48 KB at BN = 256
+    static constexpr int STRIP_BYTES = 3 * BN * ROW;                  // 48 KB at BN = 256
     static constexpr int BARS = 2 * RING + 4 + 2 * 4 + 1;
-    static constexpr int SMEM = 1024 + 2 * STRIP_BYTES + RING * SLOT_BYTES + BN * 4 + BN * 8 + BARS * 8 + 16;
+    static constexpr int SMEM = 1024 + 2 * STRIP_BYTES + RING * SLOT_BYTES + BN * 4 + BN * 8 +
+                                (int)((sizeof(Radix) + 15) / 16 * 16) + BARS * 8 + 16;
 };
 }  // namespace btc
 

@@ -170,8 +170,8 @@ comet_status_t build_batched_plan(const char *expr, int n_blocks, const char *co
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return P.block_flops[x] > P.block_flops[y]; });
     const int ncfg = n_cfg(P);
-    // split path: each operand's planes as rows of 16 K values in one array, in launch order:
-    // nk16 chunks x 3 planes x (rows rounded up to 256) rows per operand
+    // split path: each operand's planes as rows of 32 K values in one array, in launch order:
+    // ceil(K/32) chunks x 3 planes x (rows rounded up to 256) rows per operand
     size_t parts = 0;
     int64_t prow = 0;
     P.batched_dual = false;
@@ -181,23 +181,21 @@ comet_status_t build_batched_plan(const char *expr, int n_blocks, const char *co
             d.nk16 = (d.K + 15) / 16;
             d.m_pad = (d.M + 255) / 256 * 256;
             d.n_pad = (d.N + 255) / 256 * 256;
+            const int64_t nkc = (d.K + 31) / 32;
             d.a_row0 = prow;
-            prow += (int64_t)d.nk16 * 3 * d.m_pad;
+            prow += nkc * 3 * d.m_pad;
             d.b_row0 = prow;
-            prow += (int64_t)d.nk16 * 3 * d.n_pad;
+            prow += nkc * 3 * d.n_pad;
             if (d.K > 32) P.batched_dual = true;
         }
         if (prow >= (int64_t(1) << 31)) {
-            err = "the split planes exceed 2^31 rows of 16 values";
+            err = "the split planes exceed 2^31 rows of 32 values";
             return COMET_ERR_UNSUPPORTED;
         }
         parts = (size_t)prow * kBatchedPlaneRow;
     }
     P.batched_parts = parts;
     P.batched_plane_rows = prow;
-    const BLayout L = layout_of(n_blocks, ncfg, parts);
-    P.batched_ws = L.total;
-    P.batched_table.assign(L.parts - L.prefix, 0);
     P.batched_prefix.assign(ncfg, std::vector<uint32_t>(n_blocks + 1, 0));
     for (int c = 0; c < ncfg; ++c) {
         const TileCfg tc = cfg_of(P, c);
@@ -212,12 +210,47 @@ comet_status_t build_batched_plan(const char *expr, int n_blocks, const char *co
             return COMET_ERR_UNSUPPORTED;
         }
         P.batched_prefix[c][n_blocks] = (uint32_t)acc;
+    }
+    // split path: one record per work item and configuration
+    const bool split = P.opts.precision == COMET_PREC_SPLIT_BF16;
+    P.batched_item_off.assign(ncfg, 0);
+    size_t item_bytes = 0;
+    for (int c = 0; c < ncfg && split; ++c) {
+        P.batched_item_off[c] = item_bytes;
+        item_bytes += ((size_t)P.batched_prefix[c][n_blocks] * sizeof(ItemRec) + 255) / 256 * 256;
+    }
+    P.batched_item_bytes = item_bytes;
+    const BLayout L = layout_of(n_blocks, ncfg, item_bytes, parts);
+    P.batched_ws = L.total;
+    P.batched_table.assign(L.parts - L.prefix, 0);
+    for (int c = 0; c < ncfg; ++c)
         std::memcpy(P.batched_table.data() + 4 * (size_t)c * (n_blocks + 1), P.batched_prefix[c].data(),
                     4 * (size_t)(n_blocks + 1));
-    }
     for (int i = 0; i < n_blocks; ++i)
         std::memcpy(P.batched_table.data() + (L.desc - L.prefix) + sizeof(BlockDesc) * (size_t)i, &desc[order[i]],
                     sizeof(BlockDesc));
+    for (int c = 0; c < ncfg && split; ++c) {
+        const TileCfg tc = cfg_of(P, c);
+        ItemRec *rec = reinterpret_cast<ItemRec *>(P.batched_table.data() + (L.items - L.prefix) + P.batched_item_off[c]);
+        for (int i = 0; i < n_blocks; ++i) {
+            const BlockDesc &d = desc[order[i]];
+            for (uint32_t it = P.batched_prefix[c][i]; it < P.batched_prefix[c][i + 1]; ++it) {
+                ItemRec &r = rec[it];
+                r.pos = (uint32_t)i;
+                r.index = d.index;
+                r.n0 = (it - P.batched_prefix[c][i]) * (uint32_t)tc.bn;
+                r.mtiles = (d.M + tc.bm - 1) / tc.bm;
+                r.nk16 = d.nk16;
+                r.M = d.M;
+                r.N = d.N;
+                r.m_pad = d.m_pad;
+                r.n_pad = d.n_pad;
+                r.a_row0 = (int32_t)d.a_row0;
+                r.b_row0 = (int32_t)d.b_row0;
+                r.pad = 0;
+            }
+        }
+    }
     if (tile_hint >= ncfg) return COMET_ERR_ARG;
     int cfg = tile_hint;
     if (cfg < 0) {

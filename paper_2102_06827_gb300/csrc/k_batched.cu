@@ -29,6 +29,7 @@
 #include <numeric>
 #include <sstream>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/comet.h"
@@ -231,27 +232,45 @@ __global__ void __launch_bounds__(BT) batched_f64_kernel(const BatchedParams P) 
     }
 }
 
-// per-block operand scale exponents (split path): CTA c reduces operand c%2 of block c/2
+// per-block operand scale exponents (split path): CTA c reduces operand c%2 of block c/2.
+// The largest magnitude is taken on the bit patterns with the sign bit cleared (for finite
+// values the unsigned integer order is the order of magnitudes), so the reduction is exact
+// and runs on the integer pipe for both input precisions.
 template <typename TIn>
 __global__ void __launch_bounds__(256) batched_absmax_kernel(const BatchedParams P) {
-    __shared__ float red[8];
+    using U = typename std::conditional<sizeof(TIn) == 4, uint32_t, unsigned long long>::type;
+    constexpr U MAG = sizeof(TIn) == 4 ? (U)0x7FFFFFFFu : (U)0x7FFFFFFFFFFFFFFFull;
+    __shared__ U red[8];
     const BlockDesc &d = P.desc[blockIdx.x >> 1];
     const int op = blockIdx.x & 1;
     const int64_t n = op ? d.b_elems : d.a_elems;
-    const TIn *x = reinterpret_cast<const TIn *>(P.inputs[2 * d.index + (op ^ P.swap)]);
-    double m = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += 256) m = fmax(m, fabs((double)x[i]));
-    float mf = (float)m;
+    const U *x = reinterpret_cast<const U *>(P.inputs[2 * d.index + (op ^ P.swap)]);
+    U m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+    int64_t i = threadIdx.x;
+    for (; i + 3 * 256 < n; i += 4 * 256) {
+        m0 = max(m0, x[i] & MAG);
+        m1 = max(m1, x[i + 256] & MAG);
+        m2 = max(m2, x[i + 512] & MAG);
+        m3 = max(m3, x[i + 768] & MAG);
+    }
+    for (; i < n; i += 256) m0 = max(m0, x[i] & MAG);
+    U m = max(max(m0, m1), max(m2, m3));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mf = fmaxf(mf, __shfl_xor_sync(0xffffffffu, mf, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mf;
+    for (int o = 16; o > 0; o >>= 1) m = max(m, (U)__shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double mm = 0.0;
-        for (int i = 0; i < 8; ++i) mm = fmax(mm, (double)red[i]);
-        // exact maximum for the exponent: recompute from the FP64 value of the max element
+        U mm = 0;
+        for (int w = 0; w < 8; ++w) mm = max(mm, red[w]);
+        // exponent e with max |x| in [2^e, 2^(e+1)); 0 for an all-zero or non-finite operand
         int e = 0;
-        if (mm > 0.0 && !isinf(mm)) { frexp(mm, &e); e -= 1; }
+        if constexpr (sizeof(TIn) == 4) {
+            const float v = __uint_as_float((uint32_t)mm);
+            if (v > 0.0f && !isinf(v) && !isnan(v)) { frexpf(v, &e); e -= 1; }
+        } else {
+            const double v = __longlong_as_double((long long)mm);
+            if (v > 0.0 && !isinf(v) && !isnan(v)) { frexp(v, &e); e -= 1; }
+        }
         const_cast<int *>(P.exps)[2 * d.index + op] = e;
     }
 }
@@ -292,7 +311,7 @@ static int resident_ctas() {
 // the launch sequence of one batched contraction (on a prepared workspace)
 static comet_status_t run_batched(const Plan &P, const void *const *block_inputs, int mode, void *result,
                                   uint32_t key, void *ws, cudaStream_t s, int cfg, int sample_blocks) {
-    const BLayout L = layout_of(P.n_blocks, n_cfg(P), P.batched_parts);
+    const BLayout L = layout_of(P.n_blocks, n_cfg(P), P.batched_item_bytes, P.batched_parts);
     char *w = static_cast<char *>(ws);
     BatchedParams bp;
     bp.desc = reinterpret_cast<const BlockDesc *>(w + L.desc);
@@ -311,6 +330,8 @@ static comet_status_t run_batched(const Plan &P, const void *const *block_inputs
     bp.alpha = P.alpha;
     bp.ws = w;
     bp.planes = w + L.parts;
+    bp.items = P.batched_item_off.empty() ? nullptr
+                                          : reinterpret_cast<const ItemRec *>(w + L.items + P.batched_item_off[cfg]);
     bp.status = device_status_word();
     bp.timeout_ns = (P.opts.timeout_ms > 0 ? P.opts.timeout_ms : 2000) * 1000000ll;
     bp.debug_flags = P.opts.debug_flags;
@@ -390,7 +411,7 @@ comet_status_t comet_batched_prepare(comet_plan_t plan, void *workspace, void *s
     const Plan &P = plan->p;
     if (!P.batched) return COMET_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(workspace) & 15u) != 0) return COMET_ERR_ALIGN;
-    const BLayout L = layout_of(P.n_blocks, n_cfg(P), P.batched_parts);
+    const BLayout L = layout_of(P.n_blocks, n_cfg(P), P.batched_item_bytes, P.batched_parts);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemcpyAsync(static_cast<char *>(workspace) + L.prefix, P.batched_table.data(),
                                     P.batched_table.size(), cudaMemcpyHostToDevice, s);

@@ -167,6 +167,8 @@ struct Plan {
     bool batched_ak = false, batched_bk = false, batched_swap = false;
     bool batched_dual = false;            // split path: some block has K > 32 (hh kept apart)
     int64_t batched_plane_rows = 0;       // split path: rows of 16 bf16 in the plane region
+    size_t batched_item_bytes = 0;        // split path: item records of every configuration
+    std::vector<size_t> batched_item_off; // split path: byte offset of each configuration's records
     HostPipe pipe;                        // comet_contract_host slicing (one-step plans)
     bool triples = false;                 // comet_plan_triples
     TriplesPlan tri;

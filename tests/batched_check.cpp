@@ -52,7 +52,7 @@ static void check_plan(const char *expr, const std::vector<std::vector<int64_t>>
     comet_status_t st = build_batched_plan(expr, nb, names, 7, flat.data(), dt, 3, &o, 0, &P, &err);
     CHECK(st == COMET_OK, "plan failed: %s", err.c_str());
     if (st != COMET_OK) return;
-    const BLayout L = layout_of(nb, n_cfg(P), P.batched_parts);
+    const BLayout L = layout_of(nb, n_cfg(P), P.batched_item_bytes, P.batched_parts);
     CHECK(L.parts % 256 == 0, "plane region alignment");
     CHECK(P.batched_parts == (size_t)P.batched_plane_rows * kBatchedPlaneRow, "plane bytes");
     CHECK(P.batched_plane_rows < (int64_t(1) << 31), "plane rows above int32");
@@ -65,10 +65,12 @@ static void check_plan(const char *expr, const std::vector<std::vector<int64_t>>
         CHECK(d.nk16 == (d.K + 15) / 16 && d.nk16 * 16 <= 1024, "nk16");
         CHECK(d.m_pad % 256 == 0 && d.m_pad >= d.M && d.n_pad % 256 == 0 && d.n_pad >= d.N, "padding");
         if (d.K > 32) any_dual = true;
+        const uint32_t nkc = (d.K + 31) / 32;   // chunks of 32 K values, one plane row each
+        CHECK(nkc * 32 <= 1024, "pre-pass offset table");
         for (int op = 0; op < 2; ++op) {
             const int64_t r0 = op ? d.b_row0 : d.a_row0;
             const uint32_t pad = op ? d.n_pad : d.m_pad;
-            const int64_t n = (int64_t)d.nk16 * 3 * pad;
+            const int64_t n = (int64_t)nkc * 3 * pad;
             CHECK(r0 >= 0 && r0 + n <= P.batched_plane_rows, "operand planes outside the region");
             for (int64_t r = r0; r < r0 + n && r < P.batched_plane_rows; ++r) {
                 CHECK(!written[r], "plane row %lld written twice", (long long)r);
@@ -88,17 +90,27 @@ static void check_plan(const char *expr, const std::vector<std::vector<int64_t>>
         // highest column the MMA writes / the epilogue reads: last buffer + P1 + last column
         const uint32_t top = (nbuf - 1) * buf_cols + (P.batched_dual ? BN : 0) + BN;
         CHECK(top <= btc::TMEM_COLS, "tensor-memory columns %u", top);
-        const int strip_bytes = btc::MAX_RES_NK * 3 * BN * btc::ROW;
+        const int strip_bytes = 3 * BN * btc::ROW;
         const uint32_t *prefix = P.batched_prefix[c].data();
         const uint32_t n_items = prefix[nb];
         const int halves = BN / btc::BOX_ROWS;
+        CHECK(P.batched_item_off[c] + (size_t)n_items * sizeof(ItemRec) <= P.batched_item_bytes, "item records");
+        const ItemRec *items = reinterpret_cast<const ItemRec *>(P.batched_table.data() + (L.items - L.prefix) +
+                                                                 P.batched_item_off[c]);
+        CHECK(((L.items + P.batched_item_off[c]) % 16) == 0, "item records not 16-byte aligned");
         for (uint32_t it = 0; it < n_items; ++it) {
             const uint32_t pos = find_block(prefix, (uint32_t)nb, it);
             CHECK(prefix[pos] <= it && it < prefix[pos + 1], "item lookup");
             const BlockDesc &d = desc[pos];
-            const uint32_t n0 = (it - prefix[pos]) * BN;
+            const ItemRec &rec = items[it];
+            // the record the kernel reads agrees with the prefix sums and the descriptor
+            CHECK(rec.pos == pos && rec.index == d.index && rec.n0 == (it - prefix[pos]) * BN &&
+                  rec.mtiles == (d.M + btc::BM - 1) / btc::BM && rec.nk16 == d.nk16 && rec.M == d.M &&
+                  rec.N == d.N && rec.m_pad == d.m_pad && rec.n_pad == d.n_pad && rec.a_row0 == d.a_row0 &&
+                  rec.b_row0 == d.b_row0, "item record %u", it);
+            const uint32_t n0 = rec.n0;
             CHECK(n0 < d.N, "strip beyond N");
-            const uint32_t mtiles = (d.M + btc::BM - 1) / btc::BM;
+            const uint32_t mtiles = rec.mtiles;
             const bool res = d.nk16 <= (uint32_t)btc::MAX_RES_NK;
             CHECK(res || P.batched_dual, "streamed B without dual accumulators");
             auto box = [&](int64_t row0, uint32_t pad, uint32_t kc, uint32_t r0, uint32_t limit) {
@@ -111,19 +123,23 @@ static void check_plan(const char *expr, const std::vector<std::vector<int64_t>>
                 CHECK(r0 + btc::BOX_ROWS <= pad, "box rows beyond the padded rows");
                 CHECK(r0 < limit, "box starts beyond the operand's rows");
             };
+            const uint32_t nkc = (d.nk16 + 1) / 2;
+            CHECK(!res || nkc == 1, "a resident strip holds one chunk");
             if (res) {
-                for (uint32_t kc = 0; kc < d.nk16; ++kc)
-                    for (uint32_t p = 0; p < 3; ++p)
-                        for (int h = 0; h < halves; ++h) {
-                            const int off = (int)((kc * 3 + p) * BN + h * btc::BOX_ROWS) * btc::ROW;
-                            CHECK(off % 1024 == 0 && off + btc::BOX_BYTES <= strip_bytes, "strip destination");
-                        }
+                for (uint32_t p = 0; p < 3; ++p)
+                    for (int h = 0; h < halves; ++h) {
+                        const int off = (int)(p * BN + h * btc::BOX_ROWS) * btc::ROW;
+                        CHECK(off % 1024 == 0 && off + btc::BOX_BYTES <= strip_bytes, "strip destination");
+                    }
                 // (the second half of a 256-wide strip may lie wholly in the zero padding)
-                for (int h = 0; h < halves; ++h)
-                    for (uint32_t kc = 0; kc < d.nk16; ++kc) box(d.b_row0, d.n_pad, kc, n0 + h * btc::BOX_ROWS, d.n_pad);
+                for (int h = 0; h < halves; ++h) box(d.b_row0, d.n_pad, 0, n0 + h * btc::BOX_ROWS, d.n_pad);
             }
+            // a ring slot holds three 128-row plane boxes; the MMA's second K step reads 32 bytes
+            // into each 64-byte row
+            CHECK(btc::SLOT_BYTES == 3 * btc::BOX_BYTES && btc::BOX_BYTES % 1024 == 0 && 32 + 32 <= btc::ROW,
+                  "slot geometry");
             for (uint32_t mt = 0; mt < mtiles; ++mt)
-                for (uint32_t kc = 0; kc < d.nk16; ++kc) {
+                for (uint32_t kc = 0; kc < nkc; ++kc) {
                     box(d.a_row0, d.m_pad, kc, mt * btc::BM, d.M);
                     if (!res)
                         for (int h = 0; h < halves; ++h) box(d.b_row0, d.n_pad, kc, n0 + h * btc::BOX_ROWS, d.n_pad);

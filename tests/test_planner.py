@@ -283,12 +283,12 @@ def test_batched_plan_structure():
         assert p.num_tiles() == (2 if prec == "split_bf16" else 4)
         if prec == "split_bf16":
             # tcgen05 kernel; K = d <= 32 everywhere, so one accumulator per tile; each operand's
-            # planes hold ceil(K/16) chunks x 3 planes x rows rounded up to 256
+            # planes hold ceil(K/32) chunks x 3 planes x rows rounded up to 256 (rows of 32 values)
             assert info["kernel"] == "tcgen05" and info["dual_accumulators"] == 0
             rows = 0
             for a, b, c, i, j, k, d in ext:
                 r = lambda x: -(-x // 256) * 256
-                rows += -(-d // 16) * 3 * (r(a * b * i) + r(c * j * k))
+                rows += -(-d // 32) * 3 * (r(a * b * i) + r(c * j * k))
             assert info["plane_rows"] == rows
             ext2 = ext.copy()
             ext2[5, 6] = 40   # one block with K = 40: the hh products get their own accumulator
