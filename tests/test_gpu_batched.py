@@ -176,3 +176,68 @@ def test_graph_replay_and_autotune(comet):
     # a second plan of the same problem class picks up the autotuned configuration
     plan2 = comet.BatchedPlan(EXPR, LABELS, ext, "f32", precision="split_bf16")
     assert plan2.describe()["tile_cfg"] == best
+
+
+# other output orders and operand layouts: the planner swaps the GEMM roles for the first two
+# (the M operand is then B), which also swaps which weight factor belongs to the tile rows
+LAYOUTS = ["T[c,j,k,a,b,i] = A[d,a,b,i] * B[c,d,j,k]", "T[j,c,k,i,b,a] = A[d,a,b,i] * B[c,d,j,k]",
+           "T[a,c,i,j,b,k] = A[a,b,i,d] * B[d,c,j,k]"]
+
+
+def _weights(expr, ext_row, key, block):
+    """W over T's elements from its definition: h(key, b, oA) h(~key, b, oB), oA (oB) the part of
+    the column-major offset that the first (second) operand's labels contribute."""
+    _, out_labels, _, _, ops = oracle.parse(expr)
+    ext = dict(zip(LABELS, [int(x) for x in ext_row]))
+    shape = tuple(ext[l] for l in out_labels)
+    idx = np.indices(shape)
+    stride, st = {}, 1
+    for l in out_labels:
+        stride[l] = st
+        st *= ext[l]
+    a_labels = set(ops[0][1])
+    oA = sum(idx[q] * stride[l] for q, l in enumerate(out_labels) if l in a_labels)
+    oB = sum(idx[q] * stride[l] for q, l in enumerate(out_labels) if l not in a_labels)
+    fa = np.vectorize(lambda x: oracle.triples_factor(key, block, int(x)))(oA)
+    fb = np.vectorize(lambda x: oracle.triples_factor(key ^ 0xFFFFFFFF, block, int(x)))(oB)
+    return fa * fb
+
+
+@pytest.mark.parametrize("expr", LAYOUTS)
+@pytest.mark.parametrize("prec,dtype,tol", [("split_bf16", np.float32, 1e-6), ("native", np.float64, 1e-12)])
+def test_other_layouts_reduce_and_store(comet, expr, prec, dtype, tol):
+    import torch
+    ext = np.array([[5, 6, 3, 4, 7, 2, 9], [9, 2, 7, 3, 5, 4, 20], [4, 4, 4, 4, 4, 4, 33], [7, 3, 5, 2, 6, 8, 16]])
+    _, out_labels, _, _, ops = oracle.parse(expr)
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    host, dev = [], []
+    for b, row in enumerate(ext):
+        e = dict(zip(LABELS, [int(x) for x in row]))
+        pair = [synth.tensor(tuple(e[l] for l in ls), 31, 2 * b + t, kind="normal", scale=0.1, dtype=dtype)
+                for t, (_, ls) in enumerate(ops)]
+        host.append(pair)
+        dev.append([torch.from_numpy(np.ascontiguousarray(np.ravel(x, order="F"))).cuda() for x in pair])
+    ptrs = torch.tensor([t.data_ptr() for pair in dev for t in pair], dtype=torch.int64, device="cuda")
+    plan = comet.BatchedPlan(expr, LABELS, ext, "f32" if dtype == np.float32 else "f64", precision=prec)
+    assert plan.describe()["swap"] == (0 if expr.startswith("T[a,c") else 1)
+    for cfg in range(plan.num_tiles()):
+        plan.set_tile(cfg)
+        ws = plan.workspace()
+        plan.prepare(ws)
+        res = torch.zeros(2 * len(ext), dtype=torch.float64, device="cuda")
+        plan.contract(ptrs, res, ws, mode=0, key=KEY)
+        comet.sync_status()
+        got = res.cpu().numpy().reshape(-1, 2)
+        outs = [torch.zeros(int(np.prod([dict(zip(LABELS, row))[l] for l in out_labels])), dtype=tdt, device="cuda")
+                for row in ext]
+        table = torch.tensor([t.data_ptr() for t in outs], dtype=torch.int64, device="cuda")
+        plan.contract(ptrs, table, ws, mode=1)
+        comet.sync_status()
+        for b, row in enumerate(ext):
+            ref = oracle.einsum(expr, *[x.astype(np.float64) for x in host[b]])
+            T = np.reshape(outs[b].cpu().numpy().astype(np.float64), ref.shape, order="F")
+            assert np.abs(T - ref).max() <= tol * np.abs(ref).max(), (cfg, b)
+            q = float(np.sum(ref * ref))
+            s = float(np.sum(ref * _weights(expr, row, KEY, b)))
+            assert abs(got[b, 1] - q) <= tol * q, (cfg, b)
+            assert abs(got[b, 0] - s) <= tol * np.sqrt(q * ref.size), (cfg, b, got[b, 0], s)
