@@ -89,6 +89,26 @@ def test_wide_dynamic_range(comet):
     assert normwise(C, oracle.einsum(e, np.asfortranarray(A), B)) <= TOL
 
 
+def test_large_chunk_sums_exact(comet):
+    # every slice of every element equal to 127 (x' = X 2^-46 with X = 127 (256^6 - 1) / 255 in
+    # balanced base 256), some elements negated: the weight-group sums of a 192-K chunk then reach
+    # 5 x 127^2 x 192 = 1.5e7, above 2^22, where the drain's full-rate conversion does not hold and
+    # its exact fallback must take over; K spans three chunks and a tail
+    X = 127 * (256 ** 6 - 1) // 255
+    x = float(X) / 2.0 ** 46
+    assert float(X) == X and 1.0 <= x < 2.0
+    e = "C[m,n] = A[k,m] * B[k,n]"
+    M, N, K = 130, 100, 500
+    sa = np.where(synth.integers(27, 0, K * M, 0, 9) < 2, -1.0, 1.0).reshape((K, M), order="F")
+    A = np.asfortranarray(x * sa)
+    B = np.asfortranarray(np.full((K, N), x))
+    C, _ = run(comet, e, dict(m=M, n=N, k=K), [A, B], np.float64, precision=PREC)
+    ref = oracle.einsum(e, A, B)
+    assert normwise(C, ref) <= TOL
+    # about 80 % of the signs positive: the sums stay large (net 0.6 K of same-sign products)
+    assert np.abs(ref).max() >= 0.5 * K * x * x
+
+
 def test_ccsd_like_full_size_sampled(comet):
     e = "C[i,a,j,b] = A[k,a,c,i] * B[c,b,k,j]"
     ext = dict(i=64, j=64, k=64, a=192, b=192, c=192)
