@@ -419,6 +419,314 @@ __global__ void __launch_bounds__(NT, 3) triples_kernel(const Args a) {
     if (have) flush(b);
 }
 
+// ---------------------------------------------------------------------------------------------
+// FP32: one CTA of 64 threads per 4^6 tile, 2^6 elements per thread (triples.h).  Every term is
+// then an 8 x 8 outer product per summed index whatever labels its operands hold: the thread
+// reads its 8 entries of each operand as four 16-byte shared-memory loads and does 64 FMAs as
+// 32 packed ones.  (The 256-thread layout above holds 4 x 4 along two labels: a term with both on
+// one operand reads 16 + 1 entries for 16 FMAs, and the kernel is bound by shared-memory
+// wavefronts.)
+
+// the three bits of v placed at the set bits of m, lowest first
+__host__ __device__ constexpr int deposit3(int v, int m) {
+    int r = 0, b = 0;
+    for (int j = 0; j < 6; ++j)
+        if ((m >> j) & 1) {
+            if ((v >> b) & 1) r |= 1 << j;
+            ++b;
+        }
+    return r;
+}
+template <int M>
+struct DepTab {
+    int v[8];
+    constexpr DepTab() : v() {
+        for (int i = 0; i < 8; ++i) v[i] = deposit3(i, M);
+    }
+};
+
+// the bits of t at the set bits of m, packed from bit 0
+__device__ __forceinline__ int extract6(int t, int m) {
+    int r = 0, b = 0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+        if ((m >> j) & 1) {
+            r |= ((t >> j) & 1) << b;
+            ++b;
+        }
+    return r;
+}
+
+// staging addressing of one operand for a tile: element offset of the tile's corner at k0 = 0,
+// stride of the summed label, and per rank i (the operand's T labels in T order) the stride and
+// the entries left in the tile (at most 4)
+struct StageAddr {
+    int base, sd, s[3], rem[3];
+};
+
+__device__ __forceinline__ StageAddr stage_addr(const int8_t *q, const int8_t *col, const int8_t *rank,
+                                                const int32_t *ext_b, const int *tbase, const int *text) {
+    StageAddr sa;
+    int st = 1;
+    sa.base = 0;
+    sa.sd = 0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        if (q[m] < 0) {
+            sa.sd = st;
+        } else {
+            const int b0 = tbase[q[m]];
+            const int rm = min(TS, text[q[m]] - b0);
+            sa.base += b0 * st;
+            if (rank[m] == 0) { sa.s[0] = st; sa.rem[0] = rm; }
+            if (rank[m] == 1) { sa.s[1] = st; sa.rem[1] = rm; }
+            if (rank[m] == 2) { sa.s[2] = st; sa.rem[2] = rm; }
+        }
+        st *= ext_b[col[m]];
+    }
+    return sa;
+}
+
+// coordinates of the entry of staged row r along the operand's rank-i label
+__device__ __forceinline__ int row_coord(int r, int i) { return 2 * ((r >> (3 + i)) & 1) + ((r >> i) & 1); }
+
+// thread t copies row t of the operand tile for summed indices k0 .. k0 + kn - 1 (rows outside
+// the tile are not written: they only feed elements outside the block, which the energy skips)
+__device__ __forceinline__ void stage32(float (*S)[RP32], const float *__restrict__ src, const StageAddr &sa, int k0,
+                                        int kn) {
+    const int r = (int)threadIdx.x;
+    const int c0 = row_coord(r, 0), c1 = row_coord(r, 1), c2 = row_coord(r, 2);
+    if (c0 >= sa.rem[0] || c1 >= sa.rem[1] || c2 >= sa.rem[2]) return;
+    const float *g = src + (sa.base + k0 * sa.sd + c0 * sa.s[0] + c1 * sa.s[1] + c2 * sa.s[2]);
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(&S[0][r]);
+#pragma unroll 4
+    for (int kk = 0; kk < kn; ++kk)
+        cp_async_elem(dst + (unsigned)(kk * RP32 * 4), g + (int64_t)kk * sa.sd, 4);
+}
+
+// alpha times the entries this thread copied (after their copies completed)
+__device__ __forceinline__ void scale32(float (*S)[RP32], const StageAddr &sa, int kn, float alpha) {
+    const int r = (int)threadIdx.x;
+    if (row_coord(r, 0) >= sa.rem[0] || row_coord(r, 1) >= sa.rem[1] || row_coord(r, 2) >= sa.rem[2]) return;
+    for (int kk = 0; kk < kn; ++kk) S[kk][r] *= alpha;
+}
+
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t bcast2(float x) {
+    uint64_t d;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(d) : "f"(x));
+    return d;
+}
+
+// The 64 accumulators as 32 packed pairs: acc[e >> 1] holds elements e (low 32 bits) and e + 1,
+// which differ in the low bit of T label 0.  Each packed FMA is two fmaf roundings.
+//
+// One step of a term: P holds the operand with T label 0 (its labels: mask MP; label 0 is its
+// rank 0, so entries 2m and 2m + 1 of the thread's run form a natural pair), B the other one,
+// whose values are broadcast to both halves.  Element e gains P[kk][8 hp + p(e)] *
+// B[kk][8 hb + b(e)], p(e) / b(e) = the bits of e at the labels of P / B.
+template <int MP>
+__device__ __forceinline__ void outer32(const float (*P)[RP32], const float (*B)[RP32], int kn, int hp, int hb,
+                                        uint64_t (&acc)[32]) {
+    constexpr DepTab<MP> dp{};
+    constexpr DepTab<63 & ~MP> db{};
+    const float *pp = &P[0][8 * hp];
+    const float *bp = &B[0][8 * hb];
+#pragma unroll 1
+    for (int kk = 0; kk < kn; ++kk) {
+        const ulonglong2 p0 = *reinterpret_cast<const ulonglong2 *>(pp + kk * RP32);
+        const ulonglong2 p1 = *reinterpret_cast<const ulonglong2 *>(pp + kk * RP32 + 4);
+        const float4 b0 = *reinterpret_cast<const float4 *>(bp + kk * RP32);
+        const float4 b1 = *reinterpret_cast<const float4 *>(bp + kk * RP32 + 4);
+        const uint64_t pr[4] = {p0.x, p0.y, p1.x, p1.y};
+        const uint64_t bb[8] = {bcast2(b0.x), bcast2(b0.y), bcast2(b0.z), bcast2(b0.w),
+                                bcast2(b1.x), bcast2(b1.y), bcast2(b1.z), bcast2(b1.w)};
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+#pragma unroll
+            for (int bi = 0; bi < 8; ++bi) {
+                const int e2 = (dp.v[2 * m] | db.v[bi]) >> 1;
+                acc[e2] = fma2(pr[m], bb[bi], acc[e2]);
+            }
+    }
+}
+
+// the ten three-label masks that hold label 0
+__device__ __forceinline__ void outer32_dispatch(int mp, const float (*P)[RP32], const float (*B)[RP32], int kn,
+                                                 int hp, int hb, uint64_t (&acc)[32]) {
+    switch (mp) {
+#define COMET_TRI_M(v) \
+    case v: outer32<v>(P, B, kn, hp, hb, acc); break;
+        COMET_TRI_M(7) COMET_TRI_M(11) COMET_TRI_M(13) COMET_TRI_M(19) COMET_TRI_M(21)
+        COMET_TRI_M(25) COMET_TRI_M(35) COMET_TRI_M(37) COMET_TRI_M(41) COMET_TRI_M(49)
+#undef COMET_TRI_M
+        default: break;   // the planner gives every operand three T labels
+    }
+}
+
+__global__ void __launch_bounds__(NT32, CTAS32) triples_f32_kernel(const Args a) {
+    __shared__ __align__(16) float Ps[2][KC32][RP32];   // the operand holding T label 0
+    __shared__ __align__(16) float Bs[2][KC32][RP32];   // the other one
+    __shared__ int32_t s_ext[16];
+    __shared__ int64_t s_item;
+    __shared__ double s_red[NT32 / 32];
+    __shared__ StageAddr s_sa[16][2];     // per term of the current tile: X and Y
+    __shared__ const void *s_ops[32];     // the current block's operand pointers
+    __shared__ int s_tile[2][12];         // tile bases and block extents per T label, two items
+    const int t = threadIdx.x;
+
+    int b = 0;                 // current block
+    double e_acc = 0.0;
+    auto flush = [&](int blk) {   // CTA sum of e_acc into E[blk]
+        double v = e_acc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((t & 31) == 0) s_red[t >> 5] = v;
+        __syncthreads();
+        if (t == 0) {
+            double sum = 0;
+            for (int w = 0; w < NT32 / 32; ++w) sum += s_red[w];
+            if (sum != 0.0) atomicAdd(a.energies + blk, sum);
+        }
+        __syncthreads();
+        e_acc = 0.0;
+    };
+    bool have = false;
+    int slot = 0;
+    while (true) {
+        if (t == 0) s_item = (int64_t)atomicAdd(a.counter, (unsigned long long)CHUNK);
+        __syncthreads();
+        const int64_t first = s_item;
+        __syncthreads();
+        if (first >= a.total) break;
+        const int64_t last = min(first + (int64_t)CHUNK, a.total);
+        for (int64_t item = first; item < last; ++item) {
+            int nb = b;
+            if (item < a.prefix[nb]) nb = 0;
+            if (item >= a.prefix[nb + 1]) {
+                int lo = nb, hi = a.n_blocks;   // prefix[lo] <= item < prefix[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (a.prefix[mid] <= item) lo = mid; else hi = mid;
+                }
+                nb = lo;
+            }
+            if (!have || nb != b) {
+                if (have) flush(b);
+                b = nb;
+                have = true;
+                if (t < a.n_labels) s_ext[t] = a.ext[(int64_t)b * a.n_labels + t];
+                if (t < 2 * a.n_terms) s_ops[t] = a.ops[(int64_t)b * a.n_terms * 2 + t];
+                __syncthreads();
+            }
+            const int *tbase = s_tile[slot], *text = s_tile[slot] + 6;
+            if (t == 0) {
+                int rem = (int)(item - a.prefix[b]);
+                for (int q = 0; q < 6; ++q) {
+                    const int e = s_ext[a.t_col[q]];
+                    const int nt = (e + TS - 1) / TS;
+                    const int qt = rem / nt;
+                    s_tile[slot][q] = (rem - qt * nt) * TS;
+                    s_tile[slot][6 + q] = e;
+                    rem = qt;
+                }
+            }
+            slot ^= 1;
+            __syncthreads();   // the previous item's steps are done with both buffers and s_sa
+            if (t < 2 * a.n_terms) {
+                const TermDev &tm = a.term[t >> 1];
+                s_sa[t >> 1][t & 1] = (t & 1) ? stage_addr(tm.y_q, tm.y_col, tm.y_rank, s_ext, tbase, text)
+                                              : stage_addr(tm.x_q, tm.x_col, tm.x_rank, s_ext, tbase, text);
+            }
+            __syncthreads();
+            // a thread whose 2^6 box lies outside the block along some label (the ragged last
+            // tile) still copies and meets every barrier, but skips the products
+            bool live = true;
+#pragma unroll
+            for (int j = 0; j < 6; ++j) live &= tbase[j] + 2 * ((t >> j) & 1) < text[j];
+            uint64_t acc[32];
+#pragma unroll
+            for (int e = 0; e < 32; ++e) acc[e] = 0ull;
+            int p = 0, k0 = 0, buf = 0;
+            auto issue = [&](int pp, int kk0, int bb) {
+                const int K = s_ext[a.term[pp].d_col];
+                const int kn = min(KC32, K - kk0);
+                const int sp = (a.term[pp].xmask & 1) ? 0 : 1;   // operand holding T label 0
+                stage32(Ps[bb], reinterpret_cast<const float *>(s_ops[2 * pp + sp]), s_sa[pp][sp], kk0, kn);
+                stage32(Bs[bb], reinterpret_cast<const float *>(s_ops[2 * pp + 1 - sp]), s_sa[pp][1 - sp], kk0, kn);
+                cp_async_commit();
+            };
+            issue(0, 0, 0);
+            while (p < a.n_terms) {
+                const int K = s_ext[a.term[p].d_col];
+                const int kn = min(KC32, K - k0);
+                int pn = p, kn0 = k0 + KC32;   // next step
+                if (kn0 >= K) { pn = p + 1; kn0 = 0; }
+                cp_async_wait_all();
+                // alpha other than 1 scales the term's X entries (alpha = -1 exactly: the sums
+                // are the negated ones in every rounding)
+                if (a.term[p].amode != 0) {
+                    scale32((a.term[p].xmask & 1) ? Ps[buf] : Bs[buf], s_sa[p][0], kn, (float)a.term[p].alpha);
+                }
+                __syncthreads();   // step s is in buffer buf; step s-1's reads of buf^1 are done
+                if (pn < a.n_terms) issue(pn, kn0, buf ^ 1);
+                if (live) {
+                    const int m = a.term[p].xmask;
+                    const int mp = (m & 1) ? m : 63 & ~m;
+                    outer32_dispatch(mp, Ps[buf], Bs[buf], kn, extract6(t, mp), extract6(t, 63 & ~mp), acc);
+                }
+                p = pn;
+                k0 = kn0;
+                buf ^= 1;
+            }
+            // energy: D = sum_j sign_j eps_j[coordinate j], element e at coordinate tbase_j +
+            // 2 h_j + (bit j of e); FP32 T^2 / D summed in FP32 over 16 elements, then in FP64
+            if (live) {
+                float ev[6][2];
+                int ok[6];   // bit l: coordinate 2 h_j + l lies inside the block
+#pragma unroll
+                for (int j = 0; j < 6; ++j) {
+                    const float *ej = reinterpret_cast<const float *>(a.eps[(int64_t)b * 6 + j]);
+                    ok[j] = 0;
+#pragma unroll
+                    for (int l = 0; l < 2; ++l) {
+                        const int c = tbase[j] + 2 * ((t >> j) & 1) + l;
+                        const bool in = c < text[j];
+                        ok[j] |= (int)in << l;
+                        ev[j][l] = in ? a.sign[j] * ej[c] : 0.f;
+                    }
+                }
+                float d012[8], d345[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    d012[e] = (ev[0][e & 1] + ev[1][(e >> 1) & 1]) + ev[2][e >> 2];
+                    d345[e] = (ev[3][e & 1] + ev[4][(e >> 1) & 1]) + ev[5][e >> 2];
+                }
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    float part = 0.f;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int e = g * 16 + i;
+                        bool in = true;
+#pragma unroll
+                        for (int j = 0; j < 6; ++j) in &= ((ok[j] >> ((e >> j) & 1)) & 1) != 0;
+                        const float te = __uint_as_float((uint32_t)((e & 1) ? acc[e >> 1] >> 32 : acc[e >> 1]));
+                        const float v = te * te / (d012[e & 7] + d345[e >> 3]);
+                        part += in ? v : 0.f;
+                    }
+                    e_acc += (double)part;
+                }
+            }
+        }
+    }
+    if (have) flush(b);
+}
+
 }  // namespace comet
 
 using namespace comet;
@@ -492,8 +800,12 @@ comet_status_t comet_triples_energy(comet_plan_t plan, const void *operands, con
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t grid = std::min<int64_t>((int64_t)sms * 4, (a.total + CHUNK - 1) / CHUNK);
     int h = prof_begin(PK_TRIPLES_ID, s);
-    if (P.dtype == COMET_F32) triples_kernel<float><<<(unsigned)grid, NT, 0, s>>>(a);
-    else triples_kernel<double><<<(unsigned)grid, NT, 0, s>>>(a);
+    if (P.dtype == COMET_F32) {
+        const int64_t grid32 = std::min<int64_t>((int64_t)sms * CTAS32, (a.total + CHUNK - 1) / CHUNK);
+        triples_f32_kernel<<<(unsigned)grid32, NT32, 0, s>>>(a);
+    } else {
+        triples_kernel<double><<<(unsigned)grid, NT, 0, s>>>(a);
+    }
     e = cudaGetLastError();
     prof_end(h, s);
     if (e != cudaSuccess) { set_error_message(cudaGetErrorString(e)); return COMET_ERR_CUDA; }

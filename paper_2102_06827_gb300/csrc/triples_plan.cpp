@@ -178,6 +178,7 @@ void triples_args(const Plan &P, Args *out) {
         a.own[j] = (int8_t)tp.own[j];
         a.own_sign[j] = (float)tp.signs[tp.own[j]];
     }
+    for (int q = 0; q < 6; ++q) a.sign[q] = (float)tp.signs[q];
     for (int p = 0; p < tp.n_terms; ++p) {
         const TriTerm &tt = tp.terms[p];
         a.term[p].alpha = tt.alpha;
@@ -189,6 +190,20 @@ void triples_args(const Plan &P, Args *out) {
             a.term[p].y_col[m] = (int8_t)tt.y_col[m];
         }
         a.term[p].d_col = (int8_t)tt.d_col;
+        int xmask = 0;
+        for (int m = 0; m < 4; ++m) if (tt.x_q[m] >= 0) xmask |= 1 << tt.x_q[m];
+        a.term[p].xmask = (int8_t)xmask;
+        for (int side = 0; side < 2; ++side) {   // rank of each dimension's T label in T order
+            const int *q = side ? tt.y_q : tt.x_q;
+            int8_t *rk = side ? a.term[p].y_rank : a.term[p].x_rank;
+            for (int m = 0; m < 4; ++m) {
+                rk[m] = -1;
+                if (q[m] < 0) continue;
+                int r = 0;
+                for (int n = 0; n < 4; ++n) r += q[n] >= 0 && q[n] < q[m];
+                rk[m] = (int8_t)r;
+            }
+        }
         // tile digits: the owned labels an operand holds come first (own[0], then own[1]), so
         // that they run along consecutive shared-memory entries; then its fixed labels
         for (int side = 0; side < 2; ++side) {

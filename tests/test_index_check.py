@@ -37,9 +37,10 @@ def test_batched_tc_index_arithmetic_replay(tmp_path):
 
 
 def test_triples_index_arithmetic_replay(tmp_path):
-    # the fused triples kernel's staging, shared loads and eps reads, on the workload's nine
-    # terms, for the largest block of the 4096-block table, the largest of the 64 blocks the
-    # FP64 leg runs, and a small ragged block
+    # the fused triples kernels' staging, shared loads, element-to-entry mapping and eps reads,
+    # on the workload's nine terms, for the largest block of the 4096-block table, the largest
+    # of the 64 blocks the FP64 leg runs, a small ragged block, a block of extent 1 everywhere
+    # and one with every remainder mod 4 and a summed label of two FP32 passes
     import numpy as np
     import synth
     from triples_terms import LABELS, SIGNS, terms
@@ -52,7 +53,8 @@ def test_triples_index_arithmetic_replay(tmp_path):
     assert r.returncode == 0, r.stderr
     ext = synth.triples_blocks(4096)
     size = np.prod(ext[:, :6], axis=1)
-    rows = [ext[int(np.argmax(size))], ext[int(np.argmax(size[:64]))], np.array([6, 5, 7, 4, 6, 5, 9])]
+    rows = [ext[int(np.argmax(size))], ext[int(np.argmax(size[:64]))], np.array([6, 5, 7, 4, 6, 5, 9]),
+            np.ones(7, dtype=np.int64), np.array([9, 10, 11, 13, 2, 3, 40])]
     tl = terms()
     for row in rows:
         args = [exe, str(len(tl))] + tl + LABELS + [str(s) for s in SIGNS] + [str(int(x)) for x in row]

@@ -1,7 +1,20 @@
-// CPU replay of the index arithmetic of the fused triples kernel (k_triples.cu, thread tiles of
-// 4 x 4) on the argument block the real host code builds (triples_plan.cpp), for FP32 (32
-// summed values per step) and FP64 (16).  Terms, labels, signs and one block's extents come
-// from the command line: argv = n_terms, the terms, the 7 label names, 6 signs, 7 extents.
+// CPU replay of the index arithmetic of the fused triples kernels (k_triples.cu) on the argument
+// block the real host code builds (triples_plan.cpp): the FP64 kernel (256 threads, thread tiles
+// of 4 x 4, 16 summed values per step) and the FP32 kernel (64 threads, 2^6 elements per
+// thread, 32 summed values per step).  Terms, labels, signs and one block's extents come from
+// the command line: argv = n_terms, the terms, the 7 label names, 6 signs, 7 extents.
+// FP32 kernel, for every term, thread and a set of tiles that includes the first and the ragged
+// last tile along every label:
+//   - thread r stages row r of each operand tile (rows inside the block only) from the operand
+//     elements at the row's coordinates (global reads inside the operand): the operand holding
+//     T label 0 into P [16][64], the other one into B [16][64];
+//   - for every element inside the block, the X and Y entries the products read (row 8 h + x of
+//     the thread's group) are the ones staged from the operands at that element's coordinates,
+//     and the 64 (x, y) pairs of a summed index cover the thread's 64 elements once each; the
+//     packed accumulator pairs (e, e + 1) take entries 2m and 2m + 1 of the operand holding T
+//     label 0;
+//   - the 16-byte shared loads start on 16-byte boundaries and stay in the tile.
+// FP64 kernel:
 // For every thread, every term and a set of tiles that includes the first and the ragged last
 // tile along every label, it checks:
 //   - the staging entries (kk, r) of stage_async stay inside the [kc][RP] shared tile, and the
@@ -139,6 +152,166 @@ static void replay(const Args &a, const int32_t *ext_b, int elem) {
     }
 }
 
+// ---- FP32 kernel ----------------------------------------------------------------------------
+static int deposit3(int v, int m) {
+    int r = 0, b = 0;
+    for (int j = 0; j < 6; ++j)
+        if ((m >> j) & 1) { if ((v >> b) & 1) r |= 1 << j; ++b; }
+    return r;
+}
+static int extract6(int t, int m) {
+    int r = 0, b = 0;
+    for (int j = 0; j < 6; ++j)
+        if ((m >> j) & 1) { r |= ((t >> j) & 1) << b; ++b; }
+    return r;
+}
+static int row_coord(int r, int i) { return 2 * ((r >> (3 + i)) & 1) + ((r >> i) & 1); }
+
+struct SA { int base, sd, s[3], rem[3]; int64_t n_elems; };
+
+// the kernel's stage_addr(), with the element count of the operand
+static SA stage_addr(const int8_t *q, const int8_t *col, const int8_t *rank, const int32_t *ext_b, const int *tbase,
+                     const int *text) {
+    SA sa{};
+    int st = 1;
+    for (int m = 0; m < 4; ++m) {
+        if (q[m] < 0) sa.sd = st;
+        else {
+            const int b0 = tbase[q[m]];
+            sa.base += b0 * st;
+            CHECK(rank[m] >= 0 && rank[m] < 3, "rank of a T label");
+            sa.s[rank[m]] = st;
+            sa.rem[rank[m]] = std::min(TS, text[q[m]] - b0);
+        }
+        st *= ext_b[col[m]];
+    }
+    sa.n_elems = st;
+    return sa;
+}
+
+// element offset of an operand entry from the T coordinates (absolute) and the summed index
+static int64_t direct_offset(const int8_t *q, const int8_t *col, const int32_t *ext_b, const int *coord, int k) {
+    int64_t off = 0, st = 1;
+    for (int m = 0; m < 4; ++m) {
+        off += (int64_t)(q[m] < 0 ? k : coord[q[m]]) * st;
+        st *= ext_b[col[m]];
+    }
+    return off;
+}
+
+static void replay32(const Args &a, const int32_t *ext_b) {
+    static_assert(NT32 == 64 && ROW32 == 64 && RP32 >= ROW32 && (RP32 * 4) % 16 == 0, "FP32 kernel geometry");
+    int text[6], ntile[6];
+    for (int q = 0; q < 6; ++q) {
+        text[q] = ext_b[a.t_col[q]];
+        ntile[q] = (text[q] + TS - 1) / TS;
+    }
+    for (int mask = 0; mask < 64; ++mask) {
+        int tbase[6];
+        for (int q = 0; q < 6; ++q) tbase[q] = ((mask >> q) & 1) ? (ntile[q] - 1) * TS : 0;
+        for (int p = 0; p < a.n_terms; ++p) {
+            const TermDev &tm = a.term[p];
+            const int K = ext_b[tm.d_col];
+            const int M = tm.xmask;
+            int pc = 0;
+            for (int j = 0; j < 6; ++j) pc += (M >> j) & 1;
+            CHECK(pc == 3 && (M & ~63) == 0, "X mask of term %d", p);
+            // the 64 (x, y) pairs cover the 64 elements once
+            std::vector<int> cnt(64, 0);
+            for (int xi = 0; xi < 8; ++xi)
+                for (int yi = 0; yi < 8; ++yi) ++cnt[deposit3(xi, M) | deposit3(yi, 63 & ~M)];
+            for (int e = 0; e < 64; ++e) CHECK(cnt[e] == 1, "element %d covered %d times (term %d)", e, cnt[e], p);
+            // packed pairs: the operand holding T label 0 gives entries (2m, 2m + 1) of its run;
+            // with the other operand's entry bi they feed accumulator pair (e, e + 1), e even
+            {
+                const int MP = (M & 1) ? M : 63 & ~M;
+                for (int m = 0; m < 4; ++m)
+                    for (int bi = 0; bi < 8; ++bi) {
+                        const int lo = deposit3(2 * m, MP) | deposit3(bi, 63 & ~MP);
+                        const int hi = deposit3(2 * m + 1, MP) | deposit3(bi, 63 & ~MP);
+                        CHECK((lo & 1) == 0 && hi == lo + 1, "packed pair (term %d, m %d, b %d)", p, m, bi);
+                    }
+            }
+            SA sa[2];
+            sa[0] = stage_addr(tm.x_q, tm.x_col, tm.x_rank, ext_b, tbase, text);
+            sa[1] = stage_addr(tm.y_q, tm.y_col, tm.y_rank, ext_b, tbase, text);
+            for (int k0 = 0; k0 < K; k0 += KC32) {
+                const int kn = std::min(KC32, K - k0);
+                // staging, as stage32 does it: thread r copies row r for kk < kn
+                bool staged[2][ROW32];
+                int64_t soff[2][ROW32];
+                for (int side = 0; side < 2; ++side) {
+                    const SA &x = sa[side];
+                    const int8_t *q = side ? tm.y_q : tm.x_q, *col = side ? tm.y_col : tm.x_col;
+                    for (int r = 0; r < NT32; ++r) {
+                        const int c0 = row_coord(r, 0), c1 = row_coord(r, 1), c2 = row_coord(r, 2);
+                        staged[side][r] = c0 < x.rem[0] && c1 < x.rem[1] && c2 < x.rem[2];
+                        soff[side][r] = (int64_t)x.base + (int64_t)k0 * x.sd + (int64_t)c0 * x.s[0] +
+                                        (int64_t)c1 * x.s[1] + (int64_t)c2 * x.s[2];
+                        if (!staged[side][r]) continue;
+                        CHECK(r < ROW32 && kn <= KC32 && (int64_t)(kn - 1) * RP32 + r < (int64_t)KC32 * RP32,
+                              "shared entry beyond the tile");
+                        int coord[6] = {0, 0, 0, 0, 0, 0};
+                        for (int m = 0; m < 4; ++m)
+                            if (q[m] >= 0) {
+                                const int rk = (side ? tm.y_rank : tm.x_rank)[m];
+                                coord[q[m]] = tbase[q[m]] + row_coord(r, rk);
+                            }
+                        for (int kk = 0; kk < kn; ++kk) {
+                            const int64_t g = soff[side][r] + (int64_t)kk * x.sd;
+                            CHECK(g >= 0 && g < x.n_elems, "global read outside the operand (term %d side %d)", p, side);
+                            CHECK(g == direct_offset(q, col, ext_b, coord, k0 + kk),
+                                  "entry (%d, %d) staged from the wrong element (term %d side %d)", kk, r, p, side);
+                        }
+                    }
+                }
+                // products: every element inside the block reads the entries at its coordinates
+                for (int t = 0; t < NT32; ++t) {
+                    bool live = true;
+                    for (int j = 0; j < 6; ++j) live &= tbase[j] + 2 * ((t >> j) & 1) < text[j];
+                    if (!live) continue;
+                    const int hx = extract6(t, M), hy = extract6(t, 63 & ~M);
+                    // the operand holding T label 0 is read from P, the other one from B (8
+                    // entries at 8 h each)
+                    const int MP = (M & 1) ? M : 63 & ~M;
+                    const int hp = extract6(t, MP), hb = extract6(t, 63 & ~MP);
+                    CHECK((8 * hp * 4) % 16 == 0 && (RP32 * 4) % 16 == 0 &&
+                          (int64_t)(kn - 1) * RP32 + 8 * hp + 8 <= (int64_t)KC32 * RP32, "P loads of thread %d", t);
+                    CHECK((8 * hb * 4) % 16 == 0 &&
+                          (int64_t)(kn - 1) * RP32 + 8 * hb + 8 <= (int64_t)KC32 * RP32, "B loads of thread %d", t);
+                    CHECK(hp == ((M & 1) ? hx : hy) && hb == ((M & 1) ? hy : hx), "operand groups of thread %d", t);
+                    for (int xi = 0; xi < 8; ++xi)
+                        for (int yi = 0; yi < 8; ++yi) {
+                            const int e = deposit3(xi, M) | deposit3(yi, 63 & ~M);
+                            int coord[6];
+                            bool in = true;
+                            for (int j = 0; j < 6; ++j) {
+                                coord[j] = tbase[j] + 2 * ((t >> j) & 1) + ((e >> j) & 1);
+                                in &= coord[j] < text[j];
+                            }
+                            if (!in) continue;
+                            for (int side = 0; side < 2; ++side) {
+                                const int row = side ? 8 * hy + yi : 8 * hx + xi;
+                                CHECK(staged[side][row], "element reads an unstaged row (term %d side %d)", p, side);
+                                const int64_t want = direct_offset(side ? tm.y_q : tm.x_q, side ? tm.y_col : tm.x_col,
+                                                                   ext_b, coord, k0);
+                                CHECK(soff[side][row] == want, "row %d holds the wrong entry (term %d side %d)", row, p,
+                                      side);
+                            }
+                        }
+                }
+            }
+        }
+        // energy: eps reads at coordinates inside the block
+        for (int t = 0; t < NT32; ++t)
+            for (int j = 0; j < 6; ++j)
+                for (int l = 0; l < 2; ++l) {
+                    const int c = tbase[j] + 2 * ((t >> j) & 1) + l;
+                    if (c < text[j]) CHECK(c >= 0, "eps read");
+                }
+    }
+}
+
 int main(int argc, char **argv) {
     if (argc < 2) { std::printf("usage\n"); return 2; }
     const int nt = std::atoi(argv[1]);
@@ -160,7 +333,8 @@ int main(int argc, char **argv) {
         Args a;
         std::memset(&a, 0, sizeof(a));
         triples_args(P, &a);
-        replay(a, P.tri.ext.data(), e);
+        if (e == 4) replay32(a, P.tri.ext.data());
+        else replay(a, P.tri.ext.data(), e);
     }
     std::printf("%d failures\n", fails);
     return fails ? 1 : 0;
