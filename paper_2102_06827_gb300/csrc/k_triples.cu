@@ -25,6 +25,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -44,6 +45,9 @@ struct comet_plan_s {
 
 namespace comet {
 
+// the FP32 tensor-core launch sequence (k_triples_tc.cu): per batch, the split pre-pass and the
+// main kernel; a carries the device pointers, t the workspace tables and the status word
+cudaError_t launch_triples_tc(const Plan &P, const tri::Args &a, tri::TcArgs t, cudaStream_t s);
 int prof_begin(int kind, cudaStream_t s);
 void prof_end(int idx, cudaStream_t s);
 void set_error_message(const std::string &s);
@@ -769,6 +773,15 @@ comet_status_t comet_triples_prepare(comet_plan_t plan, void *workspace, void *s
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(w + P.tri.ws_prefix, P.tri.prefix.data(), P.tri.prefix.size() * sizeof(int64_t),
                             cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !P.tri.tc_batch.empty())
+        e = cudaMemcpyAsync(w + P.tri.ws_tc_prefix, P.tri.tc_prefix.data(), P.tri.tc_prefix.size() * sizeof(int64_t),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !P.tri.tc_batch.empty())
+        e = cudaMemcpyAsync(w + P.tri.ws_tc_row0, P.tri.tc_row0.data(), P.tri.tc_row0.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !P.tri.tc_batch.empty())
+        e = cudaMemcpyAsync(w + P.tri.ws_tc_rec, P.tri.tc_rec.data(), P.tri.tc_rec.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host tables may go away after the call
     if (e != cudaSuccess) { set_error_message(cudaGetErrorString(e)); return COMET_ERR_CUDA; }
     return COMET_OK;
@@ -800,7 +813,28 @@ comet_status_t comet_triples_energy(comet_plan_t plan, const void *operands, con
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t grid = std::min<int64_t>((int64_t)sms * 4, (a.total + CHUNK - 1) / CHUNK);
     int h = prof_begin(PK_TRIPLES_ID, s);
-    if (P.dtype == COMET_F32) {
+    if (P.dtype == COMET_F32 && !tp.tc_batch.empty()) {
+        TcArgs t;
+        t.prefix = reinterpret_cast<const int64_t *>(w + tp.ws_tc_prefix);
+        t.row0 = reinterpret_cast<const int32_t *>(w + tp.ws_tc_row0);
+        t.rec = reinterpret_cast<const TcRec *>(w + tp.ws_tc_rec);
+        t.planes = w + tp.ws_tc_planes;
+        t.b0 = t.b1 = 0;
+        t.item0 = t.n_items = 0;
+        t.status = device_status_word();
+        // limit of every wait: the plan's, else 2 s; COMET_WAIT_TIMEOUT_MS overrides it (a profiler
+        // that replays each kernel many times can stretch a wait past the default)
+        int64_t tmo_ms = P.opts.timeout_ms > 0 ? P.opts.timeout_ms : 2000;
+        if (const char *env = std::getenv("COMET_WAIT_TIMEOUT_MS")) {
+            const long long v = std::atoll(env);
+            if (v > 0) tmo_ms = v;
+        }
+        t.timeout_ns = tmo_ms * 1000000ll;
+        e = t.status ? launch_triples_tc(P, a, t, s) : cudaErrorInvalidValue;
+        prof_end(h, s);
+        if (e != cudaSuccess) { set_error_message(cudaGetErrorString(e)); return COMET_ERR_CUDA; }
+        return COMET_OK;
+    } else if (P.dtype == COMET_F32) {
         const int64_t grid32 = std::min<int64_t>((int64_t)sms * CTAS32, (a.total + CHUNK - 1) / CHUNK);
         triples_f32_kernel<<<(unsigned)grid32, NT32, 0, s>>>(a);
     } else {

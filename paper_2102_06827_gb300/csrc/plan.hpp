@@ -137,6 +137,15 @@ struct TriplesPlan {
     std::vector<int32_t> ext;            // n_blocks x n_labels
     std::vector<int64_t> prefix;         // tiles (4 per label) before each block; n_blocks + 1
     size_t ws_ext = 0, ws_prefix = 0, ws_counter = 0;
+    // FP32 plans, tensor-core path: pair-tiles (8 along T label 0, 4 along the others), blocks in
+    // batches whose split operand planes fit the workspace
+    std::vector<int64_t> tc_prefix;      // pair-tiles before each block; n_blocks + 1
+    std::vector<int32_t> tc_row0;        // n_blocks x n_terms x 2: first plane row of each operand in its batch
+    std::vector<int32_t> tc_rec;         // n_blocks x n_terms records of 16 words (tri::TcRec)
+    std::vector<int64_t> tc_rows;        // plane rows of each block (all its operands)
+    std::vector<int> tc_batch;           // first block of each batch, then n_blocks
+    int64_t tc_max_rows = 0;             // plane rows of the largest batch
+    size_t ws_tc_row0 = 0, ws_tc_prefix = 0, ws_tc_rec = 0, ws_tc_planes = 0;
 };
 
 struct Plan {

@@ -33,6 +33,36 @@ constexpr int ROW32 = 64;      // entries per staged row (4^3)
 constexpr int RP32 = ROW32;    // row pitch (a warp's staging writes are 32 consecutive entries)
 constexpr int CTAS32 = 8;      // resident CTAs per SM the FP32 kernel is built for
 
+// FP32 tensor-core path (k_triples_tc.cu).  A work item is a pair-tile of T: 8 values along T
+// label 0 and 4 along each other label.  For each term the operand holding label 0 gives 128
+// rows (8 x 4 x 4), the other one 64 (4 x 4 x 4); a pre-pass writes every operand as tile-
+// blocked split-BF16 planes (rows of 32 summed indices, 64 bytes, [tile][chunk][plane][row]),
+// and one 128 x 64 tcgen05 MMA tile per term and chunk accumulates the six products in tensor
+// memory; sixteen warps (four per lane quadrant) drain each term into the pair-tile in shared
+// memory, which then gives the energy.
+namespace tc {
+constexpr int WA = 8;              // pair-tile extent along T label 0
+constexpr int KCH = 32;            // summed indices per plane row
+constexpr int ROWB = 64;           // bytes per plane row
+constexpr int WROWS = 128;         // rows of the operand holding label 0 (8 x 4 x 4)
+constexpr int NROWS = 64;          // rows of the other operand (4 x 4 x 4)
+constexpr int BOX = 64;            // rows per TMA box
+constexpr int WPLANE = WROWS * ROWB, NPLANE = NROWS * ROWB;
+constexpr int SLOT = 3 * (WPLANE + NPLANE);   // one (term, chunk): three planes of both operands
+constexpr int RING = 3;
+constexpr int DRAIN_WARPS = 16;    // four per tensor-memory lane quadrant, 16 columns each
+constexpr int THREADS = 64 + 32 * DRAIN_WARPS;
+constexpr uint32_t TMEM_COLS = 128;   // two 64-column accumulators
+constexpr int TSZ = 10912;         // the pair-tile in shared memory (floats)
+// element strides of the pair-tile per T label: every label but 0 has a stride = 8 mod 32, so
+// the 32 rows a warp drains (8 along label 0 x 4 along one more label) hit 32 different banks
+constexpr int tstride(int q) {
+    return q == 0 ? 1 : q == 1 ? 8 : q == 2 ? 40 : q == 3 ? 168 : q == 4 ? 680 : 2728;
+}
+constexpr int64_t MAX_BATCH_ROWS = int64_t(1) << 27;   // plane rows per batch (8 GB)
+constexpr int SMEM = 1024 + RING * SLOT + 512;   // dynamic; the pair-tile is a static array
+}  // namespace tc
+
 struct TermDev {
     double alpha;
     int8_t x_q[4], y_q[4];     // T label position per operand dimension, -1 = summed label
@@ -61,6 +91,30 @@ struct Args {
     unsigned long long *counter;
     int64_t total;
 };
+
+// One term of one block on the tensor-core path: the plane rows of its two operand tiles for a
+// pair-tile with tile coordinates c[6] are row0[w] + sum_q coef[w][q] c[q] (w = 0: the operand
+// holding T label 0, 128 rows per tile; w = 1: the other one, 64), then + (chunk * 3 + plane) *
+// rows per tile.
+struct TcRec {
+    int32_t row0[2];
+    int32_t coef[2][6];
+    int32_t nch;               // chunks of 32 summed indices
+    int32_t ed;                // extent of the summed label
+};
+static_assert(sizeof(TcRec) == 64, "records are read as four 16-byte words");
+
+// the tensor-core path's launch arguments (one batch of blocks)
+struct TcArgs {
+    const int64_t *prefix;     // pair-tiles before each block; n_blocks + 1
+    const int32_t *row0;       // n_blocks x n_terms x 2: first plane row of each operand in its batch
+    const TcRec *rec;          // n_blocks x n_terms
+    char *planes;              // the batch's plane rows
+    int b0, b1;                // the batch's blocks
+    int64_t item0, n_items;    // its pair-tiles
+    int *status;               // device status word (a wait that ran out records COMET_ERR_TIMEOUT)
+    int64_t timeout_ns;        // limit of every wait
+};
 }  // namespace tri
 
 // the whole triples plan (host only): terms, owned pair, block table, prefix sums, workspace
@@ -70,5 +124,13 @@ comet_status_t plan_triples(const char *const *terms, int n_terms, const char *c
 
 // the kernel's argument block from a plan (every field but the device pointers and the total)
 void triples_args(const Plan &P, tri::Args *a);
+
+// the FP32 tensor-core layout of a plan: pair-tile prefix, batches, plane rows of every operand
+// (no batches when some block's planes exceed one batch: the FMA kernel then runs the plan)
+void plan_triples_tc(Plan *P);
+
+// plane rows of one operand of a block: tiles x chunks x 3 planes x rows per tile
+// (q: T label per operand dimension, -1 = the summed label)
+int64_t tc_operand_rows(const int *q, const int64_t *ext_t, int64_t ext_d);
 
 }  // namespace comet

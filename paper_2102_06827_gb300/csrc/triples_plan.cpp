@@ -140,12 +140,113 @@ comet_status_t plan_triples(const char *const *terms, int n_terms, const char *c
     off = align(off + 8);
     P->triples = true;
     P->batched = false;
+    if (dtype == COMET_F32) plan_triples_tc(P);
+    if (!tp.tc_batch.empty()) {
+        off = align(off);
+        tp.ws_tc_prefix = off;
+        off = align(off + tp.tc_prefix.size() * sizeof(int64_t));
+        tp.ws_tc_row0 = off;
+        off = align(off + tp.tc_row0.size() * sizeof(int32_t));
+        tp.ws_tc_rec = off;
+        off = align(off + tp.tc_rec.size() * sizeof(int32_t));
+        tp.ws_tc_planes = off;
+        off = align(off + (size_t)tp.tc_max_rows * tc::ROWB);
+    }
     P->workspace = off;
     P->dtype = dtype;
     P->flops = flops;
     P->flops_natural = flops;
     P->expr = all.str();
     return COMET_OK;
+}
+
+int64_t tc_operand_rows(const int *q, const int64_t *ext_t, int64_t ext_d) {
+    int64_t tiles = 1;
+    bool wide = false;
+    for (int m = 0; m < 4; ++m) {
+        if (q[m] < 0) continue;
+        const int64_t ts = q[m] == 0 ? tc::WA : TS;
+        tiles *= (ext_t[q[m]] + ts - 1) / ts;
+        wide |= q[m] == 0;
+    }
+    const int64_t chunks = (ext_d + tc::KCH - 1) / tc::KCH;
+    return tiles * chunks * 3 * (wide ? tc::WROWS : tc::NROWS);
+}
+
+void plan_triples_tc(Plan *P) {
+    TriplesPlan &tp = P->tri;
+    const int nb = tp.n_blocks, nt = tp.n_terms, nl = tp.n_labels;
+    tp.tc_prefix.assign(nb + 1, 0);
+    tp.tc_row0.assign((size_t)nb * nt * 2, 0);
+    tp.tc_rows.assign(nb, 0);
+    tp.tc_rec.clear();
+    tp.tc_rec.reserve((size_t)nb * nt * 16);
+    tp.tc_batch.clear();
+    tp.tc_max_rows = 0;
+    int64_t batch_rows = 0;
+    for (int b = 0; b < nb; ++b) {
+        int64_t ext_t[6];
+        for (int q = 0; q < 6; ++q) ext_t[q] = tp.ext[(size_t)b * nl + tp.t_col[q]];
+        int64_t items = (ext_t[0] + tc::WA - 1) / tc::WA;
+        for (int q = 1; q < 6; ++q) items *= (ext_t[q] + TS - 1) / TS;
+        tp.tc_prefix[b + 1] = tp.tc_prefix[b] + items;
+        int64_t rows = 0;
+        for (int p = 0; p < nt; ++p) {
+            const TriTerm &tt = tp.terms[p];
+            const int64_t ed = tp.ext[(size_t)b * nl + tt.d_col];
+            rows += tc_operand_rows(tt.x_q, ext_t, ed) + tc_operand_rows(tt.y_q, ext_t, ed);
+        }
+        tp.tc_rows[b] = rows;
+        if (rows > tc::MAX_BATCH_ROWS) {   // a block too large for one batch: the FMA kernel runs the plan
+            tp.tc_batch.clear();
+            tp.tc_max_rows = 0;
+            return;
+        }
+        if (tp.tc_batch.empty() || batch_rows + rows > tc::MAX_BATCH_ROWS) {
+            tp.tc_batch.push_back(b);
+            batch_rows = 0;
+        }
+        for (int p = 0; p < nt; ++p) {   // operands of the block in order, from its batch's start
+            const TriTerm &tt = tp.terms[p];
+            const int64_t ed = tp.ext[(size_t)b * nl + tt.d_col];
+            tp.tc_row0[((size_t)b * nt + p) * 2] = (int32_t)batch_rows;
+            batch_rows += tc_operand_rows(tt.x_q, ext_t, ed);
+            tp.tc_row0[((size_t)b * nt + p) * 2 + 1] = (int32_t)batch_rows;
+            batch_rows += tc_operand_rows(tt.y_q, ext_t, ed);
+        }
+        tp.tc_max_rows = std::max(tp.tc_max_rows, batch_rows);
+        // the block's term records: plane row of each operand tile as a linear form in the
+        // pair-tile coordinates
+        for (int p = 0; p < nt; ++p) {
+            const TriTerm &tt = tp.terms[p];
+            const int64_t ed = tp.ext[(size_t)b * nl + tt.d_col];
+            const int64_t nch = (ed + tc::KCH - 1) / tc::KCH;
+            TcRec r;
+            std::memset(&r, 0, sizeof(r));
+            r.nch = (int32_t)nch;
+            r.ed = (int32_t)ed;
+            bool x_wide = false;
+            for (int m = 0; m < 4; ++m) x_wide |= tt.x_q[m] == 0;
+            for (int w = 0; w < 2; ++w) {
+                const int side = (w == 0) == x_wide ? 0 : 1;
+                const int *q = side ? tt.y_q : tt.x_q;
+                r.row0[w] = tp.tc_row0[((size_t)b * nt + p) * 2 + side];
+                int lab[3], k = 0;
+                for (int l = 0; l < 6; ++l)
+                    for (int m = 0; m < 4; ++m)
+                        if (q[m] == l) lab[k++] = l;
+                int64_t step = nch * 3 * (w == 0 ? tc::WROWS : tc::NROWS);
+                for (int i = 0; i < 3; ++i) {
+                    r.coef[w][lab[i]] = (int32_t)step;
+                    const int64_t ts = lab[i] == 0 ? tc::WA : TS;
+                    step *= (ext_t[lab[i]] + ts - 1) / ts;
+                }
+            }
+            const int32_t *rw = reinterpret_cast<const int32_t *>(&r);
+            tp.tc_rec.insert(tp.tc_rec.end(), rw, rw + 16);
+        }
+    }
+    tp.tc_batch.push_back(nb);
 }
 
 std::string describe_triples(const Plan &P) {
@@ -155,7 +256,11 @@ std::string describe_triples(const Plan &P) {
     o << "{\"triples\":true,\"terms\":" << tp.n_terms << ",\"blocks\":" << tp.n_blocks
       << ",\"dtype\":\"" << (P.dtype == COMET_F32 ? "f32" : "f64") << "\",\"tiles\":" << tp.prefix.back()
       << ",\"tile\":[4,4,4,4,4,4],\"own\":[" << tp.own[0] << "," << tp.own[1] << "],\"flops\":" << P.flops
-      << ",\"workspace\":" << P.workspace << "}";
+      << ",\"workspace\":" << P.workspace << ",\"tensor_core\":" << (tp.tc_batch.empty() ? "false" : "true");
+    if (!tp.tc_batch.empty())
+        o << ",\"pair_tiles\":" << tp.tc_prefix.back() << ",\"batches\":" << tp.tc_batch.size() - 1
+          << ",\"plane_rows\":" << tp.tc_max_rows;
+    o << "}";
     return o.str();
 }
 

@@ -14,6 +14,11 @@
 //     packed accumulator pairs (e, e + 1) take entries 2m and 2m + 1 of the operand holding T
 //     label 0;
 //   - the 16-byte shared loads start on 16-byte boundaries and stay in the tile.
+// FP32 tensor-core path: the pair-tile layout in shared memory (one slot per element, the
+// drained rows of a warp in 32 banks), batches and operand plane-row segments, the TMA boxes of
+// every term and chunk inside their operand's segment, the drain's (row, column) -> element map
+// against the elements' coordinates (each of the 8192 once), the pre-pass's plane rows against
+// the operand elements, and the energy's element coverage.
 // FP64 kernel:
 // For every thread, every term and a set of tiles that includes the first and the ragged last
 // tile along every label, it checks:
@@ -312,6 +317,212 @@ static void replay32(const Args &a, const int32_t *ext_b) {
     }
 }
 
+// ---- FP32 tensor-core path (k_triples_tc.cu) --------------------------------------------------
+// the kernels' op_geo(): the operand's T labels in T order with strides, extents, tile sizes and
+// counts; the summed label's stride and extent
+struct Geo { int lab[3], st[3], ext[3], ts[3], nt[3], sd, ed, nch, rpt; bool wide; };
+
+static Geo op_geo(const TermDev &tm, int side, const int32_t *ext_b) {
+    const int8_t *q = side ? tm.y_q : tm.x_q, *col = side ? tm.y_col : tm.x_col, *rk = side ? tm.y_rank : tm.x_rank;
+    Geo g{};
+    int st = 1;
+    for (int m = 0; m < 4; ++m) {
+        const int e = ext_b[col[m]];
+        if (q[m] < 0) g.sd = st;
+        else { g.lab[rk[m]] = q[m]; g.st[rk[m]] = st; g.ext[rk[m]] = e; }
+        st *= e;
+    }
+    g.ed = ext_b[tm.d_col];
+    g.nch = (g.ed + tc::KCH - 1) / tc::KCH;
+    g.wide = g.lab[0] == 0;
+    g.rpt = g.wide ? tc::WROWS : tc::NROWS;
+    for (int i = 0; i < 3; ++i) {
+        g.ts[i] = g.lab[i] == 0 ? tc::WA : TS;
+        g.nt[i] = (g.ext[i] + g.ts[i] - 1) / g.ts[i];
+    }
+    return g;
+}
+static void tc_row_coords(bool wide, int r, int &c0, int &c1, int &c2) {
+    if (wide) { c0 = r & 7; c1 = (r >> 3) & 3; c2 = r >> 5; }
+    else { c0 = r & 3; c1 = (r >> 2) & 3; c2 = r >> 4; }
+}
+
+static void replay_tc(const Plan &P, const Args &a) {
+    const TriplesPlan &tp = P.tri;
+    CHECK(!tp.tc_batch.empty(), "FP32 plan without the tensor-core layout");
+    if (tp.tc_batch.empty()) return;
+    // the pair-tile in shared memory: one slot per element, inside TSZ; the 32 rows a drain warp
+    // holds (8 along label 0 x 4 along label L) fall in 32 different banks
+    {
+        std::vector<int> seen(tc::TSZ, 0);
+        for (int e = 0; e < 8 * 1024; ++e) {
+            const int c[6] = {e & 7, (e >> 3) & 3, (e >> 5) & 3, (e >> 7) & 3, (e >> 9) & 3, (e >> 11) & 3};
+            int off = 0;
+            for (int q = 0; q < 6; ++q) off += tc::tstride(q) * c[q];
+            CHECK(off >= 0 && off < tc::TSZ, "pair-tile offset outside TSZ");
+            if (off >= 0 && off < tc::TSZ) ++seen[off];
+        }
+        int twice = 0;
+        for (int v : seen) twice += v > 1;
+        CHECK(twice == 0, "pair-tile slots shared by %d elements", twice);
+        for (int L = 1; L < 6; ++L) {
+            int banks = 0;
+            for (int c0 = 0; c0 < 8; ++c0)
+                for (int c1 = 0; c1 < 4; ++c1) banks |= 1 << ((c0 + tc::tstride(L) * c1) & 31);
+            CHECK(banks == -1, "drain rows of label %d share banks", L);
+        }
+    }
+    const int nb = tp.n_blocks, nt = tp.n_terms;
+    CHECK(tp.tc_batch.front() == 0 && tp.tc_batch.back() == nb, "batches cover the blocks");
+    for (size_t bi = 0; bi + 1 < tp.tc_batch.size(); ++bi) {
+        int64_t next = 0;   // operands of a batch are consecutive from row 0
+        for (int b = tp.tc_batch[bi]; b < tp.tc_batch[bi + 1]; ++b) {
+            const int32_t *ext_b = tp.ext.data() + (size_t)b * tp.n_labels;
+            for (int p = 0; p < nt; ++p)
+                for (int side = 0; side < 2; ++side) {
+                    const Geo g = op_geo(a.term[p], side, ext_b);
+                    const int64_t rows = (int64_t)g.nt[0] * g.nt[1] * g.nt[2] * g.nch * 3 * g.rpt;
+                    const int64_t r0 = tp.tc_row0[((size_t)b * nt + p) * 2 + side];
+                    CHECK(r0 == next, "operand (%d, %d, %d) does not follow the previous one", b, p, side);
+                    next = r0 + rows;
+                    CHECK(next <= tp.tc_max_rows && next < (int64_t(1) << 31), "operand beyond the batch region");
+                }
+        }
+    }
+    for (int b = 0; b < nb; ++b) {
+        const int32_t *ext_b = tp.ext.data() + (size_t)b * tp.n_labels;
+        int text[6], ntile[6];
+        int64_t items = 1;
+        for (int q = 0; q < 6; ++q) {
+            text[q] = ext_b[a.t_col[q]];
+            ntile[q] = (text[q] + (q == 0 ? tc::WA : TS) - 1) / (q == 0 ? tc::WA : TS);
+            items *= ntile[q];
+        }
+        CHECK(tp.tc_prefix[b + 1] - tp.tc_prefix[b] == items, "pair-tiles of block %d", b);
+        // pair-tiles: the first and the last along every label
+        for (int mask = 0; mask < 64; ++mask) {
+            int tcq[6], tbase[6];
+            for (int q = 0; q < 6; ++q) {
+                tcq[q] = ((mask >> q) & 1) ? ntile[q] - 1 : 0;
+                tbase[q] = tcq[q] * (q == 0 ? tc::WA : TS);
+            }
+            // the kernels' decode of this item's linear index gives back these coordinates
+            int64_t lin = 0;
+            for (int q = 5; q >= 0; --q) lin = lin * ntile[q] + tcq[q];
+            {
+                int64_t rem = lin;
+                for (int q = 0; q < 6; ++q) {
+                    const int64_t qt = rem / ntile[q];
+                    CHECK((int)(rem - qt * ntile[q]) == tcq[q], "item decode");
+                    rem = qt;
+                }
+            }
+            for (int p = 0; p < nt; ++p) {
+                const TermDev &tm = a.term[p];
+                const int sw = (tm.xmask & 1) ? 0 : 1;
+                const Geo gs[2] = {op_geo(tm, sw, ext_b), op_geo(tm, 1 - sw, ext_b)};   // wide, narrow
+                CHECK(gs[0].wide && !gs[1].wide, "term %d: the operand holding label 0", p);
+                int64_t orow[2];
+                for (int w = 0; w < 2; ++w) {
+                    const Geo &g = gs[w];
+                    const int side = w == 0 ? sw : 1 - sw;
+                    const int64_t r0 = tp.tc_row0[((size_t)b * nt + p) * 2 + side];
+                    const int64_t tile = tcq[g.lab[0]] + (int64_t)g.nt[0] * (tcq[g.lab[1]] + (int64_t)g.nt[1] * tcq[g.lab[2]]);
+                    orow[w] = r0 + tile * g.nch * 3 * g.rpt;
+                    const int64_t seg_end = r0 + (int64_t)g.nt[0] * g.nt[1] * g.nt[2] * g.nch * 3 * g.rpt;
+                    // the producer's boxes: 64 rows at row + (ch * 3 + plane) * rows per tile (+ 64)
+                    for (int ch = 0; ch < g.nch; ++ch)
+                        for (int pl = 0; pl < 3; ++pl)
+                            for (int h = 0; h < g.rpt / tc::BOX; ++h) {
+                                const int64_t br = orow[w] + ((int64_t)ch * 3 + pl) * g.rpt + h * tc::BOX;
+                                CHECK(br >= r0 && br + tc::BOX <= seg_end, "box outside operand (term %d)", p);
+                            }
+                }
+                // the host-built term record gives the same rows as a linear form in the tile
+                // coordinates
+                {
+                    TcRec rec;
+                    std::memcpy(&rec, tp.tc_rec.data() + ((size_t)b * nt + p) * 16, sizeof(rec));
+                    for (int w = 0; w < 2; ++w) {
+                        int64_t v = rec.row0[w];
+                        for (int q = 0; q < 6; ++q) v += (int64_t)rec.coef[w][q] * tcq[q];
+                        CHECK(v == orow[w], "term %d: record row of operand %d", p, w);
+                    }
+                    CHECK(rec.nch == gs[0].nch && rec.ed == gs[0].ed, "term %d: record chunks", p);
+                }
+                // the drain's index map against the elements' coordinates (warp columns 16 colq + j,
+                // j = c0 + 4 c1, at the narrow labels' coordinates (c0, c1, colq)), and the pre-pass's
+                // rows against the operand elements at those coordinates
+                int lw[3] = {gs[0].lab[0], gs[0].lab[1], gs[0].lab[2]}, ln[3] = {gs[1].lab[0], gs[1].lab[1], gs[1].lab[2]};
+                std::vector<int> hit(tc::TSZ, 0);
+                for (int m = 0; m < tc::WROWS; ++m) {
+                    const int offw = (m & 7) + tc::tstride(lw[1]) * ((m >> 3) & 3) + tc::tstride(lw[2]) * (m >> 5);
+                    for (int n = 0; n < tc::NROWS; ++n) {
+                        const int off = offw + tc::tstride(ln[0]) * (n & 3) + tc::tstride(ln[1]) * ((n >> 2) & 3) +
+                                        tc::tstride(ln[2]) * (n >> 4);
+                        int cin[6];
+                        int wc[3], nc[3];
+                        tc_row_coords(true, m, wc[0], wc[1], wc[2]);
+                        tc_row_coords(false, n, nc[0], nc[1], nc[2]);
+                        for (int i = 0; i < 3; ++i) { cin[lw[i]] = wc[i]; cin[ln[i]] = nc[i]; }
+                        int want = 0;
+                        for (int q = 0; q < 6; ++q) want += tc::tstride(q) * cin[q];
+                        CHECK(off == want, "term %d: (%d, %d) drained to the wrong element", p, m, n);
+                        if (off >= 0 && off < tc::TSZ) ++hit[off];
+                    }
+                }
+                int cover = 0;
+                for (int v : hit) cover += v == 1;
+                CHECK(cover == 8192, "term %d covers %d pair-tile elements once", p, cover);
+                // rows of the wide and narrow tiles hold the operand at the element coordinates
+                for (int w = 0; w < 2; ++w) {
+                    const Geo &g = gs[w];
+                    const int side = w == 0 ? sw : 1 - sw;
+                    const int8_t *q = side ? tm.y_q : tm.x_q, *col = side ? tm.y_col : tm.x_col;
+                    const int64_t r0 = tp.tc_row0[((size_t)b * nt + p) * 2 + side];
+                    for (int r = 0; r < g.rpt; ++r) {
+                        int c[3];
+                        tc_row_coords(g.wide, r, c[0], c[1], c[2]);
+                        // the pre-pass's view of this plane row: R = tile * rpt + r
+                        const int64_t tile = (orow[w] - r0) / (g.nch * 3 * g.rpt);
+                        const int t0 = (int)(tile % g.nt[0]), t1 = (int)((tile / g.nt[0]) % g.nt[1]),
+                                  t2 = (int)(tile / ((int64_t)g.nt[0] * g.nt[1]));
+                        const int gg[3] = {t0 * g.ts[0] + c[0], t1 * g.ts[1] + c[1], t2 * g.ts[2] + c[2]};
+                        bool valid = true;
+                        int coord[6] = {0, 0, 0, 0, 0, 0};
+                        for (int i = 0; i < 3; ++i) {
+                            valid &= gg[i] < g.ext[i];
+                            CHECK(gg[i] == tbase[g.lab[i]] + c[i], "plane row %d of term %d at the wrong tile", r, p);
+                            coord[g.lab[i]] = gg[i];
+                        }
+                        if (!valid) continue;
+                        for (int k = 0; k < g.ed; k += std::max(1, g.ed - 1)) {
+                            const int64_t ro = (int64_t)gg[0] * g.st[0] + (int64_t)gg[1] * g.st[1] + (int64_t)gg[2] * g.st[2] +
+                                               (int64_t)k * g.sd;
+                            CHECK(ro == direct_offset(q, col, ext_b, coord, k), "pre-pass row %d reads the wrong element", r);
+                        }
+                    }
+                }
+            }
+            // energy: thread et takes labels 0..3 at (et & 7, et >> 3 & 3, et >> 5 & 3, et >> 7) and
+            // labels 4, 5 at (u & 3, u >> 2): each element once
+            static_assert(32 * tc::DRAIN_WARPS == 512, "one energy thread per labels 0..3 combination");
+            std::vector<int> eh(tc::TSZ, 0);
+            for (int et = 0; et < 32 * tc::DRAIN_WARPS; ++et)
+                for (int u = 0; u < 16; ++u) {
+                    const int cj = u & 3, ck = u >> 2;
+                    const int off = (et & 7) + tc::tstride(1) * ((et >> 3) & 3) + tc::tstride(2) * ((et >> 5) & 3) +
+                                    tc::tstride(3) * ((et >> 7) & 3) + tc::tstride(4) * cj + tc::tstride(5) * ck;
+                    CHECK(off < tc::TSZ, "energy read outside the pair-tile");
+                    if (off < tc::TSZ) ++eh[off];
+                }
+            int once = 0;
+            for (int v : eh) once += v == 1;
+            CHECK(once == 8192, "energy reads %d elements once", once);
+        }
+    }
+}
+
 int main(int argc, char **argv) {
     if (argc < 2) { std::printf("usage\n"); return 2; }
     const int nt = std::atoi(argv[1]);
@@ -333,8 +544,12 @@ int main(int argc, char **argv) {
         Args a;
         std::memset(&a, 0, sizeof(a));
         triples_args(P, &a);
-        if (e == 4) replay32(a, P.tri.ext.data());
-        else replay(a, P.tri.ext.data(), e);
+        if (e == 4) {
+            replay32(a, P.tri.ext.data());
+            replay_tc(P, a);
+        } else {
+            replay(a, P.tri.ext.data(), e);
+        }
     }
     std::printf("%d failures\n", fails);
     return fails ? 1 : 0;
