@@ -443,12 +443,30 @@ def run_triples_energy(a) -> int:
         # the measured FP64 probe peak); the kernel's useful flops are plan.flops
         peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12 if name == "f32" else fp64_peak["tflops"]
         achieved = plan.flops / (t * 1e-3) / 1e12
+        roof = {"bound": "alu" if name == "f32" else "fp64", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": ("FP32 FMA lanes x median SM clock under load" if name == "f32"
+                                else "measured: " + fp64_peak["how"] + ", " + fp64_peak["probe"])}
+        if name == "f32" and plan.info.get("tensor_core"):
+            # the tensor-core path: six BF16 products of 128 x 64 per pair-tile (8 x 4^5 of T), term
+            # and 16 summed indices (the summed label rounded up to 16), against the BF16 burst peak;
+            # the useful flops against the FP32 FMA rate stay beside it
+            e64 = ext.astype(np.int64)
+            pt = -(-e64[:, col["a"]] // 8)
+            for l in "bcijk":
+                pt = pt * -(-e64[:, col[l]] // 4)
+            mma_flops = float(np.sum(pt * len(tl) * 6 * 2 * 128 * 64 * 16 * -(-e64[:, col["d"]] // 16)))
+            peaks = measured_peaks() or {}
+            bpk = peaks.get("bf16_tflops", 1900.0)
+            issued = mma_flops / (t * 1e-3) / 1e12
+            roof = {"bound": "tensor", "achieved": issued, "peak": bpk, "unit": "TFLOP/s", "frac": issued / bpk,
+                    "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)",
+                    "mma_flops_issued": mma_flops, "pair_tiles": int(plan.info["pair_tiles"]),
+                    "useful_vs_fp32_fma": {"achieved": achieved, "peak": peak, "frac": achieved / peak,
+                                           "peak_source": "FP32 FMA lanes x median SM clock under load"}}
         out[name] = {"blocks": n_blocks, "ms_per_step": t, "steps": steps, "tflops": achieved,
-                     "roofline": {"bound": "alu" if name == "f32" else "fp64", "achieved": achieved,
-                                  "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                                  "peak_source": ("FP32 FMA lanes x median SM clock under load" if name == "f32"
-                                                  else "measured: " + fp64_peak["how"] + ", "
-                                                  + fp64_peak["probe"])},
+                     "roofline": roof, "path": ("tensor cores (split BF16, 6 products)"
+                                                if name == "f32" and plan.info.get("tensor_core") else "FMA"),
                      "tiles": plan.info["tiles"], "flops": plan.flops, "clocks": ck,
                      "energy_sum": float(energies.sum()),
                      "cpu_baseline": cpu_baseline(ext, buf, ebuf, sizes, eps_sizes, energies, dtype)}

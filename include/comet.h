@@ -179,8 +179,13 @@ comet_status_t comet_plan_views(const char *expr, const comet_extent_t *extents,
  *     T_b = sum_p alpha_p * X_bp * Y_bp             (term p: the contraction terms[p])
  *     E_b = sum over the elements of T_b of T_b^2 / D_b,
  *     D_b[l_1..l_6] = sum_q signs[q] * eps_bq[l_q]  (l_q: the q-th label of T)
- * T never goes to memory: each CTA holds a 4^6 tile of T_b in registers, adds every term's
- * contribution into it and reduces its energy.
+ * T never goes to memory. COMET_F32 plans run on the tensor cores: a pre-pass writes every
+ * operand as three bfloat16 parts (x = h + m + l, residual below 2^-26 |x|) into the workspace,
+ * blocks taken in batches whose parts fit it (at most 2^27 rows of 64 bytes, 8 GB; the
+ * environment variable COMET_TRIPLES_BATCH_ROWS lowers the cap); each CTA forms, per tile of
+ * 8 x 4^5 values of T_b and term, the six-product split sum in tensor memory, adds it into the
+ * tile in shared memory and reduces the tile's energy. A plan with a block whose parts exceed
+ * one batch, and COMET_F64 plans, run on the FMA pipes with 4^6 tiles held in registers.
  *   terms        n_terms (1..16) expressions with the same left-hand side T[l_1,...,l_6] (six
  *                distinct labels) and two four-label operands that share exactly one label (the
  *                summed one) and hold three labels of T each, e.g.
@@ -188,11 +193,13 @@ comet_status_t comet_plan_views(const char *expr, const comet_extent_t *extents,
  *   label_names  n_labels (<= 16) names covering every label of the terms
  *   extents      n_blocks x n_labels extents >= 1 (row b: block b, columns as label_names)
  *   signs        six entries, +1 or -1, in T's label order
- *   dtype        COMET_F32 (T, each T^2 / D and a tile's sum of them in FP32) or COMET_F64;
- *                the block energies are summed in FP64
+ *   dtype        COMET_F32 (T from the six split products accumulated in FP32, each T^2 / D
+ *                and sums of 16 of them in FP32) or COMET_F64; the block energies are summed
+ *                in FP64
  * Errors: COMET_ERR_PARSE / COMET_ERR_LABEL / COMET_ERR_UNSUPPORTED for terms outside this form,
  * COMET_ERR_SHAPE for extents below 1 or a block of 2^31 tiles or more, COMET_ERR_ARG otherwise.
- * comet_plan_workspace() gives the device bytes of the block table.
+ * comet_plan_workspace() gives the device bytes of the block table (and, for COMET_F32, of the
+ * split parts of the largest batch).
  */
 comet_status_t comet_plan_triples(const char *const *terms, int n_terms, const char *const *label_names,
                                   int n_labels, int n_blocks, const int64_t *extents, const int *signs,
@@ -211,6 +218,8 @@ comet_status_t comet_triples_prepare(comet_plan_t plan, void *workspace, void *s
  *              in T's label order
  *   energies   device array of n_blocks doubles, overwritten
  *   workspace  the prepared workspace
+ * A device wait of the tensor-core path that runs out (2 s, or COMET_WAIT_TIMEOUT_MS) records
+ * COMET_ERR_TIMEOUT for comet_sync_status().
  */
 comet_status_t comet_triples_energy(comet_plan_t plan, const void *operands, const void *eps,
                                     double *energies, void *workspace, void *stream);

@@ -107,27 +107,64 @@ struct Item {
     int tc[6];
 };
 
-__device__ __forceinline__ Item decode_item(const Args &a, const TcArgs &t, int64_t it) {
-    const int64_t g = t.item0 + it;
-    int lo = t.b0, hi = t.b1;   // prefix[lo] <= g < prefix[hi]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (t.prefix[mid] <= g) lo = mid; else hi = mid;
-    }
-    Item r;
-    r.b = lo;
-    uint32_t rem = (uint32_t)(g - t.prefix[lo]);   // a block has fewer than 2^31 pair-tiles
-    const int32_t *ext_b = a.ext + (int64_t)lo * a.n_labels;
+// The items blockIdx.x, + gridDim.x, ... of one launch, walked in order: the block is found by a
+// forward scan of the pair-tile prefix sums, and within a block the coordinates advance by
+// mixed-radix addition of the stride (divisions only when the block changes).
+struct ItemWalk {
+    Item item;
+    uint32_t local, count;     // the item's index within its block, the block's pair-tiles
+    int rad[6], step[6];       // tile counts per label; the stride in that radix
+    int64_t g;                 // the item's global index
+
+    __device__ __forceinline__ void enter_block(const Args &a, const TcArgs &t, uint32_t stride) {
+        const int32_t *ext_b = a.ext + (int64_t)item.b * a.n_labels;
+        uint32_t rem = local, st = stride;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        const uint32_t ts = q == 0 ? tc::WA : TS;
-        const uint32_t n = ((uint32_t)ext_b[a.t_col[q]] + ts - 1) / ts;
-        const uint32_t qt = rem / n;
-        r.tc[q] = (int)(rem - qt * n);
-        rem = qt;
+        for (int q = 0; q < 6; ++q) {
+            const uint32_t ts = q == 0 ? tc::WA : TS;
+            const uint32_t n = ((uint32_t)ext_b[a.t_col[q]] + ts - 1) / ts;
+            rad[q] = (int)n;
+            const uint32_t qt = rem / n;
+            item.tc[q] = (int)(rem - qt * n);
+            rem = qt;
+            const uint32_t qs = st / n;
+            step[q] = (int)(st - qs * n);
+            st = qs;
+        }
+        count = (uint32_t)(t.prefix[item.b + 1] - t.prefix[item.b]);
     }
-    return r;
-}
+    // position on global item item0 + it, scanning blocks forward from b
+    __device__ __forceinline__ void locate(const Args &a, const TcArgs &t, int b, uint32_t stride) {
+        while (b + 1 < t.b1 && t.prefix[b + 1] <= g) ++b;
+        item.b = b;
+        local = (uint32_t)(g - t.prefix[b]);   // a block has fewer than 2^31 pair-tiles
+        enter_block(a, t, stride);
+    }
+    __device__ __forceinline__ void start(const Args &a, const TcArgs &t, int64_t it) {
+        g = t.item0 + it;
+        int lo = t.b0, hi = t.b1;   // prefix[lo] <= g < prefix[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (t.prefix[mid] <= g) lo = mid; else hi = mid;
+        }
+        locate(a, t, lo, gridDim.x);
+    }
+    __device__ __forceinline__ void next(const Args &a, const TcArgs &t) {
+        g += gridDim.x;
+        local += gridDim.x;
+        if (local < count) {
+            int carry = 0;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const int d = item.tc[q] + step[q] + carry;
+                carry = d >= rad[q];
+                item.tc[q] = carry ? d - rad[q] : d;
+            }
+        } else {
+            locate(a, t, item.b, gridDim.x);
+        }
+    }
+};
 
 __device__ __forceinline__ TcRec load_rec(const TcRec *rec, int64_t i) {
     const uint4 *p = reinterpret_cast<const uint4 *>(rec + i);
@@ -291,8 +328,11 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             // ---------------- TMA producer ----------------
             uint32_t rit = 0;
             bool ok = true;
+            ItemWalk walk;
+            if ((int64_t)blockIdx.x < n_items) walk.start(a, t, blockIdx.x);
             for (int64_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
-                const Item item = decode_item(a, t, it);
+                if (it != (int64_t)blockIdx.x) walk.next(a, t);
+                const Item &item = walk.item;
                 for (int p = 0; p < a.n_terms && ok; ++p) {
                     const TcRec rec = load_rec(t.rec, (int64_t)item.b * a.n_terms + p);
                     const int32_t wrow = rec_row(rec, 0, item), nrow = rec_row(rec, 1, item);
@@ -323,8 +363,11 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             constexpr uint32_t idesc = idesc_bf16_f32(WROWS, NROWS);
             uint32_t rit = 0, tcount = 0;
             bool ok = true;
+            ItemWalk walk;
+            if ((int64_t)blockIdx.x < n_items) walk.start(a, t, blockIdx.x);
             for (int64_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
-                const Item item = decode_item(a, t, it);
+                if (it != (int64_t)blockIdx.x) walk.next(a, t);
+                const Item &item = walk.item;
                 for (int p = 0; p < a.n_terms && ok; ++p, ++tcount) {
                     const TcRec rec = load_rec(t.rec, (int64_t)item.b * a.n_terms + p);
                     const int ed = rec.ed, nch = rec.nch;
@@ -372,8 +415,11 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
         uint32_t tcount = 0;
         bool dead = false;   // once set, the warp keeps pace with the named barriers only
+        ItemWalk walk;
+        if ((int64_t)blockIdx.x < n_items) walk.start(a, t, blockIdx.x);
         for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
-            const Item item = decode_item(a, t, it);
+            if (it != (int64_t)blockIdx.x) walk.next(a, t);
+            const Item &item = walk.item;
             const int32_t *ext_b = a.ext + (int64_t)item.b * a.n_labels;
             for (int p = 0; p < a.n_terms; ++p, ++tcount) {
                 const TermDev &tm = a.term[p];

@@ -2,6 +2,7 @@
 // workspace) and the construction of the kernel's argument block.  No device code: the CPU
 // replay of the kernel's index arithmetic (tests/triples_check.cpp) links it.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <sstream>
@@ -175,6 +176,13 @@ int64_t tc_operand_rows(const int *q, const int64_t *ext_t, int64_t ext_d) {
 
 void plan_triples_tc(Plan *P) {
     TriplesPlan &tp = P->tri;
+    // plane rows per batch: MAX_BATCH_ROWS, or less from COMET_TRIPLES_BATCH_ROWS (more batches;
+    // a block larger than a batch puts the plan on the FMA kernel)
+    int64_t cap = tc::MAX_BATCH_ROWS;
+    if (const char *env = std::getenv("COMET_TRIPLES_BATCH_ROWS")) {
+        const long long v = std::atoll(env);
+        if (v > 0 && v < cap) cap = v;
+    }
     const int nb = tp.n_blocks, nt = tp.n_terms, nl = tp.n_labels;
     tp.tc_prefix.assign(nb + 1, 0);
     tp.tc_row0.assign((size_t)nb * nt * 2, 0);
@@ -197,12 +205,12 @@ void plan_triples_tc(Plan *P) {
             rows += tc_operand_rows(tt.x_q, ext_t, ed) + tc_operand_rows(tt.y_q, ext_t, ed);
         }
         tp.tc_rows[b] = rows;
-        if (rows > tc::MAX_BATCH_ROWS) {   // a block too large for one batch: the FMA kernel runs the plan
+        if (rows > cap) {   // a block too large for one batch: the FMA kernel runs the plan
             tp.tc_batch.clear();
             tp.tc_max_rows = 0;
             return;
         }
-        if (tp.tc_batch.empty() || batch_rows + rows > tc::MAX_BATCH_ROWS) {
+        if (tp.tc_batch.empty() || batch_rows + rows > cap) {
             tp.tc_batch.push_back(b);
             batch_rows = 0;
         }

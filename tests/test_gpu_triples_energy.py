@@ -89,6 +89,21 @@ def test_uniform(comet, exts, dtype, tol):
     assert np.all(np.abs(got - ref) <= tol * np.abs(ref))
 
 
+@pytest.mark.parametrize("route", ["batches", "fma"])
+def test_fp32_routes(comet, monkeypatch, route):
+    # the FP32 tensor-core path with one batch per block, and the FP32 FMA kernel (a batch cap
+    # below every block), against the oracle: integers and uniform inputs
+    exts = SHAPES[1] + SHAPES[2] + rand_exts(3, 17, 2, 12, d_hi=40)
+    monkeypatch.setenv("COMET_TRIPLES_BATCH_ROWS", "40000" if route == "batches" else "1000")
+    got, ref, plan = run(comet, exts, np.float32, 3, kind="int", lo=-3, hi=3)
+    assert plan.info["tensor_core"] == (route == "batches")
+    if route == "batches":
+        assert plan.info["batches"] > 1
+    assert np.all(np.abs(got - ref) <= 1e-6 * np.abs(ref) + 1e-300)
+    got, ref, _ = run(comet, exts, np.float32, 4)
+    assert np.all(np.abs(got - ref) <= 2e-5 * np.abs(ref))
+
+
 @pytest.mark.parametrize("dtype,tol", [(np.float64, 1e-12), (np.float32, 1e-5)])
 def test_terms_add_linearly(comet, dtype, tol):
     # the same block with terms 0..3 each split into two halves (13 terms) gives the same energy

@@ -419,3 +419,53 @@ def test_triples_plans():
     # a triples plan refuses the contraction entry point (checked before any device work)
     ptrs = (ctypes.c_void_p * 18)(*([16] * 18))
     assert comet.lib().comet_contract(p._h, ptrs, ctypes.c_void_p(16), ctypes.c_void_p(16), None) == 12
+
+
+def _tc_rows(row):
+    # plane rows of one block on the FP32 tensor-core path, counted from the layout's definition:
+    # per term and operand, tiles (8 along T label a, 4 along the others) x chunks of 32 summed
+    # indices x 3 planes x rows per tile (128 for the operand holding a, 64 for the other)
+    import sys
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import oracle
+    from triples_terms import LABELS, terms
+    ext = dict(zip(LABELS, row))
+    total = 0
+    for t in terms():
+        for _, labels in oracle.parse(t)[4]:
+            tl = [l for l in labels if l != "d"]
+            tiles = int(np.prod([-(-ext[l] // (8 if l == "a" else 4)) for l in tl]))
+            total += tiles * -(-ext["d"] // 32) * 3 * (128 if "a" in tl else 64)
+    return total
+
+
+def test_triples_tensor_core_layout(monkeypatch):
+    # FP32 plans run on the tensor cores: pair-tiles of 8 x 4^5, blocks grouped into batches of at
+    # most COMET_TRIPLES_BATCH_ROWS plane rows; a block larger than a batch puts the plan on the
+    # FMA kernel; FP64 plans always run on the FMA kernel
+    import sys
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from triples_terms import LABELS, SIGNS, terms
+    ext = [[5, 6, 7, 3, 4, 5, 9], [8, 8, 8, 8, 8, 8, 40], [9, 10, 11, 13, 2, 3, 33]]
+    rows = [_tc_rows(r) for r in ext]
+    pair_tiles = sum(-(-r[0] // 8) * int(np.prod([-(-r[q] // 4) for q in range(1, 6)])) for r in ext)
+    monkeypatch.delenv("COMET_TRIPLES_BATCH_ROWS", raising=False)
+    info = comet.TriplesPlan(terms(), LABELS, ext, SIGNS, "f32").info
+    assert info["tensor_core"] and info["batches"] == 1 and info["pair_tiles"] == pair_tiles
+    assert info["plane_rows"] == sum(rows)
+    assert not comet.TriplesPlan(terms(), LABELS, ext, SIGNS, "f64").info["tensor_core"]
+    # a cap that holds the largest block: blocks taken in order into batches while they fit
+    cap = max(rows)
+    monkeypatch.setenv("COMET_TRIPLES_BATCH_ROWS", str(cap))
+    batches, cur, region = 0, None, 0
+    for r in rows:
+        if cur is None or cur + r > cap:
+            batches, cur = batches + 1, 0
+        cur += r
+        region = max(region, cur)
+    assert batches >= 2
+    info = comet.TriplesPlan(terms(), LABELS, ext, SIGNS, "f32").info
+    assert info["tensor_core"] and info["batches"] == batches and info["plane_rows"] == region
+    # a cap below the largest block: the FMA kernel
+    monkeypatch.setenv("COMET_TRIPLES_BATCH_ROWS", str(max(rows) - 1))
+    assert not comet.TriplesPlan(terms(), LABELS, ext, SIGNS, "f32").info["tensor_core"]

@@ -29,6 +29,7 @@
 //   - the static shared arrays the 16-byte loads use have 16-byte-multiple row pitches.
 // Exit status 0 = pass.
 #include <algorithm>
+#include <array>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -523,6 +524,76 @@ static void replay_tc(const Plan &P, const Args &a) {
     }
 }
 
+// the kernels' ItemWalk (mixed-radix advance of the tile coordinates by the grid stride, forward
+// block scan) against a direct decode of every item index, on blocks of random extents (many with
+// fewer pair-tiles than the stride) and several strides
+static void replay_item_walk() {
+    uint64_t st = 88172645463325252ull;
+    auto rnd = [&](int lo, int hi) {
+        st ^= st << 13; st ^= st >> 7; st ^= st << 17;
+        return lo + (int)(st % (uint64_t)(hi - lo + 1));
+    };
+    const int nb = 200;
+    std::vector<std::array<int, 6>> rad(nb);
+    std::vector<int64_t> prefix(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) {
+        int64_t c = 1;
+        for (int q = 0; q < 6; ++q) {
+            const int e = rnd(1, b % 3 == 0 ? 3 : 20);
+            const int ts = q == 0 ? tc::WA : TS;
+            rad[b][q] = (e + ts - 1) / ts;
+            c *= rad[b][q];
+        }
+        prefix[b + 1] = prefix[b] + c;
+    }
+    for (int stride : {1, 7, 152, 1000}) {
+        for (int first = 0; first < std::min(stride, 3); ++first) {
+            // the walk, as the kernels run it
+            int b = 0, tc[6] = {0, 0, 0, 0, 0, 0}, step[6] = {0, 0, 0, 0, 0, 0};
+            uint32_t local = 0, count = 0;
+            int64_t g = first;
+            auto enter = [&]() {
+                uint32_t rem = local, s2 = (uint32_t)stride;
+                for (int q = 0; q < 6; ++q) {
+                    const uint32_t n = (uint32_t)rad[b][q];
+                    tc[q] = (int)(rem % n); rem /= n;
+                    step[q] = (int)(s2 % n); s2 /= n;
+                }
+                count = (uint32_t)(prefix[b + 1] - prefix[b]);
+            };
+            auto locate = [&](int from) {
+                b = from;
+                while (b + 1 < nb && prefix[b + 1] <= g) ++b;
+                local = (uint32_t)(g - prefix[b]);
+                enter();
+            };
+            locate(0);
+            for (; g < prefix[nb];) {
+                // direct decode
+                int db = 0;
+                while (prefix[db + 1] <= g) ++db;
+                int64_t rem = g - prefix[db];
+                bool same = db == b;
+                for (int q = 0; q < 6; ++q) { same &= (int)(rem % rad[db][q]) == tc[q]; rem /= rad[db][q]; }
+                CHECK(same, "item walk at item %lld (stride %d)", (long long)g, stride);
+                g += stride;
+                if (g >= prefix[nb]) break;
+                local += (uint32_t)stride;
+                if (local < count) {
+                    int carry = 0;
+                    for (int q = 0; q < 6; ++q) {
+                        const int d = tc[q] + step[q] + carry;
+                        carry = d >= rad[b][q];
+                        tc[q] = carry ? d - rad[b][q] : d;
+                    }
+                } else {
+                    locate(b);
+                }
+            }
+        }
+    }
+}
+
 int main(int argc, char **argv) {
     if (argc < 2) { std::printf("usage\n"); return 2; }
     const int nt = std::atoi(argv[1]);
@@ -551,6 +622,7 @@ int main(int argc, char **argv) {
             replay(a, P.tri.ext.data(), e);
         }
     }
+    replay_item_walk();
     std::printf("%d failures\n", fails);
     return fails ? 1 : 0;
 }
