@@ -326,12 +326,12 @@ static comet_status_t run_host_pipe(const Plan &P, const void *const *host_in, v
     if (nw > 31) return COMET_ERR_INTERNAL;   // one scale word per W slice in the 256-byte region
     cudaError_t e = cudaStreamCreateWithFlags(&r.cin, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r.cout, cudaStreamNonBlocking);
-    r.ev.assign(2 + 2 * n + nw, nullptr);
+    r.ev.assign(2 + 2 * n + 2 * nw, nullptr);
     for (auto &x : r.ev)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_status(e, "host pipeline streams");
     cudaEvent_t e0 = r.ev[0], e_end = r.ev[1];
-    cudaEvent_t *e_in = &r.ev[2], *e_g = &r.ev[2 + n], *e_w = &r.ev[2 + 2 * n];
+    cudaEvent_t *e_in = &r.ev[2], *e_g = &r.ev[2 + n], *e_w = &r.ev[2 + 2 * n], *e_blk = &r.ev[2 + 2 * n + nw];
 
     double alpha = P.alpha, beta = 0.0;
     if (P.op == 1) beta = 1.0;
@@ -361,6 +361,32 @@ static comet_status_t run_host_pipe(const Plan &P, const void *const *host_in, v
     const size_t w_pitch = (size_t)h.w_inner * h.w_ext * es;
     auto lx_of = [&](int q) { return std::min(h.chunk, h.ext - (int64_t)q * h.chunk); };
     auto lw_of = [&](int i) { return std::min(h.w_chunk, h.w_ext - (int64_t)i * h.w_chunk); };
+    // The last column of GEMM blocks goes back block by block, so that only its last block's
+    // copy follows the last GEMM: possible when the result's W label sits directly below X's
+    // label L (a block is then a 3-D box: W-label runs x the slice's L values x the labels above
+    // L) or directly above it.
+    const bool w_below = h.wc_inner * h.w_ext == h.c_inner, w_above = h.c_inner * h.ext == h.wc_inner;
+    const bool blockwise = nw > 1 && (w_below || w_above);
+    auto copy_block = [&](int q, int i) {   // result block (W slice i, X slice q), device to host
+        const int64_t l0 = (int64_t)q * h.chunk, lc = lx_of(q), m0 = (int64_t)i * h.w_chunk, mc = lw_of(i);
+        cudaMemcpy3DParms m = {};
+        m.kind = cudaMemcpyDeviceToHost;
+        if (w_below) {   // runs over the W label's slice, rows over L, slabs above L
+            const size_t pitch = (size_t)h.c_inner * es;
+            m.srcPtr = make_cudaPitchedPtr(dc, pitch, pitch, (size_t)h.ext);
+            m.dstPtr = make_cudaPitchedPtr(hc, pitch, pitch, (size_t)h.ext);
+            m.srcPos = m.dstPos = make_cudaPos((size_t)m0 * h.wc_inner * es, (size_t)l0, 0);
+            m.extent = make_cudaExtent((size_t)mc * h.wc_inner * es, (size_t)lc, (size_t)h.c_outer);
+        } else {         // runs over L's slice, rows over the W label, slabs above it
+            const size_t pitch = (size_t)h.wc_inner * es;
+            const size_t slabs = (size_t)(h.c_outer / h.w_ext);
+            m.srcPtr = make_cudaPitchedPtr(dc, pitch, pitch, (size_t)h.w_ext);
+            m.dstPtr = make_cudaPitchedPtr(hc, pitch, pitch, (size_t)h.w_ext);
+            m.srcPos = m.dstPos = make_cudaPos((size_t)l0 * h.c_inner * es, (size_t)m0, 0);
+            m.extent = make_cudaExtent((size_t)lc * h.c_inner * es, (size_t)mc, slabs);
+        }
+        return cudaMemcpy3DAsync(&m, r.cout);
+    };
 
     // copies in: W_0, X_0, W_1.., X_1.. (and the result slices for "+=" / "-=" with X's)
     e = cudaEventRecord(e0, s);
@@ -455,7 +481,14 @@ static comet_status_t run_host_pipe(const Plan &P, const void *const *host_in, v
                                       st.ksplit, reinterpret_cast<float *>(w + st.ws_ksplit));
             }
             if (e != cudaSuccess) return cuda_status(e, "host pipeline gemm");
+            if (blockwise && q == n - 1) {   // the last column: each block back as soon as it is done
+                e = cudaEventRecord(e_blk[i], s);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(r.cout, e_blk[i], 0);
+                if (e == cudaSuccess) e = copy_block(q, i);
+                if (e != cudaSuccess) return cuda_status(e, "host pipeline copy out (block)");
+            }
         }
+        if (blockwise && q == n - 1) continue;
         e = cudaEventRecord(e_g[q], s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(r.cout, e_g[q], 0);
         if (e == cudaSuccess) {

@@ -547,14 +547,18 @@ void setup_host_pipe(Plan *P, int64_t es, int want, int want_w) {
         for (int64_t i = 1; i < cntw; ++i) { c += wbytes(i) / bw_in; rw[i] = c; }
         for (int64_t j = 1; j < cntx; ++j) { c += (xbytes(j) + (P->op != 0 ? cbytes(j) : 0)) / bw_in; rx[j] = c; }
         const bool sliced = cntx > 1 || cntw > 1;
+        // the last column goes back block by block when the result's layout allows it
+        const bool blockwise = cntw > 1 && (h.wc_inner * h.w_ext == h.c_inner || h.c_inner * h.ext == h.wc_inner);
         double t = 0, out = 0;
         for (int64_t j = 0; j < cntx; ++j) {
+            const bool last_blocks = blockwise && j == cntx - 1;
             t = std::max(t, rx[j]) + xbytes(j) / es * (es + planes) / kHbmBytesPerS;
             for (int64_t i = 0; i < cntw; ++i) {
                 if (j == 0) t = std::max(t, rw[i]) + wbytes(i) / es * (es + planes) / kHbmBytesPerS;
                 t += (double)((tiles_of(lx_of(j), lw_of(i)) + 151) / 152) * t_tile + (sliced ? t_slice : 0);
+                if (last_blocks) out = std::max(out, t) + cbytes(j) * (double)lw_of(i) / (double)h.w_ext / bw_out;
             }
-            out = std::max(out, t) + cbytes(j) / bw_out;
+            if (!last_blocks) out = std::max(out, t) + cbytes(j) / bw_out;
         }
         return out;
     };
