@@ -297,13 +297,13 @@ static cudaError_t copy_slice(void *dst, size_t dpitch, const void *src, size_t 
     return cudaSuccess;
 }
 
-// comet_contract_host through the slice pipeline of a one-step split / emulated-FP64 plan: X
-// (and possibly W) cross in slices along the last label of their GEMM row groups into compact
-// device slices, in the order W_0, X_0, W_1.., X_1..  Each slice gets its own scale word and
-// pre-pass as soon as its copy is in; GEMM block (i, j) multiplies W slice i by X slice j (the
-// step's GEMM with both row groups shortened, writing the result through the full result
-// strides from the block's first element), column by column; result slice j goes back on a
-// third stream after its last GEMM while the next ones run.
+// comet_contract_host through the slice pipeline of a one-step split / emulated-FP64 plan (see
+// HostPipe): the slices of X and W cross into compact device slices in the planned copy order;
+// each slice gets its own scale word and planes, pre-passed before its first GEMM block; block
+// (i, j) multiplies W slice i by X slice j (the step's GEMM with both row groups shortened,
+// writing the result through the full result strides from the block's first element) in the
+// planned block order; results go back on a third stream, block by block when the layout
+// allows, else each result slice after its column's last block.
 static comet_status_t run_host_pipe(const Plan &P, const void *const *host_in, void *host_out,
                                     void *const *dev_in, void *dev_out, void *ws, cudaStream_t s) {
     const HostPipe &h = P.pipe;
@@ -323,10 +323,10 @@ static comet_status_t run_host_pipe(const Plan &P, const void *const *host_in, v
         }
     } r;
     const int n = h.n_chunks, nw = h.w_n;
-    if (nw > 31) return COMET_ERR_INTERNAL;   // one scale word per W slice in the 256-byte region
+    if (n + nw > 32) return COMET_ERR_INTERNAL;   // one scale word per slice in the 256-byte region
     cudaError_t e = cudaStreamCreateWithFlags(&r.cin, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r.cout, cudaStreamNonBlocking);
-    r.ev.assign(2 + 2 * n + 2 * nw, nullptr);
+    r.ev.assign(2 + 2 * n + nw + (size_t)n * nw, nullptr);
     for (auto &x : r.ev)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_status(e, "host pipeline streams");
@@ -338,16 +338,16 @@ static comet_status_t run_host_pipe(const Plan &P, const void *const *host_in, v
     if (P.op == 2) { alpha = -alpha; beta = 1.0; }
     const bool x_is_b = h.side == 1;
     char *w = static_cast<char *>(ws);
-    char *sc_x = w + st.ws_scales;
+    // scale words: X slices in slots 0, nw + 1, nw + 2, ...; W slices in slots 1 .. nw
+    auto sc_x = [&](int j) { return w + st.ws_scales + 8 * (j == 0 ? 0 : nw + j); };
     auto sc_w = [&](int i) { return w + st.ws_scales + 8 * (1 + i); };
-    char *parts_x = w + (x_is_b ? st.ws_parts_b : st.ws_parts_a);
+    char *parts_x0 = w + (x_is_b ? st.ws_parts_b : st.ws_parts_a);
     char *parts_w0 = w + (x_is_b ? st.ws_parts_a : st.ws_parts_b);
     const bool emu = st.kernel == KK_GEMM_EMU;
     const size_t n_planes = emu ? 6 : 3;
-    // W slice i's planes sit one after another (every slice but the last has w_chunk label values)
-    auto parts_w = [&](int i) {
-        return parts_w0 + (size_t)i * n_planes * (size_t)(h.w_rows_inner * h.w_chunk) * (size_t)st.kpad * 2;
-    };
+    // every slice's planes sit after those of the slices before it
+    auto parts_x = [&](int j) { return parts_x0 + n_planes * (size_t)(h.rows_inner * h.xb[j]) * (size_t)st.kpad * 2; };
+    auto parts_w = [&](int i) { return parts_w0 + n_planes * (size_t)(h.w_rows_inner * h.wb[i]) * (size_t)st.kpad * 2; };
     auto split = emu ? launch_split6 : launch_split;
     const char *hx = static_cast<const char *>(host_in[h.x_in]);
     const char *hw = static_cast<const char *>(host_in[h.w_in]);
@@ -359,16 +359,12 @@ static comet_status_t run_host_pipe(const Plan &P, const void *const *host_in, v
     const size_t w_unit = (size_t)h.w_inner * h.w_outer * es;
     const size_t x_pitch = (size_t)h.x_inner * h.ext * es, c_pitch = (size_t)h.c_inner * h.ext * es;
     const size_t w_pitch = (size_t)h.w_inner * h.w_ext * es;
-    auto lx_of = [&](int q) { return std::min(h.chunk, h.ext - (int64_t)q * h.chunk); };
-    auto lw_of = [&](int i) { return std::min(h.w_chunk, h.w_ext - (int64_t)i * h.w_chunk); };
-    // The last column of GEMM blocks goes back block by block, so that only its last block's
-    // copy follows the last GEMM: possible when the result's W label sits directly below X's
-    // label L (a block is then a 3-D box: W-label runs x the slice's L values x the labels above
-    // L) or directly above it.
-    const bool w_below = h.wc_inner * h.w_ext == h.c_inner, w_above = h.c_inner * h.ext == h.wc_inner;
-    const bool blockwise = nw > 1 && (w_below || w_above);
-    auto copy_block = [&](int q, int i) {   // result block (W slice i, X slice q), device to host
-        const int64_t l0 = (int64_t)q * h.chunk, lc = lx_of(q), m0 = (int64_t)i * h.w_chunk, mc = lw_of(i);
+    auto lx_of = [&](int j) { return h.xb[j + 1] - h.xb[j]; };
+    auto lw_of = [&](int i) { return h.wb[i + 1] - h.wb[i]; };
+    // a result block is a 3-D box when the result's W label sits directly below or above L
+    const bool w_below = h.wc_inner * h.w_ext == h.c_inner;
+    auto copy_block = [&](int j, int i) {   // result block (W slice i, X slice j), device to host
+        const int64_t l0 = h.xb[j], lc = lx_of(j), m0 = h.wb[i], mc = lw_of(i);
         cudaMemcpy3DParms m = {};
         m.kind = cudaMemcpyDeviceToHost;
         if (w_below) {   // runs over the W label's slice, rows over L, slabs above L
@@ -379,29 +375,28 @@ static comet_status_t run_host_pipe(const Plan &P, const void *const *host_in, v
             m.extent = make_cudaExtent((size_t)mc * h.wc_inner * es, (size_t)lc, (size_t)h.c_outer);
         } else {         // runs over L's slice, rows over the W label, slabs above it
             const size_t pitch = (size_t)h.wc_inner * es;
-            const size_t slabs = (size_t)(h.c_outer / h.w_ext);
             m.srcPtr = make_cudaPitchedPtr(dc, pitch, pitch, (size_t)h.w_ext);
             m.dstPtr = make_cudaPitchedPtr(hc, pitch, pitch, (size_t)h.w_ext);
             m.srcPos = m.dstPos = make_cudaPos((size_t)l0 * h.c_inner * es, (size_t)m0, 0);
-            m.extent = make_cudaExtent((size_t)lc * h.c_inner * es, (size_t)mc, slabs);
+            m.extent = make_cudaExtent((size_t)lc * h.c_inner * es, (size_t)mc, (size_t)(h.c_outer / h.w_ext));
         }
         return cudaMemcpy3DAsync(&m, r.cout);
     };
 
-    // copies in: W_0, X_0, W_1.., X_1.. (and the result slices for "+=" / "-=" with X's)
+    // copies in, in the planned order (and the result slices for "+=" / "-=" with X's)
     e = cudaEventRecord(e0, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(r.cin, e0, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(r.cout, e0, 0);
     auto copy_w = [&](int i) {
-        const int64_t l0 = (int64_t)i * h.w_chunk, lc = lw_of(i);
+        const int64_t l0 = h.wb[i], lc = lw_of(i);
         const size_t ww = (size_t)h.w_inner * lc * es;
         cudaError_t ee = copy_slice(dw + l0 * w_unit, ww, hw + (size_t)l0 * h.w_inner * es, w_pitch, ww,
                                     (size_t)h.w_outer, cudaMemcpyHostToDevice, r.cin);
         if (ee == cudaSuccess) ee = cudaEventRecord(e_w[i], r.cin);
         return ee;
     };
-    auto copy_x = [&](int q) {
-        const int64_t l0 = (int64_t)q * h.chunk, lc = lx_of(q);
+    auto copy_x = [&](int j) {
+        const int64_t l0 = h.xb[j], lc = lx_of(j);
         const size_t xw = (size_t)h.x_inner * lc * es;
         cudaError_t ee = copy_slice(dx + l0 * x_unit, xw, hx + (size_t)l0 * h.x_inner * es, x_pitch, xw,
                                     (size_t)h.x_outer, cudaMemcpyHostToDevice, r.cin);
@@ -410,14 +405,13 @@ static comet_status_t run_host_pipe(const Plan &P, const void *const *host_in, v
             ee = copy_slice(dc + off, c_pitch, hc + off, c_pitch, (size_t)h.c_inner * lc * es,
                             (size_t)h.c_outer, cudaMemcpyHostToDevice, r.cin);
         }
-        if (ee == cudaSuccess) ee = cudaEventRecord(e_in[q], r.cin);
+        if (ee == cudaSuccess) ee = cudaEventRecord(e_in[j], r.cin);
         return ee;
     };
-    if (e == cudaSuccess) e = copy_w(0);
-    if (e == cudaSuccess) e = copy_x(0);
-    for (int i = 1; i < nw && e == cudaSuccess; ++i) e = copy_w(i);
-    for (int q = 1; q < n && e == cudaSuccess; ++q) e = copy_x(q);
-    if (e != cudaSuccess) return cuda_status(e, "host pipeline copy in");
+    for (int q : h.copies) {
+        e = q >= 0 ? copy_x(q) : copy_w(-1 - q);
+        if (e != cudaSuccess) return cuda_status(e, "host pipeline copy in");
+    }
 
     // scale and pre-pass of one slice, on the compute stream after its copy
     auto prep = [&](cudaEvent_t ready, char *src, int64_t n_elems, void *scale, const XposeParams &tmpl,
@@ -435,68 +429,70 @@ static comet_status_t run_host_pipe(const Plan &P, const void *const *host_in, v
         }
         return ee;
     };
-    for (int q = 0; q < n; ++q) {
-        const int64_t l0 = (int64_t)q * h.chunk, lc = lx_of(q);
-        const int cls = lc == h.chunk ? 0 : 1;
-        char *xs = dx + l0 * x_unit;
-        e = prep(e_in[q], xs, h.x_inner * lc * h.x_outer, sc_x, h.pre[cls], h.pre_vec[cls], h.pre_vout[cls], parts_x);
-        if (e != cudaSuccess) return cuda_status(e, "host pipeline pre-pass (X slice)");
-        for (int i = 0; i < nw; ++i) {
-            const int64_t m0 = (int64_t)i * h.w_chunk, mc = lw_of(i);
-            char *wsl = dw + m0 * w_unit;
-            if (q == 0) {
-                const int wcls = mc == h.w_chunk ? 0 : 1;
-                e = prep(e_w[i], wsl, h.w_inner * mc * h.w_outer, sc_w(i), h.w_pre[wcls], h.w_pre_vec[wcls],
-                         h.w_pre_vout[wcls], parts_w(i));
-                if (e != cudaSuccess) return cuda_status(e, "host pipeline pre-pass (W slice)");
-            }
-            GemmParams g = st.gemm;
-            Radix &rx = x_is_b ? g.nb : g.ma;
-            Radix &rw = x_is_b ? g.ma : g.nb;
-            const uint32_t rows_x = (uint32_t)(h.rows_inner * lc), rows_w = (uint32_t)(h.w_rows_inner * mc);
-            rx.ext[rx.n - 1] = (uint32_t)lc;
-            rx.fd[rx.n - 1] = make_fastdiv((uint32_t)lc);
-            rx.total = rows_x;
-            rw.ext[rw.n - 1] = (uint32_t)mc;
-            rw.fd[rw.n - 1] = make_fastdiv((uint32_t)mc);
-            rw.total = rows_w;
-            if (x_is_b) { g.N = rows_x; g.M = rows_w; } else { g.M = rows_x; g.N = rows_w; }
-            g.A = x_is_b ? static_cast<void *>(wsl) : static_cast<void *>(xs);
-            g.B = x_is_b ? static_cast<void *>(xs) : static_cast<void *>(wsl);
-            g.C = dc + ((size_t)l0 * h.c_inner + (size_t)m0 * h.wc_inner) * es;
-            g.alpha = alpha;
-            g.beta = beta;
-            g.status = status;
-            g.timeout_ns = timeout_ns(P);
-            void *pa = x_is_b ? static_cast<void *>(parts_w(i)) : static_cast<void *>(parts_x);
-            void *pb = x_is_b ? static_cast<void *>(parts_x) : static_cast<void *>(parts_w(i));
-            void *sa = x_is_b ? static_cast<void *>(sc_w(i)) : static_cast<void *>(sc_x);
-            void *sb = x_is_b ? static_cast<void *>(sc_x) : static_cast<void *>(sc_w(i));
-            if (emu) {
-                ProfScope ps(PK_EMU, s);
-                e = launch_gemm_emu(g, pa, pb, st.kpad, sa, sb, P.opts.debug_flags, s, 0);
-            } else {
-                ProfScope ps(PK_SPLIT, s);
-                e = launch_gemm_split(g, pa, pb, st.kpad, sa, sb, P.opts.kc, (int)es, P.opts.debug_flags, s, 0,
-                                      st.ksplit, reinterpret_cast<float *>(w + st.ws_ksplit));
-            }
-            if (e != cudaSuccess) return cuda_status(e, "host pipeline gemm");
-            if (blockwise && q == n - 1) {   // the last column: each block back as soon as it is done
-                e = cudaEventRecord(e_blk[i], s);
-                if (e == cudaSuccess) e = cudaStreamWaitEvent(r.cout, e_blk[i], 0);
-                if (e == cudaSuccess) e = copy_block(q, i);
-                if (e != cudaSuccess) return cuda_status(e, "host pipeline copy out (block)");
-            }
+    std::vector<char> done_x(n, 0), done_w(nw, 0);
+    std::vector<int> left(n, nw);
+    for (int u : h.blocks) {
+        const int i = u / n, j = u % n;
+        const int64_t l0 = h.xb[j], lc = lx_of(j), m0 = h.wb[i], mc = lw_of(i);
+        char *xs = dx + l0 * x_unit, *wsl = dw + m0 * w_unit;
+        if (!done_w[i]) {
+            e = prep(e_w[i], wsl, h.w_inner * mc * h.w_outer, sc_w(i), h.w_pre[i], h.w_pre_vec[i], h.w_pre_vout[i],
+                     parts_w(i));
+            if (e != cudaSuccess) return cuda_status(e, "host pipeline pre-pass (W slice)");
+            done_w[i] = 1;
         }
-        if (blockwise && q == n - 1) continue;
-        e = cudaEventRecord(e_g[q], s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(r.cout, e_g[q], 0);
-        if (e == cudaSuccess) {
-            const size_t off = (size_t)l0 * h.c_inner * es;
-            e = copy_slice(hc + off, c_pitch, dc + off, c_pitch, (size_t)h.c_inner * lc * es,
-                           (size_t)h.c_outer, cudaMemcpyDeviceToHost, r.cout);
+        if (!done_x[j]) {
+            e = prep(e_in[j], xs, h.x_inner * lc * h.x_outer, sc_x(j), h.pre[j], h.pre_vec[j], h.pre_vout[j],
+                     parts_x(j));
+            if (e != cudaSuccess) return cuda_status(e, "host pipeline pre-pass (X slice)");
+            done_x[j] = 1;
         }
-        if (e != cudaSuccess) return cuda_status(e, "host pipeline copy out");
+        GemmParams g = st.gemm;
+        Radix &rx = x_is_b ? g.nb : g.ma;
+        Radix &rw = x_is_b ? g.ma : g.nb;
+        const uint32_t rows_x = (uint32_t)(h.rows_inner * lc), rows_w = (uint32_t)(h.w_rows_inner * mc);
+        rx.ext[rx.n - 1] = (uint32_t)lc;
+        rx.fd[rx.n - 1] = make_fastdiv((uint32_t)lc);
+        rx.total = rows_x;
+        rw.ext[rw.n - 1] = (uint32_t)mc;
+        rw.fd[rw.n - 1] = make_fastdiv((uint32_t)mc);
+        rw.total = rows_w;
+        if (x_is_b) { g.N = rows_x; g.M = rows_w; } else { g.M = rows_x; g.N = rows_w; }
+        g.A = x_is_b ? static_cast<void *>(wsl) : static_cast<void *>(xs);
+        g.B = x_is_b ? static_cast<void *>(xs) : static_cast<void *>(wsl);
+        g.C = dc + ((size_t)l0 * h.c_inner + (size_t)m0 * h.wc_inner) * es;
+        g.alpha = alpha;
+        g.beta = beta;
+        g.status = status;
+        g.timeout_ns = timeout_ns(P);
+        void *pa = x_is_b ? static_cast<void *>(parts_w(i)) : static_cast<void *>(parts_x(j));
+        void *pb = x_is_b ? static_cast<void *>(parts_x(j)) : static_cast<void *>(parts_w(i));
+        void *sa = x_is_b ? static_cast<void *>(sc_w(i)) : static_cast<void *>(sc_x(j));
+        void *sb = x_is_b ? static_cast<void *>(sc_x(j)) : static_cast<void *>(sc_w(i));
+        if (emu) {
+            ProfScope ps(PK_EMU, s);
+            e = launch_gemm_emu(g, pa, pb, st.kpad, sa, sb, P.opts.debug_flags, s, 0);
+        } else {
+            ProfScope ps(PK_SPLIT, s);
+            e = launch_gemm_split(g, pa, pb, st.kpad, sa, sb, P.opts.kc, (int)es, P.opts.debug_flags, s, 0,
+                                  st.ksplit, reinterpret_cast<float *>(w + st.ws_ksplit));
+        }
+        if (e != cudaSuccess) return cuda_status(e, "host pipeline gemm");
+        if (h.blockwise) {   // this block's result back as soon as it is done
+            e = cudaEventRecord(e_blk[u], s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(r.cout, e_blk[u], 0);
+            if (e == cudaSuccess) e = copy_block(j, i);
+            if (e != cudaSuccess) return cuda_status(e, "host pipeline copy out (block)");
+        } else if (--left[j] == 0) {   // the column's last block: its result slice back
+            e = cudaEventRecord(e_g[j], s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(r.cout, e_g[j], 0);
+            if (e == cudaSuccess) {
+                const size_t off = (size_t)l0 * h.c_inner * es;
+                e = copy_slice(hc + off, c_pitch, dc + off, c_pitch, (size_t)h.c_inner * lc * es,
+                               (size_t)h.c_outer, cudaMemcpyDeviceToHost, r.cout);
+            }
+            if (e != cudaSuccess) return cuda_status(e, "host pipeline copy out");
+        }
     }
     e = cudaEventRecord(e_end, r.cout);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, e_end, 0);

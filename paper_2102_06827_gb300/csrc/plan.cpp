@@ -487,11 +487,13 @@ void prepass_params(const Step &st, const std::vector<int> &labels, std::map<int
     xp->out_plane = prod_ext(ext, rows) * st.kpad;
 }
 
-// Slices of the host-buffer pipeline (see HostPipe).  The slice count minimises a small event
-// model: the inputs cross the host link one after another (W, then the slices of X), each
-// slice's pre-pass and GEMM start when both its copy and the previous GEMM are done, and the
-// result slices go back in order.  A GEMM takes whole waves of output tiles over the SMs, so
-// slicing costs the partial last wave of every slice.
+// Slices of the host-buffer pipeline (see HostPipe).  The slicing minimises a small event
+// model: the inputs cross the host link one after another in the copy order, each slice's
+// pre-pass runs before its first GEMM block, a block starts when its slices are pre-passed and
+// the previous block is done, and results go back block by block (or column by column).  A
+// GEMM takes whole waves of output tiles over the SMs, so slicing costs each block's partial
+// last wave.  Candidates: equal slices, and slicings whose first slice is a half or a quarter of
+// an equal one (an earlier first block) with the rest equal.
 void setup_host_pipe(Plan *P, int64_t es, int want, int want_w) {
     const Step &st = P->steps[0];
     const Slot &sa = P->slots[st.a], &sb = P->slots[st.b], &sc = P->slots[st.c];
@@ -525,80 +527,145 @@ void setup_host_pipe(Plan *P, int64_t es, int want, int want_w) {
     const double t_tile = 2.0 * tm * tn * (double)st.kpad * prods / (kBf16FlopsPerS / 152);
     const double bw_in = 200e9, bw_out = 180e9, t_slice = 20e-6;
     const double planes = emu ? 12.0 : 6.0;
+    const bool layout_blocks = h.wc_inner * h.w_ext == h.c_inner || h.c_inner * h.ext == h.wc_inner;
     auto tiles_of = [&](int64_t lx, int64_t lw) {
         const int64_t r = h.rows_inner * lx, rw = h.w_rows_inner * lw;
         return h.side ? ((rw + tm - 1) / tm) * ((r + tn - 1) / tn) : ((r + tm - 1) / tm) * ((rw + tn - 1) / tn);
     };
-    // event model: copies in the order W_0, X_0, W_1.., X_1..; the compute stream runs, per X
-    // slice j, its pre-pass, then (for j = 0 after each W slice's pre-pass) the GEMMs of W
-    // slices 0.. against it; the result slice j goes back after its last GEMM
-    auto model = [&](int64_t nx, int64_t nw) {
-        const int64_t cx = (h.ext + nx - 1) / nx, cntx = (h.ext + cx - 1) / cx;
-        const int64_t cw = (h.w_ext + nw - 1) / nw, cntw = (h.w_ext + cw - 1) / cw;
-        auto lx_of = [&](int64_t j) { return std::min(cx, h.ext - j * cx); };
-        auto lw_of = [&](int64_t i) { return std::min(cw, h.w_ext - i * cw); };
-        std::vector<double> rx(cntx), rw(cntw);
-        double c = 0;
-        auto xbytes = [&](int64_t j) { return (double)h.x_inner * lx_of(j) * h.x_outer * es; };
-        auto cbytes = [&](int64_t j) { return (double)h.c_inner * lx_of(j) * h.c_outer * es; };
-        auto wbytes = [&](int64_t i) { return (double)h.w_inner * lw_of(i) * h.w_outer * es; };
-        c += wbytes(0) / bw_in; rw[0] = c;
-        c += (xbytes(0) + (P->op != 0 ? cbytes(0) : 0)) / bw_in; rx[0] = c;
-        for (int64_t i = 1; i < cntw; ++i) { c += wbytes(i) / bw_in; rw[i] = c; }
-        for (int64_t j = 1; j < cntx; ++j) { c += (xbytes(j) + (P->op != 0 ? cbytes(j) : 0)) / bw_in; rx[j] = c; }
-        const bool sliced = cntx > 1 || cntw > 1;
-        // the last column goes back block by block when the result's layout allows it
-        const bool blockwise = cntw > 1 && (h.wc_inner * h.w_ext == h.c_inner || h.c_inner * h.ext == h.wc_inner);
-        double t = 0, out = 0;
-        for (int64_t j = 0; j < cntx; ++j) {
-            const bool last_blocks = blockwise && j == cntx - 1;
-            t = std::max(t, rx[j]) + xbytes(j) / es * (es + planes) / kHbmBytesPerS;
-            for (int64_t i = 0; i < cntw; ++i) {
-                if (j == 0) t = std::max(t, rw[i]) + wbytes(i) / es * (es + planes) / kHbmBytesPerS;
-                t += (double)((tiles_of(lx_of(j), lw_of(i)) + 151) / 152) * t_tile + (sliced ? t_slice : 0);
-                if (last_blocks) out = std::max(out, t) + cbytes(j) * (double)lw_of(i) / (double)h.w_ext / bw_out;
-            }
-            if (!last_blocks) out = std::max(out, t) + cbytes(j) / bw_out;
-        }
-        return out;
-    };
-    auto aligned = [&](int64_t chunk, int64_t unit) {   // every slice starts on a 16-byte boundary
-        return ((int64_t)chunk * unit * es) % 16 == 0;
-    };
     const int64_t xu = h.x_inner * h.x_outer, wu = h.w_inner * h.w_outer;
-    int64_t best = 1, best_w = 1;
-    double best_t = model(1, 1);
-    h.model_s[0] = best_t;
-    std::vector<int64_t> cand_x, cand_w;
-    if (want > 1) cand_x.push_back(std::min<int64_t>(want, h.ext));
-    else cand_x = {1, 2, 3, 4, 6, 8, 12, 16};
-    if (want_w > 1) cand_w.push_back(std::min<int64_t>(want_w, h.w_ext));
-    else if (want_w == 0) cand_w = {1, 2, 3, 4, 6, 8};
-    else cand_w = {1};
-    const bool forced = want > 1 || want_w > 1;
-    for (int64_t nx : cand_x)
-        for (int64_t nw : cand_w) {
-            if (nx > h.ext || nw > h.w_ext || (nx == 1 && nw == 1)) continue;
-            if (!aligned((h.ext + nx - 1) / nx, xu) || !aligned((h.w_ext + nw - 1) / nw, wu)) continue;
-            const double t = model(nx, nw);
-            if (forced ? (best == 1 && best_w == 1) || t < best_t : t < best_t * 0.97) { best = nx; best_w = nw; best_t = t; }
+    // slice boundaries: n slices, the first one 1/ramp of an equal slice, the rest equal (the
+    // last may be shorter); empty when a slice would be empty or start off a 16-byte boundary
+    auto bounds_of = [&](int64_t E, int64_t n, int64_t ramp, int64_t unit) {
+        std::vector<int64_t> b;
+        if (n <= 1) return std::vector<int64_t>{0, E};
+        if (n > E) return b;
+        const int64_t eq = (E + n - 1) / n;
+        b.push_back(0);
+        int64_t pos = 0;
+        if (ramp > 1) {
+            const int64_t first = std::max<int64_t>(1, eq / ramp);
+            if (first >= eq) return std::vector<int64_t>();
+            pos = first;
+            b.push_back(pos);
+            const int64_t c = (E - pos + (n - 1) - 1) / (n - 1);
+            while (pos < E) { pos = std::min(E, pos + c); b.push_back(pos); }
+        } else {
+            while (pos < E) { pos = std::min(E, pos + eq); b.push_back(pos); }
         }
-    if (best == 1 && best_w == 1) return;
-    h.chunk = (h.ext + best - 1) / best;
-    h.n_chunks = (int)((h.ext + h.chunk - 1) / h.chunk);
-    h.w_chunk = (h.w_ext + best_w - 1) / best_w;
-    h.w_n = (int)((h.w_ext + h.w_chunk - 1) / h.w_chunk);
-    h.model_s[1] = best_t;
-    const int64_t tail = h.ext - (h.n_chunks - 1) * h.chunk, w_tail = h.w_ext - (h.w_n - 1) * h.w_chunk;
-    for (int c = 0; c < 2; ++c) {
+        for (int64_t v : b)
+            if ((v * unit * es) % 16 != 0 && v != E) return std::vector<int64_t>();
+        return b;
+    };
+    // copy order (alternating), block order (by the later of its two arrivals, then column,
+    // then row), and the modelled finish time
+    struct Sched { std::vector<int> copies, blocks; bool blockwise; double t; };
+    auto model = [&](const std::vector<int64_t> &xb, const std::vector<int64_t> &wb) {
+        Sched sd;
+        const int nx = (int)xb.size() - 1, nw = (int)wb.size() - 1;
+        sd.blockwise = layout_blocks && (nx > 1 || nw > 1);
+        std::vector<int> posx(nx), posw(nw);
+        for (int k = 0; k < std::max(nx, nw); ++k) {
+            if (k < nw) { posw[k] = (int)sd.copies.size(); sd.copies.push_back(-1 - k); }
+            if (k < nx) { posx[k] = (int)sd.copies.size(); sd.copies.push_back(k); }
+        }
+        auto lx = [&](int j) { return xb[j + 1] - xb[j]; };
+        auto lw = [&](int i) { return wb[i + 1] - wb[i]; };
+        auto xbytes = [&](int j) { return (double)h.x_inner * lx(j) * h.x_outer * es; };
+        auto cbytes = [&](int j) { return (double)h.c_inner * lx(j) * h.c_outer * es; };
+        auto wbytes = [&](int i) { return (double)h.w_inner * lw(i) * h.w_outer * es; };
+        std::vector<double> rx(nx), rw(nw);
+        double c = 0;
+        for (int q : sd.copies) {
+            if (q >= 0) { c += (xbytes(q) + (P->op != 0 ? cbytes(q) : 0)) / bw_in; rx[q] = c; }
+            else { c += wbytes(-1 - q) / bw_in; rw[-1 - q] = c; }
+        }
+        for (int i = 0; i < nw; ++i)
+            for (int j = 0; j < nx; ++j) sd.blocks.push_back(i * nx + j);
+        std::stable_sort(sd.blocks.begin(), sd.blocks.end(), [&](int u, int v) {
+            const int iu = u / nx, ju = u % nx, iv = v / nx, jv = v % nx;
+            const int au = std::max(posw[iu], posx[ju]), av = std::max(posw[iv], posx[jv]);
+            if (au != av) return au < av;
+            if (ju != jv) return ju < jv;
+            return iu < iv;
+        });
+        const bool sliced = nx > 1 || nw > 1;
+        std::vector<char> px(nx, 0), pw(nw, 0);
+        std::vector<int> left(nx, nw);
+        double t = 0, out = 0;
+        for (int u : sd.blocks) {
+            const int i = u / nx, j = u % nx;
+            if (!pw[i]) { t = std::max(t, rw[i]) + wbytes(i) / es * (es + planes) / kHbmBytesPerS; pw[i] = 1; }
+            if (!px[j]) { t = std::max(t, rx[j]) + xbytes(j) / es * (es + planes) / kHbmBytesPerS; px[j] = 1; }
+            t += (double)((tiles_of(lx(j), lw(i)) + 151) / 152) * t_tile + (sliced ? t_slice : 0);
+            if (sd.blockwise) out = std::max(out, t) + cbytes(j) * (double)lw(i) / (double)h.w_ext / bw_out;
+            else if (--left[j] == 0) out = std::max(out, t) + cbytes(j) / bw_out;
+        }
+        sd.t = std::max(out, t);
+        return sd;
+    };
+    const std::vector<int64_t> one_x = {0, h.ext}, one_w = {0, h.w_ext};
+    Sched best = model(one_x, one_w);
+    std::vector<int64_t> bx = one_x, bw = one_w;
+    h.model_s[0] = best.t;
+    const bool forced = want > 1 || want_w > 1;
+    std::vector<std::vector<int64_t>> cand_x, cand_w;
+    if (want > 1) cand_x.push_back(bounds_of(h.ext, std::min<int64_t>(want, h.ext), 1, xu));
+    else for (int n : {1, 2, 3, 4, 6, 8}) for (int r : {1, 2, 4}) if (n > 1 || r == 1) cand_x.push_back(bounds_of(h.ext, n, r, xu));
+    if (want_w > 1) cand_w.push_back(bounds_of(h.w_ext, std::min<int64_t>(want_w, h.w_ext), 1, wu));
+    else if (want_w == 0) { for (int n : {1, 2, 3, 4, 6, 8}) for (int r : {1, 2, 4}) if (n > 1 || r == 1) cand_w.push_back(bounds_of(h.w_ext, n, r, wu)); }
+    else cand_w.push_back(one_w);
+    // among the candidates the model finishes within 1 % of the first one, the one with the
+    // fewest GEMM blocks (the model does not see every cost of a small block); unless forced,
+    // it must beat no slicing by 3 %
+    struct Cand { Sched sd; std::vector<int64_t> xb, wb; };
+    std::vector<Cand> cands;
+    const double t_whole = best.t;
+    for (const auto &xb : cand_x)
+        for (const auto &wb : cand_w) {
+            if (xb.size() < 2 || wb.size() < 2) continue;
+            const int nx = (int)xb.size() - 1, nw = (int)wb.size() - 1;
+            if ((nx == 1 && nw == 1) || nx + nw > 31 || nx * nw > 64) continue;
+            cands.push_back(Cand{model(xb, wb), xb, wb});
+        }
+    if (cands.empty()) return;
+    double t_min = cands[0].sd.t;
+    for (const Cand &c : cands) t_min = std::min(t_min, c.sd.t);
+    const Cand *pick = nullptr;
+    for (const Cand &c : cands) {
+        if (c.sd.t > t_min * 1.01) continue;
+        if (!pick || c.sd.blocks.size() < pick->sd.blocks.size() ||
+            (c.sd.blocks.size() == pick->sd.blocks.size() && c.sd.t < pick->sd.t))
+            pick = &c;
+    }
+    if (!forced && pick->sd.t > t_whole * 0.97) return;
+    best = pick->sd;
+    bx = pick->xb;
+    bw = pick->wb;
+    h.xb = bx;
+    h.wb = bw;
+    h.n_chunks = (int)bx.size() - 1;
+    h.w_n = (int)bw.size() - 1;
+    h.copies = best.copies;
+    h.blocks = best.blocks;
+    h.blockwise = best.blockwise;
+    h.model_s[1] = best.t;
+    h.pre.resize(h.n_chunks);
+    h.pre_vec.assign(h.n_chunks, 1);
+    h.pre_vout.assign(h.n_chunks, 1);
+    for (int j = 0; j < h.n_chunks; ++j) {
         std::vector<int64_t> e = P->extent;
-        e[h.label] = c == 0 ? h.chunk : tail;
-        prepass_params(st, sx.labels, label_strides(sx.labels, e), 0, rows, e, es, &h.pre[c], &h.pre_vec[c],
-                       &h.pre_vout[c]);
+        e[h.label] = bx[j + 1] - bx[j];
+        prepass_params(st, sx.labels, label_strides(sx.labels, e), 0, rows, e, es, &h.pre[j], &h.pre_vec[j],
+                       &h.pre_vout[j]);
+    }
+    h.w_pre.resize(h.w_n);
+    h.w_pre_vec.assign(h.w_n, 1);
+    h.w_pre_vout.assign(h.w_n, 1);
+    for (int i = 0; i < h.w_n; ++i) {
         std::vector<int64_t> ew = P->extent;
-        ew[h.w_label] = c == 0 ? h.w_chunk : w_tail;
-        prepass_params(st, sw.labels, label_strides(sw.labels, ew), 0, wrows, ew, es, &h.w_pre[c],
-                       &h.w_pre_vec[c], &h.w_pre_vout[c]);
+        ew[h.w_label] = bw[i + 1] - bw[i];
+        prepass_params(st, sw.labels, label_strides(sw.labels, ew), 0, wrows, ew, es, &h.w_pre[i], &h.w_pre_vec[i],
+                       &h.w_pre_vout[i]);
     }
     h.ok = true;
     P->pipe = h;
@@ -1205,12 +1272,21 @@ std::string describe_plan(const Plan &P) {
         }
         o << "]";
     }
-    if (P.pipe.ok)
+    if (P.pipe.ok) {
+        auto list = [&](const std::vector<int64_t> &v) {
+            std::ostringstream l;
+            l << "[";
+            for (size_t k = 0; k < v.size(); ++k) l << (k ? "," : "") << v[k];
+            l << "]";
+            return l.str();
+        };
         o << ",\"host_pipe\":{\"slices\":" << P.pipe.n_chunks << ",\"label\":\""
-          << P.label_names[P.pipe.label] << "\",\"chunk\":" << P.pipe.chunk << ",\"side\":\""
+          << P.label_names[P.pipe.label] << "\",\"bounds\":" << list(P.pipe.xb) << ",\"side\":\""
           << (P.pipe.side ? "N" : "M") << "\",\"w_slices\":" << P.pipe.w_n << ",\"w_label\":\""
-          << P.label_names[P.pipe.w_label] << "\",\"w_chunk\":" << P.pipe.w_chunk << ",\"model_s\":[" << P.pipe.model_s[0] << ","
+          << P.label_names[P.pipe.w_label] << "\",\"w_bounds\":" << list(P.pipe.wb)
+          << ",\"blockwise\":" << (P.pipe.blockwise ? "true" : "false") << ",\"model_s\":[" << P.pipe.model_s[0] << ","
           << P.pipe.model_s[1] << "]}";
+    }
     o << "}";
     return o.str();
 }

@@ -90,32 +90,37 @@ struct Step {
 };
 
 // Host-buffer pipeline of a one-step split or emulated-FP64 plan (comet_contract_host): the
-// larger operand X is copied to the device in slices along the last (slowest) label L of its
-// GEMM row group; the other operand W is copied whole first.  Each slice lands compact (its
-// own column-major layout with L shortened), is pre-passed and multiplied while the next slice
-// is copied, and the matching slice of the result is copied back while the next one is
-// multiplied.  Slice j of the GEMM covers rows [l0*rows_inner, (l0+lc)*rows_inner) of its group.
+// larger operand X crosses in slices along the last (slowest) label L of its GEMM row group, the
+// other operand W in slices along the last label of its own row group.  Each slice lands compact
+// (its own column-major layout with the label shortened), gets its own scale word and planes,
+// and is pre-passed when its copy is in; GEMM block (i, j) = W slice i x X slice j (the step's
+// GEMM with both row groups shortened, writing through the full result strides) runs once both
+// are in.  Copies alternate W_0, X_0, W_1, X_1, ...; blocks run in the order their inputs
+// arrive; results go back block by block when the result's layout makes a block a 3-D box,
+// else column by column after a column's last block.
 struct HostPipe {
     bool ok = false;
     int side = 1;                // 1: X is the N operand (GEMM B), 0: the M operand (GEMM A)
     int x_in = 1, w_in = 0;      // input positions of X and W
     int label = -1;              // L
-    int64_t ext = 0, chunk = 0;  // extent of L and of one slice (the last one may be shorter)
-    int n_chunks = 0;
+    int64_t ext = 0;             // extent of L
+    int n_chunks = 0;            // X slices
+    std::vector<int64_t> xb;     // X slice boundaries along L (n_chunks + 1)
     int64_t x_inner = 1, x_outer = 1;  // X elements below L (its stride), and the count above it
     int64_t c_inner = 1, c_outer = 1;  // the same for the result
     int64_t rows_inner = 1;      // GEMM rows of X's group per unit of L
-    XposeParams pre[2];          // pre-pass of a compact slice: full slice, short last slice
-    int pre_vec[2] = {1, 1}, pre_vout[2] = {1, 1};
-    // W may be sliced too, along the last label of its own row group, so that the first GEMMs
-    // start before all of W has crossed: GEMM block (i, j) = W slice i x X slice j, each W slice
-    // with its own scale and planes; order: W_0, X_0, W_1.., then X_1.. (GEMMs column by column)
+    std::vector<XposeParams> pre;      // pre-pass of each X slice
+    std::vector<int> pre_vec, pre_vout;
     int w_label = -1;
-    int64_t w_ext = 1, w_chunk = 1;
+    int64_t w_ext = 1;
     int w_n = 1;
+    std::vector<int64_t> wb;     // W slice boundaries along its label (w_n + 1)
     int64_t w_inner = 1, w_outer = 1, wc_inner = 1, w_rows_inner = 1;
-    XposeParams w_pre[2];
-    int w_pre_vec[2] = {1, 1}, w_pre_vout[2] = {1, 1};
+    std::vector<XposeParams> w_pre;
+    std::vector<int> w_pre_vec, w_pre_vout;
+    std::vector<int> copies;     // copy order: j >= 0 X slice j, -1 - i W slice i
+    std::vector<int> blocks;     // GEMM order: i * n_chunks + j
+    bool blockwise = false;      // results go back block by block
     double model_s[2] = {0, 0};  // modelled seconds: unpipelined, pipelined
 };
 

@@ -76,6 +76,19 @@ def test_pipeline_split(comet, slices, w_slices, ext):
     assert torch.equal(dout.cpu(), host_col(C, np.float32, False))
 
 
+@pytest.mark.parametrize("expr,blockwise", [
+    ("C[j,i,c] = A[i,k,c] * B[k,j]", False),   # a label between the two sliced ones: column copies
+    ("C[c,i,j] = A[i,k,c] * B[k,j]", True),    # the W label next to the sliced one: block copies
+])
+def test_pipeline_copy_out_routes(comet, expr, blockwise):
+    ext = dict(i=40, c=24, k=32, j=20)
+    A, B = inputs(expr, ext, 11)
+    C, p, _ = run_host(comet, expr, ext, [A, B], np.float32, "split_bf16", host_slices=3, host_slices_w=2)
+    hp = p.info["host_pipe"]
+    assert hp["blockwise"] == blockwise and hp["slices"] == 3 and hp["w_slices"] == 2
+    assert normwise(C, oracle.einsum(expr, A, B)) <= 1e-6
+
+
 def test_pipeline_integers_exact_and_equal_to_device_path(comet):
     ext = dict(i=16, j=12, k=16, a=32, b=48, c=32)
     A, B = inputs(CCSD, ext, 4, kind="int", lo=-3, hi=3)

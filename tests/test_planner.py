@@ -314,7 +314,11 @@ def test_host_pipeline_plans():
     hp = plan(ccsd, full, "f32", precision="split_bf16").info["host_pipe"]
     assert hp["slices"] > 1 and hp["side"] == "N" and hp["label"] == "j"
     assert hp["model_s"][1] < hp["model_s"][0]
-    assert 64 % hp["chunk"] == 0 or hp["slices"] == -(-64 // hp["chunk"])
+    # slice boundaries cover the label in order; on this layout results go back block by block
+    for key, n, ext in (("bounds", hp["slices"], 64), ("w_bounds", hp["w_slices"], 192)):
+        b = hp[key]
+        assert b[0] == 0 and b[-1] == ext and len(b) == n + 1 and all(x < y for x, y in zip(b, b[1:]))
+    assert hp["blockwise"]
     assert "host_pipe" in plan(ccsd, full, "f64", precision="emu_f64").info
     for kw in (dict(precision="native"), dict(precision="split_bf16", host_slices=1)):
         assert "host_pipe" not in plan(ccsd, full, "f32", **kw).info
@@ -324,13 +328,13 @@ def test_host_pipeline_plans():
     # explicit slice counts: ceil(ext / s) per slice, the last one shorter
     hp = plan(ccsd, dict(i=16, j=18, k=16, a=40, b=48, c=48), "f32", precision="split_bf16",
               host_slices=4).info["host_pipe"]
-    assert (hp["chunk"], hp["slices"]) == (5, 4)
+    assert hp["bounds"] == [0, 5, 10, 15, 18] and hp["slices"] == 4
     # B[k,n] slices of n hold k=5 FP32 values per unit: 3 units = 60 bytes is not 16-aligned
     e = "C[m,n] = A[m,k] * B[k,n]"
     assert "host_pipe" not in plan(e, dict(m=4, n=9, k=5), "f32", precision="split_bf16",
                                    host_slices=3).info
     hp = plan(e, dict(m=4, n=9, k=8), "f32", precision="split_bf16", host_slices=3).info["host_pipe"]
-    assert hp["label"] == "n" and hp["chunk"] == 3
+    assert hp["label"] == "n" and hp["bounds"] == [0, 3, 6, 9]
 
 
 def test_views_and_diagonals_layout():
