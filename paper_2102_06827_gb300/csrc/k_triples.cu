@@ -6,13 +6,16 @@
 // contracts a single label (the paper's Section 2 contraction with K = that label's extent),
 // so each term is a tiny-K outer-product sum and T_b is far larger than the operands: writing
 // T_b to memory and reading it back per term would make the path bound by HBM traffic that the
-// algorithm does not need.  Here T_b never leaves the SM:
+// algorithm does not need.  Here T_b never leaves the SM.  FP32 plans run on the tensor cores
+// (k_triples_tc.cu) unless a block's split operands exceed one batch of the workspace; then, and
+// for FP64 plans, the FMA kernels of this file run them:
 //
 //   * a work item is one 4^6 tile of one block; persistent CTAs take items in chunks from one
 //     atomic counter, walking the blocks in order;
-//   * each of the 256 threads holds 16 elements of the tile in registers: 4 x 4 along two
-//     "owned" labels, the other four labels fixed per thread;
-//   * a step is one term and one chunk of its summed label (32 values for FP32, 16 for FP64):
+//   * FP64 (triples_kernel<double>): each of the 256 threads holds 16 elements of the tile in
+//     registers, 4 x 4 along two "owned" labels, the other four labels fixed per thread (the
+//     FP32 kernel, triples_f32_kernel, further below, holds 2^6 per thread instead);
+//   * a step is one term and one chunk of its summed label (16 values for FP64):
 //     the X and Y tiles (chunk x 4^3) of step s+1 are copied into shared memory with cp.async
 //     while step s runs on the other buffer; each thread adds its 16 dot products into its T
 //     elements (a term with alpha = -1 negates them before and after; any other alpha but 1
