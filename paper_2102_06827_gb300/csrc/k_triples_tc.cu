@@ -18,7 +18,7 @@
 //     item, term and chunk, the three planes of both operand tiles into a ring slot (one 2-D
 //     tensor map over all plane rows, 64-row boxes, 64-byte swizzle); one thread issues the six
 //     products (hh, hm, mh, hl, lh, mm; the dropped ones are below 2^-26 relative) as tcgen05
-//     MMAs of 128 x 64 x 16 into one of two tensor-memory accumulators; sixteen drain warps
+//     MMAs of 128 x 64 x 16 into one of four tensor-memory accumulators; sixteen drain warps
 //     (four per lane quadrant, 16 columns each) load the accumulator and add alpha times it into
 //     the pair-tile, the first term storing (column offsets are constants of the term's label
 //     split: one code path per split); then the energy of the pair-tile's elements inside the
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     uint8_t *smem = smem_raw + (((raw + 1023) & ~1023u) - raw);
     uint8_t *ring = smem;                                            // RING x SLOT
     uint64_t *bars = reinterpret_cast<uint64_t *>(ring + RING * SLOT);
-    uint64_t *full = bars, *empty = bars + RING, *tfull = bars + 2 * RING, *tempty = tfull + 2, *mma_done = tempty + 2;
+    uint64_t *full = bars, *empty = bars + RING, *tfull = bars + 2 * RING, *tempty = tfull + NACC, *mma_done = tempty + NACC;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_done + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     double *s_red = reinterpret_cast<double *>(tmem_slot + 4);     // DRAIN_WARPS partial sums
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < RING; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-        for (int s = 0; s < 2; ++s) { mbar_init(&tfull[s], 1); mbar_init(&tempty[s], DRAIN_WARPS); }
+        for (int s = 0; s < NACC; ++s) { mbar_init(&tfull[s], 1); mbar_init(&tempty[s], DRAIN_WARPS); }
         mbar_init(mma_done, 1);
         *abort_flag = 0;
         fence_barrier_init();
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 for (int p = 0; p < a.n_terms && ok; ++p, ++tcount) {
                     const TcRec rec = load_rec(t.rec, (int64_t)item.b * a.n_terms + p);
                     const int ed = rec.ed, nch = rec.nch;
-                    const uint32_t ab = tcount & 1, rnd = tcount >> 1;
+                    const uint32_t ab = tcount % NACC, rnd = tcount / NACC;
                     if (rnd > 0 && !mbar_wait(&tempty[ab], (rnd - 1) & 1, tmo, abort_flag)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t d = tmem_base + ab * NROWS;
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             const int32_t *ext_b = a.ext + (int64_t)item.b * a.n_labels;
             for (int p = 0; p < a.n_terms; ++p, ++tcount) {
                 const TermDev &tm = a.term[p];
-                const uint32_t ab = tcount & 1, rnd = tcount >> 1;
+                const uint32_t ab = tcount % NACC, rnd = tcount / NACC;
                 uint32_t r[16];
                 if (!dead) {
                     bool ok = mbar_wait(&tfull[ab], rnd & 1, tmo, abort_flag);

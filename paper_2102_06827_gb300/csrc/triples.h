@@ -49,10 +49,11 @@ constexpr int NROWS = 64;          // rows of the other operand (4 x 4 x 4)
 constexpr int BOX = 64;            // rows per TMA box
 constexpr int WPLANE = WROWS * ROWB, NPLANE = NROWS * ROWB;
 constexpr int SLOT = 3 * (WPLANE + NPLANE);   // one (term, chunk): three planes of both operands
-constexpr int RING = 3;
+constexpr int RING = 4;
+constexpr int NACC = 4;            // tensor-memory accumulators (64 columns each)
 constexpr int DRAIN_WARPS = 16;    // four per tensor-memory lane quadrant, 16 columns each
 constexpr int THREADS = 64 + 32 * DRAIN_WARPS;
-constexpr uint32_t TMEM_COLS = 128;   // two 64-column accumulators
+constexpr uint32_t TMEM_COLS = NACC * NROWS;
 constexpr int TSZ = 10912;         // the pair-tile in shared memory (floats)
 // element strides of the pair-tile per T label: every label but 0 has a stride = 8 mod 32, so
 // the 32 rows a warp drains (8 along label 0 x 4 along one more label) hit 32 different banks
