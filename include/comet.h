@@ -180,7 +180,7 @@ comet_status_t comet_plan_views(const char *expr, const comet_extent_t *extents,
  *     E_b = sum over the elements of T_b of T_b^2 / D_b,
  *     D_b[l_1..l_6] = sum_q signs[q] * eps_bq[l_q]  (l_q: the q-th label of T)
  * T never goes to memory. COMET_F32 plans run on the tensor cores: a pre-pass writes every
- * operand as three bfloat16 parts (x = h + m + l, residual below 2^-26 |x|) into the workspace,
+ * operand as three bfloat16 parts (x = h + m + l, residual at most 2^-24 |x|) into the workspace,
  * blocks taken in batches whose parts fit it (at most 2^27 rows of 64 bytes, 8 GB; the
  * environment variable COMET_TRIPLES_BATCH_ROWS lowers the cap); each CTA forms, per tile of
  * 8 x 4^5 values of T_b and term, the six-product split sum in tensor memory, adds it into the

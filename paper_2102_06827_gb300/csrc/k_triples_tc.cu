@@ -11,13 +11,13 @@
 // share of E_b = sum T^2 / D_b.
 //
 //   * pre-pass (triples_tc_split_kernel): every operand of the batch's blocks is written once
-//     as split-BF16 planes (x = h + m + l, three bfloat16, residual below 2^-26 |x|), in rows of
+//     as split-BF16 planes (x = h + m + l, three bfloat16, residual at most 2^-24 |x|), in rows of
 //     32 summed indices (64 bytes), tile-blocked: [tile][chunk][plane][row of the tile], rows
 //     and summed indices outside the block zero;
 //   * main kernel (triples_tc_kernel), persistent, one CTA per SM: a TMA warp loads, per work
 //     item, term and chunk, the three planes of both operand tiles into a ring slot (one 2-D
 //     tensor map over all plane rows, 64-row boxes, 64-byte swizzle); one thread issues the six
-//     products (hh, hm, mh, hl, lh, mm; the dropped ones are below 2^-26 relative) as tcgen05
+//     products (hh, hm, mh, hl, lh, mm; the dropped ml, lm, ll sum to at most 2^-23 relative) as tcgen05
 //     MMAs of 128 x 64 x 16 into one of four tensor-memory accumulators; sixteen drain warps
 //     (four per lane quadrant, 16 columns each) load the accumulator and add alpha times it into
 //     the pair-tile, the first term storing (column offsets are constants of the term's label
@@ -43,8 +43,9 @@ using namespace tri;
 
 namespace {
 
-// x = h + m + l with each part the bfloat16 nearest to what is left: |x - h| <= 2^-9 |x|, and
-// the residual after l is below 2^-26 |x| (each subtraction is exact in FP32)
+// x = h + m + l with each part the bfloat16 nearest to what is left (8 significant bits each):
+// |x - h| <= 2^-8 |x|, |x - h - m| <= 2^-16 |x|, and the residual after l is at most 2^-24 |x|
+// (each subtraction is exact in FP32)
 __device__ __forceinline__ void split_bf16x3(float x, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &l) {
     h = __float2bfloat16_rn(x);
     const float r1 = x - __bfloat162float(h);
