@@ -833,6 +833,10 @@ comet_status_t comet_triples_energy(comet_plan_t plan, const void *operands, con
             if (v > 0) tmo_ms = v;
         }
         t.timeout_ns = tmo_ms * 1000000ll;
+        // COMET_TRIPLES_DEBUG=1 withholds one ring slot's loads (host-side fault injection: the
+        // wait for them runs out and records COMET_ERR_TIMEOUT)
+        t.debug_flags = 0;
+        if (const char *env = std::getenv("COMET_TRIPLES_DEBUG")) t.debug_flags = std::atoi(env);
         e = t.status ? launch_triples_tc(P, a, t, s) : cudaErrorInvalidValue;
         prof_end(h, s);
         if (e != cudaSuccess) { set_error_message(cudaGetErrorString(e)); return COMET_ERR_CUDA; }

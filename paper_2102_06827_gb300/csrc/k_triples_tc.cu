@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         if (lane == 0) {
             // ---------------- TMA producer ----------------
             uint32_t rit = 0;
-            bool ok = true;
+            bool ok = true, injected = false;
             ItemWalk walk;
             if ((int64_t)blockIdx.x < n_items) walk.start(a, t, blockIdx.x);
             for (int64_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
@@ -342,6 +342,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                         if (rnd > 0 && !mbar_wait(&empty[s], (rnd - 1) & 1, tmo, abort_flag)) { ok = false; break; }
                         mbar_arrive_expect_tx(&full[s], SLOT);
                         ++rit;
+                        if ((t.debug_flags & 1) && !injected && blockIdx.x == 0) {
+                            injected = true;   // fault injection: this slot's loads are withheld
+                            continue;
+                        }
                         uint8_t *dst = ring + s * SLOT;
 #pragma unroll
                         for (int pl = 0; pl < 3; ++pl) {

@@ -115,6 +115,7 @@ struct TcArgs {
     int64_t item0, n_items;    // its pair-tiles
     int *status;               // device status word (a wait that ran out records COMET_ERR_TIMEOUT)
     int64_t timeout_ns;        // limit of every wait
+    int debug_flags;           // bit 0: one ring slot's loads withheld (fault injection, host side)
 };
 }  // namespace tri
 

@@ -89,6 +89,23 @@ def test_uniform(comet, exts, dtype, tol):
     assert np.all(np.abs(got - ref) <= tol * np.abs(ref))
 
 
+def test_fp32_withheld_load_times_out_and_context_survives(comet, monkeypatch):
+    # fault injection on the host side of the tensor-core path: one ring slot's operand loads
+    # are withheld, the MMA thread's bounded wait runs out, the status word reports it, and the
+    # next launch on the same context is correct
+    exts = SHAPES[1]
+    monkeypatch.setenv("COMET_TRIPLES_DEBUG", "1")
+    monkeypatch.setenv("COMET_WAIT_TIMEOUT_MS", "100")
+    with pytest.raises(comet.CometError) as err:
+        run(comet, exts, np.float32, 3)
+    assert err.value.name == "COMET_ERR_TIMEOUT"
+    monkeypatch.delenv("COMET_TRIPLES_DEBUG")
+    monkeypatch.delenv("COMET_WAIT_TIMEOUT_MS")
+    got, ref, plan = run(comet, exts, np.float32, 3)
+    assert plan.info["tensor_core"]
+    assert np.all(np.abs(got - ref) <= 2e-5 * np.abs(ref))
+
+
 @pytest.mark.parametrize("route", ["batches", "fma"])
 def test_fp32_routes(comet, monkeypatch, route):
     # the FP32 tensor-core path with one batch per block, and the FP32 FMA kernel (a batch cap
