@@ -321,6 +321,31 @@ comet_status_t comet_contract_host(comet_plan_t plan, const void *const *host_in
                                    void *workspace, void *stream);
 
 /*
+ * comet_contract_host_n — n_calls independent evaluations of the same plan from host buffers to
+ * host buffers (the contraction of Section 2 each time), through one set of device buffers,
+ * then synchronises `stream`.  comet_contract_host() is this call with n_calls = 1.
+ *
+ *   host_inputs   n_calls x n_in host pointers, call-major: call t's input i is
+ *                 host_inputs[t * n_in + i].  The same host buffer may serve several calls.
+ *   host_outputs  n_calls host pointers; call t's result lands in host_outputs[t] (for "+=" /
+ *                 "-=" it is read as well).  Calls that share an output buffer write it in call
+ *                 order, so the buffer ends with the last of them.
+ *   dev_inputs, dev_output, workspace   as for comet_contract_host(), shared by every call; the
+ *                 device output holds the last call's result afterwards.
+ * Pipeline: with the slice pipeline (see comet_contract_host()), the copies of call t + 1 run
+ * while call t computes: a slice's copy into its device buffer waits only for call t's
+ * pre-pass of that slice, and each GEMM block of call t + 1 waits only for call t's copy-out
+ * of the same result region, so that in steady state the host link is hidden behind the GEMMs.
+ * Every call's result is the one comet_contract_host() gives for its inputs, bit for bit.
+ * Otherwise the calls run one after another on `stream`.
+ * Returns COMET_ERR_ARG for n_calls < 1, COMET_ERR_NULL for a missing pointer, else the codes
+ * of comet_contract_host(); the host buffers stay in use until the call returns.
+ */
+comet_status_t comet_contract_host_n(comet_plan_t plan, int n_calls, const void *const *host_inputs,
+                                     void *const *host_outputs, void *const *dev_inputs, void *dev_output,
+                                     void *workspace, void *stream);
+
+/*
  * comet_transpose — pure permutation of a dense tensor (Section 6, "Transpose optimization";
  * the ta.copy of Section 5 with alpha = 1).  Elements are moved as raw 4- or 8-byte words,
  * so the result is bit-exact (NaN payloads, -0.0, subnormals survive).

@@ -172,6 +172,23 @@ class Plan:
                    "comet_contract_host")
         return host_output
 
+    def contract_host_n(self, host_inputs, host_outputs, dev_inputs, dev_output, workspace=None, stream=None):
+        """comet_contract_host_n(): len(host_outputs) evaluations from host buffers, call t taking
+        host_inputs[t] (a list of the plan's inputs) and writing host_outputs[t], pipelined
+        through one set of device buffers; synchronises the stream."""
+        def hp(x):
+            return x.ctypes.data if hasattr(x, "ctypes") else x.data_ptr()
+        n = len(host_outputs)
+        if len(host_inputs) != n or any(len(x) != self.n_in for x in host_inputs):
+            raise ValueError("host_inputs: one list of the plan's inputs per output")
+        hin = (ctypes.c_void_p * (n * self.n_in))(*[hp(x) for xs in host_inputs for x in xs])
+        hout = (ctypes.c_void_p * n)(*[hp(x) for x in host_outputs])
+        din = (ctypes.c_void_p * self.n_in)(*[t.data_ptr() for t in dev_inputs])
+        _lib.check(lib().comet_contract_host_n(self._h, n, hin, hout, din, _ptr(dev_output), _ptr(workspace),
+                                               _stream_handle(stream)),
+                   "comet_contract_host_n")
+        return host_outputs
+
     def close(self):
         if getattr(self, "_h", None):
             lib().comet_plan_destroy(self._h)

@@ -22,6 +22,7 @@ ORDER_PLANNED, ORDER_NATURAL = 0, 1
 EXPORTS = [
     "comet_plan_opts_default", "comet_plan", "comet_plan_views", "comet_plan_workspace", "comet_plan_flops",
     "comet_plan_flops_natural", "comet_plan_describe", "comet_adjoint_expr", "comet_contract", "comet_contract_noalloc", "comet_contract_host",
+    "comet_contract_host_n",
     "comet_transpose", "comet_fill", "comet_plan_batched", "comet_batched_num_tiles", "comet_batched_set_tile",
     "comet_batched_prepare", "comet_contract_batched", "comet_batched_autotune",
     "comet_plan_triples", "comet_triples_prepare", "comet_triples_energy",
@@ -86,6 +87,8 @@ def load():
     L.comet_contract.argtypes = [vp, ctypes.POINTER(vp), vp, vp, vp]
     L.comet_contract_noalloc.argtypes = [vp, ctypes.POINTER(vp), vp, vp]
     L.comet_contract_host.argtypes = [vp, ctypes.POINTER(vp), vp, ctypes.POINTER(vp), vp, vp, vp]
+    L.comet_contract_host_n.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                        ctypes.POINTER(vp), vp, vp, vp]
     L.comet_transpose.argtypes = [ctypes.c_int, i64p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                   vp, vp, vp]
     L.comet_fill.argtypes = [vp, ctypes.c_int64, ctypes.c_double, ctypes.c_int, vp]

@@ -303,9 +303,14 @@ static cudaError_t copy_slice(void *dst, size_t dpitch, const void *src, size_t 
 // (i, j) multiplies W slice i by X slice j (the step's GEMM with both row groups shortened,
 // writing the result through the full result strides from the block's first element) in the
 // planned block order; results go back on a third stream, block by block when the layout
-// allows, else each result slice after its column's last block.
-static comet_status_t run_host_pipe(const Plan &P, const void *const *host_in, void *host_out,
-                                    void *const *dev_in, void *dev_out, void *ws, cudaStream_t s) {
+// allows, else each result slice after its column's last block.  n_calls contractions of the
+// same plan run back to back through the same device buffers: the copies of call t + 1 start
+// while call t still computes, each slice's copy waiting only for the pre-pass of call t that
+// read the slice's device buffer, and each GEMM block waiting only for the copy-out of call t
+// that read its result region.
+static comet_status_t run_host_pipe(const Plan &P, int n_calls, const void *const *host_in,
+                                    void *const *host_out, void *const *dev_in, void *dev_out, void *ws,
+                                    cudaStream_t s) {
     const HostPipe &h = P.pipe;
     const Step &st = P.steps[0];
     const size_t es = dtype_size(P.dtype);
@@ -326,12 +331,19 @@ static comet_status_t run_host_pipe(const Plan &P, const void *const *host_in, v
     if (n + nw > 32) return COMET_ERR_INTERNAL;   // one scale word per slice in the 256-byte region
     cudaError_t e = cudaStreamCreateWithFlags(&r.cin, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r.cout, cudaStreamNonBlocking);
-    r.ev.assign(2 + 2 * n + nw + (size_t)n * nw, nullptr);
+    // per call: start, end, X copies, column results, W copies, blocks; across calls: the
+    // pre-pass of each X and W slice, the copy-out of each block (or column)
+    const size_t n_ev = 2 + 2 * n + nw + (size_t)n * nw;
+    r.ev.assign(2 * n_ev + n + nw, nullptr);
     for (auto &x : r.ev)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_status(e, "host pipeline streams");
     cudaEvent_t e0 = r.ev[0], e_end = r.ev[1];
     cudaEvent_t *e_in = &r.ev[2], *e_g = &r.ev[2 + n], *e_w = &r.ev[2 + 2 * n], *e_blk = &r.ev[2 + 2 * n + nw];
+    // copy-out done (per block, per column in column mode, and the whole call's): a later call
+    // writes a result region only after these
+    cudaEvent_t *o_blk = &r.ev[n_ev + 2 + 2 * n + nw], *o_col = &r.ev[n_ev + 2 + n], o_end = r.ev[n_ev + 1];
+    cudaEvent_t *p_x = &r.ev[2 * n_ev], *p_w = &r.ev[2 * n_ev + n];   // pre-pass done per slice
 
     double alpha = P.alpha, beta = 0.0;
     if (P.op == 1) beta = 1.0;
@@ -349,12 +361,11 @@ static comet_status_t run_host_pipe(const Plan &P, const void *const *host_in, v
     auto parts_x = [&](int j) { return parts_x0 + n_planes * (size_t)(h.rows_inner * h.xb[j]) * (size_t)st.kpad * 2; };
     auto parts_w = [&](int i) { return parts_w0 + n_planes * (size_t)(h.w_rows_inner * h.wb[i]) * (size_t)st.kpad * 2; };
     auto split = emu ? launch_split6 : launch_split;
-    const char *hx = static_cast<const char *>(host_in[h.x_in]);
-    const char *hw = static_cast<const char *>(host_in[h.w_in]);
+    const char *hx = nullptr, *hw = nullptr;   // the current call's host buffers
+    char *hc = nullptr;
     char *dx = static_cast<char *>(dev_in[h.x_in]);
     char *dw = static_cast<char *>(dev_in[h.w_in]);
     char *dc = static_cast<char *>(dev_out);
-    char *hc = static_cast<char *>(host_out);
     const size_t x_unit = (size_t)h.x_inner * h.x_outer * es;      // compact bytes per unit of L
     const size_t w_unit = (size_t)h.w_inner * h.w_outer * es;
     const size_t x_pitch = (size_t)h.x_inner * h.ext * es, c_pitch = (size_t)h.c_inner * h.ext * es;
@@ -383,39 +394,43 @@ static comet_status_t run_host_pipe(const Plan &P, const void *const *host_in, v
         return cudaMemcpy3DAsync(&m, r.cout);
     };
 
-    // copies in, in the planned order (and the result slices for "+=" / "-=" with X's)
     e = cudaEventRecord(e0, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(r.cin, e0, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(r.cout, e0, 0);
-    auto copy_w = [&](int i) {
+    if (e != cudaSuccess) return cuda_status(e, "host pipeline fork");
+    // a later call's copy into a slice's device buffer waits for the pre-pass that read it (the
+    // wait is enqueued before this call's pre-pass records the event again)
+    auto copy_w = [&](int i, bool later) {
         const int64_t l0 = h.wb[i], lc = lw_of(i);
         const size_t ww = (size_t)h.w_inner * lc * es;
-        cudaError_t ee = copy_slice(dw + l0 * w_unit, ww, hw + (size_t)l0 * h.w_inner * es, w_pitch, ww,
-                                    (size_t)h.w_outer, cudaMemcpyHostToDevice, r.cin);
+        cudaError_t ee = later ? cudaStreamWaitEvent(r.cin, p_w[i], 0) : cudaSuccess;
+        if (ee == cudaSuccess)
+            ee = copy_slice(dw + l0 * w_unit, ww, hw + (size_t)l0 * h.w_inner * es, w_pitch, ww,
+                            (size_t)h.w_outer, cudaMemcpyHostToDevice, r.cin);
         if (ee == cudaSuccess) ee = cudaEventRecord(e_w[i], r.cin);
         return ee;
     };
-    auto copy_x = [&](int j) {
+    auto copy_x = [&](int j, bool later) {
         const int64_t l0 = h.xb[j], lc = lx_of(j);
         const size_t xw = (size_t)h.x_inner * lc * es;
-        cudaError_t ee = copy_slice(dx + l0 * x_unit, xw, hx + (size_t)l0 * h.x_inner * es, x_pitch, xw,
-                                    (size_t)h.x_outer, cudaMemcpyHostToDevice, r.cin);
-        if (ee == cudaSuccess && P.op != 0) {
-            const size_t off = (size_t)l0 * h.c_inner * es;
-            ee = copy_slice(dc + off, c_pitch, hc + off, c_pitch, (size_t)h.c_inner * lc * es,
-                            (size_t)h.c_outer, cudaMemcpyHostToDevice, r.cin);
+        cudaError_t ee = later ? cudaStreamWaitEvent(r.cin, p_x[j], 0) : cudaSuccess;
+        if (ee == cudaSuccess)
+            ee = copy_slice(dx + l0 * x_unit, xw, hx + (size_t)l0 * h.x_inner * es, x_pitch, xw,
+                            (size_t)h.x_outer, cudaMemcpyHostToDevice, r.cin);
+        if (ee == cudaSuccess && P.op != 0) {   // "+=" / "-=": the result slice in as well, once
+            const size_t off = (size_t)l0 * h.c_inner * es;   // the earlier call's copy-out is done
+            if (later) ee = cudaStreamWaitEvent(r.cin, o_end, 0);
+            if (ee == cudaSuccess)
+                ee = copy_slice(dc + off, c_pitch, hc + off, c_pitch, (size_t)h.c_inner * lc * es,
+                                (size_t)h.c_outer, cudaMemcpyHostToDevice, r.cin);
         }
         if (ee == cudaSuccess) ee = cudaEventRecord(e_in[j], r.cin);
         return ee;
     };
-    for (int q : h.copies) {
-        e = q >= 0 ? copy_x(q) : copy_w(-1 - q);
-        if (e != cudaSuccess) return cuda_status(e, "host pipeline copy in");
-    }
 
     // scale and pre-pass of one slice, on the compute stream after its copy
     auto prep = [&](cudaEvent_t ready, char *src, int64_t n_elems, void *scale, const XposeParams &tmpl,
-                    int vec, int vout, char *planes) {
+                    int vec, int vout, char *planes, cudaEvent_t done) {
         cudaError_t ee = cudaStreamWaitEvent(s, ready, 0);
         if (ee == cudaSuccess) {
             ProfScope ps(PK_PREPASS, s);
@@ -427,72 +442,93 @@ static comet_status_t run_host_pipe(const Plan &P, const void *const *host_in, v
             ProfScope ps(PK_PREPASS, s);
             ee = split(xp, (int)es, vec, vout, s);
         }
+        if (ee == cudaSuccess) ee = cudaEventRecord(done, s);
         return ee;
     };
-    std::vector<char> done_x(n, 0), done_w(nw, 0);
-    std::vector<int> left(n, nw);
-    for (int u : h.blocks) {
-        const int i = u / n, j = u % n;
-        const int64_t l0 = h.xb[j], lc = lx_of(j), m0 = h.wb[i], mc = lw_of(i);
-        char *xs = dx + l0 * x_unit, *wsl = dw + m0 * w_unit;
-        if (!done_w[i]) {
-            e = prep(e_w[i], wsl, h.w_inner * mc * h.w_outer, sc_w(i), h.w_pre[i], h.w_pre_vec[i], h.w_pre_vout[i],
-                     parts_w(i));
-            if (e != cudaSuccess) return cuda_status(e, "host pipeline pre-pass (W slice)");
-            done_w[i] = 1;
+    for (int t = 0; t < n_calls; ++t) {
+        const bool later = t > 0;
+        hx = static_cast<const char *>(host_in[(size_t)t * P.n_in + h.x_in]);
+        hw = static_cast<const char *>(host_in[(size_t)t * P.n_in + h.w_in]);
+        hc = static_cast<char *>(host_out[t]);
+        // copies in, in the planned order (and the result slices for "+=" / "-=" with X's)
+        for (int q : h.copies) {
+            e = q >= 0 ? copy_x(q, later) : copy_w(-1 - q, later);
+            if (e != cudaSuccess) return cuda_status(e, "host pipeline copy in");
         }
-        if (!done_x[j]) {
-            e = prep(e_in[j], xs, h.x_inner * lc * h.x_outer, sc_x(j), h.pre[j], h.pre_vec[j], h.pre_vout[j],
-                     parts_x(j));
-            if (e != cudaSuccess) return cuda_status(e, "host pipeline pre-pass (X slice)");
-            done_x[j] = 1;
-        }
-        GemmParams g = st.gemm;
-        Radix &rx = x_is_b ? g.nb : g.ma;
-        Radix &rw = x_is_b ? g.ma : g.nb;
-        const uint32_t rows_x = (uint32_t)(h.rows_inner * lc), rows_w = (uint32_t)(h.w_rows_inner * mc);
-        rx.ext[rx.n - 1] = (uint32_t)lc;
-        rx.fd[rx.n - 1] = make_fastdiv((uint32_t)lc);
-        rx.total = rows_x;
-        rw.ext[rw.n - 1] = (uint32_t)mc;
-        rw.fd[rw.n - 1] = make_fastdiv((uint32_t)mc);
-        rw.total = rows_w;
-        if (x_is_b) { g.N = rows_x; g.M = rows_w; } else { g.M = rows_x; g.N = rows_w; }
-        g.A = x_is_b ? static_cast<void *>(wsl) : static_cast<void *>(xs);
-        g.B = x_is_b ? static_cast<void *>(xs) : static_cast<void *>(wsl);
-        g.C = dc + ((size_t)l0 * h.c_inner + (size_t)m0 * h.wc_inner) * es;
-        g.alpha = alpha;
-        g.beta = beta;
-        g.status = status;
-        g.timeout_ns = timeout_ns(P);
-        void *pa = x_is_b ? static_cast<void *>(parts_w(i)) : static_cast<void *>(parts_x(j));
-        void *pb = x_is_b ? static_cast<void *>(parts_x(j)) : static_cast<void *>(parts_w(i));
-        void *sa = x_is_b ? static_cast<void *>(sc_w(i)) : static_cast<void *>(sc_x(j));
-        void *sb = x_is_b ? static_cast<void *>(sc_x(j)) : static_cast<void *>(sc_w(i));
-        if (emu) {
-            ProfScope ps(PK_EMU, s);
-            e = launch_gemm_emu(g, pa, pb, st.kpad, sa, sb, P.opts.debug_flags, s, 0);
-        } else {
-            ProfScope ps(PK_SPLIT, s);
-            e = launch_gemm_split(g, pa, pb, st.kpad, sa, sb, P.opts.kc, (int)es, P.opts.debug_flags, s, 0,
-                                  st.ksplit, reinterpret_cast<float *>(w + st.ws_ksplit));
-        }
-        if (e != cudaSuccess) return cuda_status(e, "host pipeline gemm");
-        if (h.blockwise) {   // this block's result back as soon as it is done
-            e = cudaEventRecord(e_blk[u], s);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(r.cout, e_blk[u], 0);
-            if (e == cudaSuccess) e = copy_block(j, i);
-            if (e != cudaSuccess) return cuda_status(e, "host pipeline copy out (block)");
-        } else if (--left[j] == 0) {   // the column's last block: its result slice back
-            e = cudaEventRecord(e_g[j], s);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(r.cout, e_g[j], 0);
-            if (e == cudaSuccess) {
-                const size_t off = (size_t)l0 * h.c_inner * es;
-                e = copy_slice(hc + off, c_pitch, dc + off, c_pitch, (size_t)h.c_inner * lc * es,
-                               (size_t)h.c_outer, cudaMemcpyDeviceToHost, r.cout);
+        std::vector<char> done_x(n, 0), done_w(nw, 0);
+        std::vector<int> left(n, nw);
+        for (int u : h.blocks) {
+            const int i = u / n, j = u % n;
+            const int64_t l0 = h.xb[j], lc = lx_of(j), m0 = h.wb[i], mc = lw_of(i);
+            char *xs = dx + l0 * x_unit, *wsl = dw + m0 * w_unit;
+            if (!done_w[i]) {
+                e = prep(e_w[i], wsl, h.w_inner * mc * h.w_outer, sc_w(i), h.w_pre[i], h.w_pre_vec[i],
+                         h.w_pre_vout[i], parts_w(i), p_w[i]);
+                if (e != cudaSuccess) return cuda_status(e, "host pipeline pre-pass (W slice)");
+                done_w[i] = 1;
             }
-            if (e != cudaSuccess) return cuda_status(e, "host pipeline copy out");
+            if (!done_x[j]) {
+                e = prep(e_in[j], xs, h.x_inner * lc * h.x_outer, sc_x(j), h.pre[j], h.pre_vec[j], h.pre_vout[j],
+                         parts_x(j), p_x[j]);
+                if (e != cudaSuccess) return cuda_status(e, "host pipeline pre-pass (X slice)");
+                done_x[j] = 1;
+            }
+            // the earlier call's copy-out of this block's result region is done
+            if (later) {
+                e = cudaStreamWaitEvent(s, h.blockwise ? o_blk[u] : o_col[j], 0);
+                if (e != cudaSuccess) return cuda_status(e, "host pipeline wait");
+            }
+            GemmParams g = st.gemm;
+            Radix &rx = x_is_b ? g.nb : g.ma;
+            Radix &rw = x_is_b ? g.ma : g.nb;
+            const uint32_t rows_x = (uint32_t)(h.rows_inner * lc), rows_w = (uint32_t)(h.w_rows_inner * mc);
+            rx.ext[rx.n - 1] = (uint32_t)lc;
+            rx.fd[rx.n - 1] = make_fastdiv((uint32_t)lc);
+            rx.total = rows_x;
+            rw.ext[rw.n - 1] = (uint32_t)mc;
+            rw.fd[rw.n - 1] = make_fastdiv((uint32_t)mc);
+            rw.total = rows_w;
+            if (x_is_b) { g.N = rows_x; g.M = rows_w; } else { g.M = rows_x; g.N = rows_w; }
+            g.A = x_is_b ? static_cast<void *>(wsl) : static_cast<void *>(xs);
+            g.B = x_is_b ? static_cast<void *>(xs) : static_cast<void *>(wsl);
+            g.C = dc + ((size_t)l0 * h.c_inner + (size_t)m0 * h.wc_inner) * es;
+            g.alpha = alpha;
+            g.beta = beta;
+            g.status = status;
+            g.timeout_ns = timeout_ns(P);
+            void *pa = x_is_b ? static_cast<void *>(parts_w(i)) : static_cast<void *>(parts_x(j));
+            void *pb = x_is_b ? static_cast<void *>(parts_x(j)) : static_cast<void *>(parts_w(i));
+            void *sa = x_is_b ? static_cast<void *>(sc_w(i)) : static_cast<void *>(sc_x(j));
+            void *sb = x_is_b ? static_cast<void *>(sc_x(j)) : static_cast<void *>(sc_w(i));
+            if (emu) {
+                ProfScope ps(PK_EMU, s);
+                e = launch_gemm_emu(g, pa, pb, st.kpad, sa, sb, P.opts.debug_flags, s, 0);
+            } else {
+                ProfScope ps(PK_SPLIT, s);
+                e = launch_gemm_split(g, pa, pb, st.kpad, sa, sb, P.opts.kc, (int)es, P.opts.debug_flags, s, 0,
+                                      st.ksplit, reinterpret_cast<float *>(w + st.ws_ksplit));
+            }
+            if (e != cudaSuccess) return cuda_status(e, "host pipeline gemm");
+            if (h.blockwise) {   // this block's result back as soon as it is done
+                e = cudaEventRecord(e_blk[u], s);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(r.cout, e_blk[u], 0);
+                if (e == cudaSuccess) e = copy_block(j, i);
+                if (e == cudaSuccess) e = cudaEventRecord(o_blk[u], r.cout);
+                if (e != cudaSuccess) return cuda_status(e, "host pipeline copy out (block)");
+            } else if (--left[j] == 0) {   // the column's last block: its result slice back
+                e = cudaEventRecord(e_g[j], s);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(r.cout, e_g[j], 0);
+                if (e == cudaSuccess) {
+                    const size_t off = (size_t)l0 * h.c_inner * es;
+                    e = copy_slice(hc + off, c_pitch, dc + off, c_pitch, (size_t)h.c_inner * lc * es,
+                                   (size_t)h.c_outer, cudaMemcpyDeviceToHost, r.cout);
+                }
+                if (e == cudaSuccess) e = cudaEventRecord(o_col[j], r.cout);
+                if (e != cudaSuccess) return cuda_status(e, "host pipeline copy out");
+            }
         }
+        e = cudaEventRecord(o_end, r.cout);
+        if (e != cudaSuccess) return cuda_status(e, "host pipeline copy out");
     }
     e = cudaEventRecord(e_end, r.cout);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, e_end, 0);
@@ -655,45 +691,65 @@ comet_status_t comet_contract_noalloc(comet_plan_t plan, const void *const *inpu
     return run_plan(P, inputs, output, scratch, static_cast<cudaStream_t>(stream));
 }
 
-comet_status_t comet_contract_host(comet_plan_t plan, const void *const *host_inputs, void *host_output,
-                                   void *const *dev_inputs, void *dev_output, void *workspace, void *stream) {
-    if (!plan || !host_inputs || !host_output || !dev_inputs || !dev_output) return COMET_ERR_NULL;
+comet_status_t comet_contract_host_n(comet_plan_t plan, int n_calls, const void *const *host_inputs,
+                                     void *const *host_outputs, void *const *dev_inputs, void *dev_output,
+                                     void *workspace, void *stream) {
+    if (!plan || !host_inputs || !host_outputs || !dev_inputs || !dev_output) return COMET_ERR_NULL;
+    if (n_calls < 1) return COMET_ERR_ARG;
     const Plan &P = plan->p;
     if (P.batched || P.triples) return COMET_ERR_ARG;
+    for (size_t q = 0; q < (size_t)n_calls * P.n_in; ++q)
+        if (!host_inputs[q]) return COMET_ERR_NULL;
+    for (int t = 0; t < n_calls; ++t)
+        if (!host_outputs[t]) return COMET_ERR_NULL;
+    for (int i = 0; i < P.n_in; ++i)
+        if (!dev_inputs[i]) return COMET_ERR_NULL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     size_t es = dtype_size(P.dtype);
     if (P.pipe.ok) {   // slice pipeline: pinned host buffers, aligned device buffers
-        bool ok = pinned_host(host_output) && aligned16(dev_output) && (P.workspace == 0 || aligned16(workspace));
-        for (int i = 0; i < P.n_in && ok; ++i)
-            ok = host_inputs[i] && dev_inputs[i] && pinned_host(host_inputs[i]) && aligned16(dev_inputs[i]);
+        bool ok = aligned16(dev_output) && (P.workspace == 0 || aligned16(workspace));
+        for (int i = 0; i < P.n_in && ok; ++i) ok = aligned16(dev_inputs[i]);
+        for (size_t q = 0; q < (size_t)n_calls * P.n_in && ok; ++q) ok = pinned_host(host_inputs[q]);
+        for (int t = 0; t < n_calls && ok; ++t) ok = pinned_host(host_outputs[t]);
         if (ok && P.workspace > 0 && !workspace) return COMET_ERR_WORKSPACE;
         if (ok) {
-            comet_status_t st = run_host_pipe(P, host_inputs, host_output, dev_inputs, dev_output, workspace, s);
+            comet_status_t st = run_host_pipe(P, n_calls, host_inputs, host_outputs, dev_inputs, dev_output,
+                                              workspace, s);
             if (st != COMET_OK) return st;
             return comet_sync_status(stream);
         }
-    }
-    for (int i = 0; i < P.n_in; ++i) {
-        if (!host_inputs[i] || !dev_inputs[i]) return COMET_ERR_NULL;
-        size_t bytes = (size_t)P.slots[i].storage * es;
-        comet_status_t st = cuda_status(cudaMemcpyAsync(dev_inputs[i], host_inputs[i], bytes,
-                                                        cudaMemcpyHostToDevice, s), "input copy");
-        if (st != COMET_OK) return st;
     }
     size_t out_bytes = 0;
     bool out_view = false;
     for (auto &sl : P.slots)
         if (sl.kind == SLOT_OUTPUT) { out_bytes = (size_t)sl.storage * es; out_view = sl.view; }
-    if (P.op != 0 || out_view) {   // read as well, or only partly written (a view)
-        comet_status_t st = cuda_status(cudaMemcpyAsync(dev_output, host_output, out_bytes,
-                                                        cudaMemcpyHostToDevice, s), "output copy in");
+    for (int t = 0; t < n_calls; ++t) {   // every copy and kernel in order on the stream
+        for (int i = 0; i < P.n_in; ++i) {
+            size_t bytes = (size_t)P.slots[i].storage * es;
+            comet_status_t st = cuda_status(cudaMemcpyAsync(dev_inputs[i], host_inputs[(size_t)t * P.n_in + i], bytes,
+                                                            cudaMemcpyHostToDevice, s), "input copy");
+            if (st != COMET_OK) return st;
+        }
+        if (P.op != 0 || out_view) {   // read as well, or only partly written (a view)
+            comet_status_t st = cuda_status(cudaMemcpyAsync(dev_output, host_outputs[t], out_bytes,
+                                                            cudaMemcpyHostToDevice, s), "output copy in");
+            if (st != COMET_OK) return st;
+        }
+        comet_status_t st = comet_contract(plan, const_cast<const void *const *>(dev_inputs), dev_output, workspace,
+                                           stream);
+        if (st != COMET_OK) return st;
+        st = cuda_status(cudaMemcpyAsync(host_outputs[t], dev_output, out_bytes, cudaMemcpyDeviceToHost, s),
+                         "output copy");
         if (st != COMET_OK) return st;
     }
-    comet_status_t st = comet_contract(plan, const_cast<const void *const *>(dev_inputs), dev_output, workspace, stream);
-    if (st != COMET_OK) return st;
-    st = cuda_status(cudaMemcpyAsync(host_output, dev_output, out_bytes, cudaMemcpyDeviceToHost, s), "output copy");
-    if (st != COMET_OK) return st;
     return comet_sync_status(stream);
+}
+
+comet_status_t comet_contract_host(comet_plan_t plan, const void *const *host_inputs, void *host_output,
+                                   void *const *dev_inputs, void *dev_output, void *workspace, void *stream) {
+    if (!host_output) return COMET_ERR_NULL;
+    void *outs[1] = {host_output};
+    return comet_contract_host_n(plan, 1, host_inputs, outs, dev_inputs, dev_output, workspace, stream);
 }
 
 comet_status_t comet_fill(void *out, int64_t n, double value, comet_dtype_t dtype, void *stream) {

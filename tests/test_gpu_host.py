@@ -148,3 +148,81 @@ def test_serial_multi_step_and_native(comet):
     D, p, _ = run_host(comet, e, ext, arrays, np.float64, "native")
     assert "host_pipe" not in p.info
     assert normwise(D, oracle.einsum(e, *arrays)) <= 1e-12
+
+
+def run_host_n(comet, expr, ext, sets, dtype, precision, pinned=True, out_inits=None, shared_out=False, **kw):
+    """comet_contract_host_n over len(sets) input sets; returns the host results (one per call, or
+    the one shared buffer), the plan and the per-call results of single comet_contract_host calls
+    on the same plan."""
+    import torch
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    p = comet.Plan(expr, ext, tdt, precision=precision, **kw)
+    _, out_labels, _, _, _ = oracle.parse(expr)
+    out_shape = tuple(ext[l] for l in out_labels)
+    inits = out_inits or [np.zeros(out_shape)] * len(sets)
+    hin = [[host_col(a, dtype, pinned) for a in arrays] for arrays in sets]
+    houts = [host_col(inits[0], dtype, pinned)] * len(sets) if shared_out else \
+        [host_col(c, dtype, pinned) for c in inits]
+    din = [torch.full(t.shape, float("nan"), dtype=tdt, device="cuda") for t in hin[0]]
+    dout = torch.full(houts[0].shape, float("nan"), dtype=tdt, device="cuda")
+    p.contract_host_n(hin, houts, din, dout, p.workspace())
+    got = [np.asfortranarray(h.numpy().T).copy() for h in houts]
+    single = []
+    for t, arrays in enumerate(hin):   # the same plan, one call per input set
+        h1 = host_col(inits[t], dtype, pinned)
+        p.contract_host(arrays, h1, din, dout, p.workspace())
+        single.append(np.asfortranarray(h1.numpy().T).copy())
+    return got, p, single
+
+
+@pytest.mark.parametrize("expr,ext,slices,w_slices", [
+    (CCSD, dict(i=16, j=16, k=16, a=48, b=48, c=48), 4, 4),          # block copies back
+    ("C[j,i,c] = A[i,k,c] * B[k,j]", dict(i=40, c=24, k=32, j=20), 3, 2),   # column copies back
+    (CCSD, dict(i=16, j=14, k=16, a=46, b=44, c=48), 3, 5),          # both ragged
+])
+def test_pipelined_calls(comet, expr, ext, slices, w_slices):
+    # three calls with their own inputs and outputs: each equals its single call bit for bit
+    sets = [inputs(expr, ext, 20 + t) for t in range(3)]
+    got, p, single = run_host_n(comet, expr, ext, sets, np.float32, "split_bf16", host_slices=slices,
+                                host_slices_w=w_slices)
+    assert p.info["host_pipe"]["slices"] == slices
+    for t, arrays in enumerate(sets):
+        assert np.array_equal(got[t], single[t])
+        assert normwise(got[t], oracle.einsum(expr, *arrays)) <= 1e-6
+
+
+def test_pipelined_calls_shared_output_and_integers(comet):
+    # integer inputs (exact on the split path); one host output for all calls ends with the last
+    ext = dict(i=16, j=12, k=16, a=32, b=48, c=32)
+    sets = [inputs(CCSD, ext, 30 + t, kind="int", lo=-3, hi=3) for t in range(4)]
+    got, p, single = run_host_n(comet, CCSD, ext, sets, np.float32, "split_bf16", shared_out=True,
+                                host_slices=3, host_slices_w=2)
+    assert np.array_equal(got[-1], oracle.einsum(CCSD, *sets[-1]))
+    assert np.array_equal(single[0], oracle.einsum(CCSD, *sets[0]))
+
+
+def test_pipelined_calls_accumulate(comet):
+    e = "C[i,j] += 0.5 * A[i,k] * B[k,j]"
+    ext = dict(i=300, j=520, k=96)
+    sets = [inputs(e, ext, 40 + t) for t in range(3)]
+    inits = [synth.tensor((300, 520), 41, t).astype(np.float32).astype(np.float64) for t in range(3)]
+    got, p, single = run_host_n(comet, e, ext, sets, np.float32, "split_bf16", out_inits=inits, host_slices=4,
+                                host_slices_w=3)
+    for t, arrays in enumerate(sets):
+        assert np.array_equal(got[t], single[t])
+        ref = oracle.einsum(e, *arrays, out=np.asfortranarray(inits[t].copy()))
+        assert normwise(got[t], ref) <= 2e-6
+
+
+def test_pipelined_calls_emulated_and_serial(comet):
+    ext = dict(i=8, j=20, k=8, a=40, b=24, c=40)
+    sets = [inputs(CCSD, ext, 50 + t) for t in range(2)]
+    got, p, _ = run_host_n(comet, CCSD, ext, sets, np.float64, "emu_f64", host_slices=3, host_slices_w=2)
+    assert "host_pipe" in p.info
+    for t, arrays in enumerate(sets):
+        assert normwise(got[t], oracle.einsum(CCSD, *arrays)) <= 1e-12
+    # pageable buffers: the calls run one after another on the stream
+    got, p, single = run_host_n(comet, CCSD, ext, sets, np.float32, "split_bf16", pinned=False, host_slices=3)
+    for t, arrays in enumerate(sets):
+        assert np.array_equal(got[t], single[t])
+        assert normwise(got[t], oracle.einsum(CCSD, *arrays)) <= 1e-6
