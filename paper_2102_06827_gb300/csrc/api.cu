@@ -183,13 +183,19 @@ static comet_status_t run_plan(const Plan &P, const void *const *inputs, void *o
         const bool split_like = st.kernel == KK_GEMM_SPLIT || st.kernel == KK_GEMM_EMU;
         if (split_like) {   // operand scales over the whole operands (every batch index shares them)
             const Slot &sa_ = P.slots[st.form.swap ? st.b : st.a], &sb_ = P.slots[st.form.swap ? st.a : st.b];
-            {
+            const void *xa = st.form.swap ? pb : pa, *xb = st.form.swap ? pa : pb;
+            if (!sa_.view && !sb_.view) {   // both dense: one launch (sc_b is the word after sc_a)
                 ProfScope ps(PK_PREPASS, stream);
-                e = operand_absmax(sa_, st.form.swap ? pb : pa, es, sc_a, stream);
-            }
-            if (e == cudaSuccess) {
-                ProfScope ps(PK_PREPASS, stream);
-                e = operand_absmax(sb_, st.form.swap ? pa : pb, es, sc_b, stream);
+                e = launch_absmax2(xa, sa_.elems, xb, sb_.elems, es, sc_a, stream);
+            } else {
+                {
+                    ProfScope ps(PK_PREPASS, stream);
+                    e = operand_absmax(sa_, xa, es, sc_a, stream);
+                }
+                if (e == cudaSuccess) {
+                    ProfScope ps(PK_PREPASS, stream);
+                    e = operand_absmax(sb_, xb, es, sc_b, stream);
+                }
             }
             if (e != cudaSuccess) return cuda_status(e, "split pre-pass (scales)");
         }

@@ -339,20 +339,22 @@ cudaError_t launch_fill(void *out, int64_t n, double value, int elem_bytes, cuda
 }
 
 // max |x| over a dense operand: grid-stride 16-byte loads, warp reduction, one atomic per warp
-// on the bit pattern (for non-negative IEEE values the bit order is the numeric order)
+// on the bit pattern (for non-negative IEEE values the bit order is the numeric order).  `bid`
+// and `nb` are this block's index and the block count among the blocks given to the operand.
 template <typename T>
-__global__ void __launch_bounds__(256) absmax_kernel(const T *__restrict__ x, int64_t n, void *out_bits) {
+__device__ __forceinline__ void absmax_body(const T *__restrict__ x, int64_t n, int64_t bid, int64_t nb,
+                                            void *out_bits) {
     constexpr int W = 16 / sizeof(T);
     using U = typename std::conditional<sizeof(T) == 4, unsigned int, unsigned long long>::type;
     T m = 0;
     const int64_t nv = n / W;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += stride) {
+    const int64_t stride = nb * blockDim.x;
+    for (int64_t i = bid * (int64_t)blockDim.x + threadIdx.x; i < nv; i += stride) {
         Vec<W, T> w = reinterpret_cast<const Vec<W, T> *>(x)[i];
 #pragma unroll
         for (int q = 0; q < W; ++q) m = fmax(m, fabs(w.v[q]));
     }
-    for (int64_t i = nv * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
+    for (int64_t i = nv * W + bid * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
         m = fmax(m, fabs(x[i]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -363,12 +365,42 @@ __global__ void __launch_bounds__(256) absmax_kernel(const T *__restrict__ x, in
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) absmax_kernel(const T *__restrict__ x, int64_t n, void *out_bits) {
+    absmax_body(x, n, blockIdx.x, gridDim.x, out_bits);
+}
+
+// both operands of a split step in one launch: blocks [0, blocks0) take x0 (word 0 of out_bits),
+// the rest x1 (word 1, 8 bytes further)
+template <typename T>
+__global__ void __launch_bounds__(256) absmax2_kernel(const T *__restrict__ x0, int64_t n0, const T *__restrict__ x1,
+                                                      int64_t n1, int blocks0, void *out_bits) {
+    if ((int)blockIdx.x < blocks0) absmax_body(x0, n0, blockIdx.x, blocks0, out_bits);
+    else absmax_body(x1, n1, blockIdx.x - blocks0, gridDim.x - blocks0, static_cast<char *>(out_bits) + 8);
+}
+
+static int absmax_blocks(int64_t n) { return (int)std::min<int64_t>(152 * 8, (n + 256 * 4 - 1) / (256 * 4)); }
+
 cudaError_t launch_absmax(const void *x, int64_t n, int elem_bytes, void *out_bits, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(out_bits, 0, 8, s);
     if (e != cudaSuccess || n == 0) return e;
-    int blocks = (int)std::min<int64_t>(152 * 8, (n + 256 * 4 - 1) / (256 * 4));
+    const int blocks = absmax_blocks(n);
     if (elem_bytes == 4) absmax_kernel<float><<<blocks, 256, 0, s>>>(reinterpret_cast<const float *>(x), n, out_bits);
     else absmax_kernel<double><<<blocks, 256, 0, s>>>(reinterpret_cast<const double *>(x), n, out_bits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_absmax2(const void *x0, int64_t n0, const void *x1, int64_t n1, int elem_bytes, void *out_bits,
+                           cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out_bits, 0, 16, s);
+    const int b0 = absmax_blocks(n0), b1 = absmax_blocks(n1);
+    if (e != cudaSuccess || b0 + b1 == 0) return e;
+    if (elem_bytes == 4)
+        absmax2_kernel<float><<<b0 + b1, 256, 0, s>>>(reinterpret_cast<const float *>(x0), n0,
+                                                      reinterpret_cast<const float *>(x1), n1, b0, out_bits);
+    else
+        absmax2_kernel<double><<<b0 + b1, 256, 0, s>>>(reinterpret_cast<const double *>(x0), n0,
+                                                       reinterpret_cast<const double *>(x1), n1, b0, out_bits);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,9 @@ cudaError_t launch_fill(void *out, int64_t n, double value, int elem_bytes, cuda
 
 // max |x| of a dense operand into *out_bits (zeroed first), as the bits of an input-precision value
 cudaError_t launch_absmax(const void *x, int64_t n, int elem_bytes, void *out_bits, cudaStream_t s);
+// max |x0| and max |x1| in one launch: words 0 and 1 (8 bytes apart) of out_bits
+cudaError_t launch_absmax2(const void *x0, int64_t n0, const void *x1, int64_t n1, int elem_bytes, void *out_bits,
+                           cudaStream_t s);
 // the same over the r.total elements of a strided view at offsets r (digit strides s0)
 cudaError_t launch_absmax_view(const void *x, const Radix &r, int elem_bytes, void *out_bits, cudaStream_t s);
 
