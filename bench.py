@@ -56,6 +56,8 @@ def args_parse():
     ap.add_argument("--pc-perm", default="3,1,0,2", help="transpose profile case permutation")
     ap.add_argument("--pc-dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--pc-tile", type=int, default=-1, help="batched tile configuration of --profile-case triples")
+    ap.add_argument("--pc-o", type=int, default=0, help="--profile-case split/emu/f64: occupied extent (0 = the case default)")
+    ap.add_argument("--pc-v", type=int, default=0, help="--profile-case split/emu/f64: virtual extent (0 = the case default)")
     ap.add_argument("--ablation", action="store_true",
                     help="Table 1 natural vs planned order, and every TTGT form vs the chosen one")
     ap.add_argument("--workload", default="ccsd", choices=["ccsd", "triples", "small", "triples_energy"],
@@ -711,6 +713,8 @@ def run_profile_case(case: str, a=None) -> int:
         print(json.dumps({"case": case, "extents": ext, "perm": perm, "bytes": 2 * x.element_size() * n}))
         return 0
     o, v = (48, 160) if case in ("split", "emu") else (16, 48)
+    if a is not None and a.pc_o > 0 and a.pc_v > 0:   # e.g. the headline size o=64 v=192
+        o, v = a.pc_o, a.pc_v
     ext = dict(i=o, j=o, k=o, a=v, b=v, c=v)
     n = o * v * v * o
     dt = torch.float32 if case == "split" else torch.float64
