@@ -23,7 +23,10 @@
  *   Errors     Every call returns a status code; nothing aborts the process, throws across
  *              the ABI or traps on the device.  A kernel whose internal wait runs out of time
  *              records COMET_ERR_TIMEOUT in a device status word and returns; the code
- *              surfaces at the next comet_sync_status().
+ *              surfaces at the next comet_sync_status().  In a library built with COMET_DEBUG
+ *              (libcomet_debug.so) the transpose, GEMM and gemv kernels also test every global
+ *              access against the buffers of their launch, skip any access outside them and
+ *              record COMET_ERR_BOUNDS the same way.
  *   Threads    Plans are immutable after comet_plan() and may be used from several host
  *              threads at once.
  */
@@ -52,7 +55,9 @@ typedef enum {
     COMET_ERR_CUDA = 9,         /* a CUDA runtime call failed (no device, launch error...) */
     COMET_ERR_TIMEOUT = 10,     /* a device-side wait ran out of time (see comet_sync_status) */
     COMET_ERR_INTERNAL = 11,
-    COMET_ERR_ARG = 12          /* an argument is out of range */
+    COMET_ERR_ARG = 12,         /* an argument is out of range */
+    COMET_ERR_BOUNDS = 13       /* builds with COMET_DEBUG only: a kernel access outside the buffer
+                                   it belongs to was skipped (see comet_sync_status) */
 } comet_status_t;
 
 typedef enum { COMET_F32 = 0, COMET_F64 = 1 } comet_dtype_t;
@@ -100,7 +105,11 @@ typedef struct {
                                    the chunk is added into the compensated sum (0 = whole K) */
     int64_t timeout_ms;         /* device-side wait limit; 0 = default (2000 ms) */
     int debug_flags;            /* bit 0: withhold one operand load in the split GEMM so that
-                                   its wait runs out (fault-injection test); others reserved */
+                                   its wait runs out (fault-injection test); bit 3, builds with
+                                   COMET_DEBUG only: the first thread of a copy step aims its
+                                   stores outside the output, so that the range check skips them
+                                   and reports COMET_ERR_BOUNDS (test of the check); others
+                                   reserved */
     int ksplit;                 /* split path: K slices per output tile; 0 = planner's choice
                                    (more slices when a GEMM has fewer tiles than the GPU has
                                    SMs; their FP32 partials are summed by a second kernel),
@@ -467,7 +476,8 @@ comet_status_t comet_profile_read(comet_kernel_stat_t *stats, int max_stats, int
 comet_status_t comet_probe_fp64(int kind, int iters, double *flops, void *sink, void *stream);
 
 /* Synchronises `stream`, then reads and clears the device status word: COMET_OK, or
- * COMET_ERR_TIMEOUT if a kernel's wait ran out, or COMET_ERR_CUDA if the stream reported an
+ * COMET_ERR_TIMEOUT if a kernel's wait ran out, COMET_ERR_BOUNDS (debug builds only) if a
+ * kernel skipped an access outside its buffers, or COMET_ERR_CUDA if the stream reported an
  * error. */
 comet_status_t comet_sync_status(void *stream);
 
@@ -478,7 +488,7 @@ const char *comet_status_string(comet_status_t status);
 /* Detail of the last error returned to the calling host thread (empty if none). */
 const char *comet_last_error_message(void);
 
-/* Library version string. */
+/* Library version string ("... debug ..." for the COMET_DEBUG build). */
 const char *comet_version(void);
 
 #ifdef __cplusplus

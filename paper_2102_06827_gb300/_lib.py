@@ -12,7 +12,7 @@ STATUS = {
     0: "COMET_OK", 1: "COMET_ERR_PARSE", 2: "COMET_ERR_LABEL", 3: "COMET_ERR_SHAPE",
     4: "COMET_ERR_DTYPE", 5: "COMET_ERR_UNSUPPORTED", 6: "COMET_ERR_ALIGN", 7: "COMET_ERR_NULL",
     8: "COMET_ERR_WORKSPACE", 9: "COMET_ERR_CUDA", 10: "COMET_ERR_TIMEOUT",
-    11: "COMET_ERR_INTERNAL", 12: "COMET_ERR_ARG",
+    11: "COMET_ERR_INTERNAL", 12: "COMET_ERR_ARG", 13: "COMET_ERR_BOUNDS",
 }
 F32, F64 = 0, 1
 PREC_NATIVE, PREC_SPLIT_BF16, PREC_EMU_F64 = 0, 1, 2
@@ -62,14 +62,16 @@ _lib = None
 
 
 def load():
-    """Loads the in-tree libcomet.so; raises if it has not been built (there is no fallback)."""
+    """Loads the in-tree libcomet.so (or the library COMET_LIBRARY names, e.g. the debug build
+    libcomet_debug.so); raises if it has not been built (there is no fallback)."""
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB_PATH):
-        raise ImportError(f"libcomet.so is not built ({LIB_PATH}); run __graft_entry__.build() "
+    path = os.environ.get("COMET_LIBRARY") or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"{os.path.basename(path)} is not built ({path}); run __graft_entry__.build() "
                           "or python paper_2102_06827_gb300/build.py")
-    L = ctypes.CDLL(LIB_PATH)
+    L = ctypes.CDLL(path)
     vp, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)
     L.comet_plan_opts_default.argtypes = [ctypes.POINTER(PlanOpts)]
     L.comet_plan_opts_default.restype = None

@@ -1,4 +1,9 @@
-"""Builds libcomet.so (all CUDA kernels + the C ABI) in-tree for sm_103a with nvcc."""
+"""Builds libcomet.so (all CUDA kernels + the C ABI) in-tree for sm_103a with nvcc.
+
+build(debug=True) builds libcomet_debug.so instead: the same sources with COMET_DEBUG defined,
+so that the transpose, GEMM and gemv kernels test every global access against the buffers of
+their launch and report COMET_ERR_BOUNDS instead of touching memory outside them.  The binding
+loads it when COMET_LIBRARY names it."""
 from __future__ import annotations
 
 import glob
@@ -27,16 +32,22 @@ def _headers():
         glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "comet.h")]
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False) -> str:
-    os.makedirs(OBJ, exist_ok=True)
+DEBUG_LIB = os.path.join(HERE, "libcomet_debug.so")
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False, debug: bool = False) -> str:
+    obj_dir = OBJ + "_debug" if debug else OBJ
+    lib_path = DEBUG_LIB if debug else LIB
+    flags = FLAGS + (["-DCOMET_DEBUG"] if debug else [])
+    os.makedirs(obj_dir, exist_ok=True)
     srcs = _sources()
     newest_hdr = max(os.path.getmtime(h) for h in _headers())
 
     def compile_one(src):
-        obj = os.path.join(OBJ, os.path.basename(src) + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src) + ".o")
         if not force and os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), newest_hdr):
             return obj, ""
-        cmd = [NVCC] + ARCH + FLAGS + (["-Xptxas", "-v"] if ptxas_verbose else []) + ["-c", src, "-o", obj]
+        cmd = [NVCC] + ARCH + flags + (["-Xptxas", "-v"] if ptxas_verbose else []) + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr}")
@@ -49,15 +60,16 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
         for _, log in results:
             if log:
                 sys.stderr.write(log)
-    if force or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or not os.path.exists(lib_path) or any(os.path.getmtime(o) > os.path.getmtime(lib_path) for o in objs):
+        tmp = lib_path + f".tmp{os.getpid()}"
         cmd = [NVCC] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs + ["-lpthread", "-ldl", "-lrt"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_verbose="-v" in sys.argv,
+                debug="--debug" in sys.argv))

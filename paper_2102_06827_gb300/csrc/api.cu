@@ -128,6 +128,16 @@ static void *slot_ptr(const Plan &P, int slot, const void *const *inputs, void *
     return static_cast<char *>(ws) + s.ws_off;
 }
 
+// byte range of a slot's buffer at launch time (the stored tensor for inputs and the output,
+// the dense intermediate in the workspace): what the debug build's range checks allow
+static DbgRange slot_range(const Plan &P, int slot, const void *const *inputs, void *output, void *ws) {
+    const Slot &s = P.slots[slot];
+    const int64_t es = (int64_t)dtype_size(P.dtype);
+    if (s.kind == SLOT_INPUT) return dbg_range(inputs[s.index], s.storage * es);
+    if (s.kind == SLOT_OUTPUT) return dbg_range(output, s.storage * es);
+    return dbg_range(static_cast<char *>(ws) + s.ws_off, s.elems * es);
+}
+
 // max |x| over the elements of a step operand (a strided walk for views)
 static cudaError_t operand_absmax(const Slot &s, const void *p, int es, void *out, cudaStream_t stream) {
     if (s.view) return launch_absmax_view(p, s.vradix, es, out, stream);
@@ -149,9 +159,12 @@ static comet_status_t run_plan(const Plan &P, const void *const *inputs, void *o
         void *pa = slot_ptr(P, st.a, inputs, output, ws);
         void *pc = slot_ptr(P, st.c, inputs, output, ws);
         cudaError_t e = cudaSuccess;
+        const DbgRange ra = slot_range(P, st.a, inputs, output, ws), rc = slot_range(P, st.c, inputs, output, ws);
         if (st.kernel == KK_COPY) {
             XposeParams x = st.copy;
             x.in = pa; x.out = pc; x.alpha = alpha; x.beta = beta;
+            x.dbg_in = ra; x.dbg_out = rc; x.status = status;
+            x.plant = (P.opts.debug_flags & 8) ? (int64_t(1) << 40) : 0;
             if (alpha == 1.0 && beta == 0.0) {
                 ProfScope ps(PK_TRANSPOSE, stream);
                 e = launch_move(x, es, st.copy_vec_in, st.copy_vec_out, stream);
@@ -167,6 +180,8 @@ static comet_status_t run_plan(const Plan &P, const void *const *inputs, void *o
             v.X = pa;
             v.v = nullptr;
             v.Y = pc;
+            v.dbg_x = ra; v.dbg_v = dbg_range(nullptr, 0); v.dbg_y = rc; v.status = status;
+            v.dbg_p = dbg_range(static_cast<char *>(ws) + st.ws_partial, (int64_t)v.n_batch * v.nchunks * v.N * 8);
             v.alpha = alpha;
             v.beta = beta;
             v.partial = reinterpret_cast<double *>(static_cast<char *>(ws) + st.ws_partial);
@@ -178,6 +193,7 @@ static comet_status_t run_plan(const Plan &P, const void *const *inputs, void *o
             continue;
         }
         void *pb = slot_ptr(P, st.b, inputs, output, ws);
+        const DbgRange rb = slot_range(P, st.b, inputs, output, ws);
         char *w = static_cast<char *>(ws);
         void *sc_a = w + st.ws_scales, *sc_b = w + st.ws_scales + 8;
         const bool split_like = st.kernel == KK_GEMM_SPLIT || st.kernel == KK_GEMM_EMU;
@@ -222,11 +238,19 @@ static comet_status_t run_plan(const Plan &P, const void *const *inputs, void *o
             g.beta = beta;
             g.status = status;
             g.timeout_ns = timeout_ns(P);
+            g.dbg_a = st.form.swap ? rb : ra;
+            g.dbg_b = st.form.swap ? ra : rb;
+            g.dbg_c = rc;
             if (st.kernel == KK_GEMV) {
                 GemvParams v = st.gemv;
                 v.v = st.gemv_vec_is_a ? g.A : g.B;
                 v.X = st.gemv_vec_is_a ? g.B : g.A;
                 v.Y = qc;
+                v.dbg_v = st.gemv_vec_is_a ? g.dbg_a : g.dbg_b;
+                v.dbg_x = st.gemv_vec_is_a ? g.dbg_b : g.dbg_a;
+                v.dbg_y = rc;
+                v.status = status;
+                v.dbg_p = dbg_range(w + st.ws_partial, (int64_t)v.n_batch * v.nchunks * v.N * 8);
                 v.alpha = alpha;
                 v.beta = beta;
                 v.partial = reinterpret_cast<double *>(w + st.ws_partial);
@@ -250,6 +274,11 @@ static comet_status_t run_plan(const Plan &P, const void *const *inputs, void *o
             XposeParams xa = st.pre_a, xb = st.pre_b;
             xa.in = g.A; xa.out = w + st.ws_parts_a; xa.scale_bits = sc_a;
             xb.in = g.B; xb.out = w + st.ws_parts_b; xb.scale_bits = sc_b;
+            const int64_t n_planes = st.kernel == KK_GEMM_EMU ? 6 : 3;
+            xa.dbg_in = g.dbg_a; xa.dbg_out = dbg_range(xa.out, n_planes * xa.out_plane * 2);
+            xb.dbg_in = g.dbg_b; xb.dbg_out = dbg_range(xb.out, n_planes * xb.out_plane * 2);
+            xa.status = xb.status = status;
+            xa.plant = xb.plant = 0;
             auto split = st.kernel == KK_GEMM_EMU ? launch_split6 : launch_split;
             {
                 ProfScope ps(PK_PREPASS, stream);
@@ -445,6 +474,10 @@ static comet_status_t run_host_pipe(const Plan &P, int n_calls, const void *cons
         if (ee == cudaSuccess) {
             XposeParams xp = tmpl;
             xp.in = src; xp.out = planes; xp.scale_bits = scale;
+            xp.dbg_in = dbg_range(src, n_elems * (int64_t)es);
+            xp.dbg_out = dbg_range(planes, (int64_t)n_planes * xp.out_plane * 2);
+            xp.status = status;
+            xp.plant = 0;
             ProfScope ps(PK_PREPASS, s);
             ee = split(xp, (int)es, vec, vout, s);
         }
@@ -502,6 +535,8 @@ static comet_status_t run_host_pipe(const Plan &P, int n_calls, const void *cons
             g.beta = beta;
             g.status = status;
             g.timeout_ns = timeout_ns(P);
+            g.dbg_a = g.dbg_b = dbg_range(nullptr, 0);   // read through tensor maps only
+            g.dbg_c = dbg_range(dc, (int64_t)P.slots[st.c].storage * (int64_t)es);
             void *pa = x_is_b ? static_cast<void *>(parts_w(i)) : static_cast<void *>(parts_x(j));
             void *pb = x_is_b ? static_cast<void *>(parts_x(j)) : static_cast<void *>(parts_w(i));
             void *sa = x_is_b ? static_cast<void *>(sc_w(i)) : static_cast<void *>(sc_x(j));
@@ -798,6 +833,10 @@ comet_status_t comet_transpose(int rank, const int64_t *extents, const int *perm
         return COMET_ERR_SHAPE;
     }
     x.in = in; x.out = out; x.alpha = 1.0; x.beta = 0.0;
+    x.dbg_in = dbg_range(in, (int64_t)tot * (int64_t)dtype_size(dtype));
+    x.dbg_out = dbg_range(out, (int64_t)tot * (int64_t)dtype_size(dtype));
+    x.status = device_status_word();
+    x.plant = 0;
     ProfScope ps(PK_TRANSPOSE, static_cast<cudaStream_t>(stream));
     return cuda_status(launch_move(x, (int)dtype_size(dtype), vi, vo, static_cast<cudaStream_t>(stream)),
                        "transpose kernel");
@@ -852,7 +891,8 @@ comet_status_t comet_sync_status(void *stream) {
     if (v != 0) {
         e = cudaMemcpy(w, &zero, sizeof(int), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_status(e, "status clear");
-        set_error("a device-side wait ran out of time");
+        set_error(v == COMET_ERR_BOUNDS ? "a kernel access outside its buffer was skipped (debug build)"
+                                        : "a device-side wait ran out of time");
         return static_cast<comet_status_t>(v);
     }
     return COMET_OK;
@@ -875,12 +915,17 @@ const char *comet_status_string(comet_status_t s) {
         case COMET_ERR_TIMEOUT: return "device wait timed out";
         case COMET_ERR_INTERNAL: return "internal error";
         case COMET_ERR_ARG: return "bad argument";
+        case COMET_ERR_BOUNDS: return "kernel access outside its buffer (debug build)";
     }
     return "unknown status";
 }
 
 const char *comet_last_error_message(void) { return t_last_error.c_str(); }
 
+#ifdef COMET_DEBUG
+const char *comet_version(void) { return "comet-gb300 0.1 (sm_103a, debug: range-checked kernels)"; }
+#else
 const char *comet_version(void) { return "comet-gb300 0.1 (sm_103a)"; }
+#endif
 
 }  // extern "C"

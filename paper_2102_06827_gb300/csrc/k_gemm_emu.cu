@@ -291,11 +291,11 @@ __global__ void __launch_bounds__(emu::THREADS, 1)
                 if (p.beta == 0.0) {
 #pragma unroll
                     for (int j = 0; j < HALF; ++j)
-                        if (j < n_here) row[cc[j]] = scale * (double)I[j];
+                        if (j < n_here && dbg_ok(p.dbg_c, row + cc[j], 8, p.status)) row[cc[j]] = scale * (double)I[j];
                 } else {
 #pragma unroll
                     for (int j = 0; j < HALF; ++j)
-                        if (j < n_here) {
+                        if (j < n_here && dbg_ok(p.dbg_c, row + cc[j], 8, p.status)) {
                             double *dst = row + cc[j];
                             *dst = scale * (double)I[j] + p.beta * *dst;
                         }

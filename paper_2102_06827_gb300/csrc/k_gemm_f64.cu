@@ -32,7 +32,8 @@ __device__ __forceinline__ void dmma(double (&d)[2], double a, double b) {
 template <typename TIn, bool KCONTIG, int TM>
 __device__ __forceinline__ void load_tile(const TIn *__restrict__ base, const int64_t *rowoff,
                                           const int64_t *koff, uint32_t row0, uint32_t rows,
-                                          uint32_t k0, uint32_t K, double (&r)[TM * FBK / FTHREADS]) {
+                                          uint32_t k0, uint32_t K, double (&r)[TM * FBK / FTHREADS],
+                                          const DbgRange &rg, int *status) {
     const int t = threadIdx.x;
 #pragma unroll
     for (int i = 0; i < TM * FBK / FTHREADS; ++i) {
@@ -41,7 +42,8 @@ __device__ __forceinline__ void load_tile(const TIn *__restrict__ base, const in
         if (KCONTIG) { k = idx % FBK; m = idx / FBK; }
         else { m = idx % TM; k = idx / TM; }
         double v = 0.0;
-        if (row0 + m < rows && k0 + k < K) v = (double)base[rowoff[m] + koff[k]];
+        if (row0 + m < rows && k0 + k < K && dbg_ok(rg, base + rowoff[m] + koff[k], (int)sizeof(TIn), status))
+            v = (double)base[rowoff[m] + koff[k]];
         r[i] = v;
     }
 }
@@ -99,8 +101,8 @@ __global__ void __launch_bounds__(FTHREADS) gemm_f64_kernel(const GemmParams p) 
         for (int j = 0; j < FI; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
 
     double ra[NL], rb[NL];
-    load_tile<TIn, AK, TM>(A, a_row, a_k[0], m0, p.M, 0, p.K, ra);
-    load_tile<TIn, BK, TM>(B, b_col, b_k[0], n0, p.N, 0, p.K, rb);
+    load_tile<TIn, AK, TM>(A, a_row, a_k[0], m0, p.M, 0, p.K, ra, p.dbg_a, p.status);
+    load_tile<TIn, BK, TM>(B, b_col, b_k[0], n0, p.N, 0, p.K, rb, p.dbg_b, p.status);
     store_tile<AK, TM>(As[0], ra);
     store_tile<BK, TM>(Bs[0], rb);
     const uint32_t nkb = (p.K + FBK - 1) / FBK;
@@ -111,8 +113,8 @@ __global__ void __launch_bounds__(FTHREADS) gemm_f64_kernel(const GemmParams p) 
         const int cur = kb & 1, nxt = cur ^ 1;
         const bool more = kb + 1 < nkb;
         if (more) {
-            load_tile<TIn, AK, TM>(A, a_row, a_k[nxt], m0, p.M, (kb + 1) * FBK, p.K, ra);
-            load_tile<TIn, BK, TM>(B, b_col, b_k[nxt], n0, p.N, (kb + 1) * FBK, p.K, rb);
+            load_tile<TIn, AK, TM>(A, a_row, a_k[nxt], m0, p.M, (kb + 1) * FBK, p.K, ra, p.dbg_a, p.status);
+            load_tile<TIn, BK, TM>(B, b_col, b_k[nxt], n0, p.N, (kb + 1) * FBK, p.K, rb, p.dbg_b, p.status);
         }
 #pragma unroll
         for (int k4 = 0; k4 < FBK / 4; ++k4) {
@@ -150,6 +152,7 @@ __global__ void __launch_bounds__(FTHREADS) gemm_f64_kernel(const GemmParams p) 
                 const int nl = wn * (TM / 2) + j * 8 + (lane & 3) * 2 + h;
                 if (n0 + nl >= p.N) continue;
                 TIn *dst = C + c_row[ml] + c_col[nl];
+                if (!dbg_ok(p.dbg_c, dst, (int)sizeof(TIn), p.status)) continue;
                 double v = p.alpha * acc[i][j][h];
                 if (p.beta != 0.0) v += p.beta * (double)*dst;
                 *dst = (TIn)v;

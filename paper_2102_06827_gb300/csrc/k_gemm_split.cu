@@ -59,6 +59,7 @@ struct SplitArgs {
     uint32_t ksplit;             // K slices (1 = whole K per tile; > 1: FP32 partials to `partial`)
     uint32_t kslice_blocks;      // K blocks per slice
     float *partial;              // ksplit x N x M partial sums (scaled by 2^(eA+eB)), m fastest
+    DbgRange dbg_p;              // debug builds: the partial sums' buffer
     int debug_flags;
     const void *scale_a;         // bits of max |A|, max |B| (input precision)
     const void *scale_b;
@@ -291,7 +292,7 @@ __global__ void __launch_bounds__(split::THREADS, 1)
                     float *P = x.partial + ((size_t)ks * p.N + nt * BN + half * 128) * p.M + m;
 #pragma unroll
                     for (int j = 0; j < 128; ++j)
-                        if (j < n_here) P[(size_t)j * p.M] = sc * S[j];
+                        if (j < n_here && dbg_ok(x.dbg_p, P + (size_t)j * p.M, 4, p.status)) P[(size_t)j * p.M] = sc * S[j];
                 }
                 continue;
             }
@@ -306,11 +307,12 @@ __global__ void __launch_bounds__(split::THREADS, 1)
                     const TOut sc = (TOut)scale;
 #pragma unroll
                     for (int j = 0; j < 128; ++j)
-                        if (j < n_here) row[cc[j]] = sc * (TOut)S[j];
+                        if (j < n_here && dbg_ok(p.dbg_c, row + cc[j], (int)sizeof(TOut), p.status))
+                            row[cc[j]] = sc * (TOut)S[j];
                 } else {
 #pragma unroll
                     for (int j = 0; j < 128; ++j)
-                        if (j < n_here) {
+                        if (j < n_here && dbg_ok(p.dbg_c, row + cc[j], (int)sizeof(TOut), p.status)) {
                             TOut *dst = row + cc[j];
                             *dst = (TOut)(scale * (double)S[j] + p.beta * (double)*dst);
                         }
@@ -326,16 +328,21 @@ __global__ void __launch_bounds__(split::THREADS, 1)
 
 // K-slice partials -> C: C[m, n] = alpha * sum_ks P[ks][n][m] (+ beta C), through C's strides
 template <typename TOut>
-__global__ void __launch_bounds__(256) split_reduce_kernel(const GemmParams p, const float *P, uint32_t ksplit) {
+__global__ void __launch_bounds__(256) split_reduce_kernel(const GemmParams p, const float *P, uint32_t ksplit,
+                                                           const DbgRange dbg_p) {
     const uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x;
     if (i >= (uint64_t)p.M * p.N) return;
     const uint32_t n = (uint32_t)(i / p.M), m = (uint32_t)(i - (uint64_t)n * p.M);
     double s = 0.0;
-    for (uint32_t k = 0; k < ksplit; ++k) s += (double)P[((size_t)k * p.N + n) * p.M + m];
+    for (uint32_t k = 0; k < ksplit; ++k) {
+        const float *q = P + ((size_t)k * p.N + n) * p.M + m;
+        if (dbg_ok(dbg_p, q, 4, p.status)) s += (double)*q;
+    }
     int64_t a, cm, b, cn;
     radix_offsets(p.ma, m, a, cm);
     radix_offsets(p.nb, n, b, cn);
     TOut *c = reinterpret_cast<TOut *>(p.C) + cm + cn;
+    if (!dbg_ok(p.dbg_c, c, (int)sizeof(TOut), p.status)) return;
     const double r = p.alpha * s;
     *c = (TOut)(p.beta != 0.0 ? r + p.beta * (double)*c : r);
 }
@@ -419,6 +426,7 @@ cudaError_t launch_gemm_split(const GemmParams &p, const void *parts_a, const vo
     x.kslice_blocks = (x.nkb + ksplit - 1) / ksplit;    // at least one K block per slice
     x.ksplit = (x.nkb + x.kslice_blocks - 1) / x.kslice_blocks;
     x.partial = partial;
+    x.dbg_p = dbg_range(partial, (int64_t)x.ksplit * p.N * p.M * 4);
     uint32_t tiles = x.m_tiles * x.n_tiles * x.ksplit;
     int ctas = sm_count();
     if (max_ctas > 0 && max_ctas < ctas) ctas = max_ctas;
@@ -434,8 +442,8 @@ cudaError_t launch_gemm_split(const GemmParams &p, const void *parts_a, const vo
     if (e != cudaSuccess || x.ksplit == 1) return e;
     const uint64_t n = (uint64_t)p.M * p.N;
     const uint32_t blocks = (uint32_t)((n + 255) / 256);
-    if (out_bytes == 8) split_reduce_kernel<double><<<blocks, 256, 0, s>>>(p, partial, x.ksplit);
-    else split_reduce_kernel<float><<<blocks, 256, 0, s>>>(p, partial, x.ksplit);
+    if (out_bytes == 8) split_reduce_kernel<double><<<blocks, 256, 0, s>>>(p, partial, x.ksplit, x.dbg_p);
+    else split_reduce_kernel<float><<<blocks, 256, 0, s>>>(p, partial, x.ksplit, x.dbg_p);
     return cudaGetLastError();
 }
 

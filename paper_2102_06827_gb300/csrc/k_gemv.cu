@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(gv::T) gemv_partial_kernel(const GemvParams p)
         int64_t ov = 0, ox = 0;
         if (i < nk) radix_offsets(p.k, k0 + i, ov, ox);
         k_off[i] = ox;
-        vk[i] = i < nk ? (p.v_ones ? (T)1 : v[ov]) : (T)0;
+        vk[i] = i < nk ? (p.v_ones ? (T)1 : dbg_ok(p.dbg_v, v + ov, (int)sizeof(T), p.status) ? v[ov] : (T)0) : (T)0;
     }
     for (uint32_t i = t; i < (uint32_t)NT; i += gv::T) {
         int64_t ox = 0, oy = 0;
@@ -87,11 +87,13 @@ __global__ void __launch_bounds__(gv::T) gemv_partial_kernel(const GemvParams p)
         if ((uint32_t)tn < nn) {
             const T *x = X + n_off[tn];
 #pragma unroll 8
-            for (uint32_t k = tk; k < nk; k += 2) a.add(vk[k], x[k_off[k]]);
+            for (uint32_t k = tk; k < nk; k += 2)
+                a.add(vk[k], dbg_ok(p.dbg_x, x + k_off[k], (int)sizeof(T), p.status) ? x[k_off[k]] : (T)0);
         }
         if (tk == 1) red[tn] = a.value();
         __syncthreads();
-        if (tk == 0 && (uint32_t)tn < nn) out[n0 + tn] = a.value() + red[tn];
+        if (tk == 0 && (uint32_t)tn < nn && dbg_ok(p.dbg_p, out + n0 + tn, 8, p.status))
+            out[n0 + tn] = a.value() + red[tn];
     } else {
         // lanes along k (contiguous in X), each warp eight n in turn, warp reduction per n
         const int lane = t & 31, w = t >> 5;
@@ -101,11 +103,12 @@ __global__ void __launch_bounds__(gv::T) gemv_partial_kernel(const GemvParams p)
             const T *x = X + n_off[tn];
             Acc<T> a;
 #pragma unroll 4
-            for (uint32_t k = lane; k < nk; k += 32) a.add(vk[k], x[k_off[k]]);
+            for (uint32_t k = lane; k < nk; k += 32)
+                a.add(vk[k], dbg_ok(p.dbg_x, x + k_off[k], (int)sizeof(T), p.status) ? x[k_off[k]] : (T)0);
             double s = a.value();
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) out[n0 + tn] = s;
+            if (lane == 0 && dbg_ok(p.dbg_p, out + n0 + tn, 8, p.status)) out[n0 + tn] = s;
         }
     }
 }
@@ -117,11 +120,13 @@ __global__ void __launch_bounds__(256) gemv_finish_kernel(const GemvParams p) {
     const uint32_t bi = (uint32_t)(i / p.N), n = (uint32_t)(i - (uint64_t)bi * p.N);
     double s = 0.0;
     const double *part = p.partial + (size_t)bi * p.nchunks * p.N;
-    for (uint32_t c = 0; c < p.nchunks; ++c) s += part[(size_t)c * p.N + n];
+    for (uint32_t c = 0; c < p.nchunks; ++c)
+        if (dbg_ok(p.dbg_p, part + (size_t)c * p.N + n, 8, p.status)) s += part[(size_t)c * p.N + n];
     int64_t ox = 0, oy = 0, by = 0, unused = 0;
     radix_offsets(p.n, n, ox, oy);
     radix_offsets(p.by, bi, by, unused);
     T *y = reinterpret_cast<T *>(p.Y) + by + oy;
+    if (!dbg_ok(p.dbg_y, y, (int)sizeof(T), p.status)) return;
     const double r = p.alpha * s;
     *y = (T)(p.beta != 0.0 ? r + p.beta * (double)*y : r);
 }

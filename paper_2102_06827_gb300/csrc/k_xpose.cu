@@ -34,13 +34,19 @@ struct alignas(sizeof(T) * N) Vec {
 
 template <int OP, typename T, int VO>
 __device__ __forceinline__ void emit(const XposeParams &p, int64_t off, const T (&x)[VO], int e) {
+#ifdef COMET_DEBUG
+    if (p.plant && blockIdx.x == 0 && threadIdx.x == 0) off += p.plant;   // test of the range check
+#endif
     if constexpr (OP == OP_MOVE) {
+        T *o = reinterpret_cast<T *>(p.out) + off;
+        if (!dbg_ok(p.dbg_out, o, VO * (int)sizeof(T), p.status)) return;
         Vec<VO, T> w;
 #pragma unroll
         for (int q = 0; q < VO; ++q) w.v[q] = x[q];
-        *reinterpret_cast<Vec<VO, T> *>(reinterpret_cast<T *>(p.out) + off) = w;
+        *reinterpret_cast<Vec<VO, T> *>(o) = w;
     } else if constexpr (OP == OP_SCALE) {
         T *o = reinterpret_cast<T *>(p.out) + off;
+        if (!dbg_ok(p.dbg_out, o, VO * (int)sizeof(T), p.status)) return;
         Vec<VO, T> w;
         if (p.beta != 0.0) {
             Vec<VO, T> old = *reinterpret_cast<const Vec<VO, T> *>(o);
@@ -56,6 +62,7 @@ __device__ __forceinline__ void emit(const XposeParams &p, int64_t off, const T 
 #pragma unroll
         for (int q = 0; q < VO; ++q) split3<T>(x[q], e, h.v[q], m.v[q], l.v[q]);
         __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(p.out) + off;
+        if (!dbg_ok(p.dbg_out, o, 2 * (2 * p.out_plane + VO), p.status)) return;   // all three planes
         *reinterpret_cast<Vec<VO, __nv_bfloat16> *>(o) = h;
         *reinterpret_cast<Vec<VO, __nv_bfloat16> *>(o + p.out_plane) = m;
         *reinterpret_cast<Vec<VO, __nv_bfloat16> *>(o + 2 * p.out_plane) = l;
@@ -70,6 +77,7 @@ __device__ __forceinline__ void emit(const XposeParams &p, int64_t off, const T 
             for (int k = 0; k < 6; ++k) sl[k].v[q] = v[k];
         }
         __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(p.out) + off;
+        if (!dbg_ok(p.dbg_out, o, 2 * (5 * p.out_plane + VO), p.status)) return;   // all six planes
 #pragma unroll
         for (int k = 0; k < 6; ++k) *reinterpret_cast<Vec<VO, __nv_bfloat16> *>(o + k * p.out_plane) = sl[k];
     }
@@ -150,6 +158,7 @@ __global__ void __launch_bounds__(XT, 8) xpose_tile_kernel(const XposeParams p) 
                 const uint32_t dst = (uint32_t)__cvta_generic_to_shared(buf + u);
                 for (uint32_t row = r0; row < rows_v; row += rpp) {
                     const uint32_t d = dst + row * pitch * (uint32_t)sizeof(T);
+                    if (!dbg_ok(p.dbg_in, src + in_row[row], (int)sizeof(T), p.status)) continue;
                     if (sizeof(T) == 4)
                         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src + in_row[row]) : "memory");
                     else
@@ -168,7 +177,8 @@ __global__ void __launch_bounds__(XT, 8) xpose_tile_kernel(const XposeParams p) 
 #pragma unroll
                 for (int j = 0; j < UB; ++j) {
                     const uint32_t row = row0 + j * rpp;
-                    if (row < rows_v) x[j] = *reinterpret_cast<const Vec<VI, T> *>(src + in_row[row]);
+                    if (row < rows_v && dbg_ok(p.dbg_in, src + in_row[row], VI * (int)sizeof(T), p.status))
+                        x[j] = *reinterpret_cast<const Vec<VI, T> *>(src + in_row[row]);
                 }
 #pragma unroll
                 for (int j = 0; j < UB; ++j) {
@@ -241,6 +251,7 @@ __global__ void __launch_bounds__(XT, 6) xpose_copy_kernel(const XposeParams p) 
         const uint32_t base = (uint32_t)__cvta_generic_to_shared(stage + u);
         for (uint32_t row = r0; row < nw; row += rpp) {
             const uint32_t d = base + row * tu * (uint32_t)sizeof(T);
+            if (!dbg_ok(p.dbg_in, src + row_in[row], (int)sizeof(T), p.status)) continue;
             if (sizeof(T) == 4)
                 asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src + row_in[row]) : "memory");
             else
@@ -260,7 +271,8 @@ __global__ void __launch_bounds__(XT, 6) xpose_copy_kernel(const XposeParams p) 
 #pragma unroll
     for (int j = 0; j < UB; ++j) {
         const uint32_t row = r0 + j * rpp;
-        if (row < nw) x[j] = *reinterpret_cast<const Vec<VW, T> *>(src + row_in[row]);
+        if (row < nw && dbg_ok(p.dbg_in, src + row_in[row], VW * (int)sizeof(T), p.status))
+            x[j] = *reinterpret_cast<const Vec<VW, T> *>(src + row_in[row]);
     }
     for (uint32_t row0 = r0; row0 < nw; row0 += UB * rpp) {
 #pragma unroll
@@ -272,7 +284,8 @@ __global__ void __launch_bounds__(XT, 6) xpose_copy_kernel(const XposeParams p) 
                 for (int q = 0; q < VW; ++q) xs[q] = x[j].v[q];
                 emit<OP, T, VW>(p, (int64_t)row_out[row] + uo, xs, e);
                 const uint32_t nr = row + UB * rpp;
-                if (nr < nw) x[j] = *reinterpret_cast<const Vec<VW, T> *>(src + row_in[nr]);
+                if (nr < nw && dbg_ok(p.dbg_in, src + row_in[nr], VW * (int)sizeof(T), p.status))
+                    x[j] = *reinterpret_cast<const Vec<VW, T> *>(src + row_in[nr]);
             }
         }
     }
@@ -297,7 +310,8 @@ __global__ void __launch_bounds__(XT) xpose_run_kernel(const XposeParams p) {
 #pragma unroll
         for (int j = 0; j < UB; ++j) {
             const uint32_t u = u00 + j * XT * VW;
-            if (u < nvec) x[j] = *reinterpret_cast<const Vec<VW, T> *>(in + ri + (int64_t)u * su);
+            if (u < nvec && dbg_ok(p.dbg_in, in + ri + (int64_t)u * su, VW * (int)sizeof(T), p.status))
+                x[j] = *reinterpret_cast<const Vec<VW, T> *>(in + ri + (int64_t)u * su);
         }
 #pragma unroll
         for (int j = 0; j < UB; ++j) {
@@ -312,6 +326,7 @@ __global__ void __launch_bounds__(XT) xpose_run_kernel(const XposeParams p) {
     }
     if (t < (int)(nu - nvec)) {
         const uint32_t u = nvec + t;
+        if (!dbg_ok(p.dbg_in, in + ri + (int64_t)u * su, (int)sizeof(T), p.status)) return;
         T xs[1] = {in[ri + (int64_t)u * su]};
         emit<OP, T, 1>(p, ro + (int64_t)u * so, xs, e);
     }

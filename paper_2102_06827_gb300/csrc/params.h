@@ -73,6 +73,21 @@ CM_HD void radix_offsets(const Radix &r, uint32_t g, int64_t &o0, int64_t &o1) {
     o1 = b;
 }
 
+// The byte range [lo, hi) of the buffer that one pointer of a launch lies in.  Builds with
+// COMET_DEBUG test every global access of the transpose, GEMM and gemv kernels against the
+// ranges of their launch and skip (and record) any access outside them; release builds carry
+// the ranges and never read them.
+struct DbgRange {
+    const char *lo, *hi;
+};
+
+inline DbgRange dbg_range(const void *base, int64_t bytes) {
+    DbgRange r;
+    r.lo = static_cast<const char *>(base);
+    r.hi = r.lo + (bytes > 0 ? bytes : 0);
+    return r;
+}
+
 // Pure permutation / element-wise tiled copy (transpose engine).  The tensor's dims are split
 // into three groups: U (leading input dims: contiguous reads), V (leading output dims:
 // contiguous writes) and R (the rest).  A CTA moves one TU x TV x TW tile of (u, v, r) through
@@ -94,6 +109,10 @@ struct XposeParams {
     FastDiv fd_ll, fd_sl, fd_tiles_u, fd_tiles_v;
     int off32;                     // every input and output offset is below 2^31
     int single_run;                // copy mode with R empty: one long run, ragged tail allowed
+    DbgRange dbg_in, dbg_out;      // debug builds: the buffers of in and out
+    int *status;                   // debug builds: device status word for an access out of range
+    int64_t plant;                 // debug builds, tests only: added to the first thread's output
+                                   // offsets so that the range check must catch them
 };
 
 constexpr int kXposeTile = 4096;   // elements per tile (32 KB of FP64, 16 KB of FP32)
@@ -121,6 +140,7 @@ struct GemmParams {
     double alpha, beta;
     int *status;
     int64_t timeout_ns;
+    DbgRange dbg_a, dbg_b, dbg_c;  // debug builds: the buffers of A, B and C
 };
 
 // Tensor-times-vector step: y[n] = alpha * sum_k v[k] X[k, n] (+ beta y[n]).  n: free digits
@@ -138,6 +158,24 @@ struct GemvParams {
     int v_ones;                    // 1: v is all ones (a sum over the k digits of X; v unused)
     uint32_t nchunks;              // ceil(K / 1024)
     double *partial;               // workspace: n_batch x nchunks x N FP64 partial sums
+    DbgRange dbg_v, dbg_x, dbg_y, dbg_p;   // debug builds: the buffers of v, X, Y and partial
+    int *status;                   // debug builds: device status word
 };
+
+#if defined(__CUDACC__)
+// True when the `bytes` at p lie inside r.  Debug builds record COMET_ERR_BOUNDS (13) in the
+// status word when they do not, and the caller skips the access; release builds: always true.
+__device__ __forceinline__ bool dbg_ok(const DbgRange &r, const void *p, int64_t bytes, int *status) {
+#ifdef COMET_DEBUG
+    const char *c = static_cast<const char *>(p);
+    if (c >= r.lo && c + bytes <= r.hi) return true;
+    if (status) atomicCAS(status, 0, 13);
+    return false;
+#else
+    (void)r; (void)p; (void)bytes; (void)status;
+    return true;
+#endif
+}
+#endif
 
 }  // namespace comet
