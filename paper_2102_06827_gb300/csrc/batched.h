@@ -59,6 +59,7 @@ struct BatchedParams {
     double alpha;
     char *ws;                    // workspace base
     char *planes;                // split path: start of the plane region
+    int64_t planes_bytes;        // split path: its size (debug builds check the pre-pass writes)
     int *status;                 // device status word (a wait that ran out records COMET_ERR_TIMEOUT)
     int64_t timeout_ns;          // limit of every wait of the tensor-core kernel
     int debug_flags;             // bit 0: one operand load withheld (fault injection, host side)

@@ -152,7 +152,10 @@ __global__ void __launch_bounds__(BT) batched_f64_kernel(const BatchedParams P) 
             for (int e = t; e < BN * KCH; e += BT) {
                 int n, k;
                 if (BKC) { k = e % KCH; n = e / KCH; } else { n = e % BN; k = e / BN; }
-                Bs[k][n] = (n0 + n < N && k0 + k < K) ? (double)B[b_col[n] + b_k[k]] : 0.0;
+                Bs[k][n] = (n0 + n < N && k0 + k < K &&
+                            dbg_ok(dbg_range(B, sd.b_elems * (int64_t)sizeof(TIn)), B + b_col[n] + b_k[k],
+                                   (int)sizeof(TIn), P.status))
+                               ? (double)B[b_col[n] + b_k[k]] : 0.0;
             }
         };
         __syncthreads();
@@ -188,7 +191,10 @@ __global__ void __launch_bounds__(BT) batched_f64_kernel(const BatchedParams P) 
                 for (int e = t; e < BM * KCH; e += BT) {
                     int m, k;
                     if (AK) { k = e % KCH; m = e / KCH; } else { m = e % BM; k = e / BM; }
-                    As[k][m] = (m0 + m < M && k0 + k < K) ? (double)A[a_row[m] + a_k[k]] : 0.0;
+                    As[k][m] = (m0 + m < M && k0 + k < K &&
+                                dbg_ok(dbg_range(A, sd.a_elems * (int64_t)sizeof(TIn)), A + a_row[m] + a_k[k],
+                                       (int)sizeof(TIn), P.status))
+                                   ? (double)A[a_row[m] + a_k[k]] : 0.0;
                 }
                 __syncthreads();
                 const int kmax = (int)min((uint32_t)KCH, K - k0);
@@ -220,7 +226,8 @@ __global__ void __launch_bounds__(BT) batched_f64_kernel(const BatchedParams P) 
                             if (P.mode == 0) {
                                 s += T * ((double)w_row[ml] * (double)w_col[nl]);
                                 q += T * T;
-                            } else if (out) {
+                            } else if (out && dbg_ok(dbg_range(out, (int64_t)M * N * (int64_t)sizeof(TIn)),
+                                                     out + o_row[ml] + o_col[nl], (int)sizeof(TIn), P.status)) {
                                 out[o_row[ml] + o_col[nl]] = (TIn)T;
                             }
                         }
@@ -330,6 +337,7 @@ static comet_status_t run_batched(const Plan &P, const void *const *block_inputs
     bp.alpha = P.alpha;
     bp.ws = w;
     bp.planes = w + L.parts;
+    bp.planes_bytes = P.batched_plane_rows * (int64_t)kBatchedPlaneRow;
     bp.items = P.batched_item_off.empty() ? nullptr
                                           : reinterpret_cast<const ItemRec *>(w + L.items + P.batched_item_off[cfg]);
     bp.status = device_status_word();

@@ -433,7 +433,9 @@ __global__ void __launch_bounds__(btc::THREADS, 1)
 #pragma unroll
                             for (int j = 0; j < 32; ++j) {
                                 const int n = col0 + c + j;
-                                if (n0 + n < N) row[ocol[n]] = sc * (TIn)__uint_as_float(r[j]);
+                                if (n0 + n < N && dbg_ok(dbg_range(out, (int64_t)M * N * (int64_t)sizeof(TIn)),
+                                                         row + ocol[n], (int)sizeof(TIn), P.status))
+                                    row[ocol[n]] = sc * (TIn)__uint_as_float(r[j]);
                             }
                         }
                     }
@@ -471,6 +473,8 @@ __global__ void __launch_bounds__(256) batched_presplit_tc_kernel(const BatchedP
     const Radix &rr = op ? d.nb : d.ma;
     const uint32_t rows = op ? d.N : d.M, pad = op ? d.n_pad : d.m_pad, K = d.K, nkc = (d.K + 31) / 32;
     const TIn *x = reinterpret_cast<const TIn *>(P.inputs[2 * d.index + (op ^ P.swap)]);
+    const DbgRange xr = dbg_range(x, (op ? d.b_elems : d.a_elems) * (int64_t)sizeof(TIn));
+    const DbgRange pr = dbg_range(P.planes, P.planes_bytes);
     const int e = P.exps[2 * d.index + op];
     uint4 *base = reinterpret_cast<uint4 *>(P.planes + (op ? d.b_row0 : d.a_row0) * kBatchedPlaneRow);
     for (uint32_t k = threadIdx.x; k < nkc * 32; k += 256) {
@@ -491,8 +495,10 @@ __global__ void __launch_bounds__(256) batched_presplit_tc_kernel(const BatchedP
                 for (int j = 0; j < 16; j += 2) {
                     __nv_bfloat16 h0, m0, l0, h1, m1, l1;
                     const uint32_t k = kc * 32 + half * 16 + j;
-                    const TIn v0 = (valid && k < K) ? x[ro + k_off[k]] : (TIn)0;
-                    const TIn v1 = (valid && k + 1 < K) ? x[ro + k_off[k + 1]] : (TIn)0;
+                    const TIn v0 = (valid && k < K && dbg_ok(xr, x + ro + k_off[k], (int)sizeof(TIn), P.status))
+                                       ? x[ro + k_off[k]] : (TIn)0;
+                    const TIn v1 = (valid && k + 1 < K && dbg_ok(xr, x + ro + k_off[k + 1], (int)sizeof(TIn), P.status))
+                                       ? x[ro + k_off[k + 1]] : (TIn)0;
                     split3<TIn>(v0, e, h0, m0, l0);
                     split3<TIn>(v1, e, h1, m1, l1);
                     w[0][j >> 1] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
@@ -502,6 +508,7 @@ __global__ void __launch_bounds__(256) batched_presplit_tc_kernel(const BatchedP
 #pragma unroll
                 for (int p = 0; p < 3; ++p) {
                     uint4 *dst = base + ((size_t)(kc * 3 + p) * pad + r) * 4 + half * 2;
+                    if (!dbg_ok(pr, dst, 32, P.status)) continue;
                     dst[0] = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
                     dst[1] = make_uint4(w[p][4], w[p][5], w[p][6], w[p][7]);
                 }

@@ -66,6 +66,7 @@ using namespace tri;
 // every operand has fewer than 2^31 elements (checked when planning).
 struct TileAddr {
     int base, sd, s[3], rem[3];
+    int n;                     // elements of the operand (debug builds check the staging reads)
 };
 
 template <typename T>
@@ -111,15 +112,18 @@ struct Lane {
 // issue the asynchronous copies of one operand tile into S (entries outside the tile are not
 // written: they only feed T elements outside the block, which the energy skips)
 template <typename T>
-__device__ __forceinline__ void stage_async(T (*S)[RP], const T *__restrict__ src, const TileAddr &ta, int kn) {
+__device__ __forceinline__ void stage_async(T (*S)[RP], const T *__restrict__ src, const TileAddr &ta, int kn,
+                                            int *status) {
     using L = Lane<T>;
     const L ln;
     if (ln.kk >= kn || ln.d0 >= ta.rem[0]) return;
     const T *row = src + (ta.base + ln.kk * ta.sd + ln.d0 * ta.s[0] + ln.h * ta.s[1]);
     const unsigned dst = (unsigned)__cvta_generic_to_shared(&S[ln.kk][ln.r0]);
+    const DbgRange rg = dbg_range(src, (int64_t)ta.n * (int64_t)sizeof(T));
 #pragma unroll
     for (int it = 0; it < L::NIT; ++it)
-        if (ln.h + L::dd1(it) < ta.rem[1] && L::d2(it) < ta.rem[2])
+        if (ln.h + L::dd1(it) < ta.rem[1] && L::d2(it) < ta.rem[2] &&
+            dbg_ok(rg, row + (L::dd1(it) * ta.s[1] + L::d2(it) * ta.s[2]), (int)sizeof(T), status))
             cp_async_elem(dst + (unsigned)(it * L::RS * (int)sizeof(T)),
                           row + (L::dd1(it) * ta.s[1] + L::d2(it) * ta.s[2]), (int)sizeof(T));
 }
@@ -146,6 +150,7 @@ __device__ __forceinline__ TileAddr tile_addr(const int8_t *q, const int8_t *col
         }
         st *= ext_b[col[m]];
     }
+    ta.n = st;
     return ta;
 }
 
@@ -359,8 +364,8 @@ __global__ void __launch_bounds__(NT, 3) triples_kernel(const Args a) {
                 const int kn = min(kc, K - kk0);
                 const T *X = reinterpret_cast<const T *>(s_ops[2 * pp]);
                 const T *Y = reinterpret_cast<const T *>(s_ops[2 * pp + 1]);
-                stage_async<T>(Xs[bb], X, addr(pp, 0, kk0), kn);
-                stage_async<T>(Ys[bb], Y, addr(pp, 1, kk0), kn);
+                stage_async<T>(Xs[bb], X, addr(pp, 0, kk0), kn, a.status);
+                stage_async<T>(Ys[bb], Y, addr(pp, 1, kk0), kn, a.status);
                 cp_async_commit();
             };
             issue(0, 0, 0);
@@ -469,6 +474,7 @@ __device__ __forceinline__ int extract6(int t, int m) {
 // the entries left in the tile (at most 4)
 struct StageAddr {
     int base, sd, s[3], rem[3];
+    int n;                     // elements of the operand (debug builds check the staging reads)
 };
 
 __device__ __forceinline__ StageAddr stage_addr(const int8_t *q, const int8_t *col, const int8_t *rank,
@@ -491,6 +497,7 @@ __device__ __forceinline__ StageAddr stage_addr(const int8_t *q, const int8_t *c
         }
         st *= ext_b[col[m]];
     }
+    sa.n = st;
     return sa;
 }
 
@@ -500,15 +507,17 @@ __device__ __forceinline__ int row_coord(int r, int i) { return 2 * ((r >> (3 + 
 // thread t copies row t of the operand tile for summed indices k0 .. k0 + kn - 1 (rows outside
 // the tile are not written: they only feed elements outside the block, which the energy skips)
 __device__ __forceinline__ void stage32(float (*S)[RP32], const float *__restrict__ src, const StageAddr &sa, int k0,
-                                        int kn) {
+                                        int kn, int *status) {
     const int r = (int)threadIdx.x;
     const int c0 = row_coord(r, 0), c1 = row_coord(r, 1), c2 = row_coord(r, 2);
     if (c0 >= sa.rem[0] || c1 >= sa.rem[1] || c2 >= sa.rem[2]) return;
     const float *g = src + (sa.base + k0 * sa.sd + c0 * sa.s[0] + c1 * sa.s[1] + c2 * sa.s[2]);
     const unsigned dst = (unsigned)__cvta_generic_to_shared(&S[0][r]);
+    const DbgRange rg = dbg_range(src, (int64_t)sa.n * 4);
 #pragma unroll 4
     for (int kk = 0; kk < kn; ++kk)
-        cp_async_elem(dst + (unsigned)(kk * RP32 * 4), g + (int64_t)kk * sa.sd, 4);
+        if (dbg_ok(rg, g + (int64_t)kk * sa.sd, 4, status))
+            cp_async_elem(dst + (unsigned)(kk * RP32 * 4), g + (int64_t)kk * sa.sd, 4);
 }
 
 // alpha times the entries this thread copied (after their copies completed)
@@ -663,8 +672,9 @@ __global__ void __launch_bounds__(NT32, CTAS32) triples_f32_kernel(const Args a)
                 const int K = s_ext[a.term[pp].d_col];
                 const int kn = min(KC32, K - kk0);
                 const int sp = (a.term[pp].xmask & 1) ? 0 : 1;   // operand holding T label 0
-                stage32(Ps[bb], reinterpret_cast<const float *>(s_ops[2 * pp + sp]), s_sa[pp][sp], kk0, kn);
-                stage32(Bs[bb], reinterpret_cast<const float *>(s_ops[2 * pp + 1 - sp]), s_sa[pp][1 - sp], kk0, kn);
+                stage32(Ps[bb], reinterpret_cast<const float *>(s_ops[2 * pp + sp]), s_sa[pp][sp], kk0, kn, a.status);
+                stage32(Bs[bb], reinterpret_cast<const float *>(s_ops[2 * pp + 1 - sp]), s_sa[pp][1 - sp], kk0, kn,
+                        a.status);
                 cp_async_commit();
             };
             issue(0, 0, 0);
@@ -808,6 +818,7 @@ comet_status_t comet_triples_energy(comet_plan_t plan, const void *operands, con
     a.energies = energies;
     a.counter = reinterpret_cast<unsigned long long *>(w + tp.ws_counter);
     a.total = tp.prefix.back();
+    a.status = device_status_word();
     cudaError_t e = cudaMemsetAsync(energies, 0, sizeof(double) * tp.n_blocks, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.counter, 0, 8, s);
     if (e != cudaSuccess) { set_error_message(cudaGetErrorString(e)); return COMET_ERR_CUDA; }

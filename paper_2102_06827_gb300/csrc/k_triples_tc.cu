@@ -238,6 +238,8 @@ __global__ void __launch_bounds__(256) triples_tc_split_kernel(const Args a, con
     const OpGeo g = op_geo(a.term[p], side, ext_b);
     const float *x = reinterpret_cast<const float *>(a.ops[((int64_t)b * a.n_terms + p) * 2 + side]);
     uint4 *base = reinterpret_cast<uint4 *>(t.planes + (int64_t)t.row0[((int64_t)b * a.n_terms + p) * 2 + side] * tc::ROWB);
+    const DbgRange xr = dbg_range(x, (int64_t)g.ext[0] * g.ext[1] * g.ext[2] * g.ed * 4);
+    const DbgRange pr = dbg_range(t.planes, t.planes_bytes);
     const int64_t rows = (int64_t)g.nt[0] * g.nt[1] * g.nt[2] * g.rpt;
     for (int64_t R = threadIdx.x; R < rows; R += blockDim.x) {
         const int64_t tile = R / g.rpt;
@@ -255,8 +257,10 @@ __global__ void __launch_bounds__(256) triples_tc_split_kernel(const Args a, con
 #pragma unroll
                 for (int j = 0; j < 16; j += 2) {
                     const int k = ch * tc::KCH + half * 16 + j;
-                    const float v0 = (valid && k < g.ed) ? x[ro + (int64_t)k * g.sd] : 0.0f;
-                    const float v1 = (valid && k + 1 < g.ed) ? x[ro + (int64_t)(k + 1) * g.sd] : 0.0f;
+                    const float v0 = (valid && k < g.ed && dbg_ok(xr, x + ro + (int64_t)k * g.sd, 4, a.status))
+                                         ? x[ro + (int64_t)k * g.sd] : 0.0f;
+                    const float v1 = (valid && k + 1 < g.ed && dbg_ok(xr, x + ro + (int64_t)(k + 1) * g.sd, 4, a.status))
+                                         ? x[ro + (int64_t)(k + 1) * g.sd] : 0.0f;
                     __nv_bfloat16 h0, m0, l0, h1, m1, l1;
                     split_bf16x3(v0, h0, m0, l0);
                     split_bf16x3(v1, h1, m1, l1);
@@ -267,6 +271,7 @@ __global__ void __launch_bounds__(256) triples_tc_split_kernel(const Args a, con
 #pragma unroll
                 for (int pl = 0; pl < 3; ++pl) {
                     uint4 *dst = base + (((tile * g.nch + ch) * 3 + pl) * g.rpt + rr) * 4 + half * 2;
+                    if (!dbg_ok(pr, dst, 32, a.status)) continue;
                     dst[0] = make_uint4(w[pl][0], w[pl][1], w[pl][2], w[pl][3]);
                     dst[1] = make_uint4(w[pl][4], w[pl][5], w[pl][6], w[pl][7]);
                 }
@@ -562,6 +567,9 @@ cudaError_t launch_triples_tc(const Plan &P, const Args &a, TcArgs t, cudaStream
         t.item0 = tp.tc_prefix[t.b0];
         t.n_items = tp.tc_prefix[t.b1] - t.item0;
         if (t.n_items == 0) continue;
+        int64_t batch_rows = 0;
+        for (int b = t.b0; b < t.b1; ++b) batch_rows += tp.tc_rows[b];
+        t.planes_bytes = batch_rows * tc::ROWB;
         const unsigned segs = (unsigned)((t.b1 - t.b0) * a.n_terms * 2);
         triples_tc_split_kernel<<<segs, 256, 0, s>>>(a, t);
         const int ctas = (int)std::min<int64_t>(t.n_items, std::max(1, sms));

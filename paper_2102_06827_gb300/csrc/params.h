@@ -81,7 +81,7 @@ struct DbgRange {
     const char *lo, *hi;
 };
 
-inline DbgRange dbg_range(const void *base, int64_t bytes) {
+CM_HD DbgRange dbg_range(const void *base, int64_t bytes) {
     DbgRange r;
     r.lo = static_cast<const char *>(base);
     r.hi = r.lo + (bytes > 0 ? bytes : 0);

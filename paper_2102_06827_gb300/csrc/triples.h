@@ -91,6 +91,7 @@ struct Args {
     double *energies;
     unsigned long long *counter;
     int64_t total;
+    int *status;               // debug builds: device status word for an operand access out of range
 };
 
 // One term of one block on the tensor-core path: the plane rows of its two operand tiles for a
@@ -116,6 +117,7 @@ struct TcArgs {
     int *status;               // device status word (a wait that ran out records COMET_ERR_TIMEOUT)
     int64_t timeout_ns;        // limit of every wait
     int debug_flags;           // bit 0: one ring slot's loads withheld (fault injection, host side)
+    int64_t planes_bytes;      // debug builds: size of the batch's plane region
 };
 }  // namespace tri
 

@@ -1,10 +1,12 @@
 """The GPU parity suite against the COMET_DEBUG build (libcomet_debug.so).
 
-In that build the transpose, GEMM and gemv kernels test every global access against the byte
-ranges of their launch's buffers and report COMET_ERR_BOUNDS instead of making it.  This test
+In that build the transpose, GEMM, gemv, batched and triples kernels test their global accesses
+(the tensor-core kernels: every access outside their tensor maps) against the byte ranges of the
+buffers they belong to and report COMET_ERR_BOUNDS instead of making them.  This test
 builds it and runs the contraction, view, batch-label, reduction, gemv, transpose, emulated-FP64,
-host-pipeline and guard-band suites in a child process that loads it (COMET_LIBRARY): every test
-there ends in comet_sync_status(), so any access outside a buffer fails it.  The planted-store
+host-pipeline, guard-band, batched and triples-energy suites in a child process that loads it
+(COMET_LIBRARY): every test there ends in comet_sync_status(), so any access outside a buffer
+fails it.  The planted-store
 test (test_gpu_debug_plant.py) runs there too and checks that the check fires.
 """
 import os
@@ -18,7 +20,7 @@ pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SUITES = ["test_gpu_debug_plant.py", "test_gpu_contract.py", "test_gpu_views.py", "test_gpu_batch_labels.py",
           "test_gpu_reduce.py", "test_gpu_gemv.py", "test_gpu_transpose.py", "test_gpu_emu.py",
-          "test_gpu_host.py", "test_gpu_canaries.py"]
+          "test_gpu_host.py", "test_gpu_canaries.py", "test_gpu_batched.py", "test_gpu_triples_energy.py"]
 
 
 def test_gpu_suite_under_range_checks():
