@@ -995,6 +995,12 @@ def main():
                "achieved_gbs": pre_bytes / (p_ms / max(1, a.steps) * 1e-3) / 1e9 if p_ms else None,
                "peak_gbs": peaks.get("hbm_gbs") if peaks else 6800.0}
     prepass["frac"] = prepass["achieved_gbs"] / prepass["peak_gbs"] if prepass["achieved_gbs"] else None
+    # the same time against every byte the pass moves: the abs-max launch reads both operands once
+    # more before the split can start (the fixed-point grid needs each operand's largest magnitude)
+    moved = pre_bytes + 2.0 * N_ELEM * 4
+    prepass["bytes_moved_per_step"] = moved
+    prepass["frac_of_bytes_moved"] = (moved / (p_ms / max(1, a.steps) * 1e-3) / 1e9 / prepass["peak_gbs"]
+                                      if p_ms else None)
 
     # ---------------- FP64 form of the same contraction ----------------
     plan64 = comet.Plan(EXPR, EXT, torch.float64, precision="native")
