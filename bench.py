@@ -461,11 +461,27 @@ def run_triples_energy(a) -> int:
             peaks = measured_peaks() or {}
             bpk = peaks.get("bf16_tflops", 1900.0)
             issued = mma_flops / (t * 1e-3) / 1e12
+            # the bound the design identifies: shared-memory bytes per pair-tile, modelled from the
+            # kernel's data flow (TMA fills of both operands' three planes per 32 summed indices;
+            # MMA operand reads of 128 + 64 rows x 32 bytes per product and 16 indices; the
+            # drain's read and write of the 32 KB pair-tile per term, the first term a write only;
+            # the energy pass's read), against 128 bytes per clock per SM at the sampled clock
+            ed = e64[:, col["d"]]
+            nt = len(tl)
+            per_pt = (nt * (-(-ed // 32) * 3 * (128 + 64) * 64 + -(-ed // 16) * 6 * (128 + 64) * 32)
+                      + 32768 + (nt - 1) * 65536 + 32768)
+            smem_bytes = float(np.sum(pt * per_pt))
+            smem_peak = 152 * 128 * sm_mhz * 1e6 / 1e12
+            smem_tbs = smem_bytes / (t * 1e-3) / 1e12
             roof = {"bound": "tensor", "achieved": issued, "peak": bpk, "unit": "TFLOP/s", "frac": issued / bpk,
                     "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)",
                     "mma_flops_issued": mma_flops, "pair_tiles": int(plan.info["pair_tiles"]),
                     "useful_vs_fp32_fma": {"achieved": achieved, "peak": peak, "frac": achieved / peak,
-                                           "peak_source": "FP32 FMA lanes x median SM clock under load"}}
+                                           "peak_source": "FP32 FMA lanes x median SM clock under load"},
+                    "shared_memory_model": {"bytes": smem_bytes, "bytes_per_pair_tile": smem_bytes / float(np.sum(pt)),
+                                            "achieved": smem_tbs, "peak": smem_peak, "unit": "TB/s",
+                                            "frac": smem_tbs / smem_peak,
+                                            "peak_source": "152 SMs x 128 bytes per clock x median SM clock"}}
         out[name] = {"blocks": n_blocks, "ms_per_step": t, "steps": steps, "tflops": achieved,
                      "roofline": roof, "path": ("tensor cores (split BF16, 6 products)"
                                                 if name == "f32" and plan.info.get("tensor_core") else "FMA"),
