@@ -151,3 +151,58 @@ def test_terms_add_linearly(comet, dtype, tol):
         comet.sync_status()
         res.append(float(en.item()))
     assert abs(res[0] - res[1]) <= tol * abs(res[0])
+
+
+def test_full_workload_sampled(comet):
+    # the 4096-block workload the bench times (extents uniform 8..32, seed 3; operands uniform
+    # [-1, 1) from seed 11 in one device buffer; eps in [1, 2) and [-2, -1)), FP32 on the tensor
+    # cores in one call: every energy finite and negative (D < 0 everywhere), and the two smallest
+    # blocks and the median-sized one within 2e-5 of the oracle on the values the GPU read
+    import torch
+    import synth
+    tl = terms()
+    col = {l: q for q, l in enumerate(LABELS)}
+    ext = synth.triples_blocks(4096)
+    opl = [[tuple(col[l] for l in ls) for ls in pair] for pair in
+           [[oracle.parse(e)[4][0][1], oracle.parse(e)[4][1][1]] for e in tl]]
+    sizes = np.array([int(np.prod(ext[b, list(c)])) for b in range(len(ext)) for pair in opl for c in pair],
+                     dtype=np.int64)
+    buf = torch.empty(int(sizes.sum()), dtype=torch.float32, device="cuda")
+    chunk = 1 << 27
+    for c0 in range(0, buf.numel(), chunk):
+        n = min(chunk, buf.numel() - c0)
+        buf[c0:c0 + n] = synth.torch_uniform(11, c0 // chunk, n, "cuda").float()
+    starts = np.concatenate([[0], np.cumsum(sizes)])
+    ops = torch.tensor(starts[:-1] * 4, dtype=torch.int64, device="cuda") + buf.data_ptr()
+    e_sizes = np.array([int(ext[b, col[l]]) for b in range(len(ext)) for l in T_LABELS], dtype=np.int64)
+    e_starts = np.concatenate([[0], np.cumsum(e_sizes)])
+    shift = np.concatenate([np.full(n, 1.5 if q % 6 < 3 else -1.5) for q, n in enumerate(e_sizes)])
+    ebuf = (synth.torch_uniform(12, 0, int(e_sizes.sum()), "cuda") * 0.5 + torch.from_numpy(shift).cuda()).float()
+    eps = torch.tensor(e_starts[:-1] * 4, dtype=torch.int64, device="cuda") + ebuf.data_ptr()
+    plan = comet.TriplesPlan(tl, LABELS, ext, SIGNS, torch.float32)
+    assert plan.info["tensor_core"]
+    ws = plan.workspace()
+    plan.prepare(ws)
+    en = torch.empty(len(ext), dtype=torch.float64, device="cuda")
+    plan.energy(ops, eps, en, ws)
+    comet.sync_status()
+    got = en.cpu().numpy()
+    assert np.all(np.isfinite(got)) and np.all(got < 0)
+    t_size = np.prod(ext[:, :6], axis=1)
+    order = np.argsort(t_size, kind="stable")
+    per_block = 2 * len(tl)
+    for b in [int(order[0]), int(order[1]), int(order[len(order) // 2])]:
+        host_ops = []
+        for p, pair in enumerate(opl):
+            xs = []
+            for q, c in enumerate(pair):
+                k = b * per_block + 2 * p + q
+                v = buf[int(starts[k]):int(starts[k + 1])].double().cpu().numpy()
+                xs.append(np.reshape(v, [int(ext[b, i]) for i in c], order="F"))
+            host_ops.append(tuple(xs))
+        host_eps = [ebuf[int(e_starts[b * 6 + q]):int(e_starts[b * 6 + q + 1])].double().cpu().numpy()
+                    for q in range(6)]
+        ref = oracle.triples_energy(tl, host_ops, host_eps, SIGNS)[0]
+        assert abs(got[b] - ref) <= 2e-5 * abs(ref), (b, got[b], ref)
+    del buf, ebuf, ws
+    torch.cuda.empty_cache()
