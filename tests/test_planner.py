@@ -337,6 +337,26 @@ def test_host_pipeline_plans():
     assert hp["label"] == "n" and hp["bounds"] == [0, 3, 6, 9]
 
 
+def test_host_n_argument_checks():
+    """comet_contract_host_n refuses a call count below 1 and missing pointers before any
+    device work (no GPU needed to reach these returns)."""
+    import ctypes
+    p = plan("C[i,j] = A[i,k] * B[k,j]", dict(i=8, j=8, k=8), "f32", precision="split_bf16")
+    L = comet.lib()
+    vp = ctypes.c_void_p
+    hin = (vp * 2)(16, 32)
+    hout = (vp * 1)(48)
+    din = (vp * 2)(64, 80)
+    assert L.comet_contract_host_n(p._h, 0, hin, hout, din, vp(96), vp(112), None) == 12    # COMET_ERR_ARG
+    assert L.comet_contract_host_n(p._h, 1, hin, hout, din, None, vp(112), None) == 7       # COMET_ERR_NULL
+    assert L.comet_contract_host_n(p._h, 1, (vp * 2)(16, None), hout, din, vp(96), vp(112), None) == 7
+    assert L.comet_contract_host_n(p._h, 1, hin, (vp * 1)(None), din, vp(96), vp(112), None) == 7
+    assert L.comet_contract_host_n(None, 1, hin, hout, din, vp(96), vp(112), None) == 7
+    # two calls need 2 x n_in host input pointers: the second call's null one is caught
+    assert L.comet_contract_host_n(p._h, 2, (vp * 4)(16, 32, 16, None), (vp * 2)(48, 48), din, vp(96), vp(112),
+                                   None) == 7
+
+
 def test_views_and_diagonals_layout():
     """comet_plan_views: strides = stored strides x steps, summed over dimensions that share a
     label (diagonals); offset = sum of lo x stored strides; checks of the view arguments."""
