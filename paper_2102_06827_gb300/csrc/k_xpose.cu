@@ -242,17 +242,19 @@ __global__ void __launch_bounds__(XT, 6) xpose_copy_kernel(const XposeParams p) 
     if (!(r0 < rpp && u < nu)) return;
     const T *__restrict__ src = in + (int64_t)u * su;
     const int64_t uo = (int64_t)u * so;
-    if constexpr (VW == 1) {
-        // element-wise rows: every load of the thread goes out at once as an asynchronous copy
-        // into its own slots of the tile (no register holds the data), then the thread stores
-        // what it copied; no other thread reads these slots, so no block barrier is needed
+    if constexpr (VW * sizeof(T) <= 8) {
+        // element-wise (or 8-byte FP32) rows: every load of the thread goes out at once as an
+        // asynchronous copy into its own slots of the tile (no register holds the data), then
+        // the thread stores what it copied; no other thread reads these slots, so no block
+        // barrier is needed
         extern __shared__ __align__(16) unsigned char csm[];
         T *stage = reinterpret_cast<T *>(csm);
         const uint32_t base = (uint32_t)__cvta_generic_to_shared(stage + u);
+        constexpr int VB = VW * (int)sizeof(T);
         for (uint32_t row = r0; row < nw; row += rpp) {
             const uint32_t d = base + row * tu * (uint32_t)sizeof(T);
-            if (!dbg_ok(p.dbg_in, src + row_in[row], (int)sizeof(T), p.status)) continue;
-            if (sizeof(T) == 4)
+            if (!dbg_ok(p.dbg_in, src + row_in[row], VB, p.status)) continue;
+            if (VB == 4)
                 asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src + row_in[row]) : "memory");
             else
                 asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src + row_in[row]) : "memory");
@@ -260,8 +262,11 @@ __global__ void __launch_bounds__(XT, 6) xpose_copy_kernel(const XposeParams p) 
         asm volatile("cp.async.wait_all;\n" ::: "memory");
 #pragma unroll 4
         for (uint32_t row = r0; row < nw; row += rpp) {
-            T xs[1] = {stage[row * tu + u]};
-            emit<OP, T, 1>(p, (int64_t)row_out[row] + uo, xs, e);
+            const Vec<VW, T> w = *reinterpret_cast<const Vec<VW, T> *>(stage + row * tu + u);
+            T xs[VW];
+#pragma unroll
+            for (int q = 0; q < VW; ++q) xs[q] = w.v[q];
+            emit<OP, T, VW>(p, (int64_t)row_out[row] + uo, xs, e);
         }
         return;
     }
@@ -492,12 +497,15 @@ static cudaError_t launch_op(const XposeParams &p, int vi, int vo, cudaStream_t 
             else xpose_run_kernel<OP, T, 1><<<g, XT, 0, s>>>(p);
             return cudaGetLastError();
         }
-        const size_t stage = (size_t)p.tu * p.tw * sizeof(T);   // element-wise rows stage in shared memory
+        const size_t stage = (size_t)p.tu * p.tw * sizeof(T);   // asynchronous rows stage in shared memory
+        const bool half = W == 4 && -vo >= 2 && vi >= 2;        // FP32 rows in 8-byte pieces
         if (p.off32) {
             if (wide) xpose_copy_kernel<OP, T, W, int32_t><<<g, XT, 0, s>>>(p);
+            else if (half) xpose_copy_kernel<OP, T, (W == 4 ? 2 : 1), int32_t><<<g, XT, stage, s>>>(p);
             else xpose_copy_kernel<OP, T, 1, int32_t><<<g, XT, stage, s>>>(p);
         } else {
             if (wide) xpose_copy_kernel<OP, T, W, int64_t><<<g, XT, 0, s>>>(p);
+            else if (half) xpose_copy_kernel<OP, T, (W == 4 ? 2 : 1), int64_t><<<g, XT, stage, s>>>(p);
             else xpose_copy_kernel<OP, T, 1, int64_t><<<g, XT, stage, s>>>(p);
         }
         return cudaGetLastError();

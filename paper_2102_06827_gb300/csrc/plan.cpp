@@ -277,18 +277,19 @@ void setup_xpose(int rank, const int64_t *ext_in, const int64_t *sin_in,
         return true;
     };
     // the transposing kernel comes in 16-byte, 8-byte (FP32) and element-wide variants, copy
-    // mode in 16-byte and element-wide ones (measured: its element-wise rows, all in flight as
-    // asynchronous copies, beat 8-byte vectors through registers).  A single long run (copy
-    // mode, R empty) moves its ragged tail element-wise, so only the strides matter there.
+    // mode in 16-byte ones through registers and 8-byte (FP32) and element-wide ones as
+    // asynchronous copies into shared memory (measured: element-wise rows all in flight beat
+    // 8-byte vectors through registers).  A single long run (copy mode, R empty) moves its
+    // ragged tail element-wise, so only the strides matter there.
     p->single_run = (same && R.empty() && Eu > TAB) ? 1 : 0;
     const bool unit = p->u.s0[0] == 1 && p->u.s1[0] == 1 && in_off % w == 0 && out_off % w == 0;
-    auto pick = [&](const auto &ok) { return ok(w) ? w : (w == 4 && !same && ok(2)) ? 2 : 1; };
+    auto pick = [&](const auto &ok) { return ok(w) ? w : (w == 4 && ok(2)) ? 2 : 1; };
     const int vi = p->single_run ? (unit ? w : 1) : pick(ok_in);
     const int vo = p->single_run ? (unit ? w : 1) : pick(ok_out);
     const int vc = std::min(vi, vo);
     *vec_in = same ? vc : vi;
     *vec_out = same ? -vc : vo;   // negative = copy mode (no shared-memory transposition)
-    if (same && !p->single_run && vc == 1)   // element-wise copy rows stage in shared memory:
+    if (same && !p->single_run && vc < w)   // asynchronous copy rows stage in shared memory:
         tw = std::min<uint32_t>(tw, std::max<uint32_t>(1, TILE / tu));   // keep the tile at TILE
     p->tu = tu; p->tv = tv; p->tw = tw;
     p->ll = (tu + *vec_in - 1) / *vec_in;

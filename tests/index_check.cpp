@@ -75,7 +75,7 @@ static bool replay(const XposeParams &p, int vi, int vo, int64_t n_in, int64_t n
                     if (c >= 0 && c < n_out_span) { CHECK(src_of_out[c] == -1, "written twice"); src_of_out[c] = a; }
                 }
             };
-            CHECK(VW != 1 || (uint64_t)tu * tw * 8 <= 48 * 1024, "copy-mode stage above 48 KB of shared memory");
+            CHECK(VW > 2 || (uint64_t)tu * tw * 8 <= 48 * 1024, "copy-mode stage above 48 KB of shared memory");
             const uint32_t lanes = p.ll;
             if (p.single_run) {
                 CHECK(nw == 1 && p.r.total == 1, "long-row copy with several rows");
@@ -319,7 +319,7 @@ int main() {
             const uint64_t grid = (uint64_t)p.tiles_u * p.tiles_v * p.tiles_w;
             CHECK(grid < (1ull << 31), "grid of %llu blocks", (unsigned long long)grid);
             if (vo > 0) CHECK(xpose_smem_bytes(p, es) <= 96 * 1024, "tile shared memory %u", xpose_smem_bytes(p, es));
-            if (vo == -1 && !p.single_run)
+            if ((vo == -1 || (vo == -2 && es == 4)) && !p.single_run)   // rows staged in shared memory
                 CHECK((uint64_t)p.tu * p.tw * es <= 48 * 1024, "copy stage of %llu bytes", (unsigned long long)p.tu * p.tw * es);
         }
     }
