@@ -247,8 +247,8 @@ def test_transpose_argument_checks():
 
 
 def test_transpose_vector_widths():
-    # 16-byte vectors where the leading runs allow, 8-byte ones for FP32 runs of even extent in
-    # the transposing kernel, element-wise rows in copy mode otherwise (widths in elements;
+    # 16-byte vectors where the leading runs allow, 8-byte ones for FP32 runs of even extent
+    # (copy mode: asynchronous 8-byte row pieces), element-wise otherwise (widths in elements;
     # a negative vec_out marks copy mode)
     def step(expr, ext, dtype):
         return comet.Plan(expr, ext, dtype).info["steps"][0]
@@ -261,9 +261,14 @@ def test_transpose_vector_widths():
     assert (s["vec_in"], s["vec_out"]) == (1, 2)
     s = step(t, dict(a=230, b=16, c=146, d=54), "f64")
     assert (s["vec_in"], s["vec_out"]) == (2, 2)
-    # copy mode (the first label stays first): 8-byte rows are not used there
+    # copy mode (the first label stays first): 8-byte pieces for an even FP32 run, element-wise
+    # for an odd one
     s = step("C[a,e,d,b,c,f] = A[a,b,c,d,e,f]", dict(a=14, b=30, c=31, d=42, e=62, f=12), "f32")
+    assert (s["vec_in"], s["vec_out"]) == (2, -2)
+    s = step("C[a,e,d,b,c,f] = A[a,b,c,d,e,f]", dict(a=15, b=30, c=31, d=42, e=62, f=12), "f32")
     assert (s["vec_in"], s["vec_out"]) == (1, -1)
+    s = step("C[a,e,d,b,c,f] = A[a,b,c,d,e,f]", dict(a=14, b=30, c=31, d=42, e=62, f=12), "f64")
+    assert (s["vec_in"], s["vec_out"]) == (2, -2)   # 16 bytes: FP64's full vector
     s = step("C[a,e,d,b,c,f] = A[a,b,c,d,e,f]", dict(a=16, b=30, c=31, d=42, e=62, f=12), "f32")
     assert (s["vec_in"], s["vec_out"]) == (4, -4)
 
