@@ -268,29 +268,29 @@ __global__ void __launch_bounds__(XT, 6) xpose_copy_kernel(const XposeParams p) 
             for (int q = 0; q < VW; ++q) xs[q] = w.v[q];
             emit<OP, T, VW>(p, (int64_t)row_out[row] + uo, xs, e);
         }
-        return;
-    }
-    // rows r0, r0 + rpp, ...: a ring of UB loads stays in flight; each store is followed by the
-    // load of the row UB passes ahead into the register it freed
-    Vec<VW, T> x[UB];
-#pragma unroll
-    for (int j = 0; j < UB; ++j) {
-        const uint32_t row = r0 + j * rpp;
-        if (row < nw && dbg_ok(p.dbg_in, src + row_in[row], VW * (int)sizeof(T), p.status))
-            x[j] = *reinterpret_cast<const Vec<VW, T> *>(src + row_in[row]);
-    }
-    for (uint32_t row0 = r0; row0 < nw; row0 += UB * rpp) {
+    } else {
+        // rows r0, r0 + rpp, ...: a ring of UB loads stays in flight; each store is followed by
+        // the load of the row UB passes ahead into the register it freed
+        Vec<VW, T> x[UB];
 #pragma unroll
         for (int j = 0; j < UB; ++j) {
-            const uint32_t row = row0 + j * rpp;
-            if (row < nw) {
-                T xs[VW];
+            const uint32_t row = r0 + j * rpp;
+            if (row < nw && dbg_ok(p.dbg_in, src + row_in[row], VW * (int)sizeof(T), p.status))
+                x[j] = *reinterpret_cast<const Vec<VW, T> *>(src + row_in[row]);
+        }
+        for (uint32_t row0 = r0; row0 < nw; row0 += UB * rpp) {
 #pragma unroll
-                for (int q = 0; q < VW; ++q) xs[q] = x[j].v[q];
-                emit<OP, T, VW>(p, (int64_t)row_out[row] + uo, xs, e);
-                const uint32_t nr = row + UB * rpp;
-                if (nr < nw && dbg_ok(p.dbg_in, src + row_in[nr], VW * (int)sizeof(T), p.status))
-                    x[j] = *reinterpret_cast<const Vec<VW, T> *>(src + row_in[nr]);
+            for (int j = 0; j < UB; ++j) {
+                const uint32_t row = row0 + j * rpp;
+                if (row < nw) {
+                    T xs[VW];
+#pragma unroll
+                    for (int q = 0; q < VW; ++q) xs[q] = x[j].v[q];
+                    emit<OP, T, VW>(p, (int64_t)row_out[row] + uo, xs, e);
+                    const uint32_t nr = row + UB * rpp;
+                    if (nr < nw && dbg_ok(p.dbg_in, src + row_in[nr], VW * (int)sizeof(T), p.status))
+                        x[j] = *reinterpret_cast<const Vec<VW, T> *>(src + row_in[nr]);
+                }
             }
         }
     }
