@@ -48,8 +48,9 @@ constexpr int B_STAGE = S * B_PLANE;            // 30 KB
 constexpr int STAGE_BYTES = A_STAGE + B_STAGE;  // 78 KB
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
-constexpr int GROUPS = 6;
+constexpr int GROUPS = 6;                       // weight groups of the slice products
 constexpr uint32_t TMEM_COLS = 512;             // groups at columns 80 w, w = 0..5
+static_assert(GROUPS * BG <= (int)TMEM_COLS, "every weight group's accumulator in tensor memory");
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + BG * 8 /*c_col*/ + 256;
 constexpr uint32_t SW64 = 4;
 constexpr uint32_t SBO = 8 * BK * 2;
