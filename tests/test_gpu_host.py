@@ -226,3 +226,16 @@ def test_pipelined_calls_emulated_and_serial(comet):
     for t, arrays in enumerate(sets):
         assert np.array_equal(got[t], single[t])
         assert normwise(got[t], oracle.einsum(CCSD, *arrays)) <= 1e-6
+
+
+def test_calls_of_a_chain_run_in_order(comet):
+    # a multi-step plan has no slice pipeline: the calls run one after another on the stream,
+    # each equal to its single call and to the oracle
+    e = "D[i,l] = A[i,j] * B[j,k] * C[k,l]"
+    ext = dict(i=40, j=50, k=60, l=30)
+    sets = [inputs(e, ext, 60 + t) for t in range(3)]
+    got, p, single = run_host_n(comet, e, ext, sets, np.float64, "native")
+    assert "host_pipe" not in p.info
+    for t, arrays in enumerate(sets):
+        assert np.array_equal(got[t], single[t])
+        assert normwise(got[t], oracle.einsum(e, *arrays)) <= 1e-12
