@@ -299,7 +299,7 @@ static comet_status_t run_plan(const Plan &P, const void *const *inputs, void *o
                 ProfScope ps(PK_SPLIT, stream);
                 e = launch_gemm_split(g, w + st.ws_parts_a, w + st.ws_parts_b, st.kpad, sc_a, sc_b,
                                       P.opts.kc, es, P.opts.debug_flags, stream, 0, st.ksplit,
-                                      reinterpret_cast<float *>(w + st.ws_ksplit));
+                                      reinterpret_cast<float *>(w + st.ws_ksplit), (int64_t)st.ksplit_bytes);
                 if (e != cudaSuccess) return cuda_status(e, "split gemm kernel");
             }
         }
@@ -547,7 +547,7 @@ static comet_status_t run_host_pipe(const Plan &P, int n_calls, const void *cons
             } else {
                 ProfScope ps(PK_SPLIT, s);
                 e = launch_gemm_split(g, pa, pb, st.kpad, sa, sb, P.opts.kc, (int)es, P.opts.debug_flags, s, 0,
-                                      st.ksplit, reinterpret_cast<float *>(w + st.ws_ksplit));
+                                      st.ksplit, reinterpret_cast<float *>(w + st.ws_ksplit), (int64_t)st.ksplit_bytes);
             }
             if (e != cudaSuccess) return cuda_status(e, "host pipeline gemm");
             if (h.blockwise) {   // this block's result back as soon as it is done

@@ -31,6 +31,8 @@
 #include <cudaTypedefs.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "launch.h"
 #include "params.h"
 #include "sm100.cuh"
@@ -55,10 +57,13 @@ constexpr int MAX_KC = 1024;                    // exactness limit of the hh chu
 
 struct SplitArgs {
     uint32_t m_tiles, n_tiles, nkb;
+    uint32_t tile0, ntiles;      // the launch's output tiles: tile0 .. tile0 + ntiles - 1
+    uint32_t items;              // work items: ntiles x ksplit
     uint32_t kc_blocks;          // K blocks (of BK) per exact chunk
     uint32_t ksplit;             // K slices (1 = whole K per tile; > 1: FP32 partials to `partial`)
     uint32_t kslice_blocks;      // K blocks per slice
-    float *partial;              // ksplit x N x M partial sums (scaled by 2^(eA+eB)), m fastest
+    float *partial;              // ksplit x ntiles tiles of BM x BN partial sums (scaled by
+                                 // 2^(eA+eB)), [slice][tile][column][row], row fastest
     DbgRange dbg_p;              // debug builds: the partial sums' buffer
     int debug_flags;
     const void *scale_a;         // bits of max |A|, max |B| (input precision)
@@ -82,6 +87,18 @@ __device__ __forceinline__ int exp_of_max(const void *bits) {
     }
 }
 
+// output tile -> (m tile, n tile): bands of 16 m-tiles, n-major inside a band, for L2 reuse
+__device__ __forceinline__ void split_tile_coords(uint32_t tile, uint32_t m_tiles, uint32_t n_tiles, uint32_t &mt,
+                                                  uint32_t &nt) {
+    const uint32_t G = 16;
+    const uint32_t band = tile / (G * n_tiles);
+    const uint32_t base = band * G;
+    const uint32_t g = min(G, m_tiles - base);
+    const uint32_t r = tile - band * G * n_tiles;
+    mt = base + r % g;
+    nt = r / g;
+}
+
 template <typename TOut, bool KSPLIT>
 __global__ void __launch_bounds__(split::THREADS, 1)
     gemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -101,15 +118,15 @@ __global__ void __launch_bounds__(split::THREADS, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t tmo = (uint64_t)p.timeout_ns;
-    const uint32_t n_tiles_total = x.m_tiles * x.n_tiles * (KSPLIT ? x.ksplit : 1u);
-    // work item t: K slice t / (m_tiles n_tiles), output tile t % (m_tiles n_tiles)
+    const uint32_t n_tiles_total = x.items;
+    // work item t: K slice t / ntiles of output tile tile0 + t % ntiles
     auto kslice = [&](uint32_t t, uint32_t &kb0, uint32_t &kb1) -> uint32_t {
         if constexpr (!KSPLIT) {
             kb0 = 0;
             kb1 = x.nkb;
             return 0;
         } else {
-            const uint32_t ks = t / (x.m_tiles * x.n_tiles);
+            const uint32_t ks = t / x.ntiles;
             kb0 = ks * x.kslice_blocks;
             kb1 = min(x.nkb, kb0 + x.kslice_blocks);
             return ks;
@@ -136,16 +153,10 @@ __global__ void __launch_bounds__(split::THREADS, 1)
         *abort_flag = 1;
         atomicExch(p.status, (int)COMET_ERR_TIMEOUT);
     };
-    // tile t -> (m tile, n tile): bands of 16 m-tiles, n-major inside a band, for L2 reuse
+    // work item t -> (m tile, n tile) of its output tile
     auto tile_coords = [&](uint32_t t, uint32_t &mt, uint32_t &nt) {
-        if constexpr (KSPLIT) t %= x.m_tiles * x.n_tiles;
-        const uint32_t G = 16;
-        uint32_t band = t / (G * x.n_tiles);
-        uint32_t base = band * G;
-        uint32_t g = min(G, x.m_tiles - base);
-        uint32_t r = t - band * G * x.n_tiles;
-        mt = base + r % g;
-        nt = r / g;
+        if constexpr (KSPLIT) t %= x.ntiles;
+        split_tile_coords(x.tile0 + t, x.m_tiles, x.n_tiles, mt, nt);
     };
 
     if (warp == 0) {
@@ -284,15 +295,16 @@ __global__ void __launch_bounds__(split::THREADS, 1)
             }
             if (dead) continue;
             const uint32_t m = mt * BM + quad * 32 + lane;
-            if constexpr (KSPLIT) {   // K slice partial: scaled sums to P[ks][n][m] (m fastest, coalesced)
+            if constexpr (KSPLIT) {   // K slice partial: scaled sums to the tile's slot, row fastest (coalesced)
                 if (m < p.M) {
                     const uint32_t n_valid = min((uint32_t)BN, p.N - nt * BN);
                     const int n_here = (int)min(128u, n_valid > (uint32_t)(half * 128) ? n_valid - half * 128 : 0u);
                     const float sc = (float)ldexp(1.0, e_sum);
-                    float *P = x.partial + ((size_t)ks * p.N + nt * BN + half * 128) * p.M + m;
+                    float *P = x.partial + ((size_t)(ks * x.ntiles + t % x.ntiles) * BN + half * 128) * BM +
+                               (quad * 32 + lane);
 #pragma unroll
                     for (int j = 0; j < 128; ++j)
-                        if (j < n_here && dbg_ok(x.dbg_p, P + (size_t)j * p.M, 4, p.status)) P[(size_t)j * p.M] = sc * S[j];
+                        if (j < n_here && dbg_ok(x.dbg_p, P + (size_t)j * BM, 4, p.status)) P[(size_t)j * BM] = sc * S[j];
                 }
                 continue;
             }
@@ -326,17 +338,23 @@ __global__ void __launch_bounds__(split::THREADS, 1)
     if (warp == 1) tmem_dealloc(tmem_base, TMEM_COLS);
 }
 
-// K-slice partials -> C: C[m, n] = alpha * sum_ks P[ks][n][m] (+ beta C), through C's strides
+// K-slice partials -> C for the launch's tiles: C[m, n] = alpha * sum_ks P[ks][tile][n][m]
+// (+ beta C), through C's strides; one thread per element of a tile
 template <typename TOut>
-__global__ void __launch_bounds__(256) split_reduce_kernel(const GemmParams p, const float *P, uint32_t ksplit,
-                                                           const DbgRange dbg_p) {
+__global__ void __launch_bounds__(256) split_reduce_kernel(const GemmParams p, const SplitArgs x) {
+    using namespace split;
     const uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x;
-    if (i >= (uint64_t)p.M * p.N) return;
-    const uint32_t n = (uint32_t)(i / p.M), m = (uint32_t)(i - (uint64_t)n * p.M);
+    if (i >= (uint64_t)x.ntiles * BM * BN) return;
+    const uint32_t jt = (uint32_t)(i / (BM * BN)), e = (uint32_t)(i - (uint64_t)jt * (BM * BN));
+    const uint32_t nl = e / BM, ml = e - nl * BM;
+    uint32_t mt, nt;
+    split_tile_coords(x.tile0 + jt, x.m_tiles, x.n_tiles, mt, nt);
+    const uint32_t m = mt * BM + ml, n = nt * BN + nl;
+    if (m >= p.M || n >= p.N) return;
     double s = 0.0;
-    for (uint32_t k = 0; k < ksplit; ++k) {
-        const float *q = P + ((size_t)k * p.N + n) * p.M + m;
-        if (dbg_ok(dbg_p, q, 4, p.status)) s += (double)*q;
+    for (uint32_t k = 0; k < x.ksplit; ++k) {
+        const float *q = x.partial + ((size_t)(k * x.ntiles + jt) * BN + nl) * BM + ml;
+        if (dbg_ok(x.dbg_p, q, 4, p.status)) s += (double)*q;
     }
     int64_t a, cm, b, cn;
     radix_offsets(p.ma, m, a, cm);
@@ -403,10 +421,41 @@ static void launch_split_kernel(const CUtensorMap &ta, const CUtensorMap &tb, co
     gemm_split_kernel<TOut, KSPLIT><<<ctas, split::THREADS, split::SMEM_BYTES, s>>>(ta, tb, p, x);
 }
 
+// one launch over output tiles tile0 .. tile0 + ntiles - 1 in k K slices (k > 1: FP32 partials
+// of every slice, then the reduce kernel)
+static cudaError_t launch_range(const CUtensorMap &ta, const CUtensorMap &tb, const GemmParams &p, SplitArgs x,
+                                uint32_t tile0, uint32_t ntiles, uint32_t k, int out_bytes, int max_ctas,
+                                cudaStream_t s) {
+    using namespace split;
+    x.tile0 = tile0;
+    x.ntiles = ntiles;
+    x.kslice_blocks = (x.nkb + k - 1) / k;    // at least one K block per slice
+    x.ksplit = (x.nkb + x.kslice_blocks - 1) / x.kslice_blocks;
+    x.items = ntiles * x.ksplit;
+    x.dbg_p = dbg_range(x.partial, x.ksplit > 1 ? (int64_t)x.ksplit * ntiles * BM * BN * 4 : 0);
+    int ctas = sm_count();
+    if (max_ctas > 0 && max_ctas < ctas) ctas = max_ctas;
+    if ((uint32_t)ctas > x.items) ctas = (int)x.items;
+    if (out_bytes == 8) {
+        if (x.ksplit > 1) launch_split_kernel<double, true>(ta, tb, p, x, ctas, s);
+        else launch_split_kernel<double, false>(ta, tb, p, x, ctas, s);
+    } else {
+        if (x.ksplit > 1) launch_split_kernel<float, true>(ta, tb, p, x, ctas, s);
+        else launch_split_kernel<float, false>(ta, tb, p, x, ctas, s);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || x.ksplit == 1) return e;
+    const uint64_t n = (uint64_t)ntiles * BM * BN;
+    const uint32_t blocks = (uint32_t)((n + 255) / 256);
+    if (out_bytes == 8) split_reduce_kernel<double><<<blocks, 256, 0, s>>>(p, x);
+    else split_reduce_kernel<float><<<blocks, 256, 0, s>>>(p, x);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gemm_split(const GemmParams &p, const void *parts_a, const void *parts_b,
                               int64_t kpad, const void *scale_a, const void *scale_b, int64_t kc,
                               int out_bytes, int debug_flags, cudaStream_t s, int max_ctas,
-                              uint32_t ksplit, float *partial) {
+                              uint32_t ksplit, float *partial, int64_t partial_bytes) {
     using namespace split;
     if (p.M == 0 || p.N == 0) return cudaSuccess;
     CUtensorMap ta, tb;
@@ -422,29 +471,23 @@ cudaError_t launch_gemm_split(const GemmParams &p, const void *parts_a, const vo
     x.debug_flags = debug_flags;
     x.scale_a = scale_a;
     x.scale_b = scale_b;
-    if (ksplit < 1 || !partial) ksplit = 1;
-    x.kslice_blocks = (x.nkb + ksplit - 1) / ksplit;    // at least one K block per slice
-    x.ksplit = (x.nkb + x.kslice_blocks - 1) / x.kslice_blocks;
     x.partial = partial;
-    x.dbg_p = dbg_range(partial, (int64_t)x.ksplit * p.N * p.M * 4);
-    uint32_t tiles = x.m_tiles * x.n_tiles * x.ksplit;
-    int ctas = sm_count();
-    if (max_ctas > 0 && max_ctas < ctas) ctas = max_ctas;
-    if ((uint32_t)ctas > tiles) ctas = (int)tiles;
-    if (out_bytes == 8) {
-        if (x.ksplit > 1) launch_split_kernel<double, true>(ta, tb, p, x, ctas, s);
-        else launch_split_kernel<double, false>(ta, tb, p, x, ctas, s);
-    } else {
-        if (x.ksplit > 1) launch_split_kernel<float, true>(ta, tb, p, x, ctas, s);
-        else launch_split_kernel<float, false>(ta, tb, p, x, ctas, s);
+    const uint32_t tiles = x.m_tiles * x.n_tiles;
+    const int64_t tile_bytes = (int64_t)BM * BN * 4;
+    if (ksplit > 1 && partial && (int64_t)ksplit * tiles * tile_bytes <= partial_bytes)   // every tile in K slices
+        return launch_range(ta, tb, p, x, 0, tiles, ksplit, out_bytes, max_ctas, s);
+    // whole-K tiles in full waves over the SMs, then a partial last wave in K slices (a
+    // stream-K tail): its tiles' slices fill the SMs the wave would leave idle
+    const uint32_t sms = (uint32_t)(max_ctas > 0 ? std::min(max_ctas, sm_count()) : sm_count());
+    const uint32_t tail = tiles % sms;
+    uint32_t tsplit = 1;
+    if (tiles > sms && tail > 0 && 2 * tail <= sms) tsplit = std::min({4u, sms / tail, x.nkb});
+    if (tsplit > 1 && partial && (int64_t)tsplit * tail * tile_bytes <= partial_bytes) {
+        cudaError_t e = launch_range(ta, tb, p, x, 0, tiles - tail, 1, out_bytes, max_ctas, s);
+        if (e != cudaSuccess) return e;
+        return launch_range(ta, tb, p, x, tiles - tail, tail, tsplit, out_bytes, max_ctas, s);
     }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || x.ksplit == 1) return e;
-    const uint64_t n = (uint64_t)p.M * p.N;
-    const uint32_t blocks = (uint32_t)((n + 255) / 256);
-    if (out_bytes == 8) split_reduce_kernel<double><<<blocks, 256, 0, s>>>(p, partial, x.ksplit, x.dbg_p);
-    else split_reduce_kernel<float><<<blocks, 256, 0, s>>>(p, partial, x.ksplit, x.dbg_p);
-    return cudaGetLastError();
+    return launch_range(ta, tb, p, x, 0, tiles, 1, out_bytes, max_ctas, s);
 }
 
 }  // namespace comet

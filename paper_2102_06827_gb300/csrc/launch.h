@@ -26,12 +26,13 @@ cudaError_t launch_absmax2(const void *x0, int64_t n0, const void *x1, int64_t n
 // the same over the r.total elements of a strided view at offsets r (digit strides s0)
 cudaError_t launch_absmax_view(const void *x, const Radix &r, int elem_bytes, void *out_bits, cudaStream_t s);
 
-// ksplit > 1: K sliced over more work items, FP32 partials in `partial` (ksplit x M x N floats)
-// summed by a reduce kernel into C
+// ksplit > 1: K sliced over more work items, FP32 partials in `partial` (ksplit x tiles x
+// 128 x 256 floats) summed by a reduce kernel into C.  ksplit = 1: whole-K tiles, except that a
+// partial last wave over the SMs runs in K slices when its partials fit `partial_bytes`.
 cudaError_t launch_gemm_split(const GemmParams &p, const void *parts_a, const void *parts_b,
                               int64_t kpad, const void *scale_a, const void *scale_b, int64_t kc,
                               int out_bytes, int debug_flags, cudaStream_t s, int max_ctas,
-                              uint32_t ksplit = 1, float *partial = nullptr);
+                              uint32_t ksplit = 1, float *partial = nullptr, int64_t partial_bytes = 0);
 
 cudaError_t launch_gemm_emu(const GemmParams &p, const void *parts_a, const void *parts_b, int64_t kpad,
                             const void *scale_a, const void *scale_b, int debug_flags, cudaStream_t s,

@@ -1054,12 +1054,18 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
             const int64_t nkb = (Kx + 31) / 32;
             int64_t k = opts.ksplit > 1 ? opts.ksplit
                                         : std::min<int64_t>({(152 + tiles - 1) / tiles, nkb / 8, 16});
-            while (k > 1 && (double)k * rows_a * rows_b * 4 > 256.0 * (1 << 20)) --k;
+            while (k > 1 && (double)k * tiles * 128 * 256 * 4 > 256.0 * (1 << 20)) --k;
             st.ksplit = (uint32_t)std::max<int64_t>(1, std::min<int64_t>(k, nkb));
         }
         st.ws_ksplit = parts_base + ba + bb;
-        const size_t bk = st.ksplit > 1 ? align((size_t)st.ksplit * rows_a * rows_b * 4) : 0;
-        parts_max = std::max(parts_max, ba + bb + bk);
+        // partials: every tile's K slices (128 x 256 floats per tile and slice), or with whole-K
+        // tiles the slices of a partial last wave over 152 SMs (at most 152 tile slices)
+        const int64_t tiles = ((rows_a + 127) / 128) * ((rows_b + 255) / 256);
+        size_t bk = 0;
+        if (st.ksplit > 1) bk = (size_t)st.ksplit * tiles * 128 * 256 * 4;
+        else if (st.kernel == KK_GEMM_SPLIT && tiles > 152) bk = (size_t)152 * 128 * 256 * 4;
+        st.ksplit_bytes = bk;
+        parts_max = std::max(parts_max, ba + bb + align(bk));
     }
     for (auto &st : P->steps) {
         if (st.kernel == KK_REDUCE) {   // y[kept] = sum over the private labels of the operand

@@ -74,6 +74,7 @@ struct Step {
     int64_t kpad = 0;
     uint32_t ksplit = 1;         // split GEMM: K slices per output tile
     size_t ws_ksplit = 0;        // workspace offset of the slices' FP32 partials
+    size_t ksplit_bytes = 0;     // their size (K slices of every tile, or of a partial last wave)
     // precomputed parameter blocks (pointers filled at launch)
     GemmParams gemm;             // for both GEMM kernels (offsets in elements)
     XposeParams pre_a, pre_b;    // split pre-passes (A then B operand)
