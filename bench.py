@@ -976,7 +976,12 @@ def main():
     ms_total = max_over_ranks(e0.elapsed_time(e1))
     ms_step = ms_total / a.steps
     value = world * flops * a.steps / (ms_total * 1e-3) / 1e9
-    launches = sum(v[0] for v in prof.values())
+    # kernels, not profiler scopes: a split GEMM scope launches the whole-K kernel, and with a
+    # stream-K tail the K-sliced kernel and its reduce as well (with K slices throughout: the
+    # sliced kernel and the reduce)
+    st0 = plan.info["steps"][0]
+    per_gemm = 3 if st0.get("tail_slices", 1) > 1 else 2 if st0.get("ksplit", 1) > 1 else 1
+    launches = sum(v[0] for k, v in prof.items()) + (per_gemm - 1) * prof.get("gemm_split_bf16", (0, 0.0))[0]
     g_launch, g_ms = prof.get("gemm_split_bf16", (0, 0.0))
     p_launch, p_ms = prof.get("split_prepass", (0, 0.0))
     gemm_ms = g_ms / max(1, g_launch)

@@ -1064,6 +1064,14 @@ comet_status_t build_plan(const char *expr, const comet_extent_t *extents, int n
         size_t bk = 0;
         if (st.ksplit > 1) bk = (size_t)st.ksplit * tiles * 128 * 256 * 4;
         else if (st.kernel == KK_GEMM_SPLIT && tiles > 152) bk = (size_t)152 * 128 * 256 * 4;
+        // the launch's tail rule on a 152-SM GB300 (it applies the rule to the device's own count)
+        st.tail_tiles = 0;
+        st.tail_slices = 1;
+        if (st.kernel == KK_GEMM_SPLIT && st.ksplit == 1 && tiles > 152 && tiles % 152 != 0 &&
+            2 * (tiles % 152) <= 152) {
+            st.tail_tiles = (uint32_t)(tiles % 152);
+            st.tail_slices = (uint32_t)std::min<int64_t>({4, 152 / (tiles % 152), (Kx + 31) / 32});
+        }
         st.ksplit_bytes = bk;
         parts_max = std::max(parts_max, ba + bb + align(bk));
     }
@@ -1256,6 +1264,8 @@ std::string describe_plan(const Plan &P) {
               << ",\"cost_s\":" << s.form.cost << ",\"pre_bytes\":" << s.form.pre_bytes
               << ",\"eff_store\":" << s.form.eff_store << ",\"flops\":" << s.flops
               << ",\"ksplit\":" << s.ksplit;
+            if (s.kernel == KK_GEMM_SPLIT)
+                o << ",\"tail_tiles\":" << s.tail_tiles << ",\"tail_slices\":" << s.tail_slices;
         }
         o << "}";
     }

@@ -75,6 +75,8 @@ struct Step {
     uint32_t ksplit = 1;         // split GEMM: K slices per output tile
     size_t ws_ksplit = 0;        // workspace offset of the slices' FP32 partials
     size_t ksplit_bytes = 0;     // their size (K slices of every tile, or of a partial last wave)
+    uint32_t tail_tiles = 0, tail_slices = 1;   // whole-K split GEMM on 152 SMs: the partial last
+                                                // wave's tiles and their K slices (1 = no tail split)
     // precomputed parameter blocks (pointers filled at launch)
     GemmParams gemm;             // for both GEMM kernels (offsets in elements)
     XposeParams pre_a, pre_b;    // split pre-passes (A then B operand)
