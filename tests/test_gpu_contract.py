@@ -222,6 +222,26 @@ def test_timeout_surfaces_and_context_survives(comet):
     assert np.array_equal(C, oracle.einsum(e, *arrays))
 
 
+@pytest.mark.parametrize("mt,nt,tail,slices", [(17, 9, 1, 4), (19, 12, 76, 2), (25, 8, 48, 3), (23, 10, 78, 1)])
+def test_split_stream_k_tail(comet, mt, nt, tail, slices):
+    # whole-K tiles in full waves over 152 SMs, the partial last wave in K slices (stream-K
+    # tail, up to half the SMs): ragged M and N so that tail tiles hold edges; integers stay
+    # exact through the slices' FP32 partials and the reduce, alpha and += included
+    e = "C[m,n] = A[m,k] * B[k,n]"
+    ext = dict(m=128 * mt - 5, n=256 * nt - 7, k=300)
+    p = comet.Plan(e, ext, "f32", precision="split_bf16")
+    st = p.info["steps"][0]
+    assert (st["ksplit"], st["tail_tiles"], st["tail_slices"]) == (1, tail if slices > 1 else 0, slices)
+    arrays = inputs(e, ext, 15)
+    C, _ = run(comet, e, ext, arrays, np.float32, precision="split_bf16")
+    assert normwise(C, oracle.einsum(e, *arrays)) <= TOL_SPLIT
+    ints = inputs(e, ext, 16, kind="int", lo=-2, hi=2)
+    C0 = synth.tensor((ext["m"], ext["n"]), 16, 7, kind="int")
+    C, _ = run(comet, "C[m,n] += 2.0 * A[m,k] * B[k,n]", ext, ints, np.float32, precision="split_bf16",
+               out_init=C0)
+    assert np.array_equal(C, C0 + 2.0 * oracle.einsum(e, *ints))
+
+
 @pytest.mark.parametrize("ksplit", [0, 3, 16])
 def test_split_k_slices(comet, ksplit):
     # a GEMM with few output tiles: K sliced over more work items, FP32 partials summed by a
