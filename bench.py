@@ -999,7 +999,10 @@ def main():
                 "peak_source": peak_src,
                 "peak_sustained": peaks.get("bf16_tflops_sustained") if peaks else None,
                 "frac_of_sustained": achieved / peaks["bf16_tflops_sustained"] if peaks else None,
-                "achieved_counts": "6 BF16 products x 2*M*N*K per launch (M=N=K=12288)",
+                "achieved_counts": "6 BF16 products x 2*M*N*K per GEMM (M=N=K=12288)",
+                "gemm_launches": (f"{st0.get('tail_tiles', 0)} tail tiles in {st0.get('tail_slices', 1)} K slices "
+                                  "after the whole-K waves, then the reduce" if st0.get("tail_slices", 1) > 1
+                                  else "one whole-K launch"),
                 "ms_per_launch": gemm_ms,
                 "effective_fp32_tflops": flops / (gemm_ms * 1e-3) / 1e12}
     # the cuBLAS peak was taken at its own clocks: time x SM clock makes the two comparable
