@@ -206,3 +206,13 @@ def test_full_workload_sampled(comet):
         assert abs(got[b] - ref) <= 2e-5 * abs(ref), (b, got[b], ref)
     del buf, ebuf, ws
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dtype,tol", [(np.float64, 1e-12), (np.float32, 2e-5)])
+def test_medium_blocks_of_the_workload_range(comet, dtype, tol):
+    # blocks from the middle of the workload's extent range (16..20 per label): the FP64 FMA
+    # kernel's 4 x 4 register tiles and the FP32 tensor-core path's pair-tiles with ragged
+    # edges along every label, against the oracle
+    exts = [dict(a=17, b=19, c=16, i=18, j=20, k=17, d=19), dict(a=20, b=16, c=18, i=17, j=16, k=19, d=33)]
+    got, ref, plan = run(comet, exts, dtype, 5)
+    assert np.all(np.abs(got - ref) <= tol * np.abs(ref))
